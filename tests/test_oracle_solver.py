@@ -1,0 +1,68 @@
+"""Pins of the oracle's Gauss-Newton-Krylov loop (CPU only).
+
+The full solve has no closed form (beta > 0 biases the minimiser away from the
+ground-truth velocity), so its parity is pinned by properties only:
+* the objective decreases monotonically and the loop stops at the requested
+  relative gradient reduction (§3.4.1 stopping test);
+* P_REG and P_2L (CHEB and nested PCG) reach the same minimiser, and P_2L
+  needs fewer fine-grid Hessian matvecs than P_REG (§4.2.2);
+* beta continuation rescales the Chebyshev bounds as (e - 1) * beta_old /
+  beta_new (§3.4.2, §4.2.1).
+"""
+
+import numpy as np
+import pytest
+
+from oracle.problem import Problem
+from oracle.solver import Solver
+from paper_1604_02153_gb300 import inputs
+
+
+def config1(n, nt=4, beta=1e-2):
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    return m_R, m_T, vstar
+
+
+@pytest.fixture(scope="module")
+def solves():
+    n = 32
+    m_R, m_T, _ = config1(n)
+    out = {}
+    for key, pc, pcs in [("REG", "REG", "cheb"), ("2L-cheb", "2L", "cheb"), ("2L-pcg", "2L", "pcg")]:
+        S = Solver(Problem(m_R, m_T, 4, 1e-2), precond=pc, pc_solver=pcs)
+        v, info = S.solve(np.zeros((2, n, n)), 1e-3)
+        out[key] = (v, info)
+    return out
+
+
+def test_monotone_decrease_and_stop(solves):
+    for key, (v, info) in solves.items():
+        Js = [r["J"] for r in info["log"]]
+        assert all(Js[i + 1] < Js[i] for i in range(len(Js) - 1)), key
+        assert info["gnorm_rel"] <= 1e-3, key
+        assert not info["line_search_fail"], key
+
+
+def test_preconditioners_agree_and_two_level_saves_matvecs(solves):
+    vr = solves["REG"][0]
+    for key in ("2L-cheb", "2L-pcg"):
+        v = solves[key][0]
+        assert np.linalg.norm(v - vr) / np.linalg.norm(vr) < 2e-2, key
+    assert solves["2L-cheb"][1]["matvecs"] < solves["REG"][1]["matvecs"]
+
+
+def test_beta_rescales_chebyshev_bounds():
+    n = 32
+    m_R, m_T, _ = config1(n)
+    S = Solver(Problem(m_R, m_T, 4, 1e-1), precond="2L")
+    e1 = dict(S.estimate_eigenvalues())
+    S.set_beta(1e-2)
+    assert abs((S.eig["emax"] - 1) - 10 * (e1["emax"] - 1)) < 1e-12 * S.eig["emax"]
+    # the analytic e_min formula at the new beta equals the rescaled one
+    S2 = Solver(Problem(m_R, m_T, 4, 1e-2), precond="2L")
+    e2 = S2.estimate_eigenvalues()
+    assert abs(e2["emin"] - S.eig["emin"]) < 1e-12
+    # and the rescaled e_max is close to a fresh estimate (eigenvalue
+    # estimates scale with 1/beta, §4.2.1)
+    assert abs(e2["emax"] - S.eig["emax"]) / e2["emax"] < 0.05
