@@ -1,0 +1,221 @@
+/*
+ * reg.h - C ABI of the GB300 semi-Lagrangian Gauss-Newton-Krylov registration
+ * library (libregnk.so).
+ *
+ * Method: Mang & Biros, "A semi-Lagrangian two-level preconditioned
+ * Newton-Krylov solver for constrained diffeomorphic image registration"
+ * (arXiv 1604.02153). The library minimises, over a stationary velocity v,
+ *     J[v] = 1/2 ||m_1 - m_R||^2_L2 + beta/2 <v, A v>_L2          (eq. varopt:objective)
+ * subject to the transport equation d_t m + grad m . v = 0, m(0) = m_T, with
+ * periodic boundary conditions on the 2-torus [0, 2 pi)^2 (§2, compressible
+ * case: no divergence constraint, K = I).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid     n1 x n2 nodes, h_i = 2 pi / n_i, node (i, j) at (i h_1, j h_2).
+ *          n1, n2 are powers of two in [32, 2048]. (§3.2)
+ * Layout   a scalar field is n1*n2 contiguous float32, row-major with x_1
+ *          fastest: u[j*n1 + i]. A vector field (v, v~, g, H v~) is two
+ *          scalar fields back to back (structure of arrays): component 1 at
+ *          offset 0, component 2 at offset n1*n2.
+ * Memory   every float pointer is a DEVICE pointer on the context's device
+ *          unless its comment says "host". The caller owns all field buffers;
+ *          the library copies what it keeps and never frees caller memory.
+ *          Device buffers must be 16-byte aligned (torch allocations are).
+ * Streams  every call runs on the stream set by reg_set_stream (default: the
+ *          legacy default stream). Calls that return a host scalar or a
+ *          status that depends on device data synchronise that stream;
+ *          the others are asynchronous with respect to the host.
+ * Errors   every call returns a reg_status. REG_EINVAL leaves the context
+ *          unchanged. After REG_ECUDA or REG_ENOMEM the context must be
+ *          destroyed. reg_last_error() gives a human-readable message.
+ * Threads  a context is not thread-safe; use one context per host thread.
+ * CPU      there is no CPU fallback: if the CUDA runtime or an sm_103a device
+ *          is missing, reg_create returns REG_ECUDA.
+ */
+#ifndef REGNK_REG_H
+#define REGNK_REG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reg_ctx reg_ctx;
+
+typedef enum {
+  REG_OK = 0,
+  REG_EINVAL = 1,       /* bad argument (size, null pointer, option value)      */
+  REG_ENOMEM = 2,       /* device allocation failed                             */
+  REG_ECUDA = 3,        /* CUDA runtime or kernel launch error                  */
+  REG_ESTATE = 4,       /* call order violated (e.g. no images set)             */
+  REG_ENOTCONV = 5,     /* reg_solve hit max_newton before the tolerance        */
+  REG_ELINESEARCH = 6,  /* Armijo backtracking exhausted (§3.4.1)               */
+  REG_ENEGCURV = 7,     /* PCG met p^T H p <= 0 and kept the last iterate       */
+  REG_ENONFINITE = 8,   /* a NaN/Inf reached a reduction                        */
+  REG_ETIMEOUT = 9      /* a bounded device wait gave up                        */
+} reg_status;
+
+/* Regularisation seminorm, eq. varopt:regv / eq. diffopregv:
+ * A = -Lap (H1), Lap^2 (H2), -Lap^3 (H3); spectral weights |k|^(2p). */
+enum { REG_H1 = 1, REG_H2 = 2, REG_H3 = 3 };
+/* Interpolation model (§3.5 "Interpolation"): C2 periodic cubic B-spline
+ * (the paper's model, default) or cubic Lagrange on raw samples (variant). */
+enum { REG_INTERP_SPLINE = 0, REG_INTERP_LAGRANGE = 1 };
+/* Preconditioner (§3.4.2): spectral P_REG = beta A, or two-level P_2L. */
+enum { REG_PC_REG = 0, REG_PC_2L = 1 };
+/* Coarse solver of P_2L (§3.4.2): CHEB(k) or nested PCG(eps). */
+enum { REG_PCSOLVER_CHEB = 0, REG_PCSOLVER_PCG = 1 };
+
+typedef struct { int n1, n2; } reg_grid;
+
+typedef struct {
+  int reg_norm;            /* REG_H1 (default) | REG_H2 | REG_H3                     */
+  int interp;              /* REG_INTERP_SPLINE (default) | REG_INTERP_LAGRANGE     */
+  int precond;             /* REG_PC_2L (default) | REG_PC_REG                       */
+  int pc_solver;           /* REG_PCSOLVER_CHEB (default) | REG_PCSOLVER_PCG         */
+  int cheb_iters;          /* k of CHEB(k), default 10 (§4.2.2)                      */
+  double pc_eps;           /* eps of PCG(eps), default 0.1 (§4.2.2)                  */
+  double gabs;             /* absolute ||g||_inf stop, default 1e-5 (§3.4.1)         */
+  int max_newton;          /* default 50                                             */
+  int max_pcg;             /* outer and nested PCG iteration cap, default 100        */
+  int lanczos_steps;       /* Lanczos steps for e_max, default 30 (§4.2.1)           */
+  double emax_safety;      /* e_max = largest Ritz value * this, default 1.05        */
+  unsigned long long lanczos_seed; /* SplitMix64 seed of the Lanczos start vector   */
+  int max_backtracks;      /* Armijo halvings, default 10                            */
+  double armijo_c1;        /* Armijo constant, default 1e-4                          */
+} reg_options;
+
+typedef struct {
+  int newton_iters;        /* accepted Newton steps                                  */
+  int pcg_iters;           /* outer PCG iterations, summed                           */
+  int matvecs;             /* fine-grid GN Hessian matvecs                           */
+  int coarse_matvecs;      /* coarse-grid GN data-term matvecs inside P_2L           */
+  int line_search_steps;   /* objective evaluations in Armijo backtracking           */
+  double J0, J;            /* objective at the initial guess and at the result       */
+  double gnorm_rel;        /* ||g||_inf / ||g_ref||_inf at the result                */
+  double gnorm_inf;        /* ||g||_inf at the result                                */
+  double gref_inf;         /* ||g(v = 0)||_inf, the reference of the relative test   */
+  double seconds;          /* host wall time of the call                             */
+  int status;              /* reg_status of the solve                                */
+} reg_info;
+
+/* Fills *opt with the defaults listed above. */
+reg_status reg_default_options(reg_options* opt);
+
+/* Creates a context for one registration problem on `grid` with nt
+ * semi-Lagrangian time steps (h_t = 1/nt, §3.2) and regularisation weight
+ * beta > 0, on the current CUDA device. opt may be NULL (defaults). The
+ * context allocates its workspace (fields, time histories, FFT buffers, the
+ * coarse grid of P_2L) on the device; *out receives the handle. */
+reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt,
+                      reg_ctx** out);
+
+/* Frees the context and its device workspace. NULL is accepted. */
+reg_status reg_destroy(reg_ctx* ctx);
+
+/* Sets the cudaStream_t (passed as void*) that later calls run on. */
+reg_status reg_set_stream(reg_ctx* ctx, void* cuda_stream);
+
+/* Copies the reference image m_R and the template image m_T (n1*n2 floats
+ * each, device) into the context (eq. varopt:objective). Invalidates every
+ * cached velocity-dependent quantity. */
+reg_status reg_set_images(reg_ctx* ctx, const float* m_R, const float* m_T);
+
+/* Changes beta (continuation). Chebyshev bounds are rescaled as
+ * (e - 1) * beta_old / beta_new, not recomputed (§3.4.2, §4.2.1). */
+reg_status reg_set_beta(reg_ctx* ctx, double beta);
+
+/* Semi-Lagrangian state solve (eq. state-pde-elim, §3.3.2): transports m0
+ * (n1*n2, device) by the stationary velocity v (2*n1*n2, device) from t = 0
+ * to t = 1 and writes m(1) to m1 (n1*n2, device). RK2 characteristic, cubic
+ * interpolation. Needs no images. */
+reg_status reg_transport(reg_ctx* ctx, const float* v, const float* m0, float* m1);
+
+/* Departure points of one time step (§3.3.2 "Tracing the Characteristic",
+ * Heun): X_D = x - h_t/2 (v(x) + v(x - h_t v(x))) for the forward-in-time
+ * equations and Y_D = x + h_t/2 (v(x) + v(x + h_t v(x))) for the backward
+ * ones. Written as displacements in cell units, (X_D - x)/h, to dX and dY
+ * (2*n1*n2 each, device, component 1 then 2). Either output may be NULL. */
+reg_status reg_departure_points(reg_ctx* ctx, const float* v, float* dX, float* dY);
+
+/* Periodic cubic interpolation (§3.5): out[x] = u(x + disp[x] * h), where
+ * disp (2*n1*n2, device) is in cell units and u (n1*n2, device) holds
+ * samples at the nodes. Uses the context's interpolation model. */
+reg_status reg_interpolate(reg_ctx* ctx, const float* u, const float* disp, float* out);
+
+/* Pseudospectral operators (§3.2, eq. diffopregv, eq. reg-precond, §3.4.2).
+ * `op` selects (in -> out, sizes in fields of n1*n2 floats):
+ *   REG_SPEC_GRAD     scalar -> vector   grad u (Nyquist zeroed)
+ *   REG_SPEC_DIV      vector -> scalar   div v  (Nyquist zeroed)
+ *   REG_SPEC_REG      vector -> vector   beta A v
+ *   REG_SPEC_REGPOW   vector -> vector   (beta A)^s v, k = 0 weight -> 1 (s < 0 or s = 1/2)
+ *   REG_SPEC_LOWPASS  vector -> vector   keep |k_i| < n_i/4
+ *   REG_SPEC_HIGHPASS vector -> vector   remove |k_i| < n_i/4
+ *   REG_SPEC_PREFILTER scalar -> scalar  periodic cubic B-spline coefficients
+ * `s` is used by REG_SPEC_REGPOW only. in and out must not alias. */
+enum { REG_SPEC_GRAD = 0, REG_SPEC_DIV = 1, REG_SPEC_REG = 2, REG_SPEC_REGPOW = 3,
+       REG_SPEC_LOWPASS = 4, REG_SPEC_HIGHPASS = 5, REG_SPEC_PREFILTER = 6 };
+reg_status reg_spectral(reg_ctx* ctx, int op, double s, const float* in, float* out);
+
+/* Spectral restriction of a vector field from the context grid to the grid
+ * (n1/2, n2/2) (cut-off filter at |k_i| < n_i/4 included) and prolongation
+ * back by zero padding (§3.4.2 "Restriction/Prolongation", "Filters").
+ * fine: 2*n1*n2 floats, coarse: 2*(n1/2)*(n2/2) floats, device. */
+reg_status reg_restrict(reg_ctx* ctx, const float* fine, float* coarse);
+reg_status reg_prolong(reg_ctx* ctx, const float* coarse, float* fine);
+
+/* Objective J (host double) and reduced gradient g = beta A v +
+ * int_0^1 lambda grad m dt (eq. control-elim, K = I) at v (device). g
+ * (2*n1*n2, device) may be NULL. Caches the state, adjoint characteristics
+ * and the time history of grad m for later Hessian matvecs at the same v.
+ * Synchronises the stream (returns a host scalar). */
+reg_status reg_objective_gradient(reg_ctx* ctx, const float* v, double* J, float* g);
+
+/* Objective only (state solve plus regularisation); *J is host. */
+reg_status reg_objective(reg_ctx* ctx, const float* v, double* J);
+
+/* Gauss-Newton Hessian matvec Hvt = H(v) vt = beta A vt + int_0^1 lambda~ grad m dt
+ * (eq. hessian-matvec with every lambda term dropped, §3.4.1 footnote, §3.5
+ * "Hessian"): incremental state solve forward, incremental adjoint solve
+ * backward, all device pointers of 2*n1*n2 floats. If v differs from the
+ * velocity cached by the last objective/gradient call (compared on the
+ * device), the velocity-dependent cache is rebuilt first; a stale result is
+ * never returned. Synchronises the stream for that comparison. */
+reg_status reg_hessian_matvec(reg_ctx* ctx, const float* v, const float* vt, float* Hvt);
+
+/* Applies the configured preconditioner inverse (P_REG^-1 or P_2L^-1,
+ * §3.4.2) at the cached velocity: z = P^-1 r (2*n1*n2 floats each, device).
+ * Requires a previous reg_objective_gradient. */
+reg_status reg_precond_apply(reg_ctx* ctx, const float* r, float* z);
+
+/* Solves H(v) x = rhs with PCG (§3.4.1; relative residual rtol, at most
+ * maxit iterations, zero initial guess) and the configured preconditioner
+ * at the velocity v. x, rhs: 2*n1*n2 floats, device. info (host) may be
+ * NULL; it receives pcg_iters, matvecs, coarse_matvecs and status. */
+reg_status reg_kkt_solve(reg_ctx* ctx, const float* v, const float* rhs, double rtol,
+                         int maxit, float* x, reg_info* info);
+
+/* Chebyshev bounds of P_2L's coarse split operator at v = 0 (§3.4.2
+ * "Eigenvalue Estimates"): e_max from Lanczos, e_min analytic. Host doubles.
+ * Computed on first use and cached; this call forces the estimate. */
+reg_status reg_eigen_bounds(reg_ctx* ctx, double* emin, double* emax);
+
+/* Inexact Gauss-Newton-Krylov solve (§3.4, §3.5): starting from v (device,
+ * 2*n1*n2, overwritten with the result), iterate until
+ * ||g||_inf / ||g(0)||_inf <= gtol or ||g||_inf <= gabs, PCG with forcing
+ * eta_k = min(0.5, ||g_k|| / ||g(0)||), Armijo backtracking. info (host)
+ * may be NULL. Returns REG_OK on convergence, REG_ENOTCONV or
+ * REG_ELINESEARCH otherwise (v then holds the last accepted iterate). */
+reg_status reg_solve(reg_ctx* ctx, float* v, double gtol, reg_info* info);
+
+/* Euclidean inner product of two float32 device vectors of length n,
+ * accumulated in float64 (the Krylov and line-search reductions); *out host. */
+reg_status reg_dot(reg_ctx* ctx, const float* a, const float* b, long long n, double* out);
+
+/* Message of the last error on this context (never NULL). */
+const char* reg_last_error(const reg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REGNK_REG_H */

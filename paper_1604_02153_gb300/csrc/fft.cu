@@ -1,0 +1,428 @@
+// Hand-written shared-memory 2D real FFT fused with the pointwise spectral
+// multipliers of the pseudospectral discretisation (§3.2; eq. diffopregv;
+// eq. reg-precond; §3.4.2 restriction, prolongation and cut-off filters).
+//
+// A spectral operator out = F^-1[ sigma(k) F[in] ] runs as three kernels:
+//   1. rows_r2c : forward FFT along x_1 of every row. Two real rows are packed
+//                 into one complex line (z = a + i b) and separated after the
+//                 transform; the half spectrum k1 = 0..n1/2 is written line by
+//                 line (one line per k1, contiguous over the rows j).
+//   2. cols     : for each k1 line: forward FFT along x_2, multiply by
+//                 sigma(k1, k2) (combining several inputs and producing several
+//                 outputs where the operator needs it: grad, div), optional
+//                 resampling to a grid of half or double size (spectral
+//                 restriction / prolongation), inverse FFT along x_2.
+//   3. rows_c2r : inverse FFT along x_1, two rows per complex line, with an
+//                 optional addend fused into the store.
+// Each transform is a radix-4 Stockham autosort FFT in shared memory (plus a
+// final radix-2 pass for odd log2 n), with FP32 twiddles rounded from an FP64
+// host table. Normalisation (1/N of the input grid) is folded into sigma.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace regnk {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// Lines per block and threads per block of the FFT kernels, by log2 of the
+// line length: P lines of N complex values = at most 32 KB of shared memory.
+template <int LOGN>
+struct FftCfg {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int P = (4096 / N) < 16 ? ((4096 / N) < 1 ? 1 : 4096 / N) : 16;
+  static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
+};
+
+// In-place FFT of P lines of length N stored contiguously at s (line l at
+// s + l*N). All NT threads of the block take part; the caller synchronises
+// before (data written) and the routine ends with a barrier.
+template <int LOGN, int P, int NT, bool INV>
+__device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN;
+  constexpr int Q4 = N / 4;
+  constexpr int TOT4 = P * Q4;
+  constexpr int B4 = (TOT4 + NT - 1) / NT;
+  const int t = threadIdx.x;
+  int lns = 0;  // log2 of the current sub-transform size Ns
+#pragma unroll 1
+  for (int pass = 0; pass < LOGN / 2; ++pass) {
+    const int Ns = 1 << lns;
+    const int tws = LOGN - lns - 2;  // twiddle stride log2: N / (4 Ns)
+    float2 v[B4][4];
+    int base[B4];
+#pragma unroll
+    for (int b = 0; b < B4; ++b) {
+      const int q = t + b * NT;
+      if (TOT4 % NT == 0 || q < TOT4) {
+        const int l = q / Q4, j = q % Q4;
+        const int k = j & (Ns - 1);
+        const float2* x = s + l * N;
+        float2 a0 = x[j], a1 = x[j + Q4], a2 = x[j + 2 * Q4], a3 = x[j + 3 * Q4];
+        if (lns > 0) {
+          const float2 w1 = __ldg(tw + ((k << tws) & (N - 1)));
+          const float2 w2 = __ldg(tw + (((2 * k) << tws) & (N - 1)));
+          const float2 w3 = __ldg(tw + (((3 * k) << tws) & (N - 1)));
+          if (INV) {
+            a1 = cmulc(a1, w1); a2 = cmulc(a2, w2); a3 = cmulc(a3, w3);
+          } else {
+            a1 = cmul(a1, w1); a2 = cmul(a2, w2); a3 = cmul(a3, w3);
+          }
+        }
+        const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+        const float2 s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
+        v[b][0] = cadd(s02, s13);
+        v[b][1] = cadd(d02, d13);
+        v[b][2] = csub(s02, s13);
+        v[b][3] = csub(d02, d13);
+        base[b] = l * N + (j - k) * 4 + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B4; ++b) {
+      const int q = t + b * NT;
+      if (TOT4 % NT == 0 || q < TOT4) {
+        s[base[b]] = v[b][0];
+        s[base[b] + Ns] = v[b][1];
+        s[base[b] + 2 * Ns] = v[b][2];
+        s[base[b] + 3 * Ns] = v[b][3];
+      }
+    }
+    __syncthreads();
+    lns += 2;
+  }
+  if (LOGN & 1) {
+    constexpr int Q2 = N / 2;
+    constexpr int TOT2 = P * Q2;
+    constexpr int B2 = (TOT2 + NT - 1) / NT;
+    const int Ns = 1 << lns;
+    float2 v0[B2], v1[B2];
+    int base[B2];
+#pragma unroll
+    for (int b = 0; b < B2; ++b) {
+      const int q = t + b * NT;
+      if (TOT2 % NT == 0 || q < TOT2) {
+        const int l = q / Q2, j = q % Q2;
+        const int k = j & (Ns - 1);
+        const float2* x = s + l * N;
+        const float2 a0 = x[j];
+        float2 a1 = x[j + Q2];
+        if (lns > 0) {
+          const float2 w = __ldg(tw + k);  // N / (2 Ns) = 1 on the last pass
+          a1 = INV ? cmulc(a1, w) : cmul(a1, w);
+        }
+        v0[b] = cadd(a0, a1);
+        v1[b] = csub(a0, a1);
+        base[b] = l * N + (j - k) * 2 + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B2; ++b) {
+      const int q = t + b * NT;
+      if (TOT2 % NT == 0 || q < TOT2) {
+        s[base[b]] = v0[b];
+        s[base[b] + Ns] = v1[b];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1. forward row transforms: F fields of n2 rows of length N = n1.
+template <int LOGN>
+__global__ void __launch_bounds__(FftCfg<LOGN>::NT)
+k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__ spec,
+           long long sstride, int n2, const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, P = FftCfg<LOGN>::P, NT = FftCfg<LOGN>::NT;
+  extern __shared__ float2 sm[];
+  const int t = threadIdx.x;
+  const int row0 = blockIdx.x * 2 * P;
+  const float* src = in + (long long)blockIdx.y * fstride;
+  for (int q = t; q < P * N; q += NT) {
+    const int l = q >> LOGN, i = q & (N - 1);
+    const long long r = (long long)(row0 + 2 * l) * N + i;
+    sm[q] = make_float2(__ldg(src + r), __ldg(src + r + N));
+  }
+  __syncthreads();
+  fft_smem<LOGN, P, NT, false>(sm, tw);
+  float2* dst = spec + (long long)blockIdx.y * sstride;
+  constexpr int R = 2 * P;
+  for (int q = t; q < (N / 2 + 1) * R; q += NT) {
+    const int r = q % R, k = q / R, l = r >> 1;
+    const float2 Z = sm[l * N + k];
+    const float2 Zm = sm[l * N + ((N - k) & (N - 1))];
+    float2 X;
+    if (r & 1) {  // X_b = (Z - conj(Zm)) / (2i)
+      X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
+    } else {      // X_a = (Z + conj(Zm)) / 2
+      X = make_float2(0.5f * (Z.x + Zm.x), 0.5f * (Z.y - Zm.y));
+    }
+    dst[(long long)k * n2 + row0 + r] = X;
+  }
+}
+
+// 3. inverse row transforms (half spectrum -> real rows), optional addend.
+template <int LOGN>
+__global__ void __launch_bounds__(FftCfg<LOGN>::NT)
+k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
+           long long fstride, const float* __restrict__ add, long long astride, int n2,
+           const float2* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, P = FftCfg<LOGN>::P, NT = FftCfg<LOGN>::NT;
+  extern __shared__ float2 sm[];
+  const int t = threadIdx.x;
+  const int row0 = blockIdx.x * 2 * P;
+  const float2* src = spec + (long long)blockIdx.y * sstride;
+  for (int q = t; q < (N / 2 + 1) * P; q += NT) {
+    const int l = q % P, k = q / P;
+    const long long a = (long long)k * n2 + row0 + 2 * l;
+    float2 Xa = src[a], Xb = src[a + 1];
+    if (k == 0 || k == N / 2) {
+      Xa.y = 0.f;
+      Xb.y = 0.f;
+    }
+    sm[l * N + k] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
+    if (k > 0 && k < N / 2) sm[l * N + N - k] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
+  }
+  __syncthreads();
+  fft_smem<LOGN, P, NT, true>(sm, tw);
+  float* dst = out + (long long)blockIdx.y * fstride;
+  const float* ad = add ? add + (long long)blockIdx.y * astride : nullptr;
+  for (int q = t; q < P * N; q += NT) {
+    const int l = q >> LOGN, i = q & (N - 1);
+    const long long r = (long long)(row0 + 2 * l) * N + i;
+    float a = sm[q].x, b = sm[q].y;
+    if (ad) {
+      a += __ldg(ad + r);
+      b += __ldg(ad + r + N);
+    }
+    dst[r] = a;
+    dst[r + N] = b;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. column pass with the spectral multiplier.
+__device__ __forceinline__ float regpow(float beta, int p, float s, int k1, int k2) {
+  const float k2n = (float)k1 * (float)k1 + (float)k2 * (float)k2;
+  float g = k2n;
+  if (p == 2) g = k2n * k2n;
+  else if (p == 3) g = k2n * k2n * k2n;
+  if (s == 1.f) return beta * g;
+  if (g == 0.f) g = 1.f;
+  const float bg = beta * g;
+  if (s == -1.f) return 1.f / bg;
+  if (s == -0.5f) return 1.f / sqrtf(bg);
+  if (s == 0.5f) return sqrtf(bg);
+  return powf(bg, s);
+}
+
+// sigma_{o,c}(k1, k2) as a complex number; k1 >= 0, k2 signed; n1, n2 of the
+// grid the Nyquist and filter conditions refer to.
+__device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1, int k2) {
+  const bool nyq1 = (k1 == a.n1 / 2), nyq2 = (k2 == -a.n2 / 2);
+  const bool low = (k1 < a.n1 / 4) && (k2 < a.n2 / 4) && (k2 > -a.n2 / 4);
+  switch (a.op) {
+    case SPOP_SCALE:
+      return make_float2(1.f, 0.f);
+    case SPOP_GRAD:
+      if (o == 0) return make_float2(0.f, nyq1 ? 0.f : (float)k1);
+      return make_float2(0.f, nyq2 ? 0.f : (float)k2);
+    case SPOP_DIV:
+      if (c == 0) return make_float2(0.f, nyq1 ? 0.f : (float)k1);
+      return make_float2(0.f, nyq2 ? 0.f : (float)k2);
+    case SPOP_REGPOW:
+      return make_float2(regpow(a.beta, a.p, a.s, k1, k2), 0.f);
+    case SPOP_LOWPASS:
+      return make_float2(low ? 1.f : 0.f, 0.f);
+    case SPOP_HIGHPASS:
+      return make_float2(low ? 0.f : 1.f, 0.f);
+    case SPOP_REGPOW_HIGH:
+      return make_float2(low ? 0.f : regpow(a.beta, a.p, a.s, k1, k2), 0.f);
+    default:
+      return make_float2(0.f, 0.f);
+  }
+}
+
+template <int LOGI, int LOGO>
+struct ColCfg {
+  static constexpr int LM = LOGI > LOGO ? LOGI : LOGO;
+  static constexpr int NM = 1 << LM;
+  static constexpr int P = FftCfg<LM>::P;
+  static constexpr int NT = FftCfg<LM>::NT;
+};
+
+template <int LOGI, int LOGO>
+__global__ void __launch_bounds__(ColCfg<LOGI, LOGO>::NT) k_cols(ColArgs a) {
+  constexpr int NI = 1 << LOGI, NO = 1 << LOGO;
+  constexpr int NM = ColCfg<LOGI, LOGO>::NM;
+  constexpr int P = ColCfg<LOGI, LOGO>::P, NT = ColCfg<LOGI, LOGO>::NT;
+  extern __shared__ float2 sm[];
+  float2* bin = sm;                      // nin buffers of P x NM
+  float2* bout = sm + a.nin * P * NM;    // 1 buffer of P x NM
+  const int t = threadIdx.x;
+  const int line0 = blockIdx.x * P;
+  const int g = blockIdx.y;
+  const int nsmall = a.n1_in < a.n1_out ? a.n1_in : a.n1_out;
+  const bool resize = (NI != NO) || (a.n1_in != a.n1_out);
+  for (int c = 0; c < a.nin; ++c) {
+    const float2* src = a.in + (long long)(g * a.nin + c) * a.in_fstride;
+    for (int q = t; q < P * NI; q += NT) {
+      const int l = q >> LOGI, k2 = q & (NI - 1);
+      const int k1 = line0 + l;
+      const bool ok = k1 < a.nk1_out && (!resize || k1 < nsmall / 2);
+      bin[c * P * NM + l * NI + k2] = ok ? src[(long long)k1 * NI + k2] : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  for (int c = 0; c < a.nin; ++c) fft_smem<LOGI, P, NT, false>(bin + c * P * NM, a.tw_in);
+  for (int o = 0; o < a.nout; ++o) {
+    for (int q = t; q < P * NO; q += NT) {
+      const int l = q >> LOGO, ko = q & (NO - 1);
+      const int k1 = line0 + l;
+      const int k2 = signed_k(ko, NO);
+      bool ok = k1 < a.nk1_out && (!resize || k1 < nsmall / 2);
+      int ki = ko;
+      if (NO < NI) {          // restriction: drop the coarse Nyquist
+        ok = ok && (k2 != -NO / 2);
+        ki = k2 < 0 ? k2 + NI : k2;
+      } else if (NO > NI) {   // prolongation: zero-pad, fine modes |k2| >= NI/2 vanish
+        ok = ok && (k2 < NI / 2) && (k2 > -NI / 2);
+        ki = k2 < 0 ? k2 + NI : k2;
+      }
+      float2 acc = make_float2(0.f, 0.f);
+      if (ok) {
+        for (int c = 0; c < a.nin; ++c) {
+          const float2 sg = symbol(a, o, c, k1, k2);
+          acc = cadd(acc, cmul(bin[c * P * NM + l * NI + ki], sg));
+        }
+        acc = cscale(acc, a.scale);
+      }
+      bout[l * NO + ko] = acc;
+    }
+    __syncthreads();
+    fft_smem<LOGO, P, NT, true>(bout, a.tw_out);
+    float2* dst = a.out + (long long)(g * a.nout + o) * a.out_fstride;
+    for (int q = t; q < P * NO; q += NT) {
+      const int l = q >> LOGO, k2 = q & (NO - 1);
+      const int k1 = line0 + l;
+      if (k1 < a.nk1_out) dst[(long long)k1 * NO + k2] = bout[q];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+static int ilog2(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <typename K>
+static void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int LOGN>
+static void launch_r2c(const float* in, long long fstride, float2* spec, long long sstride,
+                       int n2, int F, const float2* tw, cudaStream_t st) {
+  using C = FftCfg<LOGN>;
+  const size_t smem = (size_t)C::P * C::N * sizeof(float2);
+  static bool init = false;
+  if (!init) { set_smem(k_rows_r2c<LOGN>, smem); init = true; }
+  dim3 grid(n2 / (2 * C::P), F);
+  k_rows_r2c<LOGN><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw);
+}
+
+template <int LOGN>
+static void launch_c2r(const float2* spec, long long sstride, float* out, long long fstride,
+                       const float* add, long long astride, int n2, int F, const float2* tw,
+                       cudaStream_t st) {
+  using C = FftCfg<LOGN>;
+  const size_t smem = (size_t)C::P * C::N * sizeof(float2);
+  static bool init = false;
+  if (!init) { set_smem(k_rows_c2r<LOGN>, smem); init = true; }
+  dim3 grid(n2 / (2 * C::P), F);
+  k_rows_c2r<LOGN><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw);
+}
+
+template <int LOGI, int LOGO>
+static void launch_cols(const ColArgs& a, int groups, cudaStream_t st) {
+  using C = ColCfg<LOGI, LOGO>;
+  const size_t smem = (size_t)(a.nin + 1) * C::P * C::NM * sizeof(float2);
+  static bool init = false;
+  if (!init) { set_smem(k_cols<LOGI, LOGO>, 3 * (size_t)C::P * C::NM * sizeof(float2)); init = true; }
+  dim3 grid((a.nk1_out + C::P - 1) / C::P, groups);
+  k_cols<LOGI, LOGO><<<grid, C::NT, smem, st>>>(a);
+}
+
+#define REGNK_LOG_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
+#define REGNK_RESTRICT_CASES(X) X(6) X(7) X(8) X(9) X(10) X(11)
+#define REGNK_PROLONG_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10)
+
+void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
+                  long long sstride, int F, const float2* tw, cudaStream_t st) {
+  switch (ilog2(n1)) {
+#define CASE(L) case L: launch_r2c<L>(in, fstride, spec, sstride, n2, F, tw, st); break;
+    REGNK_LOG_CASES(CASE)
+#undef CASE
+    default: break;
+  }
+}
+
+void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
+                  long long fstride, const float* add, long long astride, int F,
+                  const float2* tw, cudaStream_t st) {
+  switch (ilog2(n1)) {
+#define CASE(L) case L: launch_c2r<L>(spec, sstride, out, fstride, add, astride, n2, F, tw, st); break;
+    REGNK_LOG_CASES(CASE)
+#undef CASE
+    default: break;
+  }
+}
+
+void fft_cols(const ColArgs& a, int groups, cudaStream_t st) {
+  const int li = ilog2(a.n2_in), lo = ilog2(a.n2_out);
+  if (li == lo) {
+    switch (li) {
+#define CASE(L) case L: launch_cols<L, L>(a, groups, st); break;
+      REGNK_LOG_CASES(CASE)
+#undef CASE
+      default: break;
+    }
+  } else if (lo == li - 1) {
+    switch (li) {
+#define CASE(L) case L: launch_cols<L, L - 1>(a, groups, st); break;
+      REGNK_RESTRICT_CASES(CASE)
+#undef CASE
+      default: break;
+    }
+  } else if (lo == li + 1) {
+    switch (li) {
+#define CASE(L) case L: launch_cols<L, L + 1>(a, groups, st); break;
+      REGNK_PROLONG_CASES(CASE)
+#undef CASE
+      default: break;
+    }
+  }
+}
+
+}  // namespace regnk

@@ -1,0 +1,85 @@
+// Internal launch interface between the kernels and the host runtime.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace regnk {
+
+// Spectral multipliers of the column pass (see fft.cu).
+enum SpecOp {
+  SPOP_SCALE = 0,        // sigma = 1 (with resampling: restriction / prolongation)
+  SPOP_GRAD = 1,         // 1 -> 2: i k1, i k2 (Nyquist zeroed)
+  SPOP_DIV = 2,          // 2 -> 1: i k1 u1 + i k2 u2 (Nyquist zeroed)
+  SPOP_REGPOW = 3,       // (beta |k|^2p)^s, s = 1 exact, otherwise k = 0 weight -> 1
+  SPOP_LOWPASS = 4,      // |k1| < n1/4 and |k2| < n2/4
+  SPOP_HIGHPASS = 5,     // complement of LOWPASS
+  SPOP_REGPOW_HIGH = 6,  // REGPOW restricted to the high band
+};
+
+struct ColArgs {
+  const float2* in;
+  long long in_fstride;   // complex values between consecutive input spectra
+  float2* out;
+  long long out_fstride;
+  int nin, nout;          // spectra per group in and out
+  int nk1_out;            // output lines (n1_out / 2 + 1)
+  int n1_in, n2_in, n1_out, n2_out;
+  int n1, n2;             // grid the Nyquist / filter conditions refer to
+  int op;
+  float beta;
+  int p;
+  float s;
+  float scale;            // 1 / (n1_in n2_in)
+  const float2* tw_in;    // twiddles for length n2_in
+  const float2* tw_out;   // twiddles for length n2_out
+};
+
+// fft.cu
+void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
+                  long long sstride, int F, const float2* tw, cudaStream_t st);
+void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
+                  long long fstride, const float* add, long long astride, int F,
+                  const float2* tw, cudaStream_t st);
+void fft_cols(const ColArgs& a, int groups, cudaStream_t st);
+
+// transport.cu
+struct PrefilterTaps;  // host-computed, passed by value below
+void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
+                      cudaStream_t st);
+void launch_departure(int n1, int n2, float ht, const float* v, const float* cv,
+                      float* dX, float* dY, int lagrange, cudaStream_t st);
+void launch_gather(int n1, int n2, const float* coef, const float* disp, float* out, int F,
+                   long long fstride, int lagrange, cudaStream_t st);
+void launch_state_step(int n1, int n2, const float* coef, const float* dX, float* out,
+                       int lagrange, cudaStream_t st);
+void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const float* m1,
+                         const float* gm, float* lam, float* b, float sign, cudaStream_t st);
+void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
+                         const float* dY, const float* delta, const float* delta_bar,
+                         const float* gm, float* lam_out, float* b, int lagrange,
+                         cudaStream_t st);
+void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
+                          const float* vt, const float* vtD, const float* G,
+                          const float* gm, float* out, int first, int lagrange,
+                          cudaStream_t st);
+
+// reduce.cu
+void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
+                cudaStream_t st);
+void launch_sumsq_diff(const float* a, const float* b, long long n, double* partial,
+                       double* out, cudaStream_t st);
+void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st);
+void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st);
+void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
+                  const float* x, float* y, float beta_y, cudaStream_t st);
+void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
+                    cudaStream_t st);
+void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
+                       const float* q, float* x, float* r, cudaStream_t st);
+void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,
+                          const float* z, float* p, cudaStream_t st);
+void launch_fill(float* x, long long n, float value, cudaStream_t st);
+void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st);
+int reduce_partials();
+
+}  // namespace regnk

@@ -1,0 +1,237 @@
+// Reductions and Krylov vector updates. Inner products and norms take FP32
+// fields and accumulate in FP64 (the Krylov inner products, the Armijo
+// objective comparison and the gradient-norm test of §3.4.1 are decided in
+// FP64). Reductions are two-stage with a fixed block count and a fixed
+// summation order, so repeated calls on the same data give identical bits.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace regnk {
+
+constexpr int kRT = 256;       // threads per reduction block
+constexpr int kRB = 1216;      // maximum partial sums (8 per SM on 152 SMs)
+
+int reduce_partials() { return kRB; }
+
+static int nblocks(long long n) {
+  long long b = (n + 4LL * kRT - 1) / (4LL * kRT);
+  return (int)(b < 1 ? 1 : (b > kRB ? kRB : b));
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_sum(T v) {
+  __shared__ T ws[kRT / 32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  T r = 0;
+  if (w == 0) {
+    r = lane < kRT / 32 ? ws[lane] : T(0);
+    r = warp_sum(r);
+  }
+  return r;
+}
+
+// mode 0: sum a*b; mode 1: sum (a-b)^2
+template <int MODE>
+__global__ void __launch_bounds__(kRT)
+k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
+          double* __restrict__ partial, int vec4) {
+  double acc = 0.0;
+  const long long stride = (long long)gridDim.x * kRT;
+  const long long n4 = vec4 ? (n >> 2) : 0;   // float4 path only for 16-byte aligned inputs
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  const float4* b4 = reinterpret_cast<const float4*>(b);
+  for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n4; i += stride) {
+    const float4 x = __ldg(a4 + i), y = __ldg(b4 + i);
+    if (MODE == 0) {
+      acc += (double)x.x * y.x + (double)x.y * y.y + (double)x.z * y.z + (double)x.w * y.w;
+    } else {
+      const double d0 = (double)x.x - y.x, d1 = (double)x.y - y.y;
+      const double d2 = (double)x.z - y.z, d3 = (double)x.w - y.w;
+      acc += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+    }
+  }
+  for (long long i = (n4 << 2) + (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
+    const double x = __ldg(a + i), y = __ldg(b + i);
+    acc += MODE == 0 ? x * y : (x - y) * (x - y);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRT)
+k_final_sum(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += kRT) acc += partial[i];
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) *out = s;
+}
+
+static int aligned16(const void* a, const void* b) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
+}
+
+void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
+                cudaStream_t st) {
+  const int nb = nblocks(n);
+  k_partial<0><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b));
+  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out);
+}
+
+void launch_sumsq_diff(const float* a, const float* b, long long n, double* partial,
+                       double* out, cudaStream_t st) {
+  const int nb = nblocks(n);
+  k_partial<1><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b));
+  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out);
+}
+
+__global__ void __launch_bounds__(kRT)
+k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ partial) {
+  float m = 0.f;
+  const long long stride = (long long)gridDim.x * kRT;
+  for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
+    const float x = fabsf(__ldg(a + i));
+    m = (x > m || x != x) ? x : m;  // NaN propagates
+  }
+  __shared__ float ws[kRT / 32];
+  m = warp_max(m);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) ws[w] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = ws[0];
+    for (int k = 1; k < kRT / 32; ++k) r = (ws[k] > r || ws[k] != ws[k]) ? ws[k] : r;
+    partial[blockIdx.x] = r;
+  }
+}
+
+__global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double* out) {
+  if (threadIdx.x == 0) {
+    float r = 0.f;
+    for (int i = 0; i < nb; ++i) r = (partial[i] > r || partial[i] != partial[i]) ? partial[i] : r;
+    *out = (double)r;
+  }
+}
+
+void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st) {
+  const int nb = nblocks(n);
+  k_maxabs_partial<<<nb, kRT, 0, st>>>(a, n, partial);
+  k_maxabs_final<<<1, 32, 0, st>>>(partial, nb, out);
+}
+
+// flag = 1 if any bit pattern differs (flag must be zeroed by the caller).
+__global__ void k_compare(const unsigned* __restrict__ a, const unsigned* __restrict__ b,
+                          long long n, int* flag) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int d = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    d |= (__ldg(a + i) != __ldg(b + i));
+  if (__syncthreads_or(d) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st) {
+  k_compare<<<nblocks(n), kRT, 0, st>>>(reinterpret_cast<const unsigned*>(a),
+                                        reinterpret_cast<const unsigned*>(b), n, flag);
+}
+
+// y = (alpha_num/alpha_den * cs) x + beta_y y, coefficients from device FP64 scalars.
+__global__ void k_axpby(long long n, const double* an, const double* ad, double cs,
+                        const float* __restrict__ x, float* __restrict__ y, float beta_y) {
+  const float alpha = (float)((*an / *ad) * cs);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    y[i] = fmaf(alpha, x[i], beta_y * y[i]);
+}
+
+void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
+                  const float* x, float* y, float beta_y, cudaStream_t st) {
+  k_axpby<<<nblocks(n), kRT, 0, st>>>(n, alpha_num, alpha_den, cs, x, y, beta_y);
+}
+
+// z may alias x or y (elementwise, same index)
+__global__ void k_lincomb(long long n, float a, const float* x, float b, const float* y,
+                          float* z) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    z[i] = a * x[i] + (y ? b * y[i] : 0.f);
+}
+
+void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
+                    cudaStream_t st) {
+  k_lincomb<<<nblocks(n), kRT, 0, st>>>(n, a, x, b, y, z);
+}
+
+// PCG step: alpha = rz / pq; x += alpha p; r -= alpha q.
+__global__ void k_pcg_update(long long n, const double* rz, const double* pq,
+                             const float* __restrict__ p, const float* __restrict__ q,
+                             float* __restrict__ x, float* __restrict__ r) {
+  const double ad = *rz / *pq;
+  const float alpha = (float)ad;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    x[i] = fmaf(alpha, p[i], x[i]);
+    r[i] = fmaf(-alpha, q[i], r[i]);
+  }
+}
+
+void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
+                       const float* q, float* x, float* r, cudaStream_t st) {
+  k_pcg_update<<<nblocks(n), kRT, 0, st>>>(n, rz, pq, p, q, x, r);
+}
+
+// p = z + (rz_new / rz_old) p
+__global__ void k_pcg_direction(long long n, const double* rz_new, const double* rz_old,
+                                const float* __restrict__ z, float* __restrict__ p) {
+  const float beta = (float)(*rz_new / *rz_old);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    p[i] = fmaf(beta, p[i], z[i]);
+}
+
+void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,
+                          const float* z, float* p, cudaStream_t st) {
+  k_pcg_direction<<<nblocks(n), kRT, 0, st>>>(n, rz_new, rz_old, z, p);
+}
+
+__global__ void k_fill(float* x, long long n, float value) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    x[i] = value;
+}
+
+void launch_fill(float* x, long long n, float value, cudaStream_t st) {
+  k_fill<<<nblocks(n), kRT, 0, st>>>(x, n, value);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): x[i] = uniform [-1, 1) from the
+// (i+1)-th output of the stream started at seed.
+__global__ void k_splitmix(float* x, long long n, unsigned long long seed) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    x[i] = (float)((double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+  }
+}
+
+void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st) {
+  k_splitmix<<<nblocks(n), kRT, 0, st>>>(x, n, seed);
+}
+
+}  // namespace regnk

@@ -1,0 +1,998 @@
+// Host runtime of libregnk: context and workspace management, the
+// objective / gradient / Gauss-Newton Hessian pipelines, the Krylov solvers,
+// the preconditioners and the inexact Newton loop, behind the C ABI of
+// include/reg.h. All field arithmetic runs in the kernels of fft.cu,
+// transport.cu and reduce.cu; the host only sequences launches and reads the
+// FP64 scalars that steer the iterations.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "reg.h"
+
+using namespace regnk;
+
+namespace {
+
+constexpr int kSpecSlots = 8;    // spectra in the FFT workspace of a level
+constexpr int kScalars = 32;     // FP64 device scalar slots
+
+enum Slot { S_A = 0, S_B, S_C, S_D, S_E, S_GINF, S_G2, S_J1, S_J2,
+            S_PCG_OUTER = 16, S_PCG_INNER = 24 };
+// offsets of the PCG scalars inside a PCG slot block
+enum PcgSlot { P_RZ = 0, P_RZNEW, P_PQ, P_RR, P_BB };
+
+struct Level {
+  GridDims g;
+  int nt = 0;
+  float ht = 0.f;
+  double h1 = 0, h2 = 0;
+  float2* tw1 = nullptr;   // twiddles for length n1
+  float2* tw2 = nullptr;   // twiddles for length n2
+  float* mR = nullptr;
+  float* mT = nullptr;
+  float* v = nullptr;       // cached velocity (2N)
+  float* cv = nullptr;      // its interpolation coefficients (2N)
+  float* dX = nullptr;      // departure displacement, forward characteristic (2N)
+  float* dY = nullptr;      // backward characteristic (2N)
+  float* delta = nullptr;   // div v (N)
+  float* delta_bar = nullptr;  // div v at Y_D (N)
+  float* m = nullptr;       // state history m_0..m_nt ((nt+1) N)
+  float* gm = nullptr;      // grad m_0..grad m_nt (2 (nt+1) N)
+  float* G = nullptr;       // grad m_{j-1}(X_D), j = 1..nt (2 nt N)
+  float* coef = nullptr;    // interpolation coefficients of one scalar field (N)
+  float* tmp = nullptr;     // prefilter intermediate (2N)
+  float* fA = nullptr;      // scalar ping-pong (N)
+  float* fB = nullptr;
+  float* c2 = nullptr;      // coefficients of a vector field (2N)
+  float* vtD = nullptr;     // v~ at X_D (2N)
+  float* b = nullptr;       // time-integral accumulator (2N)
+  float* Av = nullptr;      // beta A v (2N)
+  float* w1 = nullptr;      // vector scratch (2N)
+  float* w2 = nullptr;      // vector scratch (2N)
+  float2* spec = nullptr;   // kSpecSlots spectra
+  bool have_images = false;
+  bool have_v = false;      // v, dX, state valid
+  bool have_gm = false;     // grad history valid for v
+  bool have_div = false;    // delta, delta_bar, dY valid for v
+  bool have_G = false;      // G valid for v
+};
+
+}  // namespace
+
+struct reg_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  reg_options opt;
+  double beta = 0;
+  int nt = 0;
+  bool two_level = false;
+  Level fine, coarse;
+  std::vector<void*> allocs;
+  std::vector<float2*> tw;        // twiddles by log2 length
+  double* dsc = nullptr;          // device FP64 scalars
+  double* hsc = nullptr;          // pinned host mirror
+  double* partial = nullptr;      // reduction partials
+  float* partialf = nullptr;
+  int* dflag = nullptr;
+  int* hflag = nullptr;
+  // fine Krylov vectors (2N each)
+  float *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr;
+  float *vtrial = nullptr, *gcur = nullptr, *vt_tmp = nullptr;
+  // coarse vectors (2 Nc each)
+  float *cx = nullptr, *cr = nullptr, *cd = nullptr, *cAd = nullptr, *crhs = nullptr,
+        *cu = nullptr, *cq = nullptr, *cz = nullptr, *cp = nullptr;
+  bool have_eig = false;
+  double emin = 0, emax = 0, eig_beta = 0;
+  bool have_gref = false;
+  double gref_inf = 0, gref_2 = 0;
+  double eta = 0.5;
+  int coarse_matvecs = 0;
+  std::string err;
+};
+
+namespace {
+
+struct CudaError {
+  reg_status s;
+};
+
+void fail(reg_ctx* c, reg_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  c->err = buf;
+  throw CudaError{s};
+}
+
+void check(reg_ctx* c, cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(c, REG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void check_launch(reg_ctx* c, const char* what) { check(c, cudaGetLastError(), what); }
+
+template <typename T>
+T* dalloc(reg_ctx* c, size_t count) {
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess) fail(c, REG_ENOMEM, "cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+  c->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+float2* twiddles(reg_ctx* c, int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  if ((int)c->tw.size() <= l) c->tw.resize(l + 1, nullptr);
+  if (!c->tw[l]) {
+    std::vector<float2> h(n);
+    for (int m = 0; m < n; ++m) {
+      const double a = -2.0 * M_PI * (double)m / (double)n;
+      h[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    float2* d = dalloc<float2>(c, n);
+    check(c, cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "twiddle upload");
+    c->tw[l] = d;
+  }
+  return c->tw[l];
+}
+
+void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
+  L.g = make_grid(n1, n2);
+  L.nt = nt;
+  L.ht = 1.0f / (float)nt;
+  L.h1 = 2.0 * M_PI / n1;
+  L.h2 = 2.0 * M_PI / n2;
+  L.tw1 = twiddles(c, n1);
+  L.tw2 = twiddles(c, n2);
+  const size_t N = (size_t)L.g.N;
+  L.mR = dalloc<float>(c, N);
+  L.mT = dalloc<float>(c, N);
+  L.v = dalloc<float>(c, 2 * N);
+  L.cv = dalloc<float>(c, 2 * N);
+  L.dX = dalloc<float>(c, 2 * N);
+  L.dY = dalloc<float>(c, 2 * N);
+  L.delta = dalloc<float>(c, N);
+  L.delta_bar = dalloc<float>(c, N);
+  L.m = dalloc<float>(c, (nt + 1) * N);
+  L.gm = dalloc<float>(c, 2 * (nt + 1) * N);
+  L.G = dalloc<float>(c, 2 * nt * N);
+  L.coef = dalloc<float>(c, N);
+  L.tmp = dalloc<float>(c, 2 * N);
+  L.fA = dalloc<float>(c, N);
+  L.fB = dalloc<float>(c, N);
+  L.c2 = dalloc<float>(c, 2 * N);
+  L.vtD = dalloc<float>(c, 2 * N);
+  L.b = dalloc<float>(c, 2 * N);
+  L.Av = dalloc<float>(c, 2 * N);
+  L.w1 = dalloc<float>(c, 2 * N);
+  L.w2 = dalloc<float>(c, 2 * N);
+  L.spec = dalloc<float2>(c, kSpecSlots * (size_t)L.g.spec);
+}
+
+bool lagrange(const reg_ctx* c) { return c->opt.interp == REG_INTERP_LAGRANGE; }
+
+// ---------------------------------------------------------------------------
+// spectral operators
+
+ColArgs col_args(const Level& L, int op, double beta, int p, double s) {
+  ColArgs a{};
+  a.n1_in = a.n1_out = a.n1 = L.g.n1;
+  a.n2_in = a.n2_out = a.n2 = L.g.n2;
+  a.nk1_out = L.g.nk1;
+  a.op = op;
+  a.beta = (float)beta;
+  a.p = p;
+  a.s = (float)s;
+  a.scale = (float)(1.0 / (double)L.g.N);
+  a.tw_in = a.tw_out = L.tw2;
+  return a;
+}
+
+// out (groups*fout fields) = op(in (groups*fin fields)) [+ add], on level L.
+void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, int groups,
+              float* out, int fout, const float* add) {
+  const GridDims& g = L.g;
+  const int per = fin + fout;
+  const int chunk = kSpecSlots / per;
+  for (int g0 = 0; g0 < groups; g0 += chunk) {
+    const int ng = groups - g0 < chunk ? groups - g0 : chunk;
+    float2* sin = L.spec;
+    float2* sout = L.spec + (size_t)ng * fin * g.spec;
+    fft_rows_r2c(g.n1, g.n2, in + (size_t)g0 * fin * g.N, g.N, sin, g.spec, ng * fin, L.tw1, c->st);
+    ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s);
+    a.in = sin;
+    a.in_fstride = g.spec;
+    a.out = sout;
+    a.out_fstride = g.spec;
+    a.nin = fin;
+    a.nout = fout;
+    fft_cols(a, ng, c->st);
+    fft_rows_c2r(g.n1, g.n2, sout, g.spec, out + (size_t)g0 * fout * g.N, g.N,
+                 add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st);
+  }
+  check_launch(c, "spectral operator");
+}
+
+// Spectral resampling of F fields from level A to level B (restriction or
+// prolongation) with multiplier op(s), plus an optional addend on B.
+void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in, int F,
+              float* out, const float* add) {
+  float2* sin = c->fine.spec;
+  float2* sout = c->fine.spec + (size_t)F * A.g.spec;
+  fft_rows_r2c(A.g.n1, A.g.n2, in, A.g.N, sin, A.g.spec, F, A.tw1, c->st);
+  ColArgs a = col_args(A, op, c->beta, c->opt.reg_norm, s);
+  a.in = sin;
+  a.in_fstride = A.g.spec;
+  a.out = sout;
+  a.out_fstride = B.g.spec;
+  a.nin = 1;
+  a.nout = 1;
+  a.n1_out = B.g.n1;
+  a.n2_out = B.g.n2;
+  a.nk1_out = B.g.nk1;
+  a.tw_out = B.tw2;
+  fft_cols(a, F, c->st);
+  fft_rows_c2r(B.g.n1, B.g.n2, sout, B.g.spec, out, B.g.N, add, B.g.N, F, B.tw1, c->st);
+  check_launch(c, "spectral resampling");
+}
+
+// interpolation coefficients of F consecutive fields (prefilter for the
+// spline model; the samples themselves for Lagrange)
+const float* coefficients(reg_ctx* c, Level& L, const float* u, int F, float* dst) {
+  if (lagrange(c)) return u;
+  for (int f = 0; f < F; ++f)
+    launch_prefilter(L.g.n1, L.g.n2, u + (size_t)f * L.g.N, L.tmp, dst + (size_t)f * L.g.N, 1, c->st);
+  check_launch(c, "prefilter");
+  return dst;
+}
+
+// ---------------------------------------------------------------------------
+// scalars
+
+double* slot(reg_ctx* c, int s) { return c->dsc + s; }
+
+void read_slots(reg_ctx* c, int first, int count) {
+  check(c, cudaMemcpyAsync(c->hsc + first, c->dsc + first, count * sizeof(double),
+                           cudaMemcpyDeviceToHost, c->st), "scalar read");
+  check(c, cudaStreamSynchronize(c->st), "stream synchronize");
+}
+
+double dot_sync(reg_ctx* c, const float* a, const float* b, long long n, int s) {
+  launch_dot(a, b, n, c->partial, slot(c, s), c->st);
+  check_launch(c, "dot");
+  read_slots(c, s, 1);
+  return c->hsc[s];
+}
+
+// ---------------------------------------------------------------------------
+// level pipelines
+
+// Caches v, its characteristics and the state history m_0..m_nt (§3.3.2).
+void set_velocity(reg_ctx* c, Level& L, const float* v) {
+  const GridDims& g = L.g;
+  const size_t N = (size_t)g.N;
+  if (v != L.v) check(c, cudaMemcpyAsync(L.v, v, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
+  const float* cv = coefficients(c, L, L.v, 2, L.cv);
+  launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, lagrange(c), c->st);
+  check(c, cudaMemcpyAsync(L.m, L.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
+  for (int j = 1; j <= L.nt; ++j) {
+    const float* cm = coefficients(c, L, L.m + (j - 1) * N, 1, L.coef);
+    launch_state_step(g.n1, g.n2, cm, L.dX, L.m + j * N, lagrange(c), c->st);
+  }
+  check_launch(c, "state solve");
+  L.have_v = true;
+  L.have_gm = false;
+  L.have_div = true;   // dY computed together with dX; delta below
+  L.have_G = false;
+  // div v and div v at Y_D
+  spectral(c, L, SPOP_DIV, 0.0, L.v, 2, 1, L.delta, 1, nullptr);
+  const float* cd = coefficients(c, L, L.delta, 1, L.coef);
+  launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, lagrange(c), c->st);
+  check_launch(c, "div v");
+}
+
+void ensure_grad_history(reg_ctx* c, Level& L) {
+  if (L.have_gm) return;
+  const size_t N = (size_t)L.g.N;
+  // grad m_1..grad m_nt (grad m_0 = grad m_T is set with the images)
+  spectral(c, L, SPOP_GRAD, 0.0, L.m + N, 1, L.nt, L.gm + 2 * N, 2, nullptr);
+  L.have_gm = true;
+}
+
+void ensure_G(reg_ctx* c, Level& L) {
+  if (L.have_G) return;
+  ensure_grad_history(c, L);
+  const size_t N = (size_t)L.g.N;
+  for (int j = 1; j <= L.nt; ++j) {
+    const float* cg = coefficients(c, L, L.gm + 2 * (j - 1) * N, 2, L.c2);
+    launch_gather(L.g.n1, L.g.n2, cg, L.dX, L.G + 2 * (j - 1) * N, 2, (long long)N, lagrange(c), c->st);
+  }
+  check_launch(c, "G history");
+  L.have_G = true;
+}
+
+// J = 1/2 <m_1 - m_R, m_1 - m_R>_h + beta/2 <v, A v>_h (eq. varopt:objective);
+// leaves beta A v in L.Av.
+double objective(reg_ctx* c, Level& L) {
+  const size_t N = (size_t)L.g.N;
+  spectral(c, L, SPOP_REGPOW, 1.0, L.v, 1, 2, L.Av, 1, nullptr);
+  launch_sumsq_diff(L.m + L.nt * N, L.mR, (long long)N, c->partial, slot(c, S_J1), c->st);
+  launch_dot(L.v, L.Av, 2 * (long long)N, c->partial, slot(c, S_J2), c->st);
+  check_launch(c, "objective");
+  read_slots(c, S_J1, 2);
+  const double hh = L.h1 * L.h2;
+  return 0.5 * hh * c->hsc[S_J1] + 0.5 * hh * c->hsc[S_J2];
+}
+
+// b = int_0^1 lambda grad m dt by the adjoint solve (eq. adj-slm), trapezoid in
+// time; g = beta A v + b. Needs objective() for L.Av.
+void gradient(reg_ctx* c, Level& L, float* g_out) {
+  ensure_grad_history(c, L);
+  const GridDims& gd = L.g;
+  const size_t N = (size_t)gd.N;
+  const int nt = L.nt;
+  const float ht = L.ht;
+  float* lam = L.fA;
+  float* lam2 = L.fB;
+  launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, L.mR, L.m + nt * N, L.gm + 2 * nt * N, lam, L.b, 1.f, c->st);
+  for (int j = nt - 1; j >= 0; --j) {
+    const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    const float* cl = coefficients(c, L, lam, 1, L.coef);
+    launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
+                        lam2, L.b, lagrange(c), c->st);
+    std::swap(lam, lam2);
+  }
+  check_launch(c, "adjoint solve");
+  launch_lincomb(2 * (long long)N, 1.f, L.Av, 1.f, L.b, g_out, c->st);
+  check_launch(c, "gradient");
+}
+
+// Gauss-Newton Hessian matvec (eq. hessian-matvec, GN); data_only drops beta A vt.
+void hessian(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
+  ensure_G(c, L);
+  const GridDims& gd = L.g;
+  const size_t N = (size_t)gd.N;
+  const int nt = L.nt;
+  const float ht = L.ht;
+  const int lg = lagrange(c);
+  const float* cvt = coefficients(c, L, vt, 2, L.c2);
+  launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
+  float* mt = L.fA;
+  float* mt2 = L.fB;
+  for (int j = 1; j <= nt; ++j) {
+    const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
+    launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                         L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+    std::swap(mt, mt2);
+  }
+  check_launch(c, "incremental state");
+  // lambda~_nt = -m~_nt
+  float* lt = mt2;
+  launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+  float* lt2 = mt;
+  for (int j = nt - 1; j >= 0; --j) {
+    const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    const float* cl = coefficients(c, L, lt, 1, L.coef);
+    launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
+                        lt2, L.b, lg, c->st);
+    std::swap(lt, lt2);
+  }
+  check_launch(c, "incremental adjoint");
+  if (data_only) {
+    check(c, cudaMemcpyAsync(out, L.b, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  } else {
+    spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+  }
+}
+
+void set_images_level(reg_ctx* c, Level& L) {
+  spectral(c, L, SPOP_GRAD, 0.0, L.mT, 1, 1, L.gm, 2, nullptr);
+  L.have_images = true;
+  L.have_v = L.have_gm = L.have_div = L.have_G = false;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioners and Krylov solvers
+
+// (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse level.
+void coarse_split_op(reg_ctx* c, const float* s, float* out) {
+  Level& C = c->coarse;
+  spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
+  hessian(c, C, c->cu, c->cq, true);
+  spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
+  ++c->coarse_matvecs;
+}
+
+// Largest eigenvalue of a symmetric tridiagonal matrix by Sturm bisection.
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::fmin(lo, a[i] - r);
+    hi = std::fmax(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < m; ++i) {
+      d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+      if (d == 0.0) d = -1e-300;
+      if (d < 0) ++cnt;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fmax(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+void estimate_eigenvalues(reg_ctx* c) {
+  Level& C = c->coarse;
+  const long long n = 2 * C.g.N;
+  // coarse problem at v = 0
+  launch_fill(C.w1, n, 0.f, c->st);
+  set_velocity(c, C, C.w1);
+  float* q = c->cp;
+  float* qprev = c->cz;
+  float* w = c->cd;
+  launch_splitmix(q, n, c->opt.lanczos_seed, c->st);
+  const double nq = std::sqrt(dot_sync(c, q, q, n, S_A));
+  launch_lincomb(n, (float)(1.0 / nq), q, 0.f, nullptr, q, c->st);
+  launch_fill(qprev, n, 0.f, c->st);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int k = 0; k < c->opt.lanczos_steps; ++k) {
+    coarse_split_op(c, q, w);
+    const double alpha = dot_sync(c, q, w, n, S_A);
+    launch_lincomb(n, 1.f, w, (float)-alpha, q, w, c->st);
+    launch_lincomb(n, 1.f, w, (float)-beta, qprev, w, c->st);
+    al.push_back(alpha);
+    const double bn = std::sqrt(dot_sync(c, w, w, n, S_B));
+    if (!(bn > 1e-12 * std::fabs(alpha))) break;
+    be.push_back(bn);
+    std::swap(qprev, q);                       // qprev <- q
+    launch_lincomb(n, (float)(1.0 / bn), w, 0.f, nullptr, q, c->st);  // q <- w / beta
+    beta = bn;
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  const double rmax = tridiag_max_eig(al, be);
+  const int p = c->opt.reg_norm;
+  const double kn = 0.25 * ((double)C.g.n1 * C.g.n1 + (double)C.g.n2 * C.g.n2);
+  const double gmax = std::pow(kn, p);
+  c->emin = 1.0 + 1.0 / (c->beta * gmax);
+  c->emax = rmax * c->opt.emax_safety;
+  c->eig_beta = c->beta;
+  c->have_eig = true;
+}
+
+void cheb(reg_ctx* c, const float* rhs, float* x) {
+  const long long n = 2 * c->coarse.g.N;
+  const double theta = 0.5 * (c->emax + c->emin), delta = 0.5 * (c->emax - c->emin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  check(c, cudaMemcpyAsync(c->cr, rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  launch_lincomb(n, (float)(1.0 / theta), rhs, 0.f, nullptr, c->cd, c->st);
+  check(c, cudaMemcpyAsync(x, c->cd, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  for (int it = 1; it < c->opt.cheb_iters; ++it) {
+    coarse_split_op(c, c->cd, c->cAd);
+    launch_lincomb(n, 1.f, c->cr, -1.f, c->cAd, c->cr, c->st);
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    launch_lincomb(n, (float)(rho_new * rho), c->cd, (float)(2.0 * rho_new / delta), c->cr, c->cd, c->st);
+    launch_lincomb(n, 1.f, x, 1.f, c->cd, x, c->st);
+    rho = rho_new;
+  }
+  check_launch(c, "chebyshev");
+}
+
+struct PcgResult {
+  int iters = 0, matvecs = 0;
+  bool negcurv = false;
+  double relres = 1.0;
+};
+
+// PCG (Hestenes-Stiefel), zero initial guess, on vectors of length n.
+template <typename Op, typename Prec>
+PcgResult pcg(reg_ctx* c, long long n, Op A, Prec M, const float* rhs, float* x, float* r,
+              float* z, float* p, float* q, double rtol, int maxit, int sb) {
+  PcgResult res;
+  const int S_RZ = sb + P_RZ, S_RZNEW = sb + P_RZNEW, S_PQ = sb + P_PQ, S_RR = sb + P_RR,
+            S_BB = sb + P_BB;
+  launch_fill(x, n, 0.f, c->st);
+  check(c, cudaMemcpyAsync(r, rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  const double bnorm = std::sqrt(dot_sync(c, rhs, rhs, n, S_BB));
+  if (!(bnorm > 0.0)) {
+    res.relres = 0.0;
+    return res;
+  }
+  M(r, z);
+  check(c, cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  launch_dot(r, z, n, c->partial, slot(c, S_RZ), c->st);
+  for (int it = 0; it < maxit; ++it) {
+    A(p, q);
+    ++res.matvecs;
+    const double pq = dot_sync(c, p, q, n, S_PQ);
+    if (!(pq > 0.0)) {
+      res.negcurv = true;
+      if (it == 0) check(c, cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+      break;
+    }
+    launch_pcg_update(n, slot(c, S_RZ), slot(c, S_PQ), p, q, x, r, c->st);
+    res.iters = it + 1;
+    const double rr = dot_sync(c, r, r, n, S_RR);
+    res.relres = std::sqrt(rr) / bnorm;
+    if (res.relres <= rtol) break;
+    M(r, z);
+    launch_dot(r, z, n, c->partial, slot(c, S_RZNEW), c->st);
+    launch_pcg_direction(n, slot(c, S_RZNEW), slot(c, S_RZ), z, p, c->st);
+    check(c, cudaMemcpyAsync(slot(c, S_RZ), slot(c, S_RZNEW), sizeof(double), cudaMemcpyDeviceToDevice, c->st), "copy");
+    check_launch(c, "pcg");
+  }
+  return res;
+}
+
+void coarse_velocity(reg_ctx* c) {
+  resample(c, c->fine, c->coarse, SPOP_SCALE, 0.0, c->fine.v, 2, c->coarse.w2, nullptr);
+  set_velocity(c, c->coarse, c->coarse.w2);
+}
+
+void precond(reg_ctx* c, const float* r, float* z) {
+  Level& F = c->fine;
+  const long long n = 2 * F.g.N;
+  if (!c->two_level) {
+    spectral(c, F, SPOP_REGPOW, -1.0, r, 1, 2, z, 1, nullptr);
+    return;
+  }
+  Level& C = c->coarse;
+  const long long nc = 2 * C.g.N;
+  // r' = (beta A)^-1/2 r; restricted low band -> crhs; high band (beta A)^-1 H r -> F.w1
+  resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
+  spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
+  if (c->opt.pc_solver == REG_PCSOLVER_CHEB) {
+    cheb(c, c->crhs, c->cx);
+  } else {
+    auto A = [&](const float* s, float* o) { coarse_split_op(c, s, o); };
+    auto I = [&](const float* s, float* o) {
+      check(c, cudaMemcpyAsync(o, s, nc * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+    };
+    pcg(c, nc, A, I, c->crhs, c->cx, c->cr, c->cz, c->cp, c->cq, c->opt.pc_eps * c->eta,
+        c->opt.max_pcg, S_PCG_INNER);
+  }
+  // z = (beta A)^-1/2 P s_c + (beta A)^-1 H r
+  resample(c, C, F, SPOP_REGPOW, -0.5, c->cx, 2, z, F.w1);
+  (void)n;
+}
+
+PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
+  Level& F = c->fine;
+  const long long n = 2 * F.g.N;
+  if (c->two_level) {
+    if (!c->have_eig) {
+      estimate_eigenvalues(c);
+    } else if (c->eig_beta != c->beta) {
+      const double s = c->eig_beta / c->beta;
+      c->emin = 1.0 + (c->emin - 1.0) * s;
+      c->emax = 1.0 + (c->emax - 1.0) * s;
+      c->eig_beta = c->beta;
+    }
+    coarse_velocity(c);
+  }
+  auto A = [&](const float* p, float* q) { hessian(c, F, p, q, false); };
+  auto M = [&](const float* r, float* z) { precond(c, r, z); };
+  return pcg(c, n, A, M, rhs, x, c->kr, c->kz, c->kp, c->kq, rtol, maxit, S_PCG_OUTER);
+}
+
+double max_abs_sync(reg_ctx* c, const float* a, long long n, int s) {
+  launch_maxabs(a, n, c->partialf, slot(c, s), c->st);
+  check_launch(c, "maxabs");
+  read_slots(c, s, 1);
+  return c->hsc[s];
+}
+
+void require_images(reg_ctx* c) {
+  if (!c->fine.have_images) fail(c, REG_ESTATE, "reg_set_images has not been called");
+}
+
+// full objective + gradient at v on the fine level
+double objective_gradient(reg_ctx* c, const float* v, float* g) {
+  set_velocity(c, c->fine, v);
+  const double J = objective(c, c->fine);
+  if (g) gradient(c, c->fine, g);
+  return J;
+}
+
+void ensure_gref(reg_ctx* c) {
+  if (c->have_gref) return;
+  Level& F = c->fine;
+  const long long n = 2 * F.g.N;
+  launch_fill(c->vtrial, n, 0.f, c->st);
+  objective_gradient(c, c->vtrial, c->gcur);
+  c->gref_inf = max_abs_sync(c, c->gcur, n, S_GINF);
+  c->gref_2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n, S_G2));
+  c->have_gref = true;
+}
+
+reg_status guarded(reg_ctx* c, const std::function<void()>& body) {
+  if (!c) return REG_EINVAL;
+  try {
+    body();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      c->err = std::string("CUDA: ") + cudaGetErrorString(e);
+      return REG_ECUDA;
+    }
+    return REG_OK;
+  } catch (const CudaError& e) {
+    return e.s;
+  }
+}
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+reg_status reg_default_options(reg_options* o) {
+  if (!o) return REG_EINVAL;
+  o->reg_norm = REG_H1;
+  o->interp = REG_INTERP_SPLINE;
+  o->precond = REG_PC_2L;
+  o->pc_solver = REG_PCSOLVER_CHEB;
+  o->cheb_iters = 10;
+  o->pc_eps = 0.1;
+  o->gabs = 1e-5;
+  o->max_newton = 50;
+  o->max_pcg = 100;
+  o->lanczos_steps = 30;
+  o->emax_safety = 1.05;
+  o->lanczos_seed = 20160407ULL;
+  o->max_backtracks = 10;
+  o->armijo_c1 = 1e-4;
+  return REG_OK;
+}
+
+static bool pow2_in_range(int n) { return n >= 32 && n <= 2048 && (n & (n - 1)) == 0; }
+
+reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt, reg_ctx** out) {
+  if (!out) return REG_EINVAL;
+  *out = nullptr;
+  if (!pow2_in_range(grid.n1) || !pow2_in_range(grid.n2) || nt < 1 || nt > 4096 || !(beta > 0.0))
+    return REG_EINVAL;
+  reg_options o;
+  if (opt) o = *opt; else reg_default_options(&o);
+  if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
+      (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
+      o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0)
+    return REG_EINVAL;
+  if (o.precond == REG_PC_2L && (grid.n1 < 64 || grid.n2 < 64)) return REG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
+  reg_ctx* c = new reg_ctx();
+  c->device = dev;
+  c->opt = o;
+  c->beta = beta;
+  c->nt = nt;
+  c->two_level = (o.precond == REG_PC_2L);
+  const reg_status s = guarded(c, [&] {
+    alloc_level(c, c->fine, grid.n1, grid.n2, nt);
+    if (c->two_level) alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, nt);
+    c->dsc = dalloc<double>(c, kScalars);
+    void* h = nullptr;
+    check(c, cudaMallocHost(&h, kScalars * sizeof(double)), "cudaMallocHost");
+    c->hsc = static_cast<double*>(h);
+    void* hf = nullptr;
+    check(c, cudaMallocHost(&hf, sizeof(int)), "cudaMallocHost");
+    c->hflag = static_cast<int*>(hf);
+    c->partial = dalloc<double>(c, reduce_partials());
+    c->partialf = dalloc<float>(c, reduce_partials());
+    c->dflag = dalloc<int>(c, 1);
+    const size_t n = 2 * (size_t)c->fine.g.N;
+    c->kx = dalloc<float>(c, n);
+    c->kr = dalloc<float>(c, n);
+    c->kz = dalloc<float>(c, n);
+    c->kp = dalloc<float>(c, n);
+    c->kq = dalloc<float>(c, n);
+    c->vtrial = dalloc<float>(c, n);
+    c->gcur = dalloc<float>(c, n);
+    c->vt_tmp = dalloc<float>(c, n);
+    if (c->two_level) {
+      const size_t nc = 2 * (size_t)c->coarse.g.N;
+      c->cx = dalloc<float>(c, nc);
+      c->cr = dalloc<float>(c, nc);
+      c->cd = dalloc<float>(c, nc);
+      c->cAd = dalloc<float>(c, nc);
+      c->crhs = dalloc<float>(c, nc);
+      c->cu = dalloc<float>(c, nc);
+      c->cq = dalloc<float>(c, nc);
+      c->cz = dalloc<float>(c, nc);
+      c->cp = dalloc<float>(c, nc);
+    }
+    check(c, cudaDeviceSynchronize(), "create");
+  });
+  if (s != REG_OK) {
+    reg_destroy(c);
+    return s;
+  }
+  *out = c;
+  return REG_OK;
+}
+
+reg_status reg_destroy(reg_ctx* c) {
+  if (!c) return REG_OK;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  if (c->hflag) cudaFreeHost(c->hflag);
+  delete c;
+  return REG_OK;
+}
+
+reg_status reg_set_stream(reg_ctx* c, void* stream) {
+  if (!c) return REG_EINVAL;
+  c->st = static_cast<cudaStream_t>(stream);
+  return REG_OK;
+}
+
+const char* reg_last_error(const reg_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+reg_status reg_set_images(reg_ctx* c, const float* mR, const float* mT) {
+  if (!c || !mR || !mT) return REG_EINVAL;
+  return guarded(c, [&] {
+    Level& F = c->fine;
+    const size_t N = (size_t)F.g.N;
+    check(c, cudaMemcpyAsync(F.mR, mR, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_R");
+    check(c, cudaMemcpyAsync(F.mT, mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
+    set_images_level(c, F);
+    if (c->two_level) {
+      Level& C = c->coarse;
+      resample(c, F, C, SPOP_SCALE, 0.0, F.mR, 1, C.mR, nullptr);
+      resample(c, F, C, SPOP_SCALE, 0.0, F.mT, 1, C.mT, nullptr);
+      set_images_level(c, C);
+    }
+    c->have_eig = false;
+    c->have_gref = false;
+  });
+}
+
+reg_status reg_set_beta(reg_ctx* c, double beta) {
+  if (!c || !(beta > 0.0)) return REG_EINVAL;
+  c->beta = beta;  // eigenvalue bounds are rescaled lazily in kkt()
+  return REG_OK;
+}
+
+reg_status reg_transport(reg_ctx* c, const float* v, const float* m0, float* m1) {
+  if (!c || !v || !m0 || !m1) return REG_EINVAL;
+  return guarded(c, [&] {
+    Level& F = c->fine;
+    const size_t N = (size_t)F.g.N;
+    // the state solve uses m_T as initial condition: run it on a copy
+    F.have_v = F.have_gm = F.have_div = F.have_G = false;
+    check(c, cudaMemcpyAsync(F.w2, F.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "save m_T");
+    check(c, cudaMemcpyAsync(F.mT, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m0");
+    set_velocity(c, F, v);
+    check(c, cudaMemcpyAsync(m1, F.m + F.nt * N, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m1");
+    check(c, cudaMemcpyAsync(F.mT, F.w2, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "restore m_T");
+    F.have_v = F.have_gm = F.have_div = F.have_G = false;
+  });
+}
+
+reg_status reg_departure_points(reg_ctx* c, const float* v, float* dX, float* dY) {
+  if (!c || !v) return REG_EINVAL;
+  return guarded(c, [&] {
+    Level& F = c->fine;
+    const float* cv = coefficients(c, F, v, 2, F.c2);
+    launch_departure(F.g.n1, F.g.n2, F.ht, v, cv, dX, dY, lagrange(c), c->st);
+    check_launch(c, "departure points");
+  });
+}
+
+reg_status reg_interpolate(reg_ctx* c, const float* u, const float* disp, float* out) {
+  if (!c || !u || !disp || !out) return REG_EINVAL;
+  return guarded(c, [&] {
+    Level& F = c->fine;
+    const float* cu = coefficients(c, F, u, 1, F.coef);
+    launch_gather(F.g.n1, F.g.n2, cu, disp, out, 1, 0, lagrange(c), c->st);
+    check_launch(c, "interpolate");
+  });
+}
+
+reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* out) {
+  if (!c || !in || !out || in == out) return REG_EINVAL;
+  return guarded(c, [&] {
+    Level& F = c->fine;
+    switch (op) {
+      case REG_SPEC_GRAD: spectral(c, F, SPOP_GRAD, 0.0, in, 1, 1, out, 2, nullptr); break;
+      case REG_SPEC_DIV: spectral(c, F, SPOP_DIV, 0.0, in, 2, 1, out, 1, nullptr); break;
+      case REG_SPEC_REG: spectral(c, F, SPOP_REGPOW, 1.0, in, 1, 2, out, 1, nullptr); break;
+      case REG_SPEC_REGPOW:
+        if (s == 1.0) fail(c, REG_EINVAL, "REGPOW with s = 1: use REG_SPEC_REG");
+        spectral(c, F, SPOP_REGPOW, s, in, 1, 2, out, 1, nullptr);
+        break;
+      case REG_SPEC_LOWPASS: spectral(c, F, SPOP_LOWPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
+      case REG_SPEC_HIGHPASS: spectral(c, F, SPOP_HIGHPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
+      case REG_SPEC_PREFILTER:
+        if (lagrange(c)) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
+        coefficients(c, F, in, 1, out);
+        break;
+      default: fail(c, REG_EINVAL, "unknown spectral op %d", op);
+    }
+  });
+}
+
+reg_status reg_restrict(reg_ctx* c, const float* fine, float* coarse) {
+  if (!c || !fine || !coarse) return REG_EINVAL;
+  if (!c->two_level) { c->err = "restriction needs the two-level context"; return REG_ESTATE; }
+  return guarded(c, [&] { resample(c, c->fine, c->coarse, SPOP_SCALE, 0.0, fine, 2, coarse, nullptr); });
+}
+
+reg_status reg_prolong(reg_ctx* c, const float* coarse, float* fine) {
+  if (!c || !fine || !coarse) return REG_EINVAL;
+  if (!c->two_level) { c->err = "prolongation needs the two-level context"; return REG_ESTATE; }
+  return guarded(c, [&] { resample(c, c->coarse, c->fine, SPOP_SCALE, 0.0, coarse, 2, fine, nullptr); });
+}
+
+reg_status reg_objective_gradient(reg_ctx* c, const float* v, double* J, float* g) {
+  if (!c || !v || !J) return REG_EINVAL;
+  return guarded(c, [&] {
+    require_images(c);
+    *J = objective_gradient(c, v, g);
+  });
+}
+
+reg_status reg_objective(reg_ctx* c, const float* v, double* J) {
+  return reg_objective_gradient(c, v, J, nullptr);
+}
+
+// compare v with the cached velocity; rebuild the cache if it differs
+static void sync_velocity(reg_ctx* c, const float* v) {
+  Level& F = c->fine;
+  const long long n = 2 * F.g.N;
+  bool differ = true;
+  if (F.have_v) {
+    check(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "memset");
+    launch_compare(v, F.v, n, c->dflag, c->st);
+    check(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "flag");
+    check(c, cudaStreamSynchronize(c->st), "sync");
+    differ = (*c->hflag != 0);
+  }
+  if (differ) set_velocity(c, F, v);
+}
+
+reg_status reg_hessian_matvec(reg_ctx* c, const float* v, const float* vt, float* Hvt) {
+  if (!c || !v || !vt || !Hvt) return REG_EINVAL;
+  return guarded(c, [&] {
+    require_images(c);
+    sync_velocity(c, v);
+    hessian(c, c->fine, vt, Hvt, false);
+  });
+}
+
+reg_status reg_precond_apply(reg_ctx* c, const float* r, float* z) {
+  if (!c || !r || !z) return REG_EINVAL;
+  return guarded(c, [&] {
+    require_images(c);
+    if (!c->fine.have_v) fail(c, REG_ESTATE, "no cached velocity: call reg_objective_gradient first");
+    if (c->two_level) {
+      if (!c->have_eig) estimate_eigenvalues(c);
+      coarse_velocity(c);
+    }
+    precond(c, r, z);
+  });
+}
+
+reg_status reg_kkt_solve(reg_ctx* c, const float* v, const float* rhs, double rtol, int maxit,
+                         float* x, reg_info* info) {
+  if (!c || !v || !rhs || !x || maxit < 1) return REG_EINVAL;
+  return guarded(c, [&] {
+    require_images(c);
+    sync_velocity(c, v);
+    c->eta = rtol;
+    c->coarse_matvecs = 0;
+    const PcgResult r = kkt(c, rhs, rtol, maxit, x);
+    if (info) {
+      std::memset(info, 0, sizeof *info);
+      info->pcg_iters = r.iters;
+      info->matvecs = r.matvecs;
+      info->coarse_matvecs = c->coarse_matvecs;
+      info->gnorm_rel = r.relres;
+      info->status = r.negcurv ? REG_ENEGCURV : REG_OK;
+    }
+  });
+}
+
+reg_status reg_eigen_bounds(reg_ctx* c, double* emin, double* emax) {
+  if (!c || !emin || !emax) return REG_EINVAL;
+  if (!c->two_level) { c->err = "eigenvalue bounds belong to the two-level preconditioner"; return REG_ESTATE; }
+  return guarded(c, [&] {
+    require_images(c);
+    estimate_eigenvalues(c);
+    *emin = c->emin;
+    *emax = c->emax;
+  });
+}
+
+reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
+  if (!c || !a || !b || !out || n < 0) return REG_EINVAL;
+  return guarded(c, [&] { *out = dot_sync(c, a, b, n, S_C); });
+}
+
+reg_status reg_solve(reg_ctx* c, float* v, double gtol, reg_info* info) {
+  if (!c || !v || !(gtol > 0.0)) return REG_EINVAL;
+  reg_status result = REG_OK;
+  reg_info inf;
+  std::memset(&inf, 0, sizeof inf);
+  const auto t0 = std::chrono::steady_clock::now();
+  const reg_status s = guarded(c, [&] {
+    require_images(c);
+    Level& F = c->fine;
+    const long long n = 2 * F.g.N;
+    const double hh = F.h1 * F.h2;
+    ensure_gref(c);
+    inf.gref_inf = c->gref_inf;
+    double J = objective_gradient(c, v, c->gcur);
+    inf.J0 = J;
+    double rel = 1.0, ginf = 0.0;
+    c->coarse_matvecs = 0;
+    for (int k = 0;; ++k) {
+      ginf = max_abs_sync(c, c->gcur, n, S_GINF);
+      if (!std::isfinite(ginf) || !std::isfinite(J)) { result = REG_ENONFINITE; break; }
+      rel = ginf / c->gref_inf;
+      if (rel <= gtol || ginf <= c->opt.gabs) break;
+      if (k == c->opt.max_newton) { result = REG_ENOTCONV; break; }
+      const double g2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n, S_G2));
+      c->eta = std::fmin(0.5, g2 / c->gref_2);
+      launch_lincomb(n, -1.f, c->gcur, 0.f, nullptr, c->vt_tmp, c->st);   // rhs = -g
+      const PcgResult pr = kkt(c, c->vt_tmp, c->eta, c->opt.max_pcg, c->kx);
+      inf.pcg_iters += pr.iters;
+      inf.matvecs += pr.matvecs;
+      const double slope = hh * dot_sync(c, c->gcur, c->kx, n, S_D);
+      double alpha = 1.0, Jt = J;
+      bool ok = false;
+      for (int ls = 0; ls <= c->opt.max_backtracks; ++ls) {
+        launch_lincomb(n, 1.f, v, (float)alpha, c->kx, c->vtrial, c->st);
+        set_velocity(c, F, c->vtrial);
+        Jt = objective(c, F);
+        ++inf.line_search_steps;
+        if (Jt <= J + c->opt.armijo_c1 * alpha * slope) { ok = true; break; }
+        alpha *= 0.5;
+      }
+      if (!ok) {
+        set_velocity(c, F, v);
+        objective(c, F);
+        result = REG_ELINESEARCH;
+        break;
+      }
+      check(c, cudaMemcpyAsync(v, c->vtrial, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "accept");
+      J = Jt;
+      gradient(c, F, c->gcur);
+      ++inf.newton_iters;
+    }
+    inf.J = J;
+    inf.gnorm_rel = rel;
+    inf.gnorm_inf = ginf;
+    inf.coarse_matvecs = c->coarse_matvecs;
+    check(c, cudaStreamSynchronize(c->st), "sync");
+  });
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (s != REG_OK) result = s;
+  inf.status = result;
+  if (info) *info = inf;
+  return result;
+}
+
+}  // extern "C"

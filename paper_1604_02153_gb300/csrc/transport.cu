@@ -1,0 +1,337 @@
+// Semi-Lagrangian kernels: spline prefilter, RK2 departure points, periodic
+// 4x4 cubic interpolation and the fused transport steps of the state,
+// adjoint, incremental state and incremental adjoint equations
+// (§3.3.2, eq. hyperbolic-pdes-slm, eq. characteristic,
+// eq. transport-along-characteristic; §3.5 "Interpolation").
+//
+// Displacements are stored in cell units, d = (X_D - x) / h, so that the
+// node index and the sub-cell offset stay separate in FP32: the stencil base
+// is i + floor(d) and the weights use t = d - floor(d), both exact.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace regnk {
+
+// ---------------------------------------------------------------------------
+// Periodic cubic B-spline prefilter.
+//
+// The spline interpolant sum_m c[m] beta3(x - m) takes the node values
+// (c[k-1] + 4 c[k] + c[k+1]) / 6 per axis. Its inverse factors into a causal
+// and an anticausal first-order recursion with pole z1 = sqrt(3) - 2:
+//     y[k] = s[k] + z1 y[k-1],   c'[k] = y[k] + z1 c'[k+1],   c = -6 z1 c'.
+// On the torus each recursion is started W = 14 samples before the segment
+// it produces (|z1|^14 < 1e-8, below FP32 resolution), so every thread
+// filters an independent 16-sample segment with a 14-sample warm-up on each
+// side, read from the periodic neighbours.
+constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
+constexpr float kGain = 1.60769515458673624f;   // -6 z1
+constexpr int kW = 14;                          // warm-up length
+constexpr int kSeg = 16;                        // samples per thread
+constexpr int kLen = kSeg + 2 * kW;             // samples a thread touches
+
+__device__ __forceinline__ void iir_segment(const float (&s)[kLen], float (&out)[kSeg]) {
+  float y[kLen];
+  y[0] = s[0];
+#pragma unroll
+  for (int i = 1; i < kLen; ++i) y[i] = fmaf(kZ1, y[i - 1], s[i]);
+  float c = y[kLen - 1];
+#pragma unroll
+  for (int i = kLen - 2; i >= kW; --i) {
+    c = fmaf(kZ1, c, y[i]);
+    if (i < kW + kSeg) out[i - kW] = kGain * c;
+  }
+}
+
+// x pass: a block filters 32 rows x TX columns (TX = min(128, n1)).
+template <int TX>
+__global__ void __launch_bounds__(32 * (TX / kSeg))
+k_prefilter_x(const float* __restrict__ in, float* __restrict__ out, int n1, int log1,
+              long long fstride) {
+  constexpr int SEGS = TX / kSeg;
+  constexpr int NT = 32 * SEGS;
+  constexpr int WIDTH = TX + 2 * kW;
+  constexpr int PITCH = WIDTH + 1;           // odd pitch: conflict-free column walks
+  constexpr int OPITCH = TX + 1;
+  __shared__ float sin_[32 * PITCH];
+  __shared__ float sout[32 * OPITCH];
+  const int t = threadIdx.x;
+  const int x0 = blockIdx.x * TX;
+  const int y0 = blockIdx.y * 32;
+  const long long fo = (long long)blockIdx.z * fstride;
+  const float* src = in + fo;
+  for (int q = t; q < 32 * WIDTH; q += NT) {
+    const int r = q / WIDTH, c = q - r * WIDTH;
+    const int gx = (x0 - kW + c) & (n1 - 1);
+    sin_[r * PITCH + c] = __ldg(src + ((long long)(y0 + r) << log1) + gx);
+  }
+  __syncthreads();
+  const int r = t & 31, sg = t >> 5;
+  float s[kLen], o[kSeg];
+#pragma unroll
+  for (int i = 0; i < kLen; ++i) s[i] = sin_[r * PITCH + sg * kSeg + i];
+  iir_segment(s, o);
+#pragma unroll
+  for (int i = 0; i < kSeg; ++i) sout[r * OPITCH + sg * kSeg + i] = o[i];
+  __syncthreads();
+  float* dst = out + fo;
+  for (int q = t; q < 32 * TX; q += NT) {
+    const int rr = q / TX, c = q - rr * TX;
+    dst[((long long)(y0 + rr) << log1) + x0 + c] = sout[rr * OPITCH + c];
+  }
+}
+
+// y pass: a block filters 32 columns x TY rows; each thread walks one column
+// segment straight from global memory (a warp reads 32 adjacent columns).
+template <int TY>
+__global__ void __launch_bounds__(32 * (TY / kSeg))
+k_prefilter_y(const float* __restrict__ in, float* __restrict__ out, int n1, int n2,
+              int log1, long long fstride) {
+  const int t = threadIdx.x;
+  const int x = blockIdx.x * 32 + (t & 31);
+  const int ys = blockIdx.y * TY + (t >> 5) * kSeg;
+  const long long fo = (long long)blockIdx.z * fstride;
+  const float* src = in + fo;
+  float s[kLen], o[kSeg];
+#pragma unroll
+  for (int i = 0; i < kLen; ++i) {
+    const int gy = (ys - kW + i) & (n2 - 1);
+    s[i] = __ldg(src + ((long long)gy << log1) + x);
+  }
+  iir_segment(s, o);
+  float* dst = out + fo;
+#pragma unroll
+  for (int i = 0; i < kSeg; ++i) dst[((long long)(ys + i) << log1) + x] = o[i];
+}
+
+static int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
+                      cudaStream_t st) {
+  const int l1 = ilog2i(n1);
+  const long long N = (long long)n1 * n2;
+  if (n1 >= 128) {
+    k_prefilter_x<128><<<dim3(n1 / 128, n2 / 32, F), 256, 0, st>>>(in, tmp, n1, l1, N);
+  } else if (n1 == 64) {
+    k_prefilter_x<64><<<dim3(1, n2 / 32, F), 128, 0, st>>>(in, tmp, n1, l1, N);
+  } else {
+    k_prefilter_x<32><<<dim3(1, n2 / 32, F), 64, 0, st>>>(in, tmp, n1, l1, N);
+  }
+  if (n2 >= 128) {
+    k_prefilter_y<128><<<dim3(n1 / 32, n2 / 128, F), 256, 0, st>>>(tmp, out, n1, n2, l1, N);
+  } else if (n2 == 64) {
+    k_prefilter_y<64><<<dim3(n1 / 32, 1, F), 128, 0, st>>>(tmp, out, n1, n2, l1, N);
+  } else {
+    k_prefilter_y<32><<<dim3(n1 / 32, 1, F), 64, 0, st>>>(tmp, out, n1, n2, l1, N);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4x4 periodic cubic interpolation at node (i, j) + (d1, d2) cells.
+struct Stencil {
+  int ii[4];
+  int jj[4];   // row offsets (already multiplied by n1)
+  float w1[4], w2[4];
+};
+
+__device__ __forceinline__ void cubic_weights(float t, float (&w)[4], bool lagrange) {
+  if (lagrange) {  // cubic Lagrange on nodes -1, 0, 1, 2
+    const float tm1 = t - 1.f, tm2 = t - 2.f, tp1 = t + 1.f;
+    w[0] = -t * tm1 * tm2 * (1.f / 6.f);
+    w[1] = tp1 * tm1 * tm2 * 0.5f;
+    w[2] = -tp1 * t * tm2 * 0.5f;
+    w[3] = tp1 * t * tm1 * (1.f / 6.f);
+  } else {         // centred cubic B-spline
+    const float s = 1.f - t, t2 = t * t, t3 = t2 * t;
+    w[0] = s * s * s * (1.f / 6.f);
+    w[1] = (3.f * t3 - 6.f * t2 + 4.f) * (1.f / 6.f);
+    w[2] = (-3.f * t3 + 3.f * t2 + 3.f * t + 1.f) * (1.f / 6.f);
+    w[3] = t3 * (1.f / 6.f);
+  }
+}
+
+__device__ __forceinline__ Stencil make_stencil(int i, int j, float d1, float d2, int n1,
+                                                int n2, int log1, bool lagrange) {
+  Stencil S;
+  const float f1 = floorf(d1), f2 = floorf(d2);
+  cubic_weights(d1 - f1, S.w1, lagrange);
+  cubic_weights(d2 - f2, S.w2, lagrange);
+  const int i0 = i + (int)f1 - 1, j0 = j + (int)f2 - 1;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    S.ii[a] = (i0 + a) & (n1 - 1);
+    S.jj[a] = ((j0 + a) & (n2 - 1)) << log1;
+  }
+  return S;
+}
+
+__device__ __forceinline__ float apply_stencil(const Stencil& S, const float* __restrict__ c) {
+  float acc = 0.f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float* row = c + S.jj[b];
+    const float r = S.w1[0] * __ldg(row + S.ii[0]) + S.w1[1] * __ldg(row + S.ii[1]) +
+                    S.w1[2] * __ldg(row + S.ii[2]) + S.w1[3] * __ldg(row + S.ii[3]);
+    acc = fmaf(S.w2[b], r, acc);
+  }
+  return acc;
+}
+
+constexpr int kPT = 256;  // threads per block of the pointwise kernels
+
+// Departure points of both characteristics (Heun, §3.3.2):
+//   X* = x - h_t v(x),  X_D = x - h_t/2 (v(x) + v(X*))
+//   Y* = x + h_t v(x),  Y_D = x + h_t/2 (v(x) + v(Y*))
+// cv holds the interpolation coefficients of v (spline) or v itself.
+__global__ void __launch_bounds__(kPT)
+k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restrict__ v,
+            const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
+            int lagrange) {
+  const long long N = (long long)n1 * n2;
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
+  const float v1 = __ldg(v + idx), v2 = __ldg(v + N + idx);
+  const float a1 = s1 * v1, a2 = s2 * v2;   // h_t v / h in cells
+  if (dX) {
+    const Stencil S = make_stencil(i, j, -a1, -a2, n1, n2, log1, lagrange);
+    const float w1 = apply_stencil(S, cv), w2 = apply_stencil(S, cv + N);
+    dX[idx] = -0.5f * (a1 + s1 * w1);
+    dX[N + idx] = -0.5f * (a2 + s2 * w2);
+  }
+  if (dY) {
+    const Stencil S = make_stencil(i, j, a1, a2, n1, n2, log1, lagrange);
+    const float w1 = apply_stencil(S, cv), w2 = apply_stencil(S, cv + N);
+    dY[idx] = 0.5f * (a1 + s1 * w1);
+    dY[N + idx] = 0.5f * (a2 + s2 * w2);
+  }
+}
+
+void launch_departure(int n1, int n2, float ht, const float* v, const float* cv, float* dX,
+                      float* dY, int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  const float s1 = ht * n1 / (2.0f * 3.14159265358979323846f);
+  const float s2 = ht * n2 / (2.0f * 3.14159265358979323846f);
+  k_departure<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), s1, s2, v,
+                                                                cv, dX, dY, lagrange);
+}
+
+// out_f = I[coef_f](x + disp), f = 0..F-1 (fields fstride apart), one stencil.
+__global__ void __launch_bounds__(kPT)
+k_gather(int n1, int n2, int log1, const float* __restrict__ coef,
+         const float* __restrict__ disp, float* __restrict__ out, int F, long long fstride,
+         int lagrange) {
+  const long long N = (long long)n1 * n2;
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
+  const Stencil S = make_stencil(i, j, __ldg(disp + idx), __ldg(disp + N + idx), n1, n2, log1,
+                                 lagrange);
+  for (int f = 0; f < F; ++f) out[f * fstride + idx] = apply_stencil(S, coef + f * fstride);
+}
+
+void launch_gather(int n1, int n2, const float* coef, const float* disp, float* out, int F,
+                   long long fstride, int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  k_gather<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), coef, disp,
+                                                             out, F, fstride, lagrange);
+}
+
+void launch_state_step(int n1, int n2, const float* coef, const float* dX, float* out,
+                       int lagrange, cudaStream_t st) {
+  launch_gather(n1, n2, coef, dX, out, 1, 0, lagrange, st);
+}
+
+// Final condition of an adjoint solve and the first term of its time
+// integral: lam = sign * (mR - m1) (mR may be NULL: lam = -sign * m1),
+// b = coef_b * lam * grad m.
+__global__ void __launch_bounds__(kPT)
+k_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
+               const float* __restrict__ m1, const float* __restrict__ gm,
+               float* __restrict__ lam, float* __restrict__ b, float sign) {
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const float r = (mR ? __ldg(mR + idx) : 0.f) - __ldg(m1 + idx);
+  const float l = sign * r;
+  lam[idx] = l;
+  b[idx] = coef_b * l * __ldg(gm + idx);
+  b[N + idx] = coef_b * l * __ldg(gm + N + idx);
+}
+
+void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const float* m1,
+                         const float* gm, float* lam, float* b, float sign, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  k_adjoint_init<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(N, coef_b, mR, m1, gm, lam,
+                                                                  b, sign);
+}
+
+// One backward step of the (incremental) adjoint along Y_D (§3.3.2, Heun):
+//   lb = lam_{j+1}(Y_D), lam* = lb + h_t lb div v(Y_D),
+//   lam_j = lb + h_t/2 (lb div v(Y_D) + lam* div v(x)),
+// fused with the time integral b += wb * lam_j * grad m_j.
+__global__ void __launch_bounds__(kPT)
+k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ coef,
+               const float* __restrict__ dY, const float* __restrict__ delta,
+               const float* __restrict__ delta_bar, const float* __restrict__ gm,
+               float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
+  const long long N = (long long)n1 * n2;
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
+  const Stencil S = make_stencil(i, j, __ldg(dY + idx), __ldg(dY + N + idx), n1, n2, log1,
+                                 lagrange);
+  const float lb = apply_stencil(S, coef);
+  const float db = __ldg(delta_bar + idx), d = __ldg(delta + idx);
+  const float lstar = fmaf(ht * lb, db, lb);
+  const float l = lb + 0.5f * ht * (lb * db + lstar * d);
+  lam_out[idx] = l;
+  b[idx] = fmaf(wb * l, __ldg(gm + idx), b[idx]);
+  b[N + idx] = fmaf(wb * l, __ldg(gm + N + idx), b[N + idx]);
+}
+
+void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
+                         const float* dY, const float* delta, const float* delta_bar,
+                         const float* gm, float* lam_out, float* b, int lagrange,
+                         cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  k_adjoint_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
+      n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
+}
+
+// One forward step of the incremental state (Gauss-Newton, §3.3.2):
+//   m~_j = m~_{j-1}(X_D) - h_t/2 (v~(X_D) . grad m_{j-1}(X_D) + v~ . grad m_j)
+// G = grad m_{j-1}(X_D) (2 fields), vtD = v~(X_D) (2 fields), gm = grad m_j.
+// first = 1 for j = 1 where m~_0 = 0.
+__global__ void __launch_bounds__(kPT)
+k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ coef,
+                const float* __restrict__ dX, const float* __restrict__ vt,
+                const float* __restrict__ vtD, const float* __restrict__ G,
+                const float* __restrict__ gm, float* __restrict__ out, int first,
+                int lagrange) {
+  const long long N = (long long)n1 * n2;
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  float base = 0.f;
+  if (!first) {
+    const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
+    const Stencil S = make_stencil(i, j, __ldg(dX + idx), __ldg(dX + N + idx), n1, n2, log1,
+                                   lagrange);
+    base = apply_stencil(S, coef);
+  }
+  const float src_dep = __ldg(vtD + idx) * __ldg(G + idx) + __ldg(vtD + N + idx) * __ldg(G + N + idx);
+  const float src_arr = __ldg(vt + idx) * __ldg(gm + idx) + __ldg(vt + N + idx) * __ldg(gm + N + idx);
+  out[idx] = base - 0.5f * ht * (src_dep + src_arr);
+}
+
+void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
+                          const float* vt, const float* vtD, const float* G, const float* gm,
+                          float* out, int first, int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  k_incstate_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
+      n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange);
+}
+
+}  // namespace regnk

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libregnk.so (the C ABI declared in include/reg.h).
+
+Argument marshalling only: every step of the registration path runs in the
+library's CUDA kernels. Field arguments are torch tensors on the CUDA device
+(float32, contiguous); the binding passes their device pointers and the
+current torch stream. There is no CPU fallback: if the library is missing or
+the CUDA runtime is unavailable, the calls raise.
+"""
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libregnk.so")
+
+REG_OK, REG_EINVAL, REG_ENOMEM, REG_ECUDA, REG_ESTATE = 0, 1, 2, 3, 4
+REG_ENOTCONV, REG_ELINESEARCH, REG_ENEGCURV, REG_ENONFINITE, REG_ETIMEOUT = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "REG_OK", 1: "REG_EINVAL", 2: "REG_ENOMEM", 3: "REG_ECUDA", 4: "REG_ESTATE",
+                5: "REG_ENOTCONV", 6: "REG_ELINESEARCH", 7: "REG_ENEGCURV",
+                8: "REG_ENONFINITE", 9: "REG_ETIMEOUT"}
+REG_H1, REG_H2, REG_H3 = 1, 2, 3
+REG_INTERP_SPLINE, REG_INTERP_LAGRANGE = 0, 1
+REG_PC_REG, REG_PC_2L = 0, 1
+REG_PCSOLVER_CHEB, REG_PCSOLVER_PCG = 0, 1
+REG_SPEC_GRAD, REG_SPEC_DIV, REG_SPEC_REG, REG_SPEC_REGPOW = 0, 1, 2, 3
+REG_SPEC_LOWPASS, REG_SPEC_HIGHPASS, REG_SPEC_PREFILTER = 4, 5, 6
+
+
+class RegError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class reg_grid(ctypes.Structure):
+    _fields_ = [("n1", ctypes.c_int), ("n2", ctypes.c_int)]
+
+
+class reg_options(ctypes.Structure):
+    _fields_ = [("reg_norm", ctypes.c_int), ("interp", ctypes.c_int), ("precond", ctypes.c_int),
+                ("pc_solver", ctypes.c_int), ("cheb_iters", ctypes.c_int),
+                ("pc_eps", ctypes.c_double), ("gabs", ctypes.c_double),
+                ("max_newton", ctypes.c_int), ("max_pcg", ctypes.c_int),
+                ("lanczos_steps", ctypes.c_int), ("emax_safety", ctypes.c_double),
+                ("lanczos_seed", ctypes.c_ulonglong), ("max_backtracks", ctypes.c_int),
+                ("armijo_c1", ctypes.c_double)]
+
+
+class reg_info(ctypes.Structure):
+    _fields_ = [("newton_iters", ctypes.c_int), ("pcg_iters", ctypes.c_int),
+                ("matvecs", ctypes.c_int), ("coarse_matvecs", ctypes.c_int),
+                ("line_search_steps", ctypes.c_int), ("J0", ctypes.c_double),
+                ("J", ctypes.c_double), ("gnorm_rel", ctypes.c_double),
+                ("gnorm_inf", ctypes.c_double), ("gref_inf", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_SIGNATURES = {
+    "reg_default_options": [ctypes.POINTER(reg_options)],
+    "reg_create": [reg_grid, _I, _D, ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
+    "reg_destroy": [_P],
+    "reg_set_stream": [_P, _P],
+    "reg_set_images": [_P, _P, _P],
+    "reg_set_beta": [_P, _D],
+    "reg_transport": [_P, _P, _P, _P],
+    "reg_departure_points": [_P, _P, _P, _P],
+    "reg_interpolate": [_P, _P, _P, _P],
+    "reg_spectral": [_P, _I, _D, _P, _P],
+    "reg_restrict": [_P, _P, _P],
+    "reg_prolong": [_P, _P, _P],
+    "reg_objective_gradient": [_P, _P, ctypes.POINTER(_D), _P],
+    "reg_objective": [_P, _P, ctypes.POINTER(_D)],
+    "reg_hessian_matvec": [_P, _P, _P, _P],
+    "reg_precond_apply": [_P, _P, _P],
+    "reg_kkt_solve": [_P, _P, _P, _D, _I, _P, ctypes.POINTER(reg_info)],
+    "reg_eigen_bounds": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    "reg_solve": [_P, _P, _D, ctypes.POINTER(reg_info)],
+    "reg_dot": [_P, _P, _P, ctypes.c_longlong, ctypes.POINTER(_D)],
+    "reg_last_error": [_P],
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libregnk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1604_02153_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, args in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_char_p if name == "reg_last_error" else ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(t, numel=None, name="tensor"):
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_options(**overrides):
+    o = reg_options()
+    load().reg_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Registration:
+    """One registration problem: a reg_ctx handle plus argument checking.
+
+    Methods carry the C names without the ``reg_`` prefix; each passes the
+    tensors' device pointers and the current torch CUDA stream.
+    """
+
+    def __init__(self, n1, n2, nt, beta, **options):
+        import torch
+        self.lib = load()
+        self.n1, self.n2, self.nt = int(n1), int(n2), int(nt)
+        self.N = self.n1 * self.n2
+        self.options = default_options(**options)
+        self.device = torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        s = self.lib.reg_create(reg_grid(self.n1, self.n2), self.nt, float(beta),
+                                ctypes.byref(self.options), ctypes.byref(h))
+        if s != REG_OK:
+            raise RegError(s, "reg_create failed")
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.reg_destroy(h)
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def _call(self, name, *args):
+        import torch
+        self.lib.reg_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = getattr(self.lib, name)(self.h, *args)
+        if s not in (REG_OK,):
+            raise RegError(s, self.lib.reg_last_error(self.h).decode())
+        return s
+
+    # -- calls of include/reg.h ---------------------------------------------
+    def set_images(self, m_R, m_T):
+        self._call("reg_set_images", _ptr(m_R, self.N, "m_R"), _ptr(m_T, self.N, "m_T"))
+
+    def set_beta(self, beta):
+        self._call("reg_set_beta", float(beta))
+
+    def transport(self, v, m0, m1):
+        self._call("reg_transport", _ptr(v, 2 * self.N, "v"), _ptr(m0, self.N, "m0"),
+                   _ptr(m1, self.N, "m1"))
+
+    def departure_points(self, v, dX=None, dY=None):
+        self._call("reg_departure_points", _ptr(v, 2 * self.N, "v"),
+                   _ptr(dX, 2 * self.N, "dX"), _ptr(dY, 2 * self.N, "dY"))
+
+    def interpolate(self, u, disp, out):
+        self._call("reg_interpolate", _ptr(u, self.N, "u"), _ptr(disp, 2 * self.N, "disp"),
+                   _ptr(out, self.N, "out"))
+
+    def spectral(self, op, inp, out, s=0.0):
+        self._call("reg_spectral", int(op), float(s), _ptr(inp, name="in"), _ptr(out, name="out"))
+
+    def restrict(self, fine, coarse):
+        self._call("reg_restrict", _ptr(fine, 2 * self.N, "fine"), _ptr(coarse, self.N // 2, "coarse"))
+
+    def prolong(self, coarse, fine):
+        self._call("reg_prolong", _ptr(coarse, self.N // 2, "coarse"), _ptr(fine, 2 * self.N, "fine"))
+
+    def objective_gradient(self, v, g=None):
+        J = ctypes.c_double()
+        self._call("reg_objective_gradient", _ptr(v, 2 * self.N, "v"), ctypes.byref(J),
+                   _ptr(g, 2 * self.N, "g"))
+        return J.value
+
+    def objective(self, v):
+        J = ctypes.c_double()
+        self._call("reg_objective", _ptr(v, 2 * self.N, "v"), ctypes.byref(J))
+        return J.value
+
+    def hessian_matvec(self, v, vt, Hvt):
+        self._call("reg_hessian_matvec", _ptr(v, 2 * self.N, "v"), _ptr(vt, 2 * self.N, "vt"),
+                   _ptr(Hvt, 2 * self.N, "Hvt"))
+
+    def precond_apply(self, r, z):
+        self._call("reg_precond_apply", _ptr(r, 2 * self.N, "r"), _ptr(z, 2 * self.N, "z"))
+
+    def kkt_solve(self, v, rhs, rtol, maxit, x):
+        info = reg_info()
+        self._call("reg_kkt_solve", _ptr(v, 2 * self.N, "v"), _ptr(rhs, 2 * self.N, "rhs"),
+                   float(rtol), int(maxit), _ptr(x, 2 * self.N, "x"), ctypes.byref(info))
+        return info.as_dict()
+
+    def eigen_bounds(self):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        self._call("reg_eigen_bounds", ctypes.byref(lo), ctypes.byref(hi))
+        return lo.value, hi.value
+
+    def solve(self, v, gtol, allow=(REG_OK,)):
+        import torch
+        info = reg_info()
+        self.lib.reg_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = self.lib.reg_solve(self.h, _ptr(v, 2 * self.N, "v"), float(gtol), ctypes.byref(info))
+        if s not in allow:
+            raise RegError(s, self.lib.reg_last_error(self.h).decode())
+        d = info.as_dict()
+        d["status_name"] = STATUS_NAMES.get(s, str(s))
+        return d
+
+    def dot(self, a, b):
+        out = ctypes.c_double()
+        self._call("reg_dot", _ptr(a, name="a"), _ptr(b, name="b"), ctypes.c_longlong(a.numel()),
+                   ctypes.byref(out))
+        return out.value
+
+
+def reg_create(n1, n2, nt, beta, **options):
+    """Python spelling of reg_create: returns a Registration handle."""
+    return Registration(n1, n2, nt, beta, **options)

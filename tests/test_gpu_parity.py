@@ -1,0 +1,336 @@
+"""GPU parity of every hot-path row against the FP64 oracle (CUDA required).
+
+Every call goes through the C ABI (libregnk.so) via the ctypes binding.
+Tolerances (relative L2 unless stated):
+* spectral operators, prefilter, interpolation:     1e-5 (FP32 rounding
+  of an O(log n)-deep FFT or a 16-term sum)
+* transported images, gradient, Hessian matvec:     1e-4 (the stated bar)
+* objective J (FP64 accumulation of FP32 fields):   1e-5 relative
+* final velocity of a full solve:                   1e-3 (the stated bar)
+Grids span several FFT tile shapes (square and non-square, 64..1024); the
+full-size 1024^2 workload is checked by closed forms and by properties that
+hold at any size (v = 0 Hessian and gradient, symmetry, positivity) and by a
+full-size transport against the oracle.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import interp as ointerp
+from oracle import spectral, transport
+from oracle.problem import Problem
+from oracle.solver import Solver
+from paper_1604_02153_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def regnk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1604_02153_gb300 import regnk as r
+    return r
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device="cuda")
+
+
+def host(t, shape):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64).reshape(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def problem_data(n1, n2, seed=0, vmax=0.2):
+    m_T = inputs.random_field(n1, n2, seed=seed + 1, kmax=8)
+    m_R = inputs.random_field(n1, n2, seed=seed + 2, kmax=8)
+    v = inputs.random_velocity(n1, n2, seed=seed + 3, vmax=vmax)
+    return m_R, m_T, v
+
+
+GRIDS = [(64, 64), (128, 64), (64, 256), (512, 512)]
+
+
+@pytest.mark.parametrize("n1,n2", GRIDS)
+def test_spectral_operators(regnk, n1, n2):
+    R = regnk.Registration(n1, n2, 4, 0.03)
+    u = inputs.random_field(n1, n2, seed=11, kmax=min(n1, n2) // 2 - 1)
+    v = inputs.random_velocity(n1, n2, seed=12, kmax=min(n1, n2) // 4, vmax=1.0)
+    N = n1 * n2
+    ud, vd = dev(u), dev(v)
+    out1, out2 = torch.empty(N, device="cuda"), torch.empty(2 * N, device="cuda")
+    R.spectral(regnk.REG_SPEC_GRAD, ud, out2)
+    assert rel(host(out2, (2, n2, n1)), spectral.grad(u)) < 1e-5
+    R.spectral(regnk.REG_SPEC_DIV, vd, out1)
+    assert rel(host(out1, (n2, n1)), spectral.div(v)) < 1e-5
+    R.spectral(regnk.REG_SPEC_REG, vd, out2)
+    assert rel(host(out2, (2, n2, n1)), spectral.apply_reg(v, 0.03, "H1")) < 1e-5
+    for s in (-1.0, -0.5, 0.5):
+        R.spectral(regnk.REG_SPEC_REGPOW, vd, out2, s)
+        assert rel(host(out2, (2, n2, n1)), spectral.reg_power(v, 0.03, "H1", s)) < 1e-5, s
+    R.spectral(regnk.REG_SPEC_LOWPASS, vd, out2)
+    low = np.stack([spectral.lowpass(v[c]) for c in range(2)])
+    assert rel(host(out2, (2, n2, n1)), low) < 1e-5
+    R.spectral(regnk.REG_SPEC_HIGHPASS, vd, out2)
+    high = np.stack([spectral.highpass(v[c]) for c in range(2)])
+    assert np.max(np.abs(host(out2, (2, n2, n1)) - high)) < 1e-5 * np.max(np.abs(v))
+    R.spectral(regnk.REG_SPEC_PREFILTER, ud, out1)
+    assert rel(host(out1, (n2, n1)), spectral.spline_prefilter(u)) < 1e-5
+    R.close()
+
+
+@pytest.mark.parametrize("norm,p", [("H2", 2), ("H3", 3)])
+def test_higher_order_regularisation(regnk, norm, p):
+    n = 128
+    R = regnk.Registration(n, n, 4, 0.05, reg_norm=p)
+    v = inputs.random_velocity(n, seed=13, kmax=12, vmax=1.0)
+    out = torch.empty(2 * n * n, device="cuda")
+    R.spectral(regnk.REG_SPEC_REG, dev(v), out)
+    assert rel(host(out, (2, n, n)), spectral.apply_reg(v, 0.05, norm)) < 1e-5
+    R.spectral(regnk.REG_SPEC_REGPOW, dev(v), out, -1.0)
+    assert rel(host(out, (2, n, n)), spectral.reg_power(v, 0.05, norm, -1.0)) < 1e-5
+    R.close()
+
+
+@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 256), (1024, 1024)])
+def test_restriction_prolongation(regnk, n1, n2):
+    R = regnk.Registration(n1, n2, 4, 1e-2)
+    v = inputs.random_velocity(n1, n2, seed=14, kmax=min(n1, n2) // 4, vmax=1.0)
+    c = torch.empty(n1 * n2 // 2, device="cuda")
+    R.restrict(dev(v), c)
+    rc = spectral.restrict_vec(v)
+    assert rel(host(c, (2, n2 // 2, n1 // 2)), rc) < 1e-5
+    f = torch.empty(2 * n1 * n2, device="cuda")
+    R.prolong(dev(rc), f)
+    assert rel(host(f, (2, n2, n1)), spectral.prolong_vec(rc)) < 1e-5
+    R.close()
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+@pytest.mark.parametrize("n1,n2,nt", [(128, 128, 4), (256, 64, 8)])
+def test_departure_points(regnk, kind, n1, n2, nt):
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp)
+    v = inputs.random_velocity(n1, n2, seed=15, vmax=0.5)
+    dX = torch.empty(2 * n1 * n2, device="cuda")
+    dY = torch.empty(2 * n1 * n2, device="cuda")
+    R.departure_points(dev(v), dX, dY)
+    eX = np.stack(transport.characteristic(v, nt, kind, backward=False))
+    eY = np.stack(transport.characteristic(v, nt, kind, backward=True))
+    assert np.max(np.abs(host(dX, (2, n2, n1)) - eX)) < 1e-4
+    assert np.max(np.abs(host(dY, (2, n2, n1)) - eY)) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+def test_interpolation(regnk, kind):
+    n1, n2 = 256, 128
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration(n1, n2, 4, 1e-2, interp=interp)
+    u = inputs.random_field(n1, n2, seed=16, kmax=16)
+    disp = inputs.random_velocity(n1, n2, seed=17, vmax=6.0)   # up to 6 cells, wraps
+    out = torch.empty(n1 * n2, device="cuda")
+    R.interpolate(dev(u), dev(disp), out)
+    I, J = ointerp.node_coordinates(n1, n2)
+    expect = ointerp.interp(u, I + disp[0], J + disp[1], kind)
+    assert rel(host(out, (n2, n1)), expect) < 1e-5
+    R.close()
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+@pytest.mark.parametrize("n1,n2,nt", [(64, 64, 4), (256, 128, 8), (128, 128, 16)])
+def test_transport(regnk, kind, n1, n2, nt):
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp)
+    _, m_T, v = problem_data(n1, n2, vmax=0.4)
+    m1 = torch.empty(n1 * n2, device="cuda")
+    R.transport(dev(v), dev(m_T), m1)
+    P = Problem(np.zeros((n2, n1)), m_T, nt, 1e-2, kind=kind)
+    assert rel(host(m1, (n2, n1)), P.state_solve(v)) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+@pytest.mark.parametrize("n1,n2,nt,norm", [(64, 64, 4, 1), (128, 64, 8, 1), (256, 256, 4, 2)])
+def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm):
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    beta = 1e-2
+    R = regnk.Registration(n1, n2, nt, beta, interp=interp, reg_norm=norm)
+    m_R, m_T, v = problem_data(n1, n2)
+    R.set_images(dev(m_R), dev(m_T))
+    P = Problem(m_R, m_T, nt, beta, reg_norm=f"H{norm}", kind=kind)
+    J_ref, g_ref = P.objective_gradient(v)
+    vd = dev(v)
+    g = torch.empty(2 * n1 * n2, device="cuda")
+    J = R.objective_gradient(vd, g)
+    assert abs(J - J_ref) / abs(J_ref) < 1e-5
+    assert rel(host(g, (2, n2, n1)), g_ref) < 1e-4
+    u = inputs.random_velocity(n1, n2, seed=21, vmax=1.0)
+    H = torch.empty(2 * n1 * n2, device="cuda")
+    R.hessian_matvec(vd, dev(u), H)
+    assert rel(host(H, (2, n2, n1)), P.hessian_matvec(u)) < 1e-4
+    R.close()
+
+
+def test_matvec_never_stale(regnk):
+    n, nt = 64, 4
+    R = regnk.Registration(n, n, nt, 1e-2)
+    m_R, m_T, v = problem_data(n, n)
+    R.set_images(dev(m_R), dev(m_T))
+    R.objective_gradient(dev(v), None)
+    v2 = 0.5 * v
+    u = inputs.random_velocity(n, seed=22, vmax=1.0)
+    H = torch.empty(2 * n * n, device="cuda")
+    R.hessian_matvec(dev(v2), dev(u), H)
+    P = Problem(m_R, m_T, nt, 1e-2)
+    P.state_solve(v2)
+    assert rel(host(H, (2, n, n)), P.hessian_matvec(u)) < 1e-4
+    H2 = torch.empty_like(H)
+    R.hessian_matvec(dev(v2), dev(u), H2)
+    torch.cuda.synchronize()
+    assert torch.equal(H, H2)          # deterministic: identical bits
+    R.close()
+
+
+def test_full_size_closed_forms(regnk):
+    """1024^2, nt = 8 (the benchmark workload): at v = 0 the gradient is
+    (m_R - m_T) grad m_T and the GN Hessian is beta A u + (u . grad m_T) grad m_T
+    exactly; checked against FP64 evaluations of those closed forms."""
+    n, nt, beta = 1024, 8, 1e-1
+    m_R, m_T = inputs.ellipse_phantoms(n, seed=100)
+    R = regnk.Registration(n, n, nt, beta)
+    R.set_images(dev(m_R), dev(m_T))
+    z = torch.zeros(2 * n * n, device="cuda")
+    g = torch.empty_like(z)
+    J = R.objective_gradient(z, g)
+    gm = spectral.grad(m_T)
+    hh = (2 * np.pi / n) ** 2
+    assert abs(J - 0.5 * hh * np.sum((m_R - m_T) ** 2)) / J < 1e-5
+    assert rel(host(g, (2, n, n)), (m_R - m_T) * gm) < 1e-4
+    u = inputs.random_velocity(n, seed=23, vmax=1.0)
+    H = torch.empty_like(z)
+    R.hessian_matvec(z, dev(u), H)
+    expect = spectral.apply_reg(u, beta, "H1") + (u[0] * gm[0] + u[1] * gm[1]) * gm
+    assert rel(host(H, (2, n, n)), expect) < 1e-4
+    R.close()
+
+
+def test_full_size_transport_symmetry_positivity(regnk):
+    n, nt = 1024, 8
+    m_R, m_T = inputs.ellipse_phantoms(n, seed=101)
+    v = inputs.random_velocity(n, seed=24, vmax=0.2)
+    R = regnk.Registration(n, n, nt, 1e-2)
+    m1 = torch.empty(n * n, device="cuda")
+    R.transport(dev(v), dev(m_T), m1)
+    P = Problem(np.zeros((n, n)), m_T, nt, 1e-2)
+    assert rel(host(m1, (n, n)), P.state_solve(v)) < 1e-4
+    R.set_images(dev(m_R), dev(m_T))
+    vd = dev(v)
+    R.objective_gradient(vd, None)
+    a = dev(inputs.random_velocity(n, seed=25, vmax=1.0))
+    b = dev(inputs.random_velocity(n, seed=26, vmax=1.0))
+    Ha, Hb = torch.empty_like(a), torch.empty_like(b)
+    R.hessian_matvec(vd, a, Ha)
+    R.hessian_matvec(vd, b, Hb)
+    hab, hba = R.dot(Ha, b), R.dot(a, Hb)
+    assert abs(hab - hba) / abs(hab) < 1e-3
+    assert R.dot(Ha, a) > 0
+    R.close()
+
+
+def test_preconditioners(regnk):
+    n, nt, beta = 128, 4, 1e-2
+    m_R, m_T, v = problem_data(n, n)
+    r = inputs.random_velocity(n, seed=27, vmax=1.0)
+    for pc in (regnk.REG_PC_REG, regnk.REG_PC_2L):
+        R = regnk.Registration(n, n, nt, beta, precond=pc)
+        R.set_images(dev(m_R), dev(m_T))
+        R.objective_gradient(dev(v), None)
+        z = torch.empty(2 * n * n, device="cuda")
+        R.precond_apply(dev(r), z)
+        P = Problem(m_R, m_T, nt, beta)
+        P.state_solve(v)
+        S = Solver(P, precond="REG" if pc == regnk.REG_PC_REG else "2L")
+        if pc == regnk.REG_PC_2L:
+            emin, emax = R.eigen_bounds()
+            S.eig = {"emin": emin, "emax": emax, "beta": beta}
+            S.set_velocity_coarse(v)
+        assert rel(host(z, (2, n, n)), S.apply_precond(r)) < 1e-4, pc
+        R.close()
+
+
+def test_eigen_bounds(regnk):
+    n, nt, beta = 128, 4, 1e-2
+    m_R, m_T, _ = problem_data(n, n)
+    R = regnk.Registration(n, n, nt, beta)
+    R.set_images(dev(m_R), dev(m_T))
+    emin, emax = R.eigen_bounds()
+    seed = regnk.default_options().lanczos_seed
+    nc = n // 2
+    v0 = inputs.splitmix64_uniform(2 * nc * nc, seed).reshape(2, nc, nc)
+    S = Solver(Problem(m_R, m_T, nt, beta), precond="2L", lanczos_v0=v0)
+    e = S.estimate_eigenvalues()
+    assert abs(emin - e["emin"]) < 1e-12 * e["emin"]
+    assert abs(emax - e["emax"]) / e["emax"] < 1e-3
+    R.close()
+
+
+def test_kkt_recovery(regnk):
+    """§4.2.2 first experiment: H x = H x*, x* = -0.5 v*, PCG from zero."""
+    n, nt, beta = 128, 4, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    R = regnk.Registration(n, n, nt, beta)
+    R.set_images(dev(m_R), dev(m_T))
+    vd = dev(vstar)
+    R.objective_gradient(vd, None)
+    xs = dev(-0.5 * vstar)
+    rhs = torch.empty_like(xs)
+    R.hessian_matvec(vd, xs, rhs)
+    x = torch.empty_like(xs)
+    info = R.kkt_solve(vd, rhs, 1e-6, 200, x)
+    torch.cuda.synchronize()
+    err = float(torch.linalg.norm(x - xs) / torch.linalg.norm(xs))
+    assert err < 1e-4, (err, info)
+    R.close()
+
+
+@pytest.mark.parametrize("pc,pcs", [("REG", "cheb"), ("2L", "cheb"), ("2L", "pcg")])
+def test_full_solve_64(regnk, pc, pcs):
+    """The 64^2 plain-method problem (analytic template and velocity, nt = 4,
+    H1, beta = 1e-2) solved to ||g||rel <= 1e-2 on the GPU and by the oracle."""
+    n, nt, beta, gtol = 64, 4, 1e-2, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    opts = {"precond": regnk.REG_PC_REG if pc == "REG" else regnk.REG_PC_2L,
+            "pc_solver": regnk.REG_PCSOLVER_CHEB if pcs == "cheb" else regnk.REG_PCSOLVER_PCG}
+    R = regnk.Registration(n, n, nt, beta, **opts)
+    R.set_images(dev(m_R), dev(m_T))
+    v = torch.zeros(2 * n * n, device="cuda")
+    info = R.solve(v, gtol)
+    seed = regnk.default_options().lanczos_seed
+    v0 = inputs.splitmix64_uniform(2 * (n // 2) ** 2, seed)
+    S = Solver(Problem(m_R, m_T, nt, beta), precond=pc, pc_solver=pcs, lanczos_v0=v0)
+    vo, oinfo = S.solve(np.zeros((2, n, n)), gtol)
+    assert info["gnorm_rel"] <= gtol
+    assert info["newton_iters"] == oinfo["newton_iters"]
+    assert rel(host(v, (2, n, n)), vo) < 1e-3
+    assert abs(info["J"] - oinfo["J"]) / oinfo["J"] < 1e-4
+    R.close()
+
+
+def test_invalid_call_order(regnk):
+    R = regnk.Registration(64, 64, 4, 1e-2)
+    with pytest.raises(regnk.RegError) as e:
+        R.objective_gradient(torch.zeros(2 * 64 * 64, device="cuda"), None)
+    assert e.value.status == regnk.REG_ESTATE
+    R.close()

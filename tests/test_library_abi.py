@@ -1,0 +1,85 @@
+"""The C-ABI library builds, loads and exports every declared entry point
+(CPU only: no call here launches a kernel).
+
+* every ``reg_*`` function declared in include/reg.h is exported by
+  libregnk.so and bound by the Python binding;
+* reg_default_options returns the documented defaults;
+* argument validation happens on the host (REG_EINVAL), and without a GPU
+  reg_create fails with REG_ECUDA: there is no CPU fallback.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1604_02153_gb300 import build as libbuild
+from paper_1604_02153_gb300 import regnk
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(regnk.LIB_PATH):
+        libbuild.build()
+    return regnk.load()
+
+
+def declared_functions(repo_root):
+    src = open(os.path.join(repo_root, "include", "reg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(reg_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib, repo_root):
+    names = declared_functions(repo_root)
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in regnk._SIGNATURES, name
+
+
+def test_default_options(lib):
+    o = regnk.default_options()
+    assert o.reg_norm == regnk.REG_H1
+    assert o.interp == regnk.REG_INTERP_SPLINE
+    assert o.precond == regnk.REG_PC_2L
+    assert o.pc_solver == regnk.REG_PCSOLVER_CHEB
+    assert o.cheb_iters == 10 and abs(o.pc_eps - 0.1) < 1e-15
+    assert abs(o.gabs - 1e-5) < 1e-20 and o.lanczos_steps == 30
+    assert o.max_backtracks == 10 and abs(o.armijo_c1 - 1e-4) < 1e-20
+
+
+def _create(lib, n1, n2, nt, beta, **kw):
+    h = ctypes.c_void_p()
+    o = regnk.default_options(**kw)
+    return lib.reg_create(regnk.reg_grid(n1, n2), nt, beta, ctypes.byref(o), ctypes.byref(h)), h
+
+
+@pytest.mark.parametrize("n1,n2,nt,beta,kw", [
+    (48, 64, 4, 1e-2, {}),           # not a power of two
+    (64, 16, 4, 1e-2, {}),           # below the minimum size
+    (64, 64, 0, 1e-2, {}),           # no time steps
+    (64, 64, 4, 0.0, {}),            # beta must be positive
+    (64, 64, 4, 1e-2, {"reg_norm": 4}),
+    (64, 64, 4, 1e-2, {"interp": 2}),
+    (32, 32, 4, 1e-2, {"precond": 1}),  # two-level needs a 32^2 coarse grid at least
+])
+def test_invalid_arguments_rejected_on_host(lib, n1, n2, nt, beta, kw):
+    s, h = _create(lib, n1, n2, nt, beta, **kw)
+    assert s == regnk.REG_EINVAL
+    assert not h.value
+
+
+def test_null_handles(lib):
+    assert lib.reg_set_images(None, None, None) == regnk.REG_EINVAL
+    assert lib.reg_destroy(None) == regnk.REG_OK
+    assert lib.reg_last_error(None) == b"null context"
+
+
+def test_no_cpu_fallback(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s, h = _create(lib, 64, 64, 4, 1e-2)
+    assert s == regnk.REG_ECUDA and not h.value
