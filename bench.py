@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the semi-Lagrangian Gauss-Newton-Krylov registration hot path.
+
+One step is one complete registration solve, i.e. one pass through every row
+of the hot path: departure points, cubic interpolation, state and adjoint
+transport, pseudospectral operators, objective and reduced gradient,
+incremental state and adjoint (GN Hessian matvec), PCG with the two-level
+preconditioner (spectral restriction/prolongation, Chebyshev(10) on the
+512^2 coarse grid), Armijo line search and the Newton loop.
+
+Workload: 1024^2 piecewise-smooth phantom pair (12 seeded random ellipses per
+image, Gaussian blur sigma = 2 px, second image with perturbed centres and
+axes), nt = 8, H1 regularisation with beta continuation 1e-1 -> 1e-2 -> 1e-3
+(warm started), stopping at ||g||_inf / ||g(0)||_inf <= 1e-2 per stage. FP32
+fields, FP64 reductions. Inputs are resident in HBM when timing starts; L2 is
+flushed between steps (256 MB write, untimed).
+
+value     = fine-grid GN Hessian matvecs per second of solve time (all ranks).
+e2e       = the same through the C-ABI with host buffers: pinned-host images
+            copied in, the velocity copied out, inside the timed region.
+roofline  = the kernel class with the largest device time in the timed
+            region: algorithmic bytes / its CUDA-event time, against the
+            measured HBM copy bandwidth.
+cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
+            timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian matvecs/s & time-to-‖g‖rel 1e-2 at 1024² 2D; chosen form vs plain FP32"
+UNIT = "matvecs/s"
+N_GRID = 1024
+NT = 8
+BETAS = (1e-1, 1e-2, 1e-3)
+GTOL = 1e-2
+FALLBACK_HBM_GBS = 6800.0
+CLASS_NAMES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
+               "adjoint_step", "incstate_step", "reduce", "vector"]
+# source file of each kernel class (a traffic figure is only valid for the
+# source it was captured from)
+CLASS_SOURCES = {"fft_rows": "fft.cu", "fft_cols": "fft.cu", "prefilter": "transport.cu",
+                 "departure": "transport.cu", "gather": "transport.cu",
+                 "adjoint_step": "transport.cu", "incstate_step": "transport.cu",
+                 "reduce": "reduce.cu", "vector": "reduce.cu"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash(fname):
+    path = os.path.join(ROOT, "paper_1604_02153_gb300", "csrc", fname)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+def ncu_traffic(cls, launches_bytes_per_launch):
+    """Per-launch DRAM traffic of a kernel class from the committed ncu
+    summary, or None if absent or captured from a different source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(cls)
+    if not e or e.get("source_sha256_16") != source_hash(CLASS_SOURCES[cls]):
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle timed on the host (cpu_baseline and --impl reference)
+
+def oracle_matvec_sample():
+    """Set up the 1024^2 workload in the FP64 oracle (untimed state solve at
+    a smooth velocity) and return a callable doing one GN Hessian matvec."""
+    from oracle.problem import Problem
+    from paper_1604_02153_gb300 import inputs
+    m_R, m_T = inputs.ellipse_phantoms(N_GRID, seed=100)
+    P = Problem(m_R, m_T, NT, BETAS[-1])
+    P.state_solve(inputs.random_velocity(N_GRID, seed=7, vmax=0.2))
+    P.ensure_adjoint_characteristic()
+    vt = inputs.random_velocity(N_GRID, seed=8, vmax=1.0)
+    return lambda: P.hessian_matvec(vt)
+
+
+def cpu_baseline():
+    f = oracle_matvec_sample()
+    t0 = time.perf_counter()
+    f()
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 GN Hessian matvec of the FP64 numpy oracle at {N_GRID}^2, nt={NT} "
+                      f"({dt:.1f} s, single-threaded numpy)"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    f = oracle_matvec_sample()
+    for _ in range(args.warmup):
+        f()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f()
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one FP64 oracle GN Hessian matvec per step at "
+                                       f"{N_GRID}^2, nt={NT}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config():
+    return {"workload": f"phantom pair {N_GRID}x{N_GRID} (12 random ellipses, sigma 2 px), "
+                        f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, P_2L CHEB(10) 512^2 coarse, "
+                        f"||g||rel 1e-2, cubic B-spline SL",
+            "grid": [N_GRID, N_GRID], "nt": NT, "betas": list(BETAS), "gtol": GTOL,
+            "precond": "2L-CHEB(10)", "interp": "spline", "reg_norm": "H1",
+            "l2": "flushed between steps (256 MB write, untimed)"}
+
+
+# ---------------------------------------------------------------------------
+
+def aggregate_ranks(dist, device, total_ms, matvecs, e2e_ms, e2e_matvecs):
+    """Whole-job figures over replicas: time = max over ranks, work = sum.
+
+    Returns (value, e2e_value) in matvecs/s. dist may be None (one rank).
+    """
+    if dist is None:
+        return matvecs / (total_ms / 1e3), e2e_matvecs / (e2e_ms / 1e3)
+    import torch
+    t = torch.tensor([total_ms, e2e_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(matvecs), float(e2e_matvecs)], dtype=torch.float64, device=device)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(w[0]) / (float(t[0]) / 1e3), float(w[1]) / (float(t[1]) / 1e3)
+
+
+def main():
+    args = parse()
+    rank, local_rank, world = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_1604_02153_gb300 import inputs, regnk
+    regnk.load()
+
+    n = N_GRID
+    m_R, m_T = inputs.ellipse_phantoms(n, seed=100 + rank)
+    h_mR = torch.tensor(m_R.astype(np.float32).ravel()).pin_memory()
+    h_mT = torch.tensor(m_T.astype(np.float32).ravel()).pin_memory()
+    d_mR, d_mT = h_mR.to(dev), h_mT.to(dev)
+    R = regnk.Registration(n, n, NT, BETAS[0])
+    R.set_images(d_mR, d_mT)
+    v = torch.zeros(2 * n * n, device=dev)
+    h_v = torch.empty(2 * n * n).pin_memory()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    ok = (regnk.REG_OK, regnk.REG_ENOTCONV, regnk.REG_ELINESEARCH)
+
+    def step(stats):
+        v.zero_()
+        for b in BETAS:
+            R.set_beta(b)
+            info = R.solve(v, GTOL, allow=ok)
+            stats["matvecs"] += info["matvecs"]
+            stats["newton"] += info["newton_iters"]
+            stats["pcg"] += info["pcg_iters"]
+            stats["coarse_matvecs"] += info["coarse_matvecs"]
+            stats["status"].append(info["status_name"])
+            stats["gnorm_rel"] = info["gnorm_rel"]
+
+    def new_stats():
+        return {"matvecs": 0, "newton": 0, "pcg": 0, "coarse_matvecs": 0, "status": [],
+                "gnorm_rel": None}
+
+    for _ in range(args.warmup):
+        step(new_stats())
+    torch.cuda.synchronize()
+
+    # ---- timed region: K solves, inputs resident, L2 flushed between steps
+    stats = new_stats()
+    launches0 = regnk.launch_count()
+    R.profile_enable(True)
+    st = torch.cuda.current_stream()
+    step_ms = []
+    with ClockSampler(dev.index) as clocks:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            step(stats)
+            e1.record(st)
+            torch.cuda.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        if dist is not None:
+            dist.barrier()
+    prof = R.profile_read()
+    R.profile_enable(False)
+    launches = regnk.launch_count() - launches0
+    total_ms = float(sum(step_ms))
+
+    # ---- end to end through the C ABI with host buffers
+    e2e_ms = 0.0
+    e2e_mv = 0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d_mR.copy_(h_mR, non_blocking=True)
+        d_mT.copy_(h_mT, non_blocking=True)
+        R.set_images(d_mR, d_mT)
+        s2 = new_stats()
+        step(s2)
+        h_v.copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_mv += s2["matvecs"]
+    value, e2e_value = aggregate_ranks(dist, dev, total_ms, stats["matvecs"], e2e_ms, e2e_mv)
+
+    # ---- roofline of the dominant kernel class
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, nl, by = prof[dom]
+    hbm, how = peaks()
+    achieved = (by / (ms / 1e3)) / 1e9 if ms > 0 else None
+    per_launch = by / nl if nl else None
+    roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": hbm,
+            "peak_source": f"{how} HBM copy bandwidth", "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None,
+            "traffic": ncu_traffic(dom, per_launch),
+            "algorithmic_bytes_per_launch": per_launch, "launches": nl,
+            "share_of_device_time": ms / sum(p[0] for p in prof.values()),
+            "classes_ms": {k: round(p[0], 3) for k, p in prof.items()}}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(),
+                "time_to_solution_s": total_ms / args.steps / 1e3,
+                "newton_iters_per_solve": stats["newton"] / args.steps,
+                "matvecs_per_solve": stats["matvecs"] / args.steps,
+                "pcg_iters_per_solve": stats["pcg"] / args.steps,
+                "coarse_matvecs_per_solve": stats["coarse_matvecs"] / args.steps,
+                "final_gnorm_rel": stats["gnorm_rel"],
+                "solve_status": sorted(set(stats["status"])),
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": int(h_mR.numel() * 4 + h_mT.numel() * 4),
+                        "d2h_bytes_per_step": int(h_v.numel() * 4)},
+                "gpu_launches": int(launches),
+                "roofline": roof,
+                "clocks": clocks.summary()}
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    R.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -215,6 +215,32 @@ reg_status reg_dot(reg_ctx* ctx, const float* a, const float* b, long long n, do
 /* Message of the last error on this context (never NULL). */
 const char* reg_last_error(const reg_ctx* ctx);
 
+/* ---- Diagnostics (no counterpart in the paper) ----------------------------
+ * Per-kernel-class device time for roofline reporting. While profiling is
+ * enabled every launch of a class is bracketed by CUDA events on the
+ * context's stream; reg_profile_read synchronises that stream and returns the
+ * summed device time (ms), the number of bracketed launch groups and the
+ * algorithmic bytes those launches move (inputs read once, outputs written
+ * once; see the kernel sources for the per-point figures). */
+enum { REG_KC_FFT_ROWS = 0,       /* row FFT passes (forward and inverse)       */
+       REG_KC_FFT_COLS = 1,       /* column FFT pass with the spectral symbol    */
+       REG_KC_PREFILTER = 2,      /* cubic B-spline prefilter (x and y passes)   */
+       REG_KC_DEPARTURE = 3,      /* RK2 departure points                        */
+       REG_KC_GATHER = 4,         /* state steps and other 4x4 gathers           */
+       REG_KC_ADJOINT_STEP = 5,   /* adjoint / incremental adjoint steps         */
+       REG_KC_INCSTATE_STEP = 6,  /* incremental state steps                     */
+       REG_KC_REDUCE = 7,         /* FP64 inner products and norms               */
+       REG_KC_VECTOR = 8,         /* Krylov vector updates                       */
+       REG_KC_COUNT = 9 };
+/* enable != 0 starts profiling and clears the totals; 0 stops it. */
+reg_status reg_profile_enable(reg_ctx* ctx, int enable);
+/* Totals of one kernel class since the last reg_profile_enable(ctx, 1);
+ * ms, launches and bytes are host pointers (any may be NULL). */
+reg_status reg_profile_read(reg_ctx* ctx, int kclass, double* ms, long long* launches,
+                            double* bytes);
+/* Kernels launched by the library in this process so far (all contexts). */
+long long reg_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

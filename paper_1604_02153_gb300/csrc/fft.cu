@@ -349,7 +349,7 @@ static void launch_r2c(const float* in, long long fstride, float2* spec, long lo
   static bool init = false;
   if (!init) { set_smem(k_rows_r2c<LOGN>, smem); init = true; }
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_r2c<LOGN><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw);
+  k_rows_r2c<LOGN><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw); ++g_launch_count;
 }
 
 template <int LOGN>
@@ -361,7 +361,7 @@ static void launch_c2r(const float2* spec, long long sstride, float* out, long l
   static bool init = false;
   if (!init) { set_smem(k_rows_c2r<LOGN>, smem); init = true; }
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_c2r<LOGN><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw);
+  k_rows_c2r<LOGN><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw); ++g_launch_count;
 }
 
 template <int LOGI, int LOGO>
@@ -371,7 +371,7 @@ static void launch_cols(const ColArgs& a, int groups, cudaStream_t st) {
   static bool init = false;
   if (!init) { set_smem(k_cols<LOGI, LOGO>, 3 * (size_t)C::P * C::NM * sizeof(float2)); init = true; }
   dim3 grid((a.nk1_out + C::P - 1) / C::P, groups);
-  k_cols<LOGI, LOGO><<<grid, C::NT, smem, st>>>(a);
+  k_cols<LOGI, LOGO><<<grid, C::NT, smem, st>>>(a); ++g_launch_count;
 }
 
 #define REGNK_LOG_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11)

@@ -5,6 +5,10 @@
 
 namespace regnk {
 
+// Kernel launches issued by the library since load (incremented after every
+// launch; read by reg_launch_count).
+extern long long g_launch_count;
+
 // Spectral multipliers of the column pass (see fft.cu).
 enum SpecOp {
   SPOP_SCALE = 0,        // sigma = 1 (with resampling: restriction / prolongation)

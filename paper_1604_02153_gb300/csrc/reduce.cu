@@ -88,15 +88,15 @@ static int aligned16(const void* a, const void* b) {
 void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
                 cudaStream_t st) {
   const int nb = nblocks(n);
-  k_partial<0><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b));
-  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out);
+  k_partial<0><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b)); ++g_launch_count;
+  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out); ++g_launch_count;
 }
 
 void launch_sumsq_diff(const float* a, const float* b, long long n, double* partial,
                        double* out, cudaStream_t st) {
   const int nb = nblocks(n);
-  k_partial<1><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b));
-  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out);
+  k_partial<1><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b)); ++g_launch_count;
+  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out); ++g_launch_count;
 }
 
 __global__ void __launch_bounds__(kRT)
@@ -129,8 +129,8 @@ __global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double
 
 void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st) {
   const int nb = nblocks(n);
-  k_maxabs_partial<<<nb, kRT, 0, st>>>(a, n, partial);
-  k_maxabs_final<<<1, 32, 0, st>>>(partial, nb, out);
+  k_maxabs_partial<<<nb, kRT, 0, st>>>(a, n, partial); ++g_launch_count;
+  k_maxabs_final<<<1, 32, 0, st>>>(partial, nb, out); ++g_launch_count;
 }
 
 // flag = 1 if any bit pattern differs (flag must be zeroed by the caller).
@@ -145,7 +145,7 @@ __global__ void k_compare(const unsigned* __restrict__ a, const unsigned* __rest
 
 void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st) {
   k_compare<<<nblocks(n), kRT, 0, st>>>(reinterpret_cast<const unsigned*>(a),
-                                        reinterpret_cast<const unsigned*>(b), n, flag);
+                                        reinterpret_cast<const unsigned*>(b), n, flag); ++g_launch_count;
 }
 
 // y = (alpha_num/alpha_den * cs) x + beta_y y, coefficients from device FP64 scalars.
@@ -159,7 +159,7 @@ __global__ void k_axpby(long long n, const double* an, const double* ad, double 
 
 void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
                   const float* x, float* y, float beta_y, cudaStream_t st) {
-  k_axpby<<<nblocks(n), kRT, 0, st>>>(n, alpha_num, alpha_den, cs, x, y, beta_y);
+  k_axpby<<<nblocks(n), kRT, 0, st>>>(n, alpha_num, alpha_den, cs, x, y, beta_y); ++g_launch_count;
 }
 
 // z may alias x or y (elementwise, same index)
@@ -172,7 +172,7 @@ __global__ void k_lincomb(long long n, float a, const float* x, float b, const f
 
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
                     cudaStream_t st) {
-  k_lincomb<<<nblocks(n), kRT, 0, st>>>(n, a, x, b, y, z);
+  k_lincomb<<<nblocks(n), kRT, 0, st>>>(n, a, x, b, y, z); ++g_launch_count;
 }
 
 // PCG step: alpha = rz / pq; x += alpha p; r -= alpha q.
@@ -190,7 +190,7 @@ __global__ void k_pcg_update(long long n, const double* rz, const double* pq,
 
 void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
                        const float* q, float* x, float* r, cudaStream_t st) {
-  k_pcg_update<<<nblocks(n), kRT, 0, st>>>(n, rz, pq, p, q, x, r);
+  k_pcg_update<<<nblocks(n), kRT, 0, st>>>(n, rz, pq, p, q, x, r); ++g_launch_count;
 }
 
 // p = z + (rz_new / rz_old) p
@@ -204,7 +204,7 @@ __global__ void k_pcg_direction(long long n, const double* rz_new, const double*
 
 void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,
                           const float* z, float* p, cudaStream_t st) {
-  k_pcg_direction<<<nblocks(n), kRT, 0, st>>>(n, rz_new, rz_old, z, p);
+  k_pcg_direction<<<nblocks(n), kRT, 0, st>>>(n, rz_new, rz_old, z, p); ++g_launch_count;
 }
 
 __global__ void k_fill(float* x, long long n, float value) {
@@ -214,7 +214,7 @@ __global__ void k_fill(float* x, long long n, float value) {
 }
 
 void launch_fill(float* x, long long n, float value, cudaStream_t st) {
-  k_fill<<<nblocks(n), kRT, 0, st>>>(x, n, value);
+  k_fill<<<nblocks(n), kRT, 0, st>>>(x, n, value); ++g_launch_count;
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): x[i] = uniform [-1, 1) from the
@@ -231,7 +231,7 @@ __global__ void k_splitmix(float* x, long long n, unsigned long long seed) {
 }
 
 void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st) {
-  k_splitmix<<<nblocks(n), kRT, 0, st>>>(x, n, seed);
+  k_splitmix<<<nblocks(n), kRT, 0, st>>>(x, n, seed); ++g_launch_count;
 }
 
 }  // namespace regnk

@@ -18,6 +18,10 @@
 
 using namespace regnk;
 
+namespace regnk {
+long long g_launch_count = 0;
+}
+
 namespace {
 
 constexpr int kSpecSlots = 8;    // spectra in the FFT workspace of a level
@@ -95,6 +99,14 @@ struct reg_ctx {
   double eta = 0.5;
   int coarse_matvecs = 0;
   std::string err;
+  // per-kernel-class device time (diagnostics, reg_profile_*)
+  bool prof = false;
+  std::vector<cudaEvent_t> evpool;
+  struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+  std::vector<Rec> recs;
+  double prof_ms[REG_KC_COUNT] = {};
+  double prof_bytes[REG_KC_COUNT] = {};
+  long long prof_n[REG_KC_COUNT] = {};
 };
 
 namespace {
@@ -118,6 +130,57 @@ void check(reg_ctx* c, cudaError_t e, const char* what) {
 }
 
 void check_launch(reg_ctx* c, const char* what) { check(c, cudaGetLastError(), what); }
+
+cudaEvent_t take_event(reg_ctx* c) {
+  if (c->evpool.empty()) {
+    cudaEvent_t e;
+    check(c, cudaEventCreate(&e), "cudaEventCreate");
+    return e;
+  }
+  cudaEvent_t e = c->evpool.back();
+  c->evpool.pop_back();
+  return e;
+}
+
+// Folds recorded event pairs into the per-class totals (synchronises).
+void harvest(reg_ctx* c) {
+  if (c->recs.empty()) return;
+  check(c, cudaStreamSynchronize(c->st), "profile sync");
+  for (auto& r : c->recs) {
+    float ms = 0.f;
+    check(c, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    c->prof_ms[r.cls] += ms;
+    c->prof_bytes[r.cls] += r.bytes;
+    c->prof_n[r.cls] += 1;
+    c->evpool.push_back(r.a);
+    c->evpool.push_back(r.b);
+  }
+  c->recs.clear();
+}
+
+// Brackets the launches of one kernel class with events when profiling is
+// on; bytes = algorithmic bytes moved by those launches.
+class Prof {
+ public:
+  Prof(reg_ctx* c, int cls, double bytes) : c_(c) {
+    if (!c->prof) return;
+    if (c->recs.size() >= 8192) harvest(c);
+    r_.cls = cls;
+    r_.bytes = bytes;
+    r_.a = take_event(c);
+    r_.b = take_event(c);
+    cudaEventRecord(r_.a, c->st);
+  }
+  ~Prof() {
+    if (!c_->prof) return;
+    cudaEventRecord(r_.b, c_->st);
+    c_->recs.push_back(r_);
+  }
+
+ private:
+  reg_ctx* c_;
+  reg_ctx::Rec r_{};
+};
 
 template <typename T>
 T* dalloc(reg_ctx* c, size_t count) {
@@ -207,7 +270,10 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
     const int ng = groups - g0 < chunk ? groups - g0 : chunk;
     float2* sin = L.spec;
     float2* sout = L.spec + (size_t)ng * fin * g.spec;
-    fft_rows_r2c(g.n1, g.n2, in + (size_t)g0 * fin * g.N, g.N, sin, g.spec, ng * fin, L.tw1, c->st);
+    {
+      Prof P(c, REG_KC_FFT_ROWS, (double)ng * fin * (4.0 * g.N + 8.0 * g.spec));
+      fft_rows_r2c(g.n1, g.n2, in + (size_t)g0 * fin * g.N, g.N, sin, g.spec, ng * fin, L.tw1, c->st);
+    }
     ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s);
     a.in = sin;
     a.in_fstride = g.spec;
@@ -215,9 +281,15 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
     a.out_fstride = g.spec;
     a.nin = fin;
     a.nout = fout;
-    fft_cols(a, ng, c->st);
-    fft_rows_c2r(g.n1, g.n2, sout, g.spec, out + (size_t)g0 * fout * g.N, g.N,
-                 add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st);
+    {
+      Prof P(c, REG_KC_FFT_COLS, (double)ng * (fin + fout) * 8.0 * g.spec);
+      fft_cols(a, ng, c->st);
+    }
+    {
+      Prof P(c, REG_KC_FFT_ROWS, (double)ng * fout * (8.0 * g.spec + (add ? 8.0 : 4.0) * g.N));
+      fft_rows_c2r(g.n1, g.n2, sout, g.spec, out + (size_t)g0 * fout * g.N, g.N,
+                   add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st);
+    }
   }
   check_launch(c, "spectral operator");
 }
@@ -228,7 +300,10 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
               float* out, const float* add) {
   float2* sin = c->fine.spec;
   float2* sout = c->fine.spec + (size_t)F * A.g.spec;
-  fft_rows_r2c(A.g.n1, A.g.n2, in, A.g.N, sin, A.g.spec, F, A.tw1, c->st);
+  {
+    Prof P(c, REG_KC_FFT_ROWS, (double)F * (4.0 * A.g.N + 8.0 * A.g.spec));
+    fft_rows_r2c(A.g.n1, A.g.n2, in, A.g.N, sin, A.g.spec, F, A.tw1, c->st);
+  }
   ColArgs a = col_args(A, op, c->beta, c->opt.reg_norm, s);
   a.in = sin;
   a.in_fstride = A.g.spec;
@@ -240,8 +315,14 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
   a.n2_out = B.g.n2;
   a.nk1_out = B.g.nk1;
   a.tw_out = B.tw2;
-  fft_cols(a, F, c->st);
-  fft_rows_c2r(B.g.n1, B.g.n2, sout, B.g.spec, out, B.g.N, add, B.g.N, F, B.tw1, c->st);
+  {
+    Prof P(c, REG_KC_FFT_COLS, (double)F * 8.0 * (A.g.spec + B.g.spec));
+    fft_cols(a, F, c->st);
+  }
+  {
+    Prof P(c, REG_KC_FFT_ROWS, (double)F * (8.0 * B.g.spec + (add ? 8.0 : 4.0) * B.g.N));
+    fft_rows_c2r(B.g.n1, B.g.n2, sout, B.g.spec, out, B.g.N, add, B.g.N, F, B.tw1, c->st);
+  }
   check_launch(c, "spectral resampling");
 }
 
@@ -249,6 +330,7 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
 // spline model; the samples themselves for Lagrange)
 const float* coefficients(reg_ctx* c, Level& L, const float* u, int F, float* dst) {
   if (lagrange(c)) return u;
+  Prof P(c, REG_KC_PREFILTER, 16.0 * F * L.g.N);
   for (int f = 0; f < F; ++f)
     launch_prefilter(L.g.n1, L.g.n2, u + (size_t)f * L.g.N, L.tmp, dst + (size_t)f * L.g.N, 1, c->st);
   check_launch(c, "prefilter");
@@ -266,8 +348,13 @@ void read_slots(reg_ctx* c, int first, int count) {
   check(c, cudaStreamSynchronize(c->st), "stream synchronize");
 }
 
-double dot_sync(reg_ctx* c, const float* a, const float* b, long long n, int s) {
+void dot_async(reg_ctx* c, const float* a, const float* b, long long n, int s) {
+  Prof P(c, REG_KC_REDUCE, 8.0 * n);
   launch_dot(a, b, n, c->partial, slot(c, s), c->st);
+}
+
+double dot_sync(reg_ctx* c, const float* a, const float* b, long long n, int s) {
+  dot_async(c, a, b, n, s);
   check_launch(c, "dot");
   read_slots(c, s, 1);
   return c->hsc[s];
@@ -282,11 +369,17 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   const size_t N = (size_t)g.N;
   if (v != L.v) check(c, cudaMemcpyAsync(L.v, v, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
   const float* cv = coefficients(c, L, L.v, 2, L.cv);
-  launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, lagrange(c), c->st);
+  {
+    Prof P(c, REG_KC_DEPARTURE, 32.0 * N);
+    launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, lagrange(c), c->st);
+  }
   check(c, cudaMemcpyAsync(L.m, L.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
   for (int j = 1; j <= L.nt; ++j) {
     const float* cm = coefficients(c, L, L.m + (j - 1) * N, 1, L.coef);
-    launch_state_step(g.n1, g.n2, cm, L.dX, L.m + j * N, lagrange(c), c->st);
+    {
+      Prof P(c, REG_KC_GATHER, 16.0 * N);
+      launch_state_step(g.n1, g.n2, cm, L.dX, L.m + j * N, lagrange(c), c->st);
+    }
   }
   check_launch(c, "state solve");
   L.have_v = true;
@@ -296,7 +389,10 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   // div v and div v at Y_D
   spectral(c, L, SPOP_DIV, 0.0, L.v, 2, 1, L.delta, 1, nullptr);
   const float* cd = coefficients(c, L, L.delta, 1, L.coef);
-  launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, lagrange(c), c->st);
+  {
+    Prof P(c, REG_KC_GATHER, 16.0 * N);
+    launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, lagrange(c), c->st);
+  }
   check_launch(c, "div v");
 }
 
@@ -314,7 +410,10 @@ void ensure_G(reg_ctx* c, Level& L) {
   const size_t N = (size_t)L.g.N;
   for (int j = 1; j <= L.nt; ++j) {
     const float* cg = coefficients(c, L, L.gm + 2 * (j - 1) * N, 2, L.c2);
-    launch_gather(L.g.n1, L.g.n2, cg, L.dX, L.G + 2 * (j - 1) * N, 2, (long long)N, lagrange(c), c->st);
+    {
+      Prof P(c, REG_KC_GATHER, 24.0 * N);
+      launch_gather(L.g.n1, L.g.n2, cg, L.dX, L.G + 2 * (j - 1) * N, 2, (long long)N, lagrange(c), c->st);
+    }
   }
   check_launch(c, "G history");
   L.have_G = true;
@@ -325,8 +424,14 @@ void ensure_G(reg_ctx* c, Level& L) {
 double objective(reg_ctx* c, Level& L) {
   const size_t N = (size_t)L.g.N;
   spectral(c, L, SPOP_REGPOW, 1.0, L.v, 1, 2, L.Av, 1, nullptr);
-  launch_sumsq_diff(L.m + L.nt * N, L.mR, (long long)N, c->partial, slot(c, S_J1), c->st);
-  launch_dot(L.v, L.Av, 2 * (long long)N, c->partial, slot(c, S_J2), c->st);
+  {
+    Prof P(c, REG_KC_REDUCE, 8.0 * N);
+    launch_sumsq_diff(L.m + L.nt * N, L.mR, (long long)N, c->partial, slot(c, S_J1), c->st);
+  }
+  {
+    Prof P(c, REG_KC_REDUCE, 16.0 * N);
+    launch_dot(L.v, L.Av, 2 * (long long)N, c->partial, slot(c, S_J2), c->st);
+  }
   check_launch(c, "objective");
   read_slots(c, S_J1, 2);
   const double hh = L.h1 * L.h2;
@@ -343,16 +448,25 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   const float ht = L.ht;
   float* lam = L.fA;
   float* lam2 = L.fB;
-  launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, L.mR, L.m + nt * N, L.gm + 2 * nt * N, lam, L.b, 1.f, c->st);
+  {
+    Prof P(c, REG_KC_VECTOR, 28.0 * N);
+    launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, L.mR, L.m + nt * N, L.gm + 2 * nt * N, lam, L.b, 1.f, c->st);
+  }
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     const float* cl = coefficients(c, L, lam, 1, L.coef);
-    launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
-                        lam2, L.b, lagrange(c), c->st);
+    {
+      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
+                          lam2, L.b, lagrange(c), c->st);
+    }
     std::swap(lam, lam2);
   }
   check_launch(c, "adjoint solve");
-  launch_lincomb(2 * (long long)N, 1.f, L.Av, 1.f, L.b, g_out, c->st);
+  {
+    Prof P(c, REG_KC_VECTOR, 24.0 * N);
+    launch_lincomb(2 * (long long)N, 1.f, L.Av, 1.f, L.b, g_out, c->st);
+  }
   check_launch(c, "gradient");
 }
 
@@ -365,25 +479,37 @@ void hessian(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) 
   const float ht = L.ht;
   const int lg = lagrange(c);
   const float* cvt = coefficients(c, L, vt, 2, L.c2);
-  launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
+  {
+    Prof P(c, REG_KC_GATHER, 24.0 * N);
+    launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
+  }
   float* mt = L.fA;
   float* mt2 = L.fB;
   for (int j = 1; j <= nt; ++j) {
     const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
-    launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
-                         L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+    {
+      Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 36.0 : 48.0) * N);
+      launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                           L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+    }
     std::swap(mt, mt2);
   }
   check_launch(c, "incremental state");
   // lambda~_nt = -m~_nt
   float* lt = mt2;
-  launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+  {
+    Prof P(c, REG_KC_VECTOR, 24.0 * N);
+    launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+  }
   float* lt2 = mt;
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     const float* cl = coefficients(c, L, lt, 1, L.coef);
-    launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
-                        lt2, L.b, lg, c->st);
+    {
+      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
+                          lt2, L.b, lg, c->st);
+    }
     std::swap(lt, lt2);
   }
   check_launch(c, "incremental adjoint");
@@ -487,10 +613,19 @@ void cheb(reg_ctx* c, const float* rhs, float* x) {
   check(c, cudaMemcpyAsync(x, c->cd, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
   for (int it = 1; it < c->opt.cheb_iters; ++it) {
     coarse_split_op(c, c->cd, c->cAd);
-    launch_lincomb(n, 1.f, c->cr, -1.f, c->cAd, c->cr, c->st);
+    {
+      Prof P(c, REG_KC_VECTOR, 12.0 * n);
+      launch_lincomb(n, 1.f, c->cr, -1.f, c->cAd, c->cr, c->st);
+    }
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    launch_lincomb(n, (float)(rho_new * rho), c->cd, (float)(2.0 * rho_new / delta), c->cr, c->cd, c->st);
-    launch_lincomb(n, 1.f, x, 1.f, c->cd, x, c->st);
+    {
+      Prof P(c, REG_KC_VECTOR, 12.0 * n);
+      launch_lincomb(n, (float)(rho_new * rho), c->cd, (float)(2.0 * rho_new / delta), c->cr, c->cd, c->st);
+    }
+    {
+      Prof P(c, REG_KC_VECTOR, 12.0 * n);
+      launch_lincomb(n, 1.f, x, 1.f, c->cd, x, c->st);
+    }
     rho = rho_new;
   }
   check_launch(c, "chebyshev");
@@ -518,7 +653,7 @@ PcgResult pcg(reg_ctx* c, long long n, Op A, Prec M, const float* rhs, float* x,
   }
   M(r, z);
   check(c, cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
-  launch_dot(r, z, n, c->partial, slot(c, S_RZ), c->st);
+  dot_async(c, r, z, n, S_RZ);
   for (int it = 0; it < maxit; ++it) {
     A(p, q);
     ++res.matvecs;
@@ -528,14 +663,20 @@ PcgResult pcg(reg_ctx* c, long long n, Op A, Prec M, const float* rhs, float* x,
       if (it == 0) check(c, cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
       break;
     }
-    launch_pcg_update(n, slot(c, S_RZ), slot(c, S_PQ), p, q, x, r, c->st);
+    {
+      Prof P(c, REG_KC_VECTOR, 24.0 * n);
+      launch_pcg_update(n, slot(c, S_RZ), slot(c, S_PQ), p, q, x, r, c->st);
+    }
     res.iters = it + 1;
     const double rr = dot_sync(c, r, r, n, S_RR);
     res.relres = std::sqrt(rr) / bnorm;
     if (res.relres <= rtol) break;
     M(r, z);
-    launch_dot(r, z, n, c->partial, slot(c, S_RZNEW), c->st);
-    launch_pcg_direction(n, slot(c, S_RZNEW), slot(c, S_RZ), z, p, c->st);
+    dot_async(c, r, z, n, S_RZNEW);
+    {
+      Prof P(c, REG_KC_VECTOR, 12.0 * n);
+      launch_pcg_direction(n, slot(c, S_RZNEW), slot(c, S_RZ), z, p, c->st);
+    }
     check(c, cudaMemcpyAsync(slot(c, S_RZ), slot(c, S_RZNEW), sizeof(double), cudaMemcpyDeviceToDevice, c->st), "copy");
     check_launch(c, "pcg");
   }
@@ -594,7 +735,10 @@ PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
 }
 
 double max_abs_sync(reg_ctx* c, const float* a, long long n, int s) {
-  launch_maxabs(a, n, c->partialf, slot(c, s), c->st);
+  {
+    Prof P(c, REG_KC_REDUCE, 4.0 * n);
+    launch_maxabs(a, n, c->partialf, slot(c, s), c->st);
+  }
   check_launch(c, "maxabs");
   read_slots(c, s, 1);
   return c->hsc[s];
@@ -732,6 +876,11 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
 reg_status reg_destroy(reg_ctx* c) {
   if (!c) return REG_OK;
   if (c->st) cudaStreamSynchronize(c->st);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
   if (c->hflag) cudaFreeHost(c->hflag);
@@ -925,6 +1074,32 @@ reg_status reg_eigen_bounds(reg_ctx* c, double* emin, double* emax) {
     *emax = c->emax;
   });
 }
+
+reg_status reg_profile_enable(reg_ctx* c, int enable) {
+  if (!c) return REG_EINVAL;
+  return guarded(c, [&] {
+    harvest(c);
+    c->prof = enable != 0;
+    for (int k = 0; k < REG_KC_COUNT; ++k) {
+      c->prof_ms[k] = 0.0;
+      c->prof_bytes[k] = 0.0;
+      c->prof_n[k] = 0;
+    }
+  });
+}
+
+reg_status reg_profile_read(reg_ctx* c, int kclass, double* ms, long long* launches,
+                            double* bytes) {
+  if (!c || kclass < 0 || kclass >= REG_KC_COUNT) return REG_EINVAL;
+  return guarded(c, [&] {
+    harvest(c);
+    if (ms) *ms = c->prof_ms[kclass];
+    if (launches) *launches = c->prof_n[kclass];
+    if (bytes) *bytes = c->prof_bytes[kclass];
+  });
+}
+
+long long reg_launch_count(void) { return g_launch_count; }
 
 reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
   if (!c || !a || !b || !out || n < 0) return REG_EINVAL;

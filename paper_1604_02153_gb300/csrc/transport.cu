@@ -114,18 +114,18 @@ void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, i
   const int l1 = ilog2i(n1);
   const long long N = (long long)n1 * n2;
   if (n1 >= 128) {
-    k_prefilter_x<128><<<dim3(n1 / 128, n2 / 32, F), 256, 0, st>>>(in, tmp, n1, l1, N);
+    k_prefilter_x<128><<<dim3(n1 / 128, n2 / 32, F), 256, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
   } else if (n1 == 64) {
-    k_prefilter_x<64><<<dim3(1, n2 / 32, F), 128, 0, st>>>(in, tmp, n1, l1, N);
+    k_prefilter_x<64><<<dim3(1, n2 / 32, F), 128, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
   } else {
-    k_prefilter_x<32><<<dim3(1, n2 / 32, F), 64, 0, st>>>(in, tmp, n1, l1, N);
+    k_prefilter_x<32><<<dim3(1, n2 / 32, F), 64, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
   }
   if (n2 >= 128) {
-    k_prefilter_y<128><<<dim3(n1 / 32, n2 / 128, F), 256, 0, st>>>(tmp, out, n1, n2, l1, N);
+    k_prefilter_y<128><<<dim3(n1 / 32, n2 / 128, F), 256, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
   } else if (n2 == 64) {
-    k_prefilter_y<64><<<dim3(n1 / 32, 1, F), 128, 0, st>>>(tmp, out, n1, n2, l1, N);
+    k_prefilter_y<64><<<dim3(n1 / 32, 1, F), 128, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
   } else {
-    k_prefilter_y<32><<<dim3(n1 / 32, 1, F), 64, 0, st>>>(tmp, out, n1, n2, l1, N);
+    k_prefilter_y<32><<<dim3(n1 / 32, 1, F), 64, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
   }
 }
 
@@ -216,7 +216,7 @@ void launch_departure(int n1, int n2, float ht, const float* v, const float* cv,
   const float s1 = ht * n1 / (2.0f * 3.14159265358979323846f);
   const float s2 = ht * n2 / (2.0f * 3.14159265358979323846f);
   k_departure<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), s1, s2, v,
-                                                                cv, dX, dY, lagrange);
+                                                                cv, dX, dY, lagrange); ++g_launch_count;
 }
 
 // out_f = I[coef_f](x + disp), f = 0..F-1 (fields fstride apart), one stencil.
@@ -237,7 +237,7 @@ void launch_gather(int n1, int n2, const float* coef, const float* disp, float* 
                    long long fstride, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
   k_gather<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), coef, disp,
-                                                             out, F, fstride, lagrange);
+                                                             out, F, fstride, lagrange); ++g_launch_count;
 }
 
 void launch_state_step(int n1, int n2, const float* coef, const float* dX, float* out,
@@ -265,7 +265,7 @@ void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const fl
                          const float* gm, float* lam, float* b, float sign, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
   k_adjoint_init<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(N, coef_b, mR, m1, gm, lam,
-                                                                  b, sign);
+                                                                  b, sign); ++g_launch_count;
 }
 
 // One backward step of the (incremental) adjoint along Y_D (§3.3.2, Heun):
@@ -298,7 +298,7 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
                          cudaStream_t st) {
   const long long N = (long long)n1 * n2;
   k_adjoint_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
-      n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
+      n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange); ++g_launch_count;
 }
 
 // One forward step of the incremental state (Gauss-Newton, §3.3.2):
@@ -331,7 +331,7 @@ void launch_incstate_step(int n1, int n2, float ht, const float* coef, const flo
                           float* out, int first, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
   k_incstate_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
-      n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange);
+      n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange); ++g_launch_count;
 }
 
 }  // namespace regnk

@@ -24,6 +24,8 @@ REG_PC_REG, REG_PC_2L = 0, 1
 REG_PCSOLVER_CHEB, REG_PCSOLVER_PCG = 0, 1
 REG_SPEC_GRAD, REG_SPEC_DIV, REG_SPEC_REG, REG_SPEC_REGPOW = 0, 1, 2, 3
 REG_SPEC_LOWPASS, REG_SPEC_HIGHPASS, REG_SPEC_PREFILTER = 4, 5, 6
+KERNEL_CLASSES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
+                  "adjoint_step", "incstate_step", "reduce", "vector"]
 
 
 class RegError(RuntimeError):
@@ -83,6 +85,10 @@ _SIGNATURES = {
     "reg_solve": [_P, _P, _D, ctypes.POINTER(reg_info)],
     "reg_dot": [_P, _P, _P, ctypes.c_longlong, ctypes.POINTER(_D)],
     "reg_last_error": [_P],
+    "reg_profile_enable": [_P, _I],
+    "reg_profile_read": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+                         ctypes.POINTER(_D)],
+    "reg_launch_count": [],
 }
 
 _lib = None
@@ -99,7 +105,8 @@ def load(path=LIB_PATH):
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = ctypes.c_char_p if name == "reg_last_error" else ctypes.c_int
+        fn.restype = {"reg_last_error": ctypes.c_char_p,
+                      "reg_launch_count": ctypes.c_longlong}.get(name, ctypes.c_int)
     _lib = lib
     return lib
 
@@ -231,11 +238,28 @@ class Registration:
         d["status_name"] = STATUS_NAMES.get(s, str(s))
         return d
 
+    def profile_enable(self, enable=True):
+        self._call("reg_profile_enable", 1 if enable else 0)
+
+    def profile_read(self):
+        """{class name: (ms, launches, algorithmic bytes)} since profile_enable."""
+        out = {}
+        for k, name in enumerate(KERNEL_CLASSES):
+            ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+            self._call("reg_profile_read", k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by))
+            out[name] = (ms.value, n.value, by.value)
+        return out
+
     def dot(self, a, b):
         out = ctypes.c_double()
         self._call("reg_dot", _ptr(a, name="a"), _ptr(b, name="b"), ctypes.c_longlong(a.numel()),
                    ctypes.byref(out))
         return out.value
+
+
+def launch_count():
+    """Kernels launched by libregnk in this process so far."""
+    return int(load().reg_launch_count())
 
 
 def reg_create(n1, n2, nt, beta, **options):
