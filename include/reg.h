@@ -232,13 +232,17 @@ enum { REG_KC_FFT_ROWS = 0,       /* row FFT passes (forward and inverse)       
        REG_KC_REDUCE = 7,         /* FP64 inner products and norms               */
        REG_KC_VECTOR = 8,         /* Krylov vector updates                       */
        REG_KC_COUNT = 9 };
-/* enable != 0 starts profiling and clears the totals; 0 stops it. */
+/* enable != 0 starts profiling and clears the totals; 0 stops it. While
+ * profiling, launch sequences that are otherwise replayed as CUDA graphs
+ * (the fine matvec inside PCG, the P_2L application with CHEB) run as
+ * individual launches so that each is timed. */
 reg_status reg_profile_enable(reg_ctx* ctx, int enable);
 /* Totals of one kernel class since the last reg_profile_enable(ctx, 1);
  * ms, launches and bytes are host pointers (any may be NULL). */
 reg_status reg_profile_read(reg_ctx* ctx, int kclass, double* ms, long long* launches,
                             double* bytes);
-/* Kernels launched by the library in this process so far (all contexts). */
+/* Kernels launched by the library in this process so far (all contexts),
+ * counting every kernel node of every CUDA graph replay. */
 long long reg_launch_count(void);
 
 #ifdef __cplusplus

@@ -107,6 +107,12 @@ struct reg_ctx {
   double prof_ms[REG_KC_COUNT] = {};
   double prof_bytes[REG_KC_COUNT] = {};
   long long prof_n[REG_KC_COUNT] = {};
+  // CUDA graphs of fixed launch sequences (fine matvec, P_2L with CHEB)
+  cudaStream_t cap = nullptr;
+  bool graphs = true;
+  struct GraphEntry { std::string key; cudaGraphExec_t exec; long long kernels; };
+  std::vector<GraphEntry> graph_cache;
+  double graph_beta = -1, graph_emin = -1, graph_emax = -1;
 };
 
 namespace {
@@ -242,6 +248,79 @@ void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
 }
 
 bool lagrange(const reg_ctx* c) { return c->opt.interp == REG_INTERP_LAGRANGE; }
+
+void drop_graphs(reg_ctx* c) {
+  for (auto& g : c->graph_cache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  c->graph_cache.clear();
+}
+
+// Runs `body` (a fixed sequence of launches on c->st, no host synchronisation)
+// as a CUDA graph: the first call of a key runs eagerly, the second captures
+// the sequence on a private stream, later calls replay it on c->st. Graphs
+// are dropped when beta or the Chebyshev bounds change (they are launch
+// arguments). Profiling runs everything eagerly so that every launch is
+// bracketed by its own events.
+template <typename Body>
+void graphed(reg_ctx* c, const std::string& key, Body body) {
+  if (!c->graphs || c->prof) {
+    body();
+    return;
+  }
+  if (c->graph_beta != c->beta || c->graph_emin != c->emin || c->graph_emax != c->emax) {
+    drop_graphs(c);
+    c->graph_beta = c->beta;
+    c->graph_emin = c->emin;
+    c->graph_emax = c->emax;
+  }
+  reg_ctx::GraphEntry* e = nullptr;
+  for (auto& g : c->graph_cache)
+    if (g.key == key) e = &g;
+  if (!e) {
+    c->graph_cache.push_back({key, nullptr, 0});
+    body();
+    return;
+  }
+  if (!e->exec) {
+    cudaStream_t user = c->st;
+    check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c->st = c->cap;
+    cudaGraph_t graph = nullptr;
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(c->cap, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      c->st = user;
+      throw;
+    }
+    c->st = user;
+    check(c, cudaStreamEndCapture(c->cap, &graph), "end capture");
+    // the captured launches were counted; count them once per replay instead
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+    long long kn = 0;
+    for (size_t i = 0; i < nn; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+    }
+    e->kernels = kn;
+    g_launch_count -= kn;
+    const cudaError_t ie = cudaGraphInstantiate(&e->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    check(c, ie, "graph instantiate");
+  }
+  check(c, cudaGraphLaunch(e->exec, c->st), "graph launch");
+  g_launch_count += e->kernels;
+}
+
+std::string graph_key(const char* what, const void* a, const void* b) {
+  char buf[96];
+  snprintf(buf, sizeof buf, "%s:%p:%p", what, a, b);
+  return buf;
+}
 
 // ---------------------------------------------------------------------------
 // spectral operators
@@ -471,8 +550,15 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
 }
 
 // Gauss-Newton Hessian matvec (eq. hessian-matvec, GN); data_only drops beta A vt.
+void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only);
+
 void hessian(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
   ensure_G(c, L);
+  hessian_core(c, L, vt, out, data_only);
+}
+
+// the launch sequence of one GN matvec; needs ensure_G(c, L) beforehand
+void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
   const GridDims& gd = L.g;
   const size_t N = (size_t)gd.N;
   const int nt = L.nt;
@@ -533,7 +619,7 @@ void set_images_level(reg_ctx* c, Level& L) {
 void coarse_split_op(reg_ctx* c, const float* s, float* out) {
   Level& C = c->coarse;
   spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
-  hessian(c, C, c->cu, c->cq, true);
+  hessian_core(c, C, c->cu, c->cq, true);
   spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
   ++c->coarse_matvecs;
 }
@@ -570,6 +656,7 @@ void estimate_eigenvalues(reg_ctx* c) {
   // coarse problem at v = 0
   launch_fill(C.w1, n, 0.f, c->st);
   set_velocity(c, C, C.w1);
+  ensure_G(c, C);
   float* q = c->cp;
   float* qprev = c->cz;
   float* w = c->cd;
@@ -728,9 +815,18 @@ PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
       c->eig_beta = c->beta;
     }
     coarse_velocity(c);
+    ensure_G(c, c->coarse);
   }
-  auto A = [&](const float* p, float* q) { hessian(c, F, p, q, false); };
-  auto M = [&](const float* r, float* z) { precond(c, r, z); };
+  ensure_G(c, F);
+  auto A = [&](const float* p, float* q) {
+    graphed(c, graph_key("mv", p, q), [&] { hessian_core(c, F, p, q, false); });
+  };
+  auto M = [&](const float* r, float* z) {
+    if (c->two_level && c->opt.pc_solver == REG_PCSOLVER_CHEB)
+      graphed(c, graph_key("pc", r, z), [&] { precond(c, r, z); });
+    else
+      precond(c, r, z);
+  };
   return pcg(c, n, A, M, rhs, x, c->kr, c->kz, c->kp, c->kq, rtol, maxit, S_PCG_OUTER);
 }
 
@@ -832,6 +928,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   const reg_status s = guarded(c, [&] {
     alloc_level(c, c->fine, grid.n1, grid.n2, nt);
     if (c->two_level) alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, nt);
+    check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
     c->dsc = dalloc<double>(c, kScalars);
     void* h = nullptr;
     check(c, cudaMallocHost(&h, kScalars * sizeof(double)), "cudaMallocHost");
@@ -881,6 +978,8 @@ reg_status reg_destroy(reg_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
   if (c->hflag) cudaFreeHost(c->hflag);
@@ -1039,6 +1138,7 @@ reg_status reg_precond_apply(reg_ctx* c, const float* r, float* z) {
     if (c->two_level) {
       if (!c->have_eig) estimate_eigenvalues(c);
       coarse_velocity(c);
+      ensure_G(c, c->coarse);
     }
     precond(c, r, z);
   });

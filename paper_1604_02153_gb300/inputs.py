@@ -54,14 +54,18 @@ def _half_plane_modes(kmax):
 
 
 def _cosine_series(n1, n2, kmax, rng):
-    """sum over a half plane of |k|^-2 cos(k . x + phi_k), phi_k ~ U[0, 2 pi)."""
-    X1, X2 = grid_coordinates(n1, n2)
-    u = np.zeros((n2, n1))
+    """sum over a half plane of |k|^-2 cos(k . x + phi_k), phi_k ~ U[0, 2 pi).
+
+    Evaluated on the grid as the real part of an inverse DFT of the sparse
+    coefficient array (identical to summing the cosines node by node, modes
+    with |k_i| >= n_i/2 aliasing the same way).
+    """
+    C = np.zeros((n2, n1), dtype=complex)
     for (k1, k2) in _half_plane_modes(kmax):
         phi = rng.uniform(0.0, 2.0 * np.pi)
         amp = 1.0 / float(k1 * k1 + k2 * k2)
-        u += amp * np.cos(k1 * X1 + k2 * X2 + phi)
-    return u
+        C[k2 % n2, k1 % n1] += amp * np.exp(1j * phi)
+    return np.real(np.fft.ifft2(C)) * (n1 * n2)
 
 
 def rescale01(u):

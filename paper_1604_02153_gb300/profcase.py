@@ -1,0 +1,61 @@
+"""Small fixed workloads for kernel profiling (ncu) of libregnk.
+
+    python -m paper_1604_02153_gb300.profcase --n 1024 --nt 8 --matvecs 3
+
+sets up the phantom pair at n^2 (seed 100), evaluates the objective and
+gradient at a smooth velocity (max |v| = 0.2) and applies the GN Hessian
+`--matvecs` times; `--precond` also applies the two-level preconditioner
+once. Prints the wall time per matvec. The workload holds a few hundred MB
+on the device at 1024^2.
+"""
+
+import argparse
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--nt", type=int, default=8)
+    ap.add_argument("--matvecs", type=int, default=3)
+    ap.add_argument("--lagrange", action="store_true")
+    ap.add_argument("--precond", action="store_true")
+    a = ap.parse_args()
+    import numpy as np
+    import torch
+
+    from paper_1604_02153_gb300 import inputs, regnk
+    n = a.n
+    m_R, m_T = inputs.ellipse_phantoms(n, seed=100)
+    v = inputs.random_velocity(n, seed=7, vmax=0.2)
+    u = inputs.random_velocity(n, seed=8, vmax=1.0)
+    f = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32).ravel(), device="cuda")
+    R = regnk.Registration(n, n, a.nt, 1e-2,
+                           interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE)
+    R.set_images(f(m_R), f(m_T))
+    vd, ud = f(v), f(u)
+    g = torch.empty_like(vd)
+    R.objective_gradient(vd, g)
+    H = torch.empty_like(vd)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.matvecs):
+        R.hessian_matvec(vd, ud, H)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / max(1, a.matvecs)
+    if a.precond:
+        z = torch.empty_like(vd)
+        R.precond_apply(g, z)
+        torch.cuda.synchronize()
+    print(f"n={n} nt={a.nt} matvec {1e3 * dt:.3f} ms (wall, incl. host)")
+    R.close()
+
+
+if __name__ == "__main__":
+    main()
