@@ -261,11 +261,12 @@ void drop_graphs(reg_ctx* c) {
 // are dropped when beta or the Chebyshev bounds change (they are launch
 // arguments). Profiling runs everything eagerly so that every launch is
 // bracketed by its own events.
+// Returns true when the body ran eagerly (host-side counters inside it ran).
 template <typename Body>
-void graphed(reg_ctx* c, const std::string& key, Body body) {
+bool graphed(reg_ctx* c, const std::string& key, Body body) {
   if (!c->graphs || c->prof) {
     body();
-    return;
+    return true;
   }
   if (c->graph_beta != c->beta || c->graph_emin != c->emin || c->graph_emax != c->emax) {
     drop_graphs(c);
@@ -279,7 +280,7 @@ void graphed(reg_ctx* c, const std::string& key, Body body) {
   if (!e) {
     c->graph_cache.push_back({key, nullptr, 0});
     body();
-    return;
+    return true;
   }
   if (!e->exec) {
     cudaStream_t user = c->st;
@@ -314,6 +315,7 @@ void graphed(reg_ctx* c, const std::string& key, Body body) {
   }
   check(c, cudaGraphLaunch(e->exec, c->st), "graph launch");
   g_launch_count += e->kernels;
+  return false;
 }
 
 std::string graph_key(const char* what, const void* a, const void* b) {
@@ -822,9 +824,10 @@ PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
     graphed(c, graph_key("mv", p, q), [&] { hessian_core(c, F, p, q, false); });
   };
   auto M = [&](const float* r, float* z) {
-    if (c->two_level && c->opt.pc_solver == REG_PCSOLVER_CHEB)
-      graphed(c, graph_key("pc", r, z), [&] { precond(c, r, z); });
-    else
+    if (c->two_level && c->opt.pc_solver == REG_PCSOLVER_CHEB) {
+      if (!graphed(c, graph_key("pc", r, z), [&] { precond(c, r, z); }))
+        c->coarse_matvecs += c->opt.cheb_iters - 1;   // replayed: count its coarse matvecs
+    } else
       precond(c, r, z);
   };
   return pcg(c, n, A, M, rhs, x, c->kr, c->kz, c->kp, c->kq, rtol, maxit, S_PCG_OUTER);

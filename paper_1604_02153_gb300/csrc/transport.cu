@@ -7,6 +7,8 @@
 // Displacements are stored in cell units, d = (X_D - x) / h, so that the
 // node index and the sub-cell offset stay separate in FP32: the stencil base
 // is i + floor(d) and the weights use t = d - floor(d), both exact.
+#include <cmath>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -16,91 +18,77 @@ namespace regnk {
 // Periodic cubic B-spline prefilter.
 //
 // The spline interpolant sum_m c[m] beta3(x - m) takes the node values
-// (c[k-1] + 4 c[k] + c[k+1]) / 6 per axis. Its inverse factors into a causal
-// and an anticausal first-order recursion with pole z1 = sqrt(3) - 2:
-//     y[k] = s[k] + z1 y[k-1],   c'[k] = y[k] + z1 c'[k+1],   c = -6 z1 c'.
-// On the torus each recursion is started W = 14 samples before the segment
-// it produces (|z1|^14 < 1e-8, below FP32 resolution), so every thread
-// filters an independent 16-sample segment with a 14-sample warm-up on each
-// side, read from the periodic neighbours.
-constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
-constexpr float kGain = 1.60769515458673624f;   // -6 z1
-constexpr int kW = 14;                          // warm-up length
-constexpr int kSeg = 16;                        // samples per thread
-constexpr int kLen = kSeg + 2 * kW;             // samples a thread touches
+// (c[k-1] + 4 c[k] + c[k+1]) / 6 per axis, so the coefficients are the
+// samples filtered by the inverse of that symbol. Its impulse response on
+// the infinite grid is sqrt(3) z1^|m| with z1 = sqrt(3) - 2; on a periodic
+// axis of n points it is the periodised sum
+//     a_m = sqrt(3) (z1^|m| + z1^(n-|m|)) / (1 - z1^n),   |m| < n/2.
+// |z1|^14 < 1e-8, so the filter is applied as a symmetric FIR with the
+// 2L + 1 = 27 central taps (truncated tail below 5e-8 of the input, under
+// FP32 resolution). Both axes run in one kernel: a block stages a
+// (TY + 2L) x (TX + 2L) tile of samples with its periodic halo in shared
+// memory, filters along x into a (TY + 2L) x TX tile and along y into the
+// TY x TX output; every thread computes 4 consecutive outputs per pass from
+// a sliding register window.
+constexpr int kL = 13;              // FIR half-width
+constexpr int kTaps = 2 * kL + 1;
+constexpr int kPX = 32, kPY = 32;   // output tile
+constexpr int kPW = kPX + 2 * kL;   // staged tile width  (58)
+constexpr int kPH = kPY + 2 * kL;   // staged tile height (58)
+constexpr int kPIn = kPW + 1;       // odd pitches: conflict-free column and row walks
+constexpr int kPMid = kPX + 1;
+constexpr int kPThreads = 256;
 
-__device__ __forceinline__ void iir_segment(const float (&s)[kLen], float (&out)[kSeg]) {
-  float y[kLen];
-  y[0] = s[0];
-#pragma unroll
-  for (int i = 1; i < kLen; ++i) y[i] = fmaf(kZ1, y[i - 1], s[i]);
-  float c = y[kLen - 1];
-#pragma unroll
-  for (int i = kLen - 2; i >= kW; --i) {
-    c = fmaf(kZ1, c, y[i]);
-    if (i < kW + kSeg) out[i - kW] = kGain * c;
-  }
-}
+struct SplineTaps {
+  float ax[kTaps];   // taps along x_1 (periodised for n1)
+  float ay[kTaps];   // taps along x_2 (periodised for n2)
+};
 
-// x pass: a block filters 32 rows x TX columns (TX = min(128, n1)).
-template <int TX>
-__global__ void __launch_bounds__(32 * (TX / kSeg))
-k_prefilter_x(const float* __restrict__ in, float* __restrict__ out, int n1, int log1,
-              long long fstride) {
-  constexpr int SEGS = TX / kSeg;
-  constexpr int NT = 32 * SEGS;
-  constexpr int WIDTH = TX + 2 * kW;
-  constexpr int PITCH = WIDTH + 1;           // odd pitch: conflict-free column walks
-  constexpr int OPITCH = TX + 1;
-  __shared__ float sin_[32 * PITCH];
-  __shared__ float sout[32 * OPITCH];
+__global__ void __launch_bounds__(kPThreads)
+k_prefilter(const float* __restrict__ in, float* __restrict__ out, int n1, int n2, int log1,
+            long long fstride, SplineTaps taps) {
+  __shared__ float sin_[kPH * kPIn];
+  __shared__ float smid[kPH * kPMid];
   const int t = threadIdx.x;
-  const int x0 = blockIdx.x * TX;
-  const int y0 = blockIdx.y * 32;
+  const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
   const long long fo = (long long)blockIdx.z * fstride;
   const float* src = in + fo;
-  for (int q = t; q < 32 * WIDTH; q += NT) {
-    const int r = q / WIDTH, c = q - r * WIDTH;
-    const int gx = (x0 - kW + c) & (n1 - 1);
-    sin_[r * PITCH + c] = __ldg(src + ((long long)(y0 + r) << log1) + gx);
+  for (int q = t; q < kPH * kPW; q += kPThreads) {
+    const int r = q / kPW, c = q - r * kPW;
+    const int gx = (x0 - kL + c) & (n1 - 1);
+    const int gy = (y0 - kL + r) & (n2 - 1);
+    sin_[r * kPIn + c] = __ldg(src + ((long long)gy << log1) + gx);
   }
   __syncthreads();
-  const int r = t & 31, sg = t >> 5;
-  float s[kLen], o[kSeg];
+  // x pass: rows 0..kPH-1, 4 consecutive outputs per work item
+  for (int w = t; w < kPH * (kPX / 4); w += kPThreads) {
+    const int r = w / (kPX / 4), c0 = (w % (kPX / 4)) * 4;
+    const float* row = sin_ + r * kPIn + c0;
+    float win[kTaps + 3];
 #pragma unroll
-  for (int i = 0; i < kLen; ++i) s[i] = sin_[r * PITCH + sg * kSeg + i];
-  iir_segment(s, o);
+    for (int i = 0; i < kTaps + 3; ++i) win[i] = row[i];
 #pragma unroll
-  for (int i = 0; i < kSeg; ++i) sout[r * OPITCH + sg * kSeg + i] = o[i];
+    for (int o = 0; o < 4; ++o) {
+      float acc = 0.f;
+#pragma unroll
+      for (int m = 0; m < kTaps; ++m) acc = fmaf(taps.ax[m], win[o + m], acc);
+      smid[r * kPMid + c0 + o] = acc;
+    }
+  }
   __syncthreads();
-  float* dst = out + fo;
-  for (int q = t; q < 32 * TX; q += NT) {
-    const int rr = q / TX, c = q - rr * TX;
-    dst[((long long)(y0 + rr) << log1) + x0 + c] = sout[rr * OPITCH + c];
-  }
-}
-
-// y pass: a block filters 32 columns x TY rows; each thread walks one column
-// segment straight from global memory (a warp reads 32 adjacent columns).
-template <int TY>
-__global__ void __launch_bounds__(32 * (TY / kSeg))
-k_prefilter_y(const float* __restrict__ in, float* __restrict__ out, int n1, int n2,
-              int log1, long long fstride) {
-  const int t = threadIdx.x;
-  const int x = blockIdx.x * 32 + (t & 31);
-  const int ys = blockIdx.y * TY + (t >> 5) * kSeg;
-  const long long fo = (long long)blockIdx.z * fstride;
-  const float* src = in + fo;
-  float s[kLen], o[kSeg];
+  // y pass: 32 columns x 8 groups of 4 rows
+  const int c = t & 31, r0 = (t >> 5) * 4;
+  float win[kTaps + 3];
 #pragma unroll
-  for (int i = 0; i < kLen; ++i) {
-    const int gy = (ys - kW + i) & (n2 - 1);
-    s[i] = __ldg(src + ((long long)gy << log1) + x);
-  }
-  iir_segment(s, o);
+  for (int i = 0; i < kTaps + 3; ++i) win[i] = smid[(r0 + i) * kPMid + c];
   float* dst = out + fo;
 #pragma unroll
-  for (int i = 0; i < kSeg; ++i) dst[((long long)(ys + i) << log1) + x] = o[i];
+  for (int o = 0; o < 4; ++o) {
+    float acc = 0.f;
+#pragma unroll
+    for (int m = 0; m < kTaps; ++m) acc = fmaf(taps.ay[m], win[o + m], acc);
+    dst[((long long)(y0 + r0 + o) << log1) + x0 + c] = acc;
+  }
 }
 
 static int ilog2i(int n) {
@@ -109,24 +97,29 @@ static int ilog2i(int n) {
   return l;
 }
 
+static void periodised_taps(int n, float* a) {
+  const double z = std::sqrt(3.0) - 2.0;
+  const double zn = std::pow(z, n);
+  for (int m = -kL; m <= kL; ++m) {
+    const int am = m < 0 ? -m : m;
+    a[m + kL] = (float)(std::sqrt(3.0) * (std::pow(z, am) + std::pow(z, n - am)) / (1.0 - zn));
+  }
+}
+
 void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
                       cudaStream_t st) {
-  const int l1 = ilog2i(n1);
-  const long long N = (long long)n1 * n2;
-  if (n1 >= 128) {
-    k_prefilter_x<128><<<dim3(n1 / 128, n2 / 32, F), 256, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
-  } else if (n1 == 64) {
-    k_prefilter_x<64><<<dim3(1, n2 / 32, F), 128, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
-  } else {
-    k_prefilter_x<32><<<dim3(1, n2 / 32, F), 64, 0, st>>>(in, tmp, n1, l1, N); ++g_launch_count;
+  (void)tmp;
+  static int c1 = -1, c2 = -1;
+  static SplineTaps taps;
+  if (c1 != n1 || c2 != n2) {
+    periodised_taps(n1, taps.ax);
+    periodised_taps(n2, taps.ay);
+    c1 = n1;
+    c2 = n2;
   }
-  if (n2 >= 128) {
-    k_prefilter_y<128><<<dim3(n1 / 32, n2 / 128, F), 256, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
-  } else if (n2 == 64) {
-    k_prefilter_y<64><<<dim3(n1 / 32, 1, F), 128, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
-  } else {
-    k_prefilter_y<32><<<dim3(n1 / 32, 1, F), 64, 0, st>>>(tmp, out, n1, n2, l1, N); ++g_launch_count;
-  }
+  k_prefilter<<<dim3(n1 / kPX, n2 / kPY, F), kPThreads, 0, st>>>(in, out, n1, n2, ilog2i(n1),
+                                                                  (long long)n1 * n2, taps);
+  ++g_launch_count;
 }
 
 // ---------------------------------------------------------------------------

@@ -43,17 +43,33 @@ def main():
     g = torch.empty_like(vd)
     R.objective_gradient(vd, g)
     H = torch.empty_like(vd)
+    R.hessian_matvec(vd, ud, H)          # first use: module loading, attributes
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(a.matvecs):
         R.hessian_matvec(vd, ud, H)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / max(1, a.matvecs)
+    print(f"n={n} nt={a.nt} matvec {1e3 * dt:.3f} ms (wall, eager launches, incl. host)")
     if a.precond:
         z = torch.empty_like(vd)
         R.precond_apply(g, z)
         torch.cuda.synchronize()
-    print(f"n={n} nt={a.nt} matvec {1e3 * dt:.3f} ms (wall, incl. host)")
+        t0 = time.perf_counter()
+        for _ in range(a.matvecs):
+            R.precond_apply(g, z)
+        torch.cuda.synchronize()
+        dp = (time.perf_counter() - t0) / max(1, a.matvecs)
+        print(f"n={n} P_2L apply {1e3 * dp:.3f} ms (wall, eager launches, incl. host)")
+        x = torch.empty_like(vd)
+        info = R.kkt_solve(vd, g, 1e-12, a.matvecs, x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = R.kkt_solve(vd, g, 1e-12, a.matvecs, x)
+        torch.cuda.synchronize()
+        dk = time.perf_counter() - t0
+        print(f"n={n} PCG {info['pcg_iters']} iterations {1e3 * dk / max(1, info['pcg_iters']):.3f} "
+              f"ms per iteration (graph replay of matvec and P_2L)")
     R.close()
 
 
