@@ -208,6 +208,35 @@ reg_status reg_eigen_bounds(reg_ctx* ctx, double* emin, double* emax);
  * REG_ELINESEARCH otherwise (v then holds the last accepted iterate). */
 reg_status reg_solve(reg_ctx* ctx, float* v, double gtol, reg_info* info);
 
+/* ---- Allocation-free interpolation (no counterpart in the paper) ---------
+ * For callers that must not allocate device memory while they run: code
+ * whose device memory belongs to another framework's caching allocator (a
+ * cudaMalloc next to it can fail or fragment that pool) and latency-bound
+ * loops that cannot pay for cudaMalloc/cudaFree, which may block the host and
+ * synchronise the device. Needs no reg_ctx.
+ *
+ * Computes the same result as reg_interpolate with the spline model:
+ * out[x] = u(x + disp[x] * h), the periodic C2 cubic B-spline interpolant of
+ * the samples u (n1*n2 floats, device) evaluated at displacements disp
+ * (2*n1*n2 floats in cell units, component 1 then 2, device), written to out
+ * (n1*n2 floats, device), on `cuda_stream` (cudaStream_t as void*, NULL for
+ * the legacy default stream). n1, n2 are powers of two in [32, 2048] and
+ * n1*n2 <= REG_STATIC_MAX_POINTS; anything else returns REG_EINVAL.
+ *
+ * The spline coefficients go to one fixed device array of
+ * REG_STATIC_MAX_POINTS floats (4 MiB) inside the library, which each GPU
+ * that loads the library holds until the process exits. The call allocates
+ * nothing. All calls share that array, and it keeps the last call's
+ * contents (every call overwrites the part it reads before reading it):
+ * calls that can overlap on the GPU (different streams, or different host
+ * threads on one device) race on it, so issue them on one stream or order
+ * them. The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Returns REG_ECUDA if that look-up or a launch fails. */
+#define REG_STATIC_MAX_POINTS (1024 * 1024)
+reg_status reg_interpolate_static(int n1, int n2, const float* u, const float* disp,
+                                  float* out, void* cuda_stream);
+
 /* Euclidean inner product of two float32 device vectors of length n,
  * accumulated in float64 (the Krylov and line-search reductions); *out host. */
 reg_status reg_dot(reg_ctx* ctx, const float* a, const float* b, long long n, double* out);

@@ -89,6 +89,7 @@ _SIGNATURES = {
     "reg_profile_read": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(_D)],
     "reg_launch_count": [],
+    "reg_interpolate_static": [_I, _I, _P, _P, _P, _P],
 }
 
 _lib = None
@@ -255,6 +256,27 @@ class Registration:
         self._call("reg_dot", _ptr(a, name="a"), _ptr(b, name="b"), ctypes.c_longlong(a.numel()),
                    ctypes.byref(out))
         return out.value
+
+
+REG_STATIC_MAX_POINTS = 1024 * 1024
+
+
+def interpolate_static(n1, n2, u, disp, out):
+    """reg_interpolate_static: spline interpolation that allocates nothing.
+
+    For callers that may not allocate device memory while running (memory
+    owned by another framework's caching allocator, latency-bound loops);
+    the coefficient scratch is a fixed 4 MiB device array inside the
+    library, shared by all calls: calls overlapping on the GPU race on it.
+    Raises RegError on a non-zero status.
+    """
+    import torch
+    N = int(n1) * int(n2)
+    s = load().reg_interpolate_static(int(n1), int(n2), _ptr(u, N, "u"), _ptr(disp, 2 * N, "disp"),
+                                      _ptr(out, N, "out"),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if s != REG_OK:
+        raise RegError(s, "reg_interpolate_static failed")
 
 
 def launch_count():
