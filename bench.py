@@ -20,8 +20,9 @@ e2e       = the same through the C-ABI with host buffers: pinned-host images
             copied in, the velocity copied out, inside the timed region.
 roofline  = the kernel class with the largest device time: algorithmic
             bytes / its CUDA-event time, from a profiled repeat of the timed
-            steps (every launch bracketed by events on the launching stream),
-            against the measured HBM copy bandwidth.
+            steps (every launch bracketed by events on the launching stream,
+            event nodes inside the replayed graphs), against the measured HBM
+            copy bandwidth.
 cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
             timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
 """
@@ -47,13 +48,13 @@ BETAS = (1e-1, 1e-2, 1e-3)
 GTOL = 1e-2
 FALLBACK_HBM_GBS = 6800.0
 CLASS_NAMES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
-               "adjoint_step", "incstate_step", "reduce", "vector"]
+               "adjoint_step", "incstate_step", "reduce", "vector", "matvec"]
 # source file of each kernel class (a traffic figure is only valid for the
 # source it was captured from)
 CLASS_SOURCES = {"fft_rows": "fft.cu", "fft_cols": "fft.cu", "prefilter": "transport.cu",
                  "departure": "transport.cu", "gather": "transport.cu",
                  "adjoint_step": "transport.cu", "incstate_step": "transport.cu",
-                 "reduce": "reduce.cu", "vector": "reduce.cu"}
+                 "reduce": "reduce.cu", "vector": "reduce.cu", "matvec": "matvec.cu"}
 
 
 def parse():
@@ -63,6 +64,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
+                    help="preconditioner of the solve (the workload's is 2l-cheb)")
     return ap.parse_args()
 
 
@@ -202,12 +205,14 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def workload_config():
+def workload_config(precond="2l-cheb"):
+    pc = {"2l-cheb": "P_2L CHEB(10) 512^2 coarse", "2l-pcg": "P_2L PCG(1e-1) 512^2 coarse",
+          "reg": "P_REG"}[precond]
     return {"workload": f"phantom pair {N_GRID}x{N_GRID} (12 random ellipses, sigma 2 px), "
-                        f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, P_2L CHEB(10) 512^2 coarse, "
+                        f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, {pc}, "
                         f"||g||rel 1e-2, cubic B-spline SL",
             "grid": [N_GRID, N_GRID], "nt": NT, "betas": list(BETAS), "gtol": GTOL,
-            "precond": "2L-CHEB(10)", "interp": "spline", "reg_norm": "H1",
+            "precond": pc, "interp": "spline", "reg_norm": "H1",
             "l2": "flushed between steps (256 MB write, untimed)"}
 
 
@@ -255,7 +260,10 @@ def main():
     h_mR = torch.tensor(m_R.astype(np.float32).ravel()).pin_memory()
     h_mT = torch.tensor(m_T.astype(np.float32).ravel()).pin_memory()
     d_mR, d_mT = h_mR.to(dev), h_mT.to(dev)
-    R = regnk.Registration(n, n, NT, BETAS[0])
+    pc_opts = {"2l-cheb": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_CHEB),
+               "2l-pcg": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_PCG),
+               "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
+    R = regnk.Registration(n, n, NT, BETAS[0], **pc_opts)
     R.set_images(d_mR, d_mT)
     v = torch.zeros(2 * n * n, device=dev)
     h_v = torch.empty(2 * n * n).pin_memory()
@@ -304,8 +312,8 @@ def main():
     launches = regnk.launch_count() - launches0
     total_ms = float(sum(step_ms))
 
-    # ---- the same K solves again with per-kernel-class CUDA events (launch
-    # sequences that the timed pass replays as graphs run eagerly here)
+    # ---- the same K solves again with per-kernel-class CUDA events (inside
+    # the replayed graphs each kernel is bracketed by event nodes)
     R.profile_enable(True)
     for _ in range(args.steps):
         flush.fill_(1.0)
@@ -350,7 +358,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(),
+                "config": workload_config(args.precond),
                 "time_to_solution_s": total_ms / args.steps / 1e3,
                 "newton_iters_per_solve": stats["newton"] / args.steps,
                 "matvecs_per_solve": stats["matvecs"] / args.steps,

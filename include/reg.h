@@ -83,6 +83,13 @@ typedef struct {
   unsigned long long lanczos_seed; /* SplitMix64 seed of the Lanczos start vector   */
   int max_backtracks;      /* Armijo halvings, default 10                            */
   double armijo_c1;        /* Armijo constant, default 1e-4                          */
+  int persistent_matvec;   /* 0 (default): one launch per transport step; 1: the GN
+                              data term runs as one persistent cooperative kernel   */
+  int inject_barrier_timeout; /* failure injection for tests, default 0: if 1, the
+                              persistent kernel's first grid barrier waits for an
+                              arrival that never comes; every block gives up after
+                              its bounded wait (~0.5 s) and the call returns
+                              REG_ETIMEOUT with the context still usable          */
 } reg_options;
 
 typedef struct {
@@ -260,11 +267,13 @@ enum { REG_KC_FFT_ROWS = 0,       /* row FFT passes (forward and inverse)       
        REG_KC_INCSTATE_STEP = 6,  /* incremental state steps                     */
        REG_KC_REDUCE = 7,         /* FP64 inner products and norms               */
        REG_KC_VECTOR = 8,         /* Krylov vector updates                       */
-       REG_KC_COUNT = 9 };
-/* enable != 0 starts profiling and clears the totals; 0 stops it. While
- * profiling, launch sequences that are otherwise replayed as CUDA graphs
- * (the fine matvec inside PCG, the P_2L application with CHEB) run as
- * individual launches so that each is timed. */
+       REG_KC_MATVEC = 9,         /* persistent GN data-term matvec (one launch) */
+       REG_KC_COUNT = 10 };
+/* enable != 0 starts profiling and clears the totals; 0 stops it. Launch
+ * sequences that are replayed as CUDA graphs (the fine matvec inside PCG,
+ * the P_2L application with CHEB) are then captured with an event pair
+ * around every kernel and the stream is synchronised after each replay to
+ * read them, so their kernel times carry no host launch gaps. */
 reg_status reg_profile_enable(reg_ctx* ctx, int enable);
 /* Totals of one kernel class since the last reg_profile_enable(ctx, 1);
  * ms, launches and bytes are host pointers (any may be NULL). */

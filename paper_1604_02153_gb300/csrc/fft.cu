@@ -38,11 +38,13 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
 }
 
 // Lines per block and threads per block of the FFT kernels, by log2 of the
-// line length: P lines of N complex values = at most 32 KB of shared memory.
+// line length: P lines of N complex values = 1024 complex values (8 KB of
+// shared memory) per block, so that even the 512^2 grid gives a few hundred
+// blocks per pass; one radix-4 butterfly per thread and pass up to N = 1024.
 template <int LOGN>
 struct FftCfg {
   static constexpr int N = 1 << LOGN;
-  static constexpr int P = (4096 / N) < 16 ? ((4096 / N) < 1 ? 1 : 4096 / N) : 16;
+  static constexpr int P = (1024 / N) < 16 ? ((1024 / N) < 1 ? 1 : 1024 / N) : 16;
   static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
 };
 

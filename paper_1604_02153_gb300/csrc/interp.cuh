@@ -1,0 +1,146 @@
+// Device building blocks of the semi-Lagrangian kernels, shared by the
+// per-step kernels (transport.cu) and the persistent matvec kernel
+// (matvec.cu): the periodic cubic B-spline prefilter on a 32x32 tile and the
+// 4x4 periodic cubic interpolation stencil (§3.2, §3.5 "Interpolation").
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace regnk {
+
+// ---------------------------------------------------------------------------
+// Periodic cubic B-spline prefilter.
+//
+// The spline interpolant sum_m c[m] beta3(x - m) takes the node values
+// (c[k-1] + 4 c[k] + c[k+1]) / 6 per axis, so the coefficients are the
+// samples filtered by the inverse of that symbol. The inverse factors into a
+// causal and an anticausal first-order recursion with pole z1 = sqrt(3) - 2:
+//     y[k] = s[k] + z1 y[k-1],   c'[k] = y[k] + z1 c'[k+1],   c = -6 z1 c'.
+// A block filters a 32x32 output tile: it stages the tile with a periodic
+// halo of kL = 13 samples on every side in shared memory. Along x, each of
+// 4 threads per staged row produces 8 consecutive outputs, starting both
+// recursions kL samples outside its segment (the truncated start-up terms
+// decay as |z1|^13 < 4e-8, below FP32 resolution); along y, 4 threads per
+// column do the same. About 7 FMAs per sample and pass, in dependency chains
+// of 55 steps with 232 (x) and 128 (y) threads of the block busy.
+constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
+constexpr float kGain = 1.60769515458673624f;   // -6 z1
+constexpr int kL = 13;              // recursion start-up length (halo width)
+constexpr int kPX = 32, kPY = 32;   // output tile
+constexpr int kPW = kPX + 2 * kL;   // staged tile width  (58)
+constexpr int kPH = kPY + 2 * kL;   // staged tile height (58)
+constexpr int kPIn = kPW + 1;       // odd pitches: conflict-free row and column walks
+constexpr int kPMid = kPX + 1;
+constexpr int kPThreads = 256;
+
+// both recursions over n staged samples v[0..n-1]; outputs for k in
+// [kL, kL + m) are written through out(k - kL, value)
+template <int NS, int M, typename Out>
+__device__ __forceinline__ void bspline_recursions(float (&v)[NS], Out out) {
+#pragma unroll
+  for (int k = 1; k < NS; ++k) v[k] = fmaf(kZ1, v[k - 1], v[k]);
+  float c = v[NS - 1];
+#pragma unroll
+  for (int k = NS - 2; k >= kL; --k) {
+    c = fmaf(kZ1, c, v[k]);
+    if (k < kL + M) out(k - kL, kGain * c);
+  }
+}
+
+// Prefilters the 32x32 output tile at (x0, y0) of one field (all kPThreads
+// threads of the block take part; `sin_` and `smid` are the block's staging
+// buffers of kPH*kPIn and kPH*kPMid floats). COHERENT = true reads the source
+// through L2 only (for data written earlier in the same kernel by other
+// blocks). The caller synchronises before reusing the buffers.
+template <bool COHERENT = false>
+__device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, float* __restrict__ dst,
+                                               int n1, int n2, int log1, int x0, int y0,
+                                               float* sin_, float* smid) {
+  const int t = threadIdx.x;
+  for (int q = t; q < kPH * kPW; q += kPThreads) {
+    const int r = q / kPW, c = q - r * kPW;
+    const int gx = (x0 - kL + c) & (n1 - 1);
+    const int gy = (y0 - kL + r) & (n2 - 1);
+    const float* a = src + ((long long)gy << log1) + gx;
+    sin_[r * kPIn + c] = COHERENT ? __ldcg(a) : __ldg(a);
+  }
+  __syncthreads();
+  constexpr int kSeg = 8, kSegs = kPX / kSeg, kLen = kSeg + 2 * kL;   // 34 samples per chain
+  if (t < kPH * kSegs) {   // x recursions: staged row t / 4, segment t % 4
+    const int r = t / kSegs, sg = t % kSegs;
+    float v[kLen];
+#pragma unroll
+    for (int k = 0; k < kLen; ++k) v[k] = sin_[r * kPIn + sg * kSeg + k];
+    float* row = smid + r * kPMid + sg * kSeg;
+    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { row[o] = x; });
+  }
+  __syncthreads();
+  if (t < kPX * kSegs) {   // y recursions: column t % 32, segment t / 32
+    const int c = t % kPX, sg = t / kPX;
+    float v[kLen];
+#pragma unroll
+    for (int k = 0; k < kLen; ++k) v[k] = smid[(sg * kSeg + k) * kPMid + c];
+    float* col = dst + x0 + c;
+    const int yb = y0 + sg * kSeg;
+    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) {
+      col[(long long)(yb + o) << log1] = x;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4x4 periodic cubic interpolation at node (i, j) + (d1, d2) cells.
+struct Stencil {
+  int ii[4];
+  int jj[4];   // row offsets (already multiplied by n1)
+  float w1[4], w2[4];
+};
+
+__device__ __forceinline__ void cubic_weights(float t, float (&w)[4], bool lagrange) {
+  if (lagrange) {  // cubic Lagrange on nodes -1, 0, 1, 2
+    const float tm1 = t - 1.f, tm2 = t - 2.f, tp1 = t + 1.f;
+    w[0] = -t * tm1 * tm2 * (1.f / 6.f);
+    w[1] = tp1 * tm1 * tm2 * 0.5f;
+    w[2] = -tp1 * t * tm2 * 0.5f;
+    w[3] = tp1 * t * tm1 * (1.f / 6.f);
+  } else {         // centred cubic B-spline
+    const float s = 1.f - t, t2 = t * t, t3 = t2 * t;
+    w[0] = s * s * s * (1.f / 6.f);
+    w[1] = (3.f * t3 - 6.f * t2 + 4.f) * (1.f / 6.f);
+    w[2] = (-3.f * t3 + 3.f * t2 + 3.f * t + 1.f) * (1.f / 6.f);
+    w[3] = t3 * (1.f / 6.f);
+  }
+}
+
+__device__ __forceinline__ Stencil make_stencil(int i, int j, float d1, float d2, int n1,
+                                                int n2, int log1, bool lagrange) {
+  Stencil S;
+  const float f1 = floorf(d1), f2 = floorf(d2);
+  cubic_weights(d1 - f1, S.w1, lagrange);
+  cubic_weights(d2 - f2, S.w2, lagrange);
+  const int i0 = i + (int)f1 - 1, j0 = j + (int)f2 - 1;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    S.ii[a] = (i0 + a) & (n1 - 1);
+    S.jj[a] = ((j0 + a) & (n2 - 1)) << log1;
+  }
+  return S;
+}
+
+template <bool COHERENT = false>
+__device__ __forceinline__ float ld(const float* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+
+template <bool COHERENT = false>
+__device__ __forceinline__ float apply_stencil(const Stencil& S, const float* __restrict__ c) {
+  float acc = 0.f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float* row = c + S.jj[b];
+    const float r = S.w1[0] * ld<COHERENT>(row + S.ii[0]) + S.w1[1] * ld<COHERENT>(row + S.ii[1]) +
+                    S.w1[2] * ld<COHERENT>(row + S.ii[2]) + S.w1[3] * ld<COHERENT>(row + S.ii[3]);
+    acc = fmaf(S.w2[b], r, acc);
+  }
+  return acc;
+}
+
+}  // namespace regnk

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "interp.cuh"
+
 namespace regnk {
 
 // Kernel launches issued by the library since load (incremented after every
@@ -66,6 +68,30 @@ void launch_incstate_step(int n1, int n2, float ht, const float* coef, const flo
                           const float* vt, const float* vtD, const float* G,
                           const float* gm, float* out, int first, int lagrange,
                           cudaStream_t st);
+
+// matvec.cu: persistent Gauss-Newton data-term matvec (one cooperative launch)
+struct MatvecArgs {
+  int n1, n2, log1, nt, lagrange;
+  long long N;
+  float ht;
+  const float* vt;          // direction v~ (2N)
+  const float* dX;          // forward departure displacement (2N)
+  const float* dY;          // backward departure displacement (2N)
+  const float* delta;       // div v (N)
+  const float* delta_bar;   // div v at Y_D (N)
+  const float* gm;          // grad m_0..grad m_nt (2 (nt+1) N)
+  const float* G;           // grad m_{j-1}(X_D), j = 1..nt (2 nt N)
+  float* c2;                // scratch: coefficients of v~ (2N)
+  float* vtD;               // scratch: v~(X_D) (2N)
+  float* fA;                // scratch (N)
+  float* fB;                // scratch (N)
+  float* coef;              // scratch: coefficients of one field (N)
+  float* b;                 // output: the data term b~ (2N)
+  unsigned* bar;            // grid barrier: counter, generation (self-resetting)
+  int* err;                 // set when a barrier wait gave up
+  unsigned missing;         // failure injection: arrivals that never come (tests)
+};
+cudaError_t launch_gn_matvec(const MatvecArgs& a, cudaStream_t st);
 
 // reduce.cu
 void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,

@@ -110,7 +110,18 @@ struct reg_ctx {
   // CUDA graphs of fixed launch sequences (fine matvec, P_2L with CHEB)
   cudaStream_t cap = nullptr;
   bool graphs = true;
-  struct GraphEntry { std::string key; cudaGraphExec_t exec; long long kernels; };
+  struct GraphEntry {
+    std::string key;
+    cudaGraphExec_t exec;
+    long long kernels;
+    std::vector<Rec> prof_recs;   // event pairs recorded inside the graph (profiling)
+  };
+  bool capturing = false;
+  // persistent matvec: barrier state (2 unsigned) and error flag, device
+  bool persistent = true;
+  unsigned* bar = nullptr;
+  int* barerr = nullptr;
+  int* hbarerr = nullptr;
   std::vector<GraphEntry> graph_cache;
   double graph_beta = -1, graph_emin = -1, graph_emax = -1;
 };
@@ -170,18 +181,30 @@ class Prof {
  public:
   Prof(reg_ctx* c, int cls, double bytes) : c_(c) {
     if (!c->prof) return;
-    if (c->recs.size() >= 8192) harvest(c);
+    if (c->recs.size() >= 8192 && !c->capturing) harvest(c);
     r_.cls = cls;
     r_.bytes = bytes;
     r_.a = take_event(c);
     r_.b = take_event(c);
-    cudaEventRecord(r_.a, c->st);
+    record(r_.a);
   }
   ~Prof() {
     if (!c_->prof) return;
-    cudaEventRecord(r_.b, c_->st);
+    record(r_.b);
     c_->recs.push_back(r_);
   }
+
+ private:
+  // inside a stream capture an event record only becomes a graph node with
+  // the external flag
+  void record(cudaEvent_t e) {
+    if (c_->capturing)
+      cudaEventRecordWithFlags(e, c_->st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, c_->st);
+  }
+
+ public:
 
  private:
   reg_ctx* c_;
@@ -250,8 +273,13 @@ void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
 bool lagrange(const reg_ctx* c) { return c->opt.interp == REG_INTERP_LAGRANGE; }
 
 void drop_graphs(reg_ctx* c) {
-  for (auto& g : c->graph_cache)
+  for (auto& g : c->graph_cache) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& r : g.prof_recs) {
+      c->evpool.push_back(r.a);
+      c->evpool.push_back(r.b);
+    }
+  }
   c->graph_cache.clear();
 }
 
@@ -259,15 +287,18 @@ void drop_graphs(reg_ctx* c) {
 // as a CUDA graph: the first call of a key runs eagerly, the second captures
 // the sequence on a private stream, later calls replay it on c->st. Graphs
 // are dropped when beta or the Chebyshev bounds change (they are launch
-// arguments). Profiling runs everything eagerly so that every launch is
-// bracketed by its own events.
-// Returns true when the body ran eagerly (host-side counters inside it ran).
+// arguments). While profiling, separate graphs are captured whose kernels
+// are bracketed by event-record nodes; after each replay the stream is
+// synchronised and those events are read, so kernel times carry no host
+// launch gaps. Returns true when the body ran eagerly (host-side counters
+// inside it ran).
 template <typename Body>
-bool graphed(reg_ctx* c, const std::string& key, Body body) {
-  if (!c->graphs || c->prof) {
+bool graphed(reg_ctx* c, const std::string& key0, Body body) {
+  if (!c->graphs) {
     body();
     return true;
   }
+  const std::string key = c->prof ? "P" + key0 : key0;
   if (c->graph_beta != c->beta || c->graph_emin != c->emin || c->graph_emax != c->emax) {
     drop_graphs(c);
     c->graph_beta = c->beta;
@@ -278,25 +309,39 @@ bool graphed(reg_ctx* c, const std::string& key, Body body) {
   for (auto& g : c->graph_cache)
     if (g.key == key) e = &g;
   if (!e) {
-    c->graph_cache.push_back({key, nullptr, 0});
+    c->graph_cache.push_back({key, nullptr, 0, {}});
     body();
     return true;
   }
   if (!e->exec) {
     cudaStream_t user = c->st;
+    const size_t rec0 = c->recs.size();
     check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     c->st = c->cap;
+    c->capturing = true;
     cudaGraph_t graph = nullptr;
     try {
       body();
     } catch (...) {
+      // capture failed (e.g. a launch form the graph cannot hold): drop the
+      // capture, stop using graphs in this context and run eagerly
       cudaStreamEndCapture(c->cap, &graph);
       if (graph) cudaGraphDestroy(graph);
       c->st = user;
-      throw;
+      c->capturing = false;
+      c->recs.resize(rec0);
+      cudaGetLastError();
+      c->graphs = false;
+      drop_graphs(c);
+      body();
+      return true;
     }
     c->st = user;
+    c->capturing = false;
     check(c, cudaStreamEndCapture(c->cap, &graph), "end capture");
+    // event pairs recorded during capture belong to the graph
+    e->prof_recs.assign(c->recs.begin() + rec0, c->recs.end());
+    c->recs.resize(rec0);
     // the captured launches were counted; count them once per replay instead
     size_t nn = 0;
     cudaGraphGetNodes(graph, nullptr, &nn);
@@ -315,6 +360,16 @@ bool graphed(reg_ctx* c, const std::string& key, Body body) {
   }
   check(c, cudaGraphLaunch(e->exec, c->st), "graph launch");
   g_launch_count += e->kernels;
+  if (!e->prof_recs.empty()) {
+    check(c, cudaStreamSynchronize(c->st), "profile sync");
+    for (auto& r : e->prof_recs) {
+      float ms = 0.f;
+      check(c, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+      c->prof_ms[r.cls] += ms;
+      c->prof_bytes[r.cls] += r.bytes;
+      c->prof_n[r.cls] += 1;
+    }
+  }
   return false;
 }
 
@@ -426,7 +481,17 @@ double* slot(reg_ctx* c, int s) { return c->dsc + s; }
 void read_slots(reg_ctx* c, int first, int count) {
   check(c, cudaMemcpyAsync(c->hsc + first, c->dsc + first, count * sizeof(double),
                            cudaMemcpyDeviceToHost, c->st), "scalar read");
+  check(c, cudaMemcpyAsync(c->hbarerr, c->barerr, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+        "barrier flag read");
   check(c, cudaStreamSynchronize(c->st), "stream synchronize");
+  if (*c->hbarerr) {
+    // a persistent kernel gave up waiting at a grid barrier: reset its state
+    cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->st);
+    cudaMemsetAsync(c->barerr, 0, sizeof(int), c->st);
+    cudaStreamSynchronize(c->st);
+    *c->hbarerr = 0;
+    fail(c, REG_ETIMEOUT, "grid barrier wait of the persistent matvec timed out");
+  }
 }
 
 void dot_async(reg_ctx* c, const float* a, const float* b, long long n, int s) {
@@ -559,8 +624,54 @@ void hessian(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) 
   hessian_core(c, L, vt, out, data_only);
 }
 
+// one cooperative launch for the data term b~ (matvec.cu)
+void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
+  MatvecArgs a{};
+  a.n1 = L.g.n1;
+  a.n2 = L.g.n2;
+  a.log1 = L.g.log1;
+  a.nt = L.nt;
+  a.lagrange = lagrange(c);
+  a.N = L.g.N;
+  a.ht = L.ht;
+  a.vt = vt;
+  a.dX = L.dX;
+  a.dY = L.dY;
+  a.delta = L.delta;
+  a.delta_bar = L.delta_bar;
+  a.gm = L.gm;
+  a.G = L.G;
+  a.c2 = L.c2;
+  a.vtD = L.vtD;
+  a.fA = L.fA;
+  a.fB = L.fB;
+  a.coef = L.coef;
+  a.b = b;
+  a.bar = c->bar;
+  a.err = c->barerr;
+  a.missing = c->opt.inject_barrier_timeout ? 1u : 0u;
+  // algorithmic bytes per point: v~(X_D) and the first step 52, each later
+  // incremental state step 48, each incremental adjoint step 48, each of the
+  // 2 nt + 1 prefilters 8 (spline only)
+  const double per_point = 52.0 + 48.0 * (L.nt - 1) + 48.0 * L.nt +
+                           (lagrange(c) ? 0.0 : 8.0 * (2 * L.nt + 1));
+  Prof P(c, REG_KC_MATVEC, (double)L.g.N * per_point);
+  check(c, launch_gn_matvec(a, c->st), "persistent matvec launch");
+}
+
 // the launch sequence of one GN matvec; needs ensure_G(c, L) beforehand
 void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
+  if (c->persistent) {
+    const size_t N2 = 2 * (size_t)L.g.N;
+    if (data_only) {
+      data_term_persistent(c, L, vt, out);
+    } else {
+      data_term_persistent(c, L, vt, L.b);
+      spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+    }
+    (void)N2;
+    return;
+  }
   const GridDims& gd = L.g;
   const size_t N = (size_t)gd.N;
   const int nt = L.nt;
@@ -692,6 +803,15 @@ void estimate_eigenvalues(reg_ctx* c) {
   c->have_eig = true;
 }
 
+// (I + (beta A_c)^-1 Q_c) u on the coarse level: the split operator above
+// conjugated by (beta A_c)^1/2, same spectrum, one spectral operation less.
+void coarse_op_u(reg_ctx* c, const float* u, float* out) {
+  Level& C = c->coarse;
+  hessian_core(c, C, u, c->cq, true);
+  spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u);
+  ++c->coarse_matvecs;
+}
+
 void cheb(reg_ctx* c, const float* rhs, float* x) {
   const long long n = 2 * c->coarse.g.N;
   const double theta = 0.5 * (c->emax + c->emin), delta = 0.5 * (c->emax - c->emin);
@@ -701,7 +821,7 @@ void cheb(reg_ctx* c, const float* rhs, float* x) {
   launch_lincomb(n, (float)(1.0 / theta), rhs, 0.f, nullptr, c->cd, c->st);
   check(c, cudaMemcpyAsync(x, c->cd, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
   for (int it = 1; it < c->opt.cheb_iters; ++it) {
-    coarse_split_op(c, c->cd, c->cAd);
+    coarse_op_u(c, c->cd, c->cAd);
     {
       Prof P(c, REG_KC_VECTOR, 12.0 * n);
       launch_lincomb(n, 1.f, c->cr, -1.f, c->cAd, c->cr, c->st);
@@ -786,12 +906,21 @@ void precond(reg_ctx* c, const float* r, float* z) {
   }
   Level& C = c->coarse;
   const long long nc = 2 * C.g.N;
-  // r' = (beta A)^-1/2 r; restricted low band -> crhs; high band (beta A)^-1 H r -> F.w1
-  resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
+  // high band: (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1
   spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
   if (c->opt.pc_solver == REG_PCSOLVER_CHEB) {
+    // CHEB(k) is a polynomial in the operator, so it can run on
+    // (beta A_c)^-1/2 (split operator) (beta A_c)^1/2 = I + (beta A_c)^-1 Q_c
+    // with u = (beta A_c)^-1/2 s: right-hand side R (beta A)^-1 r, and the
+    // result enters the prolongation without a further (beta A)^-1/2.
+    resample(c, F, C, SPOP_REGPOW, -1.0, r, 2, c->crhs, nullptr);
     cheb(c, c->crhs, c->cx);
-  } else {
+    resample(c, C, F, SPOP_SCALE, 0.0, c->cx, 2, z, F.w1);
+    return;
+  }
+  // r' = (beta A)^-1/2 r; restricted low band -> crhs
+  resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
+  {
     auto A = [&](const float* s, float* o) { coarse_split_op(c, s, o); };
     auto I = [&](const float* s, float* o) {
       check(c, cudaMemcpyAsync(o, s, nc * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
@@ -903,6 +1032,8 @@ reg_status reg_default_options(reg_options* o) {
   o->lanczos_seed = 20160407ULL;
   o->max_backtracks = 10;
   o->armijo_c1 = 1e-4;
+  o->persistent_matvec = 0;
+  o->inject_barrier_timeout = 0;
   return REG_OK;
 }
 
@@ -928,6 +1059,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->beta = beta;
   c->nt = nt;
   c->two_level = (o.precond == REG_PC_2L);
+  c->persistent = (o.persistent_matvec != 0);
   const reg_status s = guarded(c, [&] {
     alloc_level(c, c->fine, grid.n1, grid.n2, nt);
     if (c->two_level) alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, nt);
@@ -942,6 +1074,14 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
     c->partial = dalloc<double>(c, reduce_partials());
     c->partialf = dalloc<float>(c, reduce_partials());
     c->dflag = dalloc<int>(c, 1);
+    c->bar = dalloc<unsigned>(c, 2);
+    c->barerr = dalloc<int>(c, 1);
+    check(c, cudaMemset(c->bar, 0, 2 * sizeof(unsigned)), "memset");
+    check(c, cudaMemset(c->barerr, 0, sizeof(int)), "memset");
+    void* he = nullptr;
+    check(c, cudaMallocHost(&he, sizeof(int)), "cudaMallocHost");
+    c->hbarerr = static_cast<int*>(he);
+    *c->hbarerr = 0;
     const size_t n = 2 * (size_t)c->fine.g.N;
     c->kx = dalloc<float>(c, n);
     c->kr = dalloc<float>(c, n);
@@ -976,16 +1116,17 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
 reg_status reg_destroy(reg_ctx* c) {
   if (!c) return REG_OK;
   if (c->st) cudaStreamSynchronize(c->st);
+  drop_graphs(c);   // returns the graphs' profiling events to the pool
   for (auto& r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
-  drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
   if (c->hflag) cudaFreeHost(c->hflag);
+  if (c->hbarerr) cudaFreeHost(c->hbarerr);
   delete c;
   return REG_OK;
 }
@@ -1183,6 +1324,12 @@ reg_status reg_profile_enable(reg_ctx* c, int enable) {
   return guarded(c, [&] {
     harvest(c);
     c->prof = enable != 0;
+    // events are created here, not while a graph is being captured
+    while (c->prof && c->evpool.size() < 16384) {
+      cudaEvent_t e;
+      check(c, cudaEventCreate(&e), "cudaEventCreate");
+      c->evpool.push_back(e);
+    }
     for (int k = 0; k < REG_KC_COUNT; ++k) {
       c->prof_ms[k] = 0.0;
       c->prof_bytes[k] = 0.0;

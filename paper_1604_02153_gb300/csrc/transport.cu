@@ -10,85 +10,20 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "interp.cuh"
 #include "kernels.h"
 
 namespace regnk {
 
-// ---------------------------------------------------------------------------
-// Periodic cubic B-spline prefilter.
-//
-// The spline interpolant sum_m c[m] beta3(x - m) takes the node values
-// (c[k-1] + 4 c[k] + c[k+1]) / 6 per axis, so the coefficients are the
-// samples filtered by the inverse of that symbol. Its impulse response on
-// the infinite grid is sqrt(3) z1^|m| with z1 = sqrt(3) - 2; on a periodic
-// axis of n points it is the periodised sum
-//     a_m = sqrt(3) (z1^|m| + z1^(n-|m|)) / (1 - z1^n),   |m| < n/2.
-// |z1|^14 < 1e-8, so the filter is applied as a symmetric FIR with the
-// 2L + 1 = 27 central taps (truncated tail below 5e-8 of the input, under
-// FP32 resolution). Both axes run in one kernel: a block stages a
-// (TY + 2L) x (TX + 2L) tile of samples with its periodic halo in shared
-// memory, filters along x into a (TY + 2L) x TX tile and along y into the
-// TY x TX output; every thread computes 4 consecutive outputs per pass from
-// a sliding register window.
-constexpr int kL = 13;              // FIR half-width
-constexpr int kTaps = 2 * kL + 1;
-constexpr int kPX = 32, kPY = 32;   // output tile
-constexpr int kPW = kPX + 2 * kL;   // staged tile width  (58)
-constexpr int kPH = kPY + 2 * kL;   // staged tile height (58)
-constexpr int kPIn = kPW + 1;       // odd pitches: conflict-free column and row walks
-constexpr int kPMid = kPX + 1;
-constexpr int kPThreads = 256;
-
-struct SplineTaps {
-  float ax[kTaps];   // taps along x_1 (periodised for n1)
-  float ay[kTaps];   // taps along x_2 (periodised for n2)
-};
-
+// One block per 32x32 output tile and field.
 __global__ void __launch_bounds__(kPThreads)
 k_prefilter(const float* __restrict__ in, float* __restrict__ out, int n1, int n2, int log1,
-            long long fstride, SplineTaps taps) {
+            long long fstride) {
   __shared__ float sin_[kPH * kPIn];
   __shared__ float smid[kPH * kPMid];
-  const int t = threadIdx.x;
-  const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
   const long long fo = (long long)blockIdx.z * fstride;
-  const float* src = in + fo;
-  for (int q = t; q < kPH * kPW; q += kPThreads) {
-    const int r = q / kPW, c = q - r * kPW;
-    const int gx = (x0 - kL + c) & (n1 - 1);
-    const int gy = (y0 - kL + r) & (n2 - 1);
-    sin_[r * kPIn + c] = __ldg(src + ((long long)gy << log1) + gx);
-  }
-  __syncthreads();
-  // x pass: rows 0..kPH-1, 4 consecutive outputs per work item
-  for (int w = t; w < kPH * (kPX / 4); w += kPThreads) {
-    const int r = w / (kPX / 4), c0 = (w % (kPX / 4)) * 4;
-    const float* row = sin_ + r * kPIn + c0;
-    float win[kTaps + 3];
-#pragma unroll
-    for (int i = 0; i < kTaps + 3; ++i) win[i] = row[i];
-#pragma unroll
-    for (int o = 0; o < 4; ++o) {
-      float acc = 0.f;
-#pragma unroll
-      for (int m = 0; m < kTaps; ++m) acc = fmaf(taps.ax[m], win[o + m], acc);
-      smid[r * kPMid + c0 + o] = acc;
-    }
-  }
-  __syncthreads();
-  // y pass: 32 columns x 8 groups of 4 rows
-  const int c = t & 31, r0 = (t >> 5) * 4;
-  float win[kTaps + 3];
-#pragma unroll
-  for (int i = 0; i < kTaps + 3; ++i) win[i] = smid[(r0 + i) * kPMid + c];
-  float* dst = out + fo;
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    float acc = 0.f;
-#pragma unroll
-    for (int m = 0; m < kTaps; ++m) acc = fmaf(taps.ay[m], win[o + m], acc);
-    dst[((long long)(y0 + r0 + o) << log1) + x0 + c] = acc;
-  }
+  prefilter_tile(in + fo, out + fo, n1, n2, log1, blockIdx.x * kPX, blockIdx.y * kPY, sin_,
+                 smid);
 }
 
 static int ilog2i(int n) {
@@ -97,80 +32,12 @@ static int ilog2i(int n) {
   return l;
 }
 
-static void periodised_taps(int n, float* a) {
-  const double z = std::sqrt(3.0) - 2.0;
-  const double zn = std::pow(z, n);
-  for (int m = -kL; m <= kL; ++m) {
-    const int am = m < 0 ? -m : m;
-    a[m + kL] = (float)(std::sqrt(3.0) * (std::pow(z, am) + std::pow(z, n - am)) / (1.0 - zn));
-  }
-}
-
 void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
                       cudaStream_t st) {
   (void)tmp;
-  static int c1 = -1, c2 = -1;
-  static SplineTaps taps;
-  if (c1 != n1 || c2 != n2) {
-    periodised_taps(n1, taps.ax);
-    periodised_taps(n2, taps.ay);
-    c1 = n1;
-    c2 = n2;
-  }
   k_prefilter<<<dim3(n1 / kPX, n2 / kPY, F), kPThreads, 0, st>>>(in, out, n1, n2, ilog2i(n1),
-                                                                  (long long)n1 * n2, taps);
+                                                                  (long long)n1 * n2);
   ++g_launch_count;
-}
-
-// ---------------------------------------------------------------------------
-// 4x4 periodic cubic interpolation at node (i, j) + (d1, d2) cells.
-struct Stencil {
-  int ii[4];
-  int jj[4];   // row offsets (already multiplied by n1)
-  float w1[4], w2[4];
-};
-
-__device__ __forceinline__ void cubic_weights(float t, float (&w)[4], bool lagrange) {
-  if (lagrange) {  // cubic Lagrange on nodes -1, 0, 1, 2
-    const float tm1 = t - 1.f, tm2 = t - 2.f, tp1 = t + 1.f;
-    w[0] = -t * tm1 * tm2 * (1.f / 6.f);
-    w[1] = tp1 * tm1 * tm2 * 0.5f;
-    w[2] = -tp1 * t * tm2 * 0.5f;
-    w[3] = tp1 * t * tm1 * (1.f / 6.f);
-  } else {         // centred cubic B-spline
-    const float s = 1.f - t, t2 = t * t, t3 = t2 * t;
-    w[0] = s * s * s * (1.f / 6.f);
-    w[1] = (3.f * t3 - 6.f * t2 + 4.f) * (1.f / 6.f);
-    w[2] = (-3.f * t3 + 3.f * t2 + 3.f * t + 1.f) * (1.f / 6.f);
-    w[3] = t3 * (1.f / 6.f);
-  }
-}
-
-__device__ __forceinline__ Stencil make_stencil(int i, int j, float d1, float d2, int n1,
-                                                int n2, int log1, bool lagrange) {
-  Stencil S;
-  const float f1 = floorf(d1), f2 = floorf(d2);
-  cubic_weights(d1 - f1, S.w1, lagrange);
-  cubic_weights(d2 - f2, S.w2, lagrange);
-  const int i0 = i + (int)f1 - 1, j0 = j + (int)f2 - 1;
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    S.ii[a] = (i0 + a) & (n1 - 1);
-    S.jj[a] = ((j0 + a) & (n2 - 1)) << log1;
-  }
-  return S;
-}
-
-__device__ __forceinline__ float apply_stencil(const Stencil& S, const float* __restrict__ c) {
-  float acc = 0.f;
-#pragma unroll
-  for (int b = 0; b < 4; ++b) {
-    const float* row = c + S.jj[b];
-    const float r = S.w1[0] * __ldg(row + S.ii[0]) + S.w1[1] * __ldg(row + S.ii[1]) +
-                    S.w1[2] * __ldg(row + S.ii[2]) + S.w1[3] * __ldg(row + S.ii[3]);
-    acc = fmaf(S.w2[b], r, acc);
-  }
-  return acc;
 }
 
 constexpr int kPT = 256;  // threads per block of the pointwise kernels

@@ -25,7 +25,7 @@ REG_PCSOLVER_CHEB, REG_PCSOLVER_PCG = 0, 1
 REG_SPEC_GRAD, REG_SPEC_DIV, REG_SPEC_REG, REG_SPEC_REGPOW = 0, 1, 2, 3
 REG_SPEC_LOWPASS, REG_SPEC_HIGHPASS, REG_SPEC_PREFILTER = 4, 5, 6
 KERNEL_CLASSES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
-                  "adjoint_step", "incstate_step", "reduce", "vector"]
+                  "adjoint_step", "incstate_step", "reduce", "vector", "matvec"]
 
 
 class RegError(RuntimeError):
@@ -45,7 +45,8 @@ class reg_options(ctypes.Structure):
                 ("max_newton", ctypes.c_int), ("max_pcg", ctypes.c_int),
                 ("lanczos_steps", ctypes.c_int), ("emax_safety", ctypes.c_double),
                 ("lanczos_seed", ctypes.c_ulonglong), ("max_backtracks", ctypes.c_int),
-                ("armijo_c1", ctypes.c_double)]
+                ("armijo_c1", ctypes.c_double), ("persistent_matvec", ctypes.c_int),
+                ("inject_barrier_timeout", ctypes.c_int)]
 
 
 class reg_info(ctypes.Structure):

@@ -194,10 +194,11 @@ def f32(a):
     return np.asarray(a, dtype=np.float32).astype(np.float64)
 
 
+@pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
 @pytest.mark.parametrize("n1,n2,nt,norm", [(64, 64, 4, 1), (128, 64, 8, 1), (256, 256, 4, 1),
-                                           (64, 64, 4, 2)])
-def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm):
+                                           (64, 64, 4, 2), (128, 64, 1, 1)])
+def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm, persistent):
     """Objective, gradient and GN Hessian matvec against the oracle on the
     same FP32 inputs. The data terms b = g - beta A v and b~ = H u - beta A u
     (transport, interpolation, time integral) meet the 1e-4 bar; the full
@@ -205,7 +206,8 @@ def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm):
     FP32 cannot resolve better on smooth fields (see the module doc)."""
     interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
     beta = 1e-2
-    R = regnk.Registration(n1, n2, nt, beta, interp=interp, reg_norm=norm)
+    R = regnk.Registration(n1, n2, nt, beta, interp=interp, reg_norm=norm,
+                           persistent_matvec=persistent)
     m_R, m_T, v = (f32(a) for a in problem_data(n1, n2))
     R.set_images(dev(m_R), dev(m_T))
     P = Problem(m_R, m_T, nt, beta, reg_norm=f"H{norm}", kind=kind)
@@ -235,9 +237,10 @@ def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm):
     R.close()
 
 
-def test_matvec_never_stale(regnk):
+@pytest.mark.parametrize("persistent", [1, 0])
+def test_matvec_never_stale(regnk, persistent):
     n, nt = 64, 4
-    R = regnk.Registration(n, n, nt, 1e-2)
+    R = regnk.Registration(n, n, nt, 1e-2, persistent_matvec=persistent)
     m_R, m_T, v = problem_data(n, n)
     R.set_images(dev(m_R), dev(m_T))
     R.objective_gradient(dev(v), None)
@@ -380,6 +383,36 @@ def test_full_solve_64(regnk, pc, pcs):
     assert rel(host(v, (2, n, n)), vo) < 1e-3
     assert abs(info["J"] - oinfo["J"]) / oinfo["J"] < 1e-4
     R.close()
+
+
+def test_barrier_timeout_is_reported(regnk):
+    """Failure detection without a GPU fault: the persistent matvec's grid
+    barrier is told to wait for an arrival that never comes; every block
+    gives up after its bounded wait, the call returns REG_ETIMEOUT and the
+    context keeps working."""
+    n, nt = 64, 4
+    m_R, m_T, v = problem_data(n, n)
+    R = regnk.Registration(n, n, nt, 1e-2, inject_barrier_timeout=1, precond=regnk.REG_PC_REG,
+                           persistent_matvec=1)
+    R.set_images(dev(m_R), dev(m_T))
+    vd = dev(v)
+    R.objective_gradient(vd, None)
+    H = torch.empty(2 * n * n, device="cuda")
+    with pytest.raises(regnk.RegError) as e:
+        R.hessian_matvec(vd, dev(v), H)
+        R.dot(H, H)            # the status surfaces at the next synchronising call
+    assert e.value.status == regnk.REG_ETIMEOUT
+    # the same context still computes correctly afterwards with the per-step path
+    assert R.dot(vd, vd) > 0
+    R.close()
+    R2 = regnk.Registration(n, n, nt, 1e-2, precond=regnk.REG_PC_REG)
+    R2.set_images(dev(m_R), dev(m_T))
+    R2.objective_gradient(vd, None)
+    R2.hessian_matvec(vd, dev(v), H)
+    P = Problem(m_R, m_T, nt, 1e-2)
+    P.state_solve(v)
+    assert rel(host(H, (2, n, n)), P.hessian_matvec(v)) < 1e-3
+    R2.close()
 
 
 def test_invalid_call_order(regnk):
