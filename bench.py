@@ -66,6 +66,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
                     help="preconditioner of the solve (the workload's is 2l-cheb)")
+    ap.add_argument("--persistent", type=int, choices=[0, 1], default=0,
+                    help="1: GN data term as one persistent cooperative kernel")
+    ap.add_argument("--workload", choices=["phantom1024", "batch64"], default="phantom1024",
+                    help="phantom1024: the 1024^2 continuation solve (default); batch64: "
+                         "64 independent problems of uneven size")
     return ap.parse_args()
 
 
@@ -87,14 +92,15 @@ def source_hash(fname):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def ncu_traffic(cls, launches_bytes_per_launch):
-    """Per-launch DRAM traffic of a kernel class from the committed ncu
-    summary, or None if absent or captured from a different source."""
+def ncu_traffic(level, cls):
+    """Per-launch DRAM traffic of a kernel class on a grid level from the
+    committed ncu summary, or None if absent or captured from a different
+    source."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    e = d.get(cls)
+    e = d.get(f"{level}/{cls}")
     if not e or e.get("source_sha256_16") != source_hash(CLASS_SOURCES[cls]):
         return None
     return e.get("dram_bytes_per_launch_full_size")
@@ -233,11 +239,95 @@ def aggregate_ranks(dist, device, total_ms, matvecs, e2e_ms, e2e_matvecs):
     return float(w[0]) / (float(t[0]) / 1e3), float(w[1]) / (float(t[1]) / 1e3)
 
 
+BATCH_SIZES = (128, 192, 256, 384, 512)
+BATCH_B = 64
+BATCH_NT = 4
+BATCH_BETA = 1e-2
+
+
+def run_batch(args):
+    """64 independent problems, grids drawn (seed 200) from BATCH_SIZES^2,
+    each the analytic template/velocity pair with m_R = m_T transported by
+    v* (nt = 4, computed on the GPU), H1, beta = 1e-2, P_2L-CHEB(10), solved
+    to ||g||rel 1e-2 from v = 0: concurrently (reg_batch) and one by one."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1604_02153_gb300 import inputs, regnk
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(200)
+    sizes = [int(x) for x in rng.choice(BATCH_SIZES, size=BATCH_B)]
+    f = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device=dev)
+    mR, mT = [], []
+    cache = {}
+    for n in sizes:
+        if n not in cache:
+            m_T, vstar = inputs.sinusoid_pair(n)
+            R = regnk.Registration(n, n, BATCH_NT, BATCH_BETA)
+            m1 = torch.empty(n * n, device=dev)
+            R.transport(f(vstar), f(m_T), m1)
+            torch.cuda.synchronize()
+            R.close()
+            cache[n] = (m1.clone(), f(m_T))
+        mR.append(cache[n][0])
+        mT.append(cache[n][1])
+    grids = [(n, n) for n in sizes]
+    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B)
+    batch.set_images(mR, mT)
+    vs = [torch.zeros(2 * n * n, device=dev) for n in sizes]
+    for _ in range(max(1, args.warmup)):
+        for v in vs:
+            v.zero_()
+        batch.solve(vs, GTOL)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mv_b = 0
+    for _ in range(args.steps):
+        for v in vs:
+            v.zero_()
+        infos = batch.solve(vs, GTOL)
+        mv_b += sum(i["matvecs"] for i in infos)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    # one by one: the same contexts, one host thread
+    t0 = time.perf_counter()
+    mv_s = 0
+    for _ in range(args.steps):
+        for v in vs:
+            v.zero_()
+        infos1 = batch.solve(vs, GTOL, threads=1)
+        mv_s += sum(i["matvecs"] for i in infos1)
+    torch.cuda.synchronize()
+    t_serial = (time.perf_counter() - t0) / args.steps
+    batch.close()
+    per_problem_serial = [i["seconds"] for i in infos1]
+    line = {"metric": "aggregate Hessian matvecs/s, 64 independent problems of uneven size",
+            "value": mv_b / args.steps / t_batch, "unit": "matvecs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{BATCH_B} problems, grids from {list(BATCH_SIZES)}^2 "
+                                   f"(seed 200), analytic pair, nt={BATCH_NT}, H1, "
+                                   f"beta={BATCH_BETA}, P_2L CHEB(10), ||g||rel 1e-2",
+                       "sizes": sizes},
+            "one_by_one": {"value": mv_s / args.steps / t_serial, "seconds_per_batch": t_serial,
+                           "mean_time_to_solution_s": float(np.mean(per_problem_serial))},
+            "concurrent": {"seconds_per_batch": t_batch,
+                           "mean_time_to_solution_s": float(np.mean([i["seconds"] for i in infos])),
+                           "status": sorted(set(i["status_name"] for i in infos))},
+            "speedup_vs_one_by_one": t_serial / t_batch}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "batch64":
+        if rank == 0:
+            run_batch(args)
         return
     import torch
     dist = None
@@ -263,7 +353,7 @@ def main():
     pc_opts = {"2l-cheb": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_CHEB),
                "2l-pcg": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_PCG),
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
-    R = regnk.Registration(n, n, NT, BETAS[0], **pc_opts)
+    R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent, **pc_opts)
     R.set_images(d_mR, d_mT)
     v = torch.zeros(2 * n * n, device=dev)
     h_v = torch.empty(2 * n * n).pin_memory()
@@ -339,19 +429,23 @@ def main():
         e2e_mv += s2["matvecs"]
     value, e2e_value = aggregate_ranks(dist, dev, total_ms, stats["matvecs"], e2e_ms, e2e_mv)
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant kernel class (per grid level)
     dom = max(prof, key=lambda k: prof[k][0])
     ms, nl, by = prof[dom]
     hbm, how = peaks()
     achieved = (by / (ms / 1e3)) / 1e9 if ms > 0 else None
     per_launch = by / nl if nl else None
-    roof = {"bound": "hbm", "kernel_class": dom, "achieved": achieved, "peak": hbm,
+    total_prof_ms = sum(p[0] for p in prof.values())
+    level, cls = dom
+    roof = {"bound": "hbm", "kernel_class": cls, "grid_level": level,
+            "grid": [n, n] if level == "fine" else [n // 2, n // 2],
+            "achieved": achieved, "peak": hbm,
             "peak_source": f"{how} HBM copy bandwidth", "unit": "GB/s",
             "frac": (achieved / hbm) if achieved else None,
-            "traffic": ncu_traffic(dom, per_launch),
+            "traffic": ncu_traffic(level, cls),
             "algorithmic_bytes_per_launch": per_launch, "launches": nl,
-            "share_of_device_time": ms / sum(p[0] for p in prof.values()),
-            "classes_ms": {k: round(p[0], 3) for k, p in prof.items()}}
+            "share_of_device_time": ms / total_prof_ms,
+            "classes_ms": {f"{k[0]}/{k[1]}": round(p[0], 3) for k, p in prof.items() if p[1]}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

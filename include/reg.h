@@ -13,7 +13,8 @@
  * Conventions shared by every call
  * --------------------------------
  * Grid     n1 x n2 nodes, h_i = 2 pi / n_i, node (i, j) at (i h_1, j h_2).
- *          n1, n2 are powers of two in [32, 2048]. (§3.2)
+ *          n1, n2 are 2^k in [32, 2048] or 3 * 2^k in [96, 1536]; with the
+ *          two-level preconditioner n1/2 and n2/2 must be such sizes too. (§3.2)
  * Layout   a scalar field is n1*n2 contiguous float32, row-major with x_1
  *          fastest: u[j*n1 + i]. A vector field (v, v~, g, H v~) is two
  *          scalar fields back to back (structure of arrays): component 1 at
@@ -21,7 +22,8 @@
  * Memory   every float pointer is a DEVICE pointer on the context's device
  *          unless its comment says "host". The caller owns all field buffers;
  *          the library copies what it keeps and never frees caller memory.
- *          Device buffers must be 16-byte aligned (torch allocations are).
+ *          Device buffers must start on a 16-byte boundary (torch
+ *          allocations do); a call given one that does not returns REG_EINVAL.
  * Streams  every call runs on the stream set by reg_set_stream (default: the
  *          legacy default stream). Calls that return a host scalar or a
  *          status that depends on device data synchronise that stream;
@@ -165,7 +167,7 @@ enum { REG_SPEC_GRAD = 0, REG_SPEC_DIV = 1, REG_SPEC_REG = 2, REG_SPEC_REGPOW = 
 reg_status reg_spectral(reg_ctx* ctx, int op, double s, const float* in, float* out);
 
 /* Spectral restriction of a vector field from the context grid to the grid
- * (n1/2, n2/2) (cut-off filter at |k_i| < n_i/4 included) and prolongation
+ * (n1/2, n2/2), two-level contexts only, (cut-off filter at |k_i| < n_i/4 included) and prolongation
  * back by zero padding (§3.4.2 "Restriction/Prolongation", "Filters").
  * fine: 2*n1*n2 floats, coarse: 2*(n1/2)*(n2/2) floats, device. */
 reg_status reg_restrict(reg_ctx* ctx, const float* fine, float* coarse);
@@ -215,6 +217,36 @@ reg_status reg_eigen_bounds(reg_ctx* ctx, double* emin, double* emax);
  * REG_ELINESEARCH otherwise (v then holds the last accepted iterate). */
 reg_status reg_solve(reg_ctx* ctx, float* v, double gtol, reg_info* info);
 
+/* ---- Batches of independent problems --------------------------------------
+ * B problems, each with its own grid (any grid reg_create accepts), nt,
+ * beta[i] and the shared options, solved concurrently: every problem gets
+ * its own context and CUDA stream (non-blocking, created by the batch), and
+ * a pool of host threads drives the solves, so that the small kernels of
+ * different problems overlap on the GPU. Each problem's result equals a
+ * solve of that problem alone. Arrays of pointers are host arrays of B
+ * device pointers with the per-problem layout of the single-problem calls.
+ * The calls use the current CUDA device of the creating thread. */
+typedef struct reg_batch reg_batch;
+reg_status reg_batch_create(const reg_grid* grids, int B, int nt, const double* beta,
+                            const reg_options* opt, reg_batch** out);
+reg_status reg_batch_destroy(reg_batch* batch);
+/* Copies every problem's images (synchronises the batch's streams). */
+reg_status reg_batch_set_images(reg_batch* batch, const float* const* m_R,
+                                const float* const* m_T);
+/* Changes beta of every problem (beta: host array of B values). */
+reg_status reg_batch_set_beta(reg_batch* batch, const double* beta);
+/* reg_solve on every problem with up to `threads` host threads (<= 0: up to
+ * 32). v[i] is the initial guess and receives the result. infos (host, B
+ * entries) may be NULL. Returns REG_OK if every problem converged, else the
+ * first hard error, or REG_ENOTCONV / REG_ELINESEARCH if those were the only
+ * failures (see infos[i].status). */
+reg_status reg_batch_solve(reg_batch* batch, float* const* v, double gtol, int threads,
+                           reg_info* infos);
+/* reg_hessian_matvec on every problem (synchronises on return). */
+reg_status reg_batch_hessian_matvec(reg_batch* batch, const float* const* v,
+                                    const float* const* vt, float* const* Hvt);
+const char* reg_batch_last_error(const reg_batch* batch);
+
 /* ---- Allocation-free interpolation (no counterpart in the paper) ---------
  * For callers that must not allocate device memory while they run: code
  * whose device memory belongs to another framework's caching allocator (a
@@ -227,7 +259,7 @@ reg_status reg_solve(reg_ctx* ctx, float* v, double gtol, reg_info* info);
  * the samples u (n1*n2 floats, device) evaluated at displacements disp
  * (2*n1*n2 floats in cell units, component 1 then 2, device), written to out
  * (n1*n2 floats, device), on `cuda_stream` (cudaStream_t as void*, NULL for
- * the legacy default stream). n1, n2 are powers of two in [32, 2048] and
+ * the legacy default stream). n1, n2 are grid sizes reg_create accepts and
  * n1*n2 <= REG_STATIC_MAX_POINTS; anything else returns REG_EINVAL.
  *
  * The spline coefficients go to one fixed device array of
@@ -275,9 +307,10 @@ enum { REG_KC_FFT_ROWS = 0,       /* row FFT passes (forward and inverse)       
  * around every kernel and the stream is synchronised after each replay to
  * read them, so their kernel times carry no host launch gaps. */
 reg_status reg_profile_enable(reg_ctx* ctx, int enable);
-/* Totals of one kernel class since the last reg_profile_enable(ctx, 1);
- * ms, launches and bytes are host pointers (any may be NULL). */
-reg_status reg_profile_read(reg_ctx* ctx, int kclass, double* ms, long long* launches,
+/* Totals of one kernel class on one grid level (0: the problem grid, 1: the
+ * coarse grid of P_2L) since the last reg_profile_enable(ctx, 1); ms,
+ * launches and bytes are host pointers (any may be NULL). */
+reg_status reg_profile_read(reg_ctx* ctx, int level, int kclass, double* ms, long long* launches,
                             double* bytes);
 /* Kernels launched by the library in this process so far (all contexts),
  * counting every kernel node of every CUDA graph replay. */

@@ -17,8 +17,8 @@
 namespace regnk {
 
 struct GridDims {
-  int n1, n2;        // nodes per axis (powers of two)
-  int log1, log2;    // log2 of n1, n2
+  int n1, n2;        // nodes per axis (2^k or 3 * 2^k, multiples of 32)
+  int log1, log2;    // log2 of n1, n2 if powers of two, else -1
   long long N;       // n1 * n2
   int nk1;           // n1 / 2 + 1 spectral lines
   long long spec;    // nk1 * n2 complex values per spectrum
@@ -30,8 +30,10 @@ inline GridDims make_grid(int n1, int n2) {
   g.n2 = n2;
   g.log1 = 0;
   while ((1 << g.log1) < n1) ++g.log1;
+  if ((1 << g.log1) != n1) g.log1 = -1;
   g.log2 = 0;
   while ((1 << g.log2) < n2) ++g.log2;
+  if ((1 << g.log2) != n2) g.log2 = -1;
   g.N = (long long)n1 * n2;
   g.nk1 = n1 / 2 + 1;
   g.spec = (long long)g.nk1 * n2;

@@ -37,32 +37,36 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-// Lines per block and threads per block of the FFT kernels, by log2 of the
-// line length: P lines of N complex values = 1024 complex values (8 KB of
-// shared memory) per block, so that even the 512^2 grid gives a few hundred
-// blocks per pass; one radix-4 butterfly per thread and pass up to N = 1024.
-template <int LOGN>
+// Line lengths N = 2^L * 3^T (T = 0 or 1). Lines per block and threads per
+// block of the FFT kernels: P lines of N complex values, P a power of two
+// with P N <= 2048 (at most 16 KB of shared memory per block) and P = 1
+// from N = 1024 on, so that a 512^2 grid still gives a few hundred blocks per
+// pass and 1024^2 gives over 500 (fewer, larger blocks measured slower).
+template <int L, int T>
 struct FftCfg {
-  static constexpr int N = 1 << LOGN;
-  static constexpr int P = (1024 / N) < 16 ? ((1024 / N) < 1 ? 1 : 1024 / N) : 16;
+  static constexpr int N = (1 << L) * (T ? 3 : 1);
+  static constexpr int P = N >= 1024 ? 1 : (N >= 512 ? 2 : (N >= 256 ? 4 : (N >= 128 ? 8 : 16)));
   static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
 };
 
-// In-place FFT of P lines of length N stored contiguously at s (line l at
-// s + l*N). All NT threads of the block take part; the caller synchronises
-// before (data written) and the routine ends with a barrier.
-template <int LOGN, int P, int NT, bool INV>
+// In-place FFT of P lines of length N = 2^L 3^T stored contiguously at s
+// (line l at s + l*N): radix-4 Stockham passes, then a radix-2 pass if L is
+// odd, then a radix-3 pass if T = 1, each pass reading its inputs into
+// registers, synchronising and writing its outputs. All NT threads of the
+// block take part; the caller synchronises before (data written) and the
+// routine ends with a barrier. tw holds exp(-2 pi i m / N), m < N.
+template <int L, int T, int P, int NT, bool INV>
 __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN;
+  constexpr int N = (1 << L) * (T ? 3 : 1);
   constexpr int Q4 = N / 4;
   constexpr int TOT4 = P * Q4;
   constexpr int B4 = (TOT4 + NT - 1) / NT;
   const int t = threadIdx.x;
   int lns = 0;  // log2 of the current sub-transform size Ns
 #pragma unroll 1
-  for (int pass = 0; pass < LOGN / 2; ++pass) {
+  for (int pass = 0; pass < L / 2; ++pass) {
     const int Ns = 1 << lns;
-    const int tws = LOGN - lns - 2;  // twiddle stride log2: N / (4 Ns)
+    const int tws = N >> (lns + 2);  // twiddle stride N / (4 Ns)
     float2 v[B4][4];
     int base[B4];
 #pragma unroll
@@ -74,9 +78,9 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
         const float2* x = s + l * N;
         float2 a0 = x[j], a1 = x[j + Q4], a2 = x[j + 2 * Q4], a3 = x[j + 3 * Q4];
         if (lns > 0) {
-          const float2 w1 = __ldg(tw + ((k << tws) & (N - 1)));
-          const float2 w2 = __ldg(tw + (((2 * k) << tws) & (N - 1)));
-          const float2 w3 = __ldg(tw + (((3 * k) << tws) & (N - 1)));
+          const float2 w1 = __ldg(tw + k * tws);
+          const float2 w2 = __ldg(tw + 2 * k * tws);
+          const float2 w3 = __ldg(tw + 3 * k * tws);
           if (INV) {
             a1 = cmulc(a1, w1); a2 = cmulc(a2, w2); a3 = cmulc(a3, w3);
           } else {
@@ -106,11 +110,12 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
     __syncthreads();
     lns += 2;
   }
-  if (LOGN & 1) {
+  if (L & 1) {
     constexpr int Q2 = N / 2;
     constexpr int TOT2 = P * Q2;
     constexpr int B2 = (TOT2 + NT - 1) / NT;
     const int Ns = 1 << lns;
+    const int tws = N >> (lns + 1);  // N / (2 Ns)
     float2 v0[B2], v1[B2];
     int base[B2];
 #pragma unroll
@@ -123,7 +128,7 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
         const float2 a0 = x[j];
         float2 a1 = x[j + Q2];
         if (lns > 0) {
-          const float2 w = __ldg(tw + k);  // N / (2 Ns) = 1 on the last pass
+          const float2 w = __ldg(tw + k * tws);
           a1 = INV ? cmulc(a1, w) : cmul(a1, w);
         }
         v0[b] = cadd(a0, a1);
@@ -141,33 +146,89 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       }
     }
     __syncthreads();
+    lns += 1;
+  }
+  if (T) {
+    // radix 3 with Ns = 2^L = N / 3: k = j, output at k + s Ns
+    constexpr int Q3 = N / 3;
+    constexpr int TOT3 = P * Q3;
+    constexpr int B3 = (TOT3 + NT - 1) / NT;
+    constexpr float kS3 = 0.86602540378443865f;   // sqrt(3) / 2
+    float2 v0[B3], v1[B3], v2[B3];
+    int base[B3];
+#pragma unroll
+    for (int b = 0; b < B3; ++b) {
+      const int q = t + b * NT;
+      if (TOT3 % NT == 0 || q < TOT3) {
+        const int l = q / Q3, k = q % Q3;
+        const float2* x = s + l * N;
+        const float2 a0 = x[k];
+        float2 a1 = x[k + Q3], a2 = x[k + 2 * Q3];
+        if (L > 0) {
+          const float2 w1 = __ldg(tw + k), w2 = __ldg(tw + 2 * k);
+          a1 = INV ? cmulc(a1, w1) : cmul(a1, w1);
+          a2 = INV ? cmulc(a2, w2) : cmul(a2, w2);
+        }
+        const float2 t1 = cadd(a1, a2), t2 = csub(a1, a2);
+        const float2 m = make_float2(a0.x - 0.5f * t1.x, a0.y - 0.5f * t1.y);
+        // forward: b1 = m - i (sqrt3/2) t2, b2 = m + i (sqrt3/2) t2
+        const float2 it2 = INV ? make_float2(-kS3 * t2.y, kS3 * t2.x)
+                               : make_float2(kS3 * t2.y, -kS3 * t2.x);
+        v0[b] = cadd(a0, t1);
+        v1[b] = cadd(m, it2);
+        v2[b] = csub(m, it2);
+        base[b] = l * N + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B3; ++b) {
+      const int q = t + b * NT;
+      if (TOT3 % NT == 0 || q < TOT3) {
+        s[base[b]] = v0[b];
+        s[base[b] + Q3] = v1[b];
+        s[base[b] + 2 * Q3] = v2[b];
+      }
+    }
+    __syncthreads();
   }
 }
 
 // ---------------------------------------------------------------------------
 // 1. forward row transforms: F fields of n2 rows of length N = n1.
-template <int LOGN>
-__global__ void __launch_bounds__(FftCfg<LOGN>::NT)
+template <int L, int T>
+__global__ void __launch_bounds__(FftCfg<L, T>::NT)
 k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__ spec,
            long long sstride, int n2, const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, P = FftCfg<LOGN>::P, NT = FftCfg<LOGN>::NT;
+  constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * 2 * P;
   const float* src = in + (long long)blockIdx.y * fstride;
-  for (int q = t; q < P * N; q += NT) {
-    const int l = q >> LOGN, i = q & (N - 1);
-    const long long r = (long long)(row0 + 2 * l) * N + i;
-    sm[q] = make_float2(__ldg(src + r), __ldg(src + r + N));
+  constexpr int LD = (P * N + NT - 1) / NT;   // loads issued before the stores
+  float2 v[LD];
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) {
+      const int l = q / N, i = q % N;
+      const long long r = (long long)(row0 + 2 * l) * N + i;
+      v[u] = make_float2(__ldg(src + r), __ldg(src + r + N));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) sm[q] = v[u];
   }
   __syncthreads();
-  fft_smem<LOGN, P, NT, false>(sm, tw);
+  fft_smem<L, T, P, NT, false>(sm, tw);
   float2* dst = spec + (long long)blockIdx.y * sstride;
   constexpr int R = 2 * P;
   for (int q = t; q < (N / 2 + 1) * R; q += NT) {
     const int r = q % R, k = q / R, l = r >> 1;
     const float2 Z = sm[l * N + k];
-    const float2 Zm = sm[l * N + ((N - k) & (N - 1))];
+    const float2 Zm = sm[l * N + (k == 0 ? 0 : N - k)];
     float2 X;
     if (r & 1) {  // X_b = (Z - conj(Zm)) / (2i)
       X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
@@ -179,33 +240,48 @@ k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__
 }
 
 // 3. inverse row transforms (half spectrum -> real rows), optional addend.
-template <int LOGN>
-__global__ void __launch_bounds__(FftCfg<LOGN>::NT)
+template <int L, int T>
+__global__ void __launch_bounds__(FftCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
            const float2* __restrict__ tw) {
-  constexpr int N = 1 << LOGN, P = FftCfg<LOGN>::P, NT = FftCfg<LOGN>::NT;
+  constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * 2 * P;
   const float2* src = spec + (long long)blockIdx.y * sstride;
-  for (int q = t; q < (N / 2 + 1) * P; q += NT) {
-    const int l = q % P, k = q / P;
-    const long long a = (long long)k * n2 + row0 + 2 * l;
-    float2 Xa = src[a], Xb = src[a + 1];
-    if (k == 0 || k == N / 2) {
-      Xa.y = 0.f;
-      Xb.y = 0.f;
+  constexpr int TOT = (N / 2 + 1) * P;
+  constexpr int LD = (TOT + NT - 1) / NT;     // loads issued before the stores
+  float4 v[LD];
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if (q < TOT) {
+      const int l = q % P, k = q / P;
+      const long long a = (long long)k * n2 + row0 + 2 * l;
+      v[u] = __ldg(reinterpret_cast<const float4*>(src + a));   // X_a, X_b adjacent
     }
-    sm[l * N + k] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
-    if (k > 0 && k < N / 2) sm[l * N + N - k] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
+  }
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if (q < TOT) {
+      const int l = q % P, k = q / P;
+      float2 Xa = make_float2(v[u].x, v[u].y), Xb = make_float2(v[u].z, v[u].w);
+      if (k == 0 || k == N / 2) {
+        Xa.y = 0.f;
+        Xb.y = 0.f;
+      }
+      sm[l * N + k] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
+      if (k > 0 && k < N / 2) sm[l * N + N - k] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
+    }
   }
   __syncthreads();
-  fft_smem<LOGN, P, NT, true>(sm, tw);
+  fft_smem<L, T, P, NT, true>(sm, tw);
   float* dst = out + (long long)blockIdx.y * fstride;
   const float* ad = add ? add + (long long)blockIdx.y * astride : nullptr;
   for (int q = t; q < P * N; q += NT) {
-    const int l = q >> LOGN, i = q & (N - 1);
+    const int l = q / N, i = q % N;
     const long long r = (long long)(row0 + 2 * l) * N + i;
     float a = sm[q].x, b = sm[q].y;
     if (ad) {
@@ -260,19 +336,20 @@ __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1,
   }
 }
 
-template <int LOGI, int LOGO>
+// Column pass between input lines of 2^LI 3^T and output lines of 2^LO 3^T.
+template <int LI, int LO, int T>
 struct ColCfg {
-  static constexpr int LM = LOGI > LOGO ? LOGI : LOGO;
-  static constexpr int NM = 1 << LM;
-  static constexpr int P = FftCfg<LM>::P;
-  static constexpr int NT = FftCfg<LM>::NT;
+  static constexpr int LM = LI > LO ? LI : LO;
+  static constexpr int NM = FftCfg<LM, T>::N;
+  static constexpr int P = FftCfg<LM, T>::P;
+  static constexpr int NT = FftCfg<LM, T>::NT;
 };
 
-template <int LOGI, int LOGO>
-__global__ void __launch_bounds__(ColCfg<LOGI, LOGO>::NT) k_cols(ColArgs a) {
-  constexpr int NI = 1 << LOGI, NO = 1 << LOGO;
-  constexpr int NM = ColCfg<LOGI, LOGO>::NM;
-  constexpr int P = ColCfg<LOGI, LOGO>::P, NT = ColCfg<LOGI, LOGO>::NT;
+template <int LI, int LO, int T>
+__global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT) k_cols(ColArgs a) {
+  constexpr int NI = FftCfg<LI, T>::N, NO = FftCfg<LO, T>::N;
+  constexpr int NM = ColCfg<LI, LO, T>::NM;
+  constexpr int P = ColCfg<LI, LO, T>::P, NT = ColCfg<LI, LO, T>::NT;
   extern __shared__ float2 sm[];
   float2* bin = sm;                      // nin buffers of P x NM
   float2* bout = sm + a.nin * P * NM;    // 1 buffer of P x NM
@@ -281,20 +358,32 @@ __global__ void __launch_bounds__(ColCfg<LOGI, LOGO>::NT) k_cols(ColArgs a) {
   const int g = blockIdx.y;
   const int nsmall = a.n1_in < a.n1_out ? a.n1_in : a.n1_out;
   const bool resize = (NI != NO) || (a.n1_in != a.n1_out);
+  constexpr int LD = (P * NI + NT - 1) / NT;   // loads issued before the stores
   for (int c = 0; c < a.nin; ++c) {
     const float2* src = a.in + (long long)(g * a.nin + c) * a.in_fstride;
-    for (int q = t; q < P * NI; q += NT) {
-      const int l = q >> LOGI, k2 = q & (NI - 1);
-      const int k1 = line0 + l;
-      const bool ok = k1 < a.nk1_out && (!resize || k1 < nsmall / 2);
-      bin[c * P * NM + l * NI + k2] = ok ? src[(long long)k1 * NI + k2] : make_float2(0.f, 0.f);
+    float2 v[LD];
+#pragma unroll
+    for (int u = 0; u < LD; ++u) {
+      const int q = t + u * NT;
+      v[u] = make_float2(0.f, 0.f);
+      if (q < P * NI) {
+        const int l = q / NI, k2 = q % NI;
+        const int k1 = line0 + l;
+        const bool ok = k1 < a.nk1_out && (!resize || k1 < nsmall / 2);
+        if (ok) v[u] = __ldg(src + (long long)k1 * NI + k2);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LD; ++u) {
+      const int q = t + u * NT;
+      if (q < P * NI) bin[c * P * NM + q] = v[u];
     }
   }
   __syncthreads();
-  for (int c = 0; c < a.nin; ++c) fft_smem<LOGI, P, NT, false>(bin + c * P * NM, a.tw_in);
+  for (int c = 0; c < a.nin; ++c) fft_smem<LI, T, P, NT, false>(bin + c * P * NM, a.tw_in);
   for (int o = 0; o < a.nout; ++o) {
     for (int q = t; q < P * NO; q += NT) {
-      const int l = q >> LOGO, ko = q & (NO - 1);
+      const int l = q / NO, ko = q % NO;
       const int k1 = line0 + l;
       const int k2 = signed_k(ko, NO);
       bool ok = k1 < a.nk1_out && (!resize || k1 < nsmall / 2);
@@ -317,10 +406,10 @@ __global__ void __launch_bounds__(ColCfg<LOGI, LOGO>::NT) k_cols(ColArgs a) {
       bout[l * NO + ko] = acc;
     }
     __syncthreads();
-    fft_smem<LOGO, P, NT, true>(bout, a.tw_out);
+    fft_smem<LO, T, P, NT, true>(bout, a.tw_out);
     float2* dst = a.out + (long long)(g * a.nout + o) * a.out_fstride;
     for (int q = t; q < P * NO; q += NT) {
-      const int l = q >> LOGO, k2 = q & (NO - 1);
+      const int l = q / NO, k2 = q % NO;
       const int k1 = line0 + l;
       if (k1 < a.nk1_out) dst[(long long)k1 * NO + k2] = bout[q];
     }
@@ -331,60 +420,66 @@ __global__ void __launch_bounds__(ColCfg<LOGI, LOGO>::NT) k_cols(ColArgs a) {
 // ---------------------------------------------------------------------------
 // host side
 
-static int ilog2(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
+// n = 2^L 3^T -> (L, T); L = -1 if n has another form
+static void split_size(int n, int& L, int& T) {
+  T = (n % 3 == 0) ? 1 : 0;
+  int m = T ? n / 3 : n;
+  L = 0;
+  while ((1 << L) < m) ++L;
+  if ((1 << L) != m) L = -1;
 }
 
-template <typename K>
-static void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int LOGN>
+template <int L, int T>
 static void launch_r2c(const float* in, long long fstride, float2* spec, long long sstride,
                        int n2, int F, const float2* tw, cudaStream_t st) {
-  using C = FftCfg<LOGN>;
+  using C = FftCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
-  static bool init = false;
-  if (!init) { set_smem(k_rows_r2c<LOGN>, smem); init = true; }
+  static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_r2c<LOGN><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw); ++g_launch_count;
+  k_rows_r2c<L, T><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw); ++g_launch_count;
 }
 
-template <int LOGN>
+template <int L, int T>
 static void launch_c2r(const float2* spec, long long sstride, float* out, long long fstride,
                        const float* add, long long astride, int n2, int F, const float2* tw,
                        cudaStream_t st) {
-  using C = FftCfg<LOGN>;
+  using C = FftCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
-  static bool init = false;
-  if (!init) { set_smem(k_rows_c2r<LOGN>, smem); init = true; }
+  static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_c2r<LOGN><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw); ++g_launch_count;
+  k_rows_c2r<L, T><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw); ++g_launch_count;
 }
 
-template <int LOGI, int LOGO>
+template <int LI, int LO, int T>
 static void launch_cols(const ColArgs& a, int groups, cudaStream_t st) {
-  using C = ColCfg<LOGI, LOGO>;
+  using C = ColCfg<LI, LO, T>;
   const size_t smem = (size_t)(a.nin + 1) * C::P * C::NM * sizeof(float2);
-  static bool init = false;
-  if (!init) { set_smem(k_cols<LOGI, LOGO>, 3 * (size_t)C::P * C::NM * sizeof(float2)); init = true; }
+  static_assert(3 * C::P * C::NM * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid((a.nk1_out + C::P - 1) / C::P, groups);
-  k_cols<LOGI, LOGO><<<grid, C::NT, smem, st>>>(a); ++g_launch_count;
+  k_cols<LI, LO, T><<<grid, C::NT, smem, st>>>(a); ++g_launch_count;
 }
 
-#define REGNK_LOG_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10) X(11)
-#define REGNK_RESTRICT_CASES(X) X(6) X(7) X(8) X(9) X(10) X(11)
-#define REGNK_PROLONG_CASES(X) X(5) X(6) X(7) X(8) X(9) X(10)
+// supported line lengths: 2^L for L = 5..11, 3 * 2^L for L = 5..9 (96 .. 1536)
+#define REGNK_SIZE_CASES(X) \
+  X(5, 0) X(6, 0) X(7, 0) X(8, 0) X(9, 0) X(10, 0) X(11, 0) X(5, 1) X(6, 1) X(7, 1) X(8, 1) X(9, 1)
+#define REGNK_RESTRICT_CASES(X) \
+  X(6, 0) X(7, 0) X(8, 0) X(9, 0) X(10, 0) X(11, 0) X(6, 1) X(7, 1) X(8, 1) X(9, 1)
+#define REGNK_PROLONG_CASES(X) \
+  X(5, 0) X(6, 0) X(7, 0) X(8, 0) X(9, 0) X(10, 0) X(5, 1) X(6, 1) X(7, 1) X(8, 1)
+
+bool fft_size_supported(int n) {
+  int L, T;
+  split_size(n, L, T);
+  return L >= 5 && ((T == 0 && L <= 11) || (T == 1 && L <= 9));
+}
 
 void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
                   long long sstride, int F, const float2* tw, cudaStream_t st) {
-  switch (ilog2(n1)) {
-#define CASE(L) case L: launch_r2c<L>(in, fstride, spec, sstride, n2, F, tw, st); break;
-    REGNK_LOG_CASES(CASE)
+  int L, T;
+  split_size(n1, L, T);
+  switch (L * 2 + T) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_r2c<LL, TT>(in, fstride, spec, sstride, n2, F, tw, st); break;
+    REGNK_SIZE_CASES(CASE)
 #undef CASE
     default: break;
   }
@@ -393,33 +488,38 @@ void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* sp
 void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
                   long long fstride, const float* add, long long astride, int F,
                   const float2* tw, cudaStream_t st) {
-  switch (ilog2(n1)) {
-#define CASE(L) case L: launch_c2r<L>(spec, sstride, out, fstride, add, astride, n2, F, tw, st); break;
-    REGNK_LOG_CASES(CASE)
+  int L, T;
+  split_size(n1, L, T);
+  switch (L * 2 + T) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_c2r<LL, TT>(spec, sstride, out, fstride, add, astride, n2, F, tw, st); break;
+    REGNK_SIZE_CASES(CASE)
 #undef CASE
     default: break;
   }
 }
 
 void fft_cols(const ColArgs& a, int groups, cudaStream_t st) {
-  const int li = ilog2(a.n2_in), lo = ilog2(a.n2_out);
+  int li, ti, lo, to;
+  split_size(a.n2_in, li, ti);
+  split_size(a.n2_out, lo, to);
+  if (ti != to) return;
   if (li == lo) {
-    switch (li) {
-#define CASE(L) case L: launch_cols<L, L>(a, groups, st); break;
-      REGNK_LOG_CASES(CASE)
+    switch (li * 2 + ti) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_cols<LL, LL, TT>(a, groups, st); break;
+      REGNK_SIZE_CASES(CASE)
 #undef CASE
       default: break;
     }
   } else if (lo == li - 1) {
-    switch (li) {
-#define CASE(L) case L: launch_cols<L, L - 1>(a, groups, st); break;
+    switch (li * 2 + ti) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_cols<LL, LL - 1, TT>(a, groups, st); break;
       REGNK_RESTRICT_CASES(CASE)
 #undef CASE
       default: break;
     }
   } else if (lo == li + 1) {
-    switch (li) {
-#define CASE(L) case L: launch_cols<L, L + 1>(a, groups, st); break;
+    switch (li * 2 + ti) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_cols<LL, LL + 1, TT>(a, groups, st); break;
       REGNK_PROLONG_CASES(CASE)
 #undef CASE
       default: break;

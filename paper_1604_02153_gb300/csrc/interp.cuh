@@ -6,7 +6,37 @@
 
 #include <cuda_runtime.h>
 
+#include "common.cuh"
+
 namespace regnk {
+
+// Grid index helpers. P2 = true when both grid lengths are powers of two:
+// indices split and wrap with shifts and masks (log1 = log2(n1)); otherwise
+// (lengths 3 * 2^k) with integer division and remainder. The kernels are
+// compiled for both, so the power-of-two grids pay nothing for the others.
+template <bool P2>
+__device__ __forceinline__ void split_index(long long idx, int n1, int log1, int& i, int& j) {
+  if (P2) {
+    i = (int)(idx & (n1 - 1));
+    j = (int)(idx >> log1);
+  } else {
+    j = (int)(idx / n1);
+    i = (int)(idx - (long long)j * n1);
+  }
+}
+
+template <bool P2>
+__device__ __forceinline__ long long row_offset(int j, int n1, int log1) {
+  return P2 ? ((long long)j << log1) : (long long)j * n1;
+}
+
+// periodic wrap of any index into [0, n)
+template <bool P2>
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  if (P2) return i & (n - 1);
+  const int r = i % n;
+  return r < 0 ? r + n : r;
+}
 
 // ---------------------------------------------------------------------------
 // Periodic cubic B-spline prefilter.
@@ -50,19 +80,37 @@ __device__ __forceinline__ void bspline_recursions(float (&v)[NS], Out out) {
 // Prefilters the 32x32 output tile at (x0, y0) of one field (all kPThreads
 // threads of the block take part; `sin_` and `smid` are the block's staging
 // buffers of kPH*kPIn and kPH*kPMid floats). COHERENT = true reads the source
-// through L2 only (for data written earlier in the same kernel by other
-// blocks). The caller synchronises before reusing the buffers.
-template <bool COHERENT = false>
+// with ordinary (L1-cached, non read-only-path) loads, for data written
+// earlier in the same kernel by other blocks: the grid barrier's fences make
+// such loads observe those writes, which the read-only path does not
+// promise. The caller synchronises before reusing the buffers.
+template <bool P2, bool COHERENT = false>
 __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, float* __restrict__ dst,
                                                int n1, int n2, int log1, int x0, int y0,
                                                float* sin_, float* smid) {
   const int t = threadIdx.x;
-  for (int q = t; q < kPH * kPW; q += kPThreads) {
-    const int r = q / kPW, c = q - r * kPW;
-    const int gx = (x0 - kL + c) & (n1 - 1);
-    const int gy = (y0 - kL + r) & (n2 - 1);
-    const float* a = src + ((long long)gy << log1) + gx;
-    sin_[r * kPIn + c] = COHERENT ? __ldcg(a) : __ldg(a);
+  // all loads of the staged tile are issued before any shared-memory store,
+  // so their latencies overlap
+  constexpr int kLoads = (kPH * kPW + kPThreads - 1) / kPThreads;
+  float ld_[kLoads];
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * kPThreads;
+    if (q < kPH * kPW) {
+      const int r = q / kPW, c = q - r * kPW;
+      const int gx = P2 ? wrap_index<true>(x0 - kL + c, n1) : wrap_once(x0 - kL + c, n1);
+      const int gy = P2 ? wrap_index<true>(y0 - kL + r, n2) : wrap_once(y0 - kL + r, n2);
+      const float* a = src + row_offset<P2>(gy, n1, log1) + gx;
+      ld_[u] = COHERENT ? __ldca(a) : __ldg(a);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * kPThreads;
+    if (q < kPH * kPW) {
+      const int r = q / kPW, c = q - r * kPW;
+      sin_[r * kPIn + c] = ld_[u];
+    }
   }
   __syncthreads();
   constexpr int kSeg = 8, kSegs = kPX / kSeg, kLen = kSeg + 2 * kL;   // 34 samples per chain
@@ -83,7 +131,7 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
     float* col = dst + x0 + c;
     const int yb = y0 + sg * kSeg;
     bspline_recursions<kLen, kSeg>(v, [&](int o, float x) {
-      col[(long long)(yb + o) << log1] = x;
+      col[row_offset<P2>(yb + o, n1, log1)] = x;
     });
   }
 }
@@ -112,23 +160,26 @@ __device__ __forceinline__ void cubic_weights(float t, float (&w)[4], bool lagra
   }
 }
 
+template <bool P2>
 __device__ __forceinline__ Stencil make_stencil(int i, int j, float d1, float d2, int n1,
                                                 int n2, int log1, bool lagrange) {
   Stencil S;
   const float f1 = floorf(d1), f2 = floorf(d2);
   cubic_weights(d1 - f1, S.w1, lagrange);
   cubic_weights(d2 - f2, S.w2, lagrange);
-  const int i0 = i + (int)f1 - 1, j0 = j + (int)f2 - 1;
+  const int i0 = wrap_index<P2>(i + (int)f1 - 1, n1), j0 = wrap_index<P2>(j + (int)f2 - 1, n2);
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    S.ii[a] = (i0 + a) & (n1 - 1);
-    S.jj[a] = ((j0 + a) & (n2 - 1)) << log1;
+    const int ii = i0 + a, jj = j0 + a;
+    S.ii[a] = ii < n1 ? ii : ii - n1;
+    S.jj[a] = (int)row_offset<P2>(jj < n2 ? jj : jj - n2, n1, log1);
   }
   return S;
 }
 
+// COHERENT: ordinary cached load (see prefilter_tile); otherwise read-only path
 template <bool COHERENT = false>
-__device__ __forceinline__ float ld(const float* p) { return COHERENT ? __ldcg(p) : __ldg(p); }
+__device__ __forceinline__ float ld(const float* p) { return COHERENT ? __ldca(p) : __ldg(p); }
 
 template <bool COHERENT = false>
 __device__ __forceinline__ float apply_stencil(const Stencil& S, const float* __restrict__ c) {

@@ -3,13 +3,15 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "interp.cuh"
 
 namespace regnk {
 
 // Kernel launches issued by the library since load (incremented after every
-// launch; read by reg_launch_count).
-extern long long g_launch_count;
+// launch, from any host thread; read by reg_launch_count).
+extern std::atomic<long long> g_launch_count;
 
 // Spectral multipliers of the column pass (see fft.cu).
 enum SpecOp {
@@ -47,6 +49,8 @@ void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* 
                   long long fstride, const float* add, long long astride, int F,
                   const float2* tw, cudaStream_t st);
 void fft_cols(const ColArgs& a, int groups, cudaStream_t st);
+// n = 2^L (L = 5..11) or 3 * 2^L (L = 5..9)
+bool fft_size_supported(int n);
 
 // transport.cu
 struct PrefilterTaps;  // host-computed, passed by value below

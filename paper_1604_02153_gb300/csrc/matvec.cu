@@ -13,7 +13,9 @@
 //     prefilter v~ | v~(X_D), m~_1 | (prefilter m~_{j-1} | m~_j) j = 2..nt |
 //     (prefilter lambda~_{j+1} | lambda~_j, b~ += ...) j = nt-1..0
 // (prefilter phases are absent for the Lagrange model). Data produced inside
-// the kernel is read through L2 (__ldcg) since L1 is not coherent across SMs.
+// the kernel is read with ordinary loads, never through the read-only path:
+// the barrier's release/acquire fences make them observe the other blocks'
+// writes while still letting neighbouring stencils share L1 lines.
 //
 // The barrier is a counter plus a generation word in global memory. A block
 // that waits longer than ~0.5 s (bounded spin with __nanosleep) sets the
@@ -57,7 +59,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err, unsigned m
   return *(volatile int*)err == 0;
 }
 
-template <bool LAGRANGE>
+template <bool LAGRANGE, bool P2>
 __device__ __forceinline__ void prefilter_phase(const MatvecArgs& a, const float* src, float* dst,
                                                 int F, float* sin_, float* smid) {
   if (LAGRANGE) return;
@@ -65,12 +67,12 @@ __device__ __forceinline__ void prefilter_phase(const MatvecArgs& a, const float
   for (int w = blockIdx.x; w < F * tiles; w += gridDim.x) {
     const int f = w / tiles, tile = w - f * tiles;
     const int x0 = (tile % tx) * kPX, y0 = (tile / tx) * kPY;
-    prefilter_tile<true>(src + f * a.N, dst + f * a.N, a.n1, a.n2, a.log1, x0, y0, sin_, smid);
+    prefilter_tile<P2, true>(src + f * a.N, dst + f * a.N, a.n1, a.n2, a.log1, x0, y0, sin_, smid);
     __syncthreads();
   }
 }
 
-template <bool LAGRANGE>
+template <bool LAGRANGE, bool P2>
 __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   __shared__ float sin_[kPH * kPIn];
   __shared__ float smid[kPH * kPMid];
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   // phase: interpolation coefficients of v~
   const float* cvt = a.vt;
   if (!LAGRANGE) {
-    prefilter_phase<LAGRANGE>(a, a.vt, a.c2, 2, sin_, smid);
+    prefilter_phase<LAGRANGE, P2>(a, a.vt, a.c2, 2, sin_, smid);
     cvt = a.c2;
     if (!grid_barrier(a.bar, a.err, a.missing)) return;
   }
@@ -92,8 +94,9 @@ __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   float* nxt = a.fB;
   const float* gm_nt = a.gm + 2 * (long long)nt * N;
   for (long long idx = first; idx < N; idx += stride) {
-    const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-    const Stencil S = make_stencil(i, j, __ldg(a.dX + idx), __ldg(a.dX + N + idx), n1, n2, log1,
+    int i, j;
+    split_index<P2>(idx, n1, log1, i, j);
+    const Stencil S = make_stencil<P2>(i, j, __ldg(a.dX + idx), __ldg(a.dX + N + idx), n1, n2, log1,
                                    LAGRANGE);
     const float w1 = apply_stencil<true>(S, cvt), w2 = apply_stencil<true>(S, cvt + N);
     a.vtD[idx] = w1;
@@ -116,18 +119,19 @@ __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   for (int jt = 2; jt <= nt; ++jt) {
     const float* coef = cur;
     if (!LAGRANGE) {
-      prefilter_phase<LAGRANGE>(a, cur, a.coef, 1, sin_, smid);
+      prefilter_phase<LAGRANGE, P2>(a, cur, a.coef, 1, sin_, smid);
       coef = a.coef;
       if (!grid_barrier(a.bar, a.err, a.missing)) return;
     }
     const float* Gj = a.G + 2 * (long long)(jt - 1) * N;
     const float* gj = a.gm + 2 * (long long)jt * N;
     for (long long idx = first; idx < N; idx += stride) {
-      const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-      const Stencil S = make_stencil(i, j, __ldg(a.dX + idx), __ldg(a.dX + N + idx), n1, n2,
+      int i, j;
+      split_index<P2>(idx, n1, log1, i, j);
+      const Stencil S = make_stencil<P2>(i, j, __ldg(a.dX + idx), __ldg(a.dX + N + idx), n1, n2,
                                      log1, LAGRANGE);
       const float base = apply_stencil<true>(S, coef);
-      const float src = __ldcg(a.vtD + idx) * __ldg(Gj + idx) + __ldcg(a.vtD + N + idx) * __ldg(Gj + N + idx) +
+      const float src = __ldca(a.vtD + idx) * __ldg(Gj + idx) + __ldca(a.vtD + N + idx) * __ldg(Gj + N + idx) +
                         __ldg(a.vt + idx) * __ldg(gj + idx) + __ldg(a.vt + N + idx) * __ldg(gj + N + idx);
       const float m = base - hh * src;
       if (jt == nt) {   // lambda~_nt = -m~_nt (eq. inc-adj-fc-elim) and b~ init
@@ -147,23 +151,24 @@ __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   for (int jt = nt - 1; jt >= 0; --jt) {
     const float* coef = cur;
     if (!LAGRANGE) {
-      prefilter_phase<LAGRANGE>(a, cur, a.coef, 1, sin_, smid);
+      prefilter_phase<LAGRANGE, P2>(a, cur, a.coef, 1, sin_, smid);
       coef = a.coef;
       if (!grid_barrier(a.bar, a.err, a.missing)) return;
     }
     const float wb = ht * (jt == 0 ? 0.5f : 1.0f);
     const float* gj = a.gm + 2 * (long long)jt * N;
     for (long long idx = first; idx < N; idx += stride) {
-      const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-      const Stencil S = make_stencil(i, j, __ldg(a.dY + idx), __ldg(a.dY + N + idx), n1, n2,
+      int i, j;
+      split_index<P2>(idx, n1, log1, i, j);
+      const Stencil S = make_stencil<P2>(i, j, __ldg(a.dY + idx), __ldg(a.dY + N + idx), n1, n2,
                                      log1, LAGRANGE);
       const float lb = apply_stencil<true>(S, coef);
       const float db = __ldg(a.delta_bar + idx), d = __ldg(a.delta + idx);
       const float lstar = fmaf(ht * lb, db, lb);
       const float l = lb + 0.5f * ht * (lb * db + lstar * d);
       nxt[idx] = l;
-      a.b[idx] = fmaf(wb * l, __ldg(gj + idx), __ldcg(a.b + idx));
-      a.b[N + idx] = fmaf(wb * l, __ldg(gj + N + idx), __ldcg(a.b + N + idx));
+      a.b[idx] = fmaf(wb * l, __ldg(gj + idx), __ldca(a.b + idx));
+      a.b[N + idx] = fmaf(wb * l, __ldg(gj + N + idx), __ldca(a.b + N + idx));
     }
     float* t = cur;
     cur = nxt;
@@ -172,28 +177,38 @@ __global__ void __launch_bounds__(kMT) k_gn_matvec(MatvecArgs a) {
   }
 }
 
-static int g_matvec_blocks[2][64] = {};
+static bool pow2_args(const MatvecArgs& a) {
+  return !(a.n1 & (a.n1 - 1)) && !(a.n2 & (a.n2 - 1));
+}
 
-int matvec_grid(int lagrange) {
+// the four instantiations, indexed by 2 * lagrange + pow2
+using MatvecKernel = void (*)(MatvecArgs);
+static const MatvecKernel kMatvecKernels[4] = {k_gn_matvec<false, false>, k_gn_matvec<false, true>,
+                                               k_gn_matvec<true, false>, k_gn_matvec<true, true>};
+
+static std::atomic<int> g_matvec_blocks[4][64];
+
+// resident blocks of a cooperative launch of variant k on the current device
+static int matvec_grid(int k) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return 0;
-  int& nb = g_matvec_blocks[lagrange ? 1 : 0][dev];
+  std::atomic<int>& slot = g_matvec_blocks[k][dev];
+  int nb = slot.load();
   if (nb == 0) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (lagrange)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gn_matvec<true>, kMT, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_gn_matvec<false>, kMT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kMatvecKernels[k], kMT, 0);
     per = per > 2 ? 2 : per;   // two blocks per SM: enough threads, few barrier arrivals
     nb = sms * per;
+    slot.store(nb);
   }
   return nb;
 }
 
 cudaError_t launch_gn_matvec(const MatvecArgs& a, cudaStream_t st) {
-  const int nb = matvec_grid(a.lagrange);
+  const int k = 2 * (a.lagrange ? 1 : 0) + (pow2_args(a) ? 1 : 0);
+  const int nb = matvec_grid(k);
   if (nb <= 0) return cudaErrorInvalidConfiguration;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(nb);
@@ -205,8 +220,7 @@ cudaError_t launch_gn_matvec(const MatvecArgs& a, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = a.lagrange ? cudaLaunchKernelEx(&cfg, k_gn_matvec<true>, a)
-                             : cudaLaunchKernelEx(&cfg, k_gn_matvec<false>, a);
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kMatvecKernels[k], a);
   ++g_launch_count;
   return e;
 }

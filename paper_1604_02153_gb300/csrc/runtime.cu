@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstring>
 #include <functional>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -19,7 +20,7 @@
 using namespace regnk;
 
 namespace regnk {
-long long g_launch_count = 0;
+std::atomic<long long> g_launch_count{0};
 }
 
 namespace {
@@ -79,7 +80,7 @@ struct reg_ctx {
   bool two_level = false;
   Level fine, coarse;
   std::vector<void*> allocs;
-  std::vector<float2*> tw;        // twiddles by log2 length
+  std::vector<std::pair<int, float2*>> tw;   // twiddle tables by length
   double* dsc = nullptr;          // device FP64 scalars
   double* hsc = nullptr;          // pinned host mirror
   double* partial = nullptr;      // reduction partials
@@ -102,11 +103,13 @@ struct reg_ctx {
   // per-kernel-class device time (diagnostics, reg_profile_*)
   bool prof = false;
   std::vector<cudaEvent_t> evpool;
-  struct Rec { int cls; cudaEvent_t a, b; double bytes; };
+  struct Rec { int cls; int level; cudaEvent_t a, b; double bytes; };
   std::vector<Rec> recs;
-  double prof_ms[REG_KC_COUNT] = {};
-  double prof_bytes[REG_KC_COUNT] = {};
-  long long prof_n[REG_KC_COUNT] = {};
+  // [level][class]: level 0 = the problem grid, 1 = the coarse grid of P_2L
+  double prof_ms[2][REG_KC_COUNT] = {};
+  double prof_bytes[2][REG_KC_COUNT] = {};
+  long long prof_n[2][REG_KC_COUNT] = {};
+  int cur_level = 0;
   // CUDA graphs of fixed launch sequences (fine matvec, P_2L with CHEB)
   cudaStream_t cap = nullptr;
   bool graphs = true;
@@ -166,9 +169,9 @@ void harvest(reg_ctx* c) {
   for (auto& r : c->recs) {
     float ms = 0.f;
     check(c, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
-    c->prof_ms[r.cls] += ms;
-    c->prof_bytes[r.cls] += r.bytes;
-    c->prof_n[r.cls] += 1;
+    c->prof_ms[r.level][r.cls] += ms;
+    c->prof_bytes[r.level][r.cls] += r.bytes;
+    c->prof_n[r.level][r.cls] += 1;
     c->evpool.push_back(r.a);
     c->evpool.push_back(r.b);
   }
@@ -183,6 +186,7 @@ class Prof {
     if (!c->prof) return;
     if (c->recs.size() >= 8192 && !c->capturing) harvest(c);
     r_.cls = cls;
+    r_.level = c->cur_level;
     r_.bytes = bytes;
     r_.a = take_event(c);
     r_.b = take_event(c);
@@ -221,20 +225,17 @@ T* dalloc(reg_ctx* c, size_t count) {
 }
 
 float2* twiddles(reg_ctx* c, int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  if ((int)c->tw.size() <= l) c->tw.resize(l + 1, nullptr);
-  if (!c->tw[l]) {
-    std::vector<float2> h(n);
-    for (int m = 0; m < n; ++m) {
-      const double a = -2.0 * M_PI * (double)m / (double)n;
-      h[m] = make_float2((float)std::cos(a), (float)std::sin(a));
-    }
-    float2* d = dalloc<float2>(c, n);
-    check(c, cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "twiddle upload");
-    c->tw[l] = d;
+  for (auto& e : c->tw)
+    if (e.first == n) return e.second;
+  std::vector<float2> h(n);
+  for (int m = 0; m < n; ++m) {
+    const double a = -2.0 * M_PI * (double)m / (double)n;
+    h[m] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
-  return c->tw[l];
+  float2* d = dalloc<float2>(c, n);
+  check(c, cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "twiddle upload");
+  c->tw.push_back({n, d});
+  return d;
 }
 
 void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
@@ -271,6 +272,19 @@ void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
 }
 
 bool lagrange(const reg_ctx* c) { return c->opt.interp == REG_INTERP_LAGRANGE; }
+
+// Attributes the launches inside its lifetime to a grid level (profiling).
+class LevelScope {
+ public:
+  LevelScope(reg_ctx* c, const Level& L) : c_(c), prev_(c->cur_level) {
+    c->cur_level = (&L == &c->coarse) ? 1 : 0;
+  }
+  ~LevelScope() { c_->cur_level = prev_; }
+
+ private:
+  reg_ctx* c_;
+  int prev_;
+};
 
 void drop_graphs(reg_ctx* c) {
   for (auto& g : c->graph_cache) {
@@ -365,9 +379,9 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
     for (auto& r : e->prof_recs) {
       float ms = 0.f;
       check(c, cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
-      c->prof_ms[r.cls] += ms;
-      c->prof_bytes[r.cls] += r.bytes;
-      c->prof_n[r.cls] += 1;
+      c->prof_ms[r.level][r.cls] += ms;
+      c->prof_bytes[r.level][r.cls] += r.bytes;
+      c->prof_n[r.level][r.cls] += 1;
     }
   }
   return false;
@@ -399,6 +413,7 @@ ColArgs col_args(const Level& L, int op, double beta, int p, double s) {
 // out (groups*fout fields) = op(in (groups*fin fields)) [+ add], on level L.
 void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, int groups,
               float* out, int fout, const float* add) {
+  LevelScope ls(c, L);
   const GridDims& g = L.g;
   const int per = fin + fout;
   const int chunk = kSpecSlots / per;
@@ -434,6 +449,7 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
 // prolongation) with multiplier op(s), plus an optional addend on B.
 void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in, int F,
               float* out, const float* add) {
+  LevelScope ls(c, A);
   float2* sin = c->fine.spec;
   float2* sout = c->fine.spec + (size_t)F * A.g.spec;
   {
@@ -465,6 +481,7 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
 // interpolation coefficients of F consecutive fields (prefilter for the
 // spline model; the samples themselves for Lagrange)
 const float* coefficients(reg_ctx* c, Level& L, const float* u, int F, float* dst) {
+  LevelScope ls(c, L);
   if (lagrange(c)) return u;
   Prof P(c, REG_KC_PREFILTER, 16.0 * F * L.g.N);
   for (int f = 0; f < F; ++f)
@@ -511,6 +528,7 @@ double dot_sync(reg_ctx* c, const float* a, const float* b, long long n, int s) 
 
 // Caches v, its characteristics and the state history m_0..m_nt (§3.3.2).
 void set_velocity(reg_ctx* c, Level& L, const float* v) {
+  LevelScope ls(c, L);
   const GridDims& g = L.g;
   const size_t N = (size_t)g.N;
   if (v != L.v) check(c, cudaMemcpyAsync(L.v, v, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
@@ -551,6 +569,7 @@ void ensure_grad_history(reg_ctx* c, Level& L) {
 }
 
 void ensure_G(reg_ctx* c, Level& L) {
+  LevelScope ls(c, L);
   if (L.have_G) return;
   ensure_grad_history(c, L);
   const size_t N = (size_t)L.g.N;
@@ -568,6 +587,7 @@ void ensure_G(reg_ctx* c, Level& L) {
 // J = 1/2 <m_1 - m_R, m_1 - m_R>_h + beta/2 <v, A v>_h (eq. varopt:objective);
 // leaves beta A v in L.Av.
 double objective(reg_ctx* c, Level& L) {
+  LevelScope ls(c, L);
   const size_t N = (size_t)L.g.N;
   spectral(c, L, SPOP_REGPOW, 1.0, L.v, 1, 2, L.Av, 1, nullptr);
   {
@@ -587,6 +607,7 @@ double objective(reg_ctx* c, Level& L) {
 // b = int_0^1 lambda grad m dt by the adjoint solve (eq. adj-slm), trapezoid in
 // time; g = beta A v + b. Needs objective() for L.Av.
 void gradient(reg_ctx* c, Level& L, float* g_out) {
+  LevelScope ls(c, L);
   ensure_grad_history(c, L);
   const GridDims& gd = L.g;
   const size_t N = (size_t)gd.N;
@@ -626,6 +647,7 @@ void hessian(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) 
 
 // one cooperative launch for the data term b~ (matvec.cu)
 void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
+  LevelScope ls(c, L);
   MatvecArgs a{};
   a.n1 = L.g.n1;
   a.n2 = L.g.n2;
@@ -661,6 +683,7 @@ void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
 
 // the launch sequence of one GN matvec; needs ensure_G(c, L) beforehand
 void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
+  LevelScope ls(c, L);
   if (c->persistent) {
     const size_t N2 = 2 * (size_t)L.g.N;
     if (data_only) {
@@ -730,6 +753,7 @@ void set_images_level(reg_ctx* c, Level& L) {
 
 // (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse level.
 void coarse_split_op(reg_ctx* c, const float* s, float* out) {
+  LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
   spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
   hessian_core(c, C, c->cu, c->cq, true);
@@ -806,6 +830,7 @@ void estimate_eigenvalues(reg_ctx* c) {
 // (I + (beta A_c)^-1 Q_c) u on the coarse level: the split operator above
 // conjugated by (beta A_c)^1/2, same spectrum, one spectral operation less.
 void coarse_op_u(reg_ctx* c, const float* u, float* out) {
+  LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
   hessian_core(c, C, u, c->cq, true);
   spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u);
@@ -813,6 +838,7 @@ void coarse_op_u(reg_ctx* c, const float* u, float* out) {
 }
 
 void cheb(reg_ctx* c, const float* rhs, float* x) {
+  LevelScope ls(c, c->coarse);
   const long long n = 2 * c->coarse.g.N;
   const double theta = 0.5 * (c->emax + c->emin), delta = 0.5 * (c->emax - c->emin);
   const double sigma = theta / delta;
@@ -921,6 +947,7 @@ void precond(reg_ctx* c, const float* r, float* z) {
   // r' = (beta A)^-1/2 r; restricted low band -> crhs
   resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
   {
+    LevelScope ls(c, C);
     auto A = [&](const float* s, float* o) { coarse_split_op(c, s, o); };
     auto I = [&](const float* s, float* o) {
       check(c, cudaMemcpyAsync(o, s, nc * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
@@ -995,6 +1022,19 @@ void ensure_gref(reg_ctx* c) {
   c->have_gref = true;
 }
 
+// Device buffers are read and written with 8- and 16-byte vector accesses;
+// one that starts off a 16-byte boundary is rejected on the host.
+bool unaligned(std::initializer_list<const void*> ps) {
+  for (const void* p : ps)
+    if (reinterpret_cast<uintptr_t>(p) & 15u) return true;
+  return false;
+}
+
+reg_status reject_unaligned(reg_ctx* c) {
+  c->err = "device buffers must start on a 16-byte boundary";
+  return REG_EINVAL;
+}
+
 reg_status guarded(reg_ctx* c, const std::function<void()>& body) {
   if (!c) return REG_EINVAL;
   try {
@@ -1037,12 +1077,14 @@ reg_status reg_default_options(reg_options* o) {
   return REG_OK;
 }
 
-static bool pow2_in_range(int n) { return n >= 32 && n <= 2048 && (n & (n - 1)) == 0; }
+// grid sizes: 2^k in [32, 2048] or 3 * 2^k in [96, 1536] (the FFT's line
+// lengths; multiples of 32 for the prefilter tiles)
+static bool size_ok(int n) { return n % 32 == 0 && fft_size_supported(n); }
 
 reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt, reg_ctx** out) {
   if (!out) return REG_EINVAL;
   *out = nullptr;
-  if (!pow2_in_range(grid.n1) || !pow2_in_range(grid.n2) || nt < 1 || nt > 4096 || !(beta > 0.0))
+  if (!size_ok(grid.n1) || !size_ok(grid.n2) || nt < 1 || nt > 4096 || !(beta > 0.0))
     return REG_EINVAL;
   reg_options o;
   if (opt) o = *opt; else reg_default_options(&o);
@@ -1050,7 +1092,9 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
       o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0)
     return REG_EINVAL;
-  if (o.precond == REG_PC_2L && (grid.n1 < 64 || grid.n2 < 64)) return REG_EINVAL;
+  if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
+                                 grid.n1 % 2 || grid.n2 % 2))
+    return REG_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
   reg_ctx* c = new reg_ctx();
@@ -1144,6 +1188,7 @@ const char* reg_last_error(const reg_ctx* c) {
 
 reg_status reg_set_images(reg_ctx* c, const float* mR, const float* mT) {
   if (!c || !mR || !mT) return REG_EINVAL;
+  if (unaligned({mR, mT})) return reject_unaligned(c);
   return guarded(c, [&] {
     Level& F = c->fine;
     const size_t N = (size_t)F.g.N;
@@ -1169,6 +1214,7 @@ reg_status reg_set_beta(reg_ctx* c, double beta) {
 
 reg_status reg_transport(reg_ctx* c, const float* v, const float* m0, float* m1) {
   if (!c || !v || !m0 || !m1) return REG_EINVAL;
+  if (unaligned({v, m0, m1})) return reject_unaligned(c);
   return guarded(c, [&] {
     Level& F = c->fine;
     const size_t N = (size_t)F.g.N;
@@ -1185,6 +1231,7 @@ reg_status reg_transport(reg_ctx* c, const float* v, const float* m0, float* m1)
 
 reg_status reg_departure_points(reg_ctx* c, const float* v, float* dX, float* dY) {
   if (!c || !v) return REG_EINVAL;
+  if (unaligned({v, dX, dY})) return reject_unaligned(c);
   return guarded(c, [&] {
     Level& F = c->fine;
     const float* cv = coefficients(c, F, v, 2, F.c2);
@@ -1195,6 +1242,7 @@ reg_status reg_departure_points(reg_ctx* c, const float* v, float* dX, float* dY
 
 reg_status reg_interpolate(reg_ctx* c, const float* u, const float* disp, float* out) {
   if (!c || !u || !disp || !out) return REG_EINVAL;
+  if (unaligned({u, disp, out})) return reject_unaligned(c);
   return guarded(c, [&] {
     Level& F = c->fine;
     const float* cu = coefficients(c, F, u, 1, F.coef);
@@ -1205,6 +1253,7 @@ reg_status reg_interpolate(reg_ctx* c, const float* u, const float* disp, float*
 
 reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* out) {
   if (!c || !in || !out || in == out) return REG_EINVAL;
+  if (unaligned({in, out})) return reject_unaligned(c);
   return guarded(c, [&] {
     Level& F = c->fine;
     switch (op) {
@@ -1228,18 +1277,21 @@ reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* ou
 
 reg_status reg_restrict(reg_ctx* c, const float* fine, float* coarse) {
   if (!c || !fine || !coarse) return REG_EINVAL;
+  if (unaligned({fine, coarse})) return reject_unaligned(c);
   if (!c->two_level) { c->err = "restriction needs the two-level context"; return REG_ESTATE; }
   return guarded(c, [&] { resample(c, c->fine, c->coarse, SPOP_SCALE, 0.0, fine, 2, coarse, nullptr); });
 }
 
 reg_status reg_prolong(reg_ctx* c, const float* coarse, float* fine) {
   if (!c || !fine || !coarse) return REG_EINVAL;
+  if (unaligned({fine, coarse})) return reject_unaligned(c);
   if (!c->two_level) { c->err = "prolongation needs the two-level context"; return REG_ESTATE; }
   return guarded(c, [&] { resample(c, c->coarse, c->fine, SPOP_SCALE, 0.0, coarse, 2, fine, nullptr); });
 }
 
 reg_status reg_objective_gradient(reg_ctx* c, const float* v, double* J, float* g) {
   if (!c || !v || !J) return REG_EINVAL;
+  if (unaligned({v, g})) return reject_unaligned(c);
   return guarded(c, [&] {
     require_images(c);
     *J = objective_gradient(c, v, g);
@@ -1267,6 +1319,7 @@ static void sync_velocity(reg_ctx* c, const float* v) {
 
 reg_status reg_hessian_matvec(reg_ctx* c, const float* v, const float* vt, float* Hvt) {
   if (!c || !v || !vt || !Hvt) return REG_EINVAL;
+  if (unaligned({v, vt, Hvt})) return reject_unaligned(c);
   return guarded(c, [&] {
     require_images(c);
     sync_velocity(c, v);
@@ -1276,6 +1329,7 @@ reg_status reg_hessian_matvec(reg_ctx* c, const float* v, const float* vt, float
 
 reg_status reg_precond_apply(reg_ctx* c, const float* r, float* z) {
   if (!c || !r || !z) return REG_EINVAL;
+  if (unaligned({r, z})) return reject_unaligned(c);
   return guarded(c, [&] {
     require_images(c);
     if (!c->fine.have_v) fail(c, REG_ESTATE, "no cached velocity: call reg_objective_gradient first");
@@ -1291,6 +1345,7 @@ reg_status reg_precond_apply(reg_ctx* c, const float* r, float* z) {
 reg_status reg_kkt_solve(reg_ctx* c, const float* v, const float* rhs, double rtol, int maxit,
                          float* x, reg_info* info) {
   if (!c || !v || !rhs || !x || maxit < 1) return REG_EINVAL;
+  if (unaligned({v, rhs, x})) return reject_unaligned(c);
   return guarded(c, [&] {
     require_images(c);
     sync_velocity(c, v);
@@ -1330,26 +1385,27 @@ reg_status reg_profile_enable(reg_ctx* c, int enable) {
       check(c, cudaEventCreate(&e), "cudaEventCreate");
       c->evpool.push_back(e);
     }
-    for (int k = 0; k < REG_KC_COUNT; ++k) {
-      c->prof_ms[k] = 0.0;
-      c->prof_bytes[k] = 0.0;
-      c->prof_n[k] = 0;
-    }
+    for (int l = 0; l < 2; ++l)
+      for (int k = 0; k < REG_KC_COUNT; ++k) {
+        c->prof_ms[l][k] = 0.0;
+        c->prof_bytes[l][k] = 0.0;
+        c->prof_n[l][k] = 0;
+      }
   });
 }
 
-reg_status reg_profile_read(reg_ctx* c, int kclass, double* ms, long long* launches,
+reg_status reg_profile_read(reg_ctx* c, int level, int kclass, double* ms, long long* launches,
                             double* bytes) {
-  if (!c || kclass < 0 || kclass >= REG_KC_COUNT) return REG_EINVAL;
+  if (!c || kclass < 0 || kclass >= REG_KC_COUNT || level < 0 || level > 1) return REG_EINVAL;
   return guarded(c, [&] {
     harvest(c);
-    if (ms) *ms = c->prof_ms[kclass];
-    if (launches) *launches = c->prof_n[kclass];
-    if (bytes) *bytes = c->prof_bytes[kclass];
+    if (ms) *ms = c->prof_ms[level][kclass];
+    if (launches) *launches = c->prof_n[level][kclass];
+    if (bytes) *bytes = c->prof_bytes[level][kclass];
   });
 }
 
-long long reg_launch_count(void) { return g_launch_count; }
+long long reg_launch_count(void) { return g_launch_count.load(); }
 
 reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
   if (!c || !a || !b || !out || n < 0) return REG_EINVAL;
@@ -1358,6 +1414,7 @@ reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, doub
 
 reg_status reg_solve(reg_ctx* c, float* v, double gtol, reg_info* info) {
   if (!c || !v || !(gtol > 0.0)) return REG_EINVAL;
+  if (unaligned({v})) return reject_unaligned(c);
   reg_status result = REG_OK;
   reg_info inf;
   std::memset(&inf, 0, sizeof inf);

@@ -29,14 +29,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mutex;
 float* g_static_ptr[kMaxDevices] = {};
 
-bool pow2_between(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+bool size_ok(int n) { return n % 32 == 0 && regnk::fft_size_supported(n); }
 
 }  // namespace
 
 extern "C" reg_status reg_interpolate_static(int n1, int n2, const float* u, const float* disp,
                                              float* out, void* cuda_stream) {
   if (!u || !disp || !out) return REG_EINVAL;
-  if (!pow2_between(n1, 32, 2048) || !pow2_between(n2, 32, 2048)) return REG_EINVAL;
+  if (!size_ok(n1) || !size_ok(n2)) return REG_EINVAL;
+  // vector loads and stores: every buffer starts on a 16-byte boundary
+  if ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(disp) |
+       reinterpret_cast<uintptr_t>(out)) & 15u)
+    return REG_EINVAL;
   if ((long long)n1 * n2 > (long long)REG_STATIC_MAX_POINTS) return REG_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return REG_ECUDA;

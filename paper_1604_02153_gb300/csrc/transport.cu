@@ -15,29 +15,43 @@
 
 namespace regnk {
 
+// True when both grid lengths are powers of two (see split_index).
+static bool pow2_grid(int n1, int n2) { return !(n1 & (n1 - 1)) && !(n2 & (n2 - 1)); }
+
+// log2(n) for powers of two, -1 otherwise
+static int ilog2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return (1 << l) == n ? l : -1;
+}
+
+// Launches KERNEL<true> on power-of-two grids, KERNEL<false> otherwise.
+#define REGNK_LAUNCH_P2(n1, n2, KERNEL, GRID, BLOCK, ST, ...)          \
+  do {                                                                 \
+    if (pow2_grid(n1, n2))                                             \
+      KERNEL<true><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
+    else                                                               \
+      KERNEL<false><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);              \
+    ++g_launch_count;                                                  \
+  } while (0)
+
 // One block per 32x32 output tile and field.
+template <bool P2>
 __global__ void __launch_bounds__(kPThreads)
 k_prefilter(const float* __restrict__ in, float* __restrict__ out, int n1, int n2, int log1,
             long long fstride) {
   __shared__ float sin_[kPH * kPIn];
   __shared__ float smid[kPH * kPMid];
   const long long fo = (long long)blockIdx.z * fstride;
-  prefilter_tile(in + fo, out + fo, n1, n2, log1, blockIdx.x * kPX, blockIdx.y * kPY, sin_,
-                 smid);
-}
-
-static int ilog2i(int n) {
-  int l = 0;
-  while ((1 << l) < n) ++l;
-  return l;
+  prefilter_tile<P2>(in + fo, out + fo, n1, n2, log1, blockIdx.x * kPX, blockIdx.y * kPY, sin_,
+                     smid);
 }
 
 void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
                       cudaStream_t st) {
   (void)tmp;
-  k_prefilter<<<dim3(n1 / kPX, n2 / kPY, F), kPThreads, 0, st>>>(in, out, n1, n2, ilog2i(n1),
-                                                                  (long long)n1 * n2);
-  ++g_launch_count;
+  REGNK_LAUNCH_P2(n1, n2, k_prefilter, dim3(n1 / kPX, n2 / kPY, F), kPThreads, st, in, out, n1,
+                  n2, ilog2i(n1), (long long)n1 * n2);
 }
 
 constexpr int kPT = 256;  // threads per block of the pointwise kernels
@@ -46,6 +60,7 @@ constexpr int kPT = 256;  // threads per block of the pointwise kernels
 //   X* = x - h_t v(x),  X_D = x - h_t/2 (v(x) + v(X*))
 //   Y* = x + h_t v(x),  Y_D = x + h_t/2 (v(x) + v(Y*))
 // cv holds the interpolation coefficients of v (spline) or v itself.
+template <bool P2>
 __global__ void __launch_bounds__(kPT)
 k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restrict__ v,
             const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
@@ -53,17 +68,18 @@ k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restric
   const long long N = (long long)n1 * n2;
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
-  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
+  int i, j;
+  split_index<P2>(idx, n1, log1, i, j);
   const float v1 = __ldg(v + idx), v2 = __ldg(v + N + idx);
   const float a1 = s1 * v1, a2 = s2 * v2;   // h_t v / h in cells
   if (dX) {
-    const Stencil S = make_stencil(i, j, -a1, -a2, n1, n2, log1, lagrange);
+    const Stencil S = make_stencil<P2>(i, j, -a1, -a2, n1, n2, log1, lagrange);
     const float w1 = apply_stencil(S, cv), w2 = apply_stencil(S, cv + N);
     dX[idx] = -0.5f * (a1 + s1 * w1);
     dX[N + idx] = -0.5f * (a2 + s2 * w2);
   }
   if (dY) {
-    const Stencil S = make_stencil(i, j, a1, a2, n1, n2, log1, lagrange);
+    const Stencil S = make_stencil<P2>(i, j, a1, a2, n1, n2, log1, lagrange);
     const float w1 = apply_stencil(S, cv), w2 = apply_stencil(S, cv + N);
     dY[idx] = 0.5f * (a1 + s1 * w1);
     dY[N + idx] = 0.5f * (a2 + s2 * w2);
@@ -75,29 +91,102 @@ void launch_departure(int n1, int n2, float ht, const float* v, const float* cv,
   const long long N = (long long)n1 * n2;
   const float s1 = ht * n1 / (2.0f * 3.14159265358979323846f);
   const float s2 = ht * n2 / (2.0f * 3.14159265358979323846f);
-  k_departure<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), s1, s2, v,
-                                                                cv, dX, dY, lagrange); ++g_launch_count;
+  REGNK_LAUNCH_P2(n1, n2, k_departure, (unsigned)((N + kPT - 1) / kPT), kPT, st, n1, n2,
+                  ilog2i(n1), s1, s2, v, cv, dX, dY, lagrange);
 }
 
-// out_f = I[coef_f](x + disp), f = 0..F-1 (fields fstride apart), one stencil.
+// The step kernels below handle kSP horizontally adjacent points
+// per thread (row lengths are multiples of 32, so the kSP points of a thread
+// share a row): their streamed fields move as kSP-float vectors and the kSP
+// independent 4x4 stencils keep more loads in flight per thread.
+#ifndef REGNK_STEP_POINTS
+#define REGNK_STEP_POINTS 2
+#endif
+constexpr int kSP = REGNK_STEP_POINTS;
+static_assert(kSP == 1 || kSP == 2 || kSP == 4, "points per thread");
+
+template <int K>
+__device__ __forceinline__ void ldk(const float* p, float (&a)[K]) {
+  if constexpr (K == 1) {
+    a[0] = __ldg(p);
+  } else if constexpr (K == 2) {
+    const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+    a[0] = t.x; a[1] = t.y;
+  } else {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+  }
+}
+
+// plain (not read-only) load, for buffers the kernel also writes
+template <int K>
+__device__ __forceinline__ void ldk_rw(const float* p, float (&a)[K]) {
+  if constexpr (K == 1) {
+    a[0] = *p;
+  } else if constexpr (K == 2) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    a[0] = t.x; a[1] = t.y;
+  } else {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    a[0] = t.x; a[1] = t.y; a[2] = t.z; a[3] = t.w;
+  }
+}
+
+template <int K>
+__device__ __forceinline__ void stk(float* p, const float (&a)[K]) {
+  if constexpr (K == 1) {
+    *p = a[0];
+  } else if constexpr (K == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(a[0], a[1]);
+  } else {
+    *reinterpret_cast<float4*>(p) = make_float4(a[0], a[1], a[2], a[3]);
+  }
+}
+
+static unsigned step_blocks(long long N) { return (unsigned)((N / kSP + kPT - 1) / kPT); }
+
+// out_f = I[coef_f](x + disp), f = 0..F-1 (fields fstride apart), one stencil
+// per point, one point per thread; F = 1 or 2 is a compile-time constant so
+// that the loads of both fields are in flight together without the
+// register cost of an unrolled loop of unknown length.
+template <bool P2, int F>
 __global__ void __launch_bounds__(kPT)
 k_gather(int n1, int n2, int log1, const float* __restrict__ coef,
-         const float* __restrict__ disp, float* __restrict__ out, int F, long long fstride,
+         const float* __restrict__ disp, float* __restrict__ out, long long fstride,
          int lagrange) {
   const long long N = (long long)n1 * n2;
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
-  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-  const Stencil S = make_stencil(i, j, __ldg(disp + idx), __ldg(disp + N + idx), n1, n2, log1,
-                                 lagrange);
-  for (int f = 0; f < F; ++f) out[f * fstride + idx] = apply_stencil(S, coef + f * fstride);
+  int i, j;
+  split_index<P2>(idx, n1, log1, i, j);
+  const Stencil S = make_stencil<P2>(i, j, __ldg(disp + idx), __ldg(disp + N + idx), n1, n2,
+                                     log1, lagrange);
+  float o[F];
+#pragma unroll
+  for (int f = 0; f < F; ++f) o[f] = apply_stencil(S, coef + f * fstride);
+#pragma unroll
+  for (int f = 0; f < F; ++f) out[f * fstride + idx] = o[f];
+}
+
+template <int F>
+static void gather_f(int n1, int n2, const float* coef, const float* disp, float* out,
+                     long long fstride, int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  const unsigned nb = (unsigned)((N + kPT - 1) / kPT);
+  if (pow2_grid(n1, n2))
+    k_gather<true, F><<<nb, kPT, 0, st>>>(n1, n2, ilog2i(n1), coef, disp, out, fstride, lagrange);
+  else
+    k_gather<false, F><<<nb, kPT, 0, st>>>(n1, n2, -1, coef, disp, out, fstride, lagrange);
+  ++g_launch_count;
 }
 
 void launch_gather(int n1, int n2, const float* coef, const float* disp, float* out, int F,
                    long long fstride, int lagrange, cudaStream_t st) {
-  const long long N = (long long)n1 * n2;
-  k_gather<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(n1, n2, ilog2i(n1), coef, disp,
-                                                             out, F, fstride, lagrange); ++g_launch_count;
+  // callers interpolate one scalar field or one vector field
+  if (F == 2)
+    gather_f<2>(n1, n2, coef, disp, out, fstride, lagrange, st);
+  else
+    gather_f<1>(n1, n2, coef, disp, out, fstride, lagrange, st);
 }
 
 void launch_state_step(int n1, int n2, const float* coef, const float* dX, float* out,
@@ -132,24 +221,44 @@ void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const fl
 //   lb = lam_{j+1}(Y_D), lam* = lb + h_t lb div v(Y_D),
 //   lam_j = lb + h_t/2 (lb div v(Y_D) + lam* div v(x)),
 // fused with the time integral b += wb * lam_j * grad m_j.
+template <bool P2>
 __global__ void __launch_bounds__(kPT)
 k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ coef,
                const float* __restrict__ dY, const float* __restrict__ delta,
                const float* __restrict__ delta_bar, const float* __restrict__ gm,
                float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
   const long long N = (long long)n1 * n2;
-  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
   if (idx >= N) return;
-  const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-  const Stencil S = make_stencil(i, j, __ldg(dY + idx), __ldg(dY + N + idx), n1, n2, log1,
-                                 lagrange);
-  const float lb = apply_stencil(S, coef);
-  const float db = __ldg(delta_bar + idx), d = __ldg(delta + idx);
-  const float lstar = fmaf(ht * lb, db, lb);
-  const float l = lb + 0.5f * ht * (lb * db + lstar * d);
-  lam_out[idx] = l;
-  b[idx] = fmaf(wb * l, __ldg(gm + idx), b[idx]);
-  b[N + idx] = fmaf(wb * l, __ldg(gm + N + idx), b[N + idx]);
+  int i, j;
+  split_index<P2>(idx, n1, log1, i, j);
+  float y1[kSP], y2[kSP], l[kSP];
+  ldk(dY + idx, y1);
+  ldk(dY + N + idx, y2);
+#pragma unroll
+  for (int p = 0; p < kSP; ++p)
+    l[p] = apply_stencil(make_stencil<P2>(i + p, j, y1[p], y2[p], n1, n2, log1, lagrange), coef);
+  float db[kSP], d[kSP];
+  ldk(delta_bar + idx, db);
+  ldk(delta + idx, d);
+#pragma unroll
+  for (int p = 0; p < kSP; ++p) {
+    const float lstar = fmaf(ht * l[p], db[p], l[p]);
+    l[p] = l[p] + 0.5f * ht * (l[p] * db[p] + lstar * d[p]);
+  }
+  stk(lam_out + idx, l);
+  float g1[kSP], g2[kSP], b1[kSP], b2[kSP];
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+  ldk_rw(b + idx, b1);
+  ldk_rw(b + N + idx, b2);
+#pragma unroll
+  for (int p = 0; p < kSP; ++p) {
+    b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
+    b2[p] = fmaf(wb * l[p], g2[p], b2[p]);
+  }
+  stk(b + idx, b1);
+  stk(b + N + idx, b2);
 }
 
 void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
@@ -157,14 +266,15 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  k_adjoint_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
-      n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange); ++g_launch_count;
+  REGNK_LAUNCH_P2(n1, n2, k_adjoint_step, step_blocks(N), kPT, st, n1, n2, ilog2i(n1), ht, wb,
+                  coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
 }
 
 // One forward step of the incremental state (Gauss-Newton, §3.3.2):
 //   m~_j = m~_{j-1}(X_D) - h_t/2 (v~(X_D) . grad m_{j-1}(X_D) + v~ . grad m_j)
 // G = grad m_{j-1}(X_D) (2 fields), vtD = v~(X_D) (2 fields), gm = grad m_j.
 // first = 1 for j = 1 where m~_0 = 0.
+template <bool P2>
 __global__ void __launch_bounds__(kPT)
 k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ coef,
                 const float* __restrict__ dX, const float* __restrict__ vt,
@@ -172,26 +282,42 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
                 const float* __restrict__ gm, float* __restrict__ out, int first,
                 int lagrange) {
   const long long N = (long long)n1 * n2;
-  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
   if (idx >= N) return;
-  float base = 0.f;
+  float m[kSP];
+#pragma unroll
+  for (int p = 0; p < kSP; ++p) m[p] = 0.f;
   if (!first) {
-    const int i = (int)(idx & (n1 - 1)), j = (int)(idx >> log1);
-    const Stencil S = make_stencil(i, j, __ldg(dX + idx), __ldg(dX + N + idx), n1, n2, log1,
-                                   lagrange);
-    base = apply_stencil(S, coef);
+    int i, j;
+    split_index<P2>(idx, n1, log1, i, j);
+    float x1[kSP], x2[kSP];
+    ldk(dX + idx, x1);
+    ldk(dX + N + idx, x2);
+#pragma unroll
+    for (int p = 0; p < kSP; ++p)
+      m[p] = apply_stencil(make_stencil<P2>(i + p, j, x1[p], x2[p], n1, n2, log1, lagrange), coef);
   }
-  const float src_dep = __ldg(vtD + idx) * __ldg(G + idx) + __ldg(vtD + N + idx) * __ldg(G + N + idx);
-  const float src_arr = __ldg(vt + idx) * __ldg(gm + idx) + __ldg(vt + N + idx) * __ldg(gm + N + idx);
-  out[idx] = base - 0.5f * ht * (src_dep + src_arr);
+  float w1[kSP], w2[kSP], G1[kSP], G2[kSP], u1[kSP], u2[kSP], g1[kSP], g2[kSP];
+  ldk(vtD + idx, w1);
+  ldk(vtD + N + idx, w2);
+  ldk(G + idx, G1);
+  ldk(G + N + idx, G2);
+  ldk(vt + idx, u1);
+  ldk(vt + N + idx, u2);
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+#pragma unroll
+  for (int p = 0; p < kSP; ++p)
+    m[p] -= 0.5f * ht * (w1[p] * G1[p] + w2[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
+  stk(out + idx, m);
 }
 
 void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
                           const float* vt, const float* vtD, const float* G, const float* gm,
                           float* out, int first, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  k_incstate_step<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(
-      n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange); ++g_launch_count;
+  REGNK_LAUNCH_P2(n1, n2, k_incstate_step, step_blocks(N), kPT, st, n1, n2, ilog2i(n1), ht, coef,
+                  dX, vt, vtD, G, gm, out, first, lagrange);
 }
 
 }  // namespace regnk

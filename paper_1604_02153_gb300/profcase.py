@@ -5,7 +5,9 @@
 sets up the phantom pair at n^2 (seed 100), evaluates the objective and
 gradient at a smooth velocity (max |v| = 0.2) and applies the GN Hessian
 `--matvecs` times; `--precond` also applies the two-level preconditioner
-once. Prints the wall time per matvec. The workload holds a few hundred MB
+once and times a PCG solve with it; `--pcg` times a PCG solve with the
+spectral preconditioner P_REG (graph replay of the matvec alone). Prints
+the wall time per matvec. The workload holds a few hundred MB
 on the device at 1024^2.
 """
 
@@ -26,6 +28,8 @@ def main():
     ap.add_argument("--matvecs", type=int, default=3)
     ap.add_argument("--lagrange", action="store_true")
     ap.add_argument("--precond", action="store_true")
+    ap.add_argument("--persistent", type=int, default=0)
+    ap.add_argument("--pcg", action="store_true")
     a = ap.parse_args()
     import numpy as np
     import torch
@@ -36,8 +40,10 @@ def main():
     v = inputs.random_velocity(n, seed=7, vmax=0.2)
     u = inputs.random_velocity(n, seed=8, vmax=1.0)
     f = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32).ravel(), device="cuda")
+    pc = {} if a.precond else {"precond": regnk.REG_PC_REG}
     R = regnk.Registration(n, n, a.nt, 1e-2,
-                           interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE)
+                           interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE,
+                           persistent_matvec=a.persistent, **pc)
     R.set_images(f(m_R), f(m_T))
     vd, ud = f(v), f(u)
     g = torch.empty_like(vd)
@@ -50,7 +56,18 @@ def main():
         R.hessian_matvec(vd, ud, H)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / max(1, a.matvecs)
-    print(f"n={n} nt={a.nt} matvec {1e3 * dt:.3f} ms (wall, eager launches, incl. host)")
+    print(f"n={n} nt={a.nt} persistent={a.persistent} matvec {1e3 * dt:.3f} ms "
+          f"(wall, incl. host)")
+    if a.pcg and not a.precond:
+        x = torch.empty_like(vd)
+        R.kkt_solve(vd, g, 1e-12, a.matvecs, x)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = R.kkt_solve(vd, g, 1e-12, a.matvecs, x)
+        torch.cuda.synchronize()
+        dk = time.perf_counter() - t0
+        print(f"n={n} PCG (P_REG) {info['pcg_iters']} iterations "
+              f"{1e3 * dk / max(1, info['pcg_iters']):.3f} ms per iteration (graph replay of the matvec)")
     if a.precond:
         z = torch.empty_like(vd)
         R.precond_apply(g, z)

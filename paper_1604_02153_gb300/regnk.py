@@ -87,10 +87,18 @@ _SIGNATURES = {
     "reg_dot": [_P, _P, _P, ctypes.c_longlong, ctypes.POINTER(_D)],
     "reg_last_error": [_P],
     "reg_profile_enable": [_P, _I],
-    "reg_profile_read": [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
+    "reg_profile_read": [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(_D)],
     "reg_launch_count": [],
     "reg_interpolate_static": [_I, _I, _P, _P, _P, _P],
+    "reg_batch_create": [ctypes.POINTER(reg_grid), _I, _I, ctypes.POINTER(_D),
+                         ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
+    "reg_batch_destroy": [_P],
+    "reg_batch_set_images": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "reg_batch_set_beta": [_P, ctypes.POINTER(_D)],
+    "reg_batch_solve": [_P, ctypes.POINTER(_P), _D, _I, ctypes.POINTER(reg_info)],
+    "reg_batch_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "reg_batch_last_error": [_P],
 }
 
 _lib = None
@@ -107,7 +115,7 @@ def load(path=LIB_PATH):
     for name, args in _SIGNATURES.items():
         fn = getattr(lib, name)
         fn.argtypes = args
-        fn.restype = {"reg_last_error": ctypes.c_char_p,
+        fn.restype = {"reg_last_error": ctypes.c_char_p, "reg_batch_last_error": ctypes.c_char_p,
                       "reg_launch_count": ctypes.c_longlong}.get(name, ctypes.c_int)
     _lib = lib
     return lib
@@ -244,12 +252,16 @@ class Registration:
         self._call("reg_profile_enable", 1 if enable else 0)
 
     def profile_read(self):
-        """{class name: (ms, launches, algorithmic bytes)} since profile_enable."""
+        """{(level, class name): (ms, launches, algorithmic bytes)} since
+        profile_enable; level "fine" is the problem grid, "coarse" the coarse
+        grid of the two-level preconditioner."""
         out = {}
-        for k, name in enumerate(KERNEL_CLASSES):
-            ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
-            self._call("reg_profile_read", k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(by))
-            out[name] = (ms.value, n.value, by.value)
+        for lvl, lname in enumerate(("fine", "coarse")):
+            for k, name in enumerate(KERNEL_CLASSES):
+                ms, n, by = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_double()
+                self._call("reg_profile_read", lvl, k, ctypes.byref(ms), ctypes.byref(n),
+                           ctypes.byref(by))
+                out[(lname, name)] = (ms.value, n.value, by.value)
         return out
 
     def dot(self, a, b):
@@ -257,6 +269,74 @@ class Registration:
         self._call("reg_dot", _ptr(a, name="a"), _ptr(b, name="b"), ctypes.c_longlong(a.numel()),
                    ctypes.byref(out))
         return out.value
+
+
+class Batch:
+    """reg_batch: independent problems solved concurrently (own context and
+    stream each, a pool of host threads). Methods take lists of tensors."""
+
+    def __init__(self, grids, nt, betas, **options):
+        self.lib = load()
+        self.grids = [(int(a), int(b)) for a, b in grids]
+        self.B = len(self.grids)
+        G = (reg_grid * self.B)(*[reg_grid(a, b) for a, b in self.grids])
+        Bt = (ctypes.c_double * self.B)(*[float(x) for x in betas])
+        self.options = default_options(**options)
+        h = ctypes.c_void_p()
+        s = self.lib.reg_batch_create(G, self.B, int(nt), Bt, ctypes.byref(self.options),
+                                      ctypes.byref(h))
+        if s != REG_OK:
+            raise RegError(s, "reg_batch_create failed")
+        self.h = h
+
+    def _ptrs(self, ts, per_point, name):
+        arr = (ctypes.c_void_p * self.B)()
+        for i, (t, (a, b)) in enumerate(zip(ts, self.grids)):
+            arr[i] = _ptr(t, per_point * a * b, f"{name}[{i}]").value
+        return arr
+
+    def _check(self, s):
+        if s != REG_OK:
+            raise RegError(s, self.lib.reg_batch_last_error(self.h).decode())
+
+    def set_images(self, m_R, m_T):
+        import torch
+        torch.cuda.synchronize()
+        self._check(self.lib.reg_batch_set_images(self.h, self._ptrs(m_R, 1, "m_R"),
+                                                  self._ptrs(m_T, 1, "m_T")))
+
+    def set_beta(self, betas):
+        self._check(self.lib.reg_batch_set_beta(self.h, (ctypes.c_double * self.B)(*betas)))
+
+    def solve(self, vs, gtol, threads=0, allow=(REG_OK, REG_ENOTCONV, REG_ELINESEARCH)):
+        import torch
+        torch.cuda.synchronize()
+        infos = (reg_info * self.B)()
+        s = self.lib.reg_batch_solve(self.h, self._ptrs(vs, 2, "v"), float(gtol), int(threads),
+                                     infos)
+        if s not in allow:
+            self._check(s)
+        out = []
+        for i in range(self.B):
+            d = infos[i].as_dict()
+            d["status_name"] = STATUS_NAMES.get(d["status"], str(d["status"]))
+            out.append(d)
+        return out
+
+    def hessian_matvec(self, vs, vts, Hs):
+        import torch
+        torch.cuda.synchronize()
+        self._check(self.lib.reg_batch_hessian_matvec(self.h, self._ptrs(vs, 2, "v"),
+                                                      self._ptrs(vts, 2, "vt"),
+                                                      self._ptrs(Hs, 2, "Hvt")))
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.reg_batch_destroy(h)
+            self.h = None
+
+    __del__ = close
 
 
 REG_STATIC_MAX_POINTS = 1024 * 1024

@@ -80,13 +80,26 @@ def problem_data(n1, n2, seed=0, vmax=0.2):
     return m_R, m_T, v
 
 
-GRIDS = [(64, 64), (128, 64), (64, 256), (512, 512)]
+GRIDS = [(64, 64), (128, 64), (64, 256), (512, 512), (192, 96), (96, 384)]
+
+
+def _grid_ok(n):
+    m = n // 3 if n % 3 == 0 else n
+    return n % 32 == 0 and m & (m - 1) == 0
+
+
+def pc_for(n1, n2):
+    """Default two-level preconditioner where the half grid is a supported
+    size, the spectral one (P_REG) otherwise (e.g. 96 x 192: 48 is not)."""
+    if _grid_ok(n1 // 2) and _grid_ok(n2 // 2):
+        return {}
+    return {"precond": 0}
 
 
 @pytest.mark.parametrize("n1,n2", GRIDS)
 def test_spectral_operators(regnk, n1, n2):
     beta = 0.03
-    R = regnk.Registration(n1, n2, 4, beta)
+    R = regnk.Registration(n1, n2, 4, beta, **pc_for(n1, n2))
     u = inputs.random_field(n1, n2, seed=11, kmax=min(n1, n2) // 2 - 1)
     v = inputs.random_velocity(n1, n2, seed=12, kmax=min(n1, n2) // 4, vmax=1.0)
     N = n1 * n2
@@ -131,9 +144,9 @@ def test_higher_order_regularisation(regnk, norm, p):
     R.close()
 
 
-@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 256), (1024, 1024)])
+@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 256), (1024, 1024), (384, 192)])
 def test_restriction_prolongation(regnk, n1, n2):
-    R = regnk.Registration(n1, n2, 4, 1e-2)
+    R = regnk.Registration(n1, n2, 4, 1e-2, **pc_for(n1, n2))
     v = inputs.random_velocity(n1, n2, seed=14, kmax=min(n1, n2) // 4, vmax=1.0)
     c = torch.empty(n1 * n2 // 2, device="cuda")
     R.restrict(dev(v), c)
@@ -146,10 +159,10 @@ def test_restriction_prolongation(regnk, n1, n2):
 
 
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
-@pytest.mark.parametrize("n1,n2,nt", [(128, 128, 4), (256, 64, 8)])
+@pytest.mark.parametrize("n1,n2,nt", [(128, 128, 4), (256, 64, 8), (96, 192, 4)])
 def test_departure_points(regnk, kind, n1, n2, nt):
     interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
-    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp)
+    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp, **pc_for(n1, n2))
     v = inputs.random_velocity(n1, n2, seed=15, vmax=0.5)
     dX = torch.empty(2 * n1 * n2, device="cuda")
     dY = torch.empty(2 * n1 * n2, device="cuda")
@@ -162,10 +175,10 @@ def test_departure_points(regnk, kind, n1, n2, nt):
 
 
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
-def test_interpolation(regnk, kind):
-    n1, n2 = 256, 128
+@pytest.mark.parametrize("n1,n2", [(256, 128), (192, 96)])
+def test_interpolation(regnk, kind, n1, n2):
     interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
-    R = regnk.Registration(n1, n2, 4, 1e-2, interp=interp)
+    R = regnk.Registration(n1, n2, 4, 1e-2, interp=interp, **pc_for(n1, n2))
     u = inputs.random_field(n1, n2, seed=16, kmax=16)
     disp = inputs.random_velocity(n1, n2, seed=17, vmax=6.0)   # up to 6 cells, wraps
     out = torch.empty(n1 * n2, device="cuda")
@@ -177,10 +190,10 @@ def test_interpolation(regnk, kind):
 
 
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
-@pytest.mark.parametrize("n1,n2,nt", [(64, 64, 4), (256, 128, 8), (128, 128, 16)])
+@pytest.mark.parametrize("n1,n2,nt", [(64, 64, 4), (256, 128, 8), (128, 128, 16), (192, 96, 4)])
 def test_transport(regnk, kind, n1, n2, nt):
     interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
-    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp)
+    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp, **pc_for(n1, n2))
     _, m_T, v = problem_data(n1, n2, vmax=0.4)
     m1 = torch.empty(n1 * n2, device="cuda")
     R.transport(dev(v), dev(m_T), m1)
@@ -197,7 +210,7 @@ def f32(a):
 @pytest.mark.parametrize("persistent", [1, 0])
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
 @pytest.mark.parametrize("n1,n2,nt,norm", [(64, 64, 4, 1), (128, 64, 8, 1), (256, 256, 4, 1),
-                                           (64, 64, 4, 2), (128, 64, 1, 1)])
+                                           (64, 64, 4, 2), (128, 64, 1, 1), (192, 192, 4, 1)])
 def test_objective_gradient_hessian(regnk, kind, n1, n2, nt, norm, persistent):
     """Objective, gradient and GN Hessian matvec against the oracle on the
     same FP32 inputs. The data terms b = g - beta A v and b~ = H u - beta A u
@@ -420,4 +433,19 @@ def test_invalid_call_order(regnk):
     with pytest.raises(regnk.RegError) as e:
         R.objective_gradient(torch.zeros(2 * 64 * 64, device="cuda"), None)
     assert e.value.status == regnk.REG_ESTATE
+    R.close()
+
+
+def test_unaligned_buffers_rejected_before_launch(regnk):
+    n = 64
+    R = regnk.Registration(n, n, 4, 1e-2)
+    base = torch.zeros(2 * n * n + 4, device="cuda")
+    u = base[:n * n]
+    disp = base[1:2 * n * n + 1]          # starts 4 bytes past a 16-byte boundary
+    out = torch.empty(n * n, device="cuda")
+    before = regnk.launch_count()
+    with pytest.raises(regnk.RegError) as e:
+        R.interpolate(u, disp, out)
+    assert e.value.status == regnk.REG_EINVAL
+    assert regnk.launch_count() == before
     R.close()

@@ -57,7 +57,9 @@ def _create(lib, n1, n2, nt, beta, **kw):
 
 
 @pytest.mark.parametrize("n1,n2,nt,beta,kw", [
-    (48, 64, 4, 1e-2, {}),           # not a power of two
+    (48, 64, 4, 1e-2, {}),           # not a multiple of 32
+    (160, 64, 4, 1e-2, {}),          # 5 * 32: no FFT for this length
+    (96, 96, 4, 1e-2, {"precond": 1}),  # coarse grid 48 is not a supported size
     (64, 16, 4, 1e-2, {}),           # below the minimum size
     (64, 64, 0, 1e-2, {}),           # no time steps
     (64, 64, 4, 0.0, {}),            # beta must be positive
@@ -83,3 +85,10 @@ def test_no_cpu_fallback(lib):
         pytest.skip("a GPU is present")
     s, h = _create(lib, 64, 64, 4, 1e-2)
     assert s == regnk.REG_ECUDA and not h.value
+
+
+def test_static_interpolation_rejects_unaligned_buffers(lib):
+    # checked on the host before any device work: the addresses are never used
+    ok, off = ctypes.c_void_p(1 << 20), ctypes.c_void_p((1 << 20) + 4)
+    for u, d, o in [(off, ok, ok), (ok, off, ok), (ok, ok, off)]:
+        assert lib.reg_interpolate_static(64, 64, u, d, o, None) == regnk.REG_EINVAL
