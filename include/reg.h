@@ -92,6 +92,14 @@ typedef struct {
                               arrival that never comes; every block gives up after
                               its bounded wait (~0.5 s) and the call returns
                               REG_ETIMEOUT with the context still usable          */
+  int programmatic_launch; /* 1 (default): kernels launched directly on the stream
+                              carry programmatic stream serialisation, so a
+                              kernel's blocks may be scheduled while its
+                              predecessor finishes (each waits for the
+                              predecessor's completion before touching memory:
+                              results are identical); kernels inside the
+                              library's CUDA graphs are plain launches either
+                              way. 0: plain launches everywhere                */
 } reg_options;
 
 typedef struct {

@@ -200,6 +200,7 @@ template <int L, int T>
 __global__ void __launch_bounds__(FftCfg<L, T>::NT)
 k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__ spec,
            long long sstride, int n2, const float2* __restrict__ tw) {
+  pdl_enter();
   constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(FftCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
            const float2* __restrict__ tw) {
+  pdl_enter();
   constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
@@ -347,6 +349,7 @@ struct ColCfg {
 
 template <int LI, int LO, int T>
 __global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT) k_cols(ColArgs a) {
+  pdl_enter();
   constexpr int NI = FftCfg<LI, T>::N, NO = FftCfg<LO, T>::N;
   constexpr int NM = ColCfg<LI, LO, T>::NM;
   constexpr int P = ColCfg<LI, LO, T>::P, NT = ColCfg<LI, LO, T>::NT;
@@ -436,7 +439,7 @@ static void launch_r2c(const float* in, long long fstride, float2* spec, long lo
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_r2c<L, T><<<grid, C::NT, smem, st>>>(in, fstride, spec, sstride, n2, tw); ++g_launch_count;
+  launch_k(k_rows_r2c<L, T>, dim3(grid), dim3(C::NT), smem, st, in, fstride, spec, sstride, n2, tw);
 }
 
 template <int L, int T>
@@ -447,7 +450,7 @@ static void launch_c2r(const float2* spec, long long sstride, float* out, long l
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  k_rows_c2r<L, T><<<grid, C::NT, smem, st>>>(spec, sstride, out, fstride, add, astride, n2, tw); ++g_launch_count;
+  launch_k(k_rows_c2r<L, T>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw);
 }
 
 template <int LI, int LO, int T>
@@ -456,7 +459,7 @@ static void launch_cols(const ColArgs& a, int groups, cudaStream_t st) {
   const size_t smem = (size_t)(a.nin + 1) * C::P * C::NM * sizeof(float2);
   static_assert(3 * C::P * C::NM * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid((a.nk1_out + C::P - 1) / C::P, groups);
-  k_cols<LI, LO, T><<<grid, C::NT, smem, st>>>(a); ++g_launch_count;
+  launch_k(k_cols<LI, LO, T>, dim3(grid), dim3(C::NT), smem, st, a);
 }
 
 // supported line lengths: 2^L for L = 5..11, 3 * 2^L for L = 5..9 (96 .. 1536)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <utility>
 
 #include "interp.cuh"
 
@@ -12,6 +13,42 @@ namespace regnk {
 // Kernel launches issued by the library since load (incremented after every
 // launch, from any host thread; read by reg_launch_count).
 extern std::atomic<long long> g_launch_count;
+
+// Programmatic dependent launch. A kernel launched through launch_k carries
+// the programmatic-stream-serialisation attribute: the GPU may schedule its
+// blocks while the preceding kernel of the stream is still running, which
+// hides the launch latency between the many short dependent kernels of a
+// transport sweep. Every kernel launched this way calls pdl_enter() before
+// its first global memory access: griddepcontrol.wait blocks until the
+// preceding kernel has completed and its writes are visible (it returns at
+// once for a kernel launched without the attribute), and only then does the
+// kernel allow its own successor to be scheduled. No data is read early, so
+// the results do not depend on the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Attribute value for launches from this host thread (reg_options
+// .programmatic_launch of the context being driven; 1 outside a context).
+extern thread_local int t_programmatic_launch;
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = t_programmatic_launch ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  ++g_launch_count;
+}
 
 // Spectral multipliers of the column pass (see fft.cu).
 enum SpecOp {
@@ -108,6 +145,8 @@ void launch_axpby(long long n, const double* alpha_num, const double* alpha_den,
                   const float* x, float* y, float beta_y, cudaStream_t st);
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
                     cudaStream_t st);
+void launch_cheb_update(long long n, float a, float b, const float* Ad, float* r, float* d,
+                        float* x, cudaStream_t st);
 void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
                        const float* q, float* x, float* r, cudaStream_t st);
 void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,

@@ -50,6 +50,7 @@ template <int MODE>
 __global__ void __launch_bounds__(kRT)
 k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
           double* __restrict__ partial, int vec4) {
+  pdl_enter();
   double acc = 0.0;
   const long long stride = (long long)gridDim.x * kRT;
   const long long n4 = vec4 ? (n >> 2) : 0;   // float4 path only for 16-byte aligned inputs
@@ -75,6 +76,7 @@ k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
 
 __global__ void __launch_bounds__(kRT)
 k_final_sum(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  pdl_enter();
   double acc = 0.0;
   for (int i = threadIdx.x; i < nb; i += kRT) acc += partial[i];
   const double s = block_sum(acc);
@@ -88,19 +90,20 @@ static int aligned16(const void* a, const void* b) {
 void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
                 cudaStream_t st) {
   const int nb = nblocks(n);
-  k_partial<0><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b)); ++g_launch_count;
-  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out); ++g_launch_count;
+  launch_k(k_partial<0>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial, aligned16(a, b));
+  launch_k(k_final_sum, dim3(1), dim3(kRT), 0, st, partial, nb, out);
 }
 
 void launch_sumsq_diff(const float* a, const float* b, long long n, double* partial,
                        double* out, cudaStream_t st) {
   const int nb = nblocks(n);
-  k_partial<1><<<nb, kRT, 0, st>>>(a, b, n, partial, aligned16(a, b)); ++g_launch_count;
-  k_final_sum<<<1, kRT, 0, st>>>(partial, nb, out); ++g_launch_count;
+  launch_k(k_partial<1>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial, aligned16(a, b));
+  launch_k(k_final_sum, dim3(1), dim3(kRT), 0, st, partial, nb, out);
 }
 
 __global__ void __launch_bounds__(kRT)
 k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ partial) {
+  pdl_enter();
   float m = 0.f;
   const long long stride = (long long)gridDim.x * kRT;
   for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
@@ -120,6 +123,7 @@ k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ p
 }
 
 __global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double* out) {
+  pdl_enter();
   if (threadIdx.x == 0) {
     float r = 0.f;
     for (int i = 0; i < nb; ++i) r = (partial[i] > r || partial[i] != partial[i]) ? partial[i] : r;
@@ -129,13 +133,14 @@ __global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double
 
 void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st) {
   const int nb = nblocks(n);
-  k_maxabs_partial<<<nb, kRT, 0, st>>>(a, n, partial); ++g_launch_count;
-  k_maxabs_final<<<1, 32, 0, st>>>(partial, nb, out); ++g_launch_count;
+  launch_k(k_maxabs_partial, dim3(nb), dim3(kRT), 0, st, a, n, partial);
+  launch_k(k_maxabs_final, dim3(1), dim3(32), 0, st, partial, nb, out);
 }
 
 // flag = 1 if any bit pattern differs (flag must be zeroed by the caller).
 __global__ void k_compare(const unsigned* __restrict__ a, const unsigned* __restrict__ b,
                           long long n, int* flag) {
+  pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   int d = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -144,13 +149,13 @@ __global__ void k_compare(const unsigned* __restrict__ a, const unsigned* __rest
 }
 
 void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st) {
-  k_compare<<<nblocks(n), kRT, 0, st>>>(reinterpret_cast<const unsigned*>(a),
-                                        reinterpret_cast<const unsigned*>(b), n, flag); ++g_launch_count;
+  launch_k(k_compare, dim3(nblocks(n)), dim3(kRT), 0, st, reinterpret_cast<const unsigned*>(a), reinterpret_cast<const unsigned*>(b), n, flag);
 }
 
 // y = (alpha_num/alpha_den * cs) x + beta_y y, coefficients from device FP64 scalars.
 __global__ void k_axpby(long long n, const double* an, const double* ad, double cs,
                         const float* __restrict__ x, float* __restrict__ y, float beta_y) {
+  pdl_enter();
   const float alpha = (float)((*an / *ad) * cs);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -159,12 +164,13 @@ __global__ void k_axpby(long long n, const double* an, const double* ad, double 
 
 void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
                   const float* x, float* y, float beta_y, cudaStream_t st) {
-  k_axpby<<<nblocks(n), kRT, 0, st>>>(n, alpha_num, alpha_den, cs, x, y, beta_y); ++g_launch_count;
+  launch_k(k_axpby, dim3(nblocks(n)), dim3(kRT), 0, st, n, alpha_num, alpha_den, cs, x, y, beta_y);
 }
 
 // z may alias x or y (elementwise, same index)
 __global__ void k_lincomb(long long n, float a, const float* x, float b, const float* y,
                           float* z) {
+  pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     z[i] = a * x[i] + (y ? b * y[i] : 0.f);
@@ -172,13 +178,36 @@ __global__ void k_lincomb(long long n, float a, const float* x, float b, const f
 
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
                     cudaStream_t st) {
-  k_lincomb<<<nblocks(n), kRT, 0, st>>>(n, a, x, b, y, z); ++g_launch_count;
+  launch_k(k_lincomb, dim3(nblocks(n)), dim3(kRT), 0, st, n, a, x, b, y, z);
+}
+
+// One Chebyshev update (three-term recurrence on the residual):
+//   r -= Ad;  d = a d + b r;  x += d
+// in a single pass over the five vectors.
+__global__ void k_cheb_update(long long n, float a, float b, const float* __restrict__ Ad,
+                              float* __restrict__ r, float* __restrict__ d,
+                              float* __restrict__ x) {
+  pdl_enter();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float ri = r[i] - Ad[i];
+    const float di = fmaf(a, d[i], b * ri);
+    r[i] = ri;
+    d[i] = di;
+    x[i] = x[i] + di;
+  }
+}
+
+void launch_cheb_update(long long n, float a, float b, const float* Ad, float* r, float* d,
+                        float* x, cudaStream_t st) {
+  launch_k(k_cheb_update, dim3(nblocks(n)), dim3(kRT), 0, st, n, a, b, Ad, r, d, x);
 }
 
 // PCG step: alpha = rz / pq; x += alpha p; r -= alpha q.
 __global__ void k_pcg_update(long long n, const double* rz, const double* pq,
                              const float* __restrict__ p, const float* __restrict__ q,
                              float* __restrict__ x, float* __restrict__ r) {
+  pdl_enter();
   const double ad = *rz / *pq;
   const float alpha = (float)ad;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -190,12 +219,13 @@ __global__ void k_pcg_update(long long n, const double* rz, const double* pq,
 
 void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
                        const float* q, float* x, float* r, cudaStream_t st) {
-  k_pcg_update<<<nblocks(n), kRT, 0, st>>>(n, rz, pq, p, q, x, r); ++g_launch_count;
+  launch_k(k_pcg_update, dim3(nblocks(n)), dim3(kRT), 0, st, n, rz, pq, p, q, x, r);
 }
 
 // p = z + (rz_new / rz_old) p
 __global__ void k_pcg_direction(long long n, const double* rz_new, const double* rz_old,
                                 const float* __restrict__ z, float* __restrict__ p) {
+  pdl_enter();
   const float beta = (float)(*rz_new / *rz_old);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
@@ -204,22 +234,24 @@ __global__ void k_pcg_direction(long long n, const double* rz_new, const double*
 
 void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,
                           const float* z, float* p, cudaStream_t st) {
-  k_pcg_direction<<<nblocks(n), kRT, 0, st>>>(n, rz_new, rz_old, z, p); ++g_launch_count;
+  launch_k(k_pcg_direction, dim3(nblocks(n)), dim3(kRT), 0, st, n, rz_new, rz_old, z, p);
 }
 
 __global__ void k_fill(float* x, long long n, float value) {
+  pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
     x[i] = value;
 }
 
 void launch_fill(float* x, long long n, float value, cudaStream_t st) {
-  k_fill<<<nblocks(n), kRT, 0, st>>>(x, n, value); ++g_launch_count;
+  launch_k(k_fill, dim3(nblocks(n)), dim3(kRT), 0, st, x, n, value);
 }
 
 // SplitMix64 (Steele, Lea & Flood 2014): x[i] = uniform [-1, 1) from the
 // (i+1)-th output of the stream started at seed.
 __global__ void k_splitmix(float* x, long long n, unsigned long long seed) {
+  pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ULL;
@@ -231,7 +263,7 @@ __global__ void k_splitmix(float* x, long long n, unsigned long long seed) {
 }
 
 void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st) {
-  k_splitmix<<<nblocks(n), kRT, 0, st>>>(x, n, seed); ++g_launch_count;
+  launch_k(k_splitmix, dim3(nblocks(n)), dim3(kRT), 0, st, x, n, seed);
 }
 
 }  // namespace regnk

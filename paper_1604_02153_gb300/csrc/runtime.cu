@@ -21,6 +21,7 @@ using namespace regnk;
 
 namespace regnk {
 std::atomic<long long> g_launch_count{0};
+thread_local int t_programmatic_launch = 1;
 }
 
 namespace {
@@ -297,6 +298,14 @@ void drop_graphs(reg_ctx* c) {
   c->graph_cache.clear();
 }
 
+// Launch attribute of this context for the duration of one call (see
+// launch_k); restored when the call returns.
+struct LaunchModeScope {
+  int saved;
+  explicit LaunchModeScope(int mode) : saved(t_programmatic_launch) { t_programmatic_launch = mode; }
+  ~LaunchModeScope() { t_programmatic_launch = saved; }
+};
+
 // Runs `body` (a fixed sequence of launches on c->st, no host synchronisation)
 // as a CUDA graph: the first call of a key runs eagerly, the second captures
 // the sequence on a private stream, later calls replay it on c->st. Graphs
@@ -335,6 +344,9 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
     c->capturing = true;
     cudaGraph_t graph = nullptr;
     try {
+      // plain launches inside graphs: replays of graphs with programmatic
+      // edges measured slower than with ordinary kernel-to-kernel edges
+      LaunchModeScope plain(0);
       body();
     } catch (...) {
       // capture failed (e.g. a launch form the graph cannot hold): drop the
@@ -848,18 +860,11 @@ void cheb(reg_ctx* c, const float* rhs, float* x) {
   check(c, cudaMemcpyAsync(x, c->cd, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
   for (int it = 1; it < c->opt.cheb_iters; ++it) {
     coarse_op_u(c, c->cd, c->cAd);
-    {
-      Prof P(c, REG_KC_VECTOR, 12.0 * n);
-      launch_lincomb(n, 1.f, c->cr, -1.f, c->cAd, c->cr, c->st);
-    }
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     {
-      Prof P(c, REG_KC_VECTOR, 12.0 * n);
-      launch_lincomb(n, (float)(rho_new * rho), c->cd, (float)(2.0 * rho_new / delta), c->cr, c->cd, c->st);
-    }
-    {
-      Prof P(c, REG_KC_VECTOR, 12.0 * n);
-      launch_lincomb(n, 1.f, x, 1.f, c->cd, x, c->st);
+      Prof P(c, REG_KC_VECTOR, 28.0 * n);
+      launch_cheb_update(n, (float)(rho_new * rho), (float)(2.0 * rho_new / delta), c->cAd, c->cr,
+                         c->cd, x, c->st);
     }
     rho = rho_new;
   }
@@ -1035,8 +1040,10 @@ reg_status reject_unaligned(reg_ctx* c) {
   return REG_EINVAL;
 }
 
+
 reg_status guarded(reg_ctx* c, const std::function<void()>& body) {
   if (!c) return REG_EINVAL;
+  LaunchModeScope mode(c->opt.programmatic_launch ? 1 : 0);
   try {
     body();
     const cudaError_t e = cudaGetLastError();
@@ -1074,6 +1081,7 @@ reg_status reg_default_options(reg_options* o) {
   o->armijo_c1 = 1e-4;
   o->persistent_matvec = 0;
   o->inject_barrier_timeout = 0;
+  o->programmatic_launch = 1;
   return REG_OK;
 }
 

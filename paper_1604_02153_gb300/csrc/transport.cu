@@ -25,21 +25,16 @@ static int ilog2i(int n) {
   return (1 << l) == n ? l : -1;
 }
 
-// Launches KERNEL<true> on power-of-two grids, KERNEL<false> otherwise.
-#define REGNK_LAUNCH_P2(n1, n2, KERNEL, GRID, BLOCK, ST, ...)          \
-  do {                                                                 \
-    if (pow2_grid(n1, n2))                                             \
-      KERNEL<true><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);               \
-    else                                                               \
-      KERNEL<false><<<GRID, BLOCK, 0, ST>>>(__VA_ARGS__);              \
-    ++g_launch_count;                                                  \
-  } while (0)
+// The instantiation of a kernel template for the grid's index arithmetic.
+template <typename K>
+static K pick(int n1, int n2, K p2, K general) { return pow2_grid(n1, n2) ? p2 : general; }
 
 // One block per 32x32 output tile and field.
 template <bool P2>
 __global__ void __launch_bounds__(kPThreads)
 k_prefilter(const float* __restrict__ in, float* __restrict__ out, int n1, int n2, int log1,
             long long fstride) {
+  pdl_enter();
   __shared__ float sin_[kPH * kPIn];
   __shared__ float smid[kPH * kPMid];
   const long long fo = (long long)blockIdx.z * fstride;
@@ -50,8 +45,8 @@ k_prefilter(const float* __restrict__ in, float* __restrict__ out, int n1, int n
 void launch_prefilter(int n1, int n2, const float* in, float* tmp, float* out, int F,
                       cudaStream_t st) {
   (void)tmp;
-  REGNK_LAUNCH_P2(n1, n2, k_prefilter, dim3(n1 / kPX, n2 / kPY, F), kPThreads, st, in, out, n1,
-                  n2, ilog2i(n1), (long long)n1 * n2);
+  launch_k(pick(n1, n2, k_prefilter<true>, k_prefilter<false>), dim3(n1 / kPX, n2 / kPY, F),
+           dim3(kPThreads), 0, st, in, out, n1, n2, ilog2i(n1), (long long)n1 * n2);
 }
 
 constexpr int kPT = 256;  // threads per block of the pointwise kernels
@@ -65,6 +60,7 @@ __global__ void __launch_bounds__(kPT)
 k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restrict__ v,
             const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
             int lagrange) {
+  pdl_enter();
   const long long N = (long long)n1 * n2;
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
@@ -91,8 +87,8 @@ void launch_departure(int n1, int n2, float ht, const float* v, const float* cv,
   const long long N = (long long)n1 * n2;
   const float s1 = ht * n1 / (2.0f * 3.14159265358979323846f);
   const float s2 = ht * n2 / (2.0f * 3.14159265358979323846f);
-  REGNK_LAUNCH_P2(n1, n2, k_departure, (unsigned)((N + kPT - 1) / kPT), kPT, st, n1, n2,
-                  ilog2i(n1), s1, s2, v, cv, dX, dY, lagrange);
+  launch_k(pick(n1, n2, k_departure<true>, k_departure<false>), dim3((unsigned)((N + kPT - 1) / kPT)),
+           dim3(kPT), 0, st, n1, n2, ilog2i(n1), s1, s2, v, cv, dX, dY, lagrange);
 }
 
 // The step kernels below handle kSP horizontally adjacent points
@@ -154,6 +150,7 @@ __global__ void __launch_bounds__(kPT)
 k_gather(int n1, int n2, int log1, const float* __restrict__ coef,
          const float* __restrict__ disp, float* __restrict__ out, long long fstride,
          int lagrange) {
+  pdl_enter();
   const long long N = (long long)n1 * n2;
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
@@ -173,11 +170,8 @@ static void gather_f(int n1, int n2, const float* coef, const float* disp, float
                      long long fstride, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
   const unsigned nb = (unsigned)((N + kPT - 1) / kPT);
-  if (pow2_grid(n1, n2))
-    k_gather<true, F><<<nb, kPT, 0, st>>>(n1, n2, ilog2i(n1), coef, disp, out, fstride, lagrange);
-  else
-    k_gather<false, F><<<nb, kPT, 0, st>>>(n1, n2, -1, coef, disp, out, fstride, lagrange);
-  ++g_launch_count;
+  launch_k(pick(n1, n2, k_gather<true, F>, k_gather<false, F>), dim3(nb), dim3(kPT), 0, st, n1, n2,
+           ilog2i(n1), coef, disp, out, fstride, lagrange);
 }
 
 void launch_gather(int n1, int n2, const float* coef, const float* disp, float* out, int F,
@@ -201,6 +195,7 @@ __global__ void __launch_bounds__(kPT)
 k_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
                const float* __restrict__ m1, const float* __restrict__ gm,
                float* __restrict__ lam, float* __restrict__ b, float sign) {
+  pdl_enter();
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
   const float r = (mR ? __ldg(mR + idx) : 0.f) - __ldg(m1 + idx);
@@ -213,8 +208,8 @@ k_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
 void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const float* m1,
                          const float* gm, float* lam, float* b, float sign, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  k_adjoint_init<<<(unsigned)((N + kPT - 1) / kPT), kPT, 0, st>>>(N, coef_b, mR, m1, gm, lam,
-                                                                  b, sign); ++g_launch_count;
+  launch_k(k_adjoint_init, dim3((unsigned)((N + kPT - 1) / kPT)), dim3(kPT), 0, st, N, coef_b, mR,
+           m1, gm, lam, b, sign);
 }
 
 // One backward step of the (incremental) adjoint along Y_D (§3.3.2, Heun):
@@ -227,6 +222,7 @@ k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __rest
                const float* __restrict__ dY, const float* __restrict__ delta,
                const float* __restrict__ delta_bar, const float* __restrict__ gm,
                float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
+  pdl_enter();
   const long long N = (long long)n1 * n2;
   const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
   if (idx >= N) return;
@@ -266,8 +262,8 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  REGNK_LAUNCH_P2(n1, n2, k_adjoint_step, step_blocks(N), kPT, st, n1, n2, ilog2i(n1), ht, wb,
-                  coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
+  launch_k(pick(n1, n2, k_adjoint_step<true>, k_adjoint_step<false>), dim3(step_blocks(N)), dim3(kPT),
+           0, st, n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
 }
 
 // One forward step of the incremental state (Gauss-Newton, §3.3.2):
@@ -281,6 +277,7 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
                 const float* __restrict__ vtD, const float* __restrict__ G,
                 const float* __restrict__ gm, float* __restrict__ out, int first,
                 int lagrange) {
+  pdl_enter();
   const long long N = (long long)n1 * n2;
   const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
   if (idx >= N) return;
@@ -316,8 +313,8 @@ void launch_incstate_step(int n1, int n2, float ht, const float* coef, const flo
                           const float* vt, const float* vtD, const float* G, const float* gm,
                           float* out, int first, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  REGNK_LAUNCH_P2(n1, n2, k_incstate_step, step_blocks(N), kPT, st, n1, n2, ilog2i(n1), ht, coef,
-                  dX, vt, vtD, G, gm, out, first, lagrange);
+  launch_k(pick(n1, n2, k_incstate_step<true>, k_incstate_step<false>), dim3(step_blocks(N)),
+           dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange);
 }
 
 }  // namespace regnk

@@ -48,6 +48,7 @@ def test_default_options(lib):
     assert o.cheb_iters == 10 and abs(o.pc_eps - 0.1) < 1e-15
     assert abs(o.gabs - 1e-5) < 1e-20 and o.lanczos_steps == 30
     assert o.max_backtracks == 10 and abs(o.armijo_c1 - 1e-4) < 1e-20
+    assert o.persistent_matvec == 0 and o.programmatic_launch == 1
 
 
 def _create(lib, n1, n2, nt, beta, **kw):
