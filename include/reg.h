@@ -255,6 +255,66 @@ reg_status reg_batch_hessian_matvec(reg_batch* batch, const float* const* v,
                                     const float* const* vt, float* const* Hvt);
 const char* reg_batch_last_error(const reg_batch* batch);
 
+/* ---- Learned warm start (no counterpart in the paper) --------------------
+ * A U-Net maps an image pair (m_R, m_T) on an S x S grid to a stationary
+ * velocity v_0 from which reg_solve starts; the solve runs to the same
+ * gradient tolerance and is the judge of the result (reg_warm_start keeps
+ * v_0 only if J(v_0) < J(0)). Architecture: 4 levels with 32, 64, 128, 256
+ * channels, two periodic 3x3 convolutions + bias + ReLU per level, 2x2
+ * average pooling down, nearest-neighbour 2x upsampling up, skip
+ * concatenation [upsampled, encoder output], a last periodic 3x3
+ * convolution to the 2 velocity components. Forward, backward and Adam run
+ * in the library's kernels: convolutions are implicit GEMMs on the BF16
+ * tensor cores with FP32 accumulation; activations and their gradients are
+ * BF16, master weights, weight gradients and Adam moments FP32.
+ *
+ * Parameter layout (host float arrays of reg_unet_param_count() values): for
+ * each layer in the order enc0a (2->32), enc0b (32->32), enc1a (32->64),
+ * enc1b, enc2a (64->128), enc2b, enc3a (128->256), enc3b, dec2a (384->128),
+ * dec2b, dec1a (192->64), dec1b, dec0a (96->32), dec0b, out (32->2): the
+ * weights W[co][t][ci] with tap t = 3a + b reading the input at offset
+ * (a - 1, b - 1) in (row, column), then the biases b[co].
+ *
+ * Images and velocities use the single-problem layouts: a batch of B images
+ * is B*S*S floats, a batch of velocities B*2*S*S (per problem component 1
+ * then 2). `idx` (device int32, B entries, may be NULL for 0..B-1) selects
+ * the problems of a batch from larger arrays. Device buffers start on a
+ * 16-byte boundary. Calls run on the stream set by reg_unet_set_stream. */
+typedef struct reg_unet reg_unet;
+long long reg_unet_param_count(void);
+/* S: multiple of 32 in [32, 1024]; batch_max * S * S <= 2^26. Parameters
+ * start at zero: set them before use. */
+reg_status reg_unet_create(int S, int batch_max, reg_unet** out);
+reg_status reg_unet_destroy(reg_unet* net);
+int reg_unet_size(const reg_unet* net);
+reg_status reg_unet_set_stream(reg_unet* net, void* cuda_stream);
+/* host parameters in, Adam moments and step count reset; synchronises */
+reg_status reg_unet_set_params(reg_unet* net, const float* host_params);
+reg_status reg_unet_get_params(reg_unet* net, float* host_params);
+/* v = net(m_R, m_T) for B problems (v: B*2*S*S, device) */
+reg_status reg_unet_forward(reg_unet* net, int B, const int* idx, const float* m_R,
+                            const float* m_T, float* v);
+/* mean squared error L = mean (net(m_R, m_T) - v_target)^2 over all B*2*S*S
+ * values (*loss, host; may be NULL) and its gradient dL/dparams copied to
+ * host_grad (parameter layout; may be NULL). Parameters are not changed. */
+reg_status reg_unet_gradients(reg_unet* net, int B, const int* idx, const float* m_R,
+                              const float* m_T, const float* v_target, float* host_grad,
+                              double* loss);
+/* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, learning
+ * rate lr) on the loss of reg_unet_gradients; *loss (host, may be NULL) is
+ * the loss before the step */
+reg_status reg_unet_train_step(reg_unet* net, int B, const int* idx, const float* m_R,
+                               const float* m_T, const float* v_target, float lr, double* loss);
+const char* reg_unet_last_error(const reg_unet* net);
+
+/* Warm start for the context's images: restricts m_R, m_T spectrally to the
+ * network's grid (the problem grid must be square with S, 2S or 4S points
+ * per axis), evaluates the network, prolongs v_0 spectrally to the problem
+ * grid and writes it to v (device, 2*n1*n2) if J(v_0) < J(0), else writes
+ * v = 0. *accepted (host, may be NULL) = 1 if v_0 was kept. Uses the
+ * context's stream for the network too. */
+reg_status reg_warm_start(reg_ctx* ctx, reg_unet* net, float* v, int* accepted);
+
 /* ---- Allocation-free interpolation (no counterpart in the paper) ---------
  * For callers that must not allocate device memory while they run: code
  * whose device memory belongs to another framework's caching allocator (a

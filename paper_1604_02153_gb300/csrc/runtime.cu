@@ -490,6 +490,38 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
   check_launch(c, "spectral resampling");
 }
 
+// Spectral resampling of F fields between square grids of n_a and n_b =
+// n_a / 2 or 2 n_a points per axis (same truncation / zero padding as
+// resample(), for grids that are not levels of the context).
+void resample_square(reg_ctx* c, int na, int nb, const float* in, int F, float* out) {
+  const GridDims A = make_grid(na, na), B = make_grid(nb, nb);
+  float2* sin = c->fine.spec;
+  float2* sout = c->fine.spec + (size_t)F * A.spec;
+  fft_rows_r2c(na, na, in, A.N, sin, A.spec, F, twiddles(c, na), c->st);
+  ColArgs a{};
+  a.n1_in = a.n1 = na;
+  a.n2_in = a.n2 = na;
+  a.n1_out = nb;
+  a.n2_out = nb;
+  a.nk1_out = B.nk1;
+  a.op = SPOP_SCALE;
+  a.beta = 1.f;
+  a.p = 1;
+  a.s = 0.f;
+  a.scale = (float)(1.0 / (double)A.N);
+  a.tw_in = twiddles(c, na);
+  a.tw_out = twiddles(c, nb);
+  a.in = sin;
+  a.in_fstride = A.spec;
+  a.out = sout;
+  a.out_fstride = B.spec;
+  a.nin = 1;
+  a.nout = 1;
+  fft_cols(a, F, c->st);
+  fft_rows_c2r(nb, nb, sout, B.spec, out, B.N, nullptr, B.N, F, twiddles(c, nb), c->st);
+  check_launch(c, "spectral resampling");
+}
+
 // interpolation coefficients of F consecutive fields (prefilter for the
 // spline model; the samples themselves for Lagrange)
 const float* coefficients(reg_ctx* c, Level& L, const float* u, int F, float* dst) {
@@ -1418,6 +1450,57 @@ long long reg_launch_count(void) { return g_launch_count.load(); }
 reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
   if (!c || !a || !b || !out || n < 0) return REG_EINVAL;
   return guarded(c, [&] { *out = dot_sync(c, a, b, n, S_C); });
+}
+
+reg_status reg_warm_start(reg_ctx* c, reg_unet* net, float* v, int* accepted) {
+  if (!c || !net || !v) return REG_EINVAL;
+  if (unaligned({v})) return reject_unaligned(c);
+  return guarded(c, [&] {
+    require_images(c);
+    Level& F = c->fine;
+    const int S = reg_unet_size(net);
+    int n = F.g.n1, r = 0;
+    while (n > S && n % 2 == 0) {
+      n /= 2;
+      ++r;
+    }
+    if (F.g.n1 != F.g.n2 || n != S || r > 2)
+      fail(c, REG_EINVAL, "warm start needs a square grid of 1, 2 or 4 times the network's size");
+    const long long N = F.g.N;
+    // m_R, m_T restricted to the network's grid (scratch: F.w1, F.w2)
+    const float* mR = F.mR;
+    const float* mT = F.mT;
+    float* bufR[2] = {F.w1, F.w1 + N / 2};
+    float* bufT[2] = {F.w2, F.w2 + N / 2};
+    int m = F.g.n1;
+    for (int k = 0; k < r; ++k) {
+      resample_square(c, m, m / 2, mR, 1, bufR[k & 1]);
+      resample_square(c, m, m / 2, mT, 1, bufT[k & 1]);
+      mR = bufR[k & 1];
+      mT = bufT[k & 1];
+      m /= 2;
+    }
+    float* vs = r == 0 ? v : F.w2 + N;      // 2 S^2 floats
+    reg_unet_set_stream(net, c->st);
+    const reg_status s = reg_unet_forward(net, 1, nullptr, mR, mT, vs);
+    if (s != REG_OK) fail(c, s, "network: %s", reg_unet_last_error(net));
+    // prolongation of both velocity components back to the problem grid
+    const float* src = vs;
+    for (int k = 0; k < r; ++k) {
+      float* dst = (k == r - 1) ? v : F.w1 + N;
+      resample_square(c, m, 2 * m, src, 2, dst);
+      src = dst;
+      m *= 2;
+    }
+    // accepted only if it lowers the objective below J(0)
+    const double J1 = objective_gradient(c, v, nullptr);
+    launch_fill(c->vtrial, 2 * N, 0.f, c->st);
+    const double J0 = objective_gradient(c, c->vtrial, nullptr);
+    const int ok = (J1 < J0) ? 1 : 0;
+    if (!ok) launch_fill(v, 2 * N, 0.f, c->st);
+    if (accepted) *accepted = ok;
+    check(c, cudaStreamSynchronize(c->st), "warm start");
+  });
 }
 
 reg_status reg_solve(reg_ctx* c, float* v, double gtol, reg_info* info) {

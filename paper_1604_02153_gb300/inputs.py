@@ -18,7 +18,11 @@ intensities in [0, 1] and velocities of magnitude up to 0.5):
 * ``random_velocity``   - two such fields with modes 0 < |k| <= 4, scaled so
                           that max_x |v(x)|_2 equals a given value;
 * ``ellipse_phantoms``  - a pair of piecewise-smooth phantoms made of seeded
-                          random ellipses, blurred and normalised to [0, 1].
+                          random ellipses, blurred and normalised to [0, 1];
+* ``he_normal``         - seeded He-normal initial weights (zero biases) for
+                          a stack of 3x3 convolutions given their channel
+                          counts, in the flat parameter layout of the
+                          warm-start network.
 """
 
 import numpy as np
@@ -160,3 +164,14 @@ def splitmix64_uniform(count, seed):
         z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
         z = z ^ (z >> np.uint64(31))
     return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53) * 2.0 - 1.0
+
+
+def he_normal(shapes, seed):
+    """Flat parameters for 3x3 convolutions shapes = [(Cin, Cout), ...]:
+    per layer Cout*9*Cin weights ~ N(0, 2 / (9 Cin)), then Cout zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in shapes:
+        parts.append(rng.standard_normal(co * 9 * ci) * np.sqrt(2.0 / (9 * ci)))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)

@@ -99,6 +99,18 @@ _SIGNATURES = {
     "reg_batch_solve": [_P, ctypes.POINTER(_P), _D, _I, ctypes.POINTER(reg_info)],
     "reg_batch_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "reg_batch_last_error": [_P],
+    "reg_unet_param_count": [],
+    "reg_unet_create": [_I, _I, ctypes.POINTER(_P)],
+    "reg_unet_destroy": [_P],
+    "reg_unet_size": [_P],
+    "reg_unet_set_stream": [_P, _P],
+    "reg_unet_set_params": [_P, _P],
+    "reg_unet_get_params": [_P, _P],
+    "reg_unet_forward": [_P, _I, _P, _P, _P, _P],
+    "reg_unet_gradients": [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D)],
+    "reg_unet_train_step": [_P, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.POINTER(_D)],
+    "reg_unet_last_error": [_P],
+    "reg_warm_start": [_P, _P, _P, ctypes.POINTER(_I)],
 }
 
 _lib = None
@@ -116,7 +128,8 @@ def load(path=LIB_PATH):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = {"reg_last_error": ctypes.c_char_p, "reg_batch_last_error": ctypes.c_char_p,
-                      "reg_launch_count": ctypes.c_longlong}.get(name, ctypes.c_int)
+                      "reg_unet_last_error": ctypes.c_char_p, "reg_launch_count": ctypes.c_longlong,
+                      "reg_unet_param_count": ctypes.c_longlong}.get(name, ctypes.c_int)
     _lib = lib
     return lib
 
@@ -237,6 +250,13 @@ class Registration:
         self._call("reg_eigen_bounds", ctypes.byref(lo), ctypes.byref(hi))
         return lo.value, hi.value
 
+    def warm_start(self, net, v):
+        """reg_warm_start: v <- net(m_R, m_T) prolonged to this grid if it lowers
+        J below J(0), else 0. Returns True if the network's velocity was kept."""
+        acc = ctypes.c_int(0)
+        self._call("reg_warm_start", net.h, _ptr(v, 2 * self.N, "v"), ctypes.byref(acc))
+        return bool(acc.value)
+
     def solve(self, v, gtol, allow=(REG_OK,)):
         import torch
         info = reg_info()
@@ -340,6 +360,89 @@ class Batch:
 
 
 REG_STATIC_MAX_POINTS = 1024 * 1024
+
+
+class UNet:
+    """reg_unet: the warm-start U-Net (S x S grid, batches up to batch_max).
+
+    Parameters move as flat float32 numpy arrays in the layout of
+    include/reg.h; images and velocities are contiguous float32 CUDA tensors
+    of B*S*S and B*2*S*S values; idx (optional) is an int32 CUDA tensor of
+    problem indices into larger arrays."""
+
+    def __init__(self, size, batch_max):
+        self.lib = load()
+        self.S, self.bmax = int(size), int(batch_max)
+        h = ctypes.c_void_p()
+        s = self.lib.reg_unet_create(self.S, self.bmax, ctypes.byref(h))
+        if s != REG_OK:
+            raise RegError(s, "reg_unet_create failed")
+        self.h = h
+
+    @staticmethod
+    def param_count():
+        return int(load().reg_unet_param_count())
+
+    def _call(self, name, *args):
+        import torch
+        self.lib.reg_unet_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = getattr(self.lib, name)(self.h, *args)
+        if s != REG_OK:
+            raise RegError(s, self.lib.reg_unet_last_error(self.h).decode())
+
+    def _idx(self, idx, B):
+        import torch
+        if idx is None:
+            return None
+        if not (isinstance(idx, torch.Tensor) and idx.is_cuda and idx.dtype == torch.int32
+                and idx.is_contiguous() and idx.numel() == B):
+            raise TypeError("idx must be a contiguous int32 CUDA tensor of B entries")
+        return ctypes.c_void_p(idx.data_ptr())
+
+    def set_params(self, theta):
+        import numpy as np
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.param_count():
+            raise ValueError(f"{a.size} parameters, expected {self.param_count()}")
+        self._call("reg_unet_set_params", a.ctypes.data_as(ctypes.c_void_p))
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.param_count(), dtype=np.float32)
+        self._call("reg_unet_get_params", a.ctypes.data_as(ctypes.c_void_p))
+        return a
+
+    def forward(self, B, m_R, m_T, v, idx=None):
+        self._call("reg_unet_forward", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+                   _ptr(m_T, name="m_T"), _ptr(v, 2 * B * self.S * self.S, "v"))
+
+    def gradients(self, B, m_R, m_T, v_target, idx=None):
+        """(loss, dL/dparams as a float32 numpy array)."""
+        import numpy as np
+        g = np.empty(self.param_count(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._call("reg_unet_gradients", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+                   _ptr(m_T, name="m_T"), _ptr(v_target, name="v_target"),
+                   g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss))
+        return loss.value, g
+
+    def train_step(self, B, m_R, m_T, v_target, lr, idx=None):
+        loss = ctypes.c_double()
+        self._call("reg_unet_train_step", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+                   _ptr(m_T, name="m_T"), _ptr(v_target, name="v_target"), ctypes.c_float(lr),
+                   ctypes.byref(loss))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.lib.reg_unet_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def interpolate_static(n1, n2, u, disp, out):

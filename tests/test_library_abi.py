@@ -93,3 +93,15 @@ def test_static_interpolation_rejects_unaligned_buffers(lib):
     ok, off = ctypes.c_void_p(1 << 20), ctypes.c_void_p((1 << 20) + 4)
     for u, d, o in [(off, ok, ok), (ok, off, ok), (ok, ok, off)]:
         assert lib.reg_interpolate_static(64, 64, u, d, o, None) == regnk.REG_EINVAL
+
+
+def test_unet_arguments_and_no_cpu_fallback(lib):
+    import torch
+    h = ctypes.c_void_p()
+    assert lib.reg_unet_create(48, 1, ctypes.byref(h)) == regnk.REG_EINVAL      # not a multiple of 32
+    assert lib.reg_unet_create(256, 0, ctypes.byref(h)) == regnk.REG_EINVAL
+    assert lib.reg_unet_create(1024, 128, ctypes.byref(h)) == regnk.REG_EINVAL  # over 2^26 pixels
+    assert lib.reg_unet_param_count() == 1947138
+    assert lib.reg_warm_start(None, None, None, None) == regnk.REG_EINVAL
+    if not torch.cuda.is_available():
+        assert lib.reg_unet_create(32, 1, ctypes.byref(h)) == regnk.REG_ECUDA and not h.value
