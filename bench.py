@@ -25,6 +25,11 @@ roofline  = the kernel class with the largest device time: algorithmic
             copy bandwidth.
 cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
             timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
+learned_warm_start = the trained warm-start network (weights committed with
+            the package) measured outside the timed region: cold versus warm
+            time to ||g||rel 1e-2 on held-out pairs of the learned-warm-start
+            configuration at 1024^2 (nt = 4, beta = 1e-2), and one
+            warm-started solve of the phantom workload above.
 """
 
 import argparse
@@ -64,6 +69,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
                     help="preconditioner of the solve (the workload's is 2l-cheb)")
     ap.add_argument("--persistent", type=int, choices=[0, 1], default=0,
@@ -319,6 +326,65 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_warm_start(R, v, ok, dev, pairs=4):
+    """Cold versus warm start (see the module doc). Each solve is timed alone
+    between device synchronisations."""
+    import torch
+    from paper_1604_02153_gb300 import regnk, warmstart
+    theta, record = warmstart.load_params()
+    net = regnk.UNet(warmstart.S, 1)
+    net.set_params(theta)
+    n = 4 * warmstart.S
+    seeds = np.arange(warmstart.HELD_OUT_SEED0, warmstart.HELD_OUT_SEED0 + pairs)
+    mR, mT, _ = warmstart.make_pairs(n, seeds, procs=1)
+    Rh = regnk.Registration(n, n, warmstart.NT, warmstart.BETA)
+    vh = torch.empty(2 * n * n, device=dev)
+    rows = {"cold": [], "warm": []}
+    accepted = 0
+    for i in range(pairs):
+        Rh.set_images(mR[i], mT[i])
+        for mode in ("cold", "warm", "cold", "warm"):     # second pass is measured
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "warm":
+                acc = Rh.warm_start(net, vh)
+            else:
+                vh.zero_()
+            info = Rh.solve(vh, warmstart.GTOL, allow=ok)
+            torch.cuda.synchronize()
+            rows[mode].append((time.perf_counter() - t0, info["newton_iters"], info["matvecs"]))
+        accepted += int(acc)
+    Rh.close()
+    held = {"pairs": pairs, "grid": [n, n], "nt": warmstart.NT, "beta": warmstart.BETA,
+            "warm_start_accepted": accepted}
+    for mode in ("cold", "warm"):
+        r = np.array(rows[mode][1::2])
+        held[mode] = {"time_to_solution_s": float(r[:, 0].mean()),
+                      "newton_iters": float(r[:, 1].mean()), "matvecs": float(r[:, 2].mean())}
+    held["speedup_wall"] = held["cold"]["time_to_solution_s"] / held["warm"]["time_to_solution_s"]
+    # the phantom workload, warm started at the first beta
+    stats = {"matvecs": 0, "newton": 0}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    acc = False
+    for b in BETAS:
+        R.set_beta(b)
+        if b == BETAS[0]:
+            acc = R.warm_start(net, v)
+        info = R.solve(v, GTOL, allow=ok)
+        stats["matvecs"] += info["matvecs"]
+        stats["newton"] += info["newton_iters"]
+    torch.cuda.synchronize()
+    ph = {"warm_start_accepted": bool(acc), "time_to_solution_s": time.perf_counter() - t0,
+          "newton_iters_per_solve": stats["newton"], "matvecs_per_solve": stats["matvecs"]}
+    net.close()
+    return {"network": "U-Net 4 levels, 32 base channels, BF16 (weights/unet256.npz)",
+            "training": {k: record[k] for k in ("pairs", "epochs", "batch", "seconds_training",
+                                                "train_steps_per_second")},
+            "final_training_loss": record["loss_per_epoch"][-1],
+            "heldout_1024": held, "phantom1024": ph}
+
+
 def main():
     args = parse()
     rank, local_rank, world = dist_env()
@@ -468,6 +534,8 @@ def main():
                 "clocks": clocks.summary()}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        if not args.no_warm_start:
+            line["learned_warm_start"] = learned_warm_start(R, v, ok, dev)
         print(json.dumps(line), flush=True)
     R.close()
     if dist is not None:

@@ -31,7 +31,11 @@ def main():
     ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--pcg", action="store_true")
     ap.add_argument("--pdl", type=int, default=1, help="programmatic_launch option (0 or 1)")
+    ap.add_argument("--unet", type=int, default=0,
+                    help="instead: this many warm-start network training steps (batch 8, 256^2)")
     a = ap.parse_args()
+    if a.unet:
+        return unet_case(a.unet)
     import numpy as np
     import torch
 
@@ -89,6 +93,30 @@ def main():
         print(f"n={n} PCG {info['pcg_iters']} iterations {1e3 * dk / max(1, info['pcg_iters']):.3f} "
               f"ms per iteration (graph replay of matvec and P_2L)")
     R.close()
+
+
+def unet_case(steps):
+    """Forward passes and training steps of the warm-start network on a batch
+    of 8 random 256^2 pairs (He-normal weights); prints the time per step."""
+    import torch
+    from paper_1604_02153_gb300 import inputs, regnk, warmstart
+    S, B = warmstart.S, 8
+    net = regnk.UNet(S, B)
+    net.set_params(inputs.he_normal(warmstart.SHAPES, seed=1))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    mR = torch.rand(B * S * S, device="cuda", generator=g)
+    mT = torch.rand(B * S * S, device="cuda", generator=g)
+    vt = 0.1 * torch.randn(B * 2 * S * S, device="cuda", generator=g)
+    v = torch.empty(B * 2 * S * S, device="cuda")
+    net.forward(B, mR, mT, v)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        net.train_step(B, mR, mT, vt, 1e-4)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    print(f"U-Net S={S} B={B}: {1e3 * dt:.3f} ms per training step (wall)")
+    net.close()
 
 
 if __name__ == "__main__":

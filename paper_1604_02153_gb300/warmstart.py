@@ -67,19 +67,25 @@ def host_fields(n, seeds, procs):
     return np.stack([o[0] for o in out]), np.stack([o[1] for o in out])
 
 
-def make_pairs(n, seeds, procs=8):
-    """Device arrays m_R [P, n*n], m_T [P, n*n] and v* [P, 2*n*n] (float32)."""
+def make_pairs(n, seeds, procs=8, chunk=1024):
+    """Device arrays m_R [P, n*n], m_T [P, n*n] and v* [P, 2*n*n] (float32),
+    generated in chunks of `chunk` pairs."""
     import torch
     from paper_1604_02153_gb300 import regnk
-    mT_h, vs_h = host_fields(n, seeds, procs)
     P = len(seeds)
-    mT = torch.tensor(mT_h.reshape(P, n * n), device="cuda")
-    vs = torch.tensor(vs_h.reshape(P, 2 * n * n), device="cuda")
+    mT = torch.empty(P, n * n, device="cuda")
+    vs = torch.empty(P, 2 * n * n, device="cuda")
     mR = torch.empty_like(mT)
     R = regnk.Registration(n, n, NT, BETA, precond=regnk.REG_PC_REG)
-    R.set_images(mT[0], mT[0])
-    for i in range(P):
-        R.transport(vs[i], mT[i], mR[i])
+    for p0 in range(0, P, chunk):
+        p1 = min(P, p0 + chunk)
+        mT_h, vs_h = host_fields(n, seeds[p0:p1], procs)
+        mT[p0:p1].copy_(torch.from_numpy(mT_h.reshape(p1 - p0, n * n)))
+        vs[p0:p1].copy_(torch.from_numpy(vs_h.reshape(p1 - p0, 2 * n * n)))
+        if p0 == 0:
+            R.set_images(mT[0], mT[0])
+        for i in range(p0, p1):
+            R.transport(vs[i], mT[i], mR[i])
     torch.cuda.synchronize()
     R.close()
     return mR, mT, vs
