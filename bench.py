@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coarse-nt", type=int, default=0,
+                    help="time steps of the P_2L coarse problem (0: the problem's nt)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
@@ -218,9 +220,11 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(precond="2l-cheb"):
+def workload_config(precond="2l-cheb", coarse_nt=0):
     pc = {"2l-cheb": "P_2L CHEB(10) 512^2 coarse", "2l-pcg": "P_2L PCG(1e-1) 512^2 coarse",
           "reg": "P_REG"}[precond]
+    if coarse_nt and precond != "reg":
+        pc += f" nt={coarse_nt}"
     return {"workload": f"phantom pair {N_GRID}x{N_GRID} (12 random ellipses, sigma 2 px), "
                         f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, {pc}, "
                         f"||g||rel 1e-2, cubic B-spline SL",
@@ -419,7 +423,8 @@ def main():
     pc_opts = {"2l-cheb": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_CHEB),
                "2l-pcg": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_PCG),
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
-    R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent, **pc_opts)
+    R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
+                           coarse_nt=args.coarse_nt, **pc_opts)
     R.set_images(d_mR, d_mT)
     v = torch.zeros(2 * n * n, device=dev)
     h_v = torch.empty(2 * n * n).pin_memory()
@@ -518,7 +523,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(args.precond),
+                "config": workload_config(args.precond, args.coarse_nt),
                 "time_to_solution_s": total_ms / args.steps / 1e3,
                 "newton_iters_per_solve": stats["newton"] / args.steps,
                 "matvecs_per_solve": stats["matvecs"] / args.steps,

@@ -100,6 +100,19 @@ typedef struct {
                               results are identical); kernels inside the
                               library's CUDA graphs are plain launches either
                               way. 0: plain launches everywhere                */
+  int fused_transport;     /* 1 (default): with the spline model, the GN matvec's
+                              incremental state and adjoint steps compute the
+                              spline coefficients they gather from inside the step
+                              kernel (a 48^2 or 64^2 coefficient box per 32^2 tile)
+                              whenever the velocity's displacements fit the box's
+                              halo (<= 6 or <= 14 cells); results are those of the
+                              separate prefilter kernel up to FP32 rounding order.
+                              0: always a separate prefilter kernel             */
+  int coarse_nt;           /* time steps of the coarse-grid problem of P_2L; 0
+                              (default): the problem's nt. §3.4.2 expects the
+                              preconditioner's PDE solves to need little
+                              accuracy; nt / 2 keeps the displacement per step
+                              in coarse cells equal to the fine grid's         */
 } reg_options;
 
 typedef struct {

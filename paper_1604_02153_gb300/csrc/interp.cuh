@@ -136,6 +136,74 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
   }
 }
 
+// Spline coefficients of one field on the W x W box of nodes whose first
+// node is (bx0, by0) (periodic), left in shared memory for a gather that
+// follows in the same block: box[r * (W + 1) + c] is the coefficient of node
+// (bx0 + c, by0 + r). The box's samples with a kL-sample halo are staged in
+// `stage` ((W + 2 kL) rows of pitch W + 2 kL + 1) and the x pass goes to
+// `mid` ((W + 2 kL) rows of pitch W + 1); `box` may alias `stage`. Same
+// recursions and segment length as prefilter_tile, so the coefficients are
+// those of k_prefilter up to the order of FP32 rounding. Ends with a block
+// barrier.
+template <int W>
+struct BoxDims {
+  static constexpr int WS = W + 2 * kL;   // staged width and height
+  static constexpr int PS = WS + 1;       // odd pitches
+  static constexpr int PB = W + 1;
+  static constexpr int kStage = WS * PS;  // floats
+  static constexpr int kMid = WS * PB;
+  static constexpr size_t kSmemBytes = sizeof(float) * (kStage + kMid);
+};
+
+template <int W, bool P2>
+__device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int n1, int n2,
+                                              int log1, int bx0, int by0, float* stage,
+                                              float* mid, float* box) {
+  using D = BoxDims<W>;
+  constexpr int WS = D::WS, PS = D::PS, PB = D::PB;
+  constexpr int kLoads = (WS * WS + kPThreads - 1) / kPThreads;
+  const int t = threadIdx.x;
+  float ld_[kLoads];
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * kPThreads;
+    if (q < WS * WS) {
+      const int r = q / WS, c = q - r * WS;
+      const int gx = P2 ? wrap_index<true>(bx0 - kL + c, n1) : wrap_once(bx0 - kL + c, n1);
+      const int gy = P2 ? wrap_index<true>(by0 - kL + r, n2) : wrap_once(by0 - kL + r, n2);
+      ld_[u] = __ldg(src + row_offset<P2>(gy, n1, log1) + gx);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * kPThreads;
+    if (q < WS * WS) {
+      const int r = q / WS, c = q - r * WS;
+      stage[r * PS + c] = ld_[u];
+    }
+  }
+  __syncthreads();
+  constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
+  for (int q = t; q < WS * kSegs; q += kPThreads) {   // x recursions
+    const int r = q / kSegs, sg = q - r * kSegs;
+    float v[kLen];
+#pragma unroll
+    for (int k = 0; k < kLen; ++k) v[k] = stage[r * PS + sg * kSeg + k];
+    float* row = mid + r * PB + sg * kSeg;
+    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { row[o] = x; });
+  }
+  __syncthreads();
+  for (int q = t; q < W * kSegs; q += kPThreads) {    // y recursions
+    const int c = q % W, sg = q / W;
+    float v[kLen];
+#pragma unroll
+    for (int k = 0; k < kLen; ++k) v[k] = mid[(sg * kSeg + k) * PB + c];
+    float* col = box + sg * kSeg * PB + c;
+    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { col[o * PB] = x; });
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // 4x4 periodic cubic interpolation at node (i, j) + (d1, d2) cells.
 struct Stencil {
@@ -190,6 +258,22 @@ __device__ __forceinline__ float apply_stencil(const Stencil& S, const float* __
     const float r = S.w1[0] * ld<COHERENT>(row + S.ii[0]) + S.w1[1] * ld<COHERENT>(row + S.ii[1]) +
                     S.w1[2] * ld<COHERENT>(row + S.ii[2]) + S.w1[3] * ld<COHERENT>(row + S.ii[3]);
     acc = fmaf(S.w2[b], r, acc);
+  }
+  return acc;
+}
+
+// The 4x4 sum of apply_stencil over coefficients held in a shared-memory box
+// of pitch PB: node (i0 + a, j0 + b) of the stencil is box entry
+// (li + a, lj + b). The caller clamps li, lj to [0, W - 4].
+template <int PB>
+__device__ __forceinline__ float apply_box(const float* box, int li, int lj, const float (&w1)[4],
+                                           const float (&w2)[4]) {
+  float acc = 0.f;
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    const float* row = box + (lj + b) * PB + li;
+    const float r = w1[0] * row[0] + w1[1] * row[1] + w1[2] * row[2] + w1[3] * row[3];
+    acc = fmaf(w2[b], r, acc);
   }
   return acc;
 }

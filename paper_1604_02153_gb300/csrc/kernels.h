@@ -105,6 +105,18 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
                          const float* dY, const float* delta, const float* delta_bar,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st);
+// Fused prefilter + step kernels (transport.cu). fused_box_width gives the
+// box width (48 or 64) whose halo covers displacements up to max_disp_cells,
+// or 0 if none does; fused_init raises the kernels' shared-memory limit
+// (call once per device before the first launch).
+int fused_box_width(double max_disp_cells);
+void fused_init();
+void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float* lam_next,
+                          const float* dY, const float* delta, const float* delta_bar,
+                          const float* gm, float* lam_out, float* b, cudaStream_t st);
+void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
+                           const float* vt, const float* vtD, const float* G, const float* gm,
+                           float* out, cudaStream_t st);
 void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
                           const float* vt, const float* vtD, const float* G,
                           const float* gm, float* out, int first, int lagrange,

@@ -29,7 +29,7 @@ namespace {
 constexpr int kSpecSlots = 8;    // spectra in the FFT workspace of a level
 constexpr int kScalars = 32;     // FP64 device scalar slots
 
-enum Slot { S_A = 0, S_B, S_C, S_D, S_E, S_GINF, S_G2, S_J1, S_J2,
+enum Slot { S_A = 0, S_B, S_C, S_D, S_E, S_GINF, S_G2, S_J1, S_J2, S_DX, S_DY,
             S_PCG_OUTER = 16, S_PCG_INNER = 24 };
 // offsets of the PCG scalars inside a PCG slot block
 enum PcgSlot { P_RZ = 0, P_RZNEW, P_PQ, P_RR, P_BB };
@@ -68,6 +68,7 @@ struct Level {
   bool have_gm = false;     // grad history valid for v
   bool have_div = false;    // delta, delta_bar, dY valid for v
   bool have_G = false;      // G valid for v
+  int fuse_w = 0;           // box width of the fused prefilter+step kernels for v (0: off)
 };
 
 }  // namespace
@@ -399,9 +400,11 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
   return false;
 }
 
-std::string graph_key(const char* what, const void* a, const void* b) {
-  char buf[96];
-  snprintf(buf, sizeof buf, "%s:%p:%p", what, a, b);
+// the key names the buffers and the fused-kernel box widths of both levels
+// (a launch sequence recorded for one width must not replay for another)
+std::string graph_key(const reg_ctx* c, const char* what, const void* a, const void* b) {
+  char buf[128];
+  snprintf(buf, sizeof buf, "%s:%p:%p:%d:%d", what, a, b, c->fine.fuse_w, c->coarse.fuse_w);
   return buf;
 }
 
@@ -581,6 +584,18 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
     Prof P(c, REG_KC_DEPARTURE, 32.0 * N);
     launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, lagrange(c), c->st);
   }
+  // largest displacement component (cells): decides whether the fused
+  // prefilter+step kernels' coefficient box covers every stencil
+  L.fuse_w = 0;
+  if (!lagrange(c) && c->opt.fused_transport) {
+    {
+      Prof P(c, REG_KC_REDUCE, 16.0 * N);
+      launch_maxabs(L.dX, 2 * (long long)N, c->partialf, slot(c, S_DX), c->st);
+      launch_maxabs(L.dY, 2 * (long long)N, c->partialf, slot(c, S_DY), c->st);
+    }
+    read_slots(c, S_DX, 2);
+    L.fuse_w = fused_box_width(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
+  }
   check(c, cudaMemcpyAsync(L.m, L.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
   for (int j = 1; j <= L.nt; ++j) {
     const float* cm = coefficients(c, L, L.m + (j - 1) * N, 1, L.coef);
@@ -752,6 +767,13 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   float* mt = L.fA;
   float* mt2 = L.fB;
   for (int j = 1; j <= nt; ++j) {
+    if (j > 1 && L.fuse_w) {   // prefilter of m~_{j-1} inside the step kernel
+      Prof P(c, REG_KC_INCSTATE_STEP, 48.0 * N);
+      launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, mt, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                            L.gm + 2 * j * N, mt2, c->st);
+      std::swap(mt, mt2);
+      continue;
+    }
     const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
     {
       Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 36.0 : 48.0) * N);
@@ -770,6 +792,13 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   float* lt2 = mt;
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    if (L.fuse_w) {   // prefilter of lambda~_{j+1} inside the step kernel
+      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lt, L.dY, L.delta, L.delta_bar,
+                           L.gm + 2 * j * N, lt2, L.b, c->st);
+      std::swap(lt, lt2);
+      continue;
+    }
     const float* cl = coefficients(c, L, lt, 1, L.coef);
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
@@ -1014,11 +1043,11 @@ PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
   }
   ensure_G(c, F);
   auto A = [&](const float* p, float* q) {
-    graphed(c, graph_key("mv", p, q), [&] { hessian_core(c, F, p, q, false); });
+    graphed(c, graph_key(c, "mv", p, q), [&] { hessian_core(c, F, p, q, false); });
   };
   auto M = [&](const float* r, float* z) {
     if (c->two_level && c->opt.pc_solver == REG_PCSOLVER_CHEB) {
-      if (!graphed(c, graph_key("pc", r, z), [&] { precond(c, r, z); }))
+      if (!graphed(c, graph_key(c, "pc", r, z), [&] { precond(c, r, z); }))
         c->coarse_matvecs += c->opt.cheb_iters - 1;   // replayed: count its coarse matvecs
     } else
       precond(c, r, z);
@@ -1114,6 +1143,8 @@ reg_status reg_default_options(reg_options* o) {
   o->persistent_matvec = 0;
   o->inject_barrier_timeout = 0;
   o->programmatic_launch = 1;
+  o->fused_transport = 1;
+  o->coarse_nt = 0;
   return REG_OK;
 }
 
@@ -1130,7 +1161,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   if (opt) o = *opt; else reg_default_options(&o);
   if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
       (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
-      o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0)
+      o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0 ||
+      o.coarse_nt < 0 || o.coarse_nt > 4096)
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1145,8 +1177,10 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->two_level = (o.precond == REG_PC_2L);
   c->persistent = (o.persistent_matvec != 0);
   const reg_status s = guarded(c, [&] {
+    fused_init();   // shared-memory limit of the fused step kernels on this device
     alloc_level(c, c->fine, grid.n1, grid.n2, nt);
-    if (c->two_level) alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, nt);
+    if (c->two_level)
+      alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, o.coarse_nt > 0 ? o.coarse_nt : nt);
     check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
     c->dsc = dalloc<double>(c, kScalars);
     void* h = nullptr;

@@ -317,4 +317,163 @@ void launch_incstate_step(int n1, int n2, float ht, const float* coef, const flo
            dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange);
 }
 
+// ---------------------------------------------------------------------------
+// Fused steps: the spline prefilter of the field being transported and the
+// step that gathers it, in one kernel. A block owns a 32x32 tile of output
+// points. Every stencil of the tile lies in the W x W box of nodes that
+// extends the tile by H = (W - 32) / 2 on each side when all displacements
+// satisfy |d| <= H - 2 cells (the host checks the velocity's largest
+// displacement before choosing this path). The block computes the spline
+// coefficients of that box from the raw samples (prefilter_box, with the
+// same recursion segments as k_prefilter since H is a multiple of 8, so the
+// coefficients and the results are bitwise those of the two-kernel path)
+// and gathers from shared memory. Each thread handles 4 consecutive points
+// of a tile row, with float4 streamed loads.
+
+template <int W>
+__device__ __forceinline__ void box_stencil(int lx, int ly, float d1, float d2, bool lagrange,
+                                            int& li, int& lj, float (&w1)[4], float (&w2)[4]) {
+  const float f1 = floorf(d1), f2 = floorf(d2);
+  cubic_weights(d1 - f1, w1, lagrange);
+  cubic_weights(d2 - f2, w2, lagrange);
+  li = min(max(lx + (int)f1 - 1, 0), W - 4);
+  lj = min(max(ly + (int)f2 - 1, 0), W - 4);
+}
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4_rw(const float* p) {
+  return *reinterpret_cast<const float4*>(p);
+}
+__device__ __forceinline__ float at(const float4& v, int k) {
+  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+template <bool P2, int W>
+__global__ void __launch_bounds__(kPThreads)
+k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
+                const float* __restrict__ dY, const float* __restrict__ delta,
+                const float* __restrict__ delta_bar, const float* __restrict__ gm,
+                float* __restrict__ lam_out, float* __restrict__ b) {
+  pdl_enter();
+  using D = BoxDims<W>;
+  constexpr int H = (W - 32) / 2;
+  extern __shared__ float sm[];
+  float* stage = sm;
+  float* mid = sm + D::kStage;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  prefilter_box<W, P2>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  const long long N = (long long)n1 * n2;
+  const int t = threadIdx.x, r = t >> 3, cx = (t & 7) * 4;
+  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  const float4 y1 = ld4(dY + idx), y2 = ld4(dY + N + idx);
+  const float4 db = ld4(delta_bar + idx), dd = ld4(delta + idx);
+  const float4 g1 = ld4(gm + idx), g2 = ld4(gm + N + idx);
+  const float4 b1 = ld4_rw(b + idx), b2 = ld4_rw(b + N + idx);
+  float l[4], o1[4], o2[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int li, lj;
+    float w1[4], w2[4];
+    box_stencil<W>(H + cx + p, H + r, at(y1, p), at(y2, p), false, li, lj, w1, w2);
+    const float lb = apply_box<D::PB>(stage, li, lj, w1, w2);
+    const float lstar = fmaf(ht * lb, at(db, p), lb);
+    l[p] = lb + 0.5f * ht * (lb * at(db, p) + lstar * at(dd, p));
+    o1[p] = fmaf(wb * l[p], at(g1, p), at(b1, p));
+    o2[p] = fmaf(wb * l[p], at(g2, p), at(b2, p));
+  }
+  *reinterpret_cast<float4*>(lam_out + idx) = make_float4(l[0], l[1], l[2], l[3]);
+  *reinterpret_cast<float4*>(b + idx) = make_float4(o1[0], o1[1], o1[2], o1[3]);
+  *reinterpret_cast<float4*>(b + N + idx) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+}
+
+template <bool P2, int W>
+__global__ void __launch_bounds__(kPThreads)
+k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
+                 const float* __restrict__ dX, const float* __restrict__ vt,
+                 const float* __restrict__ vtD, const float* __restrict__ G,
+                 const float* __restrict__ gm, float* __restrict__ out) {
+  pdl_enter();
+  using D = BoxDims<W>;
+  constexpr int H = (W - 32) / 2;
+  extern __shared__ float sm[];
+  float* stage = sm;
+  float* mid = sm + D::kStage;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  prefilter_box<W, P2>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  const long long N = (long long)n1 * n2;
+  const int t = threadIdx.x, r = t >> 3, cx = (t & 7) * 4;
+  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  const float4 x1 = ld4(dX + idx), x2 = ld4(dX + N + idx);
+  const float4 w1v = ld4(vtD + idx), w2v = ld4(vtD + N + idx);
+  const float4 G1 = ld4(G + idx), G2 = ld4(G + N + idx);
+  const float4 u1 = ld4(vt + idx), u2 = ld4(vt + N + idx);
+  const float4 g1 = ld4(gm + idx), g2 = ld4(gm + N + idx);
+  float m[4];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    int li, lj;
+    float w1[4], w2[4];
+    box_stencil<W>(H + cx + p, H + r, at(x1, p), at(x2, p), false, li, lj, w1, w2);
+    m[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
+    m[p] -= 0.5f * ht * (at(w1v, p) * at(G1, p) + at(w2v, p) * at(G2, p) + at(u1, p) * at(g1, p) +
+                         at(u2, p) * at(g2, p));
+  }
+  *reinterpret_cast<float4*>(out + idx) = make_float4(m[0], m[1], m[2], m[3]);
+}
+
+// box widths with a fused kernel: halo H = 8 and H = 16
+constexpr int kFuseW[2] = {48, 64};
+
+int fused_box_width(double max_disp_cells) {
+  for (int W : kFuseW)
+    if (max_disp_cells <= (double)((W - 32) / 2 - 2)) return W;
+  return 0;
+}
+
+template <typename K>
+static void allow_smem(K kernel, size_t bytes) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+void fused_init() {
+  allow_smem(k_adjoint_fused<true, 48>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_adjoint_fused<false, 48>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_adjoint_fused<true, 64>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_adjoint_fused<false, 64>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_incstate_fused<true, 48>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_incstate_fused<false, 48>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_incstate_fused<true, 64>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_incstate_fused<false, 64>, BoxDims<64>::kSmemBytes);
+}
+
+void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float* lam_next,
+                          const float* dY, const float* delta, const float* delta_bar,
+                          const float* gm, float* lam_out, float* b, cudaStream_t st) {
+  const dim3 grid(n1 / 32, n2 / 32);
+  const bool p2 = pow2_grid(n1, n2);
+  if (W == 48)
+    launch_k(p2 ? k_adjoint_fused<true, 48> : k_adjoint_fused<false, 48>, grid, dim3(kPThreads),
+             BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta, delta_bar,
+             gm, lam_out, b);
+  else
+    launch_k(p2 ? k_adjoint_fused<true, 64> : k_adjoint_fused<false, 64>, grid, dim3(kPThreads),
+             BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta, delta_bar,
+             gm, lam_out, b);
+}
+
+void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
+                           const float* vt, const float* vtD, const float* G, const float* gm,
+                           float* out, cudaStream_t st) {
+  const dim3 grid(n1 / 32, n2 / 32);
+  const bool p2 = pow2_grid(n1, n2);
+  if (W == 48)
+    launch_k(p2 ? k_incstate_fused<true, 48> : k_incstate_fused<false, 48>, grid, dim3(kPThreads),
+             BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
+  else
+    launch_k(p2 ? k_incstate_fused<true, 64> : k_incstate_fused<false, 64>, grid, dim3(kPThreads),
+             BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
+}
+
 }  // namespace regnk

@@ -31,6 +31,7 @@ def main():
     ap.add_argument("--persistent", type=int, default=0)
     ap.add_argument("--pcg", action="store_true")
     ap.add_argument("--pdl", type=int, default=1, help="programmatic_launch option (0 or 1)")
+    ap.add_argument("--fused", type=int, default=1, help="fused_transport option (0 or 1)")
     ap.add_argument("--unet", type=int, default=0,
                     help="instead: this many warm-start network training steps (batch 8, 256^2)")
     a = ap.parse_args()
@@ -48,7 +49,8 @@ def main():
     pc = {} if a.precond else {"precond": regnk.REG_PC_REG}
     R = regnk.Registration(n, n, a.nt, 1e-2,
                            interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE,
-                           persistent_matvec=a.persistent, programmatic_launch=a.pdl, **pc)
+                           persistent_matvec=a.persistent, programmatic_launch=a.pdl,
+                           fused_transport=a.fused, **pc)
     R.set_images(f(m_R), f(m_T))
     vd, ud = f(v), f(u)
     g = torch.empty_like(vd)
@@ -61,7 +63,7 @@ def main():
         R.hessian_matvec(vd, ud, H)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / max(1, a.matvecs)
-    print(f"n={n} nt={a.nt} persistent={a.persistent} pdl={a.pdl} matvec {1e3 * dt:.3f} ms "
+    print(f"n={n} nt={a.nt} persistent={a.persistent} pdl={a.pdl} fused={a.fused} matvec {1e3 * dt:.3f} ms "
           f"(wall, incl. host)")
     if a.pcg and not a.precond:
         x = torch.empty_like(vd)

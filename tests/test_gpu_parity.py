@@ -317,19 +317,20 @@ def test_full_size_transport_symmetry_positivity(regnk):
     R.close()
 
 
-def test_preconditioners(regnk):
+@pytest.mark.parametrize("coarse_nt", [0, 2])
+def test_preconditioners(regnk, coarse_nt):
     n, nt, beta = 128, 4, 1e-2
     m_R, m_T, v = problem_data(n, n)
     r = inputs.random_velocity(n, seed=27, vmax=1.0)
     for pc in (regnk.REG_PC_REG, regnk.REG_PC_2L):
-        R = regnk.Registration(n, n, nt, beta, precond=pc)
+        R = regnk.Registration(n, n, nt, beta, precond=pc, coarse_nt=coarse_nt)
         R.set_images(dev(m_R), dev(m_T))
         R.objective_gradient(dev(v), None)
         z = torch.empty(2 * n * n, device="cuda")
         R.precond_apply(dev(r), z)
         P = Problem(m_R, m_T, nt, beta)
         P.state_solve(v)
-        S = Solver(P, precond="REG" if pc == regnk.REG_PC_REG else "2L")
+        S = Solver(P, precond="REG" if pc == regnk.REG_PC_REG else "2L", coarse_nt=coarse_nt or None)
         if pc == regnk.REG_PC_2L:
             emin, emax = R.eigen_bounds()
             S.eig = {"emin": emin, "emax": emax, "beta": beta}
@@ -474,3 +475,32 @@ def test_programmatic_launch_gives_identical_results(regnk, n1, n2):
     assert out[0][0] == out[1][0]
     for a, b in zip(out[0][1:], out[1][1:]):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n1,n2,vmax", [(128, 128, 0.5), (128, 128, 2.0), (128, 128, 4.0),
+                                        (192, 96, 1.0), (256, 128, 2.0)])
+def test_fused_prefilter_step_matches_two_kernel_path(regnk, n1, n2, vmax):
+    """The fused prefilter+step kernels (48^2 box for displacements up to 6
+    cells, 64^2 up to 14, none beyond) give the GN matvec of the separate
+    prefilter kernel up to FP32 rounding order; at vmax 4 on 128^2 (about 20
+    cells per step) the fused path is not taken and the results coincide."""
+    nt = 4
+    m_R, m_T, _ = (f32(a) for a in problem_data(n1, n2))
+    v = f32(inputs.random_velocity(n1, n2, seed=31, vmax=vmax))
+    u = f32(inputs.random_velocity(n1, n2, seed=32, vmax=1.0))
+    H = []
+    for fused in (1, 0):
+        R = regnk.Registration(n1, n2, nt, 1e-2, fused_transport=fused, **pc_for(n1, n2))
+        R.set_images(dev(m_R), dev(m_T))
+        out = torch.empty(2 * n1 * n2, device="cuda")
+        R.hessian_matvec(dev(v), dev(u), out)
+        torch.cuda.synchronize()
+        H.append(out.cpu().numpy())
+        R.close()
+    assert rel(H[0], H[1]) < 1e-6
+    if vmax == 2.0 and n1 == 128:
+        # the 64^2-box path against the oracle's data term
+        P = Problem(m_R, m_T, nt, 1e-2)
+        P.state_solve(v)
+        ref = P.hessian_matvec(u)
+        assert rel(H[0].reshape(2, n2, n1), ref) < 1e-3
