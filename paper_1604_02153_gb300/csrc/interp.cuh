@@ -139,7 +139,8 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
 // Spline coefficients of one field on the W x W box of nodes whose first
 // node is (bx0, by0) (periodic), left in shared memory for a gather that
 // follows in the same block: box[r * (W + 1) + c] is the coefficient of node
-// (bx0 + c, by0 + r). The box's samples with a kL-sample halo are staged in
+// (bx0 + c, by0 + r); all NT threads of the block take part. The box's
+// samples with a kL-sample halo are staged in
 // `stage` ((W + 2 kL) rows of pitch W + 2 kL + 1) and the x pass goes to
 // `mid` ((W + 2 kL) rows of pitch W + 1); `box` may alias `stage`. Same
 // recursions and segment length as prefilter_tile, so the coefficients are
@@ -155,18 +156,18 @@ struct BoxDims {
   static constexpr size_t kSmemBytes = sizeof(float) * (kStage + kMid);
 };
 
-template <int W, bool P2>
+template <int W, bool P2, int NT = kPThreads>
 __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int n1, int n2,
                                               int log1, int bx0, int by0, float* stage,
                                               float* mid, float* box) {
   using D = BoxDims<W>;
   constexpr int WS = D::WS, PS = D::PS, PB = D::PB;
-  constexpr int kLoads = (WS * WS + kPThreads - 1) / kPThreads;
+  constexpr int kLoads = (WS * WS + NT - 1) / NT;
   const int t = threadIdx.x;
   float ld_[kLoads];
 #pragma unroll
   for (int u = 0; u < kLoads; ++u) {
-    const int q = t + u * kPThreads;
+    const int q = t + u * NT;
     if (q < WS * WS) {
       const int r = q / WS, c = q - r * WS;
       const int gx = P2 ? wrap_index<true>(bx0 - kL + c, n1) : wrap_once(bx0 - kL + c, n1);
@@ -176,7 +177,7 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
   }
 #pragma unroll
   for (int u = 0; u < kLoads; ++u) {
-    const int q = t + u * kPThreads;
+    const int q = t + u * NT;
     if (q < WS * WS) {
       const int r = q / WS, c = q - r * WS;
       stage[r * PS + c] = ld_[u];
@@ -184,7 +185,7 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
   }
   __syncthreads();
   constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
-  for (int q = t; q < WS * kSegs; q += kPThreads) {   // x recursions
+  for (int q = t; q < WS * kSegs; q += NT) {   // x recursions
     const int r = q / kSegs, sg = q - r * kSegs;
     float v[kLen];
 #pragma unroll
@@ -193,7 +194,7 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
     bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { row[o] = x; });
   }
   __syncthreads();
-  for (int q = t; q < W * kSegs; q += kPThreads) {    // y recursions
+  for (int q = t; q < W * kSegs; q += NT) {    // y recursions
     const int c = q % W, sg = q / W;
     float v[kLen];
 #pragma unroll

@@ -327,8 +327,8 @@ void launch_incstate_step(int n1, int n2, float ht, const float* coef, const flo
 // coefficients of that box from the raw samples (prefilter_box, with the
 // same recursion segments as k_prefilter since H is a multiple of 8, so the
 // coefficients and the results are bitwise those of the two-kernel path)
-// and gathers from shared memory. Each thread handles 4 consecutive points
-// of a tile row, with float4 streamed loads.
+// and gathers from shared memory. Each thread handles kFP consecutive points
+// of a tile row, with vector streamed loads.
 
 template <int W>
 __device__ __forceinline__ void box_stencil(int lx, int ly, float d1, float d2, bool lagrange,
@@ -340,18 +340,13 @@ __device__ __forceinline__ void box_stencil(int lx, int ly, float d1, float d2, 
   lj = min(max(ly + (int)f2 - 1, 0), W - 4);
 }
 
-__device__ __forceinline__ float4 ld4(const float* p) {
-  return __ldg(reinterpret_cast<const float4*>(p));
-}
-__device__ __forceinline__ float4 ld4_rw(const float* p) {
-  return *reinterpret_cast<const float4*>(p);
-}
-__device__ __forceinline__ float at(const float4& v, int k) {
-  return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
-}
+// threads of the fused kernels: one round of recursions per pass for the
+// 48^2 box (74 x 6 x-segments, 48 x 6 y-segments) and two points per thread
+constexpr int kFT = 512;
+constexpr int kFP = 1024 / kFT;   // points per thread
 
 template <bool P2, int W>
-__global__ void __launch_bounds__(kPThreads)
+__global__ void __launch_bounds__(kFT)
 k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
                 const float* __restrict__ dY, const float* __restrict__ delta,
                 const float* __restrict__ delta_bar, const float* __restrict__ gm,
@@ -363,33 +358,39 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   float* stage = sm;
   float* mid = sm + D::kStage;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-  prefilter_box<W, P2>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  prefilter_box<W, P2, kFT>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   const long long N = (long long)n1 * n2;
-  const int t = threadIdx.x, r = t >> 3, cx = (t & 7) * 4;
+  constexpr int TPR = 32 / kFP;   // threads per tile row
+  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-  const float4 y1 = ld4(dY + idx), y2 = ld4(dY + N + idx);
-  const float4 db = ld4(delta_bar + idx), dd = ld4(delta + idx);
-  const float4 g1 = ld4(gm + idx), g2 = ld4(gm + N + idx);
-  const float4 b1 = ld4_rw(b + idx), b2 = ld4_rw(b + N + idx);
-  float l[4], o1[4], o2[4];
+  float y1[kFP], y2[kFP], db[kFP], dd[kFP], g1[kFP], g2[kFP], b1[kFP], b2[kFP];
+  ldk(dY + idx, y1);
+  ldk(dY + N + idx, y2);
+  ldk(delta_bar + idx, db);
+  ldk(delta + idx, dd);
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+  ldk_rw(b + idx, b1);
+  ldk_rw(b + N + idx, b2);
+  float l[kFP];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, at(y1, p), at(y2, p), false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + p, H + r, y1[p], y2[p], false, li, lj, w1, w2);
     const float lb = apply_box<D::PB>(stage, li, lj, w1, w2);
-    const float lstar = fmaf(ht * lb, at(db, p), lb);
-    l[p] = lb + 0.5f * ht * (lb * at(db, p) + lstar * at(dd, p));
-    o1[p] = fmaf(wb * l[p], at(g1, p), at(b1, p));
-    o2[p] = fmaf(wb * l[p], at(g2, p), at(b2, p));
+    const float lstar = fmaf(ht * lb, db[p], lb);
+    l[p] = lb + 0.5f * ht * (lb * db[p] + lstar * dd[p]);
+    b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
+    b2[p] = fmaf(wb * l[p], g2[p], b2[p]);
   }
-  *reinterpret_cast<float4*>(lam_out + idx) = make_float4(l[0], l[1], l[2], l[3]);
-  *reinterpret_cast<float4*>(b + idx) = make_float4(o1[0], o1[1], o1[2], o1[3]);
-  *reinterpret_cast<float4*>(b + N + idx) = make_float4(o2[0], o2[1], o2[2], o2[3]);
+  stk(lam_out + idx, l);
+  stk(b + idx, b1);
+  stk(b + N + idx, b2);
 }
 
 template <bool P2, int W>
-__global__ void __launch_bounds__(kPThreads)
+__global__ void __launch_bounds__(kFT)
 k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
                  const float* __restrict__ dX, const float* __restrict__ vt,
                  const float* __restrict__ vtD, const float* __restrict__ G,
@@ -401,26 +402,32 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
   float* stage = sm;
   float* mid = sm + D::kStage;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-  prefilter_box<W, P2>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  prefilter_box<W, P2, kFT>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   const long long N = (long long)n1 * n2;
-  const int t = threadIdx.x, r = t >> 3, cx = (t & 7) * 4;
+  constexpr int TPR = 32 / kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-  const float4 x1 = ld4(dX + idx), x2 = ld4(dX + N + idx);
-  const float4 w1v = ld4(vtD + idx), w2v = ld4(vtD + N + idx);
-  const float4 G1 = ld4(G + idx), G2 = ld4(G + N + idx);
-  const float4 u1 = ld4(vt + idx), u2 = ld4(vt + N + idx);
-  const float4 g1 = ld4(gm + idx), g2 = ld4(gm + N + idx);
-  float m[4];
+  float x1[kFP], x2[kFP], w1v[kFP], w2v[kFP], G1[kFP], G2[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
+  ldk(dX + idx, x1);
+  ldk(dX + N + idx, x2);
+  ldk(vtD + idx, w1v);
+  ldk(vtD + N + idx, w2v);
+  ldk(G + idx, G1);
+  ldk(G + N + idx, G2);
+  ldk(vt + idx, u1);
+  ldk(vt + N + idx, u2);
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+  float m[kFP];
 #pragma unroll
-  for (int p = 0; p < 4; ++p) {
+  for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, at(x1, p), at(x2, p), false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
     m[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
-    m[p] -= 0.5f * ht * (at(w1v, p) * at(G1, p) + at(w2v, p) * at(G2, p) + at(u1, p) * at(g1, p) +
-                         at(u2, p) * at(g2, p));
+    m[p] -= 0.5f * ht * (w1v[p] * G1[p] + w2v[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
   }
-  *reinterpret_cast<float4*>(out + idx) = make_float4(m[0], m[1], m[2], m[3]);
+  stk(out + idx, m);
 }
 
 // box widths with a fused kernel: halo H = 8 and H = 16
@@ -454,11 +461,11 @@ void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float
   const dim3 grid(n1 / 32, n2 / 32);
   const bool p2 = pow2_grid(n1, n2);
   if (W == 48)
-    launch_k(p2 ? k_adjoint_fused<true, 48> : k_adjoint_fused<false, 48>, grid, dim3(kPThreads),
+    launch_k(p2 ? k_adjoint_fused<true, 48> : k_adjoint_fused<false, 48>, grid, dim3(kFT),
              BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta, delta_bar,
              gm, lam_out, b);
   else
-    launch_k(p2 ? k_adjoint_fused<true, 64> : k_adjoint_fused<false, 64>, grid, dim3(kPThreads),
+    launch_k(p2 ? k_adjoint_fused<true, 64> : k_adjoint_fused<false, 64>, grid, dim3(kFT),
              BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta, delta_bar,
              gm, lam_out, b);
 }
@@ -469,10 +476,10 @@ void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev,
   const dim3 grid(n1 / 32, n2 / 32);
   const bool p2 = pow2_grid(n1, n2);
   if (W == 48)
-    launch_k(p2 ? k_incstate_fused<true, 48> : k_incstate_fused<false, 48>, grid, dim3(kPThreads),
+    launch_k(p2 ? k_incstate_fused<true, 48> : k_incstate_fused<false, 48>, grid, dim3(kFT),
              BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
   else
-    launch_k(p2 ? k_incstate_fused<true, 64> : k_incstate_fused<false, 64>, grid, dim3(kPThreads),
+    launch_k(p2 ? k_incstate_fused<true, 64> : k_incstate_fused<false, 64>, grid, dim3(kFT),
              BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
 }
 
