@@ -357,8 +357,11 @@ reg_status reg_warm_start(reg_ctx* ctx, reg_unet* net, float* v, int* accepted);
 reg_status reg_interpolate_static(int n1, int n2, const float* u, const float* disp,
                                   float* out, void* cuda_stream);
 
-/* Euclidean inner product of two float32 device vectors of length n,
- * accumulated in float64 (the Krylov and line-search reductions); *out host. */
+/* Euclidean inner product of two float32 device vectors of length n (any
+ * alignment; n = 0 gives 0 and allows NULL), accumulated to float64 accuracy
+ * like the Krylov and line-search reductions: each thread sums exact
+ * products with compensated FP32 pairs, threads and blocks are summed in
+ * FP64. *out host. */
 reg_status reg_dot(reg_ctx* ctx, const float* a, const float* b, long long n, double* out);
 
 /* Message of the last error on this context (never NULL). */

@@ -49,6 +49,16 @@ struct FftCfg {
   static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
 };
 
+// Lines per block and threads of the row passes (k_rows_r2c, k_rows_c2r): P
+// line pairs per block; each pass writes or reads 2 P adjacent values of
+// every spectral line.
+template <int L, int T>
+struct RowCfg {
+  static constexpr int N = FftCfg<L, T>::N;
+  static constexpr int P = FftCfg<L, T>::P;
+  static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
+};
+
 // In-place FFT of P lines of length N = 2^L 3^T stored contiguously at s
 // (line l at s + l*N): radix-4 Stockham passes, then a radix-2 pass if L is
 // odd, then a radix-3 pass if T = 1, each pass reading its inputs into
@@ -197,11 +207,11 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
 // ---------------------------------------------------------------------------
 // 1. forward row transforms: F fields of n2 rows of length N = n1.
 template <int L, int T>
-__global__ void __launch_bounds__(FftCfg<L, T>::NT)
+__global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__ spec,
            long long sstride, int n2, const float2* __restrict__ tw) {
   pdl_enter();
-  constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
+  constexpr int N = RowCfg<L, T>::N, P = RowCfg<L, T>::P, NT = RowCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * 2 * P;
@@ -242,12 +252,12 @@ k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__
 
 // 3. inverse row transforms (half spectrum -> real rows), optional addend.
 template <int L, int T>
-__global__ void __launch_bounds__(FftCfg<L, T>::NT)
+__global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
            const float2* __restrict__ tw) {
   pdl_enter();
-  constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
+  constexpr int N = RowCfg<L, T>::N, P = RowCfg<L, T>::P, NT = RowCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * 2 * P;
@@ -435,7 +445,7 @@ static void split_size(int n, int& L, int& T) {
 template <int L, int T>
 static void launch_r2c(const float* in, long long fstride, float2* spec, long long sstride,
                        int n2, int F, const float2* tw, cudaStream_t st) {
-  using C = FftCfg<L, T>;
+  using C = RowCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
@@ -446,7 +456,7 @@ template <int L, int T>
 static void launch_c2r(const float2* spec, long long sstride, float* out, long long fstride,
                        const float* add, long long astride, int n2, int F, const float2* tw,
                        cudaStream_t st) {
-  using C = FftCfg<L, T>;
+  using C = RowCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);

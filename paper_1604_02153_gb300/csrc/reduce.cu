@@ -1,8 +1,15 @@
 // Reductions and Krylov vector updates. Inner products and norms take FP32
-// fields and accumulate in FP64 (the Krylov inner products, the Armijo
-// objective comparison and the gradient-norm test of §3.4.1 are decided in
-// FP64). Reductions are two-stage with a fixed block count and a fixed
-// summation order, so repeated calls on the same data give identical bits.
+// fields and are accumulated to FP64 accuracy (the Krylov inner products, the
+// Armijo objective comparison and the gradient-norm test of §3.4.1 are
+// decided in FP64). Each thread carries its partial sum as an unevaluated
+// pair of FP32 numbers built with error-free transformations (FMA-based
+// TwoProduct for a*b, TwoSum for each addition, TwoDiff for a-b), so every
+// product and difference enters exactly and only second-order rounding is
+// lost; the pair is converted to FP64 once per thread and the block and
+// final sums are FP64. This keeps the FP64 pipe (a small fraction of the
+// FP32 rate on this GPU) off the per-element path. Reductions are two-stage
+// with a fixed block count and a fixed summation order, so repeated calls on
+// the same data give identical bits.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -45,32 +52,55 @@ __device__ __forceinline__ T block_sum(T v) {
   return r;
 }
 
+// FP32 pair (s, c) accumulating a sum with Knuth's TwoSum: s + c carries the
+// exact sum up to second-order rounding terms.
+struct Pair {
+  float s = 0.f, c = 0.f;
+};
+__device__ __forceinline__ void pair_add(Pair& a, float p) {
+  const float t = a.s + p;
+  const float z = t - a.s;
+  a.c += (a.s - (t - z)) + (p - z);
+  a.s = t;
+}
+// adds x*y (MODE 0) or (x-y)^2 (MODE 1) exactly up to second-order terms
+template <int MODE>
+__device__ __forceinline__ void pair_term(Pair& a, float x, float y) {
+  if (MODE == 0) {
+    const float p = x * y;
+    pair_add(a, p);
+    a.c += fmaf(x, y, -p);                  // exact rounding error of x*y
+  } else {
+    const float d = x - y;
+    const float z = d - x;
+    const float dd = (x - (d - z)) + (-y - z);   // exact rounding error of x-y
+    const float p = d * d;
+    pair_add(a, p);
+    a.c += fmaf(d, d, -p) + 2.f * d * dd;   // (d+dd)^2 = d^2 + 2 d dd + dd^2
+  }
+}
+
 // mode 0: sum a*b; mode 1: sum (a-b)^2
 template <int MODE>
 __global__ void __launch_bounds__(kRT)
 k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
           double* __restrict__ partial, int vec4) {
   pdl_enter();
-  double acc = 0.0;
+  Pair acc;
   const long long stride = (long long)gridDim.x * kRT;
   const long long n4 = vec4 ? (n >> 2) : 0;   // float4 path only for 16-byte aligned inputs
   const float4* a4 = reinterpret_cast<const float4*>(a);
   const float4* b4 = reinterpret_cast<const float4*>(b);
   for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n4; i += stride) {
     const float4 x = __ldg(a4 + i), y = __ldg(b4 + i);
-    if (MODE == 0) {
-      acc += (double)x.x * y.x + (double)x.y * y.y + (double)x.z * y.z + (double)x.w * y.w;
-    } else {
-      const double d0 = (double)x.x - y.x, d1 = (double)x.y - y.y;
-      const double d2 = (double)x.z - y.z, d3 = (double)x.w - y.w;
-      acc += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
-    }
+    pair_term<MODE>(acc, x.x, y.x);
+    pair_term<MODE>(acc, x.y, y.y);
+    pair_term<MODE>(acc, x.z, y.z);
+    pair_term<MODE>(acc, x.w, y.w);
   }
-  for (long long i = (n4 << 2) + (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
-    const double x = __ldg(a + i), y = __ldg(b + i);
-    acc += MODE == 0 ? x * y : (x - y) * (x - y);
-  }
-  const double s = block_sum(acc);
+  for (long long i = (n4 << 2) + (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride)
+    pair_term<MODE>(acc, __ldg(a + i), __ldg(b + i));
+  const double s = block_sum((double)acc.s + (double)acc.c);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 

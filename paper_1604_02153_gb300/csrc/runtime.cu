@@ -1482,7 +1482,11 @@ reg_status reg_profile_read(reg_ctx* c, int level, int kclass, double* ms, long 
 long long reg_launch_count(void) { return g_launch_count.load(); }
 
 reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
-  if (!c || !a || !b || !out || n < 0) return REG_EINVAL;
+  if (!c || !out || n < 0 || (n > 0 && (!a || !b))) return REG_EINVAL;
+  if (n == 0) {   // the empty sum (a and b may be NULL)
+    *out = 0.0;
+    return REG_OK;
+  }
   return guarded(c, [&] { *out = dot_sync(c, a, b, n, S_C); });
 }
 

@@ -504,3 +504,22 @@ def test_fused_prefilter_step_matches_two_kernel_path(regnk, n1, n2, vmax):
         P.state_solve(v)
         ref = P.hessian_matvec(u)
         assert rel(H[0].reshape(2, n2, n1), ref) < 1e-3
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 1000003, 2 * 1024 * 1024])
+def test_dot_matches_fp64(regnk, n):
+    """reg_dot (compensated FP32 per thread, FP64 across threads) against the
+    FP64 sum of the exact products, including ragged and empty lengths and a
+    start off a 16-byte boundary (scalar path)."""
+    R = regnk.Registration(64, 64, 4, 1e-2)
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal(n + 1).astype(np.float32)
+    b = (rng.standard_normal(n + 1) * 10.0 ** rng.integers(-3, 3, n + 1)).astype(np.float32)
+    ta, tb = torch.tensor(a, device="cuda"), torch.tensor(b, device="cuda")
+    scale = float(np.sum(np.abs(a[:n].astype(np.float64) * b[:n]))) + 1e-300
+    for off in (0, 1):
+        m = n if off == 0 else max(n - 1, 0)
+        ref = float(np.sum(a[off:off + m].astype(np.float64) * b[off:off + m]))
+        got = R.dot(ta[off:off + m], tb[off:off + m]) if m else R.dot(ta[:0], tb[:0])
+        assert abs(got - ref) <= 1e-13 * scale, (n, off, got, ref)
+    R.close()
