@@ -255,7 +255,7 @@ template <int L, int T>
 __global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
-           const float2* __restrict__ tw) {
+           const float2* __restrict__ tw, ChebEpilogue cheb) {
   pdl_enter();
   constexpr int N = RowCfg<L, T>::N, P = RowCfg<L, T>::P, NT = RowCfg<L, T>::NT;
   extern __shared__ float2 sm[];
@@ -292,6 +292,29 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
   fft_smem<L, T, P, NT, true>(sm, tw);
   float* dst = out + (long long)blockIdx.y * fstride;
   const float* ad = add ? add + (long long)blockIdx.y * astride : nullptr;
+  if (cheb.r) {
+    // Ad is never stored: the addend is d itself, read and overwritten here
+    // by the same thread (plain loads, not the read-only path)
+    const long long fo = (long long)blockIdx.y * fstride;
+    float* cr = cheb.r + fo;
+    float* cd = cheb.d + fo;
+    float* cx = cheb.x + fo;
+    for (int q = t; q < P * N; q += NT) {
+      const int l = q / N, i = q % N;
+      const long long r = (long long)(row0 + 2 * l) * N + i;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long e = r + h * N;
+        const float Ad = (h ? sm[q].y : sm[q].x) + (ad ? ad[e] : 0.f);
+        const float ri = cr[e] - Ad;
+        const float di = fmaf(cheb.a, cd[e], cheb.b * ri);
+        cr[e] = ri;
+        cd[e] = di;
+        cx[e] = cx[e] + di;
+      }
+    }
+    return;
+  }
   for (int q = t; q < P * N; q += NT) {
     const int l = q / N, i = q % N;
     const long long r = (long long)(row0 + 2 * l) * N + i;
@@ -455,12 +478,12 @@ static void launch_r2c(const float* in, long long fstride, float2* spec, long lo
 template <int L, int T>
 static void launch_c2r(const float2* spec, long long sstride, float* out, long long fstride,
                        const float* add, long long astride, int n2, int F, const float2* tw,
-                       cudaStream_t st) {
+                       cudaStream_t st, const ChebEpilogue& cheb) {
   using C = RowCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  launch_k(k_rows_c2r<L, T>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw);
+  launch_k(k_rows_c2r<L, T>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
 }
 
 template <int LI, int LO, int T>
@@ -500,11 +523,13 @@ void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* sp
 
 void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
                   long long fstride, const float* add, long long astride, int F,
-                  const float2* tw, cudaStream_t st) {
+                  const float2* tw, cudaStream_t st, const ChebEpilogue* cheb) {
   int L, T;
   split_size(n1, L, T);
+  const ChebEpilogue none;
+  const ChebEpilogue& ce = cheb ? *cheb : none;
   switch (L * 2 + T) {
-#define CASE(LL, TT) case LL * 2 + TT: launch_c2r<LL, TT>(spec, sstride, out, fstride, add, astride, n2, F, tw, st); break;
+#define CASE(LL, TT) case LL * 2 + TT: launch_c2r<LL, TT>(spec, sstride, out, fstride, add, astride, n2, F, tw, st, ce); break;
     REGNK_SIZE_CASES(CASE)
 #undef CASE
     default: break;

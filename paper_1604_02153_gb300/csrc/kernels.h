@@ -82,9 +82,20 @@ struct ColArgs {
 // fft.cu
 void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
                   long long sstride, int F, const float2* tw, cudaStream_t st);
+// Optional epilogue of the inverse row pass: with Ad = the pass's output
+// (plus addend), one Chebyshev iteration r -= Ad; d = a d + b r; x += d on
+// the same points (the work of k_cheb_update), instead of storing Ad. The
+// vectors have the pass's field layout (field f at offset f * fstride).
+struct ChebEpilogue {
+  float* r = nullptr;
+  float* d = nullptr;
+  float* x = nullptr;
+  float a = 0.f, b = 0.f;
+};
 void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
                   long long fstride, const float* add, long long astride, int F,
-                  const float2* tw, cudaStream_t st);
+                  const float2* tw, cudaStream_t st,
+                  const ChebEpilogue* cheb = nullptr);
 void fft_cols(const ColArgs& a, int groups, cudaStream_t st);
 // n = 2^L (L = 5..11) or 3 * 2^L (L = 5..9)
 bool fft_size_supported(int n);
@@ -116,7 +127,10 @@ void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float
                           const float* gm, float* lam_out, float* b, cudaStream_t st);
 void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
                            const float* vt, const float* vtD, const float* G, const float* gm,
-                           float* out, cudaStream_t st);
+                           float* out, const float* gm_nt, float* b, cudaStream_t st);
+void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
+                                 const float* G1, const float* gm1, float* vtD, float* out,
+                                 cudaStream_t st);
 void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
                           const float* vt, const float* vtD, const float* G,
                           const float* gm, float* out, int first, int lagrange,
@@ -157,8 +171,6 @@ void launch_axpby(long long n, const double* alpha_num, const double* alpha_den,
                   const float* x, float* y, float beta_y, cudaStream_t st);
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
                     cudaStream_t st);
-void launch_cheb_update(long long n, float a, float b, const float* Ad, float* r, float* d,
-                        float* x, cudaStream_t st);
 void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,
                        const float* q, float* x, float* r, cudaStream_t st);
 void launch_pcg_direction(long long n, const double* rz_new, const double* rz_old,

@@ -211,28 +211,6 @@ void launch_lincomb(long long n, float a, const float* x, float b, const float* 
   launch_k(k_lincomb, dim3(nblocks(n)), dim3(kRT), 0, st, n, a, x, b, y, z);
 }
 
-// One Chebyshev update (three-term recurrence on the residual):
-//   r -= Ad;  d = a d + b r;  x += d
-// in a single pass over the five vectors.
-__global__ void k_cheb_update(long long n, float a, float b, const float* __restrict__ Ad,
-                              float* __restrict__ r, float* __restrict__ d,
-                              float* __restrict__ x) {
-  pdl_enter();
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const float ri = r[i] - Ad[i];
-    const float di = fmaf(a, d[i], b * ri);
-    r[i] = ri;
-    d[i] = di;
-    x[i] = x[i] + di;
-  }
-}
-
-void launch_cheb_update(long long n, float a, float b, const float* Ad, float* r, float* d,
-                        float* x, cudaStream_t st) {
-  launch_k(k_cheb_update, dim3(nblocks(n)), dim3(kRT), 0, st, n, a, b, Ad, r, d, x);
-}
-
 // PCG step: alpha = rz / pq; x += alpha p; r -= alpha q.
 __global__ void k_pcg_update(long long n, const double* rz, const double* pq,
                              const float* __restrict__ p, const float* __restrict__ q,

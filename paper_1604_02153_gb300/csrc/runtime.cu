@@ -426,8 +426,10 @@ ColArgs col_args(const Level& L, int op, double beta, int p, double s) {
 }
 
 // out (groups*fout fields) = op(in (groups*fin fields)) [+ add], on level L.
+// With `cheb`, the inverse row pass ends in one Chebyshev iteration on its
+// output instead of storing it (see ChebEpilogue).
 void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, int groups,
-              float* out, int fout, const float* add) {
+              float* out, int fout, const float* add, const ChebEpilogue* cheb = nullptr) {
   LevelScope ls(c, L);
   const GridDims& g = L.g;
   const int per = fin + fout;
@@ -453,8 +455,16 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
     }
     {
       Prof P(c, REG_KC_FFT_ROWS, (double)ng * fout * (8.0 * g.spec + (add ? 8.0 : 4.0) * g.N));
+      ChebEpilogue ce;
+      if (cheb) {
+        ce = *cheb;
+        ce.r += (size_t)g0 * fout * g.N;
+        ce.d += (size_t)g0 * fout * g.N;
+        ce.x += (size_t)g0 * fout * g.N;
+      }
       fft_rows_c2r(g.n1, g.n2, sout, g.spec, out + (size_t)g0 * fout * g.N, g.N,
-                   add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st);
+                   add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st,
+                   cheb ? &ce : nullptr);
     }
   }
   check_launch(c, "spectral operator");
@@ -759,37 +769,58 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const int nt = L.nt;
   const float ht = L.ht;
   const int lg = lagrange(c);
-  const float* cvt = coefficients(c, L, vt, 2, L.c2);
-  {
-    Prof P(c, REG_KC_GATHER, 24.0 * N);
-    launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
-  }
   float* mt = L.fA;
   float* mt2 = L.fB;
-  for (int j = 1; j <= nt; ++j) {
-    if (j > 1 && L.fuse_w) {   // prefilter of m~_{j-1} inside the step kernel
-      Prof P(c, REG_KC_INCSTATE_STEP, 48.0 * N);
-      launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, mt, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
-                            L.gm + 2 * j * N, mt2, c->st);
-      std::swap(mt, mt2);
-      continue;
-    }
-    const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
+  float* lt = nullptr;
+  float* lt2 = nullptr;
+  if (L.fuse_w) {
+    // prefilter of v~, v~(X_D) and m~_1 in one kernel; later steps prefilter
+    // m~_{j-1} inside the step; the last one also writes lambda~_nt and
+    // starts b~ (the work of k_adjoint_init)
     {
-      Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 36.0 : 48.0) * N);
-      launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
-                           L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+      Prof P(c, REG_KC_INCSTATE_STEP, 44.0 * N);
+      launch_incstate_first_fused(L.fuse_w, gd.n1, gd.n2, ht, vt, L.dX, L.G, L.gm + 2 * N, L.vtD,
+                                  mt2, c->st);
     }
     std::swap(mt, mt2);
+    for (int j = 2; j <= nt; ++j) {
+      const bool last = (j == nt);
+      Prof P(c, REG_KC_INCSTATE_STEP, (last ? 64.0 : 48.0) * N);
+      launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, mt, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                            L.gm + 2 * j * N, mt2, last ? L.gm + 2 * nt * N : nullptr,
+                            last ? L.b : nullptr, c->st);
+      std::swap(mt, mt2);
+    }
+    if (nt >= 2) {   // mt holds lambda~_nt
+      lt = mt;
+      lt2 = mt2;
+    }
+  } else {
+    const float* cvt = coefficients(c, L, vt, 2, L.c2);
+    {
+      Prof P(c, REG_KC_GATHER, 24.0 * N);
+      launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
+    }
+    for (int j = 1; j <= nt; ++j) {
+      const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
+      {
+        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 36.0 : 48.0) * N);
+        launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                             L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+      }
+      std::swap(mt, mt2);
+    }
   }
   check_launch(c, "incremental state");
-  // lambda~_nt = -m~_nt
-  float* lt = mt2;
-  {
-    Prof P(c, REG_KC_VECTOR, 24.0 * N);
-    launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+  if (!lt) {
+    // lambda~_nt = -m~_nt
+    lt = mt2;
+    {
+      Prof P(c, REG_KC_VECTOR, 24.0 * N);
+      launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+    }
+    lt2 = mt;
   }
-  float* lt2 = mt;
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     if (L.fuse_w) {   // prefilter of lambda~_{j+1} inside the step kernel
@@ -902,11 +933,11 @@ void estimate_eigenvalues(reg_ctx* c) {
 
 // (I + (beta A_c)^-1 Q_c) u on the coarse level: the split operator above
 // conjugated by (beta A_c)^1/2, same spectrum, one spectral operation less.
-void coarse_op_u(reg_ctx* c, const float* u, float* out) {
+void coarse_op_u(reg_ctx* c, const float* u, float* out, const ChebEpilogue* cheb = nullptr) {
   LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
   hessian_core(c, C, u, c->cq, true);
-  spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u);
+  spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u, cheb);
   ++c->coarse_matvecs;
 }
 
@@ -920,13 +951,16 @@ void cheb(reg_ctx* c, const float* rhs, float* x) {
   launch_lincomb(n, (float)(1.0 / theta), rhs, 0.f, nullptr, c->cd, c->st);
   check(c, cudaMemcpyAsync(x, c->cd, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
   for (int it = 1; it < c->opt.cheb_iters; ++it) {
-    coarse_op_u(c, c->cd, c->cAd);
+    // the operator application ends in the iteration's vector work
+    // (r -= A d; d = a d + b r; x += d) inside its last FFT pass
     const double rho_new = 1.0 / (2.0 * sigma - rho);
-    {
-      Prof P(c, REG_KC_VECTOR, 28.0 * n);
-      launch_cheb_update(n, (float)(rho_new * rho), (float)(2.0 * rho_new / delta), c->cAd, c->cr,
-                         c->cd, x, c->st);
-    }
+    ChebEpilogue ce;
+    ce.r = c->cr;
+    ce.d = c->cd;
+    ce.x = x;
+    ce.a = (float)(rho_new * rho);
+    ce.b = (float)(2.0 * rho_new / delta);
+    coarse_op_u(c, c->cd, c->cAd, &ce);
     rho = rho_new;
   }
   check_launch(c, "chebyshev");

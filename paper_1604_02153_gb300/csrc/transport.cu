@@ -389,12 +389,17 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   stk(b + N + idx, b2);
 }
 
+// gm_nt, b: non-NULL for the last step j = nt, which writes the final
+// condition of the incremental adjoint, lambda~_nt = -m~_nt, to `out` and
+// starts its time integral, b = h_t/2 lambda~_nt grad m_nt (the work of
+// k_adjoint_init).
 template <bool P2, int W>
 __global__ void __launch_bounds__(kFT)
 k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
                  const float* __restrict__ dX, const float* __restrict__ vt,
                  const float* __restrict__ vtD, const float* __restrict__ G,
-                 const float* __restrict__ gm, float* __restrict__ out) {
+                 const float* __restrict__ gm, float* __restrict__ out,
+                 const float* __restrict__ gm_nt, float* __restrict__ b) {
   pdl_enter();
   using D = BoxDims<W>;
   constexpr int H = (W - 32) / 2;
@@ -427,6 +432,73 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
     m[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
     m[p] -= 0.5f * ht * (w1v[p] * G1[p] + w2v[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
   }
+  if (!b) {
+    stk(out + idx, m);
+    return;
+  }
+  float gn1[kFP], gn2[kFP], lam[kFP], b1[kFP], b2[kFP];
+  ldk(gm_nt + idx, gn1);
+  ldk(gm_nt + N + idx, gn2);
+  const float hh = 0.5f * ht;
+#pragma unroll
+  for (int p = 0; p < kFP; ++p) {
+    lam[p] = -m[p];
+    b1[p] = hh * lam[p] * gn1[p];
+    b2[p] = hh * lam[p] * gn2[p];
+  }
+  stk(out + idx, lam);
+  stk(b + idx, b1);
+  stk(b + N + idx, b2);
+}
+
+// v~ at the departure points and the first incremental state step in one
+// kernel: both components of v~ are prefiltered on the tile's box, gathered
+// at X_D (written to vtD, needed by every later step) and
+// m~_1 = -h_t/2 (v~(X_D) . grad m_0(X_D) + v~ . grad m_1) (m~_0 = 0).
+template <bool P2, int W>
+__global__ void __launch_bounds__(kFT)
+k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restrict__ vt,
+                       const float* __restrict__ dX, const float* __restrict__ G1p,
+                       const float* __restrict__ gm1, float* __restrict__ vtD,
+                       float* __restrict__ out) {
+  pdl_enter();
+  using D = BoxDims<W>;
+  constexpr int H = (W - 32) / 2;
+  constexpr int kBox = W * D::PB;
+  extern __shared__ float sm[];
+  float* stage = sm;
+  float* mid = sm + D::kStage;
+  float* box1 = mid + D::kMid;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const long long N = (long long)n1 * n2;
+  prefilter_box<W, P2, kFT>(vt, n1, n2, log1, x0 - H, y0 - H, stage, mid, box1);
+  prefilter_box<W, P2, kFT>(vt + N, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  (void)kBox;
+  constexpr int TPR = 32 / kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  float x1[kFP], x2[kFP], Ga[kFP], Gb[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
+  ldk(dX + idx, x1);
+  ldk(dX + N + idx, x2);
+  ldk(G1p + idx, Ga);
+  ldk(G1p + N + idx, Gb);
+  ldk(vt + idx, u1);
+  ldk(vt + N + idx, u2);
+  ldk(gm1 + idx, g1);
+  ldk(gm1 + N + idx, g2);
+  float wd1[kFP], wd2[kFP], m[kFP];
+#pragma unroll
+  for (int p = 0; p < kFP; ++p) {
+    int li, lj;
+    float w1[4], w2[4];
+    box_stencil<W>(H + cx + p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
+    wd1[p] = apply_box<D::PB>(box1, li, lj, w1, w2);
+    wd2[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
+    m[p] = 0.f;
+    m[p] -= 0.5f * ht * (wd1[p] * Ga[p] + wd2[p] * Gb[p] + u1[p] * g1[p] + u2[p] * g2[p]);
+  }
+  stk(vtD + idx, wd1);
+  stk(vtD + N + idx, wd2);
   stk(out + idx, m);
 }
 
@@ -444,7 +516,16 @@ static void allow_smem(K kernel, size_t bytes) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+template <int W>
+constexpr size_t first_smem() {
+  return BoxDims<W>::kSmemBytes + sizeof(float) * W * BoxDims<W>::PB;
+}
+
 void fused_init() {
+  allow_smem(k_incstate_first_fused<true, 48>, first_smem<48>());
+  allow_smem(k_incstate_first_fused<false, 48>, first_smem<48>());
+  allow_smem(k_incstate_first_fused<true, 64>, first_smem<64>());
+  allow_smem(k_incstate_first_fused<false, 64>, first_smem<64>());
   allow_smem(k_adjoint_fused<true, 48>, BoxDims<48>::kSmemBytes);
   allow_smem(k_adjoint_fused<false, 48>, BoxDims<48>::kSmemBytes);
   allow_smem(k_adjoint_fused<true, 64>, BoxDims<64>::kSmemBytes);
@@ -472,15 +553,30 @@ void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float
 
 void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
                            const float* vt, const float* vtD, const float* G, const float* gm,
-                           float* out, cudaStream_t st) {
+                           float* out, const float* gm_nt, float* b, cudaStream_t st) {
   const dim3 grid(n1 / 32, n2 / 32);
   const bool p2 = pow2_grid(n1, n2);
   if (W == 48)
     launch_k(p2 ? k_incstate_fused<true, 48> : k_incstate_fused<false, 48>, grid, dim3(kFT),
-             BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
+             BoxDims<48>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out,
+             gm_nt, b);
   else
     launch_k(p2 ? k_incstate_fused<true, 64> : k_incstate_fused<false, 64>, grid, dim3(kFT),
-             BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out);
+             BoxDims<64>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm, out,
+             gm_nt, b);
+}
+
+void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
+                                 const float* G1, const float* gm1, float* vtD, float* out,
+                                 cudaStream_t st) {
+  const dim3 grid(n1 / 32, n2 / 32);
+  const bool p2 = pow2_grid(n1, n2);
+  if (W == 48)
+    launch_k(p2 ? k_incstate_first_fused<true, 48> : k_incstate_first_fused<false, 48>, grid,
+             dim3(kFT), first_smem<48>(), st, n1, n2, ilog2i(n1), ht, vt, dX, G1, gm1, vtD, out);
+  else
+    launch_k(p2 ? k_incstate_first_fused<true, 64> : k_incstate_first_fused<false, 64>, grid,
+             dim3(kFT), first_smem<64>(), st, n1, n2, ilog2i(n1), ht, vt, dX, G1, gm1, vtD, out);
 }
 
 }  // namespace regnk
