@@ -114,8 +114,10 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
   }
   __syncthreads();
   constexpr int kSeg = 8, kSegs = kPX / kSeg, kLen = kSeg + 2 * kL;   // 34 samples per chain
-  if (t < kPH * kSegs) {   // x recursions: staged row t / 4, segment t % 4
-    const int r = t / kSegs, sg = t % kSegs;
+  if (t < kPH * kSegs) {   // x recursions: staged row t % kPH, segment t / kPH
+    // (a warp walks 32 consecutive rows of one segment: with the odd pitch
+    // its shared-memory accesses fall in 32 different banks)
+    const int r = t % kPH, sg = t / kPH;
     float v[kLen];
 #pragma unroll
     for (int k = 0; k < kLen; ++k) v[k] = sin_[r * kPIn + sg * kSeg + k];
@@ -162,31 +164,44 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
                                               float* mid, float* box) {
   using D = BoxDims<W>;
   constexpr int WS = D::WS, PS = D::PS, PB = D::PB;
-  constexpr int kLoads = (WS * WS + NT - 1) / NT;
+  // The staged rows are read as float4 from a 4-aligned first column (a
+  // float4 never straddles the periodic seam since n1 % 4 == 0) and the
+  // first `off` columns of the first vector are dropped. Row-major thread
+  // order keeps the loads of a warp contiguous.
+  constexpr int kV = (WS + 3 + 3) / 4;          // float4 per staged row
+  constexpr int kLoads = (WS * kV + NT - 1) / NT;
+  const int cx0 = bx0 - kL;
+  const int ax0 = cx0 & ~3;
+  const int off = cx0 - ax0;
   const int t = threadIdx.x;
-  float ld_[kLoads];
+  float4 ld_[kLoads];
 #pragma unroll
   for (int u = 0; u < kLoads; ++u) {
     const int q = t + u * NT;
-    if (q < WS * WS) {
-      const int r = q / WS, c = q - r * WS;
-      const int gx = P2 ? wrap_index<true>(bx0 - kL + c, n1) : wrap_once(bx0 - kL + c, n1);
+    if (q < WS * kV) {
+      const int r = q / kV, v = q - r * kV;
+      const int gx = P2 ? wrap_index<true>(ax0 + 4 * v, n1) : wrap_once(ax0 + 4 * v, n1);
       const int gy = P2 ? wrap_index<true>(by0 - kL + r, n2) : wrap_once(by0 - kL + r, n2);
-      ld_[u] = __ldg(src + row_offset<P2>(gy, n1, log1) + gx);
+      ld_[u] = __ldg(reinterpret_cast<const float4*>(src + row_offset<P2>(gy, n1, log1) + gx));
     }
   }
 #pragma unroll
   for (int u = 0; u < kLoads; ++u) {
     const int q = t + u * NT;
-    if (q < WS * WS) {
-      const int r = q / WS, c = q - r * WS;
-      stage[r * PS + c] = ld_[u];
+    if (q < WS * kV) {
+      const int r = q / kV, v = q - r * kV;
+      const float e[4] = {ld_[u].x, ld_[u].y, ld_[u].z, ld_[u].w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = 4 * v + k - off;
+        if (c >= 0 && c < WS) stage[r * PS + c] = e[k];
+      }
     }
   }
   __syncthreads();
   constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
-  for (int q = t; q < WS * kSegs; q += NT) {   // x recursions
-    const int r = q / kSegs, sg = q - r * kSegs;
+  for (int q = t; q < WS * kSegs; q += NT) {   // x recursions, conflict-free as above
+    const int r = q % WS, sg = q / WS;
     float v[kLen];
 #pragma unroll
     for (int k = 0; k < kLen; ++k) v[k] = stage[r * PS + sg * kSeg + k];

@@ -346,7 +346,7 @@ constexpr int kFT = 512;
 constexpr int kFP = 1024 / kFT;   // points per thread
 
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT)
+__global__ void __launch_bounds__(kFT, 2)
 k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
                 const float* __restrict__ dY, const float* __restrict__ delta,
                 const float* __restrict__ delta_bar, const float* __restrict__ gm,
@@ -358,11 +358,12 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   float* stage = sm;
   float* mid = sm + D::kStage;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-  prefilter_box<W, P2, kFT>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;   // threads per tile row
   const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  // the step's streamed operands are loaded first: their latency overlaps
+  // the staging and the recursions of the prefilter
   float y1[kFP], y2[kFP], db[kFP], dd[kFP], g1[kFP], g2[kFP], b1[kFP], b2[kFP];
   ldk(dY + idx, y1);
   ldk(dY + N + idx, y2);
@@ -372,6 +373,7 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   ldk(gm + N + idx, g2);
   ldk_rw(b + idx, b1);
   ldk_rw(b + N + idx, b2);
+  prefilter_box<W, P2, kFT>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   float l[kFP];
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
@@ -394,7 +396,7 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
 // starts its time integral, b = h_t/2 lambda~_nt grad m_nt (the work of
 // k_adjoint_init).
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT)
+__global__ void __launch_bounds__(kFT, 2)
 k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
                  const float* __restrict__ dX, const float* __restrict__ vt,
                  const float* __restrict__ vtD, const float* __restrict__ G,
@@ -407,11 +409,11 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
   float* stage = sm;
   float* mid = sm + D::kStage;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
-  prefilter_box<W, P2, kFT>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
   const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  // streamed operands first (their latency overlaps the prefilter)
   float x1[kFP], x2[kFP], w1v[kFP], w2v[kFP], G1[kFP], G2[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
   ldk(dX + idx, x1);
   ldk(dX + N + idx, x2);
@@ -423,6 +425,7 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
   ldk(vt + N + idx, u2);
   ldk(gm + idx, g1);
   ldk(gm + N + idx, g2);
+  prefilter_box<W, P2, kFT>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   float m[kFP];
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
@@ -456,7 +459,7 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
 // at X_D (written to vtD, needed by every later step) and
 // m~_1 = -h_t/2 (v~(X_D) . grad m_0(X_D) + v~ . grad m_1) (m~_0 = 0).
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT)
+__global__ void __launch_bounds__(kFT, 2)
 k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restrict__ vt,
                        const float* __restrict__ dX, const float* __restrict__ G1p,
                        const float* __restrict__ gm1, float* __restrict__ vtD,
@@ -471,12 +474,14 @@ k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restri
   float* box1 = mid + D::kMid;
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
-  prefilter_box<W, P2, kFT>(vt, n1, n2, log1, x0 - H, y0 - H, stage, mid, box1);
-  prefilter_box<W, P2, kFT>(vt + N, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
-  (void)kBox;
   constexpr int TPR = 32 / kFP;
   const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  // (the streamed operands are loaded after the two prefilters: loading
+  // them first took more registers than two blocks per SM allow)
+  prefilter_box<W, P2, kFT>(vt, n1, n2, log1, x0 - H, y0 - H, stage, mid, box1);
+  prefilter_box<W, P2, kFT>(vt + N, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  (void)kBox;
   float x1[kFP], x2[kFP], Ga[kFP], Gb[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
   ldk(dX + idx, x1);
   ldk(dX + N + idx, x2);
