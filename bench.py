@@ -59,10 +59,14 @@ CLASS_NAMES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
                "adjoint_step", "incstate_step", "reduce", "vector", "matvec"]
 # source file of each kernel class (a traffic figure is only valid for the
 # source it was captured from)
-CLASS_SOURCES = {"fft_rows": "fft.cu", "fft_cols": "fft.cu", "prefilter": "transport.cu",
-                 "departure": "transport.cu", "gather": "transport.cu",
-                 "adjoint_step": "transport.cu", "incstate_step": "transport.cu",
-                 "reduce": "reduce.cu", "vector": "reduce.cu", "matvec": "matvec.cu"}
+CLASS_SOURCES = {"fft_rows": ("fft.cu",), "fft_cols": ("fft.cu",),
+                 "prefilter": ("transport.cu", "interp.cuh"),
+                 "departure": ("transport.cu", "interp.cuh"),
+                 "gather": ("transport.cu", "interp.cuh"),
+                 "adjoint_step": ("transport.cu", "interp.cuh"),
+                 "incstate_step": ("transport.cu", "interp.cuh"),
+                 "reduce": ("reduce.cu",), "vector": ("reduce.cu",),
+                 "matvec": ("matvec.cu", "interp.cuh")}
 
 
 def parse():
@@ -100,9 +104,11 @@ def peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_hash(fname):
-    path = os.path.join(ROOT, "paper_1604_02153_gb300", "csrc", fname)
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+def source_hash(fnames):
+    h = hashlib.sha256()
+    for fname in fnames:
+        h.update(open(os.path.join(ROOT, "paper_1604_02153_gb300", "csrc", fname), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(level, cls):

@@ -262,6 +262,41 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
   const int t = threadIdx.x;
   const int row0 = blockIdx.x * 2 * P;
   const float2* src = spec + (long long)blockIdx.y * sstride;
+  // The epilogue's operands at this thread's output points (the addend, or
+  // the Chebyshev vectors) are loaded first, so their latency overlaps the
+  // transform
+  constexpr int kOut = (P * N + NT - 1) / NT;
+  float cr_[kOut][2], cd_[kOut][2], cx_[kOut][2];
+  if (!cheb.r && add) {   // plain pass: the addend is prefetched into cr_
+    const float* ad0 = add + (long long)blockIdx.y * astride;
+#pragma unroll
+    for (int u = 0; u < kOut; ++u) {
+      const int q = t + u * NT;
+      if ((P * N) % NT == 0 || q < P * N) {
+        const int l = q / N, i = q % N;
+        const long long r = (long long)(row0 + 2 * l) * N + i;
+        cr_[u][0] = __ldg(ad0 + r);
+        cr_[u][1] = __ldg(ad0 + r + N);
+      }
+    }
+  }
+  if (cheb.r) {
+    const long long fo = (long long)blockIdx.y * fstride;
+#pragma unroll
+    for (int u = 0; u < kOut; ++u) {
+      const int q = t + u * NT;
+      if ((P * N) % NT == 0 || q < P * N) {
+        const int l = q / N, i = q % N;
+        const long long r = fo + (long long)(row0 + 2 * l) * N + i;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          cr_[u][h] = cheb.r[r + h * N];
+          cd_[u][h] = cheb.d[r + h * N];
+          cx_[u][h] = cheb.x[r + h * N];
+        }
+      }
+    }
+  }
   constexpr int TOT = (N / 2 + 1) * P;
   constexpr int LD = (TOT + NT - 1) / NT;     // loads issued before the stores
   float4 v[LD];
@@ -293,38 +328,46 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
   float* dst = out + (long long)blockIdx.y * fstride;
   const float* ad = add ? add + (long long)blockIdx.y * astride : nullptr;
   if (cheb.r) {
-    // Ad is never stored: the addend is d itself, read and overwritten here
-    // by the same thread (plain loads, not the read-only path)
+    // Ad is never stored. The addend is d itself (already in cd_), and r, d
+    // and x are read and overwritten here by the same thread.
     const long long fo = (long long)blockIdx.y * fstride;
     float* cr = cheb.r + fo;
     float* cd = cheb.d + fo;
     float* cx = cheb.x + fo;
-    for (int q = t; q < P * N; q += NT) {
-      const int l = q / N, i = q % N;
-      const long long r = (long long)(row0 + 2 * l) * N + i;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const long long e = r + h * N;
-        const float Ad = (h ? sm[q].y : sm[q].x) + (ad ? ad[e] : 0.f);
-        const float ri = cr[e] - Ad;
-        const float di = fmaf(cheb.a, cd[e], cheb.b * ri);
-        cr[e] = ri;
-        cd[e] = di;
-        cx[e] = cx[e] + di;
+    for (int u = 0; u < kOut; ++u) {
+      const int q = t + u * NT;
+      if ((P * N) % NT == 0 || q < P * N) {
+        const int l = q / N, i = q % N;
+        const long long r = (long long)(row0 + 2 * l) * N + i;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long e = r + h * N;
+          const float Ad = (h ? sm[q].y : sm[q].x) + (ad ? cd_[u][h] : 0.f);
+          const float ri = cr_[u][h] - Ad;
+          const float di = fmaf(cheb.a, cd_[u][h], cheb.b * ri);
+          cr[e] = ri;
+          cd[e] = di;
+          cx[e] = cx_[u][h] + di;
+        }
       }
     }
     return;
   }
-  for (int q = t; q < P * N; q += NT) {
-    const int l = q / N, i = q % N;
-    const long long r = (long long)(row0 + 2 * l) * N + i;
-    float a = sm[q].x, b = sm[q].y;
-    if (ad) {
-      a += __ldg(ad + r);
-      b += __ldg(ad + r + N);
+#pragma unroll
+  for (int u = 0; u < kOut; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) {
+      const int l = q / N, i = q % N;
+      const long long r = (long long)(row0 + 2 * l) * N + i;
+      float a = sm[q].x, b = sm[q].y;
+      if (ad) {
+        a += cr_[u][0];
+        b += cr_[u][1];
+      }
+      dst[r] = a;
+      dst[r + N] = b;
     }
-    dst[r] = a;
-    dst[r + N] = b;
   }
 }
 

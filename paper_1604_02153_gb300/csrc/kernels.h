@@ -83,9 +83,10 @@ struct ColArgs {
 void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
                   long long sstride, int F, const float2* tw, cudaStream_t st);
 // Optional epilogue of the inverse row pass: with Ad = the pass's output
-// (plus addend), one Chebyshev iteration r -= Ad; d = a d + b r; x += d on
-// the same points (the work of k_cheb_update), instead of storing Ad. The
-// vectors have the pass's field layout (field f at offset f * fstride).
+// plus its addend, one Chebyshev iteration r -= Ad; d = a d + b r; x += d on
+// the same points, instead of storing Ad. The addend, if any, must be d
+// itself (the operator is applied to d); the vectors have the pass's field
+// layout (field f at offset f * fstride).
 struct ChebEpilogue {
   float* r = nullptr;
   float* d = nullptr;
