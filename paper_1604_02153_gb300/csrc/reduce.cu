@@ -211,11 +211,13 @@ void launch_lincomb(long long n, float a, const float* x, float b, const float* 
   launch_k(k_lincomb, dim3(nblocks(n)), dim3(kRT), 0, st, n, a, x, b, y, z);
 }
 
-// PCG step: alpha = rz / pq; x += alpha p; r -= alpha q.
+// PCG step: alpha = rz / pq; x += alpha p; r -= alpha q. Nothing is changed
+// when pq <= 0 (negative curvature: the host stops with x as it is).
 __global__ void k_pcg_update(long long n, const double* rz, const double* pq,
                              const float* __restrict__ p, const float* __restrict__ q,
                              float* __restrict__ x, float* __restrict__ r) {
   pdl_enter();
+  if (!(*pq > 0.0)) return;
   const double ad = *rz / *pq;
   const float alpha = (float)ad;
   const long long stride = (long long)gridDim.x * blockDim.x;

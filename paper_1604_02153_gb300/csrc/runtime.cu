@@ -114,6 +114,8 @@ struct reg_ctx {
   int cur_level = 0;
   // CUDA graphs of fixed launch sequences (fine matvec, P_2L with CHEB)
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;   // second stream for independent work (on_side)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool graphs = true;
   struct GraphEntry {
     std::string key;
@@ -408,6 +410,22 @@ std::string graph_key(const reg_ctx* c, const char* what, const void* a, const v
   return buf;
 }
 
+// Runs `body` (launches on c->st) on the side stream after everything
+// queued on c->st so far; join_side() makes c->st wait for it. Works eagerly
+// and under stream capture (the fork and join become graph edges).
+template <typename Body>
+void on_side(reg_ctx* c, Body body) {
+  check(c, cudaEventRecord(c->ev_fork, c->st), "fork");
+  check(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork");
+  cudaStream_t main = c->st;
+  c->st = c->side;
+  body();
+  c->st = main;
+  check(c, cudaEventRecord(c->ev_join, c->side), "join");
+}
+
+void join_side(reg_ctx* c) { check(c, cudaStreamWaitEvent(c->st, c->ev_join, 0), "join"); }
+
 // ---------------------------------------------------------------------------
 // spectral operators
 
@@ -466,6 +484,46 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
                    add ? add + (size_t)g0 * fout * g.N : nullptr, g.N, ng * fout, L.tw1, c->st,
                    cheb ? &ce : nullptr);
     }
+  }
+  check_launch(c, "spectral operator");
+}
+
+// spectral() split in two for a single chunk (groups * (fin + fout) <=
+// kSpecSlots), so that independent work can run between the halves:
+// spectral_fwd leaves the output spectra in L.spec, spectral_inv transforms
+// them back (with the addend).
+void spectral_fwd(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, int groups,
+                  int fout) {
+  LevelScope ls(c, L);
+  const GridDims& g = L.g;
+  float2* sin = L.spec;
+  float2* sout = L.spec + (size_t)groups * fin * g.spec;
+  {
+    Prof P(c, REG_KC_FFT_ROWS, (double)groups * fin * (4.0 * g.N + 8.0 * g.spec));
+    fft_rows_r2c(g.n1, g.n2, in, g.N, sin, g.spec, groups * fin, L.tw1, c->st);
+  }
+  ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s);
+  a.in = sin;
+  a.in_fstride = g.spec;
+  a.out = sout;
+  a.out_fstride = g.spec;
+  a.nin = fin;
+  a.nout = fout;
+  {
+    Prof P(c, REG_KC_FFT_COLS, (double)groups * (fin + fout) * 8.0 * g.spec);
+    fft_cols(a, groups, c->st);
+  }
+  check_launch(c, "spectral operator");
+}
+
+void spectral_inv(reg_ctx* c, Level& L, int fin, int groups, float* out, int fout,
+                  const float* add) {
+  LevelScope ls(c, L);
+  const GridDims& g = L.g;
+  float2* sout = L.spec + (size_t)groups * fin * g.spec;
+  {
+    Prof P(c, REG_KC_FFT_ROWS, (double)groups * fout * (8.0 * g.spec + (add ? 8.0 : 4.0) * g.N));
+    fft_rows_c2r(g.n1, g.n2, sout, g.spec, out, g.N, add, g.N, groups * fout, L.tw1, c->st);
   }
   check_launch(c, "spectral operator");
 }
@@ -769,6 +827,9 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const int nt = L.nt;
   const float ht = L.ht;
   const int lg = lagrange(c);
+  // beta A v~: its forward transforms depend only on v~ and run on the side
+  // stream while the transport steps (which use no FFT workspace) run here
+  if (!data_only) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
   float* mt = L.fA;
   float* mt2 = L.fB;
   float* lt = nullptr;
@@ -842,7 +903,8 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   if (data_only) {
     check(c, cudaMemcpyAsync(out, L.b, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
   } else {
-    spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+    join_side(c);
+    spectral_inv(c, L, 1, 2, out, 1, L.b);
   }
 }
 
@@ -992,18 +1054,22 @@ PcgResult pcg(reg_ctx* c, long long n, Op A, Prec M, const float* rhs, float* x,
   for (int it = 0; it < maxit; ++it) {
     A(p, q);
     ++res.matvecs;
-    const double pq = dot_sync(c, p, q, n, S_PQ);
-    if (!(pq > 0.0)) {
-      res.negcurv = true;
-      if (it == 0) check(c, cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
-      break;
-    }
+    // p.q, the update (skipped on the device when p.q <= 0) and r.r are
+    // queued together and read back with one synchronisation
+    dot_async(c, p, q, n, S_PQ);
     {
       Prof P(c, REG_KC_VECTOR, 24.0 * n);
       launch_pcg_update(n, slot(c, S_RZ), slot(c, S_PQ), p, q, x, r, c->st);
     }
+    dot_async(c, r, r, n, S_RR);
+    read_slots(c, S_PQ, 2);
+    const double pq = c->hsc[S_PQ], rr = c->hsc[S_RR];
+    if (!(pq > 0.0)) {   // negative curvature: x and r were left unchanged
+      res.negcurv = true;
+      if (it == 0) check(c, cudaMemcpyAsync(x, z, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+      break;
+    }
     res.iters = it + 1;
-    const double rr = dot_sync(c, r, r, n, S_RR);
     res.relres = std::sqrt(rr) / bnorm;
     if (res.relres <= rtol) break;
     M(r, z);
@@ -1017,6 +1083,7 @@ PcgResult pcg(reg_ctx* c, long long n, Op A, Prec M, const float* rhs, float* x,
   }
   return res;
 }
+
 
 void coarse_velocity(reg_ctx* c) {
   resample(c, c->fine, c->coarse, SPOP_SCALE, 0.0, c->fine.v, 2, c->coarse.w2, nullptr);
@@ -1032,18 +1099,23 @@ void precond(reg_ctx* c, const float* r, float* z) {
   }
   Level& C = c->coarse;
   const long long nc = 2 * C.g.N;
-  // high band: (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1
-  spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
   if (c->opt.pc_solver == REG_PCSOLVER_CHEB) {
     // CHEB(k) is a polynomial in the operator, so it can run on
     // (beta A_c)^-1/2 (split operator) (beta A_c)^1/2 = I + (beta A_c)^-1 Q_c
     // with u = (beta A_c)^-1/2 s: right-hand side R (beta A)^-1 r, and the
     // result enters the prolongation without a further (beta A)^-1/2.
     resample(c, F, C, SPOP_REGPOW, -1.0, r, 2, c->crhs, nullptr);
+    // high band (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1 on
+    // the side stream, concurrently with the coarse solve (it uses only the
+    // fine grid's FFT workspace, the coarse solve only the coarse grid's)
+    on_side(c, [&] { spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr); });
     cheb(c, c->crhs, c->cx);
+    join_side(c);
     resample(c, C, F, SPOP_SCALE, 0.0, c->cx, 2, z, F.w1);
     return;
   }
+  // high band: (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1
+  spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
   // r' = (beta A)^-1/2 r; restricted low band -> crhs
   resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
   {
@@ -1216,6 +1288,9 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
     if (c->two_level)
       alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, o.coarse_nt > 0 ? o.coarse_nt : nt);
     check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
+    check(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
+    check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
+    check(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "event");
     c->dsc = dalloc<double>(c, kScalars);
     void* h = nullptr;
     check(c, cudaMallocHost(&h, kScalars * sizeof(double)), "cudaMallocHost");
@@ -1274,6 +1349,12 @@ reg_status reg_destroy(reg_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : c->evpool) cudaEventDestroy(e);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
