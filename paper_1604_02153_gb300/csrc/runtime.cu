@@ -666,6 +666,11 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   }
   check(c, cudaMemcpyAsync(L.m, L.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
   for (int j = 1; j <= L.nt; ++j) {
+    if (L.fuse_w) {   // prefilter of m_{j-1} inside the gather
+      Prof P(c, REG_KC_GATHER, 16.0 * N);
+      launch_gather_fused(L.fuse_w, g.n1, g.n2, L.m + (j - 1) * N, 0, 1, L.dX, L.m + j * N, c->st);
+      continue;
+    }
     const float* cm = coefficients(c, L, L.m + (j - 1) * N, 1, L.coef);
     {
       Prof P(c, REG_KC_GATHER, 16.0 * N);
@@ -679,8 +684,11 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   L.have_G = false;
   // div v and div v at Y_D
   spectral(c, L, SPOP_DIV, 0.0, L.v, 2, 1, L.delta, 1, nullptr);
-  const float* cd = coefficients(c, L, L.delta, 1, L.coef);
-  {
+  if (L.fuse_w) {
+    Prof P(c, REG_KC_GATHER, 16.0 * N);
+    launch_gather_fused(L.fuse_w, g.n1, g.n2, L.delta, 0, 1, L.dY, L.delta_bar, c->st);
+  } else {
+    const float* cd = coefficients(c, L, L.delta, 1, L.coef);
     Prof P(c, REG_KC_GATHER, 16.0 * N);
     launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, lagrange(c), c->st);
   }
@@ -701,6 +709,12 @@ void ensure_G(reg_ctx* c, Level& L) {
   ensure_grad_history(c, L);
   const size_t N = (size_t)L.g.N;
   for (int j = 1; j <= L.nt; ++j) {
+    if (L.fuse_w) {
+      Prof P(c, REG_KC_GATHER, 24.0 * N);
+      launch_gather_fused(L.fuse_w, L.g.n1, L.g.n2, L.gm + 2 * (j - 1) * N, (long long)N, 2, L.dX,
+                          L.G + 2 * (j - 1) * N, c->st);
+      continue;
+    }
     const float* cg = coefficients(c, L, L.gm + 2 * (j - 1) * N, 2, L.c2);
     {
       Prof P(c, REG_KC_GATHER, 24.0 * N);
@@ -748,6 +762,13 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   }
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    if (L.fuse_w) {   // prefilter of lambda_{j+1} inside the step
+      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lam, L.dY, L.delta, L.delta_bar,
+                           L.gm + 2 * j * N, lam2, L.b, c->st);
+      std::swap(lam, lam2);
+      continue;
+    }
     const float* cl = coefficients(c, L, lam, 1, L.coef);
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);

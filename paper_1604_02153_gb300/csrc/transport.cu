@@ -507,6 +507,48 @@ k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restri
   stk(out + idx, m);
 }
 
+// Prefilter + gather of F = 1 or 2 fields (fstride apart) at the departure
+// points disp, on the tile's box: the state step m_j = m_{j-1}(X_D) and the
+// history G_j = grad m_{j-1}(X_D) without a coefficient field in memory.
+template <bool P2, int W, int F>
+__global__ void __launch_bounds__(kFT, 2)
+k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long fstride,
+               const float* __restrict__ disp, float* __restrict__ out) {
+  pdl_enter();
+  using D = BoxDims<W>;
+  constexpr int H = (W - 32) / 2;
+  extern __shared__ float sm[];
+  float* stage = sm;
+  float* mid = sm + D::kStage;
+  float* box1 = mid + D::kMid;     // first field's box when F = 2
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const long long N = (long long)n1 * n2;
+  constexpr int TPR = 32 / kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
+  float d1[kFP], d2[kFP];
+  ldk(disp + idx, d1);
+  ldk(disp + N + idx, d2);
+  if (F == 2)
+    prefilter_box<W, P2, kFT>(u, n1, n2, log1, x0 - H, y0 - H, stage, mid, box1);
+  prefilter_box<W, P2, kFT>(u + (F - 1) * fstride, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
+  float o1[kFP], o2[kFP];
+#pragma unroll
+  for (int p = 0; p < kFP; ++p) {
+    int li, lj;
+    float w1[4], w2[4];
+    box_stencil<W>(H + cx + p, H + r, d1[p], d2[p], false, li, lj, w1, w2);
+    if (F == 2) o1[p] = apply_box<D::PB>(box1, li, lj, w1, w2);
+    o2[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
+  }
+  if (F == 2) {
+    stk(out + idx, o1);
+    stk(out + fstride + idx, o2);
+  } else {
+    stk(out + idx, o2);
+  }
+}
+
 // box widths with a fused kernel: halo H = 8 and H = 16
 constexpr int kFuseW[2] = {48, 64};
 
@@ -527,6 +569,14 @@ constexpr size_t first_smem() {
 }
 
 void fused_init() {
+  allow_smem(k_gather_fused<true, 48, 1>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_gather_fused<false, 48, 1>, BoxDims<48>::kSmemBytes);
+  allow_smem(k_gather_fused<true, 64, 1>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_gather_fused<false, 64, 1>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_gather_fused<true, 48, 2>, first_smem<48>());
+  allow_smem(k_gather_fused<false, 48, 2>, first_smem<48>());
+  allow_smem(k_gather_fused<true, 64, 2>, first_smem<64>());
+  allow_smem(k_gather_fused<false, 64, 2>, first_smem<64>());
   allow_smem(k_incstate_first_fused<true, 48>, first_smem<48>());
   allow_smem(k_incstate_first_fused<false, 48>, first_smem<48>());
   allow_smem(k_incstate_first_fused<true, 64>, first_smem<64>());
@@ -582,6 +632,21 @@ void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* v
   else
     launch_k(p2 ? k_incstate_first_fused<true, 64> : k_incstate_first_fused<false, 64>, grid,
              dim3(kFT), first_smem<64>(), st, n1, n2, ilog2i(n1), ht, vt, dX, G1, gm1, vtD, out);
+}
+
+void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstride, int F,
+                         const float* disp, float* out, cudaStream_t st) {
+  const dim3 grid(n1 / 32, n2 / 32);
+  const bool p2 = pow2_grid(n1, n2);
+  const int lg = ilog2i(n1);
+#define REGNK_GF(WW, FF, SM)                                                                    \
+  launch_k(p2 ? k_gather_fused<true, WW, FF> : k_gather_fused<false, WW, FF>, grid, dim3(kFT), \
+           SM, st, n1, n2, lg, u, fstride, disp, out)
+  if (W == 48 && F == 1) REGNK_GF(48, 1, BoxDims<48>::kSmemBytes);
+  else if (W == 48) REGNK_GF(48, 2, first_smem<48>());
+  else if (F == 1) REGNK_GF(64, 1, BoxDims<64>::kSmemBytes);
+  else REGNK_GF(64, 2, first_smem<64>());
+#undef REGNK_GF
 }
 
 }  // namespace regnk

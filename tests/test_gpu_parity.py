@@ -488,16 +488,20 @@ def test_fused_prefilter_step_matches_two_kernel_path(regnk, n1, n2, vmax):
     m_R, m_T, _ = (f32(a) for a in problem_data(n1, n2))
     v = f32(inputs.random_velocity(n1, n2, seed=31, vmax=vmax))
     u = f32(inputs.random_velocity(n1, n2, seed=32, vmax=1.0))
-    H = []
+    H, Gs, Js = [], [], []
     for fused in (1, 0):
         R = regnk.Registration(n1, n2, nt, 1e-2, fused_transport=fused, **pc_for(n1, n2))
         R.set_images(dev(m_R), dev(m_T))
+        g = torch.empty(2 * n1 * n2, device="cuda")
+        Js.append(R.objective_gradient(dev(v), g))   # state, delta-bar, adjoint
         out = torch.empty(2 * n1 * n2, device="cuda")
-        R.hessian_matvec(dev(v), dev(u), out)
+        R.hessian_matvec(dev(v), dev(u), out)        # G history, incremental solves
         torch.cuda.synchronize()
         H.append(out.cpu().numpy())
+        Gs.append(g.cpu().numpy())
         R.close()
     assert rel(H[0], H[1]) < 1e-6
+    assert rel(Gs[0], Gs[1]) < 1e-6 and abs(Js[0] - Js[1]) <= 1e-6 * abs(Js[1])
     if vmax == 2.0 and n1 == 128:
         # the 64^2-box path against the oracle's data term
         P = Problem(m_R, m_T, nt, 1e-2)
@@ -522,4 +526,33 @@ def test_dot_matches_fp64(regnk, n):
         ref = float(np.sum(a[off:off + m].astype(np.float64) * b[off:off + m]))
         got = R.dot(ta[off:off + m], tb[off:off + m]) if m else R.dot(ta[:0], tb[:0])
         assert abs(got - ref) <= 1e-13 * scale, (n, off, got, ref)
+    R.close()
+
+
+def test_full_size_phantom_gradient_and_hessian(regnk):
+    """The benchmark's problem at full size: 1024^2 phantom pair, nt = 8,
+    the launch configuration bench.py times (fused 48^2-box kernels,
+    programmatic launches). The oracle computes the gradient's and the GN
+    matvec's data terms in FP64 on the same FP32 inputs (about 20 s); the bar
+    is the 1e-4 of the data terms."""
+    n, nt, beta = 1024, 8, 1e-2
+    m_R, m_T = (f32(a) for a in inputs.ellipse_phantoms(n, seed=100))
+    v = f32(inputs.random_velocity(n, seed=41, vmax=0.2))
+    u = f32(inputs.random_velocity(n, seed=42, vmax=1.0))
+    R = regnk.Registration(n, n, nt, beta)
+    R.set_images(dev(m_R), dev(m_T))
+    vd, ud = dev(v), dev(u)
+    g = torch.empty(2 * n * n, device="cuda")
+    R.objective_gradient(vd, g)
+    H = torch.empty_like(g)
+    R.hessian_matvec(vd, ud, H)
+    Av, Au = torch.empty_like(g), torch.empty_like(g)
+    R.spectral(regnk.REG_SPEC_REG, vd, Av)
+    R.spectral(regnk.REG_SPEC_REG, ud, Au)
+    P = Problem(m_R, m_T, nt, beta)
+    _, g_ref = P.objective_gradient(v)
+    H_ref = P.hessian_matvec(u)
+    shape = (2, n, n)
+    assert rel(host(g, shape) - host(Av, shape), g_ref - spectral.apply_reg(v, beta, "H1")) < 1e-4
+    assert rel(host(H, shape) - host(Au, shape), H_ref - spectral.apply_reg(u, beta, "H1")) < 1e-4
     R.close()
