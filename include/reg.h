@@ -100,13 +100,15 @@ typedef struct {
                               results are identical); kernels inside the
                               library's CUDA graphs are plain launches either
                               way. 0: plain launches everywhere                */
-  int fused_transport;     /* 1 (default): with the spline model, the GN matvec's
-                              incremental state and adjoint steps compute the
-                              spline coefficients they gather from inside the step
-                              kernel (a 48^2 or 64^2 coefficient box per 32^2 tile)
-                              whenever the velocity's displacements fit the box's
-                              halo (<= 6 or <= 14 cells); results are those of the
-                              separate prefilter kernel up to FP32 rounding order.
+  int fused_transport;     /* 1 (default): with the spline model, every transport
+                              step (state, adjoint, incremental state and adjoint,
+                              and the gathers of div v at Y_D and of the gradient
+                              history) computes the spline coefficients it gathers
+                              from inside the step kernel (a 48^2 or 64^2
+                              coefficient box per 32^2 tile) whenever the
+                              velocity's displacements fit the box's halo (<= 6 or
+                              <= 14 cells); results are those of the separate
+                              prefilter kernel up to FP32 rounding order.
                               0: always a separate prefilter kernel             */
   int coarse_nt;           /* time steps of the coarse-grid problem of P_2L; 0
                               (default): the problem's nt. §3.4.2 expects the
