@@ -49,10 +49,4 @@ REG_HD int wrap_once(int i, int n) {
   return i >= n ? i - n : i;
 }
 
-// Periodic wrap of an arbitrary index.
-REG_HD int wrap_any(int i, int n) {
-  int r = i % n;
-  return r < 0 ? r + n : r;
-}
-
 }  // namespace regnk

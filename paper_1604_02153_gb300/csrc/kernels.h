@@ -170,8 +170,6 @@ void launch_sumsq_diff(const float* a, const float* b, long long n, double* part
                        double* out, cudaStream_t st);
 void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st);
 void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st);
-void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
-                  const float* x, float* y, float beta_y, cudaStream_t st);
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
                     cudaStream_t st);
 void launch_pcg_update(long long n, const double* rz, const double* pq, const float* p,

@@ -179,22 +179,8 @@ __global__ void k_compare(const unsigned* __restrict__ a, const unsigned* __rest
 }
 
 void launch_compare(const float* a, const float* b, long long n, int* flag, cudaStream_t st) {
-  launch_k(k_compare, dim3(nblocks(n)), dim3(kRT), 0, st, reinterpret_cast<const unsigned*>(a), reinterpret_cast<const unsigned*>(b), n, flag);
-}
-
-// y = (alpha_num/alpha_den * cs) x + beta_y y, coefficients from device FP64 scalars.
-__global__ void k_axpby(long long n, const double* an, const double* ad, double cs,
-                        const float* __restrict__ x, float* __restrict__ y, float beta_y) {
-  pdl_enter();
-  const float alpha = (float)((*an / *ad) * cs);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    y[i] = fmaf(alpha, x[i], beta_y * y[i]);
-}
-
-void launch_axpby(long long n, const double* alpha_num, const double* alpha_den, double cs,
-                  const float* x, float* y, float beta_y, cudaStream_t st) {
-  launch_k(k_axpby, dim3(nblocks(n)), dim3(kRT), 0, st, n, alpha_num, alpha_den, cs, x, y, beta_y);
+  launch_k(k_compare, dim3(nblocks(n)), dim3(kRT), 0, st, reinterpret_cast<const unsigned*>(a),
+           reinterpret_cast<const unsigned*>(b), n, flag);
 }
 
 // z may alias x or y (elementwise, same index)
