@@ -143,19 +143,28 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
 // follows in the same block: box[r * (W + 1) + c] is the coefficient of node
 // (bx0 + c, by0 + r); all NT threads of the block take part. The box's
 // samples with a kL-sample halo are staged in
-// `stage` ((W + 2 kL) rows of pitch W + 2 kL + 1) and the x pass goes to
-// `mid` ((W + 2 kL) rows of pitch W + 1); `box` may alias `stage`. Same
+// `stage` (W + 2 kL rows of pitch PS) and the x pass goes to `mid`
+// (transposed: W rows of pitch PT); `box` may alias `stage`. Same
 // recursions and segment length as prefilter_tile, so the coefficients are
 // those of k_prefilter up to the order of FP32 rounding. Ends with a block
 // barrier.
+// Pitches of the staged samples (rows) and of the x-pass output (stored
+// transposed, one column of the box per row of `mid`): multiples of 4 floats
+// with an odd quotient, so that each recursion chain reads its 34
+// consecutive samples as float4 and the 8 chains of a quarter warp (8
+// consecutive rows or columns) hit 8 different 16-byte bank groups.
+constexpr int quad_pitch(int n) { return ((n + 3) / 4) % 2 ? (n + 3) / 4 * 4 : (n + 3) / 4 * 4 + 4; }
+
 template <int W>
 struct BoxDims {
-  static constexpr int WS = W + 2 * kL;   // staged width and height
-  static constexpr int PS = WS + 1;       // odd pitches
-  static constexpr int PB = W + 1;
-  static constexpr int kStage = WS * PS;  // floats
-  static constexpr int kMid = WS * PB;
+  static constexpr int WS = W + 2 * kL;      // staged width and height
+  static constexpr int PS = quad_pitch(WS);  // row pitch of the staged samples
+  static constexpr int PT = quad_pitch(WS);  // row pitch of the transposed x-pass output
+  static constexpr int PB = W + 1;           // odd pitch of the coefficient box
+  static constexpr int kStage = WS * PS;     // floats
+  static constexpr int kMid = W * PT;
   static constexpr size_t kSmemBytes = sizeof(float) * (kStage + kMid);
+  static_assert(PS >= WS + 2 && PT >= WS + 2, "float4 reads run 2 samples past a chain");
 };
 
 template <int W, bool P2, int NT = kPThreads>
@@ -163,7 +172,7 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
                                               int log1, int bx0, int by0, float* stage,
                                               float* mid, float* box) {
   using D = BoxDims<W>;
-  constexpr int WS = D::WS, PS = D::PS, PB = D::PB;
+  constexpr int WS = D::WS, PS = D::PS, PT = D::PT, PB = D::PB;
   // The staged rows are read as float4 from a 4-aligned first column (a
   // float4 never straddles the periodic seam since n1 % 4 == 0) and the
   // first `off` columns of the first vector are dropped. Row-major thread
@@ -200,22 +209,43 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
   }
   __syncthreads();
   constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
-  for (int q = t; q < WS * kSegs; q += NT) {   // x recursions, conflict-free as above
+  constexpr int kQ = (kLen + 3) / 4;   // float4 reads per chain
+  // x recursions: a warp walks 32 consecutive staged rows of one segment;
+  // the outputs go to mid transposed (mid[column * PT + row])
+  for (int q = t; q < WS * kSegs; q += NT) {
     const int r = q % WS, sg = q / WS;
-    float v[kLen];
+    float v[kQ * 4];
+    const float4* src4 = reinterpret_cast<const float4*>(stage + r * PS + sg * kSeg);
 #pragma unroll
-    for (int k = 0; k < kLen; ++k) v[k] = stage[r * PS + sg * kSeg + k];
-    float* row = mid + r * PB + sg * kSeg;
-    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { row[o] = x; });
+    for (int i = 0; i < kQ; ++i) {
+      const float4 x = src4[i];
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+    float* col = mid + sg * kSeg * PT + r;
+    bspline_recursions<kLen, kSeg>(reinterpret_cast<float(&)[kLen]>(v),
+                                   [&](int o, float x) { col[o * PT] = x; });
   }
   __syncthreads();
-  for (int q = t; q < W * kSegs; q += NT) {    // y recursions
+  // y recursions: a warp walks 32 consecutive box columns of one segment,
+  // each reading its column of the x-pass output as float4
+  for (int q = t; q < W * kSegs; q += NT) {
     const int c = q % W, sg = q / W;
-    float v[kLen];
+    float v[kQ * 4];
+    const float4* src4 = reinterpret_cast<const float4*>(mid + c * PT + sg * kSeg);
 #pragma unroll
-    for (int k = 0; k < kLen; ++k) v[k] = mid[(sg * kSeg + k) * PB + c];
-    float* col = box + sg * kSeg * PB + c;
-    bspline_recursions<kLen, kSeg>(v, [&](int o, float x) { col[o * PB] = x; });
+    for (int i = 0; i < kQ; ++i) {
+      const float4 x = src4[i];
+      v[4 * i] = x.x;
+      v[4 * i + 1] = x.y;
+      v[4 * i + 2] = x.z;
+      v[4 * i + 3] = x.w;
+    }
+    float* colb = box + sg * kSeg * PB + c;
+    bspline_recursions<kLen, kSeg>(reinterpret_cast<float(&)[kLen]>(v),
+                                   [&](int o, float x) { colb[o * PB] = x; });
   }
   __syncthreads();
 }
