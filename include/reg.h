@@ -115,6 +115,11 @@ typedef struct {
                               preconditioner's PDE solves to need little
                               accuracy; nt / 2 keeps the displacement per step
                               in coarse cells equal to the fine grid's         */
+  int coarse_interp;       /* interpolation model of P_2L's coarse problem: -1
+                              (default) the problem's model, or REG_INTERP_SPLINE
+                              / REG_INTERP_LAGRANGE (cubic Lagrange needs no
+                              prefilter; §3.4.2 expects the preconditioner's PDE
+                              solves to need little accuracy)                  */
 } reg_options;
 
 typedef struct {

@@ -37,7 +37,7 @@ class Solver:
     def __init__(self, problem, precond="2L", pc_solver="cheb", cheb_iters=10,
                  pc_eps=0.1, gabs=1e-5, max_newton=50, max_pcg=100,
                  lanczos_steps=30, emax_safety=1.05, lanczos_v0=None,
-                 c1=1e-4, max_backtracks=10, coarse_nt=None):
+                 c1=1e-4, max_backtracks=10, coarse_nt=None, coarse_kind=None):
         self.p = problem
         self.precond = precond
         self.pc_solver = pc_solver
@@ -60,8 +60,9 @@ class Solver:
             # coarse_nt: time steps of the coarse problem (default: the same
             # nt; §3.4.2 expects the preconditioner's PDE solves to need
             # little accuracy)
+            # coarse_kind: its interpolation model (default: the problem's)
             self.coarse = Problem(spectral.restrict(p.m_R), spectral.restrict(p.m_T),
-                                  coarse_nt or p.nt, p.beta, p.reg_norm, p.kind)
+                                  coarse_nt or p.nt, p.beta, p.reg_norm, coarse_kind or p.kind)
 
     # -- preconditioners -----------------------------------------------------
     def precond_reg(self, r):

@@ -69,6 +69,7 @@ struct Level {
   bool have_div = false;    // delta, delta_bar, dY valid for v
   bool have_G = false;      // G valid for v
   int fuse_w = 0;           // box width of the fused prefilter+step kernels for v (0: off)
+  bool lagrange = false;    // interpolation model of this level (cubic Lagrange or spline)
 };
 
 }  // namespace
@@ -275,7 +276,6 @@ void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
   L.spec = dalloc<float2>(c, kSpecSlots * (size_t)L.g.spec);
 }
 
-bool lagrange(const reg_ctx* c) { return c->opt.interp == REG_INTERP_LAGRANGE; }
 
 // Attributes the launches inside its lifetime to a grid level (profiling).
 class LevelScope {
@@ -597,7 +597,7 @@ void resample_square(reg_ctx* c, int na, int nb, const float* in, int F, float* 
 // spline model; the samples themselves for Lagrange)
 const float* coefficients(reg_ctx* c, Level& L, const float* u, int F, float* dst) {
   LevelScope ls(c, L);
-  if (lagrange(c)) return u;
+  if (L.lagrange) return u;
   Prof P(c, REG_KC_PREFILTER, 16.0 * F * L.g.N);
   for (int f = 0; f < F; ++f)
     launch_prefilter(L.g.n1, L.g.n2, u + (size_t)f * L.g.N, L.tmp, dst + (size_t)f * L.g.N, 1, c->st);
@@ -650,12 +650,12 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   const float* cv = coefficients(c, L, L.v, 2, L.cv);
   {
     Prof P(c, REG_KC_DEPARTURE, 32.0 * N);
-    launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, lagrange(c), c->st);
+    launch_departure(g.n1, g.n2, L.ht, L.v, cv, L.dX, L.dY, L.lagrange, c->st);
   }
   // largest displacement component (cells): decides whether the fused
   // prefilter+step kernels' coefficient box covers every stencil
   L.fuse_w = 0;
-  if (!lagrange(c) && c->opt.fused_transport) {
+  if (!L.lagrange && c->opt.fused_transport) {
     {
       Prof P(c, REG_KC_REDUCE, 16.0 * N);
       launch_maxabs(L.dX, 2 * (long long)N, c->partialf, slot(c, S_DX), c->st);
@@ -674,7 +674,7 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
     const float* cm = coefficients(c, L, L.m + (j - 1) * N, 1, L.coef);
     {
       Prof P(c, REG_KC_GATHER, 16.0 * N);
-      launch_state_step(g.n1, g.n2, cm, L.dX, L.m + j * N, lagrange(c), c->st);
+      launch_state_step(g.n1, g.n2, cm, L.dX, L.m + j * N, L.lagrange, c->st);
     }
   }
   check_launch(c, "state solve");
@@ -690,7 +690,7 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   } else {
     const float* cd = coefficients(c, L, L.delta, 1, L.coef);
     Prof P(c, REG_KC_GATHER, 16.0 * N);
-    launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, lagrange(c), c->st);
+    launch_gather(g.n1, g.n2, cd, L.dY, L.delta_bar, 1, 0, L.lagrange, c->st);
   }
   check_launch(c, "div v");
 }
@@ -718,7 +718,7 @@ void ensure_G(reg_ctx* c, Level& L) {
     const float* cg = coefficients(c, L, L.gm + 2 * (j - 1) * N, 2, L.c2);
     {
       Prof P(c, REG_KC_GATHER, 24.0 * N);
-      launch_gather(L.g.n1, L.g.n2, cg, L.dX, L.G + 2 * (j - 1) * N, 2, (long long)N, lagrange(c), c->st);
+      launch_gather(L.g.n1, L.g.n2, cg, L.dX, L.G + 2 * (j - 1) * N, 2, (long long)N, L.lagrange, c->st);
     }
   }
   check_launch(c, "G history");
@@ -773,7 +773,7 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
       launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
-                          lam2, L.b, lagrange(c), c->st);
+                          lam2, L.b, L.lagrange, c->st);
     }
     std::swap(lam, lam2);
   }
@@ -801,7 +801,7 @@ void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
   a.n2 = L.g.n2;
   a.log1 = L.g.log1;
   a.nt = L.nt;
-  a.lagrange = lagrange(c);
+  a.lagrange = L.lagrange;
   a.N = L.g.N;
   a.ht = L.ht;
   a.vt = vt;
@@ -824,7 +824,7 @@ void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
   // incremental state step 48, each incremental adjoint step 48, each of the
   // 2 nt + 1 prefilters 8 (spline only)
   const double per_point = 52.0 + 48.0 * (L.nt - 1) + 48.0 * L.nt +
-                           (lagrange(c) ? 0.0 : 8.0 * (2 * L.nt + 1));
+                           (L.lagrange ? 0.0 : 8.0 * (2 * L.nt + 1));
   Prof P(c, REG_KC_MATVEC, (double)L.g.N * per_point);
   check(c, launch_gn_matvec(a, c->st), "persistent matvec launch");
 }
@@ -847,7 +847,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const size_t N = (size_t)gd.N;
   const int nt = L.nt;
   const float ht = L.ht;
-  const int lg = lagrange(c);
+  const int lg = L.lagrange;
   // beta A v~: its forward transforms depend only on v~ and run on the side
   // stream while the transport steps (which use no FFT workspace) run here
   if (!data_only) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
@@ -1272,6 +1272,7 @@ reg_status reg_default_options(reg_options* o) {
   o->programmatic_launch = 1;
   o->fused_transport = 1;
   o->coarse_nt = 0;
+  o->coarse_interp = -1;
   return REG_OK;
 }
 
@@ -1289,7 +1290,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
       (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
       o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0 ||
-      o.coarse_nt < 0 || o.coarse_nt > 4096)
+      o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1)
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1302,6 +1303,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->beta = beta;
   c->nt = nt;
   c->two_level = (o.precond == REG_PC_2L);
+  c->fine.lagrange = (o.interp == REG_INTERP_LAGRANGE);
+  c->coarse.lagrange = o.coarse_interp < 0 ? c->fine.lagrange : (o.coarse_interp == REG_INTERP_LAGRANGE);
   c->persistent = (o.persistent_matvec != 0);
   const reg_status s = guarded(c, [&] {
     fused_init();   // shared-memory limit of the fused step kernels on this device
@@ -1445,7 +1448,7 @@ reg_status reg_departure_points(reg_ctx* c, const float* v, float* dX, float* dY
   return guarded(c, [&] {
     Level& F = c->fine;
     const float* cv = coefficients(c, F, v, 2, F.c2);
-    launch_departure(F.g.n1, F.g.n2, F.ht, v, cv, dX, dY, lagrange(c), c->st);
+    launch_departure(F.g.n1, F.g.n2, F.ht, v, cv, dX, dY, F.lagrange, c->st);
     check_launch(c, "departure points");
   });
 }
@@ -1456,7 +1459,7 @@ reg_status reg_interpolate(reg_ctx* c, const float* u, const float* disp, float*
   return guarded(c, [&] {
     Level& F = c->fine;
     const float* cu = coefficients(c, F, u, 1, F.coef);
-    launch_gather(F.g.n1, F.g.n2, cu, disp, out, 1, 0, lagrange(c), c->st);
+    launch_gather(F.g.n1, F.g.n2, cu, disp, out, 1, 0, F.lagrange, c->st);
     check_launch(c, "interpolate");
   });
 }
@@ -1477,7 +1480,7 @@ reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* ou
       case REG_SPEC_LOWPASS: spectral(c, F, SPOP_LOWPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_HIGHPASS: spectral(c, F, SPOP_HIGHPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_PREFILTER:
-        if (lagrange(c)) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
+        if (F.lagrange) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
         coefficients(c, F, in, 1, out);
         break;
       default: fail(c, REG_EINVAL, "unknown spectral op %d", op);

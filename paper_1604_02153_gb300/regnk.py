@@ -47,7 +47,8 @@ class reg_options(ctypes.Structure):
                 ("lanczos_seed", ctypes.c_ulonglong), ("max_backtracks", ctypes.c_int),
                 ("armijo_c1", ctypes.c_double), ("persistent_matvec", ctypes.c_int),
                 ("inject_barrier_timeout", ctypes.c_int), ("programmatic_launch", ctypes.c_int),
-                ("fused_transport", ctypes.c_int), ("coarse_nt", ctypes.c_int)]
+                ("fused_transport", ctypes.c_int), ("coarse_nt", ctypes.c_int),
+                ("coarse_interp", ctypes.c_int)]
 
 
 class reg_info(ctypes.Structure):

@@ -317,20 +317,22 @@ def test_full_size_transport_symmetry_positivity(regnk):
     R.close()
 
 
-@pytest.mark.parametrize("coarse_nt", [0, 2])
-def test_preconditioners(regnk, coarse_nt):
+@pytest.mark.parametrize("coarse_nt,coarse_interp", [(0, -1), (2, -1), (2, 1)])
+def test_preconditioners(regnk, coarse_nt, coarse_interp):
     n, nt, beta = 128, 4, 1e-2
     m_R, m_T, v = problem_data(n, n)
     r = inputs.random_velocity(n, seed=27, vmax=1.0)
     for pc in (regnk.REG_PC_REG, regnk.REG_PC_2L):
-        R = regnk.Registration(n, n, nt, beta, precond=pc, coarse_nt=coarse_nt)
+        R = regnk.Registration(n, n, nt, beta, precond=pc, coarse_nt=coarse_nt,
+                               coarse_interp=coarse_interp)
         R.set_images(dev(m_R), dev(m_T))
         R.objective_gradient(dev(v), None)
         z = torch.empty(2 * n * n, device="cuda")
         R.precond_apply(dev(r), z)
         P = Problem(m_R, m_T, nt, beta)
         P.state_solve(v)
-        S = Solver(P, precond="REG" if pc == regnk.REG_PC_REG else "2L", coarse_nt=coarse_nt or None)
+        S = Solver(P, precond="REG" if pc == regnk.REG_PC_REG else "2L", coarse_nt=coarse_nt or None,
+                   coarse_kind="lagrange" if coarse_interp == 1 else None)
         if pc == regnk.REG_PC_2L:
             emin, emax = R.eigen_bounds()
             S.eig = {"emin": emin, "emax": emax, "beta": beta}

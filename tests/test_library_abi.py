@@ -49,7 +49,7 @@ def test_default_options(lib):
     assert abs(o.gabs - 1e-5) < 1e-20 and o.lanczos_steps == 30
     assert o.max_backtracks == 10 and abs(o.armijo_c1 - 1e-4) < 1e-20
     assert o.persistent_matvec == 0 and o.programmatic_launch == 1 and o.fused_transport == 1
-    assert o.coarse_nt == 0
+    assert o.coarse_nt == 0 and o.coarse_interp == -1
 
 
 def _create(lib, n1, n2, nt, beta, **kw):
@@ -69,6 +69,7 @@ def _create(lib, n1, n2, nt, beta, **kw):
     (64, 64, 4, 1e-2, {"interp": 2}),
     (32, 32, 4, 1e-2, {"precond": 1}),  # two-level needs a 32^2 coarse grid at least
     (64, 64, 4, 1e-2, {"coarse_nt": -1}),
+    (64, 64, 4, 1e-2, {"coarse_interp": 2}),
 ])
 def test_invalid_arguments_rejected_on_host(lib, n1, n2, nt, beta, kw):
     s, h = _create(lib, n1, n2, nt, beta, **kw)
