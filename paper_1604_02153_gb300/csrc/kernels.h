@@ -135,9 +135,10 @@ void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* v
                                  const float* G1, const float* gm1, float* vtD, float* out,
                                  cudaStream_t st);
 void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
-                          const float* vt, const float* vtD, const float* G,
-                          const float* gm, float* out, int first, int lagrange,
-                          cudaStream_t st);
+                          const float* vt, float* vtD, const float* G, const float* gm,
+                          float* out, int first, int lagrange, cudaStream_t st,
+                          const float* cvt = nullptr, const float* gm_nt = nullptr,
+                          float* b = nullptr);
 
 // matvec.cu: persistent Gauss-Newton data-term matvec (one cooperative launch)
 struct MatvecArgs {

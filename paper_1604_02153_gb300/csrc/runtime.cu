@@ -878,19 +878,23 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       lt2 = mt2;
     }
   } else {
+    // v~(X_D) is gathered by the first step; the last one (nt >= 2) also
+    // writes lambda~_nt and starts b~
     const float* cvt = coefficients(c, L, vt, 2, L.c2);
-    {
-      Prof P(c, REG_KC_GATHER, 24.0 * N);
-      launch_gather(gd.n1, gd.n2, cvt, L.dX, L.vtD, 2, (long long)N, lg, c->st);
-    }
     for (int j = 1; j <= nt; ++j) {
       const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
+      const bool last = (j == nt && nt >= 2);
       {
-        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 36.0 : 48.0) * N);
+        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 60.0 : (last ? 64.0 : 48.0)) * N);
         launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
-                             L.gm + 2 * j * N, mt2, j == 1, lg, c->st);
+                             L.gm + 2 * j * N, mt2, j == 1, lg, c->st, j == 1 ? cvt : nullptr,
+                             last ? L.gm + 2 * nt * N : nullptr, last ? L.b : nullptr);
       }
       std::swap(mt, mt2);
+    }
+    if (nt >= 2) {   // mt holds lambda~_nt
+      lt = mt;
+      lt2 = mt2;
     }
   }
   check_launch(c, "incremental state");

@@ -269,34 +269,50 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
 // One forward step of the incremental state (Gauss-Newton, §3.3.2):
 //   m~_j = m~_{j-1}(X_D) - h_t/2 (v~(X_D) . grad m_{j-1}(X_D) + v~ . grad m_j)
 // G = grad m_{j-1}(X_D) (2 fields), vtD = v~(X_D) (2 fields), gm = grad m_j.
-// first = 1 for j = 1 where m~_0 = 0.
+// first = 1 for j = 1 where m~_0 = 0; then, if cvt (the interpolation
+// coefficients of v~, or v~ itself for the Lagrange model) is given, v~(X_D)
+// is gathered here and written to vtD instead of being read from it.
+// gm_nt, b: non-NULL for the last step j = nt, which writes
+// lambda~_nt = -m~_nt and b = h_t/2 lambda~_nt grad m_nt (k_adjoint_init).
 template <bool P2>
 __global__ void __launch_bounds__(kPT)
 k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ coef,
                 const float* __restrict__ dX, const float* __restrict__ vt,
-                const float* __restrict__ vtD, const float* __restrict__ G,
+                float* __restrict__ vtD, const float* __restrict__ G,
                 const float* __restrict__ gm, float* __restrict__ out, int first,
-                int lagrange) {
+                int lagrange, const float* __restrict__ cvt, const float* __restrict__ gm_nt,
+                float* __restrict__ b) {
   pdl_enter();
   const long long N = (long long)n1 * n2;
   const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
   if (idx >= N) return;
-  float m[kSP];
+  float m[kSP], w1[kSP], w2[kSP];
 #pragma unroll
   for (int p = 0; p < kSP; ++p) m[p] = 0.f;
-  if (!first) {
+  if (!first || cvt) {
     int i, j;
     split_index<P2>(idx, n1, log1, i, j);
     float x1[kSP], x2[kSP];
     ldk(dX + idx, x1);
     ldk(dX + N + idx, x2);
 #pragma unroll
-    for (int p = 0; p < kSP; ++p)
-      m[p] = apply_stencil(make_stencil<P2>(i + p, j, x1[p], x2[p], n1, n2, log1, lagrange), coef);
+    for (int p = 0; p < kSP; ++p) {
+      const Stencil S = make_stencil<P2>(i + p, j, x1[p], x2[p], n1, n2, log1, lagrange);
+      if (!first) m[p] = apply_stencil(S, coef);
+      if (cvt) {
+        w1[p] = apply_stencil(S, cvt);
+        w2[p] = apply_stencil(S, cvt + N);
+      }
+    }
   }
-  float w1[kSP], w2[kSP], G1[kSP], G2[kSP], u1[kSP], u2[kSP], g1[kSP], g2[kSP];
-  ldk(vtD + idx, w1);
-  ldk(vtD + N + idx, w2);
+  if (cvt) {
+    stk(vtD + idx, w1);
+    stk(vtD + N + idx, w2);
+  } else {
+    ldk(vtD + idx, w1);
+    ldk(vtD + N + idx, w2);
+  }
+  float G1[kSP], G2[kSP], u1[kSP], u2[kSP], g1[kSP], g2[kSP];
   ldk(G + idx, G1);
   ldk(G + N + idx, G2);
   ldk(vt + idx, u1);
@@ -306,15 +322,33 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
 #pragma unroll
   for (int p = 0; p < kSP; ++p)
     m[p] -= 0.5f * ht * (w1[p] * G1[p] + w2[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
-  stk(out + idx, m);
+  if (!b) {
+    stk(out + idx, m);
+    return;
+  }
+  float gn1[kSP], gn2[kSP], lam[kSP], b1[kSP], b2[kSP];
+  ldk(gm_nt + idx, gn1);
+  ldk(gm_nt + N + idx, gn2);
+  const float hh = 0.5f * ht;
+#pragma unroll
+  for (int p = 0; p < kSP; ++p) {
+    lam[p] = -m[p];
+    b1[p] = hh * lam[p] * gn1[p];
+    b2[p] = hh * lam[p] * gn2[p];
+  }
+  stk(out + idx, lam);
+  stk(b + idx, b1);
+  stk(b + N + idx, b2);
 }
 
 void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
-                          const float* vt, const float* vtD, const float* G, const float* gm,
-                          float* out, int first, int lagrange, cudaStream_t st) {
+                          const float* vt, float* vtD, const float* G, const float* gm,
+                          float* out, int first, int lagrange, cudaStream_t st,
+                          const float* cvt, const float* gm_nt, float* b) {
   const long long N = (long long)n1 * n2;
   launch_k(pick(n1, n2, k_incstate_step<true>, k_incstate_step<false>), dim3(step_blocks(N)),
-           dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange);
+           dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange,
+           cvt, gm_nt, b);
 }
 
 // ---------------------------------------------------------------------------
