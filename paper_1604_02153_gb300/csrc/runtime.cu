@@ -885,7 +885,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
       const bool last = (j == nt && nt >= 2);
       {
-        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 60.0 : (last ? 64.0 : 48.0)) * N);
+        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 : (last ? 64.0 : 48.0)) * N);
         launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
                              L.gm + 2 * j * N, mt2, j == 1, lg, c->st, j == 1 ? cvt : nullptr,
                              last ? L.gm + 2 * nt * N : nullptr, last ? L.b : nullptr);
