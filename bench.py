@@ -348,7 +348,8 @@ def run_batch(args):
 
 def learned_warm_start(R, v, ok, dev, pairs=4):
     """Cold versus warm start (see the module doc). Each solve is timed alone
-    between device synchronisations."""
+    between device synchronisations and starts on freshly set images, so both
+    pay for the reference gradient at v = 0."""
     import torch
     from paper_1604_02153_gb300 import regnk, warmstart
     theta, record = warmstart.load_params()
@@ -362,8 +363,8 @@ def learned_warm_start(R, v, ok, dev, pairs=4):
     rows = {"cold": [], "warm": []}
     accepted = 0
     for i in range(pairs):
-        Rh.set_images(mR[i], mT[i])
         for mode in ("cold", "warm", "cold", "warm"):     # second pass is measured
+            Rh.set_images(mR[i], mT[i])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             if mode == "warm":
