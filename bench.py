@@ -28,6 +28,9 @@ roofline  = the kernel class with the largest device time: algorithmic
             steps (every launch bracketed by events on the launching stream,
             event nodes inside the replayed graphs), against the measured HBM
             copy bandwidth.
+step_tiles = (threads per block, points per thread) of the unfused
+            adjoint and incremental-state step kernels on each grid level, as
+            reg_create's timing of the nine shapes chose them.
 cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
             timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
 learned_warm_start = the trained warm-start network (weights committed with
@@ -561,6 +564,7 @@ def main():
                         "d2h_bytes_per_step": int(h_v.numel() * 4)},
                 "gpu_launches": int(launches),
                 "roofline": roof,
+                "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
                 "clocks": clocks.summary()}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()

@@ -120,6 +120,16 @@ typedef struct {
                               / REG_INTERP_LAGRANGE (cubic Lagrange needs no
                               prefilter; §3.4.2 expects the preconditioner's PDE
                               solves to need little accuracy)                  */
+  int step_tile;           /* tile shape of the adjoint and incremental-state step
+                              kernels where they run unfused (cubic Lagrange,
+                              or displacements beyond the fused kernels' box):
+                              k = 1..9 is 128 << ((k-1)/3) threads per block,
+                              1 << ((k-1)%3) adjacent points per thread; 0: the
+                              built-in shape (k = 5, 256 x 2); -1 (default):
+                              reg_create times the nine shapes on each grid
+                              level, once per grid and interpolation model in
+                              the process, and keeps the fastest. Results do
+                              not depend on the shape                          */
 } reg_options;
 
 typedef struct {
@@ -406,6 +416,10 @@ reg_status reg_profile_read(reg_ctx* ctx, int level, int kclass, double* ms, lon
 /* Kernels launched by the library in this process so far (all contexts),
  * counting every kernel node of every CUDA graph replay. */
 long long reg_launch_count(void);
+/* Tile shapes the context's step kernels use (see reg_options.step_tile):
+ * tiles[0..3] = adjoint and incremental-state step on the problem grid, then
+ * on the coarse grid of P_2L (0 without one). tiles: 4 ints, host. */
+reg_status reg_step_tiles(const reg_ctx* ctx, int* tiles);
 
 #ifdef __cplusplus
 }

@@ -113,7 +113,14 @@ void launch_state_step(int n1, int n2, const float* coef, const float* dX, float
                        int lagrange, cudaStream_t st);
 void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const float* m1,
                          const float* gm, float* lam, float* b, float sign, cudaStream_t st);
-void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
+// Tile shapes of the step kernels (launch_adjoint_step, launch_incstate_step):
+// index 1..kStepTiles, threads per block 128 << ((k - 1) / 3), points per
+// thread 1 << ((k - 1) % 3).
+constexpr int kStepTiles = 9;
+constexpr int kDefaultStepTile = 5;   // 256 threads x 2 points
+inline int step_tile_threads(int k) { return 128 << ((k - 1) / 3); }
+inline int step_tile_points(int k) { return 1 << ((k - 1) % 3); }
+void launch_adjoint_step(int tile, int n1, int n2, float ht, float wb, const float* coef,
                          const float* dY, const float* delta, const float* delta_bar,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st);
@@ -134,7 +141,7 @@ void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstrid
 void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
                                  const float* G1, const float* gm1, float* vtD, float* out,
                                  cudaStream_t st);
-void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
+void launch_incstate_step(int tile, int n1, int n2, float ht, const float* coef, const float* dX,
                           const float* vt, float* vtD, const float* G, const float* gm,
                           float* out, int first, int lagrange, cudaStream_t st,
                           const float* cvt = nullptr, const float* gm_nt = nullptr,

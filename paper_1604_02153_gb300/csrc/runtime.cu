@@ -10,7 +10,10 @@
 #include <cstring>
 #include <functional>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -70,6 +73,8 @@ struct Level {
   bool have_G = false;      // G valid for v
   int fuse_w = 0;           // box width of the fused prefilter+step kernels for v (0: off)
   bool lagrange = false;    // interpolation model of this level (cubic Lagrange or spline)
+  int tile_adj = kDefaultStepTile;   // tile shapes of k_adjoint_step and k_incstate_step
+  int tile_inc = kDefaultStepTile;
 };
 
 }  // namespace
@@ -308,6 +313,88 @@ struct LaunchModeScope {
   explicit LaunchModeScope(int mode) : saved(t_programmatic_launch) { t_programmatic_launch = mode; }
   ~LaunchModeScope() { t_programmatic_launch = saved; }
 };
+
+// Tile shapes of the step kernels (k_adjoint_step, k_incstate_step) for a
+// level. step_tile > 0 fixes the shape, 0 takes the default; -1 times every
+// shape on this level's grid and keeps the fastest, once per (device, grid,
+// interpolation model) in this process: later contexts (a batch of problems
+// on the same grids) reuse the choice. The timing runs the middle step of
+// each kernel on the level's own buffers, zeroed first (every stencil at its
+// own node: the same loads and arithmetic as a solve, in the same pattern
+// up to the displacement), eight launches at a time, best of three; the
+// default shape is kept unless another one is more than 3 % faster.
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tiles;
+
+void choose_step_tiles(reg_ctx* c, Level& L) {
+  const int o = c->opt.step_tile;
+  if (o >= 0) {
+    L.tile_adj = L.tile_inc = (o > 0 ? o : kDefaultStepTile);
+    return;
+  }
+  const auto key = std::make_tuple(c->device, L.g.n1, L.g.n2, (int)L.lagrange);
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    const auto it = g_tiles.find(key);
+    if (it != g_tiles.end()) {
+      L.tile_adj = it->second.first;
+      L.tile_inc = it->second.second;
+      return;
+    }
+  }
+  const size_t N = (size_t)L.g.N;
+  for (float* p : {L.coef, L.delta, L.delta_bar})
+    check(c, cudaMemsetAsync(p, 0, N * sizeof(float), c->st), "memset");
+  for (float* p : {L.dX, L.dY, L.gm, L.G, L.vtD, L.b, L.w1})
+    check(c, cudaMemsetAsync(p, 0, 2 * N * sizeof(float), c->st), "memset");
+  LaunchModeScope plain(0);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  check(c, cudaEventCreate(&e0), "cudaEventCreate");
+  const cudaError_t ee = cudaEventCreate(&e1);
+  if (ee != cudaSuccess) cudaEventDestroy(e0);
+  check(c, ee, "cudaEventCreate");
+  const int n1 = L.g.n1, n2 = L.g.n2, lg = L.lagrange ? 1 : 0;
+  const float ht = L.ht;
+  auto best_ms = [&](const std::function<void()>& launch) {
+    launch();
+    launch();
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, c->st);
+      for (int r = 0; r < 8; ++r) launch();
+      cudaEventRecord(e1, c->st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        break;
+      best = std::fmin(best, ms);
+    }
+    return best;
+  };
+  float t_adj[kStepTiles + 1], t_inc[kStepTiles + 1];
+  for (int k = 1; k <= kStepTiles; ++k) {
+    t_adj[k] = best_ms([&] {
+      launch_adjoint_step(k, n1, n2, ht, ht, L.coef, L.dY, L.delta, L.delta_bar, L.gm, L.fA, L.b,
+                          lg, c->st);
+    });
+    t_inc[k] = best_ms([&] {
+      launch_incstate_step(k, n1, n2, ht, L.coef, L.dX, L.w1, L.vtD, L.G, L.gm, L.fB, 0, lg, c->st);
+    });
+  }
+  const cudaError_t e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  check(c, e, "step tile timing");
+  auto pick_best = [](const float* t) {
+    int b = kDefaultStepTile;
+    for (int k = 1; k <= kStepTiles; ++k)
+      if (t[k] < t[b]) b = k;
+    return (t[b] < 0.97f * t[kDefaultStepTile]) ? b : kDefaultStepTile;
+  };
+  L.tile_adj = pick_best(t_adj);
+  L.tile_inc = pick_best(t_inc);
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  g_tiles[key] = {L.tile_adj, L.tile_inc};
+}
 
 // Runs `body` (a fixed sequence of launches on c->st, no host synchronisation)
 // as a CUDA graph: the first call of a key runs eagerly, the second captures
@@ -772,8 +859,8 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     const float* cl = coefficients(c, L, lam, 1, L.coef);
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
-      launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
-                          lam2, L.b, L.lagrange, c->st);
+      launch_adjoint_step(L.tile_adj, gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar,
+                          L.gm + 2 * j * N, lam2, L.b, L.lagrange, c->st);
     }
     std::swap(lam, lam2);
   }
@@ -886,7 +973,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       const bool last = (j == nt && nt >= 2);
       {
         Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 : (last ? 64.0 : 48.0)) * N);
-        launch_incstate_step(gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+        launch_incstate_step(L.tile_inc, gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
                              L.gm + 2 * j * N, mt2, j == 1, lg, c->st, j == 1 ? cvt : nullptr,
                              last ? L.gm + 2 * nt * N : nullptr, last ? L.b : nullptr);
       }
@@ -919,8 +1006,8 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     const float* cl = coefficients(c, L, lt, 1, L.coef);
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
-      launch_adjoint_step(gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar, L.gm + 2 * j * N,
-                          lt2, L.b, lg, c->st);
+      launch_adjoint_step(L.tile_adj, gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar,
+                          L.gm + 2 * j * N, lt2, L.b, lg, c->st);
     }
     std::swap(lt, lt2);
   }
@@ -1277,6 +1364,7 @@ reg_status reg_default_options(reg_options* o) {
   o->fused_transport = 1;
   o->coarse_nt = 0;
   o->coarse_interp = -1;
+  o->step_tile = -1;
   return REG_OK;
 }
 
@@ -1294,7 +1382,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
       (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
       o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0 ||
-      o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1)
+      o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1 ||
+      o.step_tile < -1 || o.step_tile > kStepTiles)
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1315,6 +1404,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
     alloc_level(c, c->fine, grid.n1, grid.n2, nt);
     if (c->two_level)
       alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, o.coarse_nt > 0 ? o.coarse_nt : nt);
+    choose_step_tiles(c, c->fine);
+    if (c->two_level) choose_step_tiles(c, c->coarse);
     check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
     check(c, cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "side stream");
     check(c, cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "event");
@@ -1623,6 +1714,15 @@ reg_status reg_profile_read(reg_ctx* c, int level, int kclass, double* ms, long 
 }
 
 long long reg_launch_count(void) { return g_launch_count.load(); }
+
+reg_status reg_step_tiles(const reg_ctx* c, int* tiles) {
+  if (!c || !tiles) return REG_EINVAL;
+  tiles[0] = c->fine.tile_adj;
+  tiles[1] = c->fine.tile_inc;
+  tiles[2] = c->two_level ? c->coarse.tile_adj : 0;
+  tiles[3] = c->two_level ? c->coarse.tile_inc : 0;
+  return REG_OK;
+}
 
 reg_status reg_dot(reg_ctx* c, const float* a, const float* b, long long n, double* out) {
   if (!c || !out || n < 0 || (n > 0 && (!a || !b))) return REG_EINVAL;

@@ -91,15 +91,17 @@ void launch_departure(int n1, int n2, float ht, const float* v, const float* cv,
            dim3(kPT), 0, st, n1, n2, ilog2i(n1), s1, s2, v, cv, dX, dY, lagrange);
 }
 
-// The step kernels below handle kSP horizontally adjacent points
-// per thread (row lengths are multiples of 32, so the kSP points of a thread
-// share a row): their streamed fields move as kSP-float vectors and the kSP
-// independent 4x4 stencils keep more loads in flight per thread.
-#ifndef REGNK_STEP_POINTS
-#define REGNK_STEP_POINTS 2
-#endif
-constexpr int kSP = REGNK_STEP_POINTS;
-static_assert(kSP == 1 || kSP == 2 || kSP == 4, "points per thread");
+// The step kernels below (k_adjoint_step, k_incstate_step) handle SP
+// horizontally adjacent points per thread in blocks of T threads (row lengths
+// are multiples of 32, so the SP points of a thread share a row): their
+// streamed fields move as SP-float vectors and the SP independent 4x4
+// stencils keep more loads in flight per thread. (SP, T) is the tile shape,
+// chosen per grid level at run time among kStepTiles shapes (index k = 1..9:
+// T = 128 << ((k - 1) / 3), SP = 1 << ((k - 1) % 3)). Every point's
+// arithmetic is the same in every shape.
+#define REGNK_STEP_TILES(X) \
+  X(1, 1, 128) X(2, 2, 128) X(3, 4, 128) X(4, 1, 256) X(5, 2, 256) X(6, 4, 256) \
+  X(7, 1, 512) X(8, 2, 512) X(9, 4, 512)
 
 template <int K>
 __device__ __forceinline__ void ldk(const float* p, float (&a)[K]) {
@@ -139,7 +141,8 @@ __device__ __forceinline__ void stk(float* p, const float (&a)[K]) {
   }
 }
 
-static unsigned step_blocks(long long N) { return (unsigned)((N / kSP + kPT - 1) / kPT); }
+template <int SP, int T>
+static unsigned step_blocks(long long N) { return (unsigned)((N / SP + T - 1) / T); }
 
 // out_f = I[coef_f](x + disp), f = 0..F-1 (fields fstride apart), one stencil
 // per point, one point per thread; F = 1 or 2 is a compile-time constant so
@@ -216,40 +219,40 @@ void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const fl
 //   lb = lam_{j+1}(Y_D), lam* = lb + h_t lb div v(Y_D),
 //   lam_j = lb + h_t/2 (lb div v(Y_D) + lam* div v(x)),
 // fused with the time integral b += wb * lam_j * grad m_j.
-template <bool P2>
-__global__ void __launch_bounds__(kPT)
+template <bool P2, int SP, int T>
+__global__ void __launch_bounds__(T)
 k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ coef,
                const float* __restrict__ dY, const float* __restrict__ delta,
                const float* __restrict__ delta_bar, const float* __restrict__ gm,
                float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
   pdl_enter();
   const long long N = (long long)n1 * n2;
-  const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
+  const long long idx = SP * ((long long)blockIdx.x * T + threadIdx.x);
   if (idx >= N) return;
   int i, j;
   split_index<P2>(idx, n1, log1, i, j);
-  float y1[kSP], y2[kSP], l[kSP];
+  float y1[SP], y2[SP], l[SP];
   ldk(dY + idx, y1);
   ldk(dY + N + idx, y2);
 #pragma unroll
-  for (int p = 0; p < kSP; ++p)
+  for (int p = 0; p < SP; ++p)
     l[p] = apply_stencil(make_stencil<P2>(i + p, j, y1[p], y2[p], n1, n2, log1, lagrange), coef);
-  float db[kSP], d[kSP];
+  float db[SP], d[SP];
   ldk(delta_bar + idx, db);
   ldk(delta + idx, d);
 #pragma unroll
-  for (int p = 0; p < kSP; ++p) {
+  for (int p = 0; p < SP; ++p) {
     const float lstar = fmaf(ht * l[p], db[p], l[p]);
     l[p] = l[p] + 0.5f * ht * (l[p] * db[p] + lstar * d[p]);
   }
   stk(lam_out + idx, l);
-  float g1[kSP], g2[kSP], b1[kSP], b2[kSP];
+  float g1[SP], g2[SP], b1[SP], b2[SP];
   ldk(gm + idx, g1);
   ldk(gm + N + idx, g2);
   ldk_rw(b + idx, b1);
   ldk_rw(b + N + idx, b2);
 #pragma unroll
-  for (int p = 0; p < kSP; ++p) {
+  for (int p = 0; p < SP; ++p) {
     b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
     b2[p] = fmaf(wb * l[p], g2[p], b2[p]);
   }
@@ -257,13 +260,27 @@ k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __rest
   stk(b + N + idx, b2);
 }
 
-void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
+template <int SP, int T>
+static void adjoint_step_t(int n1, int n2, float ht, float wb, const float* coef, const float* dY,
+                           const float* delta, const float* delta_bar, const float* gm,
+                           float* lam_out, float* b, int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  launch_k(pick(n1, n2, k_adjoint_step<true, SP, T>, k_adjoint_step<false, SP, T>),
+           dim3(step_blocks<SP, T>(N)), dim3(T), 0, st, n1, n2, ilog2i(n1), ht, wb, coef, dY, delta,
+           delta_bar, gm, lam_out, b, lagrange);
+}
+
+void launch_adjoint_step(int tile, int n1, int n2, float ht, float wb, const float* coef,
                          const float* dY, const float* delta, const float* delta_bar,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st) {
-  const long long N = (long long)n1 * n2;
-  launch_k(pick(n1, n2, k_adjoint_step<true>, k_adjoint_step<false>), dim3(step_blocks(N)), dim3(kPT),
-           0, st, n1, n2, ilog2i(n1), ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange);
+  switch (tile) {
+#define REGNK_ADJ_CASE(K, SP, T) \
+  case K: adjoint_step_t<SP, T>(n1, n2, ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange, st); break;
+    REGNK_STEP_TILES(REGNK_ADJ_CASE)
+#undef REGNK_ADJ_CASE
+    default: adjoint_step_t<2, 256>(n1, n2, ht, wb, coef, dY, delta, delta_bar, gm, lam_out, b, lagrange, st);
+  }
 }
 
 // One forward step of the incremental state (Gauss-Newton, §3.3.2):
@@ -274,8 +291,8 @@ void launch_adjoint_step(int n1, int n2, float ht, float wb, const float* coef,
 // is gathered here and written to vtD instead of being read from it.
 // gm_nt, b: non-NULL for the last step j = nt, which writes
 // lambda~_nt = -m~_nt and b = h_t/2 lambda~_nt grad m_nt (k_adjoint_init).
-template <bool P2>
-__global__ void __launch_bounds__(kPT)
+template <bool P2, int SP, int T>
+__global__ void __launch_bounds__(T)
 k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ coef,
                 const float* __restrict__ dX, const float* __restrict__ vt,
                 float* __restrict__ vtD, const float* __restrict__ G,
@@ -284,19 +301,19 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
                 float* __restrict__ b) {
   pdl_enter();
   const long long N = (long long)n1 * n2;
-  const long long idx = kSP * ((long long)blockIdx.x * kPT + threadIdx.x);
+  const long long idx = SP * ((long long)blockIdx.x * T + threadIdx.x);
   if (idx >= N) return;
-  float m[kSP], w1[kSP], w2[kSP];
+  float m[SP], w1[SP], w2[SP];
 #pragma unroll
-  for (int p = 0; p < kSP; ++p) m[p] = 0.f;
+  for (int p = 0; p < SP; ++p) m[p] = 0.f;
   if (!first || cvt) {
     int i, j;
     split_index<P2>(idx, n1, log1, i, j);
-    float x1[kSP], x2[kSP];
+    float x1[SP], x2[SP];
     ldk(dX + idx, x1);
     ldk(dX + N + idx, x2);
 #pragma unroll
-    for (int p = 0; p < kSP; ++p) {
+    for (int p = 0; p < SP; ++p) {
       const Stencil S = make_stencil<P2>(i + p, j, x1[p], x2[p], n1, n2, log1, lagrange);
       if (!first) m[p] = apply_stencil(S, coef);
       if (cvt) {
@@ -312,7 +329,7 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
     ldk(vtD + idx, w1);
     ldk(vtD + N + idx, w2);
   }
-  float G1[kSP], G2[kSP], u1[kSP], u2[kSP], g1[kSP], g2[kSP];
+  float G1[SP], G2[SP], u1[SP], u2[SP], g1[SP], g2[SP];
   ldk(G + idx, G1);
   ldk(G + N + idx, G2);
   ldk(vt + idx, u1);
@@ -320,18 +337,18 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
   ldk(gm + idx, g1);
   ldk(gm + N + idx, g2);
 #pragma unroll
-  for (int p = 0; p < kSP; ++p)
+  for (int p = 0; p < SP; ++p)
     m[p] -= 0.5f * ht * (w1[p] * G1[p] + w2[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
   if (!b) {
     stk(out + idx, m);
     return;
   }
-  float gn1[kSP], gn2[kSP], lam[kSP], b1[kSP], b2[kSP];
+  float gn1[SP], gn2[SP], lam[SP], b1[SP], b2[SP];
   ldk(gm_nt + idx, gn1);
   ldk(gm_nt + N + idx, gn2);
   const float hh = 0.5f * ht;
 #pragma unroll
-  for (int p = 0; p < kSP; ++p) {
+  for (int p = 0; p < SP; ++p) {
     lam[p] = -m[p];
     b1[p] = hh * lam[p] * gn1[p];
     b2[p] = hh * lam[p] * gn2[p];
@@ -341,14 +358,33 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
   stk(b + N + idx, b2);
 }
 
-void launch_incstate_step(int n1, int n2, float ht, const float* coef, const float* dX,
+template <int SP, int T>
+static void incstate_step_t(int n1, int n2, float ht, const float* coef, const float* dX,
+                            const float* vt, float* vtD, const float* G, const float* gm,
+                            float* out, int first, int lagrange, cudaStream_t st,
+                            const float* cvt, const float* gm_nt, float* b) {
+  const long long N = (long long)n1 * n2;
+  launch_k(pick(n1, n2, k_incstate_step<true, SP, T>, k_incstate_step<false, SP, T>),
+           dim3(step_blocks<SP, T>(N)), dim3(T), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD,
+           G, gm, out, first, lagrange, cvt, gm_nt, b);
+}
+
+void launch_incstate_step(int tile, int n1, int n2, float ht, const float* coef, const float* dX,
                           const float* vt, float* vtD, const float* G, const float* gm,
                           float* out, int first, int lagrange, cudaStream_t st,
                           const float* cvt, const float* gm_nt, float* b) {
-  const long long N = (long long)n1 * n2;
-  launch_k(pick(n1, n2, k_incstate_step<true>, k_incstate_step<false>), dim3(step_blocks(N)),
-           dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, coef, dX, vt, vtD, G, gm, out, first, lagrange,
-           cvt, gm_nt, b);
+  switch (tile) {
+#define REGNK_INC_CASE(K, SP, T)                                                                 \
+  case K:                                                                                        \
+    incstate_step_t<SP, T>(n1, n2, ht, coef, dX, vt, vtD, G, gm, out, first, lagrange, st, cvt,  \
+                           gm_nt, b);                                                            \
+    break;
+    REGNK_STEP_TILES(REGNK_INC_CASE)
+#undef REGNK_INC_CASE
+    default:
+      incstate_step_t<2, 256>(n1, n2, ht, coef, dX, vt, vtD, G, gm, out, first, lagrange, st, cvt,
+                              gm_nt, b);
+  }
 }
 
 // ---------------------------------------------------------------------------

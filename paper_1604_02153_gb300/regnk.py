@@ -48,7 +48,7 @@ class reg_options(ctypes.Structure):
                 ("armijo_c1", ctypes.c_double), ("persistent_matvec", ctypes.c_int),
                 ("inject_barrier_timeout", ctypes.c_int), ("programmatic_launch", ctypes.c_int),
                 ("fused_transport", ctypes.c_int), ("coarse_nt", ctypes.c_int),
-                ("coarse_interp", ctypes.c_int)]
+                ("coarse_interp", ctypes.c_int), ("step_tile", ctypes.c_int)]
 
 
 class reg_info(ctypes.Structure):
@@ -92,6 +92,7 @@ _SIGNATURES = {
     "reg_profile_read": [_P, _I, _I, ctypes.POINTER(_D), ctypes.POINTER(ctypes.c_longlong),
                          ctypes.POINTER(_D)],
     "reg_launch_count": [],
+    "reg_step_tiles": [_P, ctypes.POINTER(_I)],
     "reg_interpolate_static": [_I, _I, _P, _P, _P, _P],
     "reg_batch_create": [ctypes.POINTER(reg_grid), _I, _I, ctypes.POINTER(_D),
                          ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
@@ -269,6 +270,19 @@ class Registration:
         d = info.as_dict()
         d["status_name"] = STATUS_NAMES.get(s, str(s))
         return d
+
+    def step_tiles(self):
+        """Tile shapes of the step kernels, {(level, kernel): (threads, points)}
+        for levels "fine" and "coarse" (when P_2L has one) and kernels
+        "adjoint", "incstate" (reg_step_tiles)."""
+        t = (ctypes.c_int * 4)()
+        self._call("reg_step_tiles", t)
+        out = {}
+        for i, (lvl, ker) in enumerate((("fine", "adjoint"), ("fine", "incstate"),
+                                        ("coarse", "adjoint"), ("coarse", "incstate"))):
+            if t[i] > 0:
+                out[(lvl, ker)] = (128 << ((t[i] - 1) // 3), 1 << ((t[i] - 1) % 3))
+        return out
 
     def profile_enable(self, enable=True):
         self._call("reg_profile_enable", 1 if enable else 0)

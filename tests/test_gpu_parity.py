@@ -479,6 +479,42 @@ def test_programmatic_launch_gives_identical_results(regnk, n1, n2):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("n1,n2,interp,fused", [(128, 128, 1, 1), (128, 128, 0, 0), (192, 96, 1, 1)])
+def test_step_tile_shapes_give_identical_results(regnk, n1, n2, interp, fused):
+    """The nine tile shapes of the unfused step kernels (threads per block x
+    points per thread) compute every point with the same arithmetic, so
+    gradient, Hessian matvec and a preconditioned KKT solve (P_2L's coarse
+    grid included) are bitwise equal in every shape; the autotuned context
+    reports valid shapes on every level and matches them too."""
+    m_R, m_T, v = (f32(a) for a in problem_data(n1, n2))
+    u = f32(inputs.random_velocity(n1, n2, seed=23, vmax=1.0).reshape(-1))
+    out = {}
+    for tile in list(range(1, 10)) + [-1]:
+        R = regnk.Registration(n1, n2, 4, 1e-2, interp=interp, fused_transport=fused,
+                               step_tile=tile, **pc_for(n1, n2))
+        tiles = R.step_tiles()
+        assert {k[0] for k in tiles} == ({"fine", "coarse"} if R.options.precond == 1 else {"fine"})
+        for thr, pts in tiles.values():
+            assert thr in (128, 256, 512) and pts in (1, 2, 4)
+            if tile > 0:
+                assert (thr, pts) == (128 << ((tile - 1) // 3), 1 << ((tile - 1) % 3))
+        R.set_images(dev(m_R), dev(m_T))
+        g = torch.empty(2 * n1 * n2, device="cuda")
+        J = R.objective_gradient(dev(v), g)
+        H = torch.empty_like(g)
+        R.hessian_matvec(dev(v), dev(u), H)
+        x = torch.empty_like(g)
+        R.kkt_solve(dev(v), g, 1e-6, 10, x)
+        torch.cuda.synchronize()
+        out[tile] = (J, g.cpu(), H.cpu(), x.cpu())
+        R.close()
+    ref = out[5]
+    for tile, r in out.items():
+        assert r[0] == ref[0], tile
+        for a, b in zip(r[1:], ref[1:]):
+            assert torch.equal(a, b), tile
+
+
 @pytest.mark.parametrize("n1,n2,vmax", [(128, 128, 0.5), (128, 128, 2.0), (128, 128, 4.0),
                                         (192, 96, 1.0), (256, 128, 2.0)])
 def test_fused_prefilter_step_matches_two_kernel_path(regnk, n1, n2, vmax):

@@ -49,7 +49,7 @@ def test_default_options(lib):
     assert abs(o.gabs - 1e-5) < 1e-20 and o.lanczos_steps == 30
     assert o.max_backtracks == 10 and abs(o.armijo_c1 - 1e-4) < 1e-20
     assert o.persistent_matvec == 0 and o.programmatic_launch == 1 and o.fused_transport == 1
-    assert o.coarse_nt == 0 and o.coarse_interp == -1
+    assert o.coarse_nt == 0 and o.coarse_interp == -1 and o.step_tile == -1
 
 
 def _create(lib, n1, n2, nt, beta, **kw):
@@ -70,6 +70,8 @@ def _create(lib, n1, n2, nt, beta, **kw):
     (32, 32, 4, 1e-2, {"precond": 1}),  # two-level needs a 32^2 coarse grid at least
     (64, 64, 4, 1e-2, {"coarse_nt": -1}),
     (64, 64, 4, 1e-2, {"coarse_interp": 2}),
+    (64, 64, 4, 1e-2, {"step_tile": 10}),
+    (64, 64, 4, 1e-2, {"step_tile": -2}),
 ])
 def test_invalid_arguments_rejected_on_host(lib, n1, n2, nt, beta, kw):
     s, h = _create(lib, n1, n2, nt, beta, **kw)
@@ -81,6 +83,7 @@ def test_null_handles(lib):
     assert lib.reg_set_images(None, None, None) == regnk.REG_EINVAL
     assert lib.reg_destroy(None) == regnk.REG_OK
     assert lib.reg_last_error(None) == b"null context"
+    assert lib.reg_step_tiles(None, (ctypes.c_int * 4)()) == regnk.REG_EINVAL
 
 
 def test_no_cpu_fallback(lib):
