@@ -81,11 +81,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--coarse-interp", choices=["lagrange", "spline"], default="lagrange",
-                    help="interpolation model of the P_2L coarse problem (default cubic Lagrange)")
-    ap.add_argument("--coarse-nt", type=int, default=NT // 2,
+    ap.add_argument("--coarse-interp", choices=["lagrange", "spline"], default=None,
+                    help="interpolation model of the P_2L coarse problem (default: cubic "
+                         "Lagrange for phantom1024, the problems' spline for batch64)")
+    ap.add_argument("--coarse-nt", type=int, default=-1,
                     help="time steps of the P_2L coarse problem (0: the problem's nt; default "
-                         "nt/2, the fine grid's displacement per step in coarse cells)")
+                         "-1: nt/2, the fine grid's displacement per step in coarse cells, for "
+                         "phantom1024, and the problems' nt for batch64)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
@@ -95,7 +97,15 @@ def parse():
     ap.add_argument("--workload", choices=["phantom1024", "batch64"], default="phantom1024",
                     help="phantom1024: the 1024^2 continuation solve (default); batch64: "
                          "64 independent problems of uneven size")
-    return ap.parse_args()
+    args = ap.parse_args()
+    # batch64: the cheaper coarse problem raises matvecs per solve as much as
+    # it lowers their cost there, so the batch keeps the problems' own model
+    batch = args.workload == "batch64"
+    if args.coarse_nt < 0:
+        args.coarse_nt = 0 if batch else NT // 2
+    if args.coarse_interp is None:
+        args.coarse_interp = "spline" if batch else "lagrange"
+    return args
 
 
 def dist_env():
@@ -278,8 +288,9 @@ BATCH_BETA = 1e-2
 def run_batch(args):
     """64 independent problems, grids drawn (seed 200) from BATCH_SIZES^2,
     each the analytic template/velocity pair with m_R = m_T transported by
-    v* (nt = 4, computed on the GPU), H1, beta = 1e-2, P_2L-CHEB(10), solved
-    to ||g||rel 1e-2 from v = 0: concurrently (reg_batch) and one by one."""
+    v* (nt = 4, computed on the GPU), H1, beta = 1e-2, P_2L-CHEB(10) (coarse
+    problem as --coarse-nt / --coarse-interp), solved to ||g||rel 1e-2 from
+    v = 0: concurrently (reg_batch) and one by one."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -302,7 +313,9 @@ def run_batch(args):
         mR.append(cache[n][0])
         mT.append(cache[n][1])
     grids = [(n, n) for n in sizes]
-    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B)
+    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
+                        coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
+                                       "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp])
     batch.set_images(mR, mT)
     vs = [torch.zeros(2 * n * n, device=dev) for n in sizes]
     for _ in range(max(1, args.warmup)):
@@ -338,7 +351,8 @@ def run_batch(args):
             "data": "synthetic",
             "config": {"workload": f"{BATCH_B} problems, grids from {list(BATCH_SIZES)}^2 "
                                    f"(seed 200), analytic pair, nt={BATCH_NT}, H1, "
-                                   f"beta={BATCH_BETA}, P_2L CHEB(10), ||g||rel 1e-2",
+                                   f"beta={BATCH_BETA}, P_2L CHEB(10) coarse nt="
+                                   f"{args.coarse_nt or BATCH_NT} {args.coarse_interp}, ||g||rel 1e-2",
                        "sizes": sizes},
             "one_by_one": {"value": mv_s / args.steps / t_serial, "seconds_per_batch": t_serial,
                            "mean_time_to_solution_s": float(np.mean(per_problem_serial))},

@@ -105,6 +105,7 @@ struct reg_ctx {
   double emin = 0, emax = 0, eig_beta = 0;
   bool have_gref = false;
   double gref_inf = 0, gref_2 = 0;
+  double J_zero = 0;               // J(0), computed with the reference gradient
   double eta = 0.5;
   int coarse_matvecs = 0;
   std::string err;
@@ -1300,7 +1301,7 @@ void ensure_gref(reg_ctx* c) {
   Level& F = c->fine;
   const long long n = 2 * F.g.N;
   launch_fill(c->vtrial, n, 0.f, c->st);
-  objective_gradient(c, c->vtrial, c->gcur);
+  c->J_zero = objective_gradient(c, c->vtrial, c->gcur);
   c->gref_inf = max_abs_sync(c, c->gcur, n, S_GINF);
   c->gref_2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n, S_G2));
   c->have_gref = true;
@@ -1773,11 +1774,11 @@ reg_status reg_warm_start(reg_ctx* c, reg_unet* net, float* v, int* accepted) {
       src = dst;
       m *= 2;
     }
-    // accepted only if it lowers the objective below J(0)
+    // accepted only if it lowers the objective below J(0); J(0) comes with
+    // the gradient at v = 0 that the solve's relative tolerance needs anyway
+    ensure_gref(c);
     const double J1 = objective_gradient(c, v, nullptr);
-    launch_fill(c->vtrial, 2 * N, 0.f, c->st);
-    const double J0 = objective_gradient(c, c->vtrial, nullptr);
-    const int ok = (J1 < J0) ? 1 : 0;
+    const int ok = (J1 < c->J_zero) ? 1 : 0;
     if (!ok) launch_fill(v, 2 * N, 0.f, c->st);
     if (accepted) *accepted = ok;
     check(c, cudaStreamSynchronize(c->st), "warm start");
