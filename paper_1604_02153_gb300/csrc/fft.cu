@@ -40,12 +40,12 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
 // Line lengths N = 2^L * 3^T (T = 0 or 1). Lines per block and threads per
 // block of the FFT kernels: P lines of N complex values, P a power of two
 // with P N <= 2048 (at most 16 KB of shared memory per block) and P = 1
-// from N = 1024 on, so that a 512^2 grid still gives a few hundred blocks per
-// pass and 1024^2 gives over 500 (fewer, larger blocks measured slower).
+// from N = 512 on, so that a 512^2 grid gives 256 blocks per field and pass
+// and 1024^2 over 500 (fewer, larger blocks measured slower at both sizes).
 template <int L, int T>
 struct FftCfg {
   static constexpr int N = (1 << L) * (T ? 3 : 1);
-  static constexpr int P = N >= 1024 ? 1 : (N >= 512 ? 2 : (N >= 256 ? 4 : (N >= 128 ? 8 : 16)));
+  static constexpr int P = N >= 512 ? 1 : (N >= 256 ? 4 : (N >= 128 ? 8 : 16));
   static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
 };
 

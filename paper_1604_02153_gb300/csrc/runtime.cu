@@ -701,10 +701,11 @@ double* slot(reg_ctx* c, int s) { return c->dsc + s; }
 void read_slots(reg_ctx* c, int first, int count) {
   check(c, cudaMemcpyAsync(c->hsc + first, c->dsc + first, count * sizeof(double),
                            cudaMemcpyDeviceToHost, c->st), "scalar read");
-  check(c, cudaMemcpyAsync(c->hbarerr, c->barerr, sizeof(int), cudaMemcpyDeviceToHost, c->st),
-        "barrier flag read");
+  if (c->persistent)   // only the persistent matvec can raise the barrier flag
+    check(c, cudaMemcpyAsync(c->hbarerr, c->barerr, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+          "barrier flag read");
   check(c, cudaStreamSynchronize(c->st), "stream synchronize");
-  if (*c->hbarerr) {
+  if (c->persistent && *c->hbarerr) {
     // a persistent kernel gave up waiting at a grid barrier: reset its state
     cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->st);
     cudaMemsetAsync(c->barerr, 0, sizeof(int), c->st);

@@ -231,26 +231,26 @@ k_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __rest
   if (idx >= N) return;
   int i, j;
   split_index<P2>(idx, n1, log1, i, j);
-  float y1[SP], y2[SP], l[SP];
+  // every streamed operand is requested together with the displacement, so
+  // that their latency overlaps the dependent gather
+  float y1[SP], y2[SP], l[SP], db[SP], d[SP], g1[SP], g2[SP], b1[SP], b2[SP];
   ldk(dY + idx, y1);
   ldk(dY + N + idx, y2);
+  ldk(delta_bar + idx, db);
+  ldk(delta + idx, d);
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+  ldk_rw(b + idx, b1);
+  ldk_rw(b + N + idx, b2);
 #pragma unroll
   for (int p = 0; p < SP; ++p)
     l[p] = apply_stencil(make_stencil<P2>(i + p, j, y1[p], y2[p], n1, n2, log1, lagrange), coef);
-  float db[SP], d[SP];
-  ldk(delta_bar + idx, db);
-  ldk(delta + idx, d);
 #pragma unroll
   for (int p = 0; p < SP; ++p) {
     const float lstar = fmaf(ht * l[p], db[p], l[p]);
     l[p] = l[p] + 0.5f * ht * (l[p] * db[p] + lstar * d[p]);
   }
   stk(lam_out + idx, l);
-  float g1[SP], g2[SP], b1[SP], b2[SP];
-  ldk(gm + idx, g1);
-  ldk(gm + N + idx, g2);
-  ldk_rw(b + idx, b1);
-  ldk_rw(b + N + idx, b2);
 #pragma unroll
   for (int p = 0; p < SP; ++p) {
     b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
@@ -306,6 +306,23 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
   float m[SP], w1[SP], w2[SP];
 #pragma unroll
   for (int p = 0; p < SP; ++p) m[p] = 0.f;
+  // the streamed operands are requested before the dependent gather
+  float G1[SP], G2[SP], u1[SP], u2[SP], g1[SP], g2[SP];
+  ldk(G + idx, G1);
+  ldk(G + N + idx, G2);
+  ldk(vt + idx, u1);
+  ldk(vt + N + idx, u2);
+  ldk(gm + idx, g1);
+  ldk(gm + N + idx, g2);
+  if (!cvt) {
+    ldk(vtD + idx, w1);
+    ldk(vtD + N + idx, w2);
+  }
+  float gn1[SP], gn2[SP];
+  if (b) {
+    ldk(gm_nt + idx, gn1);
+    ldk(gm_nt + N + idx, gn2);
+  }
   if (!first || cvt) {
     int i, j;
     split_index<P2>(idx, n1, log1, i, j);
@@ -325,17 +342,7 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
   if (cvt) {
     stk(vtD + idx, w1);
     stk(vtD + N + idx, w2);
-  } else {
-    ldk(vtD + idx, w1);
-    ldk(vtD + N + idx, w2);
   }
-  float G1[SP], G2[SP], u1[SP], u2[SP], g1[SP], g2[SP];
-  ldk(G + idx, G1);
-  ldk(G + N + idx, G2);
-  ldk(vt + idx, u1);
-  ldk(vt + N + idx, u2);
-  ldk(gm + idx, g1);
-  ldk(gm + N + idx, g2);
 #pragma unroll
   for (int p = 0; p < SP; ++p)
     m[p] -= 0.5f * ht * (w1[p] * G1[p] + w2[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
@@ -343,9 +350,7 @@ k_incstate_step(int n1, int n2, int log1, float ht, const float* __restrict__ co
     stk(out + idx, m);
     return;
   }
-  float gn1[SP], gn2[SP], lam[SP], b1[SP], b2[SP];
-  ldk(gm_nt + idx, gn1);
-  ldk(gm_nt + N + idx, gn2);
+  float lam[SP], b1[SP], b2[SP];
   const float hh = 0.5f * ht;
 #pragma unroll
   for (int p = 0; p < SP; ++p) {
