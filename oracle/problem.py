@@ -2,20 +2,22 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Problem (§2, eq. varopt, compressible case, w and its constraint omitted):
+Problem (§2, eq. varopt, w and its constraint omitted):
     minimise J[v] = 1/2 ||m_1 - m_R||^2 + beta/2 <v, A v>
-    subject to d_t m + grad m . v = 0, m(0) = m_T, periodic.
+    subject to d_t m + grad m . v = 0, m(0) = m_T, periodic;
+compressible (K = I, the default) or incompressible (div v = 0, w = 0:
+K = the Leray projection of §3.1, spectral.leray).
 
 Discrete inner product (§3.2, midpoint rule): <a, b>_h = h_1 h_2 sum a b.
 
 Optimise-then-discretise (§3.1):
-* reduced gradient, eq. control-elim with K = I:
-      g = beta A v + int_0^1 lambda grad m dt,
+* reduced gradient, eq. control-elim:
+      g = beta A v + K[int_0^1 lambda grad m dt],
   lambda from the adjoint eq. adj-pde-elim with final value
   lambda_1 = -(m_1 - m_R) (eq. adj-pde-fc-elim);
 * Gauss-Newton Hessian matvec, eq. hessian-matvec with every term in lambda
   dropped (§3.4.1 footnote, §3.5 "Hessian"):
-      H v~ = beta A v~ + int_0^1 lambda~ grad m dt,
+      H v~ = beta A v~ + K[int_0^1 lambda~ grad m dt],
   m~ from eq. inc-state-pde-elim (m~(0) = 0), lambda~ from
   eq. inc-adj-pde-elim without the div(lambda v~) term, lambda~_1 = -m~_1.
 Time integrals use the trapezoidal rule on the nt + 1 time levels (the paper
@@ -28,7 +30,9 @@ columns): ``counts[row] = [FFTs, IPs]`` for rows "SE", "AE", "incSE",
 is stored across solves, so grad m_j is recomputed by FFT (1 forward + d
 inverse FFTs) wherever it is used; grad m_0 = grad m_T is computed once per
 image pair. An FFT is one 2D transform of one scalar field; an IP is one
-scalar interpolation including its spline prefilter.
+scalar interpolation including its spline prefilter. With K the Leray
+projection, each application of K adds 2d FFTs (d forward, d inverse: one
+Fourier multiplier on a d-vector field), beyond the table.
 """
 
 import numpy as np
@@ -41,7 +45,7 @@ D = 2  # spatial dimension
 class Problem:
     """One registration problem on an (n2, n1) grid with nt time steps."""
 
-    def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline"):
+    def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline", incompressible=False):
         self.m_R = np.asarray(m_R, dtype=np.float64)
         self.m_T = np.asarray(m_T, dtype=np.float64)
         self.n2, self.n1 = self.m_R.shape
@@ -50,6 +54,7 @@ class Problem:
         self.beta = float(beta)
         self.reg_norm = reg_norm
         self.kind = kind
+        self.incompressible = bool(incompressible)
         self.h1 = 2.0 * np.pi / self.n1
         self.h2 = 2.0 * np.pi / self.n2
         self.w = transport.trapezoid_weights(self.nt)
@@ -58,6 +63,14 @@ class Problem:
         self.v = None
 
     # -- bookkeeping --------------------------------------------------------
+    def K(self, b, row):
+        """The operator K of eq. control-elim: identity (compressible) or the
+        Leray projection (incompressible, w = 0)."""
+        if not self.incompressible:
+            return b
+        self._count(row, ffts=2 * D)
+        return spectral.leray(b)
+
     def _count(self, row, ffts=0, ips=0):
         c = self.counts.setdefault(row, [0, 0])
         c[0] += ffts
@@ -123,7 +136,7 @@ class Problem:
         return lam
 
     def gradient(self, v=None):
-        """Reduced gradient g (eq. control-elim, K = I), row "g".
+        """Reduced gradient g (eq. control-elim), row "g".
 
         Runs the state solve first if v is given (counted under "J", as the
         paper charges the forward solve to the objective).
@@ -136,7 +149,7 @@ class Problem:
             gm = self._grad_m(j, "g")
             b += self.ht * self.w[j] * lam[j] * gm
         self._count("g", ffts=2 * D)
-        return spectral.apply_reg(self.v, self.beta, self.reg_norm) + b
+        return spectral.apply_reg(self.v, self.beta, self.reg_norm) + self.K(b, "g")
 
     def objective_gradient(self, v):
         J = self.objective(v)
@@ -182,7 +195,7 @@ class Problem:
             self._count(row, ips=1)
             bt = bt + self.ht * self.w[j] * lt * self._grad_m(j, row)
         self._count(row, ffts=2 * D)
-        return spectral.apply_reg(vt, self.beta, self.reg_norm) + bt
+        return spectral.apply_reg(vt, self.beta, self.reg_norm) + self.K(bt, row)
 
     def data_matvec(self, vt):
         """Data term Q v~ = H v~ - beta A v~ (eq. reduced-space-kkt-system)."""

@@ -18,6 +18,10 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
   a safety factor of 1.05 (the paper gives none); e_min from
   min(1 + 1/(beta gamma_k)) over the coarse grid; a change of beta rescales
   (e - 1) by beta_old / beta_new.
+* Incompressible problems (K the Leray projection): the initial guess and
+  the Lanczos start vector are projected onto divergence-free fields, so
+  that every iterate stays in the space the constraint div v = 0 defines
+  (K commutes with A and with the filters, restriction and prolongation).
 * Outer loop (§3.4.1, §3.5): stop when ||g_k||_inf / ||g_ref||_inf <= gtol or
   ||g_k||_inf <= gabs; g_ref = g(v = 0) (the paper's g_0 for a zero initial
   guess; fixed at v = 0 so that warm starts and beta stages share one
@@ -62,7 +66,8 @@ class Solver:
             # little accuracy)
             # coarse_kind: its interpolation model (default: the problem's)
             self.coarse = Problem(spectral.restrict(p.m_R), spectral.restrict(p.m_T),
-                                  coarse_nt or p.nt, p.beta, p.reg_norm, coarse_kind or p.kind)
+                                  coarse_nt or p.nt, p.beta, p.reg_norm, coarse_kind or p.kind,
+                                  p.incompressible)
 
     # -- preconditioners -----------------------------------------------------
     def precond_reg(self, r):
@@ -85,6 +90,8 @@ class Solver:
             v0 = np.random.default_rng(1234).uniform(-1.0, 1.0, (2, c.n2, c.n1))
         else:
             v0 = np.asarray(self.lanczos_v0, dtype=np.float64).reshape(2, c.n2, c.n1)
+        if c.incompressible:
+            v0 = spectral.leray(v0)
         _, rmax, _ = krylov.lanczos_extremal(self.coarse_split_op, v0, self.lanczos_steps)
         gam = spectral.reg_symbol(c.n1, c.n2, c.reg_norm).astype(np.float64)
         gam[0, 0] = 1.0
@@ -148,6 +155,8 @@ class Solver:
         if self.precond == "2L" and self.eig is None:
             self.estimate_eigenvalues()
         v = np.array(v0, dtype=np.float64, copy=True)
+        if p.incompressible:
+            v = spectral.leray(v)
         J, g = p.objective_gradient(v)
         info = {"J0": J, "newton_iters": 0, "pcg_iters": 0, "matvecs": 0,
                 "line_search_fail": False, "log": []}

@@ -64,6 +64,24 @@ def div(v):
     return ifft2_real(1j * K1 * fft2(v[0]) + 1j * K2 * fft2(v[1]))
 
 
+def leray(b):
+    """Leray projection K[b] = -grad Lap^-1 div b + b (§3.1, the K of
+    eq. control-elim when the divergence w is set to zero): the part of a
+    periodic vector field that the spectral divergence maps to zero.
+
+    Written out as its definition: phi solves Lap phi = div b with the
+    Laplacian taken as div(grad .) of the two operators above (so that div K b
+    is exactly zero for the discrete div; the modes where div(grad .) vanishes,
+    k = 0 and the Nyquist lines, keep phi = 0), then K b = b - grad phi.
+    """
+    n2, n1 = b.shape[1:]
+    K1, K2 = _k_grids(n1, n2, zero_nyquist=True)
+    lap = -(K1 * K1 + K2 * K2)                      # symbol of div(grad .)
+    dh = fft2(div(b))
+    phih = np.where(lap != 0.0, dh / np.where(lap != 0.0, lap, 1.0), 0.0)
+    return b - grad(ifft2_real(phih))
+
+
 def reg_symbol(n1, n2, reg_norm):
     """Spectral weights gamma(k) = |k|^(2p) of the regularisation operator A.
 

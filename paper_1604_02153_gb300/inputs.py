@@ -45,6 +45,17 @@ def sinusoid_pair(n1, n2=None):
     return m_T, v
 
 
+def vortex_pair(n1, n2=None):
+    """m_T as in sinusoid_pair and the divergence-free v* = (-0.5 sin x1 cos x2,
+    0.5 cos x1 sin x2) (stream function 0.5 sin x1 sin x2), for the
+    incompressible problem."""
+    n2 = n1 if n2 is None else n2
+    X1, X2 = grid_coordinates(n1, n2)
+    m_T = 0.5 * (np.sin(X1) ** 2 + np.sin(X2) ** 2)
+    v = np.stack([-0.5 * np.sin(X1) * np.cos(X2), 0.5 * np.cos(X1) * np.sin(X2)])
+    return m_T, v
+
+
 def _half_plane_modes(kmax):
     modes = []
     for k2 in range(0, kmax + 1):

@@ -206,3 +206,34 @@ def test_gauss_newton_equals_gradient_derivative_at_zero_residual():
     eps = 1e-4
     fd = (P.gradient(v + eps * u) - P.gradient(v - eps * u)) / (2 * eps)
     assert np.linalg.norm(fd - Hu) / np.linalg.norm(Hu) < 2e-4
+
+
+def test_incompressible_gradient_and_hessian_are_leray_projections():
+    """Incompressible problem (w = 0, K the Leray projection of §3.1): for a
+    divergence-free v and u, g_inc = K g and H_inc u = K H u (K commutes
+    with A and fixes v and u); g_inc is divergence free and orthogonal to
+    gradient fields, and its slope along a divergence-free direction
+    matches central finite differences of J."""
+    n, nt = 64, 8
+    m_T = inputs.random_field(n, seed=1, kmax=4)
+    m_R = inputs.random_field(n, seed=2, kmax=4)
+    v = spectral.leray(inputs.random_velocity(n, seed=3, vmax=0.05))
+    u = spectral.leray(inputs.random_velocity(n, seed=9, vmax=1.0))
+    Pc = Problem(m_R, m_T, nt, 1e-2)
+    Pi = Problem(m_R, m_T, nt, 1e-2, incompressible=True)
+    Jc, gc = Pc.objective_gradient(v)
+    Ji, gi = Pi.objective_gradient(v)
+    assert Ji == Jc
+    assert np.max(np.abs(gi - spectral.leray(gc))) < 1e-12 * np.max(np.abs(gc))
+    assert np.max(np.abs(spectral.div(gi))) < 1e-12 * n * np.max(np.abs(gi))
+    w = spectral.grad(inputs.random_field(n, seed=5, kmax=4))
+    assert abs(Pi.inner(gi, w)) < 1e-10 * abs(Pc.inner(gc, w))
+    Hc = Pc.hessian_matvec(u)
+    Hi = Pi.hessian_matvec(u)
+    assert np.max(np.abs(Hi - spectral.leray(Hc))) < 1e-12 * np.max(np.abs(Hc))
+    assert np.max(np.abs(Hi - Hc)) > 1e-3 * np.max(np.abs(Hc))   # K is not the identity here
+    dv = spectral.leray(inputs.random_velocity(n, seed=4, vmax=1.0))
+    d = Pi.inner(gi, dv)
+    eps = 1e-4
+    fd = (Pi.objective(v + eps * dv) - Pi.objective(v - eps * dv)) / (2 * eps)
+    assert abs(fd - d) < 1e-4 * abs(d)

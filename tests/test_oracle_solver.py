@@ -66,3 +66,27 @@ def test_beta_rescales_chebyshev_bounds():
     # and the rescaled e_max is close to a fresh estimate (eigenvalue
     # estimates scale with 1/beta, §4.2.1)
     assert abs(e2["emax"] - S.eig["emax"]) / e2["emax"] < 0.05
+
+
+def test_incompressible_solve_stays_divergence_free():
+    """K = Leray (w = 0): from a velocity that is not divergence free, the
+    solve projects it and every iterate stays divergence free; P_REG and
+    P_2L reach the same minimiser, J decreases monotonically and the loop
+    stops at the requested gradient reduction."""
+    from oracle import spectral
+    n, nt = 32, 4
+    m_T, vstar = inputs.vortex_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, 1e-2).state_solve(vstar)
+    v0 = inputs.random_velocity(n, seed=6, vmax=0.05)
+    out = {}
+    for pc in ("REG", "2L"):
+        S = Solver(Problem(m_R, m_T, nt, 1e-2, incompressible=True), precond=pc)
+        v, info = S.solve(v0, 1e-3)
+        Js = [r["J"] for r in info["log"]]
+        assert all(Js[i + 1] < Js[i] for i in range(len(Js) - 1)), pc
+        assert info["gnorm_rel"] <= 1e-3 and not info["line_search_fail"], pc
+        assert np.max(np.abs(spectral.div(v))) < 1e-10 * np.max(np.abs(v)), pc
+        out[pc] = v
+    assert np.linalg.norm(out["2L"] - out["REG"]) / np.linalg.norm(out["REG"]) < 2e-2
+    # the recovered field points the way of the divergence-free v* that made m_R
+    assert np.sum(out["REG"] * vstar) > 0.5 * np.linalg.norm(out["REG"]) * np.linalg.norm(vstar)

@@ -144,3 +144,58 @@ def test_spline_symbol_matches_bspline_samples():
         for b in (-1, 0, 1):
             u += w[a] * w[b] * np.roll(np.roll(c, -a, axis=1), -b, axis=0)
     assert np.max(np.abs(spectral.spline_prefilter(u) - c)) < 1e-12
+
+
+def test_leray_keeps_solenoidal_part_of_hodge_decomposition():
+    """b = grad phi + curl psi + const (curl psi = (-d2 psi, d1 psi)): the
+    Leray projection (§3.1, K[b] = -grad Lap^-1 div b + b) removes exactly
+    the gradient part."""
+    n1, n2 = 32, 24
+    modes = [(1, 0), (0, 1), (3, -2), (-5, 7), (7, 3), (2, 9)]
+    phi, p1, p2, _ = trig_poly(n1, n2, modes, seed=41)
+    psi, s1, s2, _ = trig_poly(n1, n2, modes, seed=42)
+    const = np.array([0.3, -0.7])[:, None, None]
+    sol = np.stack([-s2, s1]) + const
+    b = np.stack([p1, p2]) + sol
+    assert np.max(np.abs(spectral.leray(b) - sol)) < 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(spectral.leray(np.stack([p1, p2])))) < 1e-12 * np.max(np.abs(p1))
+    assert np.max(np.abs(spectral.leray(sol) - sol)) < 1e-12
+
+
+@pytest.mark.parametrize("n1,n2", [(16, 16), (16, 12), (12, 20)])
+def test_leray_is_an_orthogonal_projector_onto_discretely_solenoidal_fields(n1, n2):
+    rng = np.random.default_rng(n1 * 100 + n2)
+    a = rng.standard_normal((2, n2, n1))     # all modes, Nyquist lines included
+    b = rng.standard_normal((2, n2, n1))
+    Ka, Kb = spectral.leray(a), spectral.leray(b)
+    scale = np.max(np.abs(b))
+    assert np.max(np.abs(spectral.div(Kb))) < 1e-12 * n1 * scale
+    assert np.max(np.abs(spectral.leray(Kb) - Kb)) < 1e-12 * scale
+    assert abs(np.sum(Ka * b) - np.sum(a * Kb)) < 1e-11 * np.sum(np.abs(a * b))
+    assert abs(np.sum(Kb * (b - Kb))) < 1e-11 * np.sum(b * b)
+    # a field that is a gradient is removed entirely
+    g = spectral.grad(rng.standard_normal((n2, n1)))
+    assert np.max(np.abs(spectral.leray(g))) < 1e-11 * np.max(np.abs(g))
+
+
+def test_leray_matches_dense_projection_built_from_grad_and_div():
+    """Brute force on a 6 x 8 grid: the matrix of K equals
+    I - G (D G)^+ D with G, D the dense matrices of the (pinned) spectral
+    gradient and divergence; (D G)^+ is the pseudo-inverse, which leaves the
+    modes where div(grad .) vanishes untouched."""
+    n1, n2 = 8, 6
+    N = n1 * n2
+    G = np.zeros((2 * N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        G[:, j] = spectral.grad(e.reshape(n2, n1)).ravel()
+    D = np.zeros((N, 2 * N))
+    Kmat = np.zeros((2 * N, 2 * N))
+    for j in range(2 * N):
+        e = np.zeros(2 * N)
+        e[j] = 1.0
+        D[:, j] = spectral.div(e.reshape(2, n2, n1)).ravel()
+        Kmat[:, j] = spectral.leray(e.reshape(2, n2, n1)).ravel()
+    K_bf = np.eye(2 * N) - G @ np.linalg.pinv(D @ G, rcond=1e-10) @ D
+    assert np.max(np.abs(Kmat - K_bf)) < 1e-12
