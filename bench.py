@@ -88,6 +88,8 @@ def parse():
                     help="time steps of the P_2L coarse problem (0: the problem's nt; default "
                          "-1: nt/2, the fine grid's displacement per step in coarse cells, for "
                          "phantom1024, and the problems' nt for batch64)")
+    ap.add_argument("--incompressible", action="store_true",
+                    help="the incompressible problem (div v = 0, K the Leray projection)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
@@ -200,21 +202,21 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle timed on the host (cpu_baseline and --impl reference)
 
-def oracle_matvec_sample():
+def oracle_matvec_sample(incompressible=False):
     """Set up the 1024^2 workload in the FP64 oracle (untimed state solve at
     a smooth velocity) and return a callable doing one GN Hessian matvec."""
     from oracle.problem import Problem
     from paper_1604_02153_gb300 import inputs
     m_R, m_T = inputs.ellipse_phantoms(N_GRID, seed=100)
-    P = Problem(m_R, m_T, NT, BETAS[-1])
+    P = Problem(m_R, m_T, NT, BETAS[-1], incompressible=incompressible)
     P.state_solve(inputs.random_velocity(N_GRID, seed=7, vmax=0.2))
     P.ensure_adjoint_characteristic()
     vt = inputs.random_velocity(N_GRID, seed=8, vmax=1.0)
     return lambda: P.hessian_matvec(vt)
 
 
-def cpu_baseline():
-    f = oracle_matvec_sample()
+def cpu_baseline(incompressible=False):
+    f = oracle_matvec_sample(incompressible)
     t0 = time.perf_counter()
     f()
     dt = time.perf_counter() - t0
@@ -226,7 +228,7 @@ def cpu_baseline():
 def run_reference(args, rank):
     if rank != 0:
         return
-    f = oracle_matvec_sample()
+    f = oracle_matvec_sample(args.incompressible)
     for _ in range(args.warmup):
         f()
     t0 = time.perf_counter()
@@ -238,7 +240,7 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp),
+            "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"one FP64 oracle GN Hessian matvec per step at "
                                        f"{N_GRID}^2, nt={NT}"},
@@ -247,7 +249,7 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline"):
+def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", incompressible=False):
     pc = {"2l-cheb": "P_2L CHEB(10) 512^2 coarse", "2l-pcg": "P_2L PCG(1e-1) 512^2 coarse",
           "reg": "P_REG"}[precond]
     if coarse_nt and precond != "reg":
@@ -256,9 +258,11 @@ def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline"):
         pc += " cubic-Lagrange"
     return {"workload": f"phantom pair {N_GRID}x{N_GRID} (12 random ellipses, sigma 2 px), "
                         f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, {pc}, "
-                        f"||g||rel 1e-2, cubic B-spline SL",
+                        f"||g||rel 1e-2, cubic B-spline SL"
+                        + (", incompressible (K = Leray projection)" if incompressible else ""),
             "grid": [N_GRID, N_GRID], "nt": NT, "betas": list(BETAS), "gtol": GTOL,
             "precond": pc, "interp": "spline", "reg_norm": "H1",
+            "incompressible": bool(incompressible),
             "l2": "flushed between steps (256 MB write, untimed)"}
 
 
@@ -458,6 +462,7 @@ def main():
                "2l-pcg": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_PCG),
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
     R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
+                           incompressible=int(args.incompressible),
                            coarse_nt=args.coarse_nt,
                            coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
                                           "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
@@ -565,7 +570,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp),
+                "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible),
                 "time_to_solution_s": total_ms / args.steps / 1e3,
                 "newton_iters_per_solve": stats["newton"] / args.steps,
                 "matvecs_per_solve": stats["matvecs"] / args.steps,
@@ -581,7 +586,7 @@ def main():
                 "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
                 "clocks": clocks.summary()}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.incompressible)
         if not args.no_warm_start:
             line["learned_warm_start"] = learned_warm_start(R, v, ok, dev)
         print(json.dumps(line), flush=True)

@@ -7,8 +7,9 @@
  * (arXiv 1604.02153). The library minimises, over a stationary velocity v,
  *     J[v] = 1/2 ||m_1 - m_R||^2_L2 + beta/2 <v, A v>_L2          (eq. varopt:objective)
  * subject to the transport equation d_t m + grad m . v = 0, m(0) = m_T, with
- * periodic boundary conditions on the 2-torus [0, 2 pi)^2 (§2, compressible
- * case: no divergence constraint, K = I).
+ * periodic boundary conditions on the 2-torus [0, 2 pi)^2 (§2): compressible
+ * (no divergence constraint, K = I, the default) or incompressible (div v = 0
+ * with w = 0, K the Leray projection; reg_options.incompressible).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -130,6 +131,16 @@ typedef struct {
                               level, once per grid and interpolation model in
                               the process, and keeps the fastest. Results do
                               not depend on the shape                          */
+  int incompressible;      /* 0 (default): K = I in the gradient and the Hessian
+                              (eq. control-elim, eq. hessian-matvec). 1: the
+                              incompressible problem, div v = 0 with w = 0 (§2):
+                              K = the Leray projection -grad Lap^-1 div + I of
+                              §3.1, applied spectrally (the derivative
+                              wavenumbers of REG_SPEC_GRAD/DIV, identity where
+                              |k| = 0); reg_solve and reg_warm_start project
+                              the velocity onto divergence-free fields first,
+                              and P_2L's coarse operator and Lanczos start
+                              vector carry K as well                          */
 } reg_options;
 
 typedef struct {
@@ -199,9 +210,11 @@ reg_status reg_interpolate(reg_ctx* ctx, const float* u, const float* disp, floa
  *   REG_SPEC_LOWPASS  vector -> vector   keep |k_i| < n_i/4
  *   REG_SPEC_HIGHPASS vector -> vector   remove |k_i| < n_i/4
  *   REG_SPEC_PREFILTER scalar -> scalar  periodic cubic B-spline coefficients
+ *   REG_SPEC_LERAY    vector -> vector   K = -grad Lap^-1 div + I (§3.1, w = 0):
+ *                                        the divergence-free part
  * `s` is used by REG_SPEC_REGPOW only. in and out must not alias. */
 enum { REG_SPEC_GRAD = 0, REG_SPEC_DIV = 1, REG_SPEC_REG = 2, REG_SPEC_REGPOW = 3,
-       REG_SPEC_LOWPASS = 4, REG_SPEC_HIGHPASS = 5, REG_SPEC_PREFILTER = 6 };
+       REG_SPEC_LOWPASS = 4, REG_SPEC_HIGHPASS = 5, REG_SPEC_PREFILTER = 6, REG_SPEC_LERAY = 7 };
 reg_status reg_spectral(reg_ctx* ctx, int op, double s, const float* in, float* out);
 
 /* Spectral restriction of a vector field from the context grid to the grid
@@ -212,7 +225,7 @@ reg_status reg_restrict(reg_ctx* ctx, const float* fine, float* coarse);
 reg_status reg_prolong(reg_ctx* ctx, const float* coarse, float* fine);
 
 /* Objective J (host double) and reduced gradient g = beta A v +
- * int_0^1 lambda grad m dt (eq. control-elim, K = I) at v (device). g
+ * K[int_0^1 lambda grad m dt] (eq. control-elim) at v (device). g
  * (2*n1*n2, device) may be NULL. Caches the state, adjoint characteristics
  * and the time history of grad m for later Hessian matvecs at the same v.
  * Synchronises the stream (returns a host scalar). */
@@ -221,7 +234,7 @@ reg_status reg_objective_gradient(reg_ctx* ctx, const float* v, double* J, float
 /* Objective only (state solve plus regularisation); *J is host. */
 reg_status reg_objective(reg_ctx* ctx, const float* v, double* J);
 
-/* Gauss-Newton Hessian matvec Hvt = H(v) vt = beta A vt + int_0^1 lambda~ grad m dt
+/* Gauss-Newton Hessian matvec Hvt = H(v) vt = beta A vt + K[int_0^1 lambda~ grad m dt]
  * (eq. hessian-matvec with every lambda term dropped, §3.4.1 footnote, §3.5
  * "Hessian"): incremental state solve forward, incremental adjoint solve
  * backward, all device pointers of 2*n1*n2 floats. If v differs from the

@@ -387,6 +387,18 @@ __device__ __forceinline__ float regpow(float beta, int p, float s, int k1, int 
   return powf(bg, s);
 }
 
+// Leray projection K = I - grad (div grad)^-1 div (§3.1, the K of the
+// gradient for an incompressible velocity): entry (o, c) of its symbol
+// delta_oc - k_o k_c / |k|^2 with the derivative wavenumbers of grad and div
+// (Nyquist zeroed), so that div K b vanishes for the discrete div; the
+// identity on the modes where div grad vanishes.
+__device__ __forceinline__ float leray(int o, int c, float kd1, float kd2) {
+  const float q = kd1 * kd1 + kd2 * kd2;
+  const float d = (o == c) ? 1.f : 0.f;
+  if (q == 0.f) return d;
+  return d - (o == 0 ? kd1 : kd2) * (c == 0 ? kd1 : kd2) / q;
+}
+
 // sigma_{o,c}(k1, k2) as a complex number; k1 >= 0, k2 signed; n1, n2 of the
 // grid the Nyquist and filter conditions refer to.
 __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1, int k2) {
@@ -409,6 +421,12 @@ __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1,
       return make_float2(low ? 0.f : 1.f, 0.f);
     case SPOP_REGPOW_HIGH:
       return make_float2(low ? 0.f : regpow(a.beta, a.p, a.s, k1, k2), 0.f);
+    case SPOP_LERAY:
+      return make_float2(leray(o, c, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
+    case SPOP_REGPOW_LERAY:
+      return make_float2(regpow(a.beta, a.p, a.s, k1, k2) *
+                             leray(o, c, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2),
+                         0.f);
     default:
       return make_float2(0.f, 0.f);
   }

@@ -59,6 +59,8 @@ enum SpecOp {
   SPOP_LOWPASS = 4,      // |k1| < n1/4 and |k2| < n2/4
   SPOP_HIGHPASS = 5,     // complement of LOWPASS
   SPOP_REGPOW_HIGH = 6,  // REGPOW restricted to the high band
+  SPOP_LERAY = 7,        // 2 -> 2: delta_oc - k_o k_c / |k|^2 (Nyquist zeroed; 1 where |k| = 0)
+  SPOP_REGPOW_LERAY = 8, // 2 -> 2: REGPOW times LERAY
 };
 
 struct ColArgs {

@@ -86,6 +86,7 @@ struct reg_ctx {
   double beta = 0;
   int nt = 0;
   bool two_level = false;
+  bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
   Level fine, coarse;
   std::vector<void*> allocs;
   std::vector<std::pair<int, float2*>> tw;   // twiddle tables by length
@@ -867,11 +868,20 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     std::swap(lam, lam2);
   }
   check_launch(c, "adjoint solve");
-  {
+  if (c->incompressible) {   // g = beta A v + K[b], K the Leray projection
+    spectral(c, L, SPOP_LERAY, 0.0, L.b, 2, 1, g_out, 2, L.Av);
+  } else {
     Prof P(c, REG_KC_VECTOR, 24.0 * N);
     launch_lincomb(2 * (long long)N, 1.f, L.Av, 1.f, L.b, g_out, c->st);
   }
   check_launch(c, "gradient");
+}
+
+// beta A v~ + K[b~] for the incompressible problem (K the Leray projection),
+// with b~ in L.b; L.w1 holds beta A v~ in between.
+void finish_hessian_incompressible(reg_ctx* c, Level& L, const float* vt, float* out) {
+  spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, L.w1, 1, nullptr);
+  spectral(c, L, SPOP_LERAY, 0.0, L.b, 2, 1, out, 2, L.w1);
 }
 
 // Gauss-Newton Hessian matvec (eq. hessian-matvec, GN); data_only drops beta A vt.
@@ -927,7 +937,10 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       data_term_persistent(c, L, vt, out);
     } else {
       data_term_persistent(c, L, vt, L.b);
-      spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+      if (c->incompressible)
+        finish_hessian_incompressible(c, L, vt, out);
+      else
+        spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
     }
     (void)N2;
     return;
@@ -939,7 +952,8 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const int lg = L.lagrange;
   // beta A v~: its forward transforms depend only on v~ and run on the side
   // stream while the transport steps (which use no FFT workspace) run here
-  if (!data_only) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
+  const bool fork = !data_only && !c->incompressible;
+  if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
   float* mt = L.fA;
   float* mt2 = L.fB;
   float* lt = nullptr;
@@ -1016,6 +1030,8 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   check_launch(c, "incremental adjoint");
   if (data_only) {
     check(c, cudaMemcpyAsync(out, L.b, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  } else if (c->incompressible) {
+    finish_hessian_incompressible(c, L, vt, out);
   } else {
     join_side(c);
     spectral_inv(c, L, 1, 2, out, 1, L.b);
@@ -1037,7 +1053,10 @@ void coarse_split_op(reg_ctx* c, const float* s, float* out) {
   Level& C = c->coarse;
   spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
   hessian_core(c, C, c->cu, c->cq, true);
-  spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
+  if (c->incompressible)
+    spectral(c, C, SPOP_REGPOW_LERAY, -0.5, c->cq, 2, 1, out, 2, s);
+  else
+    spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
   ++c->coarse_matvecs;
 }
 
@@ -1078,6 +1097,10 @@ void estimate_eigenvalues(reg_ctx* c) {
   float* qprev = c->cz;
   float* w = c->cd;
   launch_splitmix(q, n, c->opt.lanczos_seed, c->st);
+  if (c->incompressible) {   // start (and stay) among divergence-free fields
+    spectral(c, C, SPOP_LERAY, 0.0, q, 2, 1, C.w2, 2, nullptr);
+    check(c, cudaMemcpyAsync(q, C.w2, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  }
   const double nq = std::sqrt(dot_sync(c, q, q, n, S_A));
   launch_lincomb(n, (float)(1.0 / nq), q, 0.f, nullptr, q, c->st);
   launch_fill(qprev, n, 0.f, c->st);
@@ -1113,7 +1136,10 @@ void coarse_op_u(reg_ctx* c, const float* u, float* out, const ChebEpilogue* che
   LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
   hessian_core(c, C, u, c->cq, true);
-  spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u, cheb);
+  if (c->incompressible)
+    spectral(c, C, SPOP_REGPOW_LERAY, -1.0, c->cq, 2, 1, out, 2, u, cheb);
+  else
+    spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u, cheb);
   ++c->coarse_matvecs;
 }
 
@@ -1367,6 +1393,7 @@ reg_status reg_default_options(reg_options* o) {
   o->coarse_nt = 0;
   o->coarse_interp = -1;
   o->step_tile = -1;
+  o->incompressible = 0;
   return REG_OK;
 }
 
@@ -1385,7 +1412,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.precond != 0 && o.precond != 1) || (o.pc_solver != 0 && o.pc_solver != 1) ||
       o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0 ||
       o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1 ||
-      o.step_tile < -1 || o.step_tile > kStepTiles)
+      o.step_tile < -1 || o.step_tile > kStepTiles ||
+      (o.incompressible != 0 && o.incompressible != 1))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1398,6 +1426,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->beta = beta;
   c->nt = nt;
   c->two_level = (o.precond == REG_PC_2L);
+  c->incompressible = (o.incompressible != 0);
   c->fine.lagrange = (o.interp == REG_INTERP_LAGRANGE);
   c->coarse.lagrange = o.coarse_interp < 0 ? c->fine.lagrange : (o.coarse_interp == REG_INTERP_LAGRANGE);
   c->persistent = (o.persistent_matvec != 0);
@@ -1576,6 +1605,7 @@ reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* ou
         break;
       case REG_SPEC_LOWPASS: spectral(c, F, SPOP_LOWPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_HIGHPASS: spectral(c, F, SPOP_HIGHPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
+      case REG_SPEC_LERAY: spectral(c, F, SPOP_LERAY, 0.0, in, 2, 1, out, 2, nullptr); break;
       case REG_SPEC_PREFILTER:
         if (F.lagrange) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
         coefficients(c, F, in, 1, out);
@@ -1775,6 +1805,10 @@ reg_status reg_warm_start(reg_ctx* c, reg_unet* net, float* v, int* accepted) {
       src = dst;
       m *= 2;
     }
+    if (c->incompressible) {   // the network's velocity made divergence free
+      spectral(c, F, SPOP_LERAY, 0.0, v, 2, 1, F.w1, 2, nullptr);
+      check(c, cudaMemcpyAsync(v, F.w1, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+    }
     // accepted only if it lowers the objective below J(0); J(0) comes with
     // the gradient at v = 0 that the solve's relative tolerance needs anyway
     ensure_gref(c);
@@ -1798,6 +1832,10 @@ reg_status reg_solve(reg_ctx* c, float* v, double gtol, reg_info* info) {
     Level& F = c->fine;
     const long long n = 2 * F.g.N;
     const double hh = F.h1 * F.h2;
+    if (c->incompressible) {   // iterates stay divergence free from a projected start
+      spectral(c, F, SPOP_LERAY, 0.0, v, 2, 1, c->vt_tmp, 2, nullptr);
+      check(c, cudaMemcpyAsync(v, c->vt_tmp, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+    }
     ensure_gref(c);
     inf.gref_inf = c->gref_inf;
     double J = objective_gradient(c, v, c->gcur);

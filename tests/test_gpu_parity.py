@@ -594,3 +594,122 @@ def test_full_size_phantom_gradient_and_hessian(regnk):
     assert rel(host(g, shape) - host(Av, shape), g_ref - spectral.apply_reg(v, beta, "H1")) < 1e-4
     assert rel(host(H, shape) - host(Au, shape), H_ref - spectral.apply_reg(u, beta, "H1")) < 1e-4
     R.close()
+
+
+# ---------------------------------------------------------------------------
+# incompressible problem (div v = 0, w = 0): K = Leray projection (§3.1)
+
+@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 64), (192, 96), (512, 512)])
+def test_leray_projection(regnk, n1, n2):
+    """REG_SPEC_LERAY against the oracle's K = -grad Lap^-1 div + I on a field
+    with every mode (Nyquist lines included): within the FP32 bound of a
+    spectral multiply with |sigma| <= 1, and the GPU divergence of the result
+    at the FP32 roundoff of a derivative."""
+    R = regnk.Registration(n1, n2, 4, 1e-2, **pc_for(n1, n2))
+    rng = np.random.default_rng(n1 + n2)
+    v = f32(rng.standard_normal((2, n2, n1)))
+    N = n1 * n2
+    out2, out1 = torch.empty(2 * N, device="cuda"), torch.empty(N, device="cuda")
+    R.spectral(regnk.REG_SPEC_LERAY, dev(v), out2)
+    Kv = host(out2, (2, n2, n1))
+    assert within(Kv, spectral.leray(v), fp32_bound(n1, n2, 1.0, v))
+    R.spectral(regnk.REG_SPEC_DIV, out2, out1)
+    assert float(np.linalg.norm(host(out1, (n2, n1)))) <= 2 * fp32_bound(n1, n2, max(n1, n2), v)
+    R.close()
+
+
+@pytest.mark.parametrize("n1,n2,nt,persistent", [(64, 64, 4, 0), (128, 64, 8, 0), (64, 64, 4, 1),
+                                                 (192, 96, 4, 0)])
+def test_incompressible_gradient_and_hessian(regnk, n1, n2, nt, persistent):
+    """g = beta A v + K[b] and H u = beta A u + K[b~] against the oracle's
+    incompressible problem on the same FP32 inputs (divergence-free v and
+    u), with the bars of the compressible test."""
+    beta = 1e-2
+    R = regnk.Registration(n1, n2, nt, beta, incompressible=1, persistent_matvec=persistent,
+                           **pc_for(n1, n2))
+    m_R, m_T, v0 = problem_data(n1, n2)
+    m_R, m_T = f32(m_R), f32(m_T)
+    v = f32(spectral.leray(v0))
+    u = f32(spectral.leray(inputs.random_velocity(n1, n2, seed=21, vmax=1.0)))
+    R.set_images(dev(m_R), dev(m_T))
+    P = Problem(m_R, m_T, nt, beta, incompressible=True)
+    J_ref, g_ref = P.objective_gradient(v)
+    Av_ref = spectral.apply_reg(v, beta, "H1")
+    vd = dev(v)
+    g = torch.empty(2 * n1 * n2, device="cuda")
+    J = R.objective_gradient(vd, g)
+    Av = torch.empty_like(g)
+    R.spectral(regnk.REG_SPEC_REG, vd, Av)
+    shape = (2, n2, n1)
+    assert abs(J - J_ref) / abs(J_ref) < 1e-5
+    assert rel(host(g, shape) - host(Av, shape), g_ref - Av_ref) < 1e-4
+    assert within(host(g, shape), g_ref, 1e-4 * np.linalg.norm(g_ref)
+                  + fp32_bound(n1, n2, beta * gamma_max(n1, n2, 1), v))
+    H = torch.empty_like(g)
+    R.hessian_matvec(vd, dev(u), H)
+    Au = torch.empty_like(H)
+    R.spectral(regnk.REG_SPEC_REG, dev(u), Au)
+    H_ref = P.hessian_matvec(u)
+    Au_ref = spectral.apply_reg(u, beta, "H1")
+    assert rel(host(H, shape) - host(Au, shape), H_ref - Au_ref) < 1e-4
+    assert within(host(H, shape), H_ref, 1e-4 * np.linalg.norm(H_ref)
+                  + fp32_bound(n1, n2, beta * gamma_max(n1, n2, 1), u))
+    R.close()
+
+
+@pytest.mark.parametrize("pc_solver", [0, 1])
+def test_incompressible_two_level_preconditioner(regnk, pc_solver):
+    """P_2L with K in the coarse operator (CHEB with Lanczos bounds from a
+    projected start vector, or nested PCG) against the oracle."""
+    n, nt, beta = 128, 4, 1e-2
+    m_R, m_T, v0 = problem_data(n, n)
+    v = f32(spectral.leray(v0))
+    r = f32(spectral.leray(inputs.random_velocity(n, seed=27, vmax=1.0)))
+    R = regnk.Registration(n, n, nt, beta, incompressible=1, pc_solver=pc_solver)
+    R.set_images(dev(m_R), dev(m_T))
+    emin, emax = R.eigen_bounds()
+    R.objective_gradient(dev(v), None)
+    z = torch.empty(2 * n * n, device="cuda")
+    R.precond_apply(dev(r), z)
+    seed = regnk.default_options().lanczos_seed
+    nc = n // 2
+    lv0 = inputs.splitmix64_uniform(2 * nc * nc, seed).reshape(2, nc, nc)
+    S = Solver(Problem(m_R, m_T, nt, beta, incompressible=True), precond="2L",
+               pc_solver="cheb" if pc_solver == 0 else "pcg", lanczos_v0=lv0)
+    e = S.estimate_eigenvalues()
+    assert abs(emax - e["emax"]) / e["emax"] < 1e-3 and abs(emin - e["emin"]) < 1e-12 * emin
+    S.eig = {"emin": emin, "emax": emax, "beta": beta}
+    S.p.state_solve(v)
+    S.set_velocity_coarse(v)
+    assert rel(host(z, (2, n, n)), S.apply_precond(r)) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("pc", ["REG", "2L"])
+def test_incompressible_full_solve_64(regnk, pc):
+    """The divergence-free vortex pair solved from a start that is not
+    divergence free (both sides project it): same Newton iterations, final
+    velocity within 1e-3 of the oracle's, and divergence free."""
+    n, nt, beta, gtol = 64, 4, 1e-2, 1e-2
+    m_T, vstar = inputs.vortex_pair(n)
+    m_R = f32(Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar))
+    m_T = f32(m_T)
+    v0 = f32(inputs.random_velocity(n, seed=6, vmax=0.05))
+    R = regnk.Registration(n, n, nt, beta, incompressible=1,
+                           precond=regnk.REG_PC_REG if pc == "REG" else regnk.REG_PC_2L)
+    R.set_images(dev(m_R), dev(m_T))
+    v = dev(v0)
+    info = R.solve(v, gtol)
+    seed = regnk.default_options().lanczos_seed
+    lv0 = inputs.splitmix64_uniform(2 * (n // 2) ** 2, seed)
+    S = Solver(Problem(m_R, m_T, nt, beta, incompressible=True), precond=pc, lanczos_v0=lv0)
+    vo, oinfo = S.solve(v0, gtol)
+    assert info["gnorm_rel"] <= gtol
+    assert info["newton_iters"] == oinfo["newton_iters"]
+    vg = host(v, (2, n, n))
+    assert rel(vg, vo) < 1e-3
+    assert abs(info["J"] - oinfo["J"]) / oinfo["J"] < 1e-4
+    d = torch.empty(n * n, device="cuda")
+    R.spectral(regnk.REG_SPEC_DIV, v, d)
+    assert float(np.linalg.norm(host(d, (n, n)))) <= 2 * fp32_bound(n, n, n, vg)
+    R.close()
