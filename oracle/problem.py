@@ -19,7 +19,11 @@ Optimise-then-discretise (§3.1):
   dropped (§3.4.1 footnote, §3.5 "Hessian"):
       H v~ = beta A v~ + K[int_0^1 lambda~ grad m dt],
   m~ from eq. inc-state-pde-elim (m~(0) = 0), lambda~ from
-  eq. inc-adj-pde-elim without the div(lambda v~) term, lambda~_1 = -m~_1.
+  eq. inc-adj-pde-elim without the div(lambda v~) term, lambda~_1 = -m~_1;
+* full-Newton Hessian matvec (hessian="full"), eq. hessian-matvec as
+  written: H v~ = beta A v~ + K[int_0^1 lambda~ grad m + lambda grad m~ dt],
+  lambda~ from eq. inc-adj-slm with the div(lambda v~) source, lambda the
+  adjoint of the last gradient evaluation (its history is kept).
 Time integrals use the trapezoidal rule on the nt + 1 time levels (the paper
 only states a midpoint rule for integral operators, which fixes the spatial
 sum; no half-step values exist in time).
@@ -45,7 +49,8 @@ D = 2  # spatial dimension
 class Problem:
     """One registration problem on an (n2, n1) grid with nt time steps."""
 
-    def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline", incompressible=False):
+    def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline", incompressible=False,
+                 hessian="gn"):
         self.m_R = np.asarray(m_R, dtype=np.float64)
         self.m_T = np.asarray(m_T, dtype=np.float64)
         self.n2, self.n1 = self.m_R.shape
@@ -55,6 +60,9 @@ class Problem:
         self.reg_norm = reg_norm
         self.kind = kind
         self.incompressible = bool(incompressible)
+        assert hessian in ("gn", "full")
+        self.full_newton = hessian == "full"
+        self.lam = None
         self.h1 = 2.0 * np.pi / self.n1
         self.h2 = 2.0 * np.pi / self.n2
         self.w = transport.trapezoid_weights(self.nt)
@@ -102,6 +110,7 @@ class Problem:
             self._count(row, ips=1)
         self.m = m
         self.dY = None
+        self.lam = None          # the adjoint belongs to the previous velocity
         return m[-1]
 
     def objective(self, v):
@@ -171,6 +180,8 @@ class Problem:
         """
         nt, ht, kind = self.nt, self.ht, self.kind
         vt = np.asarray(vt, dtype=np.float64)
+        if self.full_newton:
+            return self._hessian_matvec_full(vt, row)
         self.ensure_adjoint_characteristic()
         vt_dep = np.stack([transport.at_departure(vt[c], self.dX, kind) for c in range(2)])
         self._count(row, ips=D)
@@ -194,6 +205,58 @@ class Problem:
             lt = transport.adjoint_step(lt, self.dY, delta, delta_bar, ht, kind)
             self._count(row, ips=1)
             bt = bt + self.ht * self.w[j] * lt * self._grad_m(j, row)
+        self._count(row, ffts=2 * D)
+        return spectral.apply_reg(vt, self.beta, self.reg_norm) + self.K(bt, row)
+
+    def _hessian_matvec_full(self, vt, row):
+        """Full-Newton matvec (eq. hessian-matvec with its lambda terms).
+
+        Needs the adjoint history lambda_0..lambda_nt of a gradient evaluation
+        at the current velocity. incSE as in the GN matvec, keeping m~_j;
+        div(lambda_j v~) at the nt + 1 time levels (d + 1 FFTs each); incAE
+        with that source (2 IPs per step: lambda~_{j+1} and the source at
+        Y_D, plus div v at Y_D once); the time integral of
+        lambda~ grad m + lambda grad m~ recomputes grad m_j and grad m~_j
+        (d + 1 FFTs per level j >= 1; m~_0 = 0).
+        """
+        assert self.lam is not None, "full-Newton matvec needs the gradient at this velocity"
+        nt, ht, kind = self.nt, self.ht, self.kind
+        lam = self.lam
+        self.ensure_adjoint_characteristic()
+        vt_dep = np.stack([transport.at_departure(vt[c], self.dX, kind) for c in range(2)])
+        self._count(row, ips=D)
+        mt = [np.zeros((self.n2, self.n1))]
+        gm_prev = self.grad_mT
+        for j in range(1, nt + 1):
+            gm_cur = self._grad_m(j, row)
+            gm_prev_dep = np.stack([transport.at_departure(gm_prev[c], self.dX, kind)
+                                    for c in range(2)])
+            mt.append(transport.incstate_step(mt[-1], self.dX, vt_dep, gm_prev_dep, vt, gm_cur,
+                                              ht, kind))
+            self._count(row, ips=1 + D)
+            gm_prev = gm_cur
+        self.mt_final = mt[-1]
+        src = []
+        for j in range(nt + 1):
+            src.append(spectral.div(lam[j] * vt))
+            self._count(row, ffts=D + 1)
+        delta = self._div_v(row)
+        delta_bar = transport.at_departure(delta, self.dY, kind)
+        self._count(row, ips=1)
+
+        def grad_mt(j):
+            if j == 0:
+                return np.zeros((2, self.n2, self.n1))
+            self._count(row, ffts=1 + D)
+            return spectral.grad(mt[j])
+
+        lt = -mt[nt]                                   # eq. inc-adj-fc-elim
+        bt = ht * self.w[nt] * (lt * self._grad_m(nt, row) + lam[nt] * grad_mt(nt))
+        for j in range(nt - 1, -1, -1):
+            lt = transport.incadjoint_step_full(lt, self.dY, delta, delta_bar, src[j + 1], src[j],
+                                                ht, kind)
+            self._count(row, ips=2)
+            bt = bt + ht * self.w[j] * (lt * self._grad_m(j, row) + lam[j] * grad_mt(j))
         self._count(row, ffts=2 * D)
         return spectral.apply_reg(vt, self.beta, self.reg_norm) + self.K(bt, row)
 

@@ -78,6 +78,22 @@ def adjoint_step(lam_next, dY, delta, delta_bar, ht, kind):
     return lb + 0.5 * ht * (lb * delta_bar + lstar * delta)
 
 
+def incadjoint_step_full(lt_next, dY, delta, delta_bar, src_next, src, ht, kind):
+    """Full-Newton incremental adjoint eq. inc-adj-slm in reversed time:
+    D_tau lam~ = lam~ div v + div(lambda v~).
+
+    src_next = div(lambda_{j+1} v~), src = div(lambda_j v~) at the nodes;
+    src_next is interpolated at Y_D like lam~_{j+1}. Heun with the source at
+    the departure point (level j+1) and at the node (level j); dropping both
+    sources gives adjoint_step (the Gauss-Newton incremental adjoint).
+    """
+    lb = at_departure(lt_next, dY, kind)
+    sb = at_departure(src_next, dY, kind)
+    f_dep = lb * delta_bar + sb
+    lstar = lb + ht * f_dep
+    return lb + 0.5 * ht * (f_dep + lstar * delta + src)
+
+
 def incstate_step(mt_prev, dX, vt_dep, gm_prev_dep, vt, gm_cur, ht, kind):
     """Incremental state eq. inc-state-slm: D_t m~ = -v~ . grad m.
 

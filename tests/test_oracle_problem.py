@@ -237,3 +237,84 @@ def test_incompressible_gradient_and_hessian_are_leray_projections():
     eps = 1e-4
     fd = (Pi.objective(v + eps * dv) - Pi.objective(v - eps * dv)) / (2 * eps)
     assert abs(fd - d) < 1e-4 * abs(d)
+
+
+def _fn_problem(n, nt, zero_residual=False):
+    m_T = inputs.random_field(n, seed=1, kmax=4)
+    m_R = inputs.random_field(n, seed=2, kmax=4)
+    v = inputs.random_velocity(n, seed=3, vmax=0.3)
+    if zero_residual:
+        m_R = Problem(np.zeros((n, n)), m_T, nt, 1e-2).state_solve(v)
+    return m_R, m_T, v
+
+
+def test_full_newton_hessian_is_the_derivative_of_the_gradient():
+    """eq. hessian-matvec with its lambda terms (full Newton): H u equals the
+    central difference of the reduced gradient along u up to the
+    optimise-then-discretise gap, which shrinks with the grid; on this
+    problem (large residual) the Gauss-Newton matvec misses it by O(1), so
+    a dropped or flipped lambda term would fail."""
+    errs = []
+    for n in (32, 128):
+        nt = 8
+        m_R, m_T, v = _fn_problem(n, nt)
+        u = inputs.random_velocity(n, seed=9, vmax=1.0)
+        P = Problem(m_R, m_T, nt, 1e-2, hessian="full")
+        P.objective_gradient(v)
+        Hfn = P.hessian_matvec(u)
+        G = Problem(m_R, m_T, nt, 1e-2)
+        G.objective_gradient(v)
+        Hgn = G.hessian_matvec(u)
+        eps = 1e-4
+        _, gp = G.objective_gradient(v + eps * u)
+        _, gm = G.objective_gradient(v - eps * u)
+        fd = (gp - gm) / (2 * eps)
+        e_fn = np.linalg.norm(Hfn - fd) / np.linalg.norm(fd)
+        e_gn = np.linalg.norm(Hgn - fd) / np.linalg.norm(fd)
+        assert e_fn < 2e-3 and e_gn > 0.5, (n, e_fn, e_gn)
+        errs.append(e_fn)
+    assert errs[1] < errs[0] / 3, errs
+
+
+def test_full_newton_equals_gauss_newton_at_zero_residual():
+    """m_R = m_1(v): the adjoint lambda vanishes, so do the terms that the
+    Gauss-Newton approximation drops (§3.4.1 footnote)."""
+    n, nt = 32, 4
+    m_R, m_T, v = _fn_problem(n, nt, zero_residual=True)
+    u = inputs.random_velocity(n, seed=9, vmax=1.0)
+    out = []
+    for h in ("gn", "full"):
+        P = Problem(m_R, m_T, nt, 1e-2, hessian=h)
+        P.objective_gradient(v)
+        assert max(np.max(np.abs(l)) for l in P.lam) < 1e-13
+        out.append(P.hessian_matvec(u))
+    assert np.max(np.abs(out[0] - out[1])) < 1e-12 * np.max(np.abs(out[0]))
+
+
+def test_full_newton_matvec_is_symmetric_within_the_adjoint_error():
+    n, nt = 64, 8
+    m_R, m_T, v = _fn_problem(n, nt)
+    P = Problem(m_R, m_T, nt, 1e-2, hessian="full")
+    P.objective_gradient(v)
+    a = inputs.random_velocity(n, seed=11, vmax=1.0)
+    b = inputs.random_velocity(n, seed=12, vmax=1.0)
+    ab, ba = P.inner(P.hessian_matvec(a), b), P.inner(a, P.hessian_matvec(b))
+    assert abs(ab - ba) < 1e-2 * abs(ab)
+
+
+@pytest.mark.parametrize("nt", [1, 4, 7])
+def test_full_newton_counts_against_appendix_c(repo_root, nt):
+    """Interpolations per full-Newton matvec equal Appendix C's FN row
+    (d + (d+3) nt + 1: the source div(lambda v~) is interpolated at Y_D once
+    per step). FFTs: the table's FN row counts 2(d+1) fewer than this
+    schedule, which recomputes div v (as the GN row does) and takes the
+    source at all nt + 1 time levels that Heun's rule touches."""
+    fn = _golden_counts(f"{repo_root}/tests/golden/complexity_sl_fn.txt", nt)
+    n, d = 16, 2
+    m_R, m_T, v = _fn_problem(n, nt)
+    P = Problem(m_R, m_T, nt, 1e-2, hessian="full")
+    P.objective_gradient(v)
+    P.reset_counts()
+    P.hessian_matvec(inputs.random_velocity(n, seed=9, vmax=1.0))
+    assert P.counts["matvec"][1] == fn["matvec"][1]
+    assert P.counts["matvec"][0] == fn["matvec"][0] + 2 * (d + 1)
