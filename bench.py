@@ -88,6 +88,8 @@ def parse():
                     help="time steps of the P_2L coarse problem (0: the problem's nt; default "
                          "-1: nt/2, the fine grid's displacement per step in coarse cells, for "
                          "phantom1024, and the problems' nt for batch64)")
+    ap.add_argument("--hessian", choices=["gn", "full"], default="gn",
+                    help="Gauss-Newton (the workload's) or full-Newton Hessian matvec")
     ap.add_argument("--incompressible", action="store_true",
                     help="the incompressible problem (div v = 0, K the Leray projection)")
     ap.add_argument("--no-warm-start", action="store_true",
@@ -240,7 +242,8 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible),
+            "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible,
+                                  args.hessian),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"one FP64 oracle GN Hessian matvec per step at "
                                        f"{N_GRID}^2, nt={NT}"},
@@ -249,7 +252,8 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", incompressible=False):
+def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", incompressible=False,
+                    hessian="gn"):
     pc = {"2l-cheb": "P_2L CHEB(10) 512^2 coarse", "2l-pcg": "P_2L PCG(1e-1) 512^2 coarse",
           "reg": "P_REG"}[precond]
     if coarse_nt and precond != "reg":
@@ -259,10 +263,12 @@ def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", inco
     return {"workload": f"phantom pair {N_GRID}x{N_GRID} (12 random ellipses, sigma 2 px), "
                         f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, {pc}, "
                         f"||g||rel 1e-2, cubic B-spline SL"
-                        + (", incompressible (K = Leray projection)" if incompressible else ""),
+                        + (", incompressible (K = Leray projection)" if incompressible else "")
+                        + (", full-Newton Hessian" if hessian == "full" else ""),
             "grid": [N_GRID, N_GRID], "nt": NT, "betas": list(BETAS), "gtol": GTOL,
             "precond": pc, "interp": "spline", "reg_norm": "H1",
             "incompressible": bool(incompressible),
+            "hessian": {"gn": "Gauss-Newton", "full": "full Newton"}[hessian],
             "l2": "flushed between steps (256 MB write, untimed)"}
 
 
@@ -463,6 +469,7 @@ def main():
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
     R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
                            incompressible=int(args.incompressible),
+                           hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
                            coarse_nt=args.coarse_nt,
                            coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
                                           "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
@@ -570,7 +577,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible),
+                "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible,
+                                  args.hessian),
                 "time_to_solution_s": total_ms / args.steps / 1e3,
                 "newton_iters_per_solve": stats["newton"] / args.steps,
                 "matvecs_per_solve": stats["matvecs"] / args.steps,

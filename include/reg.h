@@ -68,6 +68,8 @@ enum { REG_INTERP_SPLINE = 0, REG_INTERP_LAGRANGE = 1 };
 enum { REG_PC_REG = 0, REG_PC_2L = 1 };
 /* Coarse solver of P_2L (§3.4.2): CHEB(k) or nested PCG(eps). */
 enum { REG_PCSOLVER_CHEB = 0, REG_PCSOLVER_PCG = 1 };
+/* reg_options.hessian */
+enum { REG_HESSIAN_GN = 0, REG_HESSIAN_FULL = 1 };
 
 typedef struct { int n1, n2; } reg_grid;
 
@@ -141,6 +143,19 @@ typedef struct {
                               the velocity onto divergence-free fields first,
                               and P_2L's coarse operator and Lanczos start
                               vector carry K as well                          */
+  int hessian;             /* REG_HESSIAN_GN (default): the Gauss-Newton matvec
+                              (every lambda term of eq. hessian-matvec and
+                              eq. inc-adj-pde-elim dropped, §3.4.1 footnote).
+                              REG_HESSIAN_FULL: eq. hessian-matvec as written,
+                              K[int lambda~ grad m + lambda grad m~ dt] with the
+                              div(lambda v~) source in the incremental adjoint;
+                              the gradient then keeps the adjoint history
+                              (nt+1 fields) and the matvec needs it at the same
+                              velocity (recomputed if missing). Problem grid
+                              only: P_2L's coarse operator stays Gauss-Newton.
+                              The full Hessian may be indefinite: PCG stops at
+                              negative curvature (REG_ENEGCURV in kkt_solve).
+                              Needs persistent_matvec = 0                     */
 } reg_options;
 
 typedef struct {

@@ -126,6 +126,19 @@ void launch_adjoint_step(int tile, int n1, int n2, float ht, float wb, const flo
                          const float* dY, const float* delta, const float* delta_bar,
                          const float* gm, float* lam_out, float* b, int lagrange,
                          cudaStream_t st);
+// Full-Newton incremental adjoint (transport.cu): products lambda_j v~ of L
+// time levels, the final condition with the first term of the time
+// integral, and one backward step with the div(lambda v~) source.
+void launch_lam_times_vt(long long N, int L, const float* lam, const float* vt, float* out,
+                         cudaStream_t st);
+void launch_fn_adjoint_init(long long N, float coef_b, const float* mt, const float* gm,
+                            const float* lam, const float* gmt, float* lt, float* b,
+                            cudaStream_t st);
+void launch_fn_adjoint_step(int n1, int n2, float ht, float wb, const float* coef_l,
+                            const float* coef_s, const float* dY, const float* delta,
+                            const float* delta_bar, const float* src, const float* gm,
+                            const float* lam, const float* gmt, float* lt_out, float* b,
+                            int lagrange, cudaStream_t st);
 // Fused prefilter + step kernels (transport.cu). fused_box_width gives the
 // box width (48 or 64) whose halo covers displacements up to max_disp_cells,
 // or 0 if none does; fused_init raises the kernels' shared-memory limit

@@ -75,6 +75,14 @@ struct Level {
   bool lagrange = false;    // interpolation model of this level (cubic Lagrange or spline)
   int tile_adj = kDefaultStepTile;   // tile shapes of k_adjoint_step and k_incstate_step
   int tile_inc = kDefaultStepTile;
+  // full-Newton matvec (problem grid only): adjoint history lambda_0..lambda_nt of
+  // the last gradient, incremental state history, div(lambda_j v~), grad m~_j
+  float* lam_hist = nullptr;  // (nt+1) N
+  float* mt_hist = nullptr;   // (nt+1) N
+  float* src = nullptr;       // (nt+1) N
+  float* gmt = nullptr;       // 2 nt N
+  float* prod = nullptr;      // 2 (nt+1) N
+  bool have_lam = false;      // lam_hist belongs to the cached velocity
 };
 
 }  // namespace
@@ -87,6 +95,7 @@ struct reg_ctx {
   int nt = 0;
   bool two_level = false;
   bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
+  bool full_newton = false;      // full Hessian on the problem grid (P_2L's coarse stays GN)
   Level fine, coarse;
   std::vector<void*> allocs;
   std::vector<std::pair<int, float2*>> tw;   // twiddle tables by length
@@ -769,6 +778,7 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
   }
   check_launch(c, "state solve");
   L.have_v = true;
+  L.have_lam = false;
   L.have_gm = false;
   L.have_div = true;   // dY computed together with dX; delta below
   L.have_G = false;
@@ -844,7 +854,9 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   const size_t N = (size_t)gd.N;
   const int nt = L.nt;
   const float ht = L.ht;
-  float* lam = L.fA;
+  // the full-Newton matvec needs every lambda_j: then they are kept in lam_hist
+  float* hist = L.lam_hist;
+  float* lam = hist ? hist + nt * N : L.fA;
   float* lam2 = L.fB;
   {
     Prof P(c, REG_KC_VECTOR, 28.0 * N);
@@ -852,6 +864,7 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   }
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    if (hist) lam2 = hist + j * N;
     if (L.fuse_w) {   // prefilter of lambda_{j+1} inside the step
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
       launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lam, L.dY, L.delta, L.delta_bar,
@@ -868,6 +881,7 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     std::swap(lam, lam2);
   }
   check_launch(c, "adjoint solve");
+  if (hist) L.have_lam = true;
   if (c->incompressible) {   // g = beta A v + K[b], K the Leray projection
     spectral(c, L, SPOP_LERAY, 0.0, L.b, 2, 1, g_out, 2, L.Av);
   } else {
@@ -929,8 +943,14 @@ void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
 }
 
 // the launch sequence of one GN matvec; needs ensure_G(c, L) beforehand
+void hessian_full(reg_ctx* c, Level& L, const float* vt, float* out);
+
 void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_only) {
   LevelScope ls(c, L);
+  if (c->full_newton && !data_only && &L == &c->fine) {
+    hessian_full(c, L, vt, out);
+    return;
+  }
   if (c->persistent) {
     const size_t N2 = 2 * (size_t)L.g.N;
     if (data_only) {
@@ -1046,6 +1066,81 @@ void set_images_level(reg_ctx* c, Level& L) {
 
 // ---------------------------------------------------------------------------
 // preconditioners and Krylov solvers
+
+// Full-Newton Hessian matvec (eq. hessian-matvec with its lambda terms):
+// H v~ = beta A v~ + K[int_0^1 lambda~ grad m + lambda grad m~ dt], lambda~
+// from eq. inc-adj-slm with the div(lambda v~) source. Uses the adjoint
+// history of the gradient at the cached velocity (recomputed if missing),
+// keeps m~_j, and runs the steps unfused (the source is a second gathered
+// field). Problem grid only.
+void hessian_full(reg_ctx* c, Level& L, const float* vt, float* out) {
+  const GridDims& gd = L.g;
+  const size_t N = (size_t)gd.N;
+  const int nt = L.nt;
+  const float ht = L.ht;
+  const int lg = L.lagrange;
+  ensure_G(c, L);
+  if (!L.have_lam) {
+    objective(c, L);
+    gradient(c, L, L.w2);
+  }
+  // incremental state, m~_j kept in mt_hist (m~_0 = 0 is never read)
+  if (L.fuse_w) {
+    {
+      Prof P(c, REG_KC_INCSTATE_STEP, 44.0 * N);
+      launch_incstate_first_fused(L.fuse_w, gd.n1, gd.n2, ht, vt, L.dX, L.G, L.gm + 2 * N, L.vtD,
+                                  L.mt_hist + N, c->st);
+    }
+    for (int j = 2; j <= nt; ++j) {
+      Prof P(c, REG_KC_INCSTATE_STEP, 48.0 * N);
+      launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, L.mt_hist + (j - 1) * N, L.dX, vt, L.vtD,
+                            L.G + 2 * (j - 1) * N, L.gm + 2 * j * N, L.mt_hist + j * N, nullptr,
+                            nullptr, c->st);
+    }
+  } else {
+    const float* cvt = coefficients(c, L, vt, 2, L.c2);
+    for (int j = 1; j <= nt; ++j) {
+      const float* cm = (j == 1) ? nullptr : coefficients(c, L, L.mt_hist + (j - 1) * N, 1, L.coef);
+      Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 : 48.0) * N);
+      launch_incstate_step(L.tile_inc, gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
+                           L.gm + 2 * j * N, L.mt_hist + j * N, j == 1, lg, c->st,
+                           j == 1 ? cvt : nullptr, nullptr, nullptr);
+    }
+  }
+  check_launch(c, "incremental state");
+  // s_j = div(lambda_j v~), j = 0..nt, and grad m~_j, j = 1..nt
+  {
+    Prof P(c, REG_KC_VECTOR, 16.0 * (nt + 1) * N);
+    launch_lam_times_vt((long long)N, nt + 1, L.lam_hist, vt, L.prod, c->st);
+  }
+  spectral(c, L, SPOP_DIV, 0.0, L.prod, 2, nt + 1, L.src, 1, nullptr);
+  spectral(c, L, SPOP_GRAD, 0.0, L.mt_hist + N, 1, nt, L.gmt, 2, nullptr);
+  // lambda~_nt = -m~_nt and the first term of the time integral
+  float* lt = L.fA;
+  float* lt2 = L.fB;
+  {
+    Prof P(c, REG_KC_VECTOR, 36.0 * N);
+    launch_fn_adjoint_init((long long)N, 0.5f * ht, L.mt_hist + nt * N, L.gm + 2 * nt * N,
+                           L.lam_hist + nt * N, L.gmt + 2 * (nt - 1) * N, lt, L.b, c->st);
+  }
+  for (int j = nt - 1; j >= 0; --j) {
+    const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    const float* cl = coefficients(c, L, lt, 1, L.coef);
+    const float* cs = coefficients(c, L, L.src + (j + 1) * N, 1, L.c2);
+    {
+      Prof P(c, REG_KC_ADJOINT_STEP, 68.0 * N);
+      launch_fn_adjoint_step(gd.n1, gd.n2, ht, wb, cl, cs, L.dY, L.delta, L.delta_bar,
+                             L.src + j * N, L.gm + 2 * j * N, L.lam_hist + j * N,
+                             j ? L.gmt + 2 * (j - 1) * N : nullptr, lt2, L.b, lg, c->st);
+    }
+    std::swap(lt, lt2);
+  }
+  check_launch(c, "incremental adjoint (full Newton)");
+  if (c->incompressible)
+    finish_hessian_incompressible(c, L, vt, out);
+  else
+    spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+}
 
 // (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse level.
 void coarse_split_op(reg_ctx* c, const float* s, float* out) {
@@ -1394,6 +1489,7 @@ reg_status reg_default_options(reg_options* o) {
   o->coarse_interp = -1;
   o->step_tile = -1;
   o->incompressible = 0;
+  o->hessian = 0;
   return REG_OK;
 }
 
@@ -1413,7 +1509,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       o.cheb_iters < 1 || o.max_pcg < 1 || o.lanczos_steps < 1 || o.max_newton < 0 ||
       o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1 ||
       o.step_tile < -1 || o.step_tile > kStepTiles ||
-      (o.incompressible != 0 && o.incompressible != 1))
+      (o.incompressible != 0 && o.incompressible != 1) || (o.hessian != 0 && o.hessian != 1) ||
+      (o.hessian == 1 && o.persistent_matvec != 0))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1427,6 +1524,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->nt = nt;
   c->two_level = (o.precond == REG_PC_2L);
   c->incompressible = (o.incompressible != 0);
+  c->full_newton = (o.hessian == REG_HESSIAN_FULL);
   c->fine.lagrange = (o.interp == REG_INTERP_LAGRANGE);
   c->coarse.lagrange = o.coarse_interp < 0 ? c->fine.lagrange : (o.coarse_interp == REG_INTERP_LAGRANGE);
   c->persistent = (o.persistent_matvec != 0);
@@ -1435,6 +1533,15 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
     alloc_level(c, c->fine, grid.n1, grid.n2, nt);
     if (c->two_level)
       alloc_level(c, c->coarse, grid.n1 / 2, grid.n2 / 2, o.coarse_nt > 0 ? o.coarse_nt : nt);
+    if (c->full_newton) {
+      Level& F = c->fine;
+      const size_t N = (size_t)F.g.N, L1 = (size_t)nt + 1;
+      F.lam_hist = dalloc<float>(c, L1 * N);
+      F.mt_hist = dalloc<float>(c, L1 * N);
+      F.src = dalloc<float>(c, L1 * N);
+      F.gmt = dalloc<float>(c, 2 * (size_t)nt * N);
+      F.prod = dalloc<float>(c, 2 * L1 * N);
+    }
     choose_step_tiles(c, c->fine);
     if (c->two_level) choose_step_tiles(c, c->coarse);
     check(c, cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");

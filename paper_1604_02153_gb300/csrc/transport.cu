@@ -393,6 +393,99 @@ void launch_incstate_step(int tile, int n1, int n2, float ht, const float* coef,
 }
 
 // ---------------------------------------------------------------------------
+// Full-Newton incremental adjoint (eq. inc-adj-slm with the div(lambda v~)
+// source) and the time integral of lambda~ grad m + lambda grad m~
+// (eq. hessian-matvec as written). One point per thread.
+
+// out[j][c] = lam_j * vt_c, j = 0..L-1, c = 0, 1 (the fields whose divergence
+// is the source of the full-Newton incremental adjoint)
+__global__ void __launch_bounds__(kPT)
+k_lam_times_vt(long long N, int L, const float* __restrict__ lam, const float* __restrict__ vt,
+               float* __restrict__ out) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N * L) return;
+  const long long j = idx / N, i = idx - j * N;
+  const float l = __ldg(lam + idx);
+  out[2 * j * N + i] = l * __ldg(vt + i);
+  out[(2 * j + 1) * N + i] = l * __ldg(vt + N + i);
+}
+
+void launch_lam_times_vt(long long N, int L, const float* lam, const float* vt, float* out,
+                         cudaStream_t st) {
+  launch_k(k_lam_times_vt, dim3((unsigned)((N * L + kPT - 1) / kPT)), dim3(kPT), 0, st, N, L, lam,
+           vt, out);
+}
+
+// lam~_nt = -m~_nt; b~ = coef_b (lam~_nt grad m_nt + lam_nt grad m~_nt)
+__global__ void __launch_bounds__(kPT)
+k_fn_adjoint_init(long long N, float coef_b, const float* __restrict__ mt,
+                  const float* __restrict__ gm, const float* __restrict__ lam,
+                  const float* __restrict__ gmt, float* __restrict__ lt, float* __restrict__ b) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const float l = -__ldg(mt + idx);
+  const float a = __ldg(lam + idx);
+  lt[idx] = l;
+  b[idx] = coef_b * (l * __ldg(gm + idx) + a * __ldg(gmt + idx));
+  b[N + idx] = coef_b * (l * __ldg(gm + N + idx) + a * __ldg(gmt + N + idx));
+}
+
+void launch_fn_adjoint_init(long long N, float coef_b, const float* mt, const float* gm,
+                            const float* lam, const float* gmt, float* lt, float* b,
+                            cudaStream_t st) {
+  launch_k(k_fn_adjoint_init, dim3((unsigned)((N + kPT - 1) / kPT)), dim3(kPT), 0, st, N, coef_b,
+           mt, gm, lam, gmt, lt, b);
+}
+
+// One backward step (Heun, reversed time): with lb = lam~_{j+1}(Y_D) and
+// sb = s_{j+1}(Y_D), s_j = div(lambda_j v~),
+//   f = lb div v(Y_D) + sb,  lam* = lb + h_t f,
+//   lam~_j = lb + h_t/2 (f + lam* div v + s_j),
+// then b~ += wb (lam~_j grad m_j + lambda_j grad m~_j) (gmt NULL: grad m~_0 = 0).
+// coef_l, coef_s: interpolation coefficients of lam~_{j+1} and s_{j+1}.
+template <bool P2>
+__global__ void __launch_bounds__(kPT)
+k_fn_adjoint_step(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ coef_l,
+                  const float* __restrict__ coef_s, const float* __restrict__ dY,
+                  const float* __restrict__ delta, const float* __restrict__ delta_bar,
+                  const float* __restrict__ src, const float* __restrict__ gm,
+                  const float* __restrict__ lam, const float* __restrict__ gmt,
+                  float* __restrict__ lt_out, float* __restrict__ b, int lagrange) {
+  pdl_enter();
+  const long long N = (long long)n1 * n2;
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  int i, j;
+  split_index<P2>(idx, n1, log1, i, j);
+  const Stencil S = make_stencil<P2>(i, j, __ldg(dY + idx), __ldg(dY + N + idx), n1, n2, log1,
+                                     lagrange);
+  const float lb = apply_stencil(S, coef_l);
+  const float sb = apply_stencil(S, coef_s);
+  const float f = fmaf(lb, __ldg(delta_bar + idx), sb);
+  const float lstar = fmaf(ht, f, lb);
+  const float l = lb + 0.5f * ht * (f + fmaf(lstar, __ldg(delta + idx), __ldg(src + idx)));
+  lt_out[idx] = l;
+  const float a = __ldg(lam + idx);
+  const float t1 = gmt ? a * __ldg(gmt + idx) : 0.f;
+  const float t2 = gmt ? a * __ldg(gmt + N + idx) : 0.f;
+  b[idx] = fmaf(wb, fmaf(l, __ldg(gm + idx), t1), b[idx]);
+  b[N + idx] = fmaf(wb, fmaf(l, __ldg(gm + N + idx), t2), b[N + idx]);
+}
+
+void launch_fn_adjoint_step(int n1, int n2, float ht, float wb, const float* coef_l,
+                            const float* coef_s, const float* dY, const float* delta,
+                            const float* delta_bar, const float* src, const float* gm,
+                            const float* lam, const float* gmt, float* lt_out, float* b,
+                            int lagrange, cudaStream_t st) {
+  const long long N = (long long)n1 * n2;
+  launch_k(pick(n1, n2, k_fn_adjoint_step<true>, k_fn_adjoint_step<false>),
+           dim3((unsigned)((N + kPT - 1) / kPT)), dim3(kPT), 0, st, n1, n2, ilog2i(n1), ht, wb,
+           coef_l, coef_s, dY, delta, delta_bar, src, gm, lam, gmt, lt_out, b, lagrange);
+}
+
+// ---------------------------------------------------------------------------
 // Fused steps: the spline prefilter of the field being transported and the
 // step that gathers it, in one kernel. A block owns a 32x32 tile of output
 // points. Every stencil of the tile lies in the W x W box of nodes that

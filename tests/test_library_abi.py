@@ -50,7 +50,7 @@ def test_default_options(lib):
     assert o.max_backtracks == 10 and abs(o.armijo_c1 - 1e-4) < 1e-20
     assert o.persistent_matvec == 0 and o.programmatic_launch == 1 and o.fused_transport == 1
     assert o.coarse_nt == 0 and o.coarse_interp == -1 and o.step_tile == -1
-    assert o.incompressible == 0
+    assert o.incompressible == 0 and o.hessian == regnk.REG_HESSIAN_GN
 
 
 def _create(lib, n1, n2, nt, beta, **kw):
@@ -74,6 +74,8 @@ def _create(lib, n1, n2, nt, beta, **kw):
     (64, 64, 4, 1e-2, {"step_tile": 10}),
     (64, 64, 4, 1e-2, {"step_tile": -2}),
     (64, 64, 4, 1e-2, {"incompressible": 2}),
+    (64, 64, 4, 1e-2, {"hessian": 2}),
+    (64, 64, 4, 1e-2, {"hessian": 1, "persistent_matvec": 1}),   # full Newton runs per step
 ])
 def test_invalid_arguments_rejected_on_host(lib, n1, n2, nt, beta, kw):
     s, h = _create(lib, n1, n2, nt, beta, **kw)
