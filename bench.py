@@ -204,33 +204,36 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle timed on the host (cpu_baseline and --impl reference)
 
-def oracle_matvec_sample(incompressible=False):
+def oracle_matvec_sample(incompressible=False, hessian="gn"):
     """Set up the 1024^2 workload in the FP64 oracle (untimed state solve at
     a smooth velocity) and return a callable doing one GN Hessian matvec."""
     from oracle.problem import Problem
     from paper_1604_02153_gb300 import inputs
     m_R, m_T = inputs.ellipse_phantoms(N_GRID, seed=100)
-    P = Problem(m_R, m_T, NT, BETAS[-1], incompressible=incompressible)
+    P = Problem(m_R, m_T, NT, BETAS[-1], incompressible=incompressible, hessian=hessian)
     P.state_solve(inputs.random_velocity(N_GRID, seed=7, vmax=0.2))
+    if hessian == "full":
+        P.adjoint_solve()          # the full-Newton matvec needs the adjoint history
     P.ensure_adjoint_characteristic()
     vt = inputs.random_velocity(N_GRID, seed=8, vmax=1.0)
     return lambda: P.hessian_matvec(vt)
 
 
-def cpu_baseline(incompressible=False):
-    f = oracle_matvec_sample(incompressible)
+def cpu_baseline(incompressible=False, hessian="gn"):
+    f = oracle_matvec_sample(incompressible, hessian)
     t0 = time.perf_counter()
     f()
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 GN Hessian matvec of the FP64 numpy oracle at {N_GRID}^2, nt={NT} "
+            "sample": f"1 {'full-Newton' if hessian == 'full' else 'GN'} Hessian matvec of the "
+                      f"FP64 numpy oracle at {N_GRID}^2, nt={NT} "
                       f"({dt:.1f} s, single-threaded numpy)"}
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    f = oracle_matvec_sample(args.incompressible)
+    f = oracle_matvec_sample(args.incompressible, args.hessian)
     for _ in range(args.warmup):
         f()
     t0 = time.perf_counter()
@@ -594,7 +597,7 @@ def main():
                 "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
                 "clocks": clocks.summary()}
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.incompressible)
+            line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian)
         if not args.no_warm_start:
             line["learned_warm_start"] = learned_warm_start(R, v, ok, dev)
         print(json.dumps(line), flush=True)
