@@ -204,7 +204,20 @@ reg_status reg_set_beta(reg_ctx* ctx, double beta);
  * interpolation. Needs no images. */
 reg_status reg_transport(reg_ctx* ctx, const float* v, const float* m0, float* m1);
 
-/* Departure points of one time step (§3.3.2 "Tracing the Characteristic",
+/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"): the state equation
+ * in antisymmetric form d_t m + 1/2 (grad m . v + div(m v) - m div v) = 0,
+ * solved from m0 to m1 = m(1) with nt Heun steps and pseudospectral
+ * derivatives (FFT-heavy Eulerian transport, 12 FFTs per step), and its
+ * adjoint -d_t lam - 1/2 (div(lam v) + grad lam . v + lam div v) = 0 from
+ * lam1 = lam(1) back to lam0 = lam(0), whose Heun step is the transpose of
+ * the state's. The scheme is stable only for small CFL numbers (the paper
+ * uses 0.2: nt >= max|v_i| / (0.2 h_i)). All fields n1*n2 floats (v: 2*n1*n2),
+ * device; needs no images; allocates 9*n1*n2 floats of workspace on first
+ * use. */
+reg_status reg_transport_rk2a(reg_ctx* ctx, const float* v, const float* m0, float* m1, int nt);
+reg_status reg_adjoint_rk2a(reg_ctx* ctx, const float* v, const float* lam1, float* lam0, int nt);
+
+/* Departure points of one time step/* Departure points of one time step (§3.3.2 "Tracing the Characteristic",
  * Heun): X_D = x - h_t/2 (v(x) + v(x - h_t v(x))) for the forward-in-time
  * equations and Y_D = x + h_t/2 (v(x) + v(x + h_t v(x))) for the backward
  * ones. Written as displacements in cell units, (X_D - x)/h, to dX and dY

@@ -96,6 +96,7 @@ struct reg_ctx {
   bool two_level = false;
   bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
   bool full_newton = false;      // full Hessian on the problem grid (P_2L's coarse stays GN)
+  float* rk2a = nullptr;         // RK2A comparator workspace (9 N), allocated on first use
   Level fine, coarse;
   std::vector<void*> allocs;
   std::vector<std::pair<int, float2*>> tw;   // twiddle tables by length
@@ -1673,6 +1674,49 @@ reg_status reg_transport(reg_ctx* c, const float* v, const float* m0, float* m1)
     check(c, cudaMemcpyAsync(F.mT, F.w2, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "restore m_T");
     F.have_v = F.have_gm = F.have_div = F.have_G = false;
   });
+}
+
+// RK2A comparator (Appendix "RK2A derivation"): nt Heun steps of the
+// antisymmetric-form state equation (sign -1) or of its adjoint backward in
+// time (sign +1), pseudospectral derivatives on the problem grid.
+static void rk2a_solve(reg_ctx* c, const float* v, const float* u0, float* u1, int nt, float sign) {
+  Level& F = c->fine;
+  const size_t N = (size_t)F.g.N;
+  if (!c->rk2a) c->rk2a = dalloc<float>(c, 9 * N);
+  float* delta = c->rk2a;
+  float* m = delta + N;
+  float* ms = m + N;
+  float* k1 = ms + N;
+  float* g = k1 + N;
+  float* prod = g + 2 * N;
+  float* dv = prod + 2 * N;
+  spectral(c, F, SPOP_DIV, 0.0, v, 2, 1, delta, 1, nullptr);
+  check(c, cudaMemcpyAsync(m, u0, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  const float ht = 1.0f / (float)nt;
+  auto stage = [&](const float* u, float a, const float* kprev, float b, float* out, float* kout) {
+    launch_lam_times_vt((long long)N, 1, u, v, prod, c->st);   // u v
+    spectral(c, F, SPOP_GRAD, 0.0, u, 1, 1, g, 2, nullptr);
+    spectral(c, F, SPOP_DIV, 0.0, prod, 2, 1, dv, 1, nullptr);
+    launch_rk2a_stage((long long)N, sign, u, g, v, dv, delta, m, a, kprev, b, out, kout, c->st);
+  };
+  for (int j = 0; j < nt; ++j) {
+    stage(m, ht, nullptr, 0.f, ms, k1);            // u* = u + h_t k1
+    stage(ms, 0.5f * ht, k1, 0.5f * ht, m, nullptr);   // u <- u + h_t/2 (k1 + k2)
+  }
+  check_launch(c, "RK2A solve");
+  check(c, cudaMemcpyAsync(u1, m, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+}
+
+reg_status reg_transport_rk2a(reg_ctx* c, const float* v, const float* m0, float* m1, int nt) {
+  if (!c || !v || !m0 || !m1 || nt < 1 || nt > (1 << 20)) return REG_EINVAL;
+  if (unaligned({v, m0, m1})) return reject_unaligned(c);
+  return guarded(c, [&] { rk2a_solve(c, v, m0, m1, nt, -1.f); });
+}
+
+reg_status reg_adjoint_rk2a(reg_ctx* c, const float* v, const float* lam1, float* lam0, int nt) {
+  if (!c || !v || !lam1 || !lam0 || nt < 1 || nt > (1 << 20)) return REG_EINVAL;
+  if (unaligned({v, lam1, lam0})) return reject_unaligned(c);
+  return guarded(c, [&] { rk2a_solve(c, v, lam1, lam0, nt, 1.f); });
 }
 
 reg_status reg_departure_points(reg_ctx* c, const float* v, float* dX, float* dY) {

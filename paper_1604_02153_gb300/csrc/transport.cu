@@ -486,6 +486,36 @@ void launch_fn_adjoint_step(int n1, int n2, float ht, float wb, const float* coe
 }
 
 // ---------------------------------------------------------------------------
+// RK2A comparator (antisymmetric form, Appendix "RK2A derivation"): one Heun
+// stage. With g = grad u, dv = div(u v) (spectral) and delta = div v,
+//   k = 1/2 (s (g . v + dv) + u delta),
+// s = -1 for the state equation, +1 for the adjoint in reversed time; then
+// out = base + a k (+ b kprev) and, if kout, kout = k. out may be base.
+__global__ void __launch_bounds__(kPT)
+k_rk2a_stage(long long N, float s, const float* __restrict__ u, const float* __restrict__ g,
+             const float* __restrict__ v, const float* __restrict__ dv,
+             const float* __restrict__ delta, const float* base, float a,
+             const float* __restrict__ kprev, float b, float* out, float* __restrict__ kout) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const float adv = fmaf(__ldg(g + idx), __ldg(v + idx), fmaf(__ldg(g + N + idx), __ldg(v + N + idx),
+                                                               __ldg(dv + idx)));
+  const float k = 0.5f * fmaf(s, adv, __ldg(u + idx) * __ldg(delta + idx));
+  if (kout) kout[idx] = k;
+  float o = fmaf(a, k, base[idx]);
+  if (kprev) o = fmaf(b, __ldg(kprev + idx), o);
+  out[idx] = o;
+}
+
+void launch_rk2a_stage(long long N, float s, const float* u, const float* g, const float* v,
+                       const float* dv, const float* delta, const float* base, float a,
+                       const float* kprev, float b, float* out, float* kout, cudaStream_t st) {
+  launch_k(k_rk2a_stage, dim3((unsigned)((N + kPT - 1) / kPT)), dim3(kPT), 0, st, N, s, u, g, v, dv,
+           delta, base, a, kprev, b, out, kout);
+}
+
+// ---------------------------------------------------------------------------
 // Fused steps: the spline prefilter of the field being transported and the
 // step that gathers it, in one kernel. A block owns a 32x32 tile of output
 // points. Every stencil of the tile lies in the W x W box of nodes that

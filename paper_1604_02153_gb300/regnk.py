@@ -77,6 +77,8 @@ _SIGNATURES = {
     "reg_set_beta": [_P, _D],
     "reg_transport": [_P, _P, _P, _P],
     "reg_departure_points": [_P, _P, _P, _P],
+    "reg_transport_rk2a": [_P, _P, _P, _P, _I],
+    "reg_adjoint_rk2a": [_P, _P, _P, _P, _I],
     "reg_interpolate": [_P, _P, _P, _P],
     "reg_spectral": [_P, _I, _D, _P, _P],
     "reg_restrict": [_P, _P, _P],
@@ -208,6 +210,14 @@ class Registration:
     def transport(self, v, m0, m1):
         self._call("reg_transport", _ptr(v, 2 * self.N, "v"), _ptr(m0, self.N, "m0"),
                    _ptr(m1, self.N, "m1"))
+
+    def transport_rk2a(self, v, m0, m1, nt):
+        self._call("reg_transport_rk2a", _ptr(v, 2 * self.N, "v"), _ptr(m0, self.N, "m0"),
+                   _ptr(m1, self.N, "m1"), int(nt))
+
+    def adjoint_rk2a(self, v, lam1, lam0, nt):
+        self._call("reg_adjoint_rk2a", _ptr(v, 2 * self.N, "v"), _ptr(lam1, self.N, "lam1"),
+                   _ptr(lam0, self.N, "lam0"), int(nt))
 
     def departure_points(self, v, dX=None, dY=None):
         self._call("reg_departure_points", _ptr(v, 2 * self.N, "v"),

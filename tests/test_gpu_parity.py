@@ -789,3 +789,32 @@ def test_full_newton_solve_64(regnk, pc):
     assert info["newton_iters"] == oinfo["newton_iters"]
     assert rel(host(v, (2, n, n)), vo) < 1e-3
     R.close()
+
+
+# ---------------------------------------------------------------------------
+# RK2A comparator (Appendix "RK2A derivation")
+
+@pytest.mark.parametrize("n1,n2", [(64, 64), (128, 64), (192, 96)])
+def test_rk2a_state_and_adjoint(regnk, n1, n2):
+    """reg_transport_rk2a / reg_adjoint_rk2a against the oracle at CFL 0.2
+    (FP32 roundoff over tens of steps: 1e-4), and the GPU's discrete
+    adjoint is the transpose of its state solve to FP32 roundoff."""
+    from oracle import rk2a
+    v = f32(inputs.random_velocity(n1, n2, seed=3, vmax=0.5))
+    m0 = f32(inputs.random_field(n1, n2, seed=1, kmax=8))
+    lam1 = f32(inputs.random_field(n1, n2, seed=2, kmax=8))
+    nt = rk2a.cfl_steps(v, 0.2)
+    R = regnk.Registration(n1, n2, 4, 1e-2, **pc_for(n1, n2))
+    N = n1 * n2
+    m1 = torch.empty(N, device="cuda")
+    R.transport_rk2a(dev(v), dev(m0), m1, nt)
+    assert rel(host(m1, (n2, n1)), rk2a.state_solve(m0, v, nt)) < 1e-4
+    lam0 = torch.empty(N, device="cuda")
+    R.adjoint_rk2a(dev(v), dev(lam1), lam0, nt)
+    assert rel(host(lam0, (n2, n1)), rk2a.adjoint_solve(lam1, v, nt)) < 1e-4
+    back = torch.empty(N, device="cuda")
+    R.adjoint_rk2a(dev(v), m1, back, nt)
+    a = float(torch.dot(m1.double(), m1.double()))
+    b = float(torch.dot(back.double(), dev(m0).double()))
+    assert abs(a - b) / a < 1e-5
+    R.close()
