@@ -82,6 +82,14 @@ def leray(b):
     return b - grad(ifft2_real(phih))
 
 
+def det_grad_map(u):
+    """det grad y for y = x + u (u periodic, (2, n2, n1)): (1 + d1 u1)(1 + d2 u2)
+    - d2 u1 d1 u2 with spectral derivatives (the determinant of the deformation
+    gradient of §2 and the bound of §4's beta selection)."""
+    g1, g2 = grad(u[0]), grad(u[1])
+    return (1.0 + g1[0]) * (1.0 + g2[1]) - g1[1] * g2[0]
+
+
 def reg_symbol(n1, n2, reg_norm):
     """Spectral weights gamma(k) = |k|^(2p) of the regularisation operator A.
 

@@ -115,3 +115,21 @@ def trapezoid_weights(nt):
     w[0] = 0.5
     w[-1] = 0.5
     return w
+
+
+def deformation_map(v, nt, kind):
+    """Displacement u = y - x (physical units, (2, n2, n1)) of the
+    deformation map y with m_1 = m_T o y (§2): y(x) is where the
+    characteristic through x at t = 1 was at t = 0, the composition of the
+    nt departure maps X_D. With u_0 = 0, each step interpolates the previous
+    displacement at the departure points and adds the step's own:
+        u_j = u_{j-1}(X_D) + (X_D - x),
+    so that interpolating m_T at x + u is the SL state solve's m_1 up to the
+    interpolation error of composing instead of chaining."""
+    n2, n1 = v.shape[1:]
+    h = (2.0 * np.pi / n1, 2.0 * np.pi / n2)
+    dX = characteristic(v, nt, kind, backward=False)
+    u = np.zeros((2, n2, n1))
+    for _ in range(nt):
+        u = np.stack([at_departure(u[c], dX, kind) + h[c] * dX[c] for c in range(2)])
+    return u
