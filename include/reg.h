@@ -204,7 +204,17 @@ reg_status reg_set_beta(reg_ctx* ctx, double beta);
  * interpolation. Needs no images. */
 reg_status reg_transport(reg_ctx* ctx, const float* v, const float* m0, float* m1);
 
-/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"): the state equation
+/* Deformation map of the velocity v (§2: m_1 = m_T o y, computed from v in
+ * a post-processing step): u = y - x (2*n1*n2 floats, physical units,
+ * component 1 then 2), the composition of the nt semi-Lagrangian departure
+ * maps of the context (u_j = u_{j-1}(X_D) + X_D - x, interpolation model of
+ * the context), and, if det is not NULL, det grad y = (1 + d1 u1)(1 + d2 u2)
+ * - d2 u1 d1 u2 with spectral derivatives (n1*n2 floats; the quantity that
+ * §4 bounds when choosing beta, 1 for divergence-free v). Device buffers;
+ * needs no images; allocates 10*n1*n2 floats of workspace on first use. */
+reg_status reg_deformation_map(reg_ctx* ctx, const float* v, float* u, float* det);
+
+/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"):/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"): the state equation
  * in antisymmetric form d_t m + 1/2 (grad m . v + div(m v) - m div v) = 0,
  * solved from m0 to m1 = m(1) with nt Heun steps and pseudospectral
  * derivatives (FFT-heavy Eulerian transport, 12 FFTs per step), and its

@@ -144,6 +144,8 @@ void launch_fn_adjoint_step(int n1, int n2, float ht, float wb, const float* coe
 void launch_rk2a_stage(long long N, float s, const float* u, const float* g, const float* v,
                        const float* dv, const float* delta, const float* base, float a,
                        const float* kprev, float b, float* out, float* kout, cudaStream_t st);
+// det grad y from the four spectral derivatives of u = y - x (transport.cu).
+void launch_det_grad(long long N, const float* g, float* det, cudaStream_t st);
 // Fused prefilter + step kernels (transport.cu). fused_box_width gives the
 // box width (48 or 64) whose halo covers displacements up to max_disp_cells,
 // or 0 if none does; fused_init raises the kernels' shared-memory limit

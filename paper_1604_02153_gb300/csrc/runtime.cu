@@ -97,6 +97,7 @@ struct reg_ctx {
   bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
   bool full_newton = false;      // full Hessian on the problem grid (P_2L's coarse stays GN)
   float* rk2a = nullptr;         // RK2A comparator workspace (9 N), allocated on first use
+  float* defmap = nullptr;       // deformation map workspace (10 N), allocated on first use
   Level fine, coarse;
   std::vector<void*> allocs;
   std::vector<std::pair<int, float2*>> tw;   // twiddle tables by length
@@ -1705,6 +1706,45 @@ static void rk2a_solve(reg_ctx* c, const float* v, const float* u0, float* u1, i
   }
   check_launch(c, "RK2A solve");
   check(c, cudaMemcpyAsync(u1, m, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+}
+
+// Deformation map (§2: m_1 = m_T o y): u = y - x as the composition of the
+// nt departure maps X_D of v, u_j = u_{j-1}(X_D) + (X_D - x) from u_0 = 0,
+// and optionally det grad y (spectral derivatives of u).
+static void deformation_map(reg_ctx* c, const float* v, float* u, float* det) {
+  Level& F = c->fine;
+  const GridDims& g = F.g;
+  const size_t N = (size_t)g.N;
+  if (!c->defmap) c->defmap = dalloc<float>(c, 10 * N);
+  float* dX = c->defmap;
+  float* ua = dX + 2 * N;
+  float* ub = ua + 2 * N;
+  float* gr = ub + 2 * N;
+  const float h1 = (float)F.h1, h2 = (float)F.h2;
+  const float* cv = coefficients(c, F, v, 2, F.c2);
+  launch_departure(g.n1, g.n2, F.ht, v, cv, dX, nullptr, F.lagrange, c->st);
+  launch_lincomb((long long)N, h1, dX, 0.f, nullptr, ua, c->st);
+  launch_lincomb((long long)N, h2, dX + N, 0.f, nullptr, ua + N, c->st);
+  for (int j = 2; j <= F.nt; ++j) {
+    const float* cu = coefficients(c, F, ua, 2, F.c2);
+    launch_gather(g.n1, g.n2, cu, dX, ub, 2, (long long)N, F.lagrange, c->st);
+    launch_lincomb((long long)N, 1.f, ub, h1, dX, ub, c->st);
+    launch_lincomb((long long)N, 1.f, ub + N, h2, dX + N, ub + N, c->st);
+    std::swap(ua, ub);
+  }
+  check_launch(c, "deformation map");
+  check(c, cudaMemcpyAsync(u, ua, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  if (det) {
+    spectral(c, F, SPOP_GRAD, 0.0, ua, 1, 2, gr, 2, nullptr);
+    launch_det_grad((long long)N, gr, det, c->st);
+    check_launch(c, "det grad y");
+  }
+}
+
+reg_status reg_deformation_map(reg_ctx* c, const float* v, float* u, float* det) {
+  if (!c || !v || !u) return REG_EINVAL;
+  if (unaligned({v, u, det})) return reject_unaligned(c);
+  return guarded(c, [&] { deformation_map(c, v, u, det); });
 }
 
 reg_status reg_transport_rk2a(reg_ctx* c, const float* v, const float* m0, float* m1, int nt) {

@@ -515,6 +515,22 @@ void launch_rk2a_stage(long long N, float s, const float* u, const float* g, con
            delta, base, a, kprev, b, out, kout);
 }
 
+// det grad y for y = x + u from the spectral derivatives g = [d1 u1, d2 u1,
+// d1 u2, d2 u2] (4 fields): (1 + d1 u1)(1 + d2 u2) - d2 u1 d1 u2.
+__global__ void __launch_bounds__(kPT)
+k_det_grad(long long N, const float* __restrict__ g, float* __restrict__ det) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= N) return;
+  const float a = 1.f + __ldg(g + idx), b = __ldg(g + N + idx);
+  const float c = __ldg(g + 2 * N + idx), d = 1.f + __ldg(g + 3 * N + idx);
+  det[idx] = fmaf(a, d, -b * c);
+}
+
+void launch_det_grad(long long N, const float* g, float* det, cudaStream_t st) {
+  launch_k(k_det_grad, dim3((unsigned)((N + kPT - 1) / kPT)), dim3(kPT), 0, st, N, g, det);
+}
+
 // ---------------------------------------------------------------------------
 // Fused steps: the spline prefilter of the field being transported and the
 // step that gathers it, in one kernel. A block owns a 32x32 tile of output

@@ -78,6 +78,7 @@ _SIGNATURES = {
     "reg_transport": [_P, _P, _P, _P],
     "reg_departure_points": [_P, _P, _P, _P],
     "reg_transport_rk2a": [_P, _P, _P, _P, _I],
+    "reg_deformation_map": [_P, _P, _P, _P],
     "reg_adjoint_rk2a": [_P, _P, _P, _P, _I],
     "reg_interpolate": [_P, _P, _P, _P],
     "reg_spectral": [_P, _I, _D, _P, _P],
@@ -210,6 +211,10 @@ class Registration:
     def transport(self, v, m0, m1):
         self._call("reg_transport", _ptr(v, 2 * self.N, "v"), _ptr(m0, self.N, "m0"),
                    _ptr(m1, self.N, "m1"))
+
+    def deformation_map(self, v, u, det=None):
+        self._call("reg_deformation_map", _ptr(v, 2 * self.N, "v"), _ptr(u, 2 * self.N, "u"),
+                   _ptr(det, self.N, "det"))
 
     def transport_rk2a(self, v, m0, m1, nt):
         self._call("reg_transport_rk2a", _ptr(v, 2 * self.N, "v"), _ptr(m0, self.N, "m0"),

@@ -818,3 +818,33 @@ def test_rk2a_state_and_adjoint(regnk, n1, n2):
     b = float(torch.dot(back.double(), dev(m0).double()))
     assert abs(a - b) / a < 1e-5
     R.close()
+
+
+# ---------------------------------------------------------------------------
+# deformation map y (m_1 = m_T o y) and det grad y
+
+@pytest.mark.parametrize("n1,n2,kind", [(64, 64, "spline"), (128, 64, "spline"), (64, 64, "lagrange"),
+                                        (192, 96, "spline")])
+def test_deformation_map_and_determinant(regnk, n1, n2, kind):
+    """reg_deformation_map against the oracle's composition of departure
+    maps (1e-4 relative) and det grad y (1e-4 absolute), and the shear-flow
+    closed form y = (x1 - a sin x2, x2), det = 1."""
+    nt = 8
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration(n1, n2, nt, 1e-2, interp=interp, **pc_for(n1, n2))
+    v = f32(inputs.random_velocity(n1, n2, seed=3, vmax=0.4))
+    N = n1 * n2
+    u = torch.empty(2 * N, device="cuda")
+    det = torch.empty(N, device="cuda")
+    R.deformation_map(dev(v), u, det)
+    u_ref = transport.deformation_map(v, nt, kind)
+    assert rel(host(u, (2, n2, n1)), u_ref) < 1e-4
+    assert np.max(np.abs(host(det, (n2, n1)) - spectral.det_grad_map(u_ref))) < 1e-4
+    X1, X2 = inputs.grid_coordinates(n1, n2)
+    a = 0.4
+    vs = np.stack([a * np.sin(X2), np.zeros_like(X2)])
+    R.deformation_map(dev(vs), u, det)
+    us = host(u, (2, n2, n1))
+    assert np.max(np.abs(us[0] + a * np.sin(X2))) < 1e-5 and np.max(np.abs(us[1])) < 1e-6
+    assert np.max(np.abs(host(det, (n2, n1)) - 1.0)) < 1e-5
+    R.close()

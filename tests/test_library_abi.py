@@ -89,6 +89,7 @@ def test_null_handles(lib):
     assert lib.reg_last_error(None) == b"null context"
     assert lib.reg_step_tiles(None, (ctypes.c_int * 4)()) == regnk.REG_EINVAL
     assert lib.reg_transport_rk2a(None, None, None, None, 4) == regnk.REG_EINVAL
+    assert lib.reg_deformation_map(None, None, None, None) == regnk.REG_EINVAL
     assert lib.reg_adjoint_rk2a(None, None, None, None, 4) == regnk.REG_EINVAL
 
 
