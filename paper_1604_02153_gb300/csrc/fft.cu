@@ -73,7 +73,7 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
   constexpr int B4 = (TOT4 + NT - 1) / NT;
   const int t = threadIdx.x;
   int lns = 0;  // log2 of the current sub-transform size Ns
-#pragma unroll 1
+#pragma unroll   // constant twiddle strides per pass
   for (int pass = 0; pass < L / 2; ++pass) {
     const int Ns = 1 << lns;
     const int tws = N >> (lns + 2);  // twiddle stride N / (4 Ns)
