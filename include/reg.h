@@ -324,8 +324,8 @@ reg_status reg_batch_set_images(reg_batch* batch, const float* const* m_R,
                                 const float* const* m_T);
 /* Changes beta of every problem (beta: host array of B values). */
 reg_status reg_batch_set_beta(reg_batch* batch, const double* beta);
-/* reg_solve on every problem with up to `threads` host threads (<= 0: up to
- * 32). v[i] is the initial guess and receives the result. infos (host, B
+/* reg_solve on every problem with up to `threads` host threads (<= 0: half
+ * the host's hardware threads). v[i] is the initial guess and receives the result. infos (host, B
  * entries) may be NULL. Returns REG_OK if every problem converged, else the
  * first hard error, or REG_ENOTCONV / REG_ELINESEARCH if those were the only
  * failures (see infos[i].status). */

@@ -100,7 +100,16 @@ reg_status reg_batch_solve(reg_batch* b, float* const* v, double gtol, int threa
                            reg_info* infos) {
   if (!b || !v || !(gtol > 0.0)) return REG_EINVAL;
   const int B = (int)b->ctx.size();
-  const int T = threads <= 0 ? (B < 32 ? B : 32) : (threads < B ? threads : B);
+  // default: half the host's hardware threads (at least 1, at most B). Each
+  // worker alternates between launching and waiting for its problem's
+  // scalars; on a 16-core host 8 workers measured fastest (59-60 ms per
+  // batch of 64, against 64-70 ms with 32 and 68 ms with 4)
+  int T = threads;
+  if (T <= 0) {
+    const int hc = (int)std::thread::hardware_concurrency();
+    T = hc > 1 ? hc / 2 : 1;
+  }
+  if (T > B) T = B;
   std::vector<reg_info> info(B);
   std::vector<reg_status> st(B, REG_OK);
   std::atomic<int> next{0};
