@@ -33,6 +33,9 @@ step_tiles = (threads per block, points per thread) of the unfused
             reg_create's timing of the nine shapes chose them.
 cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
             timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
+plain_form = the same solve with FP32 reductions, no CUDA graphs and plain
+            launches (one solve after one warm-up, CUDA events): the "plain
+            FP32" form the chosen one is compared against.
 learned_warm_start = the trained warm-start network (weights committed with
             the package) measured outside the timed region: cold versus warm
             time to ||g||rel 1e-2 on held-out pairs of the learned-warm-start
@@ -92,6 +95,8 @@ def parse():
                     help="Gauss-Newton (the workload's) or full-Newton Hessian matvec")
     ap.add_argument("--incompressible", action="store_true",
                     help="the incompressible problem (div v = 0, K the Leray projection)")
+    ap.add_argument("--no-plain-form", action="store_true",
+                    help="skip the plain-form solve (FP32 reductions, no graphs)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
@@ -552,6 +557,37 @@ def main():
         e2e_mv += s2["matvecs"]
     value, e2e_value = aggregate_ranks(dist, dev, total_ms, stats["matvecs"], e2e_ms, e2e_mv)
 
+    # ---- the plain form of the same solve: FP32 reductions, no CUDA graphs,
+    # plain launches (cold start, as above); one warm-up and one timed solve
+    plain = None
+    if not args.no_plain_form and rank == 0:
+        Rp = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
+                                incompressible=int(args.incompressible),
+                                hessian={"gn": regnk.REG_HESSIAN_GN,
+                                         "full": regnk.REG_HESSIAN_FULL}[args.hessian],
+                                coarse_nt=args.coarse_nt,
+                                coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
+                                               "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
+                                precision=regnk.REG_PRECISION_FP32, use_graphs=0,
+                                programmatic_launch=0, **pc_opts)
+        Rp.set_images(d_mR, d_mT)
+        R, Rmain = Rp, R
+        step(new_stats())
+        sp = new_stats()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        step(sp)
+        e1.record(st)
+        torch.cuda.synchronize()
+        R = Rmain
+        Rp.close()
+        plain = {"options": "FP32 reductions, no CUDA graphs, plain launches, cold start",
+                 "time_to_solution_s": e0.elapsed_time(e1) / 1e3,
+                 "matvecs_per_solve": sp["matvecs"], "newton_iters_per_solve": sp["newton"],
+                 "solve_status": sorted(set(sp["status"])), "final_gnorm_rel": sp["gnorm_rel"]}
+
     # ---- roofline of the dominant kernel class (per grid level)
     dom = max(prof, key=lambda k: prof[k][0])
     ms, nl, by = prof[dom]
@@ -595,6 +631,7 @@ def main():
                 "gpu_launches": int(launches),
                 "roofline": roof,
                 "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
+                "plain_form": plain,
                 "clocks": clocks.summary()}
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian)

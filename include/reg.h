@@ -70,6 +70,8 @@ enum { REG_PC_REG = 0, REG_PC_2L = 1 };
 enum { REG_PCSOLVER_CHEB = 0, REG_PCSOLVER_PCG = 1 };
 /* reg_options.hessian */
 enum { REG_HESSIAN_GN = 0, REG_HESSIAN_FULL = 1 };
+/* reg_options.precision */
+enum { REG_PRECISION_FP64 = 0, REG_PRECISION_FP32 = 1 };
 
 typedef struct { int n1, n2; } reg_grid;
 
@@ -156,6 +158,19 @@ typedef struct {
                               The full Hessian may be indefinite: PCG stops at
                               negative curvature (REG_ENEGCURV in kkt_solve).
                               Needs persistent_matvec = 0                     */
+  int precision;           /* accumulation of inner products, squared norms and
+                              the objective: REG_PRECISION_FP64 (default):
+                              error-free FP32 products and sums per thread,
+                              FP64 across threads (FP64 accuracy, bitwise
+                              reproducible); REG_PRECISION_FP32: plain FP32 at
+                              every level (the "plain FP32" comparison form;
+                              the Armijo test and the Krylov scalars then carry
+                              FP32 rounding). Fields are FP32 either way       */
+  int use_graphs;          /* 1 (default): fixed launch sequences (the fine
+                              matvec inside PCG, P_2L with CHEB) are replayed
+                              as CUDA graphs after their first two calls;
+                              0: every launch is issued from the host. Results
+                              are identical                                    */
 } reg_options;
 
 typedef struct {

@@ -32,6 +32,9 @@ __device__ __forceinline__ void pdl_enter() {
 // Attribute value for launches from this host thread (reg_options
 // .programmatic_launch of the context being driven; 1 outside a context).
 extern thread_local int t_programmatic_launch;
+// 1 while a context with reg_options.precision = REG_PRECISION_FP32 runs a
+// call: inner products and squared norms accumulate in plain FP32
+extern thread_local int t_plain_fp32_reduce;
 
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,

@@ -104,6 +104,33 @@ k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// The same sums accumulated in plain FP32 at every level (the "plain FP32"
+// form the FP64-accurate reductions are compared against): per-thread sums,
+// block sums and the final sum in FP32; the result is stored as a double.
+template <int MODE>
+__global__ void __launch_bounds__(kRT)
+k_partial_fp32(const float* __restrict__ a, const float* __restrict__ b, long long n,
+               double* __restrict__ partial) {
+  pdl_enter();
+  float acc = 0.f;
+  const long long stride = (long long)gridDim.x * kRT;
+  for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
+    const float x = __ldg(a + i), y = __ldg(b + i);
+    acc = MODE == 0 ? fmaf(x, y, acc) : fmaf(x - y, x - y, acc);
+  }
+  const float s = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = (double)s;
+}
+
+__global__ void __launch_bounds__(kRT)
+k_final_sum_fp32(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  pdl_enter();
+  float acc = 0.f;
+  for (int i = threadIdx.x; i < nb; i += kRT) acc += (float)partial[i];
+  const float s = block_sum(acc);
+  if (threadIdx.x == 0) *out = (double)s;
+}
+
 __global__ void __launch_bounds__(kRT)
 k_final_sum(const double* __restrict__ partial, int nb, double* __restrict__ out) {
   pdl_enter();
@@ -117,18 +144,27 @@ static int aligned16(const void* a, const void* b) {
   return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15u) == 0;
 }
 
+template <int MODE>
+static void launch_sum(const float* a, const float* b, long long n, double* partial, double* out,
+                       cudaStream_t st) {
+  const int nb = nblocks(n);
+  if (t_plain_fp32_reduce) {
+    launch_k(k_partial_fp32<MODE>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial);
+    launch_k(k_final_sum_fp32, dim3(1), dim3(kRT), 0, st, partial, nb, out);
+    return;
+  }
+  launch_k(k_partial<MODE>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial, aligned16(a, b));
+  launch_k(k_final_sum, dim3(1), dim3(kRT), 0, st, partial, nb, out);
+}
+
 void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
                 cudaStream_t st) {
-  const int nb = nblocks(n);
-  launch_k(k_partial<0>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial, aligned16(a, b));
-  launch_k(k_final_sum, dim3(1), dim3(kRT), 0, st, partial, nb, out);
+  launch_sum<0>(a, b, n, partial, out, st);
 }
 
 void launch_sumsq_diff(const float* a, const float* b, long long n, double* partial,
                        double* out, cudaStream_t st) {
-  const int nb = nblocks(n);
-  launch_k(k_partial<1>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial, aligned16(a, b));
-  launch_k(k_final_sum, dim3(1), dim3(kRT), 0, st, partial, nb, out);
+  launch_sum<1>(a, b, n, partial, out, st);
 }
 
 __global__ void __launch_bounds__(kRT)

@@ -25,6 +25,7 @@ using namespace regnk;
 namespace regnk {
 std::atomic<long long> g_launch_count{0};
 thread_local int t_programmatic_launch = 1;
+thread_local int t_plain_fp32_reduce = 0;
 }
 
 namespace {
@@ -325,6 +326,13 @@ struct LaunchModeScope {
   int saved;
   explicit LaunchModeScope(int mode) : saved(t_programmatic_launch) { t_programmatic_launch = mode; }
   ~LaunchModeScope() { t_programmatic_launch = saved; }
+};
+
+// Reduction precision of this context for the duration of one call.
+struct ReducePrecisionScope {
+  int saved;
+  explicit ReducePrecisionScope(int plain) : saved(t_plain_fp32_reduce) { t_plain_fp32_reduce = plain; }
+  ~ReducePrecisionScope() { t_plain_fp32_reduce = saved; }
 };
 
 // Tile shapes of the step kernels (k_adjoint_step, k_incstate_step) for a
@@ -1448,6 +1456,7 @@ reg_status reject_unaligned(reg_ctx* c) {
 reg_status guarded(reg_ctx* c, const std::function<void()>& body) {
   if (!c) return REG_EINVAL;
   LaunchModeScope mode(c->opt.programmatic_launch ? 1 : 0);
+  ReducePrecisionScope prec(c->opt.precision == REG_PRECISION_FP32 ? 1 : 0);
   try {
     body();
     const cudaError_t e = cudaGetLastError();
@@ -1492,6 +1501,8 @@ reg_status reg_default_options(reg_options* o) {
   o->step_tile = -1;
   o->incompressible = 0;
   o->hessian = 0;
+  o->precision = REG_PRECISION_FP64;
+  o->use_graphs = 1;
   return REG_OK;
 }
 
@@ -1512,7 +1523,9 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       o.coarse_nt < 0 || o.coarse_nt > 4096 || o.coarse_interp < -1 || o.coarse_interp > 1 ||
       o.step_tile < -1 || o.step_tile > kStepTiles ||
       (o.incompressible != 0 && o.incompressible != 1) || (o.hessian != 0 && o.hessian != 1) ||
-      (o.hessian == 1 && o.persistent_matvec != 0))
+      (o.hessian == 1 && o.persistent_matvec != 0) ||
+      (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
+      (o.use_graphs != 0 && o.use_graphs != 1))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1527,6 +1540,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->two_level = (o.precond == REG_PC_2L);
   c->incompressible = (o.incompressible != 0);
   c->full_newton = (o.hessian == REG_HESSIAN_FULL);
+  c->graphs = (o.use_graphs != 0);
   c->fine.lagrange = (o.interp == REG_INTERP_LAGRANGE);
   c->coarse.lagrange = o.coarse_interp < 0 ? c->fine.lagrange : (o.coarse_interp == REG_INTERP_LAGRANGE);
   c->persistent = (o.persistent_matvec != 0);

@@ -848,3 +848,53 @@ def test_deformation_map_and_determinant(regnk, n1, n2, kind):
     assert np.max(np.abs(us[0] + a * np.sin(X2))) < 1e-5 and np.max(np.abs(us[1])) < 1e-6
     assert np.max(np.abs(host(det, (n2, n1)) - 1.0)) < 1e-5
     R.close()
+
+
+# ---------------------------------------------------------------------------
+# the plain form: FP32 reductions, no CUDA graphs
+
+def test_graphs_off_gives_identical_solve(regnk):
+    """use_graphs = 0 issues every launch from the host; the kernels and
+    their order are the same, so the solve is bitwise that of the graphed
+    one (P_2L with CHEB, whose preconditioner and matvec are replayed)."""
+    n, nt, beta = 64, 4, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = f32(Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar))
+    out = []
+    for g in (1, 0):
+        R = regnk.Registration(n, n, nt, beta, use_graphs=g)
+        R.set_images(dev(m_R), dev(f32(m_T)))
+        v = torch.zeros(2 * n * n, device="cuda")
+        info = R.solve(v, 1e-3)
+        out.append((v.cpu(), info["newton_iters"], info["matvecs"]))
+        R.close()
+    assert torch.equal(out[0][0], out[1][0]) and out[0][1:] == out[1][1:]
+
+
+def test_fp32_reductions(regnk):
+    """precision = FP32: the inner product accumulates in FP32 (relative
+    error ~1e-6 on 2 M terms, not the FP64-accurate value), and the 64^2
+    solve still reaches its tolerance."""
+    n = 1024
+    R64 = regnk.Registration(n, n, 4, 1e-2)
+    R32 = regnk.Registration(n, n, 4, 1e-2, precision=regnk.REG_PRECISION_FP32)
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(2 * n * n).astype(np.float32)
+    b = rng.standard_normal(2 * n * n).astype(np.float32)
+    exact = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+    d64 = R64.dot(dev(a), dev(b))
+    d32 = R32.dot(dev(a), dev(b))
+    scale = float(np.dot(np.abs(a).astype(np.float64), np.abs(b).astype(np.float64)))
+    assert abs(d64 - exact) <= 1e-13 * scale
+    assert abs(d32 - exact) <= 1e-5 * scale and d32 != d64
+    R64.close()
+    R32.close()
+    n, nt, beta = 64, 4, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = f32(Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar))
+    R = regnk.Registration(n, n, nt, beta, precision=regnk.REG_PRECISION_FP32, use_graphs=0)
+    R.set_images(dev(m_R), dev(f32(m_T)))
+    v = torch.zeros(2 * n * n, device="cuda")
+    info = R.solve(v, 1e-2)
+    assert info["gnorm_rel"] <= 1e-2
+    R.close()

@@ -51,6 +51,7 @@ def test_default_options(lib):
     assert o.persistent_matvec == 0 and o.programmatic_launch == 1 and o.fused_transport == 1
     assert o.coarse_nt == 0 and o.coarse_interp == -1 and o.step_tile == -1
     assert o.incompressible == 0 and o.hessian == regnk.REG_HESSIAN_GN
+    assert o.precision == regnk.REG_PRECISION_FP64 and o.use_graphs == 1
 
 
 def _create(lib, n1, n2, nt, beta, **kw):
@@ -76,6 +77,8 @@ def _create(lib, n1, n2, nt, beta, **kw):
     (64, 64, 4, 1e-2, {"incompressible": 2}),
     (64, 64, 4, 1e-2, {"hessian": 2}),
     (64, 64, 4, 1e-2, {"hessian": 1, "persistent_matvec": 1}),   # full Newton runs per step
+    (64, 64, 4, 1e-2, {"precision": 2}),
+    (64, 64, 4, 1e-2, {"use_graphs": 2}),
 ])
 def test_invalid_arguments_rejected_on_host(lib, n1, n2, nt, beta, kw):
     s, h = _create(lib, n1, n2, nt, beta, **kw)
