@@ -59,22 +59,96 @@ struct RowCfg {
   static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
 };
 
+// 8-point DFT in registers: two 4-point DFTs of the even and odd inputs,
+// the odd ones turned by W8^s, then the radix-2 combination (forward
+// W = exp(-2 pi i / 8), inverse its conjugate).
+template <bool INV>
+__device__ __forceinline__ void dft4(float2 a0, float2 a1, float2 a2, float2 a3, float2& y0,
+                                     float2& y1, float2& y2, float2& y3) {
+  const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const float2 s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
+  y0 = cadd(s02, s13);
+  y1 = cadd(d02, d13);
+  y2 = csub(s02, s13);
+  y3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(const float2 (&a)[8], float2 (&y)[8]) {
+  constexpr float kR2 = 0.70710678118654752f;   // sqrt(2) / 2
+  float2 e0, e1, e2, e3, o0, o1, o2, o3;
+  dft4<INV>(a[0], a[2], a[4], a[6], e0, e1, e2, e3);
+  dft4<INV>(a[1], a[3], a[5], a[7], o0, o1, o2, o3);
+  // o_s *= W8^s
+  o1 = INV ? make_float2(kR2 * (o1.x - o1.y), kR2 * (o1.x + o1.y))
+           : make_float2(kR2 * (o1.x + o1.y), kR2 * (o1.y - o1.x));
+  o2 = mul_mi<INV>(o2);
+  o3 = INV ? make_float2(-kR2 * (o3.x + o3.y), kR2 * (o3.x - o3.y))
+           : make_float2(kR2 * (o3.y - o3.x), -kR2 * (o3.x + o3.y));
+  y[0] = cadd(e0, o0); y[4] = csub(e0, o0);
+  y[1] = cadd(e1, o1); y[5] = csub(e1, o1);
+  y[2] = cadd(e2, o2); y[6] = csub(e2, o2);
+  y[3] = cadd(e3, o3); y[7] = csub(e3, o3);
+}
+
 // In-place FFT of P lines of length N = 2^L 3^T stored contiguously at s
-// (line l at s + l*N): radix-4 Stockham passes, then a radix-2 pass if L is
-// odd, then a radix-3 pass if T = 1, each pass reading its inputs into
-// registers, synchronising and writing its outputs. All NT threads of the
-// block take part; the caller synchronises before (data written) and the
-// routine ends with a barrier. tw holds exp(-2 pi i m / N), m < N.
+// (line l at s + l*N): radix-8 Stockham passes, then one radix-4 or radix-2
+// pass for the remaining factor of 2^L, then a radix-3 pass if T = 1, each
+// pass reading its inputs into registers, synchronising and writing its
+// outputs. All NT threads of the block take part; the caller synchronises
+// before (data written) and the routine ends with a barrier. tw holds
+// exp(-2 pi i m / N), m < N.
 template <int L, int T, int P, int NT, bool INV>
 __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
   constexpr int N = (1 << L) * (T ? 3 : 1);
-  constexpr int Q4 = N / 4;
-  constexpr int TOT4 = P * Q4;
-  constexpr int B4 = (TOT4 + NT - 1) / NT;
   const int t = threadIdx.x;
   int lns = 0;  // log2 of the current sub-transform size Ns
+  constexpr int Q8 = N / 8;
+  constexpr int TOT8 = P * Q8;
+  constexpr int B8 = (TOT8 + NT - 1) / NT;
 #pragma unroll   // constant twiddle strides per pass
-  for (int pass = 0; pass < L / 2; ++pass) {
+  for (int pass = 0; pass < L / 3; ++pass) {
+    const int Ns = 1 << lns;
+    const int tws = N >> (lns + 3);  // twiddle stride N / (8 Ns)
+    float2 v[B8][8];
+    int base[B8];
+#pragma unroll
+    for (int b = 0; b < B8; ++b) {
+      const int q = t + b * NT;
+      if (TOT8 % NT == 0 || q < TOT8) {
+        const int l = q / Q8, j = q % Q8;
+        const int k = j & (Ns - 1);
+        const float2* x = s + l * N;
+        float2 a[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) a[r] = x[j + r * Q8];
+        if (lns > 0) {
+#pragma unroll
+          for (int r = 1; r < 8; ++r) {
+            const float2 w = __ldg(tw + r * k * tws);
+            a[r] = INV ? cmulc(a[r], w) : cmul(a[r], w);
+          }
+        }
+        dft8<INV>(a, v[b]);
+        base[b] = l * N + (j - k) * 8 + k;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B8; ++b) {
+      const int q = t + b * NT;
+      if (TOT8 % NT == 0 || q < TOT8) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) s[base[b] + r * Ns] = v[b][r];
+      }
+    }
+    __syncthreads();
+    lns += 3;
+  }
+  if (L % 3 == 2) {
+    constexpr int Q4 = N / 4;
+    constexpr int TOT4 = P * Q4;
+    constexpr int B4 = (TOT4 + NT - 1) / NT;
     const int Ns = 1 << lns;
     const int tws = N >> (lns + 2);  // twiddle stride N / (4 Ns)
     float2 v[B4][4];
@@ -97,12 +171,7 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
             a1 = cmul(a1, w1); a2 = cmul(a2, w2); a3 = cmul(a3, w3);
           }
         }
-        const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-        const float2 s13 = cadd(a1, a3), d13 = mul_mi<INV>(csub(a1, a3));
-        v[b][0] = cadd(s02, s13);
-        v[b][1] = cadd(d02, d13);
-        v[b][2] = csub(s02, s13);
-        v[b][3] = csub(d02, d13);
+        dft4<INV>(a0, a1, a2, a3, v[b][0], v[b][1], v[b][2], v[b][3]);
         base[b] = l * N + (j - k) * 4 + k;
       }
     }
@@ -120,7 +189,7 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
     __syncthreads();
     lns += 2;
   }
-  if (L & 1) {
+  if (L % 3 == 1) {
     constexpr int Q2 = N / 2;
     constexpr int TOT2 = P * Q2;
     constexpr int B2 = (TOT2 + NT - 1) / NT;
