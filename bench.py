@@ -361,6 +361,27 @@ def run_batch(args):
     torch.cuda.synchronize()
     t_serial = (time.perf_counter() - t0) / args.steps
     batch.close()
+    # the plain FP32 method on the same problems: one by one, FP32 reductions,
+    # no CUDA graphs, plain launches (one warm-up pass, then timed)
+    plain = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
+                        coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
+                                       "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
+                        precision=regnk.REG_PRECISION_FP32, use_graphs=0, programmatic_launch=0)
+    plain.set_images(mR, mT)
+    for v in vs:
+        v.zero_()
+    plain.solve(vs, GTOL, threads=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mv_p = 0
+    for _ in range(args.steps):
+        for v in vs:
+            v.zero_()
+        infos_p = plain.solve(vs, GTOL, threads=1)
+        mv_p += sum(i["matvecs"] for i in infos_p)
+    torch.cuda.synchronize()
+    t_plain = (time.perf_counter() - t0) / args.steps
+    plain.close()
     per_problem_serial = [i["seconds"] for i in infos1]
     line = {"metric": "aggregate Hessian matvecs/s, 64 independent problems of uneven size",
             "value": mv_b / args.steps / t_batch, "unit": "matvecs/s", "n_gpus": 1,
@@ -377,7 +398,11 @@ def run_batch(args):
             "concurrent": {"seconds_per_batch": t_batch,
                            "mean_time_to_solution_s": float(np.mean([i["seconds"] for i in infos])),
                            "status": sorted(set(i["status_name"] for i in infos))},
-            "speedup_vs_one_by_one": t_serial / t_batch}
+            "speedup_vs_one_by_one": t_serial / t_batch,
+            "plain_fp32": {"options": "one by one, FP32 reductions, no CUDA graphs, plain launches",
+                           "seconds_per_batch": t_plain, "value": mv_p / args.steps / t_plain,
+                           "status": sorted(set(i["status_name"] for i in infos_p))},
+            "speedup_vs_plain_fp32": t_plain / t_batch}
     print(json.dumps(line), flush=True)
 
 
