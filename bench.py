@@ -161,7 +161,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # the raw samples go to the directory named by REGNK_CLOCKS_DIR (kept for
+        # inspection), else to the system's temporary directory
+        import tempfile
+        d = os.environ.get("REGNK_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

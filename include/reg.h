@@ -354,7 +354,7 @@ const char* reg_batch_last_error(const reg_batch* batch);
 /* ---- Learned warm start (no counterpart in the paper) --------------------
  * A U-Net maps an image pair (m_R, m_T) on an S x S grid to a stationary
  * velocity v_0 from which reg_solve starts; the solve runs to the same
- * gradient tolerance and is the judge of the result (reg_warm_start keeps
+ * gradient tolerance and decides the result (reg_warm_start keeps
  * v_0 only if J(v_0) < J(0)). Architecture: 4 levels with 32, 64, 128, 256
  * channels, two periodic 3x3 convolutions + bias + ReLU per level, 2x2
  * average pooling down, nearest-neighbour 2x upsampling up, skip

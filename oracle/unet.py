@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY (see the package docstring).
 The learned warm start is not part of the paper: a small U-Net maps the
 image pair (m_R, m_T) to a stationary velocity v_0 from which the
 Gauss-Newton-Krylov solve of §3.4 starts; the solve, run to the same
-gradient tolerance, stays the judge of the result (the warm start is used
+gradient tolerance, still decides the result (the warm start is used
 only if J(v_0) < J(0)). This module is the plain definition of that network,
 of the mean-squared-error training loss, of its gradient (written out layer
 by layer, checked against central finite differences in the tests) and of

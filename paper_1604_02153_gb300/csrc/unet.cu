@@ -1,7 +1,7 @@
 // Learned warm start: a U-Net that maps (m_R, m_T) to a stationary velocity
 // v_0 for the Gauss-Newton-Krylov solve (no counterpart in the paper; the
 // solve of §3.4 runs to the same gradient tolerance from v_0 and is the
-// judge of the result). Forward pass, backward pass and Adam are the
+// arbiter of the result). Forward pass, backward pass and Adam are the
 // library's own kernels: every 3x3 convolution, its data gradient and its
 // weight gradient are implicit GEMMs on the BF16 tensor cores (mma.sync
 // m16n8k16, FP32 accumulation), with activations and activation gradients
