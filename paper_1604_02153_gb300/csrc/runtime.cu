@@ -1393,6 +1393,12 @@ PcgResult kkt(reg_ctx* c, const float* rhs, double rtol, int maxit, float* x) {
     ensure_G(c, c->coarse);
   }
   ensure_G(c, F);
+  // the full-Newton matvec reads the adjoint history of this velocity; a
+  // replayed graph cannot recompute it, so it is brought up to date here
+  if (c->full_newton && !F.have_lam) {
+    objective(c, F);
+    gradient(c, F, F.w2);
+  }
   auto A = [&](const float* p, float* q) {
     graphed(c, graph_key(c, "mv", p, q), [&] { hessian_core(c, F, p, q, false); });
   };

@@ -898,3 +898,28 @@ def test_fp32_reductions(regnk):
     info = R.solve(v, 1e-2)
     assert info["gnorm_rel"] <= 1e-2
     R.close()
+
+
+def test_full_newton_kkt_after_velocity_change(regnk):
+    """The full-Newton matvec inside PCG is replayed from a CUDA graph; after
+    a kkt_solve at another velocity the adjoint history it reads must belong
+    to the new velocity: the result equals that of a fresh context."""
+    n, nt, beta = 64, 4, 1e-2
+    m_R, m_T, v1 = (f32(a) for a in problem_data(n, n))
+    v2 = f32(inputs.random_velocity(n, n, seed=44, vmax=0.2))
+    rhs = dev(f32(inputs.random_velocity(n, n, seed=45, vmax=1.0)))
+    R = regnk.Registration(n, n, nt, beta, hessian=regnk.REG_HESSIAN_FULL)
+    R.set_images(dev(m_R), dev(m_T))
+    x = torch.empty(2 * n * n, device="cuda")
+    R.objective_gradient(dev(v1), None)
+    for _ in range(2):
+        R.kkt_solve(dev(v1), rhs, 1e-8, 6, x)
+    R.kkt_solve(dev(v2), rhs, 1e-8, 6, x)
+    R2 = regnk.Registration(n, n, nt, beta, hessian=regnk.REG_HESSIAN_FULL)
+    R2.set_images(dev(m_R), dev(m_T))
+    x2 = torch.empty_like(x)
+    R2.kkt_solve(dev(v2), rhs, 1e-8, 6, x2)
+    torch.cuda.synchronize()
+    assert torch.equal(x, x2)
+    R.close()
+    R2.close()
