@@ -88,3 +88,21 @@ def test_sl_converges_to_rk2a_reference():
         errs.append(np.linalg.norm(up - ref) / np.linalg.norm(ref))
     assert errs[1] < errs[0] / 2, errs
     assert errs[1] < 1e-2, errs
+
+
+def test_sl_error_grows_with_cfl_number():
+    """The paper's transport tables: SL at CFL 0.2 matches the RK2A(0.2)
+    reference closely and loses one to two digits at CFL 5 (here at 64^2
+    against RK2A(0.2) on 128^2)."""
+    nref = 128
+    m0f = inputs.random_field(nref, seed=1, kmax=6)
+    vf = inputs.random_velocity(nref, seed=3, kmax=3, vmax=0.5)
+    ref = rk2a.state_solve(m0f, vf, rk2a.cfl_steps(vf, 0.2))
+    m0, v = spectral.restrict(m0f), spectral.restrict_vec(vf)
+    n = m0.shape[0]
+    errs = {}
+    for c in (0.2, 1.0, 5.0):
+        m1 = Problem(np.zeros((n, n)), m0, rk2a.cfl_steps(v, c), 1e-2).state_solve(v)
+        errs[c] = np.linalg.norm(spectral.prolong(m1) - ref) / np.linalg.norm(ref)
+    assert errs[0.2] < errs[1.0] < errs[5.0], errs
+    assert errs[5.0] > 5 * errs[0.2], errs
