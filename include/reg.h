@@ -229,7 +229,7 @@ reg_status reg_transport(reg_ctx* ctx, const float* v, const float* m0, float* m
  * needs no images; allocates 10*n1*n2 floats of workspace on first use. */
 reg_status reg_deformation_map(reg_ctx* ctx, const float* v, float* u, float* det);
 
-/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"):/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"): the state equation
+/* RK2A comparator (§3.3.1, Appendix "RK2A derivation"): the state equation
  * in antisymmetric form d_t m + 1/2 (grad m . v + div(m v) - m div v) = 0,
  * solved from m0 to m1 = m(1) with nt Heun steps and pseudospectral
  * derivatives (FFT-heavy Eulerian transport, 12 FFTs per step), and its
@@ -242,7 +242,7 @@ reg_status reg_deformation_map(reg_ctx* ctx, const float* v, float* u, float* de
 reg_status reg_transport_rk2a(reg_ctx* ctx, const float* v, const float* m0, float* m1, int nt);
 reg_status reg_adjoint_rk2a(reg_ctx* ctx, const float* v, const float* lam1, float* lam0, int nt);
 
-/* Departure points of one time step/* Departure points of one time step (§3.3.2 "Tracing the Characteristic",
+/* Departure points of one time step (§3.3.2 "Tracing the Characteristic",
  * Heun): X_D = x - h_t/2 (v(x) + v(x - h_t v(x))) for the forward-in-time
  * equations and Y_D = x + h_t/2 (v(x) + v(x + h_t v(x))) for the backward
  * ones. Written as displacements in cell units, (X_D - x)/h, to dX and dY
