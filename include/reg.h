@@ -435,7 +435,8 @@ reg_status reg_warm_start(reg_ctx* ctx, reg_unet* net, float* v, int* accepted);
  * threads on one device) race on it, so issue them on one stream or order
  * them. The first call on a device looks up the array's device address with
  * that device current; make that first call before any stream capture.
- * Returns REG_ECUDA if that look-up or a launch fails. */
+ * Returns REG_ECUDA if that look-up or one of its own launches fails (a
+ * launch error pending from earlier work is cleared first, not reported). */
 #define REG_STATIC_MAX_POINTS (1024 * 1024)
 reg_status reg_interpolate_static(int n1, int n2, const float* u, const float* disp,
                                   float* out, void* cuda_stream);

@@ -57,6 +57,11 @@ extern "C" reg_status reg_interpolate_static(int n1, int n2, const float* u, con
     coef = g_static_ptr[dev];
   }
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // A launch error left pending by earlier, unrelated work is not this
+  // call's failure: take it off the error slot here, so that only an error
+  // raised by the two launches below turns into REG_ECUDA. (An error that
+  // has made the context unusable fails these launches too.)
+  (void)cudaGetLastError();
   // every coefficient is written by the prefilter before the gather reads it,
   // so nothing has to be cleared between calls
   regnk::launch_prefilter(n1, n2, u, nullptr, coef, 1, st);

@@ -1,6 +1,6 @@
 """Small fixed workloads for kernel profiling (ncu) of libregnk.
 
-    python -m paper_1604_02153_gb300.profcase --n 1024 --nt 8 --matvecs 3
+    python profcase.py --n 1024 --nt 8 --matvecs 3
 
 sets up the phantom pair at n^2 (seed 100), evaluates the objective and
 gradient at a smooth velocity (max |v| = 0.2) and applies the GN Hessian
@@ -16,7 +16,7 @@ import os
 import sys
 import time
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -91,9 +91,9 @@ def test_sl_converges_to_rk2a_reference():
 
 
 def test_sl_error_grows_with_cfl_number():
-    """The paper's transport tables: SL at CFL 0.2 matches the RK2A(0.2)
-    reference closely and loses one to two digits at CFL 5 (here at 64^2
-    against RK2A(0.2) on 128^2)."""
+    """Table t:convergence-SL-to-RK2A-transporteqs (§4.1.2): SL at CFL 0.2
+    matches the RK2A(0.2) reference closely and loses one to two digits at
+    CFL 5 (here at 64^2 against RK2A(0.2) on 128^2)."""
     nref = 128
     m0f = inputs.random_field(nref, seed=1, kmax=6)
     vf = inputs.random_velocity(nref, seed=3, kmax=3, vmax=0.5)
