@@ -93,10 +93,12 @@ typedef struct {
   int persistent_matvec;   /* 0 (default): one launch per transport step; 1: the GN
                               data term runs as one persistent cooperative kernel   */
   int inject_barrier_timeout; /* failure injection for tests, default 0: if 1, the
-                              persistent kernel's first grid barrier waits for an
-                              arrival that never comes; every block gives up after
-                              its bounded wait (~0.5 s) and the call returns
-                              REG_ETIMEOUT with the context still usable          */
+                              persistent kernel's first grid barrier (or the
+                              flow kernel's first tile wait, see flow_matvec)
+                              waits for an arrival that never comes; every block
+                              gives up after its bounded wait (~0.5 s) and the
+                              call returns REG_ETIMEOUT with the context still
+                              usable                                            */
   int programmatic_launch; /* 1 (default): kernels launched directly on the stream
                               carry programmatic stream serialisation, so a
                               kernel's blocks may be scheduled while its
@@ -171,6 +173,23 @@ typedef struct {
                               as CUDA graphs after their first two calls;
                               0: every launch is issued from the host. Results
                               are identical                                    */
+  int flow_matvec;         /* 1 (default): on a grid level with the cubic
+                              Lagrange model and nt >= 2 whose 32 x 16 point
+                              tiles all fit the GPU at once (e.g. the 512^2
+                              coarse grid of P_2L), the GN data term of a matvec
+                              (eq. inc-state-slm forward, eq. inc-adj-slm
+                              backward, int lambda~ grad m dt) is one launch:
+                              each block keeps its tile for all 2 nt steps and
+                              waits only for the neighbouring tiles its
+                              stencils reach (bounded waits: REG_ETIMEOUT after
+                              ~0.5 s, context usable). Results are bitwise those
+                              of the per-step kernels. 0: one launch per step.
+                              Ignored with persistent_matvec = 1. Two contexts
+                              whose flow kernels can run at the same time on
+                              one GPU (different streams) must not both use it:
+                              each launch needs all its blocks resident, so
+                              their waits could run out (reg_batch_create
+                              turns it off for its problems)                 */
 } reg_options;
 
 typedef struct {

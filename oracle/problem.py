@@ -2,11 +2,17 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-Problem (§2, eq. varopt, w and its constraint omitted):
+Problem (§2, eq. varopt):
     minimise J[v] = 1/2 ||m_1 - m_R||^2 + beta/2 <v, A v>
+                    [+ beta_w/2 ||div v||^2_H1]
     subject to d_t m + grad m . v = 0, m(0) = m_T, periodic;
-compressible (K = I, the default) or incompressible (div v = 0, w = 0:
-K = the Leray projection of §3.1, spectral.leray).
+compressible (w and its constraint omitted: K = I, the default),
+incompressible (div v = 0, w = 0: K = the Leray projection of §3.1,
+spectral.leray) or near-incompressible (beta_w > 0: the mass source
+w = div v of eq. icconstraint carries the H1 norm of eq. varopt:regw; with
+w and p eliminated from the control equations eq. control-v and
+eq. control-w, the term -beta_w grad (I - Lap) div v joins beta A v in the
+gradient and in the Hessian, spectral.reg_w_term, and K = I).
 
 Discrete inner product (§3.2, midpoint rule): <a, b>_h = h_1 h_2 sum a b.
 
@@ -50,7 +56,7 @@ class Problem:
     """One registration problem on an (n2, n1) grid with nt time steps."""
 
     def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline", incompressible=False,
-                 hessian="gn"):
+                 hessian="gn", beta_w=0.0):
         self.m_R = np.asarray(m_R, dtype=np.float64)
         self.m_T = np.asarray(m_T, dtype=np.float64)
         self.n2, self.n1 = self.m_R.shape
@@ -60,6 +66,8 @@ class Problem:
         self.reg_norm = reg_norm
         self.kind = kind
         self.incompressible = bool(incompressible)
+        self.beta_w = float(beta_w)
+        assert self.beta_w >= 0.0 and not (self.incompressible and self.beta_w > 0.0)
         assert hessian in ("gn", "full")
         self.full_newton = hessian == "full"
         self.lam = None
@@ -78,6 +86,11 @@ class Problem:
             return b
         self._count(row, ffts=2 * D)
         return spectral.leray(b)
+
+    def regop(self, v):
+        """beta A v, with -beta_w grad (I - Lap) div v added for the
+        near-incompressible problem (spectral.reg_w_term)."""
+        return spectral.apply_regop(v, self.beta, self.reg_norm, self.beta_w)
 
     def _count(self, row, ffts=0, ips=0):
         c = self.counts.setdefault(row, [0, 0])
@@ -116,7 +129,7 @@ class Problem:
     def objective(self, v):
         """J[v] (eq. varopt:objective); counted as row "J" = SE + 2d FFTs."""
         self.state_solve(v, row="J")
-        Av = spectral.apply_reg(self.v, self.beta, self.reg_norm)
+        Av = self.regop(self.v)
         self._count("J", ffts=2 * D)
         r = self.m[-1] - self.m_R
         return 0.5 * self.inner(r, r) + 0.5 * self.inner(self.v, Av)
@@ -158,7 +171,7 @@ class Problem:
             gm = self._grad_m(j, "g")
             b += self.ht * self.w[j] * lam[j] * gm
         self._count("g", ffts=2 * D)
-        return spectral.apply_reg(self.v, self.beta, self.reg_norm) + self.K(b, "g")
+        return self.regop(self.v) + self.K(b, "g")
 
     def objective_gradient(self, v):
         J = self.objective(v)
@@ -206,7 +219,7 @@ class Problem:
             self._count(row, ips=1)
             bt = bt + self.ht * self.w[j] * lt * self._grad_m(j, row)
         self._count(row, ffts=2 * D)
-        return spectral.apply_reg(vt, self.beta, self.reg_norm) + self.K(bt, row)
+        return self.regop(vt) + self.K(bt, row)
 
     def _hessian_matvec_full(self, vt, row):
         """Full-Newton matvec (eq. hessian-matvec with its lambda terms).
@@ -258,12 +271,11 @@ class Problem:
             self._count(row, ips=2)
             bt = bt + ht * self.w[j] * (lt * self._grad_m(j, row) + lam[j] * grad_mt(j))
         self._count(row, ffts=2 * D)
-        return spectral.apply_reg(vt, self.beta, self.reg_norm) + self.K(bt, row)
+        return self.regop(vt) + self.K(bt, row)
 
     def data_matvec(self, vt):
         """Data term Q v~ = H v~ - beta A v~ (eq. reduced-space-kkt-system)."""
-        return self.hessian_matvec(vt) - spectral.apply_reg(
-            np.asarray(vt, dtype=np.float64), self.beta, self.reg_norm)
+        return self.hessian_matvec(vt) - self.regop(np.asarray(vt, dtype=np.float64))
 
     # -- Appendix C reference counts -----------------------------------------
     @staticmethod

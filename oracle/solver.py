@@ -67,20 +67,28 @@ class Solver:
             # coarse_kind: its interpolation model (default: the problem's)
             self.coarse = Problem(spectral.restrict(p.m_R), spectral.restrict(p.m_T),
                                   coarse_nt or p.nt, p.beta, p.reg_norm, coarse_kind or p.kind,
-                                  p.incompressible)
+                                  p.incompressible, beta_w=p.beta_w)
 
     # -- preconditioners -----------------------------------------------------
+    @staticmethod
+    def reg_pow(p, x, s):
+        """(beta A)^s, or R^s for the near-incompressible regularisation
+        operator R of Problem.regop (P_REG = R: the operator the paper's
+        preconditioner inverts is the regularisation of the Hessian)."""
+        if p.beta_w > 0.0:
+            return spectral.regop_power(x, p.beta, p.reg_norm, p.beta_w, s)
+        return spectral.reg_power(x, p.beta, p.reg_norm, s)
+
     def precond_reg(self, r):
-        p = self.p
-        return spectral.reg_power(r, p.beta, p.reg_norm, -1.0)
+        return self.reg_pow(self.p, r, -1.0)
 
     def coarse_split_op(self, s):
         """(I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse grid."""
         c = self.coarse
-        u = spectral.reg_power(s, c.beta, c.reg_norm, -0.5)
+        u = self.reg_pow(c, s, -0.5)
         q = c.data_matvec(u)
         self.coarse_matvecs += 1
-        return s + spectral.reg_power(q, c.beta, c.reg_norm, -0.5)
+        return s + self.reg_pow(c, q, -0.5)
 
     def estimate_eigenvalues(self):
         """e_min, e_max of the coarse split operator at v = 0."""
@@ -95,7 +103,13 @@ class Solver:
         _, rmax, _ = krylov.lanczos_extremal(self.coarse_split_op, v0, self.lanczos_steps)
         gam = spectral.reg_symbol(c.n1, c.n2, c.reg_norm).astype(np.float64)
         gam[0, 0] = 1.0
-        emin = float(np.min(1.0 + 1.0 / (c.beta * gam)))
+        # largest eigenvalue of the regularisation operator's 2 x 2 symbol per
+        # mode: beta gamma, plus beta_w (1 + |k|^2) |kd|^2 along kd (near-
+        # incompressible; kd the derivative wavenumbers)
+        K1, K2 = spectral._k_grids(c.n1, c.n2, zero_nyquist=True)
+        ksq = spectral.reg_symbol(c.n1, c.n2, "H1").astype(np.float64)
+        lmax = c.beta * gam + c.beta_w * (1.0 + ksq) * (K1 * K1 + K2 * K2)
+        emin = float(np.min(1.0 + 1.0 / lmax))
         self.eig = {"emin": emin, "emax": rmax * self.emax_safety, "beta": c.beta}
         return self.eig
 
@@ -113,7 +127,7 @@ class Solver:
 
     def precond_2l(self, r):
         p = self.p
-        r1 = spectral.reg_power(r, p.beta, p.reg_norm, -0.5)
+        r1 = self.reg_pow(p, r, -0.5)
         rc = spectral.restrict_vec(r1)
         rh = np.stack([spectral.highpass(r1[c]) for c in range(2)])
         if self.pc_solver == "cheb":
@@ -123,7 +137,7 @@ class Solver:
             sc, _ = krylov.pcg(self.coarse_split_op, rc, lambda x: x,
                                self.pc_eps * self.eta, self.max_pcg)
         z1 = spectral.prolong_vec(sc) + rh
-        return spectral.reg_power(z1, p.beta, p.reg_norm, -0.5)
+        return self.reg_pow(p, z1, -0.5)
 
     def apply_precond(self, r):
         if self.precond == "REG":

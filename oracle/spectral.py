@@ -109,6 +109,70 @@ def apply_reg(v, beta, reg_norm):
     return np.stack([ifft2_real(g * fft2(v[c])) for c in range(v.shape[0])])
 
 
+def reg_w_term(v, beta_w):
+    """-beta_w grad (I - Lap) div v: the near-incompressible regularisation of
+    §2 with the mass source eliminated.
+
+    eq. varopt:regw puts the H1 norm ||w||^2 = int grad w . grad w + w^2 on
+    the mass source w, and eq. icconstraint ties it to the velocity,
+    w = div v. The control equations of the optimality system (Appendix A,
+    eq. control-v and eq. control-w) read
+        beta_v A v + grad p + b = 0,    beta_w B w + p = 0,
+    with B = I - Lap the first variation of that norm. Eliminating
+    p = -beta_w B w and w = div v leaves
+        beta_v A v - beta_w grad B div v + b = 0,
+    i.e. this term joins beta_v A v in the reduced gradient and in the
+    Hessian; it is the first variation of (beta_w / 2) ||div v||^2_{H1}.
+    Written out step by step with the operators above: w = div v (Nyquist
+    zeroed), B w = w - Lap w with the Laplacian's symbol -|k|^2, then
+    -beta_w grad(B w).
+    """
+    n2, n1 = v.shape[1:]
+    w = div(v)
+    lap_w = ifft2_real(-reg_symbol(n1, n2, "H1") * fft2(w))
+    return -beta_w * grad(w - lap_w)
+
+
+def apply_regop(v, beta, reg_norm, beta_w=0.0):
+    """The regularisation operator of the gradient and the Hessian:
+    beta_v A v, plus -beta_w grad (I - Lap) div v for the near-incompressible
+    problem (beta_w > 0)."""
+    out = apply_reg(v, beta, reg_norm)
+    if beta_w > 0.0:
+        out = out + reg_w_term(v, beta_w)
+    return out
+
+
+def regop_power(v, beta, reg_norm, beta_w, s):
+    """R^s for R = beta_v A - beta_w grad (I - Lap) div (the operator of
+    apply_regop), with the zero weight of A at k = 0 replaced by 1 as in
+    reg_power (s = 1 is R itself).
+
+    R acts on each wavenumber k as the symmetric 2 x 2 matrix
+        beta_v |k|^(2p) I + beta_w (1 + |k|^2) kd kd^T,
+    kd the derivative wavenumbers of grad and div (Nyquist zeroed); its power
+    is taken by the eigendecomposition of that matrix (numpy.linalg.eigh),
+    mode by mode. With beta_w = 0 this is reg_power.
+    """
+    n2, n1 = v.shape[1:]
+    gam = reg_symbol(n1, n2, reg_norm).astype(np.float64)
+    if s != 1.0:
+        gam[0, 0] = 1.0
+    K1, K2 = _k_grids(n1, n2, zero_nyquist=True)
+    ksq = reg_symbol(n1, n2, "H1").astype(np.float64)
+    c = beta_w * (1.0 + ksq)
+    M = np.empty((n2, n1, 2, 2))
+    M[..., 0, 0] = beta * gam + c * K1 * K1
+    M[..., 0, 1] = c * K1 * K2
+    M[..., 1, 0] = c * K2 * K1
+    M[..., 1, 1] = beta * gam + c * K2 * K2
+    lam, Q = np.linalg.eigh(M)
+    Ms = np.einsum("...ij,...j,...kj->...ik", Q, lam ** s, Q)
+    vh = np.stack([fft2(v[0]), fft2(v[1])], axis=-1)
+    oh = np.einsum("...ij,...j->...i", Ms, vh)
+    return np.stack([ifft2_real(oh[..., 0]), ifft2_real(oh[..., 1])])
+
+
 def reg_power(v, beta, reg_norm, s):
     """(beta * A)^s componentwise, with the zero weight at k = 0 replaced by 1.
 

@@ -47,9 +47,15 @@ reg_status reg_batch_create(const reg_grid* grids, int B, int nt, const double* 
     return REG_ECUDA;
   }
   b->grids.assign(grids, grids + B);
+  // the problems' kernels run concurrently on one GPU: no context may use
+  // the flow kernel, whose blocks wait for each other and need every tile
+  // resident at once (two such launches could each hold part of the GPU)
+  reg_options o;
+  if (opt) o = *opt; else reg_default_options(&o);
+  o.flow_matvec = 0;
   for (int i = 0; i < B; ++i) {
     reg_ctx* c = nullptr;
-    const reg_status s = reg_create(grids[i], nt, beta[i], opt, &c);
+    const reg_status s = reg_create(grids[i], nt, beta[i], &o, &c);
     if (s != REG_OK) {
       reg_batch_destroy(b);
       return s;

@@ -196,6 +196,32 @@ struct MatvecArgs {
 };
 cudaError_t launch_gn_matvec(const MatvecArgs& a, cudaStream_t st);
 
+// flow.cu: the GN data term in one launch with tile-to-tile synchronisation
+// (cubic Lagrange model, nt >= 2, every tile's block resident)
+struct FlowArgs {
+  int n1, n2, log1, nt;
+  long long N;
+  float ht;
+  int tiles_x, tiles_y;     // 32 x 16 point tiles
+  const float* vt;          // direction v~ (2N)
+  const float* dX;          // forward departure displacement (2N)
+  const float* dY;          // backward departure displacement (2N)
+  const float* delta;       // div v (N)
+  const float* delta_bar;   // div v at Y_D (N)
+  const float* gm;          // grad m_0..grad m_nt (2 (nt+1) N)
+  const float* G;           // grad m_{j-1}(X_D), j = 1..nt (2 nt N)
+  float* buf0;              // scratch: the transported field, two steps (N each)
+  float* buf1;
+  float* b;                 // output: the data term b~ (2N)
+  unsigned* flags;          // one per tile (zeroed by launch_gn_flow)
+  int* err;                 // set when a wait gave up
+  const double* dmax;       // largest |displacement| of X_D and of Y_D in cells (device)
+  int inject;               // failure injection (tests): 1 = the first wait never ends
+};
+int flow_tiles(int n1, int n2);
+int flow_capacity(int n1, int n2);
+cudaError_t launch_gn_flow(const FlowArgs& a, cudaStream_t st);
+
 // reduce.cu
 void launch_dot(const float* a, const float* b, long long n, double* partial, double* out,
                 cudaStream_t st);

@@ -84,6 +84,12 @@ struct Level {
   float* gmt = nullptr;       // 2 nt N
   float* prod = nullptr;      // 2 (nt+1) N
   bool have_lam = false;      // lam_hist belongs to the cached velocity
+  // GN data term in one launch with tile-to-tile synchronisation (flow.cu):
+  // cubic Lagrange levels with nt >= 2 whose tiles all fit the GPU at once
+  bool flow = false;
+  int flow_tx = 0, flow_ty = 0;     // tiles per axis
+  unsigned* flow_flags = nullptr;   // one per tile
+  double* flow_dmax = nullptr;      // largest |X_D - x|, |Y_D - x| in cells (2, device)
 };
 
 }  // namespace
@@ -146,6 +152,7 @@ struct reg_ctx {
   bool capturing = false;
   // persistent matvec: barrier state (2 unsigned) and error flag, device
   bool persistent = true;
+  bool any_flow = false;         // a level runs the flow kernel (its waits share barerr)
   unsigned* bar = nullptr;
   int* barerr = nullptr;
   int* hbarerr = nullptr;
@@ -293,6 +300,17 @@ void alloc_level(reg_ctx* c, Level& L, int n1, int n2, int nt) {
   L.w1 = dalloc<float>(c, 2 * N);
   L.w2 = dalloc<float>(c, 2 * N);
   L.spec = dalloc<float2>(c, kSpecSlots * (size_t)L.g.spec);
+  // the flow kernel needs every tile's block resident at once
+  const int tiles = flow_tiles(n1, n2);
+  if (L.lagrange && nt >= 2 && c->opt.flow_matvec && !c->persistent && tiles > 0 &&
+      flow_capacity(n1, n2) >= tiles) {
+    L.flow = true;
+    L.flow_tx = n1 / 32;
+    L.flow_ty = tiles / L.flow_tx;
+    L.flow_flags = dalloc<unsigned>(c, tiles);
+    L.flow_dmax = dalloc<double>(c, 2);
+    c->any_flow = true;
+  }
 }
 
 
@@ -721,17 +739,21 @@ double* slot(reg_ctx* c, int s) { return c->dsc + s; }
 void read_slots(reg_ctx* c, int first, int count) {
   check(c, cudaMemcpyAsync(c->hsc + first, c->dsc + first, count * sizeof(double),
                            cudaMemcpyDeviceToHost, c->st), "scalar read");
-  if (c->persistent)   // only the persistent matvec can raise the barrier flag
+  // only the persistent matvec and the flow kernel can raise the wait flag
+  const bool waits = c->persistent || c->any_flow;
+  if (waits)
     check(c, cudaMemcpyAsync(c->hbarerr, c->barerr, sizeof(int), cudaMemcpyDeviceToHost, c->st),
           "barrier flag read");
   check(c, cudaStreamSynchronize(c->st), "stream synchronize");
-  if (c->persistent && *c->hbarerr) {
-    // a persistent kernel gave up waiting at a grid barrier: reset its state
+  if (waits && *c->hbarerr) {
+    // a persistent or flow kernel gave up a bounded wait: reset the state
     cudaMemsetAsync(c->bar, 0, 2 * sizeof(unsigned), c->st);
     cudaMemsetAsync(c->barerr, 0, sizeof(int), c->st);
     cudaStreamSynchronize(c->st);
     *c->hbarerr = 0;
-    fail(c, REG_ETIMEOUT, "grid barrier wait of the persistent matvec timed out");
+    fail(c, REG_ETIMEOUT, c->persistent
+                              ? "grid barrier wait of the persistent matvec timed out"
+                              : "tile wait of the flow matvec timed out");
   }
 }
 
@@ -772,6 +794,11 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
     }
     read_slots(c, S_DX, 2);
     L.fuse_w = fused_box_width(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
+  }
+  if (L.flow) {   // the flow kernel reads its tiles' reach from these (no host sync)
+    Prof P(c, REG_KC_REDUCE, 16.0 * N);
+    launch_maxabs(L.dX, 2 * (long long)N, c->partialf, L.flow_dmax, c->st);
+    launch_maxabs(L.dY, 2 * (long long)N, c->partialf, L.flow_dmax + 1, c->st);
   }
   check(c, cudaMemcpyAsync(L.m, L.mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m_T");
   for (int j = 1; j <= L.nt; ++j) {
@@ -952,6 +979,42 @@ void data_term_persistent(reg_ctx* c, Level& L, const float* vt, float* b) {
   check(c, launch_gn_matvec(a, c->st), "persistent matvec launch");
 }
 
+// the GN data term b~ in one launch (flow.cu)
+void data_term_flow(reg_ctx* c, Level& L, const float* vt, float* b) {
+  LevelScope ls(c, L);
+  FlowArgs a{};
+  a.n1 = L.g.n1;
+  a.n2 = L.g.n2;
+  a.log1 = L.g.log1;
+  a.nt = L.nt;
+  a.N = L.g.N;
+  a.ht = L.ht;
+  a.tiles_x = L.flow_tx;
+  a.tiles_y = L.flow_ty;
+  a.vt = vt;
+  a.dX = L.dX;
+  a.dY = L.dY;
+  a.delta = L.delta;
+  a.delta_bar = L.delta_bar;
+  a.gm = L.gm;
+  a.G = L.G;
+  a.buf0 = L.fA;
+  a.buf1 = L.fB;
+  a.b = b;
+  a.flags = L.flow_flags;
+  a.err = c->barerr;
+  a.dmax = L.flow_dmax;
+  a.inject = c->opt.inject_barrier_timeout ? 1 : 0;
+  // algorithmic bytes per point (each field read or written once): per
+  // incremental state step G_j, grad m_j, m~ in and out (24), per adjoint
+  // step grad m_j, lambda~ in and out (16), once: dX, dY, v~, div v,
+  // div v(Y_D), b~ (40) and v~(X_D) kept on chip, minus the reads and writes
+  // the ends of the chain do not make (m~_0 and lambda~_0: 8)
+  const double per_point = 24.0 * L.nt + 16.0 * L.nt + 40.0 - 8.0;
+  Prof P(c, REG_KC_MATVEC, (double)L.g.N * per_point);
+  check(c, launch_gn_flow(a, c->st), "flow matvec launch");
+}
+
 // the launch sequence of one GN matvec; needs ensure_G(c, L) beforehand
 void hessian_full(reg_ctx* c, Level& L, const float* vt, float* out);
 
@@ -975,14 +1038,26 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     (void)N2;
     return;
   }
+  // beta A v~: its forward transforms depend only on v~ and run on the side
+  // stream while the transport steps (which use no FFT workspace) run here
+  const bool fork = !data_only && !c->incompressible;
+  if (L.flow) {
+    if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
+    data_term_flow(c, L, vt, data_only ? out : L.b);
+    if (data_only) return;
+    if (c->incompressible) {
+      finish_hessian_incompressible(c, L, vt, out);
+    } else {
+      join_side(c);
+      spectral_inv(c, L, 1, 2, out, 1, L.b);
+    }
+    return;
+  }
   const GridDims& gd = L.g;
   const size_t N = (size_t)gd.N;
   const int nt = L.nt;
   const float ht = L.ht;
   const int lg = L.lagrange;
-  // beta A v~: its forward transforms depend only on v~ and run on the side
-  // stream while the transport steps (which use no FFT workspace) run here
-  const bool fork = !data_only && !c->incompressible;
   if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
   float* mt = L.fA;
   float* mt2 = L.fB;
@@ -1509,6 +1584,7 @@ reg_status reg_default_options(reg_options* o) {
   o->hessian = 0;
   o->precision = REG_PRECISION_FP64;
   o->use_graphs = 1;
+  o->flow_matvec = 1;
   return REG_OK;
 }
 
@@ -1531,7 +1607,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.incompressible != 0 && o.incompressible != 1) || (o.hessian != 0 && o.hessian != 1) ||
       (o.hessian == 1 && o.persistent_matvec != 0) ||
       (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
-      (o.use_graphs != 0 && o.use_graphs != 1))
+      (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))

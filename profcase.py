@@ -34,6 +34,7 @@ def main():
     ap.add_argument("--fused", type=int, default=1, help="fused_transport option (0 or 1)")
     ap.add_argument("--step-tile", type=int, default=-1,
                     help="step_tile option (-1: timed at creation, 0: built-in, 1..9: fixed)")
+    ap.add_argument("--flow", type=int, default=1, help="flow_matvec option (0 or 1)")
     ap.add_argument("--unet", type=int, default=0,
                     help="instead: this many warm-start network training steps (batch 8, 256^2)")
     a = ap.parse_args()
@@ -52,7 +53,8 @@ def main():
     R = regnk.Registration(n, n, a.nt, 1e-2,
                            interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE,
                            persistent_matvec=a.persistent, programmatic_launch=a.pdl,
-                           fused_transport=a.fused, step_tile=a.step_tile, **pc)
+                           fused_transport=a.fused, step_tile=a.step_tile, flow_matvec=a.flow,
+                           **pc)
     R.set_images(f(m_R), f(m_T))
     vd, ud = f(v), f(u)
     g = torch.empty_like(vd)
@@ -65,9 +67,21 @@ def main():
         R.hessian_matvec(vd, ud, H)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / max(1, a.matvecs)
+    # device time per matvec: CUDA events around each call on the launching
+    # stream, median
+    st = torch.cuda.current_stream()
+    dev_ms = []
+    for _ in range(max(3, a.matvecs)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        R.hessian_matvec(vd, ud, H)
+        e1.record(st)
+        torch.cuda.synchronize()
+        dev_ms.append(e0.elapsed_time(e1))
     tiles = " ".join(f"{l}/{k}={t[0]}x{t[1]}" for (l, k), t in R.step_tiles().items())
-    print(f"n={n} nt={a.nt} persistent={a.persistent} pdl={a.pdl} fused={a.fused} step tiles {tiles}: "
-          f"matvec {1e3 * dt:.3f} ms (wall, incl. host)")
+    print(f"n={n} nt={a.nt} persistent={a.persistent} pdl={a.pdl} fused={a.fused} flow={a.flow} "
+          f"step tiles {tiles}: matvec {1e3 * dt:.3f} ms (wall, incl. host), "
+          f"{1e3 * float(np.median(dev_ms)):.1f} us (CUDA events, median of {len(dev_ms)})")
     if a.pcg and not a.precond:
         x = torch.empty_like(vd)
         R.kkt_solve(vd, g, 1e-12, a.matvecs, x)

@@ -318,6 +318,10 @@ def test_full_size_transport_symmetry_positivity(regnk):
     R.hessian_matvec(vd, a, Ha)
     R.hessian_matvec(vd, b, Hb)
     hab, hba = R.dot(Ha, b), R.dot(a, Hb)
+    # the optimise-then-discretise SL Hessian is symmetric only up to the
+    # adjoint error of the scheme (§4.1.3, reading R9); 1e-3 is ten times
+    # the oracle's own symmetry defect pinned in the oracle tests, not an
+    # FP32 bar
     assert abs(hab - hba) / abs(hab) < 1e-3
     assert R.dot(Ha, a) > 0
     R.close()
@@ -359,6 +363,10 @@ def test_eigen_bounds(regnk):
     S = Solver(Problem(m_R, m_T, nt, beta), precond="2L", lanczos_v0=v0)
     e = S.estimate_eigenvalues()
     assert abs(emin - e["emin"]) < 1e-12 * e["emin"]
+    # e_max is the largest Ritz value of 30 Lanczos steps (R16): the GPU
+    # recurrence carries FP32 rounding in its vectors and does not
+    # reorthogonalise, the oracle's does, so the two Ritz values differ
+    # beyond the operator's 1e-4; the bound enters CHEB(k) with a 5 % margin
     assert abs(emax - e["emax"]) / e["emax"] < 1e-3
     R.close()
 
@@ -431,9 +439,13 @@ def test_barrier_timeout_is_reported(regnk):
     R2.set_images(dev(m_R), dev(m_T))
     R2.objective_gradient(vd, None)
     R2.hessian_matvec(vd, dev(v), H)
+    Av = torch.empty_like(H)
+    R2.spectral(regnk.REG_SPEC_REG, vd, Av)
     P = Problem(m_R, m_T, nt, 1e-2)
     P.state_solve(v)
-    assert rel(host(H, (2, n, n)), P.hessian_matvec(v)) < 1e-3
+    shape = (2, n, n)
+    ref = P.hessian_matvec(v) - spectral.apply_reg(v, 1e-2, "H1")
+    assert rel(host(H, shape) - host(Av, shape), ref) < 1e-4
     R2.close()
 
 
@@ -560,6 +572,88 @@ def test_fused_prefilter_step_matches_two_kernel_path(regnk, n1, n2, vmax):
         ref = P.hessian_matvec(u) - spectral.apply_reg(u, beta, "H1")
         for fused in (0, 1):
             assert rel(D[fused], ref) < 1e-4, (fused, rel(D[fused], ref))
+
+
+@pytest.mark.parametrize("n1,n2,nt,vmax", [(128, 128, 4, 0.5), (128, 128, 4, 4.0), (192, 96, 2, 1.0),
+                                           (256, 128, 8, 2.0), (512, 512, 4, 0.2), (96, 384, 3, 1.0)])
+def test_flow_matvec_matches_per_step_kernels(regnk, n1, n2, nt, vmax):
+    """The GN data term as one launch with tile-to-tile waits (cubic
+    Lagrange, flow_matvec = 1) against one launch per step: bitwise equal
+    (same arithmetic per point), for displacements of a few cells up to ~20
+    cells per step (the stencils then reach two tiles away in y), power-of-two
+    and 3*2^k grids, nt from 2 to 8; and the data term H u - beta A u against
+    the oracle at the 1e-4 bar."""
+    beta = 1e-2
+    m_R, m_T, _ = (f32(a) for a in problem_data(n1, n2))
+    v = f32(inputs.random_velocity(n1, n2, seed=33, vmax=vmax))
+    u = f32(inputs.random_velocity(n1, n2, seed=34, vmax=1.0))
+    out = {}
+    for flow in (1, 0):
+        R = regnk.Registration(n1, n2, nt, beta, interp=regnk.REG_INTERP_LAGRANGE,
+                               flow_matvec=flow, precond=regnk.REG_PC_REG)
+        R.set_images(dev(m_R), dev(m_T))
+        R.objective_gradient(dev(v), None)
+        H = torch.empty(2 * n1 * n2, device="cuda")
+        R.hessian_matvec(dev(v), dev(u), H)
+        H2 = torch.empty_like(H)
+        R.hessian_matvec(dev(v), dev(u), H2)        # repeat: flags and buffers reused
+        Au = torch.empty_like(H)
+        R.spectral(regnk.REG_SPEC_REG, dev(u), Au)
+        torch.cuda.synchronize()
+        out[flow] = (H.cpu(), H2.cpu(), Au.cpu())
+        R.close()
+    assert torch.equal(out[1][0], out[0][0])
+    assert torch.equal(out[1][1], out[1][0])
+    P = Problem(m_R, m_T, nt, beta, kind="lagrange")
+    P.state_solve(v)
+    ref = P.hessian_matvec(u) - spectral.apply_reg(u, beta, "H1")
+    shape = (2, n2, n1)
+    data = out[1][0].numpy().astype(np.float64).reshape(shape) - \
+        out[1][2].numpy().astype(np.float64).reshape(shape)
+    assert rel(data, ref) < 1e-4
+
+
+def test_flow_matvec_in_two_level_solve(regnk):
+    """P_2L with the cubic Lagrange coarse problem (the benchmark's chosen
+    coarse model) runs its coarse matvecs through the flow kernel, inside the
+    replayed CUDA graph of CHEB(10): the solve is bitwise the one with
+    per-step coarse kernels (same Newton and PCG iterations, same velocity)."""
+    n, nt = 256, 4
+    m_R, m_T, _ = (f32(a) for a in problem_data(n, n))
+    res = {}
+    for flow in (1, 0):
+        R = regnk.Registration(n, n, nt, 1e-2, coarse_interp=regnk.REG_INTERP_LAGRANGE,
+                               coarse_nt=2, flow_matvec=flow)
+        R.set_images(dev(m_R), dev(m_T))
+        v = torch.zeros(2 * n * n, device="cuda")
+        info = R.solve(v, 1e-2)
+        torch.cuda.synchronize()
+        res[flow] = (info["newton_iters"], info["pcg_iters"], info["coarse_matvecs"], v.cpu())
+        R.close()
+    assert res[1][:3] == res[0][:3]
+    assert res[1][2] > 0
+    assert torch.equal(res[1][3], res[0][3])
+
+
+def test_flow_wait_timeout_is_reported(regnk):
+    """Failure detection of the flow kernel without a GPU fault: its first
+    tile wait asks for a step no tile publishes; every wait gives up after
+    its bounded spin, the call returns REG_ETIMEOUT and the context keeps
+    working (a later matvec through the per-step kernels is exact)."""
+    n, nt = 128, 4
+    m_R, m_T, v = (f32(a) for a in problem_data(n, n))
+    R = regnk.Registration(n, n, nt, 1e-2, interp=regnk.REG_INTERP_LAGRANGE,
+                           inject_barrier_timeout=1, precond=regnk.REG_PC_REG)
+    R.set_images(dev(m_R), dev(m_T))
+    vd = dev(v)
+    R.objective_gradient(vd, None)
+    H = torch.empty(2 * n * n, device="cuda")
+    with pytest.raises(regnk.RegError) as e:
+        R.hessian_matvec(vd, dev(v), H)
+        R.dot(H, H)            # the status surfaces at the next synchronising call
+    assert e.value.status == regnk.REG_ETIMEOUT
+    assert R.dot(vd, vd) > 0
+    R.close()
 
 
 @pytest.mark.parametrize("n", [0, 1, 3, 1000003, 2 * 1024 * 1024])
@@ -691,6 +785,8 @@ def test_incompressible_two_level_preconditioner(regnk, pc_solver):
     S = Solver(Problem(m_R, m_T, nt, beta, incompressible=True), precond="2L",
                pc_solver="cheb" if pc_solver == 0 else "pcg", lanczos_v0=lv0)
     e = S.estimate_eigenvalues()
+    # Lanczos Ritz value: FP32 recurrence without reorthogonalisation (see
+    # test_eigen_bounds)
     assert abs(emax - e["emax"]) / e["emax"] < 1e-3 and abs(emin - e["emin"]) < 1e-12 * emin
     S.eig = {"emin": emin, "emax": emax, "beta": beta}
     S.p.state_solve(v)
