@@ -97,6 +97,11 @@ def parse():
                     help="the incompressible problem (div v = 0, K the Leray projection)")
     ap.add_argument("--no-plain-form", action="store_true",
                     help="skip the plain-form solve (FP32 reductions, no graphs)")
+    ap.add_argument("--no-arms", action="store_true",
+                    help="skip the coarse-solver arms (nested PCG, coarse problem at nt and splines)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the cuFFT comparator, the 256^2/512^2 measurements and the batch64 "
+                         "comparison")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the learned warm-start measurement")
     ap.add_argument("--precond", choices=["2l-cheb", "2l-pcg", "reg"], default="2l-cheb",
@@ -228,15 +233,74 @@ def oracle_matvec_sample(incompressible=False, hessian="gn"):
     return lambda: P.hessian_matvec(vt)
 
 
-def cpu_baseline(incompressible=False, hessian="gn"):
+def _oracle_matvec_worker(args):
+    """One oracle matvec in a worker process (set-up untimed); returns its
+    start and end on the shared monotonic clock."""
+    incompressible, hessian = args
+    f = oracle_matvec_sample(incompressible, hessian)
+    t0 = time.perf_counter()
+    f()
+    return t0, time.perf_counter()
+
+
+def host_cpu():
+    """Core count and model of the host that runs the oracle."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_c1_solve():
+    """The 64^2 plain-method configuration solved by the oracle (P_2L CHEB(10),
+    ||g||rel 1e-2): seconds and iterations, single-threaded."""
+    from oracle.problem import Problem
+    from oracle.solver import Solver
+    from paper_1604_02153_gb300 import inputs
+    n, nt, beta = 64, 4, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    t0 = time.perf_counter()
+    S = Solver(Problem(m_R, m_T, nt, beta), precond="2L", pc_solver="cheb")
+    _, info = S.solve(np.zeros((2, n, n)), GTOL)
+    return {"seconds": time.perf_counter() - t0, "newton_iters": info["newton_iters"],
+            "matvecs": info["matvecs"], "grid": [n, n], "nt": nt,
+            "what": "FP64 oracle full solve of the 64^2 analytic problem, P_2L CHEB(10), "
+                    "||g||rel 1e-2, one core"}
+
+
+def cpu_baseline(incompressible=False, hessian="gn", all_cores=True):
+    """The oracle on the host: one GN matvec at 1024^2 on one core, then one
+    independent matvec per core at once (process pool started with spawn),
+    and the 64^2 oracle full solve."""
     f = oracle_matvec_sample(incompressible, hessian)
     t0 = time.perf_counter()
     f()
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 {'full-Newton' if hessian == 'full' else 'GN'} Hessian matvec of the "
-                      f"FP64 numpy oracle at {N_GRID}^2, nt={NT} "
-                      f"({dt:.1f} s, single-threaded numpy)"}
+    cpu = host_cpu()
+    what = f"{'full-Newton' if hessian == 'full' else 'GN'} Hessian matvec"
+    line = {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 {what} of the FP64 numpy oracle at {N_GRID}^2, nt={NT} "
+                      f"({dt:.1f} s, single-threaded numpy)",
+            "host": cpu}
+    if all_cores and (cpu["nproc"] or 1) > 1:
+        import multiprocessing as mp
+        k = int(cpu["nproc"])
+        with mp.get_context("spawn").Pool(k) as pool:
+            spans = pool.map(_oracle_matvec_worker, [(incompressible, hessian)] * k)
+        wall = max(e for _, e in spans) - min(s0 for s0, _ in spans)
+        line["all_cores"] = {"value": k / wall, "unit": UNIT, "cores": k,
+                             "sample": f"{k} independent {what}s at {N_GRID}^2, one per core "
+                                       f"(process pool), {wall:.1f} s from the first start to "
+                                       f"the last end"}
+    line["c1_full_solve"] = oracle_c1_solve()
+    return line
 
 
 def run_reference(args, rank):
@@ -285,6 +349,135 @@ def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", inco
 
 
 # ---------------------------------------------------------------------------
+# measurements beside the headline (outside the timed region, rank 0)
+
+def _median_ms(fn, reps=7, inner=20, warm=5):
+    """Median over `reps` of the device time of `inner` back-to-back calls,
+    divided by `inner` (CUDA events on the current stream; warm caches)."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(inner):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / inner)
+    return float(np.median(ts))
+
+
+def fft_comparator(dev, hbm, sizes=(512, 1024), beta=1e-2):
+    """The hand-written spectral operator (beta A)^-1 v on a vector field (a
+    row R2C pass, the column pass with the multiplier, a row C2R pass) timed
+    beside cuFFT doing the same operator (torch.fft.rfft2, multiply by the
+    same symbol, torch.fft.irfft2); both results are compared. GB/s counts the
+    operator's algorithmic bytes: both components read and written once
+    (16 B per grid point)."""
+    import torch
+    from paper_1604_02153_gb300 import inputs, regnk
+    rows = []
+    for n in sizes:
+        R = regnk.Registration(n, n, 4, beta, precond=regnk.REG_PC_REG)
+        v = torch.tensor(inputs.random_velocity(n, seed=9, kmax=n // 4, vmax=1.0)
+                         .astype(np.float32).ravel(), device=dev)
+        ours = torch.empty_like(v)
+        k1 = torch.fft.rfftfreq(n, d=1.0 / n, device=dev).to(torch.float64)
+        k2 = torch.fft.fftfreq(n, d=1.0 / n, device=dev).to(torch.float64)
+        gam = k2[:, None] ** 2 + k1[None, :] ** 2
+        gam[0, 0] = 1.0                     # the k = 0 weight of (beta A)^s is 1
+        sym = (1.0 / (beta * gam)).to(torch.float32)
+        V = v.view(2, n, n)
+
+        def run_ours():
+            R.spectral(regnk.REG_SPEC_REGPOW, v, ours, -1.0)
+
+        def run_cufft():
+            return torch.fft.irfft2(torch.fft.rfft2(V) * sym, s=(n, n))
+
+        t_ours = _median_ms(run_ours)
+        t_cu = _median_ms(run_cufft)
+        run_ours()
+        theirs = run_cufft()
+        torch.cuda.synchronize()
+        agree = float(torch.linalg.norm(ours.view(2, n, n) - theirs) / torch.linalg.norm(theirs))
+        by = 16.0 * n * n
+        rows.append({"grid": [n, n], "operator": "(beta A)^-1 on 2 fields",
+                     "ours_us": 1e3 * t_ours, "cufft_us": 1e3 * t_cu,
+                     "ours_gbs": by / (t_ours / 1e3) / 1e9, "cufft_gbs": by / (t_cu / 1e3) / 1e9,
+                     "ours_frac": by / (t_ours / 1e3) / 1e9 / hbm,
+                     "speedup_vs_cufft": t_cu / t_ours, "rel_diff": agree})
+        R.close()
+    return {"what": "hand-written FFT + multiplier (3 kernels) vs cuFFT R2C -> multiply -> C2R "
+                    "(torch.fft), median of 7 x 20 calls, CUDA events, warm caches",
+            "rows": rows}
+
+
+def measurement_c2(dev, hbm, l2_bytes):
+    """The 256^2 / 512^2 random-field configuration at nt = 4, 8, 16: GN
+    Hessian matvecs/s, state transport solves/s and objective+gradient
+    evaluations (state + adjoint) per second through the C ABI, CUDA events,
+    with the algorithmic bytes of each unit and whether the matvec's working
+    set fits the L2 cache (then the HBM fraction does not bound it)."""
+    import torch
+    from paper_1604_02153_gb300 import inputs, regnk
+    f = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device=dev)
+    out = []
+    for n in (256, 512):
+        m_T = inputs.random_field(n, seed=1, kmax=16)
+        vstar = inputs.random_velocity(n, seed=3, kmax=4, vmax=0.2)
+        for nt in (4, 8, 16):
+            R = regnk.Registration(n, n, nt, 1e-2)
+            m_T_d, v_d = f(m_T), f(vstar)
+            m_R_d = torch.empty(n * n, device=dev)
+            R.transport(v_d, m_T_d, m_R_d)
+            R.set_images(m_R_d, m_T_d)
+            u = f(inputs.random_velocity(n, seed=8, vmax=1.0))
+            H = torch.empty_like(u)
+            g = torch.empty_like(u)
+            R.objective_gradient(v_d, g)
+            m1 = torch.empty(n * n, device=dev)
+            N = n * n
+            t_mv = _median_ms(lambda: R.hessian_matvec(v_d, u, H))
+            t_tr = _median_ms(lambda: R.transport(v_d, m_T_d, m1))
+            # a new velocity every call (alternating), so the state solve is redone
+            va, vb = v_d, v_d * (1.0 + 1e-3)
+            flip = [0]
+
+            def grad():
+                flip[0] ^= 1
+                R.objective_gradient(va if flip[0] else vb, g)
+            t_gr = _median_ms(grad, reps=5, inner=10)
+            b_mv = 4.0 * N * (10 * nt + 16)                 # GN matvec, stored grad m_j
+            b_tr = 4.0 * N * (2 * nt + 4)                   # state transport solve
+            b_gr = 4.0 * N * (2 * nt + 4 * nt + 2 * (nt + 1) + 16)
+            # fields a matvec touches: dX, dY, v~, v~(X_D), div v, div v(Y_D),
+            # b~, two transported fields (14 N), G_1..G_nt and grad m_0..grad m_nt
+            ws = 4.0 * N * (16 + 4 * nt)
+            row = {"grid": [n, n], "nt": nt,
+                   "matvecs_per_s": 1e3 / t_mv, "transport_solves_per_s": 1e3 / t_tr,
+                   "gradients_per_s": 1e3 / t_gr,
+                   "matvec_us": 1e3 * t_mv, "matvec_algorithmic_bytes": b_mv,
+                   "roofline_matvec": {"achieved": b_mv / (t_mv / 1e3) / 1e9, "peak": hbm,
+                                       "unit": "GB/s",
+                                       "frac": b_mv / (t_mv / 1e3) / 1e9 / hbm,
+                                       "l2_resident": bool(ws < l2_bytes)},
+                   "roofline_transport": {"achieved": b_tr / (t_tr / 1e3) / 1e9,
+                                          "frac": b_tr / (t_tr / 1e3) / 1e9 / hbm},
+                   "roofline_gradient": {"achieved": b_gr / (t_gr / 1e3) / 1e9,
+                                         "frac": b_gr / (t_gr / 1e3) / 1e9 / hbm}}
+            out.append(row)
+            R.close()
+    return {"what": "random-field pairs (m_T k <= 16, v* k <= 4, max |v| 0.2, m_R = m_T "
+                    "transported by v*), beta 1e-2, spline SL, eager calls through the C ABI, "
+                    "median of CUDA-event timings; algorithmic bytes per unit: matvec "
+                    "4N(10nt+16), transport solve 4N(2nt+4), gradient 4N(8nt+18)",
+            "rows": out}
+
 
 def aggregate_ranks(dist, device, total_ms, matvecs, e2e_ms, e2e_matvecs):
     """Whole-job figures over replicas: time = max over ranks, work = sum.
@@ -307,12 +500,16 @@ BATCH_NT = 4
 BATCH_BETA = 1e-2
 
 
-def run_batch(args):
+def batch_comparison(args, samples, warmup):
     """64 independent problems, grids drawn (seed 200) from BATCH_SIZES^2,
     each the analytic template/velocity pair with m_R = m_T transported by
     v* (nt = 4, computed on the GPU), H1, beta = 1e-2, P_2L-CHEB(10) (coarse
     problem as --coarse-nt / --coarse-interp), solved to ||g||rel 1e-2 from
-    v = 0: concurrently (reg_batch) and one by one."""
+    v = 0: concurrently (reg_batch: one context and stream per problem, CUDA
+    graphs, FP64-accurate reductions), one by one on the same contexts, and
+    by the plain FP32 method one by one (FP32 reductions, no CUDA graphs,
+    plain launches). Wall time per batch between device synchronisations,
+    `samples` batches per arm after `warmup`."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -335,78 +532,72 @@ def run_batch(args):
         mR.append(cache[n][0])
         mT.append(cache[n][1])
     grids = [(n, n) for n in sizes]
-    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
-                        coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
-                                       "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp])
-    batch.set_images(mR, mT)
+    ci = {"lagrange": regnk.REG_INTERP_LAGRANGE, "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp]
     vs = [torch.zeros(2 * n * n, device=dev) for n in sizes]
-    for _ in range(max(1, args.warmup)):
-        for v in vs:
-            v.zero_()
-        batch.solve(vs, GTOL)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    mv_b = 0
-    for _ in range(args.steps):
-        for v in vs:
-            v.zero_()
-        infos = batch.solve(vs, GTOL)
-        mv_b += sum(i["matvecs"] for i in infos)
-    torch.cuda.synchronize()
-    t_batch = (time.perf_counter() - t0) / args.steps
-    # one by one: the same contexts, one host thread
-    t0 = time.perf_counter()
-    mv_s = 0
-    for _ in range(args.steps):
-        for v in vs:
-            v.zero_()
-        infos1 = batch.solve(vs, GTOL, threads=1)
-        mv_s += sum(i["matvecs"] for i in infos1)
-    torch.cuda.synchronize()
-    t_serial = (time.perf_counter() - t0) / args.steps
+
+    def arm(batch, threads):
+        for _ in range(max(1, warmup)):
+            for v in vs:
+                v.zero_()
+            batch.solve(vs, GTOL, threads=threads)
+        torch.cuda.synchronize()
+        times, mv, infos = [], 0, None
+        for _ in range(samples):
+            for v in vs:
+                v.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            infos = batch.solve(vs, GTOL, threads=threads)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            mv += sum(i["matvecs"] for i in infos)
+        return times, mv, infos
+
+    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
+                        coarse_interp=ci)
+    batch.set_images(mR, mT)
+    t_b, mv_b, infos = arm(batch, 0)
+    t_s, mv_s, infos1 = arm(batch, 1)        # one by one: the same contexts, one host thread
     batch.close()
-    # the plain FP32 method on the same problems: one by one, FP32 reductions,
-    # no CUDA graphs, plain launches (one warm-up pass, then timed)
     plain = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
-                        coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
-                                       "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
-                        precision=regnk.REG_PRECISION_FP32, use_graphs=0, programmatic_launch=0)
+                        coarse_interp=ci, precision=regnk.REG_PRECISION_FP32, use_graphs=0,
+                        programmatic_launch=0)
     plain.set_images(mR, mT)
-    for v in vs:
-        v.zero_()
-    plain.solve(vs, GTOL, threads=1)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    mv_p = 0
-    for _ in range(args.steps):
-        for v in vs:
-            v.zero_()
-        infos_p = plain.solve(vs, GTOL, threads=1)
-        mv_p += sum(i["matvecs"] for i in infos_p)
-    torch.cuda.synchronize()
-    t_plain = (time.perf_counter() - t0) / args.steps
+    t_p, mv_p, infos_p = arm(plain, 1)
     plain.close()
-    per_problem_serial = [i["seconds"] for i in infos1]
+
+    def stats(t):
+        return {"samples": len(t), "seconds_per_batch_mean": float(np.mean(t)),
+                "seconds_per_batch_min": float(np.min(t)), "seconds_per_batch_std": float(np.std(t))}
+    tb, ts, tp = float(np.mean(t_b)), float(np.mean(t_s)), float(np.mean(t_p))
+    return {"workload": f"{BATCH_B} problems, grids from {list(BATCH_SIZES)}^2 (seed 200), analytic "
+                        f"pair, nt={BATCH_NT}, H1, beta={BATCH_BETA}, P_2L CHEB(10) coarse nt="
+                        f"{args.coarse_nt or BATCH_NT} {args.coarse_interp}, ||g||rel 1e-2",
+            "sizes": sizes,
+            "concurrent": dict(stats(t_b), matvecs_per_s=mv_b / sum(t_b),
+                               mean_time_to_solution_s=float(np.mean([i["seconds"] for i in infos])),
+                               status=sorted(set(i["status_name"] for i in infos))),
+            "one_by_one": dict(stats(t_s), matvecs_per_s=mv_s / sum(t_s),
+                               mean_time_to_solution_s=float(np.mean([i["seconds"] for i in infos1]))),
+            "plain_fp32": dict(stats(t_p), matvecs_per_s=mv_p / sum(t_p),
+                               options="one by one, FP32 reductions, no CUDA graphs, plain launches",
+                               status=sorted(set(i["status_name"] for i in infos_p))),
+            "speedup_vs_one_by_one": ts / tb, "speedup_vs_plain_fp32": tp / tb,
+            "learned_warm_start": "not applied: the network's input grid is 256^2 and it was "
+                                  "trained on random-field pairs; the batch's analytic problems "
+                                  "converge from v = 0 in a few Newton steps"}
+
+
+def run_batch(args):
+    """The batch workload as its own bench line (--workload batch64)."""
+    c = batch_comparison(args, max(1, args.steps), args.warmup)
     line = {"metric": "aggregate Hessian matvecs/s, 64 independent problems of uneven size",
-            "value": mv_b / args.steps / t_batch, "unit": "matvecs/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_batch,
+            "value": c["concurrent"]["matvecs_per_s"], "unit": "matvecs/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * c["concurrent"]["seconds_per_batch_mean"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": f"{BATCH_B} problems, grids from {list(BATCH_SIZES)}^2 "
-                                   f"(seed 200), analytic pair, nt={BATCH_NT}, H1, "
-                                   f"beta={BATCH_BETA}, P_2L CHEB(10) coarse nt="
-                                   f"{args.coarse_nt or BATCH_NT} {args.coarse_interp}, ||g||rel 1e-2",
-                       "sizes": sizes},
-            "one_by_one": {"value": mv_s / args.steps / t_serial, "seconds_per_batch": t_serial,
-                           "mean_time_to_solution_s": float(np.mean(per_problem_serial))},
-            "concurrent": {"seconds_per_batch": t_batch,
-                           "mean_time_to_solution_s": float(np.mean([i["seconds"] for i in infos])),
-                           "status": sorted(set(i["status_name"] for i in infos))},
-            "speedup_vs_one_by_one": t_serial / t_batch,
-            "plain_fp32": {"options": "one by one, FP32 reductions, no CUDA graphs, plain launches",
-                           "seconds_per_batch": t_plain, "value": mv_p / args.steps / t_plain,
-                           "status": sorted(set(i["status_name"] for i in infos_p))},
-            "speedup_vs_plain_fp32": t_plain / t_batch}
+            "data": "synthetic", "config": {"workload": c["workload"], "sizes": c["sizes"]},
+            "comparison": c}
     print(json.dumps(line), flush=True)
 
 
@@ -586,36 +777,62 @@ def main():
         e2e_mv += s2["matvecs"]
     value, e2e_value = aggregate_ranks(dist, dev, total_ms, stats["matvecs"], e2e_ms, e2e_mv)
 
+    def solve_samples(K, **opts):
+        """K timed solves (CUDA events) of the workload with other options,
+        after one untimed solve; contexts are created and closed here."""
+        base = dict(persistent_matvec=args.persistent, incompressible=int(args.incompressible),
+                    hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
+                    coarse_nt=args.coarse_nt,
+                    coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
+                                   "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp])
+        base.update(pc_opts)
+        base.update(opts)
+        nonlocal R
+        Rx = regnk.Registration(n, n, NT, BETAS[0], **base)
+        Rx.set_images(d_mR, d_mT)
+        R, Rmain = Rx, R
+        try:
+            step(new_stats())
+            times, sp = [], new_stats()
+            for _ in range(K):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                step(sp)
+                e1.record(st)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+        finally:
+            R = Rmain
+            Rx.close()
+        return {"samples": K, "time_to_solution_s": float(np.mean(times)),
+                "time_to_solution_min_s": float(np.min(times)),
+                "time_to_solution_std_s": float(np.std(times)),
+                "matvecs_per_solve": sp["matvecs"] / K, "newton_iters_per_solve": sp["newton"] / K,
+                "coarse_matvecs_per_solve": sp["coarse_matvecs"] / K,
+                "solve_status": sorted(set(sp["status"])), "final_gnorm_rel": sp["gnorm_rel"]}
+
     # ---- the plain form of the same solve: FP32 reductions, no CUDA graphs,
-    # plain launches (cold start, as above); one warm-up and one timed solve
+    # plain launches, one launch per transport step (cold start, as above),
+    # as many timed solves as the chosen form
     plain = None
+    arms = None
     if not args.no_plain_form and rank == 0:
-        Rp = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
-                                incompressible=int(args.incompressible),
-                                hessian={"gn": regnk.REG_HESSIAN_GN,
-                                         "full": regnk.REG_HESSIAN_FULL}[args.hessian],
-                                coarse_nt=args.coarse_nt,
-                                coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
-                                               "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp],
-                                precision=regnk.REG_PRECISION_FP32, use_graphs=0,
-                                programmatic_launch=0, **pc_opts)
-        Rp.set_images(d_mR, d_mT)
-        R, Rmain = Rp, R
-        step(new_stats())
-        sp = new_stats()
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        step(sp)
-        e1.record(st)
-        torch.cuda.synchronize()
-        R = Rmain
-        Rp.close()
-        plain = {"options": "FP32 reductions, no CUDA graphs, plain launches, cold start",
-                 "time_to_solution_s": e0.elapsed_time(e1) / 1e3,
-                 "matvecs_per_solve": sp["matvecs"], "newton_iters_per_solve": sp["newton"],
-                 "solve_status": sorted(set(sp["status"])), "final_gnorm_rel": sp["gnorm_rel"]}
+        plain = solve_samples(args.steps, precision=regnk.REG_PRECISION_FP32, use_graphs=0,
+                              programmatic_launch=0, flow_matvec=0)
+        plain["options"] = ("FP32 reductions, no CUDA graphs, plain launches, per-step transport "
+                            "kernels, cold start")
+        plain["speedup_of_chosen_form"] = plain["time_to_solution_s"] / (total_ms / args.steps / 1e3)
+    if not args.no_arms and rank == 0 and args.precond == "2l-cheb":
+        # the coarse solver of P_2L: nested PCG(0.1 eta) against CHEB(10), and
+        # the coarse problem at the problem's nt and model (the library default)
+        arms = {"pcg_coarse": solve_samples(2, pc_solver=regnk.REG_PCSOLVER_PCG),
+                "coarse_problem_nt_and_spline": solve_samples(2, coarse_nt=0,
+                                                              coarse_interp=regnk.REG_INTERP_SPLINE)}
+        arms["pcg_coarse"]["what"] = "P_2L with nested PCG(0.1 eta) on the coarse grid"
+        arms["coarse_problem_nt_and_spline"]["what"] = (
+            "P_2L CHEB(10) with the coarse problem at nt = 8 and splines (library default)")
 
     # ---- roofline of the dominant kernel class (per grid level)
     dom = max(prof, key=lambda k: prof[k][0])
@@ -661,7 +878,16 @@ def main():
                 "roofline": roof,
                 "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
                 "plain_form": plain,
+                "solver_arms": arms,
                 "clocks": clocks.summary()}
+        if world == 1 and not args.no_extras:
+            l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+            line["fft_comparator"] = fft_comparator(dev, hbm)
+            line["config_256_512"] = measurement_c2(dev, hbm, l2)
+            # the batch workload's own coarse model (the problems' nt and splines)
+            bargs = argparse.Namespace(**vars(args))
+            bargs.coarse_nt, bargs.coarse_interp = 0, "spline"
+            line["batch64_chosen_vs_plain"] = batch_comparison(bargs, 5, 2)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian)
         if not args.no_warm_start:

@@ -14,9 +14,11 @@
 //                 restriction / prolongation), inverse FFT along x_2.
 //   3. rows_c2r : inverse FFT along x_1, two rows per complex line, with an
 //                 optional addend fused into the store.
-// Each transform is a radix-4 Stockham autosort FFT in shared memory (plus a
-// final radix-2 pass for odd log2 n), with FP32 twiddles rounded from an FP64
-// host table. Normalisation (1/N of the input grid) is folded into sigma.
+// Each transform is a Stockham autosort FFT in shared memory: radix-8
+// passes (8-point DFTs in registers), one radix-4 or radix-2 pass for the
+// rest of 2^L, and a radix-3 pass for lengths 3 * 2^L, with FP32 twiddles
+// rounded from an FP64 host table. Normalisation (1/N of the input grid) is
+// folded into sigma.
 #include "common.cuh"
 #include "kernels.h"
 

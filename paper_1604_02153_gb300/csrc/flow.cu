@@ -25,7 +25,8 @@
 //
 // Flags: one unsigned per tile, zeroed before the launch; a block publishes
 // step s after all its stores (block barrier, fence, release store) and a
-// waiting block polls its neighbours with acquire loads. Two field buffers
+// waiting block polls its neighbours with relaxed loads, then takes one
+// acquire fence. Two field buffers
 // suffice: a tile starts step s only after its neighbours finished step
 // s - 1, so nobody still reads the buffer it overwrites (step s - 2), and no
 // neighbour can run ahead to step s + 1 before this tile has published s.
@@ -45,10 +46,17 @@ constexpr int kFlowSP = 2;                  // adjacent points per thread
 constexpr int kFlowT = kFlowTX * kFlowTY / kFlowSP;   // 256 threads
 constexpr long long kFlowSpinLimit = 1LL << 21;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+// polls read the flags with relaxed loads (no ordering, no L1 invalidation
+// per poll); one acquire fence after the last successful poll orders the
+// block's later loads after the neighbours' release stores
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
@@ -99,7 +107,7 @@ __device__ __forceinline__ bool flow_wait(const FlowArgs& a, const Reach& r, int
     if (nb == tile) continue;
     const unsigned* f = a.flags + nb;
     long long spins = 0;
-    while (ld_acquire_u32(f) < target) {
+    while (ld_relaxed_u32(f) < target) {
       if (++spins > kFlowSpinLimit || *(volatile int*)a.err) {
         atomicExch(a.err, 1);
         ok = false;
@@ -108,6 +116,7 @@ __device__ __forceinline__ bool flow_wait(const FlowArgs& a, const Reach& r, int
       __nanosleep(32);
     }
   }
+  if (threadIdx.x < K) fence_acq_rel_gpu();
   return __syncthreads_or(!ok) == 0;
 }
 

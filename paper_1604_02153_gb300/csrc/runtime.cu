@@ -1584,7 +1584,7 @@ reg_status reg_default_options(reg_options* o) {
   o->hessian = 0;
   o->precision = REG_PRECISION_FP64;
   o->use_graphs = 1;
-  o->flow_matvec = 1;
+  o->flow_matvec = 0;
   return REG_OK;
 }
 
