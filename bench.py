@@ -95,6 +95,8 @@ def parse():
                     help="Gauss-Newton (the workload's) or full-Newton Hessian matvec")
     ap.add_argument("--incompressible", action="store_true",
                     help="the incompressible problem (div v = 0, K the Leray projection)")
+    ap.add_argument("--beta-w", type=float, default=0.0,
+                    help="near-incompressible problem: weight of ||div v||^2_H1 (0: off)")
     ap.add_argument("--no-plain-form", action="store_true",
                     help="skip the plain-form solve (FP32 reductions, no graphs)")
     ap.add_argument("--no-arms", action="store_true",
@@ -218,13 +220,14 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle timed on the host (cpu_baseline and --impl reference)
 
-def oracle_matvec_sample(incompressible=False, hessian="gn"):
+def oracle_matvec_sample(incompressible=False, hessian="gn", beta_w=0.0):
     """Set up the 1024^2 workload in the FP64 oracle (untimed state solve at
     a smooth velocity) and return a callable doing one GN Hessian matvec."""
     from oracle.problem import Problem
     from paper_1604_02153_gb300 import inputs
     m_R, m_T = inputs.ellipse_phantoms(N_GRID, seed=100)
-    P = Problem(m_R, m_T, NT, BETAS[-1], incompressible=incompressible, hessian=hessian)
+    P = Problem(m_R, m_T, NT, BETAS[-1], incompressible=incompressible, hessian=hessian,
+                beta_w=beta_w)
     P.state_solve(inputs.random_velocity(N_GRID, seed=7, vmax=0.2))
     if hessian == "full":
         P.adjoint_solve()          # the full-Newton matvec needs the adjoint history
@@ -236,8 +239,8 @@ def oracle_matvec_sample(incompressible=False, hessian="gn"):
 def _oracle_matvec_worker(args):
     """One oracle matvec in a worker process (set-up untimed); returns its
     start and end on the shared monotonic clock."""
-    incompressible, hessian = args
-    f = oracle_matvec_sample(incompressible, hessian)
+    incompressible, hessian, beta_w = args
+    f = oracle_matvec_sample(incompressible, hessian, beta_w)
     t0 = time.perf_counter()
     f()
     return t0, time.perf_counter()
@@ -275,11 +278,11 @@ def oracle_c1_solve():
                     "||g||rel 1e-2, one core"}
 
 
-def cpu_baseline(incompressible=False, hessian="gn", all_cores=True):
+def cpu_baseline(incompressible=False, hessian="gn", beta_w=0.0, all_cores=True):
     """The oracle on the host: one GN matvec at 1024^2 on one core, then one
     independent matvec per core at once (process pool started with spawn),
     and the 64^2 oracle full solve."""
-    f = oracle_matvec_sample(incompressible, hessian)
+    f = oracle_matvec_sample(incompressible, hessian, beta_w)
     t0 = time.perf_counter()
     f()
     dt = time.perf_counter() - t0
@@ -293,7 +296,7 @@ def cpu_baseline(incompressible=False, hessian="gn", all_cores=True):
         import multiprocessing as mp
         k = int(cpu["nproc"])
         with mp.get_context("spawn").Pool(k) as pool:
-            spans = pool.map(_oracle_matvec_worker, [(incompressible, hessian)] * k)
+            spans = pool.map(_oracle_matvec_worker, [(incompressible, hessian, beta_w)] * k)
         wall = max(e for _, e in spans) - min(s0 for s0, _ in spans)
         line["all_cores"] = {"value": k / wall, "unit": UNIT, "cores": k,
                              "sample": f"{k} independent {what}s at {N_GRID}^2, one per core "
@@ -306,7 +309,7 @@ def cpu_baseline(incompressible=False, hessian="gn", all_cores=True):
 def run_reference(args, rank):
     if rank != 0:
         return
-    f = oracle_matvec_sample(args.incompressible, args.hessian)
+    f = oracle_matvec_sample(args.incompressible, args.hessian, args.beta_w)
     for _ in range(args.warmup):
         f()
     t0 = time.perf_counter()
@@ -319,7 +322,7 @@ def run_reference(args, rank):
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible,
-                                  args.hessian),
+                                  args.hessian, args.beta_w),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"one FP64 oracle GN Hessian matvec per step at "
                                        f"{N_GRID}^2, nt={NT}"},
@@ -329,7 +332,7 @@ def run_reference(args, rank):
 
 
 def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", incompressible=False,
-                    hessian="gn"):
+                    hessian="gn", beta_w=0.0):
     pc = {"2l-cheb": "P_2L CHEB(10) 512^2 coarse", "2l-pcg": "P_2L PCG(1e-1) 512^2 coarse",
           "reg": "P_REG"}[precond]
     if coarse_nt and precond != "reg":
@@ -340,10 +343,11 @@ def workload_config(precond="2l-cheb", coarse_nt=0, coarse_interp="spline", inco
                         f"nt={NT}, H1, beta 1e-1->1e-2->1e-3, {pc}, "
                         f"||g||rel 1e-2, cubic B-spline SL"
                         + (", incompressible (K = Leray projection)" if incompressible else "")
+                        + (f", near-incompressible (beta_w = {beta_w:g})" if beta_w > 0 else "")
                         + (", full-Newton Hessian" if hessian == "full" else ""),
             "grid": [N_GRID, N_GRID], "nt": NT, "betas": list(BETAS), "gtol": GTOL,
             "precond": pc, "interp": "spline", "reg_norm": "H1",
-            "incompressible": bool(incompressible),
+            "incompressible": bool(incompressible), "beta_w": float(beta_w),
             "hessian": {"gn": "Gauss-Newton", "full": "full Newton"}[hessian],
             "l2": "flushed between steps (256 MB write, untimed)"}
 
@@ -371,13 +375,47 @@ def _median_ms(fn, reps=7, inner=20, warm=5):
     return float(np.median(ts))
 
 
+def _graph_ms(fn, inner=20, reps=7):
+    """Device time per call of fn: `inner` calls captured in one CUDA graph
+    (no host launch overhead in the timing), replayed `reps` times between
+    CUDA events; median. Falls back to eager calls if capture fails."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(inner):
+                fn()
+    except RuntimeError:
+        return _median_ms(fn, reps=reps, inner=inner), "eager"
+    st = torch.cuda.current_stream()
+    g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / inner)
+    return float(np.median(ts)), "graph"
+
+
 def fft_comparator(dev, hbm, sizes=(512, 1024), beta=1e-2):
     """The hand-written spectral operator (beta A)^-1 v on a vector field (a
     row R2C pass, the column pass with the multiplier, a row C2R pass) timed
     beside cuFFT doing the same operator (torch.fft.rfft2, multiply by the
-    same symbol, torch.fft.irfft2); both results are compared. GB/s counts the
-    operator's algorithmic bytes: both components read and written once
-    (16 B per grid point)."""
+    same symbol, torch.fft.irfft2); both results are compared. Each side runs
+    20 calls captured in one CUDA graph, so host launch overhead is not
+    timed. GB/s counts the operator's algorithmic bytes: both components read
+    and written once (16 B per grid point)."""
     import torch
     from paper_1604_02153_gb300 import inputs, regnk
     rows = []
@@ -392,28 +430,29 @@ def fft_comparator(dev, hbm, sizes=(512, 1024), beta=1e-2):
         gam[0, 0] = 1.0                     # the k = 0 weight of (beta A)^s is 1
         sym = (1.0 / (beta * gam)).to(torch.float32)
         V = v.view(2, n, n)
+        theirs = torch.empty(2, n, n, device=dev)
 
         def run_ours():
             R.spectral(regnk.REG_SPEC_REGPOW, v, ours, -1.0)
 
         def run_cufft():
-            return torch.fft.irfft2(torch.fft.rfft2(V) * sym, s=(n, n))
+            torch.fft.irfft2(torch.fft.rfft2(V) * sym, s=(n, n), out=theirs)
 
-        t_ours = _median_ms(run_ours)
-        t_cu = _median_ms(run_cufft)
+        t_ours, mode_o = _graph_ms(run_ours)
+        t_cu, mode_c = _graph_ms(run_cufft)
         run_ours()
-        theirs = run_cufft()
+        run_cufft()
         torch.cuda.synchronize()
         agree = float(torch.linalg.norm(ours.view(2, n, n) - theirs) / torch.linalg.norm(theirs))
         by = 16.0 * n * n
         rows.append({"grid": [n, n], "operator": "(beta A)^-1 on 2 fields",
-                     "ours_us": 1e3 * t_ours, "cufft_us": 1e3 * t_cu,
+                     "ours_us": 1e3 * t_ours, "cufft_us": 1e3 * t_cu, "timing": [mode_o, mode_c],
                      "ours_gbs": by / (t_ours / 1e3) / 1e9, "cufft_gbs": by / (t_cu / 1e3) / 1e9,
                      "ours_frac": by / (t_ours / 1e3) / 1e9 / hbm,
                      "speedup_vs_cufft": t_cu / t_ours, "rel_diff": agree})
         R.close()
     return {"what": "hand-written FFT + multiplier (3 kernels) vs cuFFT R2C -> multiply -> C2R "
-                    "(torch.fft), median of 7 x 20 calls, CUDA events, warm caches",
+                    "(torch.fft), 20 calls per CUDA graph, median of 7 replays, warm caches",
             "rows": rows}
 
 
@@ -696,7 +735,7 @@ def main():
                "2l-pcg": dict(precond=regnk.REG_PC_2L, pc_solver=regnk.REG_PCSOLVER_PCG),
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
     R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
-                           incompressible=int(args.incompressible),
+                           incompressible=int(args.incompressible), beta_w=args.beta_w,
                            hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
                            coarse_nt=args.coarse_nt,
                            coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
@@ -781,6 +820,7 @@ def main():
         """K timed solves (CUDA events) of the workload with other options,
         after one untimed solve; contexts are created and closed here."""
         base = dict(persistent_matvec=args.persistent, incompressible=int(args.incompressible),
+                    beta_w=args.beta_w,
                     hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
                     coarse_nt=args.coarse_nt,
                     coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
@@ -863,7 +903,7 @@ def main():
                 "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.precond, args.coarse_nt, args.coarse_interp, args.incompressible,
-                                  args.hessian),
+                                  args.hessian, args.beta_w),
                 "time_to_solution_s": total_ms / args.steps / 1e3,
                 "newton_iters_per_solve": stats["newton"] / args.steps,
                 "matvecs_per_solve": stats["matvecs"] / args.steps,
@@ -889,7 +929,7 @@ def main():
             bargs.coarse_nt, bargs.coarse_interp = 0, "spline"
             line["batch64_chosen_vs_plain"] = batch_comparison(bargs, 5, 2)
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian)
+            line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian, args.beta_w)
         if not args.no_warm_start:
             line["learned_warm_start"] = learned_warm_start(R, v, ok, dev)
         print(json.dumps(line), flush=True)

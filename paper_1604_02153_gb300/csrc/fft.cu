@@ -470,6 +470,43 @@ __device__ __forceinline__ float leray(int o, int c, float kd1, float kd2) {
   return d - (o == 0 ? kd1 : kd2) * (c == 0 ? kd1 : kd2) / q;
 }
 
+// (beta g)^s for the powers the solver uses (s = 1, -1, -1/2, 1/2), powf
+// otherwise
+__device__ __forceinline__ float pow_s(float x, float s) {
+  if (s == 1.f) return x;
+  if (s == -1.f) return 1.f / x;
+  if (s == -0.5f) return 1.f / sqrtf(x);
+  if (s == 0.5f) return sqrtf(x);
+  return powf(x, s);
+}
+
+// Entry (o, c) of R^s for the near-incompressible regularisation operator
+// R = beta A - beta_w grad (I - Lap) div (§2: the H1 norm of the mass
+// source w = div v, eq. varopt:regw, with w and p eliminated from the
+// control equations eq. control-v and eq. control-w of Appendix A). Per
+// wavenumber R is the symmetric 2 x 2 matrix a I + cw kd kd^T with
+// a = beta |k|^2p (k = 0 weight 1 unless s = 1), cw = beta_w (1 + |k|^2) and
+// kd the derivative wavenumbers (Nyquist zeroed): eigenvalue a + cw |kd|^2
+// along kd, a across it, so
+//     R^s = a^s I + ((a + cw |kd|^2)^s - a^s) kd kd^T / |kd|^2.
+__device__ __forceinline__ float regw(const ColArgs& a, int o, int c, int k1, int k2, float kd1,
+                                      float kd2) {
+  const float k2n = (float)k1 * (float)k1 + (float)k2 * (float)k2;
+  float g = k2n;
+  if (a.p == 2) g = k2n * k2n;
+  else if (a.p == 3) g = k2n * k2n * k2n;
+  const float d = (o == c) ? 1.f : 0.f;
+  const float ko = o == 0 ? kd1 : kd2, kc = c == 0 ? kd1 : kd2;
+  const float cw = a.beta_w * (1.f + k2n);
+  if (a.s == 1.f) return a.beta * g * d + cw * ko * kc;
+  if (g == 0.f) g = 1.f;
+  const float av = a.beta * g;
+  const float q = kd1 * kd1 + kd2 * kd2;
+  const float as = pow_s(av, a.s);
+  if (q == 0.f) return as * d;
+  return as * d + (pow_s(av + cw * q, a.s) - as) * ko * kc / q;
+}
+
 // sigma_{o,c}(k1, k2) as a complex number; k1 >= 0, k2 signed; n1, n2 of the
 // grid the Nyquist and filter conditions refer to.
 __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1, int k2) {
@@ -497,6 +534,12 @@ __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1,
     case SPOP_REGPOW_LERAY:
       return make_float2(regpow(a.beta, a.p, a.s, k1, k2) *
                              leray(o, c, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2),
+                         0.f);
+    case SPOP_REGW:
+      return make_float2(regw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
+    case SPOP_REGW_HIGH:
+      return make_float2(low ? 0.f : regw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1,
+                                          nyq2 ? 0.f : (float)k2),
                          0.f);
     default:
       return make_float2(0.f, 0.f);

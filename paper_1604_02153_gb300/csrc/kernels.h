@@ -64,6 +64,8 @@ enum SpecOp {
   SPOP_REGPOW_HIGH = 6,  // REGPOW restricted to the high band
   SPOP_LERAY = 7,        // 2 -> 2: delta_oc - k_o k_c / |k|^2 (Nyquist zeroed; 1 where |k| = 0)
   SPOP_REGPOW_LERAY = 8, // 2 -> 2: REGPOW times LERAY
+  SPOP_REGW = 9,         // 2 -> 2: R^s, R = beta A - beta_w grad (I - Lap) div (near-incompressible)
+  SPOP_REGW_HIGH = 10,   // 2 -> 2: REGW restricted to the high band
 };
 
 struct ColArgs {
@@ -79,6 +81,7 @@ struct ColArgs {
   float beta;
   int p;
   float s;
+  float beta_w;           // weight of the divergence norm (SPOP_REGW*)
   float scale;            // 1 / (n1_in n2_in)
   const float2* tw_in;    // twiddles for length n2_in
   const float2* tw_out;   // twiddles for length n2_out

@@ -103,6 +103,7 @@ struct reg_ctx {
   bool two_level = false;
   bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
   bool full_newton = false;      // full Hessian on the problem grid (P_2L's coarse stays GN)
+  double beta_w = 0;             // near-incompressible: weight of ||div v||^2_H1 (0: off)
   float* rk2a = nullptr;         // RK2A comparator workspace (9 N), allocated on first use
   float* defmap = nullptr;       // deformation map workspace (10 N), allocated on first use
   Level fine, coarse;
@@ -555,8 +556,9 @@ void join_side(reg_ctx* c) { check(c, cudaStreamWaitEvent(c->st, c->ev_join, 0),
 // ---------------------------------------------------------------------------
 // spectral operators
 
-ColArgs col_args(const Level& L, int op, double beta, int p, double s) {
+ColArgs col_args(const Level& L, int op, double beta, int p, double s, double beta_w = 0.0) {
   ColArgs a{};
+  a.beta_w = (float)beta_w;
   a.n1_in = a.n1_out = a.n1 = L.g.n1;
   a.n2_in = a.n2_out = a.n2 = L.g.n2;
   a.nk1_out = L.g.nk1;
@@ -586,7 +588,7 @@ void spectral(reg_ctx* c, Level& L, int op, double s, const float* in, int fin, 
       Prof P(c, REG_KC_FFT_ROWS, (double)ng * fin * (4.0 * g.N + 8.0 * g.spec));
       fft_rows_r2c(g.n1, g.n2, in + (size_t)g0 * fin * g.N, g.N, sin, g.spec, ng * fin, L.tw1, c->st);
     }
-    ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s);
+    ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s, c->beta_w);
     a.in = sin;
     a.in_fstride = g.spec;
     a.out = sout;
@@ -628,7 +630,7 @@ void spectral_fwd(reg_ctx* c, Level& L, int op, double s, const float* in, int f
     Prof P(c, REG_KC_FFT_ROWS, (double)groups * fin * (4.0 * g.N + 8.0 * g.spec));
     fft_rows_r2c(g.n1, g.n2, in, g.N, sin, g.spec, groups * fin, L.tw1, c->st);
   }
-  ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s);
+  ColArgs a = col_args(L, op, c->beta, c->opt.reg_norm, s, c->beta_w);
   a.in = sin;
   a.in_fstride = g.spec;
   a.out = sout;
@@ -655,9 +657,10 @@ void spectral_inv(reg_ctx* c, Level& L, int fin, int groups, float* out, int fou
 }
 
 // Spectral resampling of F fields from level A to level B (restriction or
-// prolongation) with multiplier op(s), plus an optional addend on B.
+// prolongation) with multiplier op(s), plus an optional addend on B; with
+// vec2, op maps vector fields to vector fields (F = 2, one group of two).
 void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in, int F,
-              float* out, const float* add) {
+              float* out, const float* add, bool vec2 = false) {
   LevelScope ls(c, A);
   float2* sin = c->fine.spec;
   float2* sout = c->fine.spec + (size_t)F * A.g.spec;
@@ -665,20 +668,20 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
     Prof P(c, REG_KC_FFT_ROWS, (double)F * (4.0 * A.g.N + 8.0 * A.g.spec));
     fft_rows_r2c(A.g.n1, A.g.n2, in, A.g.N, sin, A.g.spec, F, A.tw1, c->st);
   }
-  ColArgs a = col_args(A, op, c->beta, c->opt.reg_norm, s);
+  ColArgs a = col_args(A, op, c->beta, c->opt.reg_norm, s, c->beta_w);
   a.in = sin;
   a.in_fstride = A.g.spec;
   a.out = sout;
   a.out_fstride = B.g.spec;
-  a.nin = 1;
-  a.nout = 1;
+  a.nin = vec2 ? 2 : 1;
+  a.nout = vec2 ? 2 : 1;
   a.n1_out = B.g.n1;
   a.n2_out = B.g.n2;
   a.nk1_out = B.g.nk1;
   a.tw_out = B.tw2;
   {
     Prof P(c, REG_KC_FFT_COLS, (double)F * 8.0 * (A.g.spec + B.g.spec));
-    fft_cols(a, F, c->st);
+    fft_cols(a, vec2 ? F / 2 : F, c->st);
   }
   {
     Prof P(c, REG_KC_FFT_ROWS, (double)F * (8.0 * B.g.spec + (add ? 8.0 : 4.0) * B.g.N));
@@ -717,6 +720,50 @@ void resample_square(reg_ctx* c, int na, int nb, const float* in, int F, float* 
   fft_cols(a, F, c->st);
   fft_rows_c2r(nb, nb, sout, B.spec, out, B.N, nullptr, B.N, F, twiddles(c, nb), c->st);
   check_launch(c, "spectral resampling");
+}
+
+// The regularisation operator of the gradient and the Hessian and its
+// powers on a vector field: (beta A)^s componentwise, or R^s for the
+// near-incompressible problem, R = beta A - beta_w grad (I - Lap) div (a
+// 2 -> 2 multiplier). out = op(in) [+ add]; cheb as in spectral().
+void regop(reg_ctx* c, Level& L, double s, const float* in, float* out, const float* add,
+           const ChebEpilogue* cheb = nullptr) {
+  if (c->beta_w > 0.0)
+    spectral(c, L, SPOP_REGW, s, in, 2, 1, out, 2, add, cheb);
+  else
+    spectral(c, L, SPOP_REGPOW, s, in, 1, 2, out, 1, add, cheb);
+}
+
+// regop restricted to the high band |k_i| >= n_i / 4 (P_2L)
+void regop_high(reg_ctx* c, Level& L, double s, const float* in, float* out) {
+  if (c->beta_w > 0.0)
+    spectral(c, L, SPOP_REGW_HIGH, s, in, 2, 1, out, 2, nullptr);
+  else
+    spectral(c, L, SPOP_REGPOW_HIGH, s, in, 1, 2, out, 1, nullptr);
+}
+
+// regop in two halves (see spectral_fwd / spectral_inv)
+void regop_fwd(reg_ctx* c, Level& L, double s, const float* in) {
+  if (c->beta_w > 0.0)
+    spectral_fwd(c, L, SPOP_REGW, s, in, 2, 1, 2);
+  else
+    spectral_fwd(c, L, SPOP_REGPOW, s, in, 1, 2, 1);
+}
+
+void regop_inv(reg_ctx* c, Level& L, float* out, const float* add) {
+  if (c->beta_w > 0.0)
+    spectral_inv(c, L, 2, 1, out, 2, add);
+  else
+    spectral_inv(c, L, 1, 2, out, 1, add);
+}
+
+// restriction or prolongation of a vector field with regop's multiplier
+void resample_regop(reg_ctx* c, Level& A, Level& B, double s, const float* in, float* out,
+                    const float* add) {
+  if (c->beta_w > 0.0)
+    resample(c, A, B, SPOP_REGW, s, in, 2, out, add, true);
+  else
+    resample(c, A, B, SPOP_REGPOW, s, in, 2, out, add);
 }
 
 // interpolation coefficients of F consecutive fields (prefilter for the
@@ -867,7 +914,7 @@ void ensure_G(reg_ctx* c, Level& L) {
 double objective(reg_ctx* c, Level& L) {
   LevelScope ls(c, L);
   const size_t N = (size_t)L.g.N;
-  spectral(c, L, SPOP_REGPOW, 1.0, L.v, 1, 2, L.Av, 1, nullptr);
+  regop(c, L, 1.0, L.v, L.Av, nullptr);
   {
     Prof P(c, REG_KC_REDUCE, 8.0 * N);
     launch_sumsq_diff(L.m + L.nt * N, L.mR, (long long)N, c->partial, slot(c, S_J1), c->st);
@@ -1033,7 +1080,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       if (c->incompressible)
         finish_hessian_incompressible(c, L, vt, out);
       else
-        spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+        regop(c, L, 1.0, vt, out, L.b);
     }
     (void)N2;
     return;
@@ -1042,14 +1089,14 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   // stream while the transport steps (which use no FFT workspace) run here
   const bool fork = !data_only && !c->incompressible;
   if (L.flow) {
-    if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
+    if (fork) on_side(c, [&] { regop_fwd(c, L, 1.0, vt); });
     data_term_flow(c, L, vt, data_only ? out : L.b);
     if (data_only) return;
     if (c->incompressible) {
       finish_hessian_incompressible(c, L, vt, out);
     } else {
       join_side(c);
-      spectral_inv(c, L, 1, 2, out, 1, L.b);
+      regop_inv(c, L, out, L.b);
     }
     return;
   }
@@ -1058,7 +1105,10 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const int nt = L.nt;
   const float ht = L.ht;
   const int lg = L.lagrange;
-  if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
+  if (fork) on_side(c, [&] { regop_fwd(c, L, 1.0, vt); });
+  // the time integral b~ accumulates in the output itself when only the data
+  // term is wanted (out must not alias vt)
+  float* bacc = data_only ? out : L.b;
   float* mt = L.fA;
   float* mt2 = L.fB;
   float* lt = nullptr;
@@ -1078,7 +1128,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       Prof P(c, REG_KC_INCSTATE_STEP, (last ? 64.0 : 48.0) * N);
       launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, mt, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
                             L.gm + 2 * j * N, mt2, last ? L.gm + 2 * nt * N : nullptr,
-                            last ? L.b : nullptr, c->st);
+                            last ? bacc : nullptr, c->st);
       std::swap(mt, mt2);
     }
     if (nt >= 2) {   // mt holds lambda~_nt
@@ -1096,7 +1146,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
         Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 : (last ? 64.0 : 48.0)) * N);
         launch_incstate_step(L.tile_inc, gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
                              L.gm + 2 * j * N, mt2, j == 1, lg, c->st, j == 1 ? cvt : nullptr,
-                             last ? L.gm + 2 * nt * N : nullptr, last ? L.b : nullptr);
+                             last ? L.gm + 2 * nt * N : nullptr, last ? bacc : nullptr);
       }
       std::swap(mt, mt2);
     }
@@ -1111,7 +1161,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     lt = mt2;
     {
       Prof P(c, REG_KC_VECTOR, 24.0 * N);
-      launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, L.b, 1.f, c->st);
+      launch_adjoint_init(gd.n1, gd.n2, 0.5f * ht, nullptr, mt, L.gm + 2 * nt * N, lt, bacc, 1.f, c->st);
     }
     lt2 = mt;
   }
@@ -1120,7 +1170,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     if (L.fuse_w) {   // prefilter of lambda~_{j+1} inside the step kernel
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
       launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lt, L.dY, L.delta, L.delta_bar,
-                           L.gm + 2 * j * N, lt2, L.b, c->st);
+                           L.gm + 2 * j * N, lt2, bacc, c->st);
       std::swap(lt, lt2);
       continue;
     }
@@ -1128,18 +1178,18 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
       launch_adjoint_step(L.tile_adj, gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar,
-                          L.gm + 2 * j * N, lt2, L.b, lg, c->st);
+                          L.gm + 2 * j * N, lt2, bacc, lg, c->st);
     }
     std::swap(lt, lt2);
   }
   check_launch(c, "incremental adjoint");
   if (data_only) {
-    check(c, cudaMemcpyAsync(out, L.b, 2 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+    // b~ is already in out
   } else if (c->incompressible) {
     finish_hessian_incompressible(c, L, vt, out);
   } else {
     join_side(c);
-    spectral_inv(c, L, 1, 2, out, 1, L.b);
+    regop_inv(c, L, out, L.b);
   }
 }
 
@@ -1224,19 +1274,19 @@ void hessian_full(reg_ctx* c, Level& L, const float* vt, float* out) {
   if (c->incompressible)
     finish_hessian_incompressible(c, L, vt, out);
   else
-    spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
+    regop(c, L, 1.0, vt, out, L.b);
 }
 
 // (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse level.
 void coarse_split_op(reg_ctx* c, const float* s, float* out) {
   LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
-  spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
+  regop(c, C, -0.5, s, c->cu, nullptr);
   hessian_core(c, C, c->cu, c->cq, true);
   if (c->incompressible)
     spectral(c, C, SPOP_REGPOW_LERAY, -0.5, c->cq, 2, 1, out, 2, s);
   else
-    spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
+    regop(c, C, -0.5, c->cq, out, s);
   ++c->coarse_matvecs;
 }
 
@@ -1305,6 +1355,22 @@ void estimate_eigenvalues(reg_ctx* c) {
   const double kn = 0.25 * ((double)C.g.n1 * C.g.n1 + (double)C.g.n2 * C.g.n2);
   const double gmax = std::pow(kn, p);
   c->emin = 1.0 + 1.0 / (c->beta * gmax);
+  if (c->beta_w > 0.0) {
+    // largest eigenvalue of the 2 x 2 symbol of R over the coarse modes:
+    // beta |k|^2p, plus beta_w (1 + |k|^2) |kd|^2 along kd (derivative
+    // wavenumbers, Nyquist zeroed)
+    double lmax = 0.0;
+    for (int k1 = 0; k1 <= C.g.n1 / 2; ++k1)
+      for (int j2 = 0; j2 < C.g.n2; ++j2) {
+        const int k2 = signed_k(j2, C.g.n2);
+        const double ksq = (double)k1 * k1 + (double)k2 * k2;
+        double gam = std::pow(ksq, p);
+        if (gam == 0.0) gam = 1.0;
+        const double kd1 = (k1 == C.g.n1 / 2) ? 0.0 : k1, kd2 = (k2 == -C.g.n2 / 2) ? 0.0 : k2;
+        lmax = std::fmax(lmax, c->beta * gam + c->beta_w * (1.0 + ksq) * (kd1 * kd1 + kd2 * kd2));
+      }
+    c->emin = 1.0 + 1.0 / lmax;
+  }
   c->emax = rmax * c->opt.emax_safety;
   c->eig_beta = c->beta;
   c->have_eig = true;
@@ -1319,7 +1385,7 @@ void coarse_op_u(reg_ctx* c, const float* u, float* out, const ChebEpilogue* che
   if (c->incompressible)
     spectral(c, C, SPOP_REGPOW_LERAY, -1.0, c->cq, 2, 1, out, 2, u, cheb);
   else
-    spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u, cheb);
+    regop(c, C, -1.0, c->cq, out, u, cheb);
   ++c->coarse_matvecs;
 }
 
@@ -1414,7 +1480,7 @@ void precond(reg_ctx* c, const float* r, float* z) {
   Level& F = c->fine;
   const long long n = 2 * F.g.N;
   if (!c->two_level) {
-    spectral(c, F, SPOP_REGPOW, -1.0, r, 1, 2, z, 1, nullptr);
+    regop(c, F, -1.0, r, z, nullptr);
     return;
   }
   Level& C = c->coarse;
@@ -1424,20 +1490,20 @@ void precond(reg_ctx* c, const float* r, float* z) {
     // (beta A_c)^-1/2 (split operator) (beta A_c)^1/2 = I + (beta A_c)^-1 Q_c
     // with u = (beta A_c)^-1/2 s: right-hand side R (beta A)^-1 r, and the
     // result enters the prolongation without a further (beta A)^-1/2.
-    resample(c, F, C, SPOP_REGPOW, -1.0, r, 2, c->crhs, nullptr);
+    resample_regop(c, F, C, -1.0, r, c->crhs, nullptr);
     // high band (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1 on
     // the side stream, concurrently with the coarse solve (it uses only the
     // fine grid's FFT workspace, the coarse solve only the coarse grid's)
-    on_side(c, [&] { spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr); });
+    on_side(c, [&] { regop_high(c, F, -1.0, r, F.w1); });
     cheb(c, c->crhs, c->cx);
     join_side(c);
     resample(c, C, F, SPOP_SCALE, 0.0, c->cx, 2, z, F.w1);
     return;
   }
   // high band: (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1
-  spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
+  regop_high(c, F, -1.0, r, F.w1);
   // r' = (beta A)^-1/2 r; restricted low band -> crhs
-  resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
+  resample_regop(c, F, C, -0.5, r, c->crhs, nullptr);
   {
     LevelScope ls(c, C);
     auto A = [&](const float* s, float* o) { coarse_split_op(c, s, o); };
@@ -1448,7 +1514,7 @@ void precond(reg_ctx* c, const float* r, float* z) {
         c->opt.max_pcg, S_PCG_INNER);
   }
   // z = (beta A)^-1/2 P s_c + (beta A)^-1 H r
-  resample(c, C, F, SPOP_REGPOW, -0.5, c->cx, 2, z, F.w1);
+  resample_regop(c, C, F, -0.5, c->cx, z, F.w1);
   (void)n;
 }
 
@@ -1585,6 +1651,7 @@ reg_status reg_default_options(reg_options* o) {
   o->precision = REG_PRECISION_FP64;
   o->use_graphs = 1;
   o->flow_matvec = 0;
+  o->beta_w = 0.0;
   return REG_OK;
 }
 
@@ -1607,7 +1674,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.incompressible != 0 && o.incompressible != 1) || (o.hessian != 0 && o.hessian != 1) ||
       (o.hessian == 1 && o.persistent_matvec != 0) ||
       (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
-      (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1))
+      (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1) ||
+      !(o.beta_w >= 0.0 && o.beta_w < 1e30) || (o.beta_w > 0.0 && o.incompressible))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
@@ -1622,6 +1690,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
   c->two_level = (o.precond == REG_PC_2L);
   c->incompressible = (o.incompressible != 0);
   c->full_newton = (o.hessian == REG_HESSIAN_FULL);
+  c->beta_w = o.beta_w;
   c->graphs = (o.use_graphs != 0);
   c->fine.lagrange = (o.interp == REG_INTERP_LAGRANGE);
   c->coarse.lagrange = o.coarse_interp < 0 ? c->fine.lagrange : (o.coarse_interp == REG_INTERP_LAGRANGE);
@@ -1893,6 +1962,7 @@ reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* ou
       case REG_SPEC_LOWPASS: spectral(c, F, SPOP_LOWPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_HIGHPASS: spectral(c, F, SPOP_HIGHPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_LERAY: spectral(c, F, SPOP_LERAY, 0.0, in, 2, 1, out, 2, nullptr); break;
+      case REG_SPEC_REGOP: regop(c, F, s, in, out, nullptr); break;
       case REG_SPEC_PREFILTER:
         if (F.lagrange) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
         coefficients(c, F, in, 1, out);
@@ -1950,7 +2020,16 @@ reg_status reg_hessian_matvec(reg_ctx* c, const float* v, const float* vt, float
   return guarded(c, [&] {
     require_images(c);
     sync_velocity(c, v);
-    hessian(c, c->fine, vt, Hvt, false);
+    Level& F = c->fine;
+    ensure_G(c, F);
+    // the full-Newton matvec reads the adjoint history of this velocity
+    if (c->full_newton && !F.have_lam) {
+      objective(c, F);
+      gradient(c, F, F.w2);
+    }
+    // repeated calls with the same buffers replay the launch sequence as a
+    // CUDA graph, as inside the solver's PCG
+    graphed(c, graph_key(c, "mv", vt, Hvt), [&] { hessian_core(c, F, vt, Hvt, false); });
   });
 }
 

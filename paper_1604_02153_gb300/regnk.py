@@ -26,6 +26,7 @@ REG_HESSIAN_GN, REG_HESSIAN_FULL = 0, 1
 REG_PRECISION_FP64, REG_PRECISION_FP32 = 0, 1
 REG_SPEC_GRAD, REG_SPEC_DIV, REG_SPEC_REG, REG_SPEC_REGPOW = 0, 1, 2, 3
 REG_SPEC_LOWPASS, REG_SPEC_HIGHPASS, REG_SPEC_PREFILTER, REG_SPEC_LERAY = 4, 5, 6, 7
+REG_SPEC_REGOP = 8
 KERNEL_CLASSES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
                   "adjoint_step", "incstate_step", "reduce", "vector", "matvec"]
 
@@ -52,7 +53,8 @@ class reg_options(ctypes.Structure):
                 ("fused_transport", ctypes.c_int), ("coarse_nt", ctypes.c_int),
                 ("coarse_interp", ctypes.c_int), ("step_tile", ctypes.c_int), ("incompressible", ctypes.c_int),
                 ("hessian", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("flow_matvec", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("flow_matvec", ctypes.c_int),
+                ("beta_w", ctypes.c_double)]
 
 
 class reg_info(ctypes.Structure):

@@ -828,6 +828,141 @@ def test_incompressible_full_solve_64(regnk, pc):
 
 
 # ---------------------------------------------------------------------------
+# near-incompressible problem (beta_w > 0): R = beta A - beta_w grad (I - Lap) div
+
+def nearinc_lmax(n1, n2, beta, bw, p):
+    """Largest eigenvalue of R's 2 x 2 symbol (bound for the FP32 spectral
+    roundoff estimate)."""
+    return beta * gamma_max(n1, n2, p) + bw * (1.0 + gamma_max(n1, n2, 1)) * gamma_max(n1, n2, 1)
+
+
+@pytest.mark.parametrize("n1,n2,norm", [(128, 128, 1), (192, 96, 1), (128, 64, 2)])
+def test_nearinc_operator(regnk, n1, n2, norm):
+    """R^s (REG_SPEC_REGOP) against the oracle's mode-by-mode 2 x 2
+    eigendecomposition: element-wise 1e-5 where the symbol is bounded
+    (s < 0), the FP32 spectral bound with R's largest eigenvalue otherwise."""
+    beta, bw = 0.03, 0.5
+    R = regnk.Registration(n1, n2, 4, beta, reg_norm=norm, beta_w=bw, **pc_for(n1, n2))
+    v = inputs.random_velocity(n1, n2, seed=12, kmax=min(n1, n2) // 4, vmax=1.0)
+    vd = dev(v)
+    out = torch.empty(2 * n1 * n2, device="cuda")
+    lmax = nearinc_lmax(n1, n2, beta, bw, norm)
+    for s in (1.0, -1.0, -0.5, 0.5):
+        R.spectral(regnk.REG_SPEC_REGOP, vd, out, s)
+        ref = spectral.regop_power(v, beta, f"H{norm}", bw, s)
+        got = host(out, (2, n2, n1))
+        if s < 0:
+            assert rel(got, ref) < 1e-5, s
+        else:
+            assert within(got, ref, fp32_bound(n1, n2, lmax ** s, v)), s
+    R.close()
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+@pytest.mark.parametrize("bw", [0.05, 2.0])
+def test_nearinc_gradient_hessian(regnk, kind, bw):
+    """Objective, gradient and GN Hessian of the near-incompressible problem
+    against the oracle: J to 1e-5, the data terms g - R v and H u - R u to
+    the 1e-4 bar (R applied on each side), R v itself within its FP32
+    spectral bound."""
+    n1, n2, nt, beta = 128, 96, 4, 1e-2
+    interp = regnk.REG_INTERP_SPLINE if kind == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration(n1, n2, nt, beta, interp=interp, beta_w=bw, **pc_for(n1, n2))
+    m_R, m_T, v = (f32(a) for a in problem_data(n1, n2))
+    R.set_images(dev(m_R), dev(m_T))
+    P = Problem(m_R, m_T, nt, beta, kind=kind, beta_w=bw)
+    J_ref, g_ref = P.objective_gradient(v)
+    vd = dev(v)
+    g = torch.empty(2 * n1 * n2, device="cuda")
+    J = R.objective_gradient(vd, g)
+    Rv = torch.empty_like(g)
+    R.spectral(regnk.REG_SPEC_REGOP, vd, Rv, 1.0)
+    shape = (2, n2, n1)
+    Rv_ref = spectral.apply_regop(v, beta, "H1", bw)
+    assert abs(J - J_ref) / abs(J_ref) < 1e-5
+    assert within(host(Rv, shape), Rv_ref, fp32_bound(n1, n2, nearinc_lmax(n1, n2, beta, bw, 1), v))
+    assert rel(host(g, shape) - host(Rv, shape), g_ref - Rv_ref) < 1e-4
+    u = f32(inputs.random_velocity(n1, n2, seed=21, vmax=1.0))
+    ud = dev(u)
+    H = torch.empty_like(g)
+    R.hessian_matvec(vd, ud, H)
+    Ru = torch.empty_like(g)
+    R.spectral(regnk.REG_SPEC_REGOP, ud, Ru, 1.0)
+    H_ref = P.hessian_matvec(u)
+    assert rel(host(H, shape) - host(Ru, shape), H_ref - spectral.apply_regop(u, beta, "H1", bw)) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("pc,pcs", [("REG", "cheb"), ("2L", "cheb"), ("2L", "pcg")])
+def test_nearinc_preconditioners(regnk, pc, pcs):
+    """P_REG = R^-1 and P_2L (split with R^-1/2, CHEB(10) with the Lanczos
+    bounds or nested PCG) against the oracle; e_min from R's largest
+    eigenvalue on the coarse grid exactly."""
+    n, nt, beta, bw = 128, 4, 1e-2, 0.3
+    m_R, m_T, v = problem_data(n, n)
+    r = inputs.random_velocity(n, seed=27, vmax=1.0)
+    R = regnk.Registration(n, n, nt, beta, beta_w=bw,
+                           precond=regnk.REG_PC_REG if pc == "REG" else regnk.REG_PC_2L,
+                           pc_solver=regnk.REG_PCSOLVER_CHEB if pcs == "cheb" else regnk.REG_PCSOLVER_PCG)
+    R.set_images(dev(m_R), dev(m_T))
+    seed = regnk.default_options().lanczos_seed
+    nc = n // 2
+    lv0 = inputs.splitmix64_uniform(2 * nc * nc, seed).reshape(2, nc, nc)
+    S = Solver(Problem(m_R, m_T, nt, beta, beta_w=bw), precond=pc, pc_solver=pcs, lanczos_v0=lv0)
+    if pc == "2L":
+        emin, emax = R.eigen_bounds()
+        e = S.estimate_eigenvalues()
+        assert abs(emin - e["emin"]) < 1e-12 * e["emin"]
+        # Lanczos Ritz value: FP32 recurrence without reorthogonalisation
+        # (see test_eigen_bounds)
+        assert abs(emax - e["emax"]) / e["emax"] < 1e-3
+        S.eig = {"emin": emin, "emax": emax, "beta": beta}
+    R.objective_gradient(dev(v), None)
+    z = torch.empty(2 * n * n, device="cuda")
+    R.precond_apply(dev(r), z)
+    S.p.state_solve(v)
+    S.set_velocity_coarse(v)
+    assert rel(host(z, (2, n, n)), S.apply_precond(r)) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("pc", ["REG", "2L"])
+def test_nearinc_full_solve_64(regnk, pc):
+    """The 64^2 analytic problem solved with the divergence penalty: same
+    Newton iterations as the oracle, final velocity within 1e-3, J within
+    1e-4; and the penalty lowers the velocity's divergence against the
+    compressible solve."""
+    n, nt, beta, bw, gtol = 64, 4, 1e-2, 0.05, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = f32(Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar))
+    m_T = f32(m_T)
+    opts = {"precond": regnk.REG_PC_REG if pc == "REG" else regnk.REG_PC_2L}
+    R = regnk.Registration(n, n, nt, beta, beta_w=bw, **opts)
+    R.set_images(dev(m_R), dev(m_T))
+    v = torch.zeros(2 * n * n, device="cuda")
+    info = R.solve(v, gtol)
+    seed = regnk.default_options().lanczos_seed
+    lv0 = inputs.splitmix64_uniform(2 * (n // 2) ** 2, seed)
+    S = Solver(Problem(m_R, m_T, nt, beta, beta_w=bw), precond=pc, lanczos_v0=lv0)
+    vo, oinfo = S.solve(np.zeros((2, n, n)), gtol)
+    assert info["gnorm_rel"] <= gtol
+    assert info["newton_iters"] == oinfo["newton_iters"]
+    vg = host(v, (2, n, n))
+    assert rel(vg, vo) < 1e-3
+    assert abs(info["J"] - oinfo["J"]) / oinfo["J"] < 1e-4
+    Rc = regnk.Registration(n, n, nt, beta, **opts)
+    Rc.set_images(dev(m_R), dev(m_T))
+    vc = torch.zeros(2 * n * n, device="cuda")
+    Rc.solve(vc, gtol)
+    dw, dc = torch.empty(n * n, device="cuda"), torch.empty(n * n, device="cuda")
+    R.spectral(regnk.REG_SPEC_DIV, v, dw)
+    R.spectral(regnk.REG_SPEC_DIV, vc, dc)
+    assert float(torch.linalg.norm(dw)) < float(torch.linalg.norm(dc))
+    R.close()
+    Rc.close()
+
+
+# ---------------------------------------------------------------------------
 # full-Newton Hessian (eq. hessian-matvec with its lambda terms)
 
 @pytest.mark.parametrize("n1,n2,nt,kind,vmax,incomp", [(64, 64, 4, "spline", 0.2, 0),
