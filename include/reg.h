@@ -195,18 +195,24 @@ typedef struct {
   double beta_w;           /* 0 (default): no mass source. > 0: the near-
                               incompressible problem of §2: the mass source
                               w = div v (eq. icconstraint) carries the H1 norm
-                              of eq. varopt:regw with weight beta_w. w and its
-                              multiplier p are eliminated from the control
-                              equations (Appendix A, eq. control-v,
-                              eq. control-w: p = -beta_w (I - Lap) w), which
-                              adds -beta_w grad (I - Lap) div v to beta A v:
-                              R = beta A - beta_w grad (I - Lap) div replaces
-                              beta A in the objective (beta/2 <v, A v> +
-                              beta_w/2 ||div v||^2_H1), the gradient, the
-                              Hessian and the preconditioners (P_REG = R; P_2L
-                              splits with R^-1/2), as a 2 -> 2 spectral
-                              multiplier; K = I. Not with incompressible = 1;
-                              reg_set_beta changes beta only                 */
+                              of eq. varopt:regw with weight beta_w, so J adds
+                              beta_w/2 ||div v||^2_H1. Eliminating w and its
+                              multiplier p from the control equations
+                              (Appendix A, eq. control-v, eq. control-w:
+                              p = -beta_w (I - Lap) w) gives the reduced
+                              gradient g = beta A v + K[b] and Hessian
+                              beta A v~ + K[b~] of eq. control-elim and
+                              eq. hessian-matvec with K = beta A M^-1,
+                              M = beta A - beta_w grad (I - Lap) div: per
+                              wavenumber I - c kd kd^T/|kd|^2 with
+                              c = beta_w (1+|k|^2)|kd|^2 / (beta |k|^2p +
+                              beta_w (1+|k|^2)|kd|^2) in [0, 1) (kd the
+                              derivative wavenumbers), a bounded 2 -> 2
+                              multiplier like the Leray projection it tends to
+                              as beta_w grows. P_REG and P_2L keep beta A (the
+                              coarse operator carries K). Not with
+                              incompressible = 1; reg_set_beta changes beta
+                              only                                            */
 } reg_options;
 
 typedef struct {
@@ -301,13 +307,17 @@ reg_status reg_interpolate(reg_ctx* ctx, const float* u, const float* disp, floa
  *   REG_SPEC_PREFILTER scalar -> scalar  periodic cubic B-spline coefficients
  *   REG_SPEC_LERAY    vector -> vector   K = -grad Lap^-1 div + I (§3.1, w = 0):
  *                                        the divergence-free part
- *   REG_SPEC_REGOP    vector -> vector   R^s, the context's regularisation operator
- *                     (beta A, or beta A - beta_w grad (I - Lap) div with
- *                     reg_options.beta_w > 0), k = 0 weight -> 1 unless s = 1
+ *   REG_SPEC_REGOP    vector -> vector   R^s for the regularisation of J: beta A, or
+ *                     R = beta A - beta_w grad (I - Lap) div with
+ *                     reg_options.beta_w > 0 (J = ... + 1/2 <v, R v>), k = 0
+ *                     weight -> 1 unless s = 1
+ *   REG_SPEC_K        vector -> vector   the context's K of eq. control-elim: identity,
+ *                     Leray projection (incompressible) or the
+ *                     near-incompressible K (beta_w > 0)
  * `s` is used by REG_SPEC_REGPOW and REG_SPEC_REGOP. in and out must not alias. */
 enum { REG_SPEC_GRAD = 0, REG_SPEC_DIV = 1, REG_SPEC_REG = 2, REG_SPEC_REGPOW = 3,
        REG_SPEC_LOWPASS = 4, REG_SPEC_HIGHPASS = 5, REG_SPEC_PREFILTER = 6, REG_SPEC_LERAY = 7,
-       REG_SPEC_REGOP = 8 };
+       REG_SPEC_REGOP = 8, REG_SPEC_K = 9 };
 reg_status reg_spectral(reg_ctx* ctx, int op, double s, const float* in, float* out);
 
 /* Spectral restriction of a vector field from the context grid to the grid

@@ -9,10 +9,10 @@ Problem (§2, eq. varopt):
 compressible (w and its constraint omitted: K = I, the default),
 incompressible (div v = 0, w = 0: K = the Leray projection of §3.1,
 spectral.leray) or near-incompressible (beta_w > 0: the mass source
-w = div v of eq. icconstraint carries the H1 norm of eq. varopt:regw; with
-w and p eliminated from the control equations eq. control-v and
-eq. control-w, the term -beta_w grad (I - Lap) div v joins beta A v in the
-gradient and in the Hessian, spectral.reg_w_term, and K = I).
+w = div v of eq. icconstraint carries the H1 norm of eq. varopt:regw, so J
+adds beta_w/2 ||div v||^2_H1; with w and p eliminated from the control
+equations eq. control-v and eq. control-w, K = beta A M^-1 with
+M = beta A - beta_w grad (I - Lap) div, spectral.near_inc_K).
 
 Discrete inner product (§3.2, midpoint rule): <a, b>_h = h_1 h_2 sum a b.
 
@@ -80,17 +80,26 @@ class Problem:
 
     # -- bookkeeping --------------------------------------------------------
     def K(self, b, row):
-        """The operator K of eq. control-elim: identity (compressible) or the
-        Leray projection (incompressible, w = 0)."""
+        """The operator K of eq. control-elim: identity (compressible), the
+        Leray projection (incompressible, w = 0) or beta A M^-1
+        (near-incompressible)."""
+        if self.beta_w > 0.0:
+            self._count(row, ffts=2 * D)
+            return spectral.near_inc_K(b, self.beta, self.reg_norm, self.beta_w)
         if not self.incompressible:
             return b
         self._count(row, ffts=2 * D)
         return spectral.leray(b)
 
     def regop(self, v):
-        """beta A v, with -beta_w grad (I - Lap) div v added for the
-        near-incompressible problem (spectral.reg_w_term)."""
+        """R v for the regularisation term 1/2 <v, R v> of J: beta A v, with
+        -beta_w grad (I - Lap) div v added for the near-incompressible
+        problem (spectral.reg_w_term)."""
         return spectral.apply_regop(v, self.beta, self.reg_norm, self.beta_w)
+
+    def reg(self, v):
+        """beta A v, the first term of the reduced gradient and the Hessian."""
+        return spectral.apply_reg(v, self.beta, self.reg_norm)
 
     def _count(self, row, ffts=0, ips=0):
         c = self.counts.setdefault(row, [0, 0])
@@ -171,7 +180,16 @@ class Problem:
             gm = self._grad_m(j, "g")
             b += self.ht * self.w[j] * lam[j] * gm
         self._count("g", ffts=2 * D)
-        return self.regop(self.v) + self.K(b, "g")
+        self.b = b
+        return self.reg(self.v) + self.K(b, "g")
+
+    def gradient_l2(self, v=None):
+        """The L2 gradient of J, R v + int_0^1 lambda grad m dt (R of regop):
+        the derivative that finite differences of J check. For the
+        compressible and near-incompressible problems the reduced gradient
+        of eq. control-elim is K of it: K M = beta A and K b = K[b]."""
+        self.gradient(v)
+        return self.regop(self.v) + self.b
 
     def objective_gradient(self, v):
         J = self.objective(v)
@@ -219,7 +237,7 @@ class Problem:
             self._count(row, ips=1)
             bt = bt + self.ht * self.w[j] * lt * self._grad_m(j, row)
         self._count(row, ffts=2 * D)
-        return self.regop(vt) + self.K(bt, row)
+        return self.reg(vt) + self.K(bt, row)
 
     def _hessian_matvec_full(self, vt, row):
         """Full-Newton matvec (eq. hessian-matvec with its lambda terms).
@@ -271,11 +289,11 @@ class Problem:
             self._count(row, ips=2)
             bt = bt + ht * self.w[j] * (lt * self._grad_m(j, row) + lam[j] * grad_mt(j))
         self._count(row, ffts=2 * D)
-        return self.regop(vt) + self.K(bt, row)
+        return self.reg(vt) + self.K(bt, row)
 
     def data_matvec(self, vt):
         """Data term Q v~ = H v~ - beta A v~ (eq. reduced-space-kkt-system)."""
-        return self.hessian_matvec(vt) - self.regop(np.asarray(vt, dtype=np.float64))
+        return self.hessian_matvec(vt) - self.reg(np.asarray(vt, dtype=np.float64))
 
     # -- Appendix C reference counts -----------------------------------------
     @staticmethod

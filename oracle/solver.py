@@ -72,11 +72,7 @@ class Solver:
     # -- preconditioners -----------------------------------------------------
     @staticmethod
     def reg_pow(p, x, s):
-        """(beta A)^s, or R^s for the near-incompressible regularisation
-        operator R of Problem.regop (P_REG = R: the operator the paper's
-        preconditioner inverts is the regularisation of the Hessian)."""
-        if p.beta_w > 0.0:
-            return spectral.regop_power(x, p.beta, p.reg_norm, p.beta_w, s)
+        """(beta A)^s (eq. reg-precond)."""
         return spectral.reg_power(x, p.beta, p.reg_norm, s)
 
     def precond_reg(self, r):
@@ -103,13 +99,7 @@ class Solver:
         _, rmax, _ = krylov.lanczos_extremal(self.coarse_split_op, v0, self.lanczos_steps)
         gam = spectral.reg_symbol(c.n1, c.n2, c.reg_norm).astype(np.float64)
         gam[0, 0] = 1.0
-        # largest eigenvalue of the regularisation operator's 2 x 2 symbol per
-        # mode: beta gamma, plus beta_w (1 + |k|^2) |kd|^2 along kd (near-
-        # incompressible; kd the derivative wavenumbers)
-        K1, K2 = spectral._k_grids(c.n1, c.n2, zero_nyquist=True)
-        ksq = spectral.reg_symbol(c.n1, c.n2, "H1").astype(np.float64)
-        lmax = c.beta * gam + c.beta_w * (1.0 + ksq) * (K1 * K1 + K2 * K2)
-        emin = float(np.min(1.0 + 1.0 / lmax))
+        emin = float(np.min(1.0 + 1.0 / (c.beta * gam)))
         self.eig = {"emin": emin, "emax": rmax * self.emax_safety, "beta": c.beta}
         return self.eig
 

@@ -173,6 +173,24 @@ def regop_power(v, beta, reg_norm, beta_w, s):
     return np.stack([ifft2_real(oh[..., 0]), ifft2_real(oh[..., 1])])
 
 
+def near_inc_K(b, beta, reg_norm, beta_w):
+    """The operator K of eq. control-elim for the near-incompressible problem.
+
+    With w = div v and p = -beta_w (I - Lap) w eliminated (see reg_w_term)
+    the control equation reads M v + b = 0 with
+    M = beta A - beta_w grad (I - Lap) div (apply_regop). Writing it in the
+    paper's form beta A v + K[b] = 0 (eq. control-elim) gives
+    K = beta A M^-1 on every mode where M is invertible; on the mean (k = 0),
+    where both regularisation terms vanish, K is the identity (as the Leray
+    projection is there). Written out as that definition: M^-1 b by
+    regop_power(s = -1), then beta A of it, plus the mean of b.
+    """
+    n2, n1 = b.shape[1:]
+    x = regop_power(b, beta, reg_norm, beta_w, -1.0)
+    out = apply_reg(x, beta, reg_norm)
+    return out + b.mean(axis=(1, 2), keepdims=True)
+
+
 def reg_power(v, beta, reg_norm, s):
     """(beta * A)^s componentwise, with the zero weight at k = 0 replaced by 1.
 

@@ -507,6 +507,28 @@ __device__ __forceinline__ float regw(const ColArgs& a, int o, int c, int k1, in
   return as * d + (pow_s(av + cw * q, a.s) - as) * ko * kc / q;
 }
 
+// Entry (o, c) of the near-incompressible K of the reduced gradient and the
+// Hessian (eq. control-elim, eq. hessian-matvec). Eliminating w and p from
+// the control equations gives beta A v - beta_w grad (I - Lap) div v + b = 0,
+// i.e. beta A v + K[b] = 0 with K = beta A M^-1, M = beta A - beta_w grad
+// (I - Lap) div; per wavenumber M = a I + cw kd kd^T (see regw), so
+//     K = I - c kd kd^T / |kd|^2,  c = cw |kd|^2 / (a + cw |kd|^2)  in [0, 1)
+// (the identity where kd = 0; c -> 1 is the Leray projection, c -> 0 the
+// identity). Its symbol is bounded, unlike M's.
+__device__ __forceinline__ float kw(const ColArgs& a, int o, int c, int k1, int k2, float kd1,
+                                    float kd2) {
+  const float q = kd1 * kd1 + kd2 * kd2;
+  const float d = (o == c) ? 1.f : 0.f;
+  if (q == 0.f) return d;
+  const float k2n = (float)k1 * (float)k1 + (float)k2 * (float)k2;
+  float g = k2n;
+  if (a.p == 2) g = k2n * k2n;
+  else if (a.p == 3) g = k2n * k2n * k2n;
+  const float cq = a.beta_w * (1.f + k2n) * q;
+  const float w = cq / (a.beta * g + cq);
+  return d - w * (o == 0 ? kd1 : kd2) * (c == 0 ? kd1 : kd2) / q;
+}
+
 // sigma_{o,c}(k1, k2) as a complex number; k1 >= 0, k2 signed; n1, n2 of the
 // grid the Nyquist and filter conditions refer to.
 __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1, int k2) {
@@ -537,9 +559,11 @@ __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1,
                          0.f);
     case SPOP_REGW:
       return make_float2(regw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
-    case SPOP_REGW_HIGH:
-      return make_float2(low ? 0.f : regw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1,
-                                          nyq2 ? 0.f : (float)k2),
+    case SPOP_KW:
+      return make_float2(kw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
+    case SPOP_REGPOW_KW:
+      return make_float2(regpow(a.beta, a.p, a.s, k1, k2) *
+                             kw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2),
                          0.f);
     default:
       return make_float2(0.f, 0.f);

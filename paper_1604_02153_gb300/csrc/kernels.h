@@ -65,7 +65,8 @@ enum SpecOp {
   SPOP_LERAY = 7,        // 2 -> 2: delta_oc - k_o k_c / |k|^2 (Nyquist zeroed; 1 where |k| = 0)
   SPOP_REGPOW_LERAY = 8, // 2 -> 2: REGPOW times LERAY
   SPOP_REGW = 9,         // 2 -> 2: R^s, R = beta A - beta_w grad (I - Lap) div (near-incompressible)
-  SPOP_REGW_HIGH = 10,   // 2 -> 2: REGW restricted to the high band
+  SPOP_KW = 10,          // 2 -> 2: near-incompressible K = I - c(k) kd kd^T / |kd|^2
+  SPOP_REGPOW_KW = 11,   // 2 -> 2: REGPOW times KW
 };
 
 struct ColArgs {
@@ -166,6 +167,16 @@ void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev,
                            float* out, const float* gm_nt, float* b, cudaStream_t st);
 void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstride, int F,
                          const float* disp, float* out, cudaStream_t st);
+// Two cubic Lagrange time steps per launch (transport.cu), for velocities
+// whose displacements are at most 6 cells (pair_steps_ok): incremental state
+// steps j, j + 1 and incremental adjoint steps j, j - 1.
+bool pair_steps_ok(double max_disp_cells);
+void launch_incstate_pair(int n1, int n2, float ht, int j, const float* m_prev, const float* dX,
+                          const float* vt, float* vtD, const float* G, const float* gm, float* out,
+                          int last, float* b, cudaStream_t st);
+void launch_adjoint_pair(int n1, int n2, float ht, int j, const float* lam_next, const float* dY,
+                         const float* delta, const float* delta_bar, const float* gm,
+                         float* lam_out, float* b, cudaStream_t st);
 void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
                                  const float* G1, const float* gm1, float* vtD, float* out,
                                  cudaStream_t st);

@@ -73,6 +73,7 @@ struct Level {
   bool have_div = false;    // delta, delta_bar, dY valid for v
   bool have_G = false;      // G valid for v
   int fuse_w = 0;           // box width of the fused prefilter+step kernels for v (0: off)
+  bool pair = false;        // cubic Lagrange: two incremental steps per launch for v
   bool lagrange = false;    // interpolation model of this level (cubic Lagrange or spline)
   int tile_adj = kDefaultStepTile;   // tile shapes of k_adjoint_step and k_incstate_step
   int tile_inc = kDefaultStepTile;
@@ -103,7 +104,8 @@ struct reg_ctx {
   bool two_level = false;
   bool incompressible = false;   // K = Leray projection (w = 0) instead of K = I
   bool full_newton = false;      // full Hessian on the problem grid (P_2L's coarse stays GN)
-  double beta_w = 0;             // near-incompressible: weight of ||div v||^2_H1 (0: off)
+  double beta_w = 0;             // near-incompressible: weight of ||div v||^2_H1 (0: off;
+                                 // then K is the multiplier of has_K below)
   float* rk2a = nullptr;         // RK2A comparator workspace (9 N), allocated on first use
   float* defmap = nullptr;       // deformation map workspace (10 N), allocated on first use
   Level fine, coarse;
@@ -533,7 +535,8 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
 // (a launch sequence recorded for one width must not replay for another)
 std::string graph_key(const reg_ctx* c, const char* what, const void* a, const void* b) {
   char buf[128];
-  snprintf(buf, sizeof buf, "%s:%p:%p:%d:%d", what, a, b, c->fine.fuse_w, c->coarse.fuse_w);
+  snprintf(buf, sizeof buf, "%s:%p:%p:%d:%d:%d:%d", what, a, b, c->fine.fuse_w, c->coarse.fuse_w,
+           (int)c->fine.pair, (int)c->coarse.pair);
   return buf;
 }
 
@@ -657,10 +660,9 @@ void spectral_inv(reg_ctx* c, Level& L, int fin, int groups, float* out, int fou
 }
 
 // Spectral resampling of F fields from level A to level B (restriction or
-// prolongation) with multiplier op(s), plus an optional addend on B; with
-// vec2, op maps vector fields to vector fields (F = 2, one group of two).
+// prolongation) with multiplier op(s), plus an optional addend on B.
 void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in, int F,
-              float* out, const float* add, bool vec2 = false) {
+              float* out, const float* add) {
   LevelScope ls(c, A);
   float2* sin = c->fine.spec;
   float2* sout = c->fine.spec + (size_t)F * A.g.spec;
@@ -673,15 +675,15 @@ void resample(reg_ctx* c, Level& A, Level& B, int op, double s, const float* in,
   a.in_fstride = A.g.spec;
   a.out = sout;
   a.out_fstride = B.g.spec;
-  a.nin = vec2 ? 2 : 1;
-  a.nout = vec2 ? 2 : 1;
+  a.nin = 1;
+  a.nout = 1;
   a.n1_out = B.g.n1;
   a.n2_out = B.g.n2;
   a.nk1_out = B.g.nk1;
   a.tw_out = B.tw2;
   {
     Prof P(c, REG_KC_FFT_COLS, (double)F * 8.0 * (A.g.spec + B.g.spec));
-    fft_cols(a, vec2 ? F / 2 : F, c->st);
+    fft_cols(a, F, c->st);
   }
   {
     Prof P(c, REG_KC_FFT_ROWS, (double)F * (8.0 * B.g.spec + (add ? 8.0 : 4.0) * B.g.N));
@@ -722,49 +724,18 @@ void resample_square(reg_ctx* c, int na, int nb, const float* in, int F, float* 
   check_launch(c, "spectral resampling");
 }
 
-// The regularisation operator of the gradient and the Hessian and its
-// powers on a vector field: (beta A)^s componentwise, or R^s for the
-// near-incompressible problem, R = beta A - beta_w grad (I - Lap) div (a
-// 2 -> 2 multiplier). out = op(in) [+ add]; cheb as in spectral().
-void regop(reg_ctx* c, Level& L, double s, const float* in, float* out, const float* add,
-           const ChebEpilogue* cheb = nullptr) {
-  if (c->beta_w > 0.0)
-    spectral(c, L, SPOP_REGW, s, in, 2, 1, out, 2, add, cheb);
-  else
-    spectral(c, L, SPOP_REGPOW, s, in, 1, 2, out, 1, add, cheb);
-}
-
-// regop restricted to the high band |k_i| >= n_i / 4 (P_2L)
-void regop_high(reg_ctx* c, Level& L, double s, const float* in, float* out) {
-  if (c->beta_w > 0.0)
-    spectral(c, L, SPOP_REGW_HIGH, s, in, 2, 1, out, 2, nullptr);
-  else
-    spectral(c, L, SPOP_REGPOW_HIGH, s, in, 1, 2, out, 1, nullptr);
-}
-
-// regop in two halves (see spectral_fwd / spectral_inv)
-void regop_fwd(reg_ctx* c, Level& L, double s, const float* in) {
-  if (c->beta_w > 0.0)
-    spectral_fwd(c, L, SPOP_REGW, s, in, 2, 1, 2);
-  else
-    spectral_fwd(c, L, SPOP_REGPOW, s, in, 1, 2, 1);
-}
-
-void regop_inv(reg_ctx* c, Level& L, float* out, const float* add) {
-  if (c->beta_w > 0.0)
-    spectral_inv(c, L, 2, 1, out, 2, add);
-  else
-    spectral_inv(c, L, 1, 2, out, 1, add);
-}
-
-// restriction or prolongation of a vector field with regop's multiplier
-void resample_regop(reg_ctx* c, Level& A, Level& B, double s, const float* in, float* out,
-                    const float* add) {
-  if (c->beta_w > 0.0)
-    resample(c, A, B, SPOP_REGW, s, in, 2, out, add, true);
-  else
-    resample(c, A, B, SPOP_REGPOW, s, in, 2, out, add);
-}
+// The operator K of the reduced gradient and the Hessian (eq. control-elim,
+// eq. hessian-matvec): the identity (compressible), the Leray projection
+// (incompressible, w = 0, §3.1) or, for the near-incompressible problem, the
+// 2 -> 2 multiplier I - c(k) kd kd^T / |kd|^2 with
+// c = beta_w (1 + |k|^2) |kd|^2 / (beta |k|^2p + beta_w (1 + |k|^2) |kd|^2)
+// that eliminating the mass source w = div v and its multiplier p from the
+// control equations of Appendix A leaves (beta A M^-1, M = beta A -
+// beta_w grad (I - Lap) div); and K times (beta A)^s for P_2L's coarse
+// operator.
+bool has_K(const reg_ctx* c) { return c->incompressible || c->beta_w > 0.0; }
+int K_op(const reg_ctx* c) { return c->incompressible ? SPOP_LERAY : SPOP_KW; }
+int regpow_K_op(const reg_ctx* c) { return c->incompressible ? SPOP_REGPOW_LERAY : SPOP_REGPOW_KW; }
 
 // interpolation coefficients of F consecutive fields (prefilter for the
 // spline model; the samples themselves for Lagrange)
@@ -842,6 +813,18 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
     read_slots(c, S_DX, 2);
     L.fuse_w = fused_box_width(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
   }
+  // cubic Lagrange: two incremental steps per launch when every stencil of
+  // the second step stays within the first step's extended tile
+  L.pair = false;
+  if (L.lagrange && c->opt.fused_transport && !L.flow) {
+    {
+      Prof P(c, REG_KC_REDUCE, 16.0 * N);
+      launch_maxabs(L.dX, 2 * (long long)N, c->partialf, slot(c, S_DX), c->st);
+      launch_maxabs(L.dY, 2 * (long long)N, c->partialf, slot(c, S_DY), c->st);
+    }
+    read_slots(c, S_DX, 2);
+    L.pair = pair_steps_ok(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
+  }
   if (L.flow) {   // the flow kernel reads its tiles' reach from these (no host sync)
     Prof P(c, REG_KC_REDUCE, 16.0 * N);
     launch_maxabs(L.dX, 2 * (long long)N, c->partialf, L.flow_dmax, c->st);
@@ -914,14 +897,22 @@ void ensure_G(reg_ctx* c, Level& L) {
 double objective(reg_ctx* c, Level& L) {
   LevelScope ls(c, L);
   const size_t N = (size_t)L.g.N;
-  regop(c, L, 1.0, L.v, L.Av, nullptr);
+  spectral(c, L, SPOP_REGPOW, 1.0, L.v, 1, 2, L.Av, 1, nullptr);
+  // near-incompressible: the regularisation of J is beta/2 <v, A v> +
+  // beta_w/2 ||div v||^2_H1 = 1/2 <v, R v> (R the 2 -> 2 multiplier
+  // beta A - beta_w grad (I - Lap) div); the gradient keeps beta A v
+  const float* Rv = L.Av;
+  if (c->beta_w > 0.0) {
+    spectral(c, L, SPOP_REGW, 1.0, L.v, 2, 1, L.w1, 2, nullptr);
+    Rv = L.w1;
+  }
   {
     Prof P(c, REG_KC_REDUCE, 8.0 * N);
     launch_sumsq_diff(L.m + L.nt * N, L.mR, (long long)N, c->partial, slot(c, S_J1), c->st);
   }
   {
     Prof P(c, REG_KC_REDUCE, 16.0 * N);
-    launch_dot(L.v, L.Av, 2 * (long long)N, c->partial, slot(c, S_J2), c->st);
+    launch_dot(L.v, Rv, 2 * (long long)N, c->partial, slot(c, S_J2), c->st);
   }
   check_launch(c, "objective");
   read_slots(c, S_J1, 2);
@@ -966,8 +957,8 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   }
   check_launch(c, "adjoint solve");
   if (hist) L.have_lam = true;
-  if (c->incompressible) {   // g = beta A v + K[b], K the Leray projection
-    spectral(c, L, SPOP_LERAY, 0.0, L.b, 2, 1, g_out, 2, L.Av);
+  if (has_K(c)) {   // g = beta A v + K[b]
+    spectral(c, L, K_op(c), 0.0, L.b, 2, 1, g_out, 2, L.Av);
   } else {
     Prof P(c, REG_KC_VECTOR, 24.0 * N);
     launch_lincomb(2 * (long long)N, 1.f, L.Av, 1.f, L.b, g_out, c->st);
@@ -975,11 +966,11 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
   check_launch(c, "gradient");
 }
 
-// beta A v~ + K[b~] for the incompressible problem (K the Leray projection),
-// with b~ in L.b; L.w1 holds beta A v~ in between.
-void finish_hessian_incompressible(reg_ctx* c, Level& L, const float* vt, float* out) {
+// beta A v~ + K[b~] with K the Leray projection (incompressible) or the
+// near-incompressible K, with b~ in L.b; L.w1 holds beta A v~ in between.
+void finish_hessian_K(reg_ctx* c, Level& L, const float* vt, float* out) {
   spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, L.w1, 1, nullptr);
-  spectral(c, L, SPOP_LERAY, 0.0, L.b, 2, 1, out, 2, L.w1);
+  spectral(c, L, K_op(c), 0.0, L.b, 2, 1, out, 2, L.w1);
 }
 
 // Gauss-Newton Hessian matvec (eq. hessian-matvec, GN); data_only drops beta A vt.
@@ -1077,26 +1068,26 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       data_term_persistent(c, L, vt, out);
     } else {
       data_term_persistent(c, L, vt, L.b);
-      if (c->incompressible)
-        finish_hessian_incompressible(c, L, vt, out);
+      if (has_K(c))
+        finish_hessian_K(c, L, vt, out);
       else
-        regop(c, L, 1.0, vt, out, L.b);
+        spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
     }
     (void)N2;
     return;
   }
   // beta A v~: its forward transforms depend only on v~ and run on the side
   // stream while the transport steps (which use no FFT workspace) run here
-  const bool fork = !data_only && !c->incompressible;
+  const bool fork = !data_only && !has_K(c);
   if (L.flow) {
-    if (fork) on_side(c, [&] { regop_fwd(c, L, 1.0, vt); });
+    if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
     data_term_flow(c, L, vt, data_only ? out : L.b);
     if (data_only) return;
-    if (c->incompressible) {
-      finish_hessian_incompressible(c, L, vt, out);
+    if (has_K(c)) {
+      finish_hessian_K(c, L, vt, out);
     } else {
       join_side(c);
-      regop_inv(c, L, out, L.b);
+      spectral_inv(c, L, 1, 2, out, 1, L.b);
     }
     return;
   }
@@ -1105,7 +1096,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   const int nt = L.nt;
   const float ht = L.ht;
   const int lg = L.lagrange;
-  if (fork) on_side(c, [&] { regop_fwd(c, L, 1.0, vt); });
+  if (fork) on_side(c, [&] { spectral_fwd(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, 1); });
   // the time integral b~ accumulates in the output itself when only the data
   // term is wanted (out must not alias vt)
   float* bacc = data_only ? out : L.b;
@@ -1139,7 +1130,16 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     // v~(X_D) is gathered by the first step; the last one (nt >= 2) also
     // writes lambda~_nt and starts b~
     const float* cvt = coefficients(c, L, vt, 2, L.c2);
-    for (int j = 1; j <= nt; ++j) {
+    for (int j = 1; j <= nt;) {
+      if (L.pair && j + 1 <= nt) {   // steps j and j + 1 in one launch (cubic Lagrange)
+        const bool last = (j + 1 == nt);
+        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 + 48.0 : 96.0 + (last ? 16.0 : 0.0)) * N);
+        launch_incstate_pair(gd.n1, gd.n2, ht, j, mt, L.dX, vt, L.vtD, L.G, L.gm, mt2, last ? 1 : 0,
+                             bacc, c->st);
+        std::swap(mt, mt2);
+        j += 2;
+        continue;
+      }
       const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
       const bool last = (j == nt && nt >= 2);
       {
@@ -1149,6 +1149,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
                              last ? L.gm + 2 * nt * N : nullptr, last ? bacc : nullptr);
       }
       std::swap(mt, mt2);
+      ++j;
     }
     if (nt >= 2) {   // mt holds lambda~_nt
       lt = mt;
@@ -1174,6 +1175,14 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       std::swap(lt, lt2);
       continue;
     }
+    if (L.pair && j >= 1) {   // steps j and j - 1 in one launch (cubic Lagrange)
+      Prof P(c, REG_KC_ADJOINT_STEP, 96.0 * N);
+      launch_adjoint_pair(gd.n1, gd.n2, ht, j, lt, L.dY, L.delta, L.delta_bar, L.gm, lt2, bacc,
+                          c->st);
+      std::swap(lt, lt2);
+      --j;
+      continue;
+    }
     const float* cl = coefficients(c, L, lt, 1, L.coef);
     {
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
@@ -1185,11 +1194,11 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   check_launch(c, "incremental adjoint");
   if (data_only) {
     // b~ is already in out
-  } else if (c->incompressible) {
-    finish_hessian_incompressible(c, L, vt, out);
+  } else if (has_K(c)) {
+    finish_hessian_K(c, L, vt, out);
   } else {
     join_side(c);
-    regop_inv(c, L, out, L.b);
+    spectral_inv(c, L, 1, 2, out, 1, L.b);
   }
 }
 
@@ -1271,22 +1280,22 @@ void hessian_full(reg_ctx* c, Level& L, const float* vt, float* out) {
     std::swap(lt, lt2);
   }
   check_launch(c, "incremental adjoint (full Newton)");
-  if (c->incompressible)
-    finish_hessian_incompressible(c, L, vt, out);
+  if (has_K(c))
+    finish_hessian_K(c, L, vt, out);
   else
-    regop(c, L, 1.0, vt, out, L.b);
+    spectral(c, L, SPOP_REGPOW, 1.0, vt, 1, 2, out, 1, L.b);
 }
 
 // (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse level.
 void coarse_split_op(reg_ctx* c, const float* s, float* out) {
   LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
-  regop(c, C, -0.5, s, c->cu, nullptr);
+  spectral(c, C, SPOP_REGPOW, -0.5, s, 1, 2, c->cu, 1, nullptr);
   hessian_core(c, C, c->cu, c->cq, true);
-  if (c->incompressible)
-    spectral(c, C, SPOP_REGPOW_LERAY, -0.5, c->cq, 2, 1, out, 2, s);
+  if (has_K(c))
+    spectral(c, C, regpow_K_op(c), -0.5, c->cq, 2, 1, out, 2, s);
   else
-    regop(c, C, -0.5, c->cq, out, s);
+    spectral(c, C, SPOP_REGPOW, -0.5, c->cq, 1, 2, out, 1, s);
   ++c->coarse_matvecs;
 }
 
@@ -1355,22 +1364,6 @@ void estimate_eigenvalues(reg_ctx* c) {
   const double kn = 0.25 * ((double)C.g.n1 * C.g.n1 + (double)C.g.n2 * C.g.n2);
   const double gmax = std::pow(kn, p);
   c->emin = 1.0 + 1.0 / (c->beta * gmax);
-  if (c->beta_w > 0.0) {
-    // largest eigenvalue of the 2 x 2 symbol of R over the coarse modes:
-    // beta |k|^2p, plus beta_w (1 + |k|^2) |kd|^2 along kd (derivative
-    // wavenumbers, Nyquist zeroed)
-    double lmax = 0.0;
-    for (int k1 = 0; k1 <= C.g.n1 / 2; ++k1)
-      for (int j2 = 0; j2 < C.g.n2; ++j2) {
-        const int k2 = signed_k(j2, C.g.n2);
-        const double ksq = (double)k1 * k1 + (double)k2 * k2;
-        double gam = std::pow(ksq, p);
-        if (gam == 0.0) gam = 1.0;
-        const double kd1 = (k1 == C.g.n1 / 2) ? 0.0 : k1, kd2 = (k2 == -C.g.n2 / 2) ? 0.0 : k2;
-        lmax = std::fmax(lmax, c->beta * gam + c->beta_w * (1.0 + ksq) * (kd1 * kd1 + kd2 * kd2));
-      }
-    c->emin = 1.0 + 1.0 / lmax;
-  }
   c->emax = rmax * c->opt.emax_safety;
   c->eig_beta = c->beta;
   c->have_eig = true;
@@ -1382,10 +1375,10 @@ void coarse_op_u(reg_ctx* c, const float* u, float* out, const ChebEpilogue* che
   LevelScope ls(c, c->coarse);
   Level& C = c->coarse;
   hessian_core(c, C, u, c->cq, true);
-  if (c->incompressible)
-    spectral(c, C, SPOP_REGPOW_LERAY, -1.0, c->cq, 2, 1, out, 2, u, cheb);
+  if (has_K(c))
+    spectral(c, C, regpow_K_op(c), -1.0, c->cq, 2, 1, out, 2, u, cheb);
   else
-    regop(c, C, -1.0, c->cq, out, u, cheb);
+    spectral(c, C, SPOP_REGPOW, -1.0, c->cq, 1, 2, out, 1, u, cheb);
   ++c->coarse_matvecs;
 }
 
@@ -1480,7 +1473,7 @@ void precond(reg_ctx* c, const float* r, float* z) {
   Level& F = c->fine;
   const long long n = 2 * F.g.N;
   if (!c->two_level) {
-    regop(c, F, -1.0, r, z, nullptr);
+    spectral(c, F, SPOP_REGPOW, -1.0, r, 1, 2, z, 1, nullptr);
     return;
   }
   Level& C = c->coarse;
@@ -1490,20 +1483,20 @@ void precond(reg_ctx* c, const float* r, float* z) {
     // (beta A_c)^-1/2 (split operator) (beta A_c)^1/2 = I + (beta A_c)^-1 Q_c
     // with u = (beta A_c)^-1/2 s: right-hand side R (beta A)^-1 r, and the
     // result enters the prolongation without a further (beta A)^-1/2.
-    resample_regop(c, F, C, -1.0, r, c->crhs, nullptr);
+    resample(c, F, C, SPOP_REGPOW, -1.0, r, 2, c->crhs, nullptr);
     // high band (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1 on
     // the side stream, concurrently with the coarse solve (it uses only the
     // fine grid's FFT workspace, the coarse solve only the coarse grid's)
-    on_side(c, [&] { regop_high(c, F, -1.0, r, F.w1); });
+    on_side(c, [&] { spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr); });
     cheb(c, c->crhs, c->cx);
     join_side(c);
     resample(c, C, F, SPOP_SCALE, 0.0, c->cx, 2, z, F.w1);
     return;
   }
   // high band: (beta A)^-1/2 H (beta A)^-1/2 r = (beta A)^-1 H r -> F.w1
-  regop_high(c, F, -1.0, r, F.w1);
+  spectral(c, F, SPOP_REGPOW_HIGH, -1.0, r, 1, 2, F.w1, 1, nullptr);
   // r' = (beta A)^-1/2 r; restricted low band -> crhs
-  resample_regop(c, F, C, -0.5, r, c->crhs, nullptr);
+  resample(c, F, C, SPOP_REGPOW, -0.5, r, 2, c->crhs, nullptr);
   {
     LevelScope ls(c, C);
     auto A = [&](const float* s, float* o) { coarse_split_op(c, s, o); };
@@ -1514,7 +1507,7 @@ void precond(reg_ctx* c, const float* r, float* z) {
         c->opt.max_pcg, S_PCG_INNER);
   }
   // z = (beta A)^-1/2 P s_c + (beta A)^-1 H r
-  resample_regop(c, C, F, -0.5, c->cx, z, F.w1);
+  resample(c, C, F, SPOP_REGPOW, -0.5, c->cx, 2, z, F.w1);
   (void)n;
 }
 
@@ -1962,7 +1955,19 @@ reg_status reg_spectral(reg_ctx* c, int op, double s, const float* in, float* ou
       case REG_SPEC_LOWPASS: spectral(c, F, SPOP_LOWPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_HIGHPASS: spectral(c, F, SPOP_HIGHPASS, 0.0, in, 1, 2, out, 1, nullptr); break;
       case REG_SPEC_LERAY: spectral(c, F, SPOP_LERAY, 0.0, in, 2, 1, out, 2, nullptr); break;
-      case REG_SPEC_REGOP: regop(c, F, s, in, out, nullptr); break;
+      case REG_SPEC_REGOP:
+        if (c->beta_w > 0.0)
+          spectral(c, F, SPOP_REGW, s, in, 2, 1, out, 2, nullptr);
+        else
+          spectral(c, F, SPOP_REGPOW, s, in, 1, 2, out, 1, nullptr);
+        break;
+      case REG_SPEC_K:
+        if (has_K(c))
+          spectral(c, F, K_op(c), 0.0, in, 2, 1, out, 2, nullptr);
+        else
+          check(c, cudaMemcpyAsync(out, in, 2 * (size_t)F.g.N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->st), "copy");
+        break;
       case REG_SPEC_PREFILTER:
         if (F.lagrange) fail(c, REG_EINVAL, "PREFILTER needs the spline model");
         coefficients(c, F, in, 1, out);

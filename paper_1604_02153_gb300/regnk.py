@@ -26,7 +26,7 @@ REG_HESSIAN_GN, REG_HESSIAN_FULL = 0, 1
 REG_PRECISION_FP64, REG_PRECISION_FP32 = 0, 1
 REG_SPEC_GRAD, REG_SPEC_DIV, REG_SPEC_REG, REG_SPEC_REGPOW = 0, 1, 2, 3
 REG_SPEC_LOWPASS, REG_SPEC_HIGHPASS, REG_SPEC_PREFILTER, REG_SPEC_LERAY = 4, 5, 6, 7
-REG_SPEC_REGOP = 8
+REG_SPEC_REGOP, REG_SPEC_K = 8, 9
 KERNEL_CLASSES = ["fft_rows", "fft_cols", "prefilter", "departure", "gather",
                   "adjoint_step", "incstate_step", "reduce", "vector", "matvec"]
 

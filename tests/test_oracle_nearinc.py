@@ -1,10 +1,13 @@
 """Pins of the oracle's near-incompressible variant (CPU only).
 
 The mass source w of eq. varopt carries the H1 norm of eq. varopt:regw and is
-tied to the velocity by eq. icconstraint, w = div v; eliminating w and p from
-the control equations (Appendix A, eq. control-v, eq. control-w) adds
--beta_w grad (I - Lap) div v to beta A v in the gradient and the Hessian.
-Pinned here against what the mathematics fixes:
+tied to the velocity by eq. icconstraint, w = div v, so J adds
+beta_w/2 ||div v||^2_H1 = 1/2 <v, (M - beta A) v>,
+M = beta A - beta_w grad (I - Lap) div. Eliminating w and p from the control
+equations (Appendix A, eq. control-v, eq. control-w) leaves M v + b = 0,
+which in the paper's form beta A v + K[b] = 0 (eq. control-elim) fixes
+K = beta A M^-1 (identity on the mean). Pinned here against what the
+mathematics fixes:
 * trigonometric polynomials: on a gradient field grad phi the term is
   beta_w |k|^2 (1 + |k|^2) grad phi exactly, on a divergence-free field zero;
 * it is the derivative of the quadratic (beta_w / 2) ||div v||^2_{H1} written
@@ -12,8 +15,12 @@ Pinned here against what the mathematics fixes:
   differences (exact for a quadratic up to roundoff), symmetric and positive;
 * the powers R^s of R = beta A - beta_w grad (I - Lap) div: R^-1 R = I,
   R^1/2 R^1/2 = R, and R^s = (beta A)^s for beta_w = 0;
-* the problem's gradient matches central differences of its objective, and
-  beta_w = 0 is the compressible problem;
+* K on trigonometric polynomials: a gradient field scales by
+  beta |k|^2 / (beta |k|^2 + beta_w (1 + |k|^2) |k|^2), a divergence-free
+  field is kept; K tends to the Leray projection as beta_w grows;
+* the L2 gradient R v + b matches central differences of J, the reduced
+  gradient and Hessian are K of the L2 ones, and beta_w = 0 is the
+  compressible problem;
 * beta_w -> infinity: the solution approaches the incompressible (Leray)
   solution and its divergence vanishes.
 """
@@ -109,7 +116,7 @@ def test_gradient_against_finite_differences():
     slopes = {}
     for bw in (0.5, 0.0):
         P = Problem(m_R, m_T, nt, 1e-2, beta_w=bw)
-        _, g = P.objective_gradient(v)
+        g = P.gradient_l2(v)
         d = P.inner(g, dv)
         fd = (P.objective(v + eps * dv) - P.objective(v - eps * dv)) / (2 * eps)
         slopes[bw] = (fd, d)
@@ -132,17 +139,47 @@ def test_gradient_against_finite_differences():
     assert Jc == J0 and np.array_equal(gc, g0)
 
 
-def test_hessian_adds_the_divergence_term():
+def test_K_on_trigonometric_polynomials_and_limits():
+    n1, n2, beta = 32, 24, 0.02
+    X1, X2 = _grid(n1, n2)
+    a, b = 3, -2
+    k2 = a * a + b * b
+    gphi = np.stack([-a * np.sin(a * X1 + b * X2), -b * np.sin(a * X1 + b * X2)])
+    rot = np.stack([5 * np.cos(2 * X1 - 5 * X2), 2 * np.cos(2 * X1 - 5 * X2)])
+    for bw in (1e-3, 0.1, 10.0):
+        scale = beta * k2 / (beta * k2 + bw * (1 + k2) * k2)
+        Kg = spectral.near_inc_K(gphi, beta, "H1", bw)
+        assert np.max(np.abs(Kg - scale * gphi)) < 1e-11, bw
+        assert np.max(np.abs(spectral.near_inc_K(rot, beta, "H1", bw) - rot)) < 1e-11, bw
+    # limits on a random field (modes |k| <= 8): identity as beta_w -> 0, the
+    # Leray projection as beta_w -> infinity, with the gap 1 - c of the
+    # gradient part below beta |k|^2 / (beta_w (1 + |k|^2) |k|^2) <= beta / (2 beta_w)
+    w = inputs.random_velocity(n1, n2, seed=8, kmax=8, vmax=1.0)
+    assert np.max(np.abs(spectral.near_inc_K(w, beta, "H1", 1e-12) - w)) < 1e-8
+    gaps = [np.linalg.norm(spectral.near_inc_K(w, beta, "H1", bw) - spectral.leray(w))
+            / np.linalg.norm(w) for bw in (1.0, 1e3)]
+    assert gaps[1] < beta / (2 * 1e3) and gaps[0] > 100 * gaps[1], gaps
+
+
+def test_reduced_gradient_and_hessian_are_K_of_the_L2_ones():
     n, nt = 32, 8
     m_R, m_T = _pair(n, nt)
     v = inputs.random_velocity(n, seed=3, vmax=0.1)
     u = inputs.random_velocity(n, seed=7, kmax=6, vmax=1.0)
+    bw = 2.0
+    P = Problem(m_R, m_T, nt, 1e-2, beta_w=bw)
+    J, g = P.objective_gradient(v)
+    gl2 = P.gradient_l2(v)
+    K = lambda x: spectral.near_inc_K(x, P.beta, "H1", bw)
+    assert np.max(np.abs(g - K(gl2))) < 1e-10 * np.max(np.abs(g))
+    # the Hessian: beta A u + K[b~] = K[R u + b~]
     Pc = Problem(m_R, m_T, nt, 1e-2)
-    Pw = Problem(m_R, m_T, nt, 1e-2, beta_w=2.0)
     Pc.state_solve(v)
-    Pw.state_solve(v)
-    diff = Pw.hessian_matvec(u) - Pc.hessian_matvec(u)
-    assert np.max(np.abs(diff - spectral.reg_w_term(u, 2.0))) < 1e-11 * np.max(np.abs(diff))
+    P.state_solve(v)
+    bt = Pc.hessian_matvec(u) - spectral.apply_reg(u, 1e-2, "H1")   # K = I: the data term b~
+    Hu = P.hessian_matvec(u)
+    assert np.max(np.abs(Hu - K(spectral.apply_regop(u, 1e-2, "H1", bw) + bt))) < 1e-10 * np.max(np.abs(Hu))
+    assert np.max(np.abs(Hu - (spectral.apply_reg(u, 1e-2, "H1") + bt))) > 1e-3 * np.max(np.abs(Hu))
 
 
 def test_large_beta_w_approaches_the_incompressible_solution():
