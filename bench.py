@@ -95,6 +95,9 @@ def parse():
                     help="Gauss-Newton (the workload's) or full-Newton Hessian matvec")
     ap.add_argument("--incompressible", action="store_true",
                     help="the incompressible problem (div v = 0, K the Leray projection)")
+    ap.add_argument("--graph-pdl", type=int, choices=[0, 1, 2], default=0,
+                    help="programmatic edges inside the library's CUDA graphs: 0 none, 1 coarse "
+                         "grid, 2 all")
     ap.add_argument("--beta-w", type=float, default=0.0,
                     help="near-incompressible problem: weight of ||div v||^2_H1 (0: off)")
     ap.add_argument("--no-plain-form", action="store_true",
@@ -736,6 +739,7 @@ def main():
                "reg": dict(precond=regnk.REG_PC_REG)}[args.precond]
     R = regnk.Registration(n, n, NT, BETAS[0], persistent_matvec=args.persistent,
                            incompressible=int(args.incompressible), beta_w=args.beta_w,
+                           graph_pdl=args.graph_pdl,
                            hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
                            coarse_nt=args.coarse_nt,
                            coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,
@@ -820,7 +824,7 @@ def main():
         """K timed solves (CUDA events) of the workload with other options,
         after one untimed solve; contexts are created and closed here."""
         base = dict(persistent_matvec=args.persistent, incompressible=int(args.incompressible),
-                    beta_w=args.beta_w,
+                    beta_w=args.beta_w, graph_pdl=args.graph_pdl,
                     hessian={"gn": regnk.REG_HESSIAN_GN, "full": regnk.REG_HESSIAN_FULL}[args.hessian],
                     coarse_nt=args.coarse_nt,
                     coarse_interp={"lagrange": regnk.REG_INTERP_LAGRANGE,

@@ -213,6 +213,13 @@ typedef struct {
                               coarse operator carries K). Not with
                               incompressible = 1; reg_set_beta changes beta
                               only                                            */
+  int graph_pdl;           /* launches captured into the library's CUDA graphs:
+                              0 (default) plain kernel-to-kernel edges; 1 the
+                              coarse grid's launches carry programmatic stream
+                              serialisation (see programmatic_launch), so a
+                              kernel's blocks are scheduled while its
+                              predecessor drains; 2 every launch does. Results
+                              are identical                                   */
 } reg_options;
 
 typedef struct {

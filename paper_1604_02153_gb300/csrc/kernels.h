@@ -32,6 +32,11 @@ __device__ __forceinline__ void pdl_enter() {
 // Attribute value for launches from this host thread (reg_options
 // .programmatic_launch of the context being driven; 1 outside a context).
 extern thread_local int t_programmatic_launch;
+// While a CUDA graph is captured: 1 = launches on the coarse grid level carry
+// the attribute as well, 2 = all launches do (reg_options.graph_pdl); the
+// level of the launches being issued (0 problem grid, 1 coarse grid).
+extern thread_local int t_graph_pdl;
+extern thread_local int t_level;
 // 1 while a context with reg_options.precision = REG_PRECISION_FP32 runs a
 // call: inner products and squared norms accumulate in plain FP32
 extern thread_local int t_plain_fp32_reduce;
@@ -46,7 +51,8 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = t_programmatic_launch ? 1 : 0;
+  attr[0].val.programmaticStreamSerializationAllowed =
+      (t_programmatic_launch || t_graph_pdl == 2 || (t_graph_pdl == 1 && t_level == 1)) ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
@@ -167,16 +173,6 @@ void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev,
                            float* out, const float* gm_nt, float* b, cudaStream_t st);
 void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstride, int F,
                          const float* disp, float* out, cudaStream_t st);
-// Two cubic Lagrange time steps per launch (transport.cu), for velocities
-// whose displacements are at most 6 cells (pair_steps_ok): incremental state
-// steps j, j + 1 and incremental adjoint steps j, j - 1.
-bool pair_steps_ok(double max_disp_cells);
-void launch_incstate_pair(int n1, int n2, float ht, int j, const float* m_prev, const float* dX,
-                          const float* vt, float* vtD, const float* G, const float* gm, float* out,
-                          int last, float* b, cudaStream_t st);
-void launch_adjoint_pair(int n1, int n2, float ht, int j, const float* lam_next, const float* dY,
-                         const float* delta, const float* delta_bar, const float* gm,
-                         float* lam_out, float* b, cudaStream_t st);
 void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
                                  const float* G1, const float* gm1, float* vtD, float* out,
                                  cudaStream_t st);

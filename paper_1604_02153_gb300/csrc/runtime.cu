@@ -25,6 +25,8 @@ using namespace regnk;
 namespace regnk {
 std::atomic<long long> g_launch_count{0};
 thread_local int t_programmatic_launch = 1;
+thread_local int t_graph_pdl = 0;
+thread_local int t_level = 0;
 thread_local int t_plain_fp32_reduce = 0;
 }
 
@@ -73,7 +75,6 @@ struct Level {
   bool have_div = false;    // delta, delta_bar, dY valid for v
   bool have_G = false;      // G valid for v
   int fuse_w = 0;           // box width of the fused prefilter+step kernels for v (0: off)
-  bool pair = false;        // cubic Lagrange: two incremental steps per launch for v
   bool lagrange = false;    // interpolation model of this level (cubic Lagrange or spline)
   int tile_adj = kDefaultStepTile;   // tile shapes of k_adjoint_step and k_incstate_step
   int tile_inc = kDefaultStepTile;
@@ -322,8 +323,12 @@ class LevelScope {
  public:
   LevelScope(reg_ctx* c, const Level& L) : c_(c), prev_(c->cur_level) {
     c->cur_level = (&L == &c->coarse) ? 1 : 0;
+    t_level = c->cur_level;
   }
-  ~LevelScope() { c_->cur_level = prev_; }
+  ~LevelScope() {
+    c_->cur_level = prev_;
+    t_level = prev_;
+  }
 
  private:
   reg_ctx* c_;
@@ -347,6 +352,13 @@ struct LaunchModeScope {
   int saved;
   explicit LaunchModeScope(int mode) : saved(t_programmatic_launch) { t_programmatic_launch = mode; }
   ~LaunchModeScope() { t_programmatic_launch = saved; }
+};
+
+// Programmatic edges for the launches captured into a graph (see launch_k).
+struct GraphPdlScope {
+  int saved;
+  explicit GraphPdlScope(int mode) : saved(t_graph_pdl) { t_graph_pdl = mode; }
+  ~GraphPdlScope() { t_graph_pdl = saved; }
 };
 
 // Reduction precision of this context for the duration of one call.
@@ -476,9 +488,10 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
     c->capturing = true;
     cudaGraph_t graph = nullptr;
     try {
-      // plain launches inside graphs: replays of graphs with programmatic
-      // edges measured slower than with ordinary kernel-to-kernel edges
+      // plain launches inside graphs, unless reg_options.graph_pdl asks for
+      // programmatic edges on the coarse grid (1) or everywhere (2)
       LaunchModeScope plain(0);
+      GraphPdlScope gp(c->opt.graph_pdl);
       body();
     } catch (...) {
       // capture failed (e.g. a launch form the graph cannot hold): drop the
@@ -535,8 +548,7 @@ bool graphed(reg_ctx* c, const std::string& key0, Body body) {
 // (a launch sequence recorded for one width must not replay for another)
 std::string graph_key(const reg_ctx* c, const char* what, const void* a, const void* b) {
   char buf[128];
-  snprintf(buf, sizeof buf, "%s:%p:%p:%d:%d:%d:%d", what, a, b, c->fine.fuse_w, c->coarse.fuse_w,
-           (int)c->fine.pair, (int)c->coarse.pair);
+  snprintf(buf, sizeof buf, "%s:%p:%p:%d:%d", what, a, b, c->fine.fuse_w, c->coarse.fuse_w);
   return buf;
 }
 
@@ -812,18 +824,6 @@ void set_velocity(reg_ctx* c, Level& L, const float* v) {
     }
     read_slots(c, S_DX, 2);
     L.fuse_w = fused_box_width(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
-  }
-  // cubic Lagrange: two incremental steps per launch when every stencil of
-  // the second step stays within the first step's extended tile
-  L.pair = false;
-  if (L.lagrange && c->opt.fused_transport && !L.flow) {
-    {
-      Prof P(c, REG_KC_REDUCE, 16.0 * N);
-      launch_maxabs(L.dX, 2 * (long long)N, c->partialf, slot(c, S_DX), c->st);
-      launch_maxabs(L.dY, 2 * (long long)N, c->partialf, slot(c, S_DY), c->st);
-    }
-    read_slots(c, S_DX, 2);
-    L.pair = pair_steps_ok(std::fmax(c->hsc[S_DX], c->hsc[S_DY]));
   }
   if (L.flow) {   // the flow kernel reads its tiles' reach from these (no host sync)
     Prof P(c, REG_KC_REDUCE, 16.0 * N);
@@ -1130,16 +1130,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     // v~(X_D) is gathered by the first step; the last one (nt >= 2) also
     // writes lambda~_nt and starts b~
     const float* cvt = coefficients(c, L, vt, 2, L.c2);
-    for (int j = 1; j <= nt;) {
-      if (L.pair && j + 1 <= nt) {   // steps j and j + 1 in one launch (cubic Lagrange)
-        const bool last = (j + 1 == nt);
-        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 + 48.0 : 96.0 + (last ? 16.0 : 0.0)) * N);
-        launch_incstate_pair(gd.n1, gd.n2, ht, j, mt, L.dX, vt, L.vtD, L.G, L.gm, mt2, last ? 1 : 0,
-                             bacc, c->st);
-        std::swap(mt, mt2);
-        j += 2;
-        continue;
-      }
+    for (int j = 1; j <= nt; ++j) {
       const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
       const bool last = (j == nt && nt >= 2);
       {
@@ -1149,7 +1140,6 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
                              last ? L.gm + 2 * nt * N : nullptr, last ? bacc : nullptr);
       }
       std::swap(mt, mt2);
-      ++j;
     }
     if (nt >= 2) {   // mt holds lambda~_nt
       lt = mt;
@@ -1173,14 +1163,6 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lt, L.dY, L.delta, L.delta_bar,
                            L.gm + 2 * j * N, lt2, bacc, c->st);
       std::swap(lt, lt2);
-      continue;
-    }
-    if (L.pair && j >= 1) {   // steps j and j - 1 in one launch (cubic Lagrange)
-      Prof P(c, REG_KC_ADJOINT_STEP, 96.0 * N);
-      launch_adjoint_pair(gd.n1, gd.n2, ht, j, lt, L.dY, L.delta, L.delta_bar, L.gm, lt2, bacc,
-                          c->st);
-      std::swap(lt, lt2);
-      --j;
       continue;
     }
     const float* cl = coefficients(c, L, lt, 1, L.coef);
@@ -1645,6 +1627,7 @@ reg_status reg_default_options(reg_options* o) {
   o->use_graphs = 1;
   o->flow_matvec = 0;
   o->beta_w = 0.0;
+  o->graph_pdl = 0;
   return REG_OK;
 }
 
@@ -1668,7 +1651,8 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.hessian == 1 && o.persistent_matvec != 0) ||
       (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
       (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1) ||
-      !(o.beta_w >= 0.0 && o.beta_w < 1e30) || (o.beta_w > 0.0 && o.incompressible))
+      !(o.beta_w >= 0.0 && o.beta_w < 1e30) || (o.beta_w > 0.0 && o.incompressible) ||
+      o.graph_pdl < 0 || o.graph_pdl > 2)
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))

@@ -393,212 +393,6 @@ void launch_incstate_step(int tile, int n1, int n2, float ht, const float* coef,
 }
 
 // ---------------------------------------------------------------------------
-// Two time steps per launch for the cubic Lagrange model (no prefilter: an
-// interpolated value depends only on the 4 x 4 raw samples around it). A
-// block owns a 32 x 16 tile. When every displacement is at most kPairD
-// cells, the stencils of the tile's points at step j + 1 only touch the
-// previous step's values on the tile extended by kPairH = kPairD + 2 cells on
-// each side (48 x 32 points). Phase A computes step j on that extended region
-// into shared memory (the neighbouring tiles' part is computed again by
-// their own blocks: 3x the points of one step), phase B computes step j + 1
-// on the tile from shared memory. Each point's arithmetic is that of
-// k_incstate_step / k_adjoint_step, so the results are bitwise those of two
-// per-step launches; one launch, and one dependent global round trip, fewer
-// per pair of steps. Used on the two-level preconditioner's coarse grid,
-// where each step kernel is a few microseconds of launch and memory latency.
-constexpr int kPairTX = 32, kPairTY = 16, kPairT = 256;
-constexpr int kPairD = 6, kPairH = kPairD + 2;
-constexpr int kPairEX = kPairTX + 2 * kPairH, kPairEY = kPairTY + 2 * kPairH;   // 48 x 32
-constexpr int kPairE = kPairEX * kPairEY;
-constexpr int kPairPB = kPairEX + 1;   // odd pitch of the shared-memory region
-
-bool pair_steps_ok(double max_disp_cells) { return max_disp_cells <= (double)kPairD; }
-
-// global index of extended-region point q (row-major in the 48 x 32 region)
-template <bool P2>
-__device__ __forceinline__ long long pair_point(int q, int x0, int y0, int n1, int n2, int log1,
-                                                int& gi, int& gj) {
-  const int ly = q / kPairEX, lx = q - ly * kPairEX;
-  gi = wrap_index<P2>(x0 - kPairH + lx, n1);
-  gj = wrap_index<P2>(y0 - kPairH + ly, n2);
-  return row_offset<P2>(gj, n1, log1) + gi;
-}
-
-// the 4 x 4 Lagrange sum of the stencil at tile point (lx, ly) (tile
-// coordinates) with displacement (d1, d2) over the shared-memory region,
-// in the order of apply_stencil
-__device__ __forceinline__ float pair_gather(const float* S, int lx, int ly, float d1, float d2) {
-  const float f1 = floorf(d1), f2 = floorf(d2);
-  float w1[4], w2[4];
-  cubic_weights(d1 - f1, w1, true);
-  cubic_weights(d2 - f2, w2, true);
-  const int li = lx + kPairH + (int)f1 - 1, lj = ly + kPairH + (int)f2 - 1;
-  return apply_box<kPairPB>(S, li, lj, w1, w2);
-}
-
-// incremental state steps j and j + 1 (j >= 1): m~_j on the extended region,
-// then m~_{j+1} on the tile. m_prev = m~_{j-1} (unused for j = 1, where v~ is
-// gathered at X_D and written to vtD instead of read). last: j + 1 = nt,
-// which writes lambda~_nt = -m~_nt and starts b (see k_incstate_step).
-template <bool P2>
-__global__ void __launch_bounds__(kPairT)
-k_incstate_pair(int n1, int n2, int log1, float ht, int j, const float* __restrict__ m_prev,
-                const float* __restrict__ dX, const float* __restrict__ vt, float* __restrict__ vtD,
-                const float* __restrict__ G, const float* __restrict__ gm, float* __restrict__ out,
-                int last, float* __restrict__ b) {
-  pdl_enter();
-  __shared__ float S[kPairEY * kPairPB];
-  const long long N = (long long)n1 * n2;
-  const int x0 = blockIdx.x * kPairTX, y0 = blockIdx.y * kPairTY;
-  const int t = threadIdx.x;
-  const bool first = (j == 1);
-  const float* Gj = G + 2 * (long long)(j - 1) * N;
-  const float* gj = gm + 2 * (long long)j * N;
-  // phase A: m~_j on the extended region
-#pragma unroll 2
-  for (int q = t; q < kPairE; q += kPairT) {
-    int gi, gjj;
-    const long long idx = pair_point<P2>(q, x0, y0, n1, n2, log1, gi, gjj);
-    const float x1 = __ldg(dX + idx), x2 = __ldg(dX + N + idx);
-    const float G1 = __ldg(Gj + idx), G2 = __ldg(Gj + N + idx);
-    const float u1 = __ldg(vt + idx), u2 = __ldg(vt + N + idx);
-    const float g1 = __ldg(gj + idx), g2 = __ldg(gj + N + idx);
-    float m = 0.f, w1, w2;
-    const Stencil St = make_stencil<P2>(gi, gjj, x1, x2, n1, n2, log1, true);
-    if (first) {
-      w1 = apply_stencil(St, vt);
-      w2 = apply_stencil(St, vt + N);
-      const int ly = q / kPairEX, lx = q - ly * kPairEX;
-      if (lx >= kPairH && lx < kPairH + kPairTX && ly >= kPairH && ly < kPairH + kPairTY) {
-        vtD[idx] = w1;
-        vtD[N + idx] = w2;
-      }
-    } else {
-      w1 = __ldg(vtD + idx);
-      w2 = __ldg(vtD + N + idx);
-      m = apply_stencil(St, m_prev);
-    }
-    m -= 0.5f * ht * (w1 * G1 + w2 * G2 + u1 * g1 + u2 * g2);
-    const int ly = q / kPairEX;
-    S[ly * kPairPB + (q - ly * kPairEX)] = m;
-  }
-  __syncthreads();
-  // phase B: m~_{j+1} on the tile (two adjacent points per thread)
-  const float* Gn = G + 2 * (long long)j * N;
-  const float* gn = gm + 2 * (long long)(j + 1) * N;
-  const int r = t / (kPairTX / 2), cx = (t % (kPairTX / 2)) * 2;
-  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-  float x1[2], x2[2], G1[2], G2[2], u1[2], u2[2], g1[2], g2[2], w1[2], w2[2], m[2];
-  ldk(dX + idx, x1);
-  ldk(dX + N + idx, x2);
-  ldk(Gn + idx, G1);
-  ldk(Gn + N + idx, G2);
-  ldk(vt + idx, u1);
-  ldk(vt + N + idx, u2);
-  ldk(gn + idx, g1);
-  ldk(gn + N + idx, g2);
-  ldk_rw(vtD + idx, w1);   // written by this block in phase A when j = 1
-  ldk_rw(vtD + N + idx, w2);
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    m[p] = pair_gather(S, cx + p, r, x1[p], x2[p]);
-    m[p] -= 0.5f * ht * (w1[p] * G1[p] + w2[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
-  }
-  if (!last) {
-    stk(out + idx, m);
-    return;
-  }
-  float lam[2], b1[2], b2[2];
-  const float hh = 0.5f * ht;
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    lam[p] = -m[p];
-    b1[p] = hh * lam[p] * g1[p];
-    b2[p] = hh * lam[p] * g2[p];
-  }
-  stk(out + idx, lam);
-  stk(b + idx, b1);
-  stk(b + N + idx, b2);
-}
-
-// incremental adjoint steps j and j - 1 (j >= 1) along Y_D: lambda~_j on the
-// extended region from lam_next = lambda~_{j+1}, then lambda~_{j-1} on the
-// tile; b += wb_j lambda~_j grad m_j and then wb_{j-1} lambda~_{j-1} grad
-// m_{j-1} at the tile's points, in the order of two k_adjoint_step calls.
-template <bool P2>
-__global__ void __launch_bounds__(kPairT)
-k_adjoint_pair(int n1, int n2, int log1, float ht, int j, const float* __restrict__ lam_next,
-               const float* __restrict__ dY, const float* __restrict__ delta,
-               const float* __restrict__ delta_bar, const float* __restrict__ gm,
-               float* __restrict__ lam_out, float* __restrict__ b) {
-  pdl_enter();
-  __shared__ float S[kPairEY * kPairPB];
-  const long long N = (long long)n1 * n2;
-  const int x0 = blockIdx.x * kPairTX, y0 = blockIdx.y * kPairTY;
-  const int t = threadIdx.x;
-#pragma unroll 2
-  for (int q = t; q < kPairE; q += kPairT) {
-    int gi, gjj;
-    const long long idx = pair_point<P2>(q, x0, y0, n1, n2, log1, gi, gjj);
-    const float y1 = __ldg(dY + idx), y2 = __ldg(dY + N + idx);
-    const float db = __ldg(delta_bar + idx), d = __ldg(delta + idx);
-    float l = apply_stencil(make_stencil<P2>(gi, gjj, y1, y2, n1, n2, log1, true), lam_next);
-    const float lstar = fmaf(ht * l, db, l);
-    l = l + 0.5f * ht * (l * db + lstar * d);
-    const int ly = q / kPairEX;
-    S[ly * kPairPB + (q - ly * kPairEX)] = l;
-  }
-  __syncthreads();
-  const int r = t / (kPairTX / 2), cx = (t % (kPairTX / 2)) * 2;
-  const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-  const float* gj = gm + 2 * (long long)j * N;
-  const float* gp = gm + 2 * (long long)(j - 1) * N;
-  float y1[2], y2[2], db[2], dd[2], g1[2], g2[2], h1[2], h2[2], b1[2], b2[2], l[2];
-  ldk(dY + idx, y1);
-  ldk(dY + N + idx, y2);
-  ldk(delta_bar + idx, db);
-  ldk(delta + idx, dd);
-  ldk(gj + idx, g1);
-  ldk(gj + N + idx, g2);
-  ldk(gp + idx, h1);
-  ldk(gp + N + idx, h2);
-  ldk_rw(b + idx, b1);
-  ldk_rw(b + N + idx, b2);
-  const float wj = ht * (j == 0 ? 0.5f : 1.0f), wp = ht * (j - 1 == 0 ? 0.5f : 1.0f);
-#pragma unroll
-  for (int p = 0; p < 2; ++p) {
-    // the tile's own lambda~_j (step j's time-integral term)
-    const float lj = S[(r + kPairH) * kPairPB + cx + p + kPairH];
-    b1[p] = fmaf(wj * lj, g1[p], b1[p]);
-    b2[p] = fmaf(wj * lj, g2[p], b2[p]);
-    float v = pair_gather(S, cx + p, r, y1[p], y2[p]);
-    const float lstar = fmaf(ht * v, db[p], v);
-    l[p] = v + 0.5f * ht * (v * db[p] + lstar * dd[p]);
-    b1[p] = fmaf(wp * l[p], h1[p], b1[p]);
-    b2[p] = fmaf(wp * l[p], h2[p], b2[p]);
-  }
-  stk(lam_out + idx, l);
-  stk(b + idx, b1);
-  stk(b + N + idx, b2);
-}
-
-void launch_incstate_pair(int n1, int n2, float ht, int j, const float* m_prev, const float* dX,
-                          const float* vt, float* vtD, const float* G, const float* gm, float* out,
-                          int last, float* b, cudaStream_t st) {
-  launch_k(pick(n1, n2, k_incstate_pair<true>, k_incstate_pair<false>),
-           dim3(n1 / kPairTX, n2 / kPairTY), dim3(kPairT), 0, st, n1, n2, ilog2i(n1), ht, j, m_prev,
-           dX, vt, vtD, G, gm, out, last, b);
-}
-
-void launch_adjoint_pair(int n1, int n2, float ht, int j, const float* lam_next, const float* dY,
-                         const float* delta, const float* delta_bar, const float* gm,
-                         float* lam_out, float* b, cudaStream_t st) {
-  launch_k(pick(n1, n2, k_adjoint_pair<true>, k_adjoint_pair<false>),
-           dim3(n1 / kPairTX, n2 / kPairTY), dim3(kPairT), 0, st, n1, n2, ilog2i(n1), ht, j,
-           lam_next, dY, delta, delta_bar, gm, lam_out, b);
-}
-
-// ---------------------------------------------------------------------------
 // Full-Newton incremental adjoint (eq. inc-adj-slm with the div(lambda v~)
 // source) and the time integral of lambda~ grad m + lambda grad m~
 // (eq. hessian-matvec as written). One point per thread.

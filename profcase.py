@@ -34,7 +34,11 @@ def main():
     ap.add_argument("--fused", type=int, default=1, help="fused_transport option (0 or 1)")
     ap.add_argument("--step-tile", type=int, default=-1,
                     help="step_tile option (-1: timed at creation, 0: built-in, 1..9: fixed)")
-    ap.add_argument("--flow", type=int, default=1, help="flow_matvec option (0 or 1)")
+    ap.add_argument("--flow", type=int, default=0, help="flow_matvec option (0 or 1)")
+    ap.add_argument("--graph-pdl", type=int, default=0, help="graph_pdl option (0, 1 or 2)")
+    ap.add_argument("--coarse-nt", type=int, default=0, help="coarse_nt option (0: the problem's)")
+    ap.add_argument("--coarse-lagrange", action="store_true",
+                    help="cubic Lagrange on P_2L's coarse grid (the bench's chosen form)")
     ap.add_argument("--unet", type=int, default=0,
                     help="instead: this many warm-start network training steps (batch 8, 256^2)")
     a = ap.parse_args()
@@ -54,6 +58,8 @@ def main():
                            interp=regnk.REG_INTERP_LAGRANGE if a.lagrange else regnk.REG_INTERP_SPLINE,
                            persistent_matvec=a.persistent, programmatic_launch=a.pdl,
                            fused_transport=a.fused, step_tile=a.step_tile, flow_matvec=a.flow,
+                           graph_pdl=a.graph_pdl, coarse_nt=a.coarse_nt,
+                           coarse_interp=regnk.REG_INTERP_LAGRANGE if a.coarse_lagrange else -1,
                            **pc)
     R.set_images(f(m_R), f(m_T))
     vd, ud = f(v), f(u)
