@@ -489,22 +489,24 @@ __device__ __forceinline__ float pow_s(float x, float s) {
 // kd the derivative wavenumbers (Nyquist zeroed): eigenvalue a + cw |kd|^2
 // along kd, a across it, so
 //     R^s = a^s I + ((a + cw |kd|^2)^s - a^s) kd kd^T / |kd|^2.
-__device__ __forceinline__ float regw(const ColArgs& a, int o, int c, int k1, int k2, float kd1,
-                                      float kd2) {
+// (out of line, like kw below: inlined into the shared column-pass code they
+// raised its register count for every operator)
+__device__ __noinline__ float regw(float beta, int p, float s, float beta_w, int o, int c, int k1,
+                                   int k2, float kd1, float kd2) {
   const float k2n = (float)k1 * (float)k1 + (float)k2 * (float)k2;
   float g = k2n;
-  if (a.p == 2) g = k2n * k2n;
-  else if (a.p == 3) g = k2n * k2n * k2n;
+  if (p == 2) g = k2n * k2n;
+  else if (p == 3) g = k2n * k2n * k2n;
   const float d = (o == c) ? 1.f : 0.f;
   const float ko = o == 0 ? kd1 : kd2, kc = c == 0 ? kd1 : kd2;
-  const float cw = a.beta_w * (1.f + k2n);
-  if (a.s == 1.f) return a.beta * g * d + cw * ko * kc;
+  const float cw = beta_w * (1.f + k2n);
+  if (s == 1.f) return beta * g * d + cw * ko * kc;
   if (g == 0.f) g = 1.f;
-  const float av = a.beta * g;
+  const float av = beta * g;
   const float q = kd1 * kd1 + kd2 * kd2;
-  const float as = pow_s(av, a.s);
+  const float as = pow_s(av, s);
   if (q == 0.f) return as * d;
-  return as * d + (pow_s(av + cw * q, a.s) - as) * ko * kc / q;
+  return as * d + (pow_s(av + cw * q, s) - as) * ko * kc / q;
 }
 
 // Entry (o, c) of the near-incompressible K of the reduced gradient and the
@@ -515,17 +517,17 @@ __device__ __forceinline__ float regw(const ColArgs& a, int o, int c, int k1, in
 //     K = I - c kd kd^T / |kd|^2,  c = cw |kd|^2 / (a + cw |kd|^2)  in [0, 1)
 // (the identity where kd = 0; c -> 1 is the Leray projection, c -> 0 the
 // identity). Its symbol is bounded, unlike M's.
-__device__ __forceinline__ float kw(const ColArgs& a, int o, int c, int k1, int k2, float kd1,
-                                    float kd2) {
+__device__ __noinline__ float kw(float beta, int p, float beta_w, int o, int c, int k1, int k2,
+                                 float kd1, float kd2) {
   const float q = kd1 * kd1 + kd2 * kd2;
   const float d = (o == c) ? 1.f : 0.f;
   if (q == 0.f) return d;
   const float k2n = (float)k1 * (float)k1 + (float)k2 * (float)k2;
   float g = k2n;
-  if (a.p == 2) g = k2n * k2n;
-  else if (a.p == 3) g = k2n * k2n * k2n;
-  const float cq = a.beta_w * (1.f + k2n) * q;
-  const float w = cq / (a.beta * g + cq);
+  if (p == 2) g = k2n * k2n;
+  else if (p == 3) g = k2n * k2n * k2n;
+  const float cq = beta_w * (1.f + k2n) * q;
+  const float w = cq / (beta * g + cq);
   return d - w * (o == 0 ? kd1 : kd2) * (c == 0 ? kd1 : kd2) / q;
 }
 
@@ -558,12 +560,17 @@ __device__ __forceinline__ float2 symbol(const ColArgs& a, int o, int c, int k1,
                              leray(o, c, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2),
                          0.f);
     case SPOP_REGW:
-      return make_float2(regw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
+      return make_float2(regw(a.beta, a.p, a.s, a.beta_w, o, c, k1, k2, nyq1 ? 0.f : (float)k1,
+                              nyq2 ? 0.f : (float)k2),
+                         0.f);
     case SPOP_KW:
-      return make_float2(kw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2), 0.f);
+      return make_float2(kw(a.beta, a.p, a.beta_w, o, c, k1, k2, nyq1 ? 0.f : (float)k1,
+                            nyq2 ? 0.f : (float)k2),
+                         0.f);
     case SPOP_REGPOW_KW:
       return make_float2(regpow(a.beta, a.p, a.s, k1, k2) *
-                             kw(a, o, c, k1, k2, nyq1 ? 0.f : (float)k1, nyq2 ? 0.f : (float)k2),
+                             kw(a.beta, a.p, a.beta_w, o, c, k1, k2, nyq1 ? 0.f : (float)k1,
+                                nyq2 ? 0.f : (float)k2),
                          0.f);
     default:
       return make_float2(0.f, 0.f);
@@ -580,7 +587,7 @@ struct ColCfg {
 };
 
 template <int LI, int LO, int T>
-__global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 4) k_cols(ColArgs a) {
   pdl_enter();
   constexpr int NI = FftCfg<LI, T>::N, NO = FftCfg<LO, T>::N;
   constexpr int NM = ColCfg<LI, LO, T>::NM;

@@ -167,47 +167,32 @@ struct BoxDims {
   static_assert(PS >= WS + 2 && PT >= WS + 2, "float4 reads run 2 samples past a chain");
 };
 
-template <int W, bool P2, int NT = kPThreads>
-__device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int n1, int n2,
-                                              int log1, int bx0, int by0, float* stage,
-                                              float* mid, float* box) {
+// float4 vectors per staged row (the first one starts at the 4-aligned
+// column at or left of the staged region's first column)
+template <int W>
+constexpr int box_row_vectors() { return (BoxDims<W>::WS + 3 + 3) / 4; }
+
+// Places the float4 vector v = (e0..e3) of staged row r (first column `off`
+// left of the staged region) into the staging buffer.
+template <int W>
+__device__ __forceinline__ void put_staged(float* stage, int r, int v, int off, float4 x) {
+  using D = BoxDims<W>;
+  const float e[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int c = 4 * v + k - off;
+    if (c >= 0 && c < D::WS) stage[r * D::PS + c] = e[k];
+  }
+}
+
+// The two recursion passes of prefilter_box on samples already staged
+// (stage[r * PS + c] = sample at node (bx0 - kL + c, by0 - kL + r)); ends
+// with a block barrier.
+template <int W, int NT>
+__device__ __forceinline__ void box_recursions(float* stage, float* mid, float* box) {
   using D = BoxDims<W>;
   constexpr int WS = D::WS, PS = D::PS, PT = D::PT, PB = D::PB;
-  // The staged rows are read as float4 from a 4-aligned first column (a
-  // float4 never straddles the periodic seam since n1 % 4 == 0) and the
-  // first `off` columns of the first vector are dropped. Row-major thread
-  // order keeps the loads of a warp contiguous.
-  constexpr int kV = (WS + 3 + 3) / 4;          // float4 per staged row
-  constexpr int kLoads = (WS * kV + NT - 1) / NT;
-  const int cx0 = bx0 - kL;
-  const int ax0 = cx0 & ~3;
-  const int off = cx0 - ax0;
   const int t = threadIdx.x;
-  float4 ld_[kLoads];
-#pragma unroll
-  for (int u = 0; u < kLoads; ++u) {
-    const int q = t + u * NT;
-    if (q < WS * kV) {
-      const int r = q / kV, v = q - r * kV;
-      const int gx = P2 ? wrap_index<true>(ax0 + 4 * v, n1) : wrap_once(ax0 + 4 * v, n1);
-      const int gy = P2 ? wrap_index<true>(by0 - kL + r, n2) : wrap_once(by0 - kL + r, n2);
-      ld_[u] = __ldg(reinterpret_cast<const float4*>(src + row_offset<P2>(gy, n1, log1) + gx));
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < kLoads; ++u) {
-    const int q = t + u * NT;
-    if (q < WS * kV) {
-      const int r = q / kV, v = q - r * kV;
-      const float e[4] = {ld_[u].x, ld_[u].y, ld_[u].z, ld_[u].w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int c = 4 * v + k - off;
-        if (c >= 0 && c < WS) stage[r * PS + c] = e[k];
-      }
-    }
-  }
-  __syncthreads();
   constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
   constexpr int kQ = (kLen + 3) / 4;   // float4 reads per chain
   // x recursions: a warp walks 32 consecutive staged rows of one segment;
@@ -248,6 +233,45 @@ __device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int
                                    [&](int o, float x) { colb[o * PB] = x; });
   }
   __syncthreads();
+}
+
+template <int W, bool P2, int NT = kPThreads>
+__device__ __forceinline__ void prefilter_box(const float* __restrict__ src, int n1, int n2,
+                                              int log1, int bx0, int by0, float* stage,
+                                              float* mid, float* box) {
+  using D = BoxDims<W>;
+  constexpr int WS = D::WS;
+  // The staged rows are read as float4 from a 4-aligned first column (a
+  // float4 never straddles the periodic seam since n1 % 4 == 0) and the
+  // first `off` columns of the first vector are dropped. Row-major thread
+  // order keeps the loads of a warp contiguous.
+  constexpr int kV = box_row_vectors<W>();      // float4 per staged row
+  constexpr int kLoads = (WS * kV + NT - 1) / NT;
+  const int cx0 = bx0 - kL;
+  const int ax0 = cx0 & ~3;
+  const int off = cx0 - ax0;
+  const int t = threadIdx.x;
+  float4 ld_[kLoads];
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * NT;
+    if (q < WS * kV) {
+      const int r = q / kV, v = q - r * kV;
+      const int gx = P2 ? wrap_index<true>(ax0 + 4 * v, n1) : wrap_once(ax0 + 4 * v, n1);
+      const int gy = P2 ? wrap_index<true>(by0 - kL + r, n2) : wrap_once(by0 - kL + r, n2);
+      ld_[u] = __ldg(reinterpret_cast<const float4*>(src + row_offset<P2>(gy, n1, log1) + gx));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kLoads; ++u) {
+    const int q = t + u * NT;
+    if (q < WS * kV) {
+      const int r = q / kV, v = q - r * kV;
+      put_staged<W>(stage, r, v, off, ld_[u]);
+    }
+  }
+  __syncthreads();
+  box_recursions<W, NT>(stage, mid, box);
 }
 
 // ---------------------------------------------------------------------------

@@ -920,6 +920,30 @@ double objective(reg_ctx* c, Level& L) {
   return 0.5 * hh * c->hsc[S_J1] + 0.5 * hh * c->hsc[S_J2];
 }
 
+// One fused adjoint step (prefilter of lambda_{j+1} inside the step) and one
+// fused incremental state step j >= 2: the pipelined persistent kernels
+// (reg_options.pipeline_steps) or one block per tile.
+void adjoint_fused(reg_ctx* c, Level& L, float wb, const float* lam_next, const float* gmj,
+                   float* lam_out, float* b) {
+  if (c->opt.pipeline_steps)
+    launch_adjoint_pipe(L.fuse_w, L.g.n1, L.g.n2, L.ht, wb, lam_next, L.dY, L.delta, L.delta_bar,
+                        gmj, lam_out, b, c->st);
+  else
+    launch_adjoint_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, wb, lam_next, L.dY, L.delta, L.delta_bar,
+                         gmj, lam_out, b, c->st);
+}
+
+// b non-NULL for the last step j = nt (gmj is then grad m_nt)
+void incstate_fused(reg_ctx* c, Level& L, const float* m_prev, const float* vt, const float* Gj,
+                    const float* gmj, float* out, float* b) {
+  if (c->opt.pipeline_steps)
+    launch_incstate_pipe(L.fuse_w, L.g.n1, L.g.n2, L.ht, m_prev, L.dX, vt, L.vtD, Gj, gmj, out, b,
+                         c->st);
+  else
+    launch_incstate_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, m_prev, L.dX, vt, L.vtD, Gj, gmj, out,
+                          b ? gmj : nullptr, b, c->st);
+}
+
 // b = int_0^1 lambda grad m dt by the adjoint solve (eq. adj-slm), trapezoid in
 // time; g = beta A v + b. Needs objective() for L.Av.
 void gradient(reg_ctx* c, Level& L, float* g_out) {
@@ -942,8 +966,7 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     if (hist) lam2 = hist + j * N;
     if (L.fuse_w) {   // prefilter of lambda_{j+1} inside the step
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
-      launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lam, L.dY, L.delta, L.delta_bar,
-                           L.gm + 2 * j * N, lam2, L.b, c->st);
+      adjoint_fused(c, L, wb, lam, L.gm + 2 * j * N, lam2, L.b);
       std::swap(lam, lam2);
       continue;
     }
@@ -1117,9 +1140,8 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     for (int j = 2; j <= nt; ++j) {
       const bool last = (j == nt);
       Prof P(c, REG_KC_INCSTATE_STEP, (last ? 64.0 : 48.0) * N);
-      launch_incstate_fused(L.fuse_w, gd.n1, gd.n2, ht, mt, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
-                            L.gm + 2 * j * N, mt2, last ? L.gm + 2 * nt * N : nullptr,
-                            last ? bacc : nullptr, c->st);
+      incstate_fused(c, L, mt, vt, L.G + 2 * (j - 1) * N, L.gm + 2 * j * N, mt2,
+                     last ? bacc : nullptr);
       std::swap(mt, mt2);
     }
     if (nt >= 2) {   // mt holds lambda~_nt
@@ -1160,8 +1182,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     if (L.fuse_w) {   // prefilter of lambda~_{j+1} inside the step kernel
       Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
-      launch_adjoint_fused(L.fuse_w, gd.n1, gd.n2, ht, wb, lt, L.dY, L.delta, L.delta_bar,
-                           L.gm + 2 * j * N, lt2, bacc, c->st);
+      adjoint_fused(c, L, wb, lt, L.gm + 2 * j * N, lt2, bacc);
       std::swap(lt, lt2);
       continue;
     }
@@ -1628,6 +1649,7 @@ reg_status reg_default_options(reg_options* o) {
   o->flow_matvec = 0;
   o->beta_w = 0.0;
   o->graph_pdl = 0;
+  o->pipeline_steps = 1;
   return REG_OK;
 }
 
@@ -1652,7 +1674,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
       (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1) ||
       !(o.beta_w >= 0.0 && o.beta_w < 1e30) || (o.beta_w > 0.0 && o.incompressible) ||
-      o.graph_pdl < 0 || o.graph_pdl > 2)
+      o.graph_pdl < 0 || o.graph_pdl > 2 || (o.pipeline_steps != 0 && o.pipeline_steps != 1))
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))
