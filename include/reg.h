@@ -220,14 +220,6 @@ typedef struct {
                               kernel's blocks are scheduled while its
                               predecessor drains; 2 every launch does. Results
                               are identical                                   */
-  int pipeline_steps;      /* 1 (default): the fused prefilter+step kernels of
-                              the incremental state (steps 2..nt) and of the
-                              adjoint solves run persistent, one block per SM
-                              walking its 32 x 32 tiles, copying the next
-                              tile's coefficient box samples and streamed
-                              fields into shared memory (cp.async) while it
-                              computes the current one; 0: one block per tile.
-                              Results are identical                           */
 } reg_options;
 
 typedef struct {

@@ -586,8 +586,11 @@ struct ColCfg {
   static constexpr int NT = FftCfg<LM, T>::NT;
 };
 
+// 64 registers per thread at most (1024 threads' worth of blocks per SM):
+// left to itself the compiler gave the 1024-point column pass 108 registers,
+// two blocks per SM
 template <int LI, int LO, int T>
-__global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 4) k_cols(ColArgs a) {
+__global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 1024 / ColCfg<LI, LO, T>::NT) k_cols(ColArgs a) {
   pdl_enter();
   constexpr int NI = FftCfg<LI, T>::N, NO = FftCfg<LO, T>::N;
   constexpr int NM = ColCfg<LI, LO, T>::NM;

@@ -173,14 +173,6 @@ void launch_incstate_fused(int W, int n1, int n2, float ht, const float* m_prev,
                            float* out, const float* gm_nt, float* b, cudaStream_t st);
 void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstride, int F,
                          const float* disp, float* out, cudaStream_t st);
-// Pipelined persistent versions of the two fused steps (one block per SM,
-// cp.async prefetch of the next tile; bitwise the same results).
-void launch_incstate_pipe(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
-                          const float* vt, const float* vtD, const float* G, const float* gm,
-                          float* out, float* b, cudaStream_t st);
-void launch_adjoint_pipe(int W, int n1, int n2, float ht, float wb, const float* lam_next,
-                         const float* dY, const float* delta, const float* delta_bar,
-                         const float* gm, float* lam_out, float* b, cudaStream_t st);
 void launch_incstate_first_fused(int W, int n1, int n2, float ht, const float* vt, const float* dX,
                                  const float* G1, const float* gm1, float* vtD, float* out,
                                  cudaStream_t st);

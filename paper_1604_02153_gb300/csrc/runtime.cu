@@ -921,27 +921,18 @@ double objective(reg_ctx* c, Level& L) {
 }
 
 // One fused adjoint step (prefilter of lambda_{j+1} inside the step) and one
-// fused incremental state step j >= 2: the pipelined persistent kernels
-// (reg_options.pipeline_steps) or one block per tile.
+// fused incremental state step j >= 2 (b non-NULL for the last, j = nt,
+// where gmj is grad m_nt).
 void adjoint_fused(reg_ctx* c, Level& L, float wb, const float* lam_next, const float* gmj,
                    float* lam_out, float* b) {
-  if (c->opt.pipeline_steps)
-    launch_adjoint_pipe(L.fuse_w, L.g.n1, L.g.n2, L.ht, wb, lam_next, L.dY, L.delta, L.delta_bar,
-                        gmj, lam_out, b, c->st);
-  else
-    launch_adjoint_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, wb, lam_next, L.dY, L.delta, L.delta_bar,
-                         gmj, lam_out, b, c->st);
+  launch_adjoint_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, wb, lam_next, L.dY, L.delta, L.delta_bar,
+                       gmj, lam_out, b, c->st);
 }
 
-// b non-NULL for the last step j = nt (gmj is then grad m_nt)
 void incstate_fused(reg_ctx* c, Level& L, const float* m_prev, const float* vt, const float* Gj,
                     const float* gmj, float* out, float* b) {
-  if (c->opt.pipeline_steps)
-    launch_incstate_pipe(L.fuse_w, L.g.n1, L.g.n2, L.ht, m_prev, L.dX, vt, L.vtD, Gj, gmj, out, b,
-                         c->st);
-  else
-    launch_incstate_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, m_prev, L.dX, vt, L.vtD, Gj, gmj, out,
-                          b ? gmj : nullptr, b, c->st);
+  launch_incstate_fused(L.fuse_w, L.g.n1, L.g.n2, L.ht, m_prev, L.dX, vt, L.vtD, Gj, gmj, out,
+                        b ? gmj : nullptr, b, c->st);
 }
 
 // b = int_0^1 lambda grad m dt by the adjoint solve (eq. adj-slm), trapezoid in
@@ -1649,7 +1640,6 @@ reg_status reg_default_options(reg_options* o) {
   o->flow_matvec = 0;
   o->beta_w = 0.0;
   o->graph_pdl = 0;
-  o->pipeline_steps = 1;
   return REG_OK;
 }
 
@@ -1674,7 +1664,7 @@ reg_status reg_create(reg_grid grid, int nt, double beta, const reg_options* opt
       (o.precision != REG_PRECISION_FP64 && o.precision != REG_PRECISION_FP32) ||
       (o.use_graphs != 0 && o.use_graphs != 1) || (o.flow_matvec != 0 && o.flow_matvec != 1) ||
       !(o.beta_w >= 0.0 && o.beta_w < 1e30) || (o.beta_w > 0.0 && o.incompressible) ||
-      o.graph_pdl < 0 || o.graph_pdl > 2 || (o.pipeline_steps != 0 && o.pipeline_steps != 1))
+      o.graph_pdl < 0 || o.graph_pdl > 2)
     return REG_EINVAL;
   if (o.precond == REG_PC_2L && (!size_ok(grid.n1 / 2) || !size_ok(grid.n2 / 2) ||
                                  grid.n1 % 2 || grid.n2 % 2))

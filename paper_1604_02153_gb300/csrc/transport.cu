@@ -763,291 +763,6 @@ k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Pipelined fused steps. The fused step kernels above spend most of their
-// time waiting: each block loads its tile's streamed operands and the staged
-// box of the transported field, then runs the prefilter recursions and the
-// gather, with two blocks per SM and the grid in 3-4 waves at 1024^2. Here a
-// persistent block (one per SM) walks its tiles in turn and copies the next
-// tile's staged box and streamed operands into shared memory with cp.async
-// while it computes the current tile, so the global-memory latency overlaps
-// the recursions. Double buffers: raw box (rows of whole float4 vectors, as
-// prefilter_box loads them), streamed operands (32 x 32 per field). The
-// staged box is rebuilt from the raw copy exactly as prefilter_box builds it
-// and filtered by the same recursions, so the results are bitwise those of
-// the unpipelined fused kernels.
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-constexpr int kPipeT = 512;            // threads of a pipelined block (two points each)
-
-template <int W, int F>
-struct PipeDims {
-  using D = BoxDims<W>;
-  static constexpr int H = (W - 32) / 2;
-  static constexpr int kV = box_row_vectors<W>();   // float4 per staged row
-  static constexpr int RAWP = 4 * kV;               // raw row pitch (floats)
-  static constexpr int kRaw = D::WS * RAWP;         // one raw box
-  static constexpr int kStrm = F * 1024;            // one tile's streamed fields
-  static constexpr size_t kSmemBytes =
-      sizeof(float) * (2 * kRaw + 2 * kStrm + D::kStage + D::kMid);
-};
-
-// Issues the copies of tile `tile` (raw box of `field` and F streamed 32 x 32
-// fields, src[f]) into buffer set `raw`, `strm`.
-template <int W, int F, bool P2>
-__device__ __forceinline__ void pipe_prefetch(int tile, int tiles_x, const float* __restrict__ field,
-                                              const float* const (&src)[F], int n1, int n2,
-                                              int log1, float* raw, float* strm) {
-  using PD = PipeDims<W, F>;
-  constexpr int WS = BoxDims<W>::WS;
-  const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * 32;
-  const int cx0 = x0 - PD::H - kL;
-  const int ax0 = cx0 & ~3;
-  const int t = threadIdx.x;
-  for (int q = t; q < WS * PD::kV; q += kPipeT) {
-    const int r = q / PD::kV, v = q - r * PD::kV;
-    const int gx = P2 ? wrap_index<true>(ax0 + 4 * v, n1) : wrap_once(ax0 + 4 * v, n1);
-    const int gy = P2 ? wrap_index<true>(y0 - PD::H - kL + r, n2) : wrap_once(y0 - PD::H - kL + r, n2);
-    cp_async16(raw + r * PD::RAWP + 4 * v, field + row_offset<P2>(gy, n1, log1) + gx);
-  }
-  // streamed fields: 32 rows x 8 float4 each, one float4 per field and
-  // thread of the first half of the block
-  if (t < 256) {
-    const int r = t >> 3, v = t & 7;
-    const long long o = row_offset<P2>(y0 + r, n1, log1) + x0 + 4 * v;
-#pragma unroll
-    for (int f = 0; f < F; ++f) cp_async16(strm + f * 1024 + r * 32 + 4 * v, src[f] + o);
-  }
-}
-
-// The staged box of prefilter_box rebuilt from the raw copy (same values at
-// the same places), then its recursions; ends with a block barrier.
-template <int W>
-__device__ __forceinline__ void pipe_prefilter(const float* raw, int x0, float* stage, float* mid) {
-  using PD = PipeDims<W, 1>;
-  constexpr int WS = BoxDims<W>::WS;
-  const int cx0 = x0 - PD::H - kL;
-  const int off = cx0 - (cx0 & ~3);
-  for (int q = threadIdx.x; q < WS * PD::kV; q += kPipeT) {
-    const int r = q / PD::kV, v = q - r * PD::kV;
-    put_staged<W>(stage, r, v, off,
-                  *reinterpret_cast<const float4*>(raw + r * PD::RAWP + 4 * v));
-  }
-  __syncthreads();
-  box_recursions<W, kPipeT>(stage, mid, stage);
-}
-
-template <int K>
-__device__ __forceinline__ void lds2(const float* p, float (&a)[K]) {
-  const float2 t = *reinterpret_cast<const float2*>(p);
-  a[0] = t.x;
-  a[1] = t.y;
-}
-
-// Incremental state step j >= 2 (see k_incstate_fused), pipelined. Streamed
-// fields per tile: dX (2), v~(X_D) (2), G_j (2), v~ (2), grad m_j (2). With
-// b non-NULL (the last step j = nt) it writes lambda~_nt = -m~_nt and starts
-// b = h_t/2 lambda~_nt grad m_nt (grad m_j is grad m_nt then).
-template <bool P2, int W>
-__global__ void __launch_bounds__(kPipeT, 1)
-k_incstate_pipe(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
-                const float* __restrict__ dX, const float* __restrict__ vt,
-                const float* __restrict__ vtD, const float* __restrict__ G,
-                const float* __restrict__ gm, float* __restrict__ out, float* __restrict__ b) {
-  pdl_enter();
-  constexpr int F = 10;
-  using PD = PipeDims<W, F>;
-  using D = BoxDims<W>;
-  constexpr int H = PD::H;
-  extern __shared__ float sm[];
-  // buffer sets 0 and 1: raw box at sm + set * kRaw, streamed fields at
-  // sm + 2 kRaw + set * kStrm
-  float* const strm0 = sm + 2 * PD::kRaw;
-  float* stage = sm + 2 * PD::kRaw + 2 * PD::kStrm;
-  float* mid = stage + D::kStage;
-  const long long N = (long long)n1 * n2;
-  const int tiles_x = n1 / 32, tiles = tiles_x * (n2 / 32);
-  const float* const src[F] = {dX, dX + N, vtD, vtD + N, G, G + N, vt, vt + N, gm, gm + N};
-  const int t = threadIdx.x;
-  constexpr int TPR = 32 / kFP;
-  const int r = t / TPR, cx = (t % TPR) * kFP;
-  int tile = blockIdx.x;
-  if (tile < tiles) pipe_prefetch<W, F, P2>(tile, tiles_x, m_prev, src, n1, n2, log1, sm, strm0);
-  cp_async_commit();
-  for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
-    const int cb = it & 1;
-    const int next = tile + gridDim.x;
-    if (next < tiles)
-      pipe_prefetch<W, F, P2>(next, tiles_x, m_prev, src, n1, n2, log1, sm + (cb ^ 1) * PD::kRaw,
-                              strm0 + (cb ^ 1) * PD::kStrm);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * 32;
-    pipe_prefilter<W>(sm + cb * PD::kRaw, x0, stage, mid);
-    const float* sp = strm0 + cb * PD::kStrm + r * 32 + cx;
-    float x1[kFP], x2[kFP], w1v[kFP], w2v[kFP], G1[kFP], G2[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
-    lds2(sp, x1);
-    lds2(sp + 1024, x2);
-    lds2(sp + 2 * 1024, w1v);
-    lds2(sp + 3 * 1024, w2v);
-    lds2(sp + 4 * 1024, G1);
-    lds2(sp + 5 * 1024, G2);
-    lds2(sp + 6 * 1024, u1);
-    lds2(sp + 7 * 1024, u2);
-    lds2(sp + 8 * 1024, g1);
-    lds2(sp + 9 * 1024, g2);
-    float m[kFP];
-#pragma unroll
-    for (int p = 0; p < kFP; ++p) {
-      int li, lj;
-      float w1[4], w2[4];
-      box_stencil<W>(H + cx + p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
-      m[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
-      m[p] -= 0.5f * ht * (w1v[p] * G1[p] + w2v[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
-    }
-    const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-    if (!b) {
-      stk(out + idx, m);
-    } else {
-      float lam[kFP], b1[kFP], b2[kFP];
-      const float hh = 0.5f * ht;
-#pragma unroll
-      for (int p = 0; p < kFP; ++p) {
-        lam[p] = -m[p];
-        b1[p] = hh * lam[p] * g1[p];
-        b2[p] = hh * lam[p] * g2[p];
-      }
-      stk(out + idx, lam);
-      stk(b + idx, b1);
-      stk(b + N + idx, b2);
-    }
-    __syncthreads();   // the buffers of this tile are refilled next
-  }
-  cp_async_wait<0>();
-}
-
-// Adjoint step (see k_adjoint_fused), pipelined. Streamed fields per tile:
-// dY (2), div v(Y_D), div v, grad m_j (2), b (2).
-template <bool P2, int W>
-__global__ void __launch_bounds__(kPipeT, 1)
-k_adjoint_pipe(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
-               const float* __restrict__ dY, const float* __restrict__ delta,
-               const float* __restrict__ delta_bar, const float* __restrict__ gm,
-               float* __restrict__ lam_out, float* __restrict__ b) {
-  pdl_enter();
-  constexpr int F = 8;
-  using PD = PipeDims<W, F>;
-  using D = BoxDims<W>;
-  constexpr int H = PD::H;
-  extern __shared__ float sm[];
-  // buffer sets 0 and 1: raw box at sm + set * kRaw, streamed fields at
-  // sm + 2 kRaw + set * kStrm
-  float* const strm0 = sm + 2 * PD::kRaw;
-  float* stage = sm + 2 * PD::kRaw + 2 * PD::kStrm;
-  float* mid = stage + D::kStage;
-  const long long N = (long long)n1 * n2;
-  const int tiles_x = n1 / 32, tiles = tiles_x * (n2 / 32);
-  const float* const src[F] = {dY, dY + N, delta_bar, delta, gm, gm + N, b, b + N};
-  const int t = threadIdx.x;
-  constexpr int TPR = 32 / kFP;
-  const int r = t / TPR, cx = (t % TPR) * kFP;
-  int tile = blockIdx.x;
-  if (tile < tiles) pipe_prefetch<W, F, P2>(tile, tiles_x, lam_next, src, n1, n2, log1, sm, strm0);
-  cp_async_commit();
-  for (int it = 0; tile < tiles; ++it, tile += gridDim.x) {
-    const int cb = it & 1;
-    const int next = tile + gridDim.x;
-    if (next < tiles)
-      pipe_prefetch<W, F, P2>(next, tiles_x, lam_next, src, n1, n2, log1, sm + (cb ^ 1) * PD::kRaw,
-                              strm0 + (cb ^ 1) * PD::kStrm);
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
-    const int x0 = (tile % tiles_x) * 32, y0 = (tile / tiles_x) * 32;
-    pipe_prefilter<W>(sm + cb * PD::kRaw, x0, stage, mid);
-    const float* sp = strm0 + cb * PD::kStrm + r * 32 + cx;
-    float y1[kFP], y2[kFP], db[kFP], dd[kFP], g1[kFP], g2[kFP], b1[kFP], b2[kFP], l[kFP];
-    lds2(sp, y1);
-    lds2(sp + 1024, y2);
-    lds2(sp + 2 * 1024, db);
-    lds2(sp + 3 * 1024, dd);
-    lds2(sp + 4 * 1024, g1);
-    lds2(sp + 5 * 1024, g2);
-    lds2(sp + 6 * 1024, b1);
-    lds2(sp + 7 * 1024, b2);
-#pragma unroll
-    for (int p = 0; p < kFP; ++p) {
-      int li, lj;
-      float w1[4], w2[4];
-      box_stencil<W>(H + cx + p, H + r, y1[p], y2[p], false, li, lj, w1, w2);
-      const float lb = apply_box<D::PB>(stage, li, lj, w1, w2);
-      const float lstar = fmaf(ht * lb, db[p], lb);
-      l[p] = lb + 0.5f * ht * (lb * db[p] + lstar * dd[p]);
-      b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
-      b2[p] = fmaf(wb * l[p], g2[p], b2[p]);
-    }
-    const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
-    stk(lam_out + idx, l);
-    stk(b + idx, b1);
-    stk(b + N + idx, b2);
-    __syncthreads();
-  }
-  cp_async_wait<0>();
-}
-
-static int g_pipe_blocks[64];   // SMs of each device (one pipelined block per SM)
-
-static int pipe_blocks(int tiles) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) return tiles;
-  if (!g_pipe_blocks[dev]) {
-    int sms = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_pipe_blocks[dev] = sms > 0 ? sms : 1;
-  }
-  return tiles < g_pipe_blocks[dev] ? tiles : g_pipe_blocks[dev];
-}
-
-void launch_incstate_pipe(int W, int n1, int n2, float ht, const float* m_prev, const float* dX,
-                          const float* vt, const float* vtD, const float* G, const float* gm,
-                          float* out, float* b, cudaStream_t st) {
-  const int tiles = (n1 / 32) * (n2 / 32);
-  const dim3 grid(pipe_blocks(tiles));
-  const bool p2 = pow2_grid(n1, n2);
-  if (W == 48)
-    launch_k(p2 ? k_incstate_pipe<true, 48> : k_incstate_pipe<false, 48>, grid, dim3(kPipeT),
-             PipeDims<48, 10>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm,
-             out, b);
-  else
-    launch_k(p2 ? k_incstate_pipe<true, 64> : k_incstate_pipe<false, 64>, grid, dim3(kPipeT),
-             PipeDims<64, 10>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, m_prev, dX, vt, vtD, G, gm,
-             out, b);
-}
-
-void launch_adjoint_pipe(int W, int n1, int n2, float ht, float wb, const float* lam_next,
-                         const float* dY, const float* delta, const float* delta_bar,
-                         const float* gm, float* lam_out, float* b, cudaStream_t st) {
-  const int tiles = (n1 / 32) * (n2 / 32);
-  const dim3 grid(pipe_blocks(tiles));
-  const bool p2 = pow2_grid(n1, n2);
-  if (W == 48)
-    launch_k(p2 ? k_adjoint_pipe<true, 48> : k_adjoint_pipe<false, 48>, grid, dim3(kPipeT),
-             PipeDims<48, 8>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta,
-             delta_bar, gm, lam_out, b);
-  else
-    launch_k(p2 ? k_adjoint_pipe<true, 64> : k_adjoint_pipe<false, 64>, grid, dim3(kPipeT),
-             PipeDims<64, 8>::kSmemBytes, st, n1, n2, ilog2i(n1), ht, wb, lam_next, dY, delta,
-             delta_bar, gm, lam_out, b);
-}
-
 // box widths with a fused kernel: halo H = 8 and H = 16
 constexpr int kFuseW[2] = {48, 64};
 
@@ -1088,14 +803,6 @@ void fused_init() {
   allow_smem(k_incstate_fused<false, 48>, BoxDims<48>::kSmemBytes);
   allow_smem(k_incstate_fused<true, 64>, BoxDims<64>::kSmemBytes);
   allow_smem(k_incstate_fused<false, 64>, BoxDims<64>::kSmemBytes);
-  allow_smem(k_incstate_pipe<true, 48>, PipeDims<48, 10>::kSmemBytes);
-  allow_smem(k_incstate_pipe<false, 48>, PipeDims<48, 10>::kSmemBytes);
-  allow_smem(k_incstate_pipe<true, 64>, PipeDims<64, 10>::kSmemBytes);
-  allow_smem(k_incstate_pipe<false, 64>, PipeDims<64, 10>::kSmemBytes);
-  allow_smem(k_adjoint_pipe<true, 48>, PipeDims<48, 8>::kSmemBytes);
-  allow_smem(k_adjoint_pipe<false, 48>, PipeDims<48, 8>::kSmemBytes);
-  allow_smem(k_adjoint_pipe<true, 64>, PipeDims<64, 8>::kSmemBytes);
-  allow_smem(k_adjoint_pipe<false, 64>, PipeDims<64, 8>::kSmemBytes);
 }
 
 void launch_adjoint_fused(int W, int n1, int n2, float ht, float wb, const float* lam_next,

@@ -54,8 +54,7 @@ class reg_options(ctypes.Structure):
                 ("coarse_interp", ctypes.c_int), ("step_tile", ctypes.c_int), ("incompressible", ctypes.c_int),
                 ("hessian", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("flow_matvec", ctypes.c_int),
-                ("beta_w", ctypes.c_double), ("graph_pdl", ctypes.c_int),
-                ("pipeline_steps", ctypes.c_int)]
+                ("beta_w", ctypes.c_double), ("graph_pdl", ctypes.c_int)]
 
 
 class reg_info(ctypes.Structure):

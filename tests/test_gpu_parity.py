@@ -682,34 +682,6 @@ def test_flow_wait_timeout_is_reported(regnk):
     R.close()
 
 
-@pytest.mark.parametrize("n1,n2,nt,vmax", [(1024, 1024, 8, 0.2), (256, 128, 4, 1.0), (192, 96, 4, 1.0),
-                                           (128, 128, 4, 2.0), (32, 64, 3, 0.5)])
-def test_pipelined_steps_match_one_block_per_tile(regnk, n1, n2, nt, vmax):
-    """The persistent pipelined fused steps (pipeline_steps = 1: one block per
-    SM, next tile prefetched with cp.async) against one block per tile:
-    bitwise equal gradient and GN matvec (48^2 and, at vmax 2, 64^2 boxes;
-    power-of-two and 3*2^k grids; grids with fewer tiles than SMs)."""
-    m_R, m_T, _ = (f32(a) for a in problem_data(n1, n2))
-    v = f32(inputs.random_velocity(n1, n2, seed=37, vmax=vmax))
-    u = f32(inputs.random_velocity(n1, n2, seed=38, vmax=1.0))
-    out = {}
-    for pipe in (1, 0):
-        R = regnk.Registration(n1, n2, nt, 1e-2, pipeline_steps=pipe, precond=regnk.REG_PC_REG)
-        R.set_images(dev(m_R), dev(m_T))
-        g = torch.empty(2 * n1 * n2, device="cuda")
-        J = R.objective_gradient(dev(v), g)
-        H = torch.empty_like(g)
-        R.hessian_matvec(dev(v), dev(u), H)
-        H2 = torch.empty_like(g)
-        R.hessian_matvec(dev(v), dev(u), H2)       # replayed from a CUDA graph
-        torch.cuda.synchronize()
-        out[pipe] = (J, g.cpu(), H.cpu(), H2.cpu())
-        R.close()
-    assert out[1][0] == out[0][0]
-    for a, b in zip(out[1][1:], out[0][1:]):
-        assert torch.equal(a, b)
-
-
 @pytest.mark.parametrize("n", [0, 1, 3, 1000003, 2 * 1024 * 1024])
 def test_dot_matches_fp64(regnk, n):
     """reg_dot (compensated FP32 per thread, FP64 across threads) against the
