@@ -27,15 +27,33 @@ roofline  = the kernel class with the largest device time: algorithmic
             bytes / its CUDA-event time, from a profiled repeat of the timed
             steps (every launch bracketed by events on the launching stream,
             event nodes inside the replayed graphs), against the measured HBM
-            copy bandwidth.
+            copy bandwidth. Algorithmic bytes per grid point: 24 per
+            incremental state step, 16 per adjoint step (+16 for the first of
+            each solve, +8 for the last incremental state step: the
+            per-velocity inputs and the handover of b~), 4 N (10 nt + 16) per
+            GN matvec.
+roofline_gn_matvec = the fine GN matvec as one unit (the library call,
+            replayed from its CUDA graph) against 4 N (10 nt + 16) bytes.
 step_tiles = (threads per block, points per thread) of the unfused
             adjoint and incremental-state step kernels on each grid level, as
             reg_create's timing of the nine shapes chose them.
 cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
-            timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8.
+            timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8
+            on one core; one such matvec per core at once (process pool); and
+            the 64^2 analytic problem solved to ||g||rel 1e-2 on one core.
 plain_form = the same solve with FP32 reductions, no CUDA graphs and plain
-            launches (one solve after one warm-up, CUDA events): the "plain
-            FP32" form the chosen one is compared against.
+            launches (as many timed solves as the chosen form, after one
+            warm-up, CUDA events): the "plain FP32" form the chosen one is
+            compared against.
+solver_arms = the coarse solver of P_2L as nested PCG(0.1 eta) against
+            CHEB(10), and the coarse problem at the problem's nt and splines.
+fft_comparator = the hand-written spectral operator (beta A)^-1 on two fields
+            against cuFFT doing the same (torch.fft), 512^2 and 1024^2.
+config_256_512 = the 256^2 / 512^2 random-field configuration at nt 4, 8, 16:
+            GN matvecs/s, transport solves/s and gradients/s through the C ABI.
+batch64_chosen_vs_plain = 64 problems of uneven size: concurrent contexts
+            (CUDA graphs, FP64-accurate reductions) against the plain FP32
+            method one by one, 5 batches per arm.
 learned_warm_start = the trained warm-start network (weights committed with
             the package) measured outside the timed region: cold versus warm
             time to ||g||rel 1e-2 on held-out pairs of the learned-warm-start
@@ -878,6 +896,25 @@ def main():
         arms["coarse_problem_nt_and_spline"]["what"] = (
             "P_2L CHEB(10) with the coarse problem at nt = 8 and splines (library default)")
 
+    # ---- the fine GN Hessian matvec as one unit: CUDA events around the
+    # library call at the final velocity (replayed from its CUDA graph),
+    # against its algorithmic bytes 4 N (10 nt + 16) (every field read or
+    # written once; grad m_j stored, X_D, Y_D, div v computed once per velocity)
+    u_dir = torch.tensor(inputs.random_velocity(n, seed=8, vmax=1.0).astype(np.float32).ravel(), device=dev)
+    Hu = torch.empty_like(u_dir)
+    for _ in range(3):
+        R.hessian_matvec(v, u_dir, Hu)
+    torch.cuda.synchronize()
+    mv_ms = []
+    for _ in range(20):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        R.hessian_matvec(v, u_dir, Hu)
+        e1.record(st)
+        torch.cuda.synchronize()
+        mv_ms.append(e0.elapsed_time(e1))
+    b_mv = 4.0 * n * n * (10 * NT + 16)
+
     # ---- roofline of the dominant kernel class (per grid level)
     dom = max(prof, key=lambda k: prof[k][0])
     ms, nl, by = prof[dom]
@@ -900,6 +937,12 @@ def main():
             "algorithmic_bytes_per_launch": per_launch, "launches": nl,
             "share_of_device_time": ms / total_prof_ms,
             "classes_ms": {f"{k[0]}/{k[1]}": round(p[0], 3) for k, p in prof.items() if p[1]}}
+    t_mv = float(np.median(mv_ms)) / 1e3
+    roof_mv = {"unit": "GN Hessian matvec at 1024^2, nt = 8 (fine grid, graph replay, CUDA events, "
+                       "median of 20)",
+               "time_us": 1e6 * t_mv, "algorithmic_bytes": b_mv,
+               "achieved": b_mv / t_mv / 1e9, "peak": hbm, "unit_bw": "GB/s",
+               "frac": b_mv / t_mv / 1e9 / hbm}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -920,6 +963,7 @@ def main():
                         "d2h_bytes_per_step": int(h_v.numel() * 4)},
                 "gpu_launches": int(launches),
                 "roofline": roof,
+                "roofline_gn_matvec": roof_mv,
                 "step_tiles": {f"{lvl}/{ker}": list(t) for (lvl, ker), t in R.step_tiles().items()},
                 "plain_form": plain,
                 "solver_arms": arms,

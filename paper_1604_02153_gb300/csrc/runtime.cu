@@ -920,6 +920,18 @@ double objective(reg_ctx* c, Level& L) {
   return 0.5 * hh * c->hsc[S_J1] + 0.5 * hh * c->hsc[S_J2];
 }
 
+// Algorithmic bytes per grid point of the transport steps, as the
+// profile counts them (each field the step needs read once, each result
+// written once): an incremental state step moves m~_{j-1} in, m~_j out and
+// the two time-level fields G_j, grad m_j (24 B); the first also reads v~
+// and X_D, the matvec's per-velocity inputs (+16); the last also hands over
+// b~ (+8). An adjoint step moves lambda_{j+1} in, lambda_j out and grad m_j
+// (16 B); the first also reads Y_D, div v and div v(Y_D) (+16). The
+// kernels move more (the running sum b, v~(X_D) and v~ at every step):
+// those re-reads are the kernels' cost, not the method's.
+double kIncStepBytes(int j, int nt) { return 24.0 + (j == 1 ? 16.0 : 0.0) + (j == nt ? 8.0 : 0.0); }
+double kAdjStepBytes(bool first) { return 16.0 + (first ? 16.0 : 0.0); }
+
 // One fused adjoint step (prefilter of lambda_{j+1} inside the step) and one
 // fused incremental state step j >= 2 (b non-NULL for the last, j = nt,
 // where gmj is grad m_nt).
@@ -956,14 +968,14 @@ void gradient(reg_ctx* c, Level& L, float* g_out) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     if (hist) lam2 = hist + j * N;
     if (L.fuse_w) {   // prefilter of lambda_{j+1} inside the step
-      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      Prof P(c, REG_KC_ADJOINT_STEP, kAdjStepBytes(j == nt - 1) * N);
       adjoint_fused(c, L, wb, lam, L.gm + 2 * j * N, lam2, L.b);
       std::swap(lam, lam2);
       continue;
     }
     const float* cl = coefficients(c, L, lam, 1, L.coef);
     {
-      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      Prof P(c, REG_KC_ADJOINT_STEP, kAdjStepBytes(j == nt - 1) * N);
       launch_adjoint_step(L.tile_adj, gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar,
                           L.gm + 2 * j * N, lam2, L.b, L.lagrange, c->st);
     }
@@ -1123,14 +1135,14 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
     // m~_{j-1} inside the step; the last one also writes lambda~_nt and
     // starts b~ (the work of k_adjoint_init)
     {
-      Prof P(c, REG_KC_INCSTATE_STEP, 44.0 * N);
+      Prof P(c, REG_KC_INCSTATE_STEP, kIncStepBytes(1, nt) * N);
       launch_incstate_first_fused(L.fuse_w, gd.n1, gd.n2, ht, vt, L.dX, L.G, L.gm + 2 * N, L.vtD,
                                   mt2, c->st);
     }
     std::swap(mt, mt2);
     for (int j = 2; j <= nt; ++j) {
       const bool last = (j == nt);
-      Prof P(c, REG_KC_INCSTATE_STEP, (last ? 64.0 : 48.0) * N);
+      Prof P(c, REG_KC_INCSTATE_STEP, kIncStepBytes(j, nt) * N);
       incstate_fused(c, L, mt, vt, L.G + 2 * (j - 1) * N, L.gm + 2 * j * N, mt2,
                      last ? bacc : nullptr);
       std::swap(mt, mt2);
@@ -1147,7 +1159,7 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
       const float* cm = (j == 1) ? nullptr : coefficients(c, L, mt, 1, L.coef);
       const bool last = (j == nt && nt >= 2);
       {
-        Prof P(c, REG_KC_INCSTATE_STEP, (j == 1 ? 52.0 : (last ? 64.0 : 48.0)) * N);
+        Prof P(c, REG_KC_INCSTATE_STEP, kIncStepBytes(j, nt) * N);
         launch_incstate_step(L.tile_inc, gd.n1, gd.n2, ht, cm, L.dX, vt, L.vtD, L.G + 2 * (j - 1) * N,
                              L.gm + 2 * j * N, mt2, j == 1, lg, c->st, j == 1 ? cvt : nullptr,
                              last ? L.gm + 2 * nt * N : nullptr, last ? bacc : nullptr);
@@ -1172,14 +1184,14 @@ void hessian_core(reg_ctx* c, Level& L, const float* vt, float* out, bool data_o
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
     if (L.fuse_w) {   // prefilter of lambda~_{j+1} inside the step kernel
-      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      Prof P(c, REG_KC_ADJOINT_STEP, kAdjStepBytes(j == nt - 1) * N);
       adjoint_fused(c, L, wb, lt, L.gm + 2 * j * N, lt2, bacc);
       std::swap(lt, lt2);
       continue;
     }
     const float* cl = coefficients(c, L, lt, 1, L.coef);
     {
-      Prof P(c, REG_KC_ADJOINT_STEP, 48.0 * N);
+      Prof P(c, REG_KC_ADJOINT_STEP, kAdjStepBytes(j == nt - 1) * N);
       launch_adjoint_step(L.tile_adj, gd.n1, gd.n2, ht, wb, cl, L.dY, L.delta, L.delta_bar,
                           L.gm + 2 * j * N, lt2, bacc, lg, c->st);
     }
