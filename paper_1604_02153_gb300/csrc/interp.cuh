@@ -47,18 +47,22 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 // causal and an anticausal first-order recursion with pole z1 = sqrt(3) - 2:
 //     y[k] = s[k] + z1 y[k-1],   c'[k] = y[k] + z1 c'[k+1],   c = -6 z1 c'.
 // A block filters a 32x32 output tile: it stages the tile with a periodic
-// halo of kL = 13 samples on every side in shared memory. Along x, each of
+// halo of kL = 12 samples on every side in shared memory. Along x, each of
 // 4 threads per staged row produces 8 consecutive outputs, starting both
 // recursions kL samples outside its segment (the truncated start-up terms
-// decay as |z1|^13 < 4e-8, below FP32 resolution); along y, 4 threads per
-// column do the same. About 7 FMAs per sample and pass, in dependency chains
-// of 55 steps with 232 (x) and 128 (y) threads of the block busy.
+// decay as |z1|^12 < 1.5e-7, the order of the FP32 rounding of the
+// recursions themselves); along y, 4 threads per column do the same. About
+// 7 FMAs per sample and pass, in dependency chains of 52 steps with 224 (x)
+// and 128 (y) threads of the block busy. kL is a multiple of 4 so that the
+// staged region of a fused step kernel's box (which starts kL + 8 or kL + 16
+// samples left of a tile) begins on a 16-byte boundary: its rows are staged
+// with aligned float4 stores, and each chain of 32 samples is 8 float4.
 constexpr float kZ1 = -0.26794919243112270f;    // sqrt(3) - 2
 constexpr float kGain = 1.60769515458673624f;   // -6 z1
-constexpr int kL = 13;              // recursion start-up length (halo width)
+constexpr int kL = 12;              // recursion start-up length (halo width)
 constexpr int kPX = 32, kPY = 32;   // output tile
-constexpr int kPW = kPX + 2 * kL;   // staged tile width  (58)
-constexpr int kPH = kPY + 2 * kL;   // staged tile height (58)
+constexpr int kPW = kPX + 2 * kL;   // staged tile width  (56)
+constexpr int kPH = kPY + 2 * kL;   // staged tile height (56)
 constexpr int kPIn = kPW + 1;       // odd pitches: conflict-free row and column walks
 constexpr int kPMid = kPX + 1;
 constexpr int kPThreads = 256;
@@ -113,7 +117,7 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
     }
   }
   __syncthreads();
-  constexpr int kSeg = 8, kSegs = kPX / kSeg, kLen = kSeg + 2 * kL;   // 34 samples per chain
+  constexpr int kSeg = 8, kSegs = kPX / kSeg, kLen = kSeg + 2 * kL;   // 32 samples per chain
   if (t < kPH * kSegs) {   // x recursions: staged row t % kPH, segment t / kPH
     // (a warp walks 32 consecutive rows of one segment: with the odd pitch
     // its shared-memory accesses fall in 32 different banks)
@@ -150,7 +154,7 @@ __device__ __forceinline__ void prefilter_tile(const float* __restrict__ src, fl
 // barrier.
 // Pitches of the staged samples (rows) and of the x-pass output (stored
 // transposed, one column of the box per row of `mid`): multiples of 4 floats
-// with an odd quotient, so that each recursion chain reads its 34
+// with an odd quotient, so that each recursion chain reads its 32
 // consecutive samples as float4 and the 8 chains of a quarter warp (8
 // consecutive rows or columns) hit 8 different 16-byte bank groups.
 constexpr int quad_pitch(int n) { return ((n + 3) / 4) % 2 ? (n + 3) / 4 * 4 : (n + 3) / 4 * 4 + 4; }
@@ -177,6 +181,10 @@ constexpr int box_row_vectors() { return (BoxDims<W>::WS + 3 + 3) / 4; }
 template <int W>
 __device__ __forceinline__ void put_staged(float* stage, int r, int v, int off, float4 x) {
   using D = BoxDims<W>;
+  if (off == 0 && 4 * v + 3 < D::WS) {   // aligned whole vector (PS % 4 == 0)
+    *reinterpret_cast<float4*>(stage + r * D::PS + 4 * v) = x;
+    return;
+  }
   const float e[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
   for (int k = 0; k < 4; ++k) {

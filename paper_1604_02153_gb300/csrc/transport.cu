@@ -541,8 +541,8 @@ void launch_det_grad(long long N, const float* g, float* det, cudaStream_t st) {
 // coefficients of that box from the raw samples (prefilter_box, with the
 // same recursion segments as k_prefilter since H is a multiple of 8, so the
 // coefficients and the results are bitwise those of the two-kernel path)
-// and gathers from shared memory. Each thread handles kFP consecutive points
-// of a tile row, with vector streamed loads.
+// and gathers from shared memory. Each thread handles kFP points of a tile
+// row, kFS apart.
 
 template <int W>
 __device__ __forceinline__ void box_stencil(int lx, int ly, float d1, float d2, bool lagrange,
@@ -558,6 +558,30 @@ __device__ __forceinline__ void box_stencil(int lx, int ly, float d1, float d2, 
 // 48^2 box (74 x 6 x-segments, 48 x 6 y-segments) and two points per thread
 constexpr int kFT = 512;
 constexpr int kFP = 1024 / kFT;   // points per thread
+constexpr int kFS = 32 / kFP;     // their spacing along the tile row
+
+// The kFP points of a thread in a fused kernel are kFS apart in the tile row,
+// so that the 32 lanes of a warp touch consecutive columns for each point: the
+// 4x4 gathers from the shared-memory coefficient box then hit 32 different
+// banks (adjacent points per thread gave 2-way conflicts), and the streamed
+// loads and stores stay coalesced.
+template <int K>
+__device__ __forceinline__ void ldf(const float* p, float (&a)[K]) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) a[q] = __ldg(p + q * kFS);
+}
+
+template <int K>
+__device__ __forceinline__ void ldf_rw(const float* p, float (&a)[K]) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) a[q] = p[q * kFS];
+}
+
+template <int K>
+__device__ __forceinline__ void stf(float* p, const float (&a)[K]) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) p[q * kFS] = a[q];
+}
 
 template <bool P2, int W>
 __global__ void __launch_bounds__(kFT, 2)
@@ -574,35 +598,35 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;   // threads per tile row
-  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
   // the step's streamed operands are loaded first: their latency overlaps
   // the staging and the recursions of the prefilter
   float y1[kFP], y2[kFP], db[kFP], dd[kFP], g1[kFP], g2[kFP], b1[kFP], b2[kFP];
-  ldk(dY + idx, y1);
-  ldk(dY + N + idx, y2);
-  ldk(delta_bar + idx, db);
-  ldk(delta + idx, dd);
-  ldk(gm + idx, g1);
-  ldk(gm + N + idx, g2);
-  ldk_rw(b + idx, b1);
-  ldk_rw(b + N + idx, b2);
+  ldf(dY + idx, y1);
+  ldf(dY + N + idx, y2);
+  ldf(delta_bar + idx, db);
+  ldf(delta + idx, dd);
+  ldf(gm + idx, g1);
+  ldf(gm + N + idx, g2);
+  ldf_rw(b + idx, b1);
+  ldf_rw(b + N + idx, b2);
   prefilter_box<W, P2, kFT>(lam_next, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   float l[kFP];
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, y1[p], y2[p], false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + kFS * p, H + r, y1[p], y2[p], false, li, lj, w1, w2);
     const float lb = apply_box<D::PB>(stage, li, lj, w1, w2);
     const float lstar = fmaf(ht * lb, db[p], lb);
     l[p] = lb + 0.5f * ht * (lb * db[p] + lstar * dd[p]);
     b1[p] = fmaf(wb * l[p], g1[p], b1[p]);
     b2[p] = fmaf(wb * l[p], g2[p], b2[p]);
   }
-  stk(lam_out + idx, l);
-  stk(b + idx, b1);
-  stk(b + N + idx, b2);
+  stf(lam_out + idx, l);
+  stf(b + idx, b1);
+  stf(b + N + idx, b2);
 }
 
 // gm_nt, b: non-NULL for the last step j = nt, which writes the final
@@ -625,37 +649,37 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
-  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
   // streamed operands first (their latency overlaps the prefilter)
   float x1[kFP], x2[kFP], w1v[kFP], w2v[kFP], G1[kFP], G2[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
-  ldk(dX + idx, x1);
-  ldk(dX + N + idx, x2);
-  ldk(vtD + idx, w1v);
-  ldk(vtD + N + idx, w2v);
-  ldk(G + idx, G1);
-  ldk(G + N + idx, G2);
-  ldk(vt + idx, u1);
-  ldk(vt + N + idx, u2);
-  ldk(gm + idx, g1);
-  ldk(gm + N + idx, g2);
+  ldf(dX + idx, x1);
+  ldf(dX + N + idx, x2);
+  ldf(vtD + idx, w1v);
+  ldf(vtD + N + idx, w2v);
+  ldf(G + idx, G1);
+  ldf(G + N + idx, G2);
+  ldf(vt + idx, u1);
+  ldf(vt + N + idx, u2);
+  ldf(gm + idx, g1);
+  ldf(gm + N + idx, g2);
   prefilter_box<W, P2, kFT>(m_prev, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   float m[kFP];
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + kFS * p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
     m[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
     m[p] -= 0.5f * ht * (w1v[p] * G1[p] + w2v[p] * G2[p] + u1[p] * g1[p] + u2[p] * g2[p]);
   }
   if (!b) {
-    stk(out + idx, m);
+    stf(out + idx, m);
     return;
   }
   float gn1[kFP], gn2[kFP], lam[kFP], b1[kFP], b2[kFP];
-  ldk(gm_nt + idx, gn1);
-  ldk(gm_nt + N + idx, gn2);
+  ldf(gm_nt + idx, gn1);
+  ldf(gm_nt + N + idx, gn2);
   const float hh = 0.5f * ht;
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
@@ -663,9 +687,9 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
     b1[p] = hh * lam[p] * gn1[p];
     b2[p] = hh * lam[p] * gn2[p];
   }
-  stk(out + idx, lam);
-  stk(b + idx, b1);
-  stk(b + N + idx, b2);
+  stf(out + idx, lam);
+  stf(b + idx, b1);
+  stf(b + N + idx, b2);
 }
 
 // v~ at the departure points and the first incremental state step in one
@@ -689,7 +713,7 @@ k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restri
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
-  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
   // (the streamed operands are loaded after the two prefilters: loading
   // them first took more registers than two blocks per SM allow)
@@ -697,28 +721,28 @@ k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restri
   prefilter_box<W, P2, kFT>(vt + N, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
   (void)kBox;
   float x1[kFP], x2[kFP], Ga[kFP], Gb[kFP], u1[kFP], u2[kFP], g1[kFP], g2[kFP];
-  ldk(dX + idx, x1);
-  ldk(dX + N + idx, x2);
-  ldk(G1p + idx, Ga);
-  ldk(G1p + N + idx, Gb);
-  ldk(vt + idx, u1);
-  ldk(vt + N + idx, u2);
-  ldk(gm1 + idx, g1);
-  ldk(gm1 + N + idx, g2);
+  ldf(dX + idx, x1);
+  ldf(dX + N + idx, x2);
+  ldf(G1p + idx, Ga);
+  ldf(G1p + N + idx, Gb);
+  ldf(vt + idx, u1);
+  ldf(vt + N + idx, u2);
+  ldf(gm1 + idx, g1);
+  ldf(gm1 + N + idx, g2);
   float wd1[kFP], wd2[kFP], m[kFP];
 #pragma unroll
   for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + kFS * p, H + r, x1[p], x2[p], false, li, lj, w1, w2);
     wd1[p] = apply_box<D::PB>(box1, li, lj, w1, w2);
     wd2[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
     m[p] = 0.f;
     m[p] -= 0.5f * ht * (wd1[p] * Ga[p] + wd2[p] * Gb[p] + u1[p] * g1[p] + u2[p] * g2[p]);
   }
-  stk(vtD + idx, wd1);
-  stk(vtD + N + idx, wd2);
-  stk(out + idx, m);
+  stf(vtD + idx, wd1);
+  stf(vtD + N + idx, wd2);
+  stf(out + idx, m);
 }
 
 // Prefilter + gather of F = 1 or 2 fields (fstride apart) at the departure
@@ -738,11 +762,11 @@ k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long 
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
-  const int t = threadIdx.x, r = t / TPR, cx = (t % TPR) * kFP;
+  const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
   const long long idx = row_offset<P2>(y0 + r, n1, log1) + x0 + cx;
   float d1[kFP], d2[kFP];
-  ldk(disp + idx, d1);
-  ldk(disp + N + idx, d2);
+  ldf(disp + idx, d1);
+  ldf(disp + N + idx, d2);
   if (F == 2)
     prefilter_box<W, P2, kFT>(u, n1, n2, log1, x0 - H, y0 - H, stage, mid, box1);
   prefilter_box<W, P2, kFT>(u + (F - 1) * fstride, n1, n2, log1, x0 - H, y0 - H, stage, mid, stage);
@@ -751,15 +775,15 @@ k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long 
   for (int p = 0; p < kFP; ++p) {
     int li, lj;
     float w1[4], w2[4];
-    box_stencil<W>(H + cx + p, H + r, d1[p], d2[p], false, li, lj, w1, w2);
+    box_stencil<W>(H + cx + kFS * p, H + r, d1[p], d2[p], false, li, lj, w1, w2);
     if (F == 2) o1[p] = apply_box<D::PB>(box1, li, lj, w1, w2);
     o2[p] = apply_box<D::PB>(stage, li, lj, w1, w2);
   }
   if (F == 2) {
-    stk(out + idx, o1);
-    stk(out + fstride + idx, o2);
+    stf(out + idx, o1);
+    stf(out + fstride + idx, o2);
   } else {
-    stk(out + idx, o2);
+    stf(out + idx, o2);
   }
 }
 
