@@ -408,6 +408,55 @@ reg_status reg_batch_hessian_matvec(reg_batch* batch, const float* const* v,
                                     const float* const* vt, float* const* Hvt);
 const char* reg_batch_last_error(const reg_batch* batch);
 
+/* ---- Lockstep batches: one launch per step over every problem ------------
+ * B independent problems (any grids reg_create accepts, nt shared, beta[i]
+ * per problem) held in one set of device arrays with a table of (n1, n2,
+ * offset) per problem. Every semi-Lagrangian step (departure points, state,
+ * adjoint, incremental state and incremental adjoint steps, the gathers of
+ * div v and of the gradient history; eq. state-slm, eq. adj-slm,
+ * eq. inc-state-slm, eq. inc-adj-slm) is ONE kernel launch over the 32 x 32
+ * tiles of all problems; every FFT pass is one launch per run of problems
+ * with the same grid and beta (the batch orders the problems so that such
+ * runs are contiguous); every per-problem inner product and norm is one
+ * segmented reduction launch with an FP64 result per problem; the
+ * Gauss-Newton matvec is captured once as a CUDA graph and replayed by every
+ * PCG iteration. The Newton-Krylov method (§3.4.1) runs in lockstep: each
+ * problem follows its own iteration (gradient test, forcing term, PCG stop,
+ * Armijo step) and a device mask lets the kernels skip the problems that do
+ * not take part in a phase. Each problem's results are bitwise those of the
+ * one-problem calls on a context with the same options (the same kernels'
+ * arithmetic, the same reduction partition and order).
+ * Options: the defaults of reg_default_options except precond = REG_PC_REG
+ * (required: P_REG, §3.4.2); interp must be REG_INTERP_SPLINE, hessian GN,
+ * precision FP64, incompressible 0, beta_w 0, fused_transport 1,
+ * persistent_matvec 0; anything else returns REG_EINVAL. The steps run the
+ * fused prefilter+step kernels only: a velocity whose displacement per step
+ * exceeds their 64^2 box (14 cells) makes objective_gradient and
+ * hessian_matvec return REG_EINVAL, and inside reg_lockstep_solve an Armijo
+ * trial with such a displacement counts as a rejected trial (J = +inf),
+ * where a one-problem context would take the separate prefilter instead.
+ * Pointer arrays are host arrays of B device pointers, 16-byte aligned, with
+ * the per-problem layout of the single-problem calls. The batch runs on its
+ * own non-blocking stream; every call returns after synchronising it. */
+typedef struct reg_lockstep reg_lockstep;
+reg_status reg_lockstep_create(const reg_grid* grids, int B, int nt, const double* beta,
+                               const reg_options* opt, reg_lockstep** out);
+reg_status reg_lockstep_destroy(reg_lockstep* batch);
+/* Orders the batch's work after what is queued on cuda_stream so far. */
+reg_status reg_lockstep_set_stream(reg_lockstep* batch, void* cuda_stream);
+reg_status reg_lockstep_set_images(reg_lockstep* batch, const float* const* m_R,
+                                   const float* const* m_T);
+/* J[i] (host, B entries) and, if g is not NULL, g[i] for every problem. */
+reg_status reg_lockstep_objective_gradient(reg_lockstep* batch, const float* const* v, double* J,
+                                           float* const* g);
+reg_status reg_lockstep_hessian_matvec(reg_lockstep* batch, const float* const* v,
+                                       const float* const* vt, float* const* Hvt);
+/* reg_solve of every problem in lockstep; v[i] is the initial guess and
+ * receives the result; infos (host, B entries) may be NULL (seconds is the
+ * whole batch's wall time). Returns as reg_batch_solve. */
+reg_status reg_lockstep_solve(reg_lockstep* batch, float* const* v, double gtol, reg_info* infos);
+const char* reg_lockstep_last_error(const reg_lockstep* batch);
+
 /* ---- Learned warm start (no counterpart in the paper) --------------------
  * A U-Net maps an image pair (m_R, m_T) on an S x S grid to a stationary
  * velocity v_0 from which reg_solve starts; the solve runs to the same

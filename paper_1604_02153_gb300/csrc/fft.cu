@@ -324,7 +324,9 @@ k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__
 }
 
 // 3. inverse row transforms (half spectrum -> real rows), optional addend.
-template <int L, int T>
+// CHEB: the Chebyshev epilogue (a separate instantiation: its prefetched
+// operands would otherwise set the register count of every inverse pass).
+template <int L, int T, bool CHEB>
 __global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
@@ -340,7 +342,7 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
   // transform
   constexpr int kOut = (P * N + NT - 1) / NT;
   float cr_[kOut][2], cd_[kOut][2], cx_[kOut][2];
-  if (!cheb.r && add) {   // plain pass: the addend is prefetched into cr_
+  if (!CHEB && add) {   // plain pass: the addend is prefetched into cr_
     const float* ad0 = add + (long long)blockIdx.y * astride;
 #pragma unroll
     for (int u = 0; u < kOut; ++u) {
@@ -353,7 +355,7 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
       }
     }
   }
-  if (cheb.r) {
+  if (CHEB) {
     const long long fo = (long long)blockIdx.y * fstride;
 #pragma unroll
     for (int u = 0; u < kOut; ++u) {
@@ -400,7 +402,7 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
   fft_smem<L, T, P, NT, true>(sm, tw);
   float* dst = out + (long long)blockIdx.y * fstride;
   const float* ad = add ? add + (long long)blockIdx.y * astride : nullptr;
-  if (cheb.r) {
+  if (CHEB) {
     // Ad is never stored. The addend is d itself (already in cd_), and r, d
     // and x are read and overwritten here by the same thread.
     const long long fo = (long long)blockIdx.y * fstride;
@@ -694,7 +696,10 @@ static void launch_c2r(const float2* spec, long long sstride, float* out, long l
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  launch_k(k_rows_c2r<L, T>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
+  if (cheb.r)
+    launch_k(k_rows_c2r<L, T, true>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
+  else
+    launch_k(k_rows_c2r<L, T, false>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
 }
 
 template <int LI, int LO, int T>

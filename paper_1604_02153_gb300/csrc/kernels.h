@@ -249,4 +249,95 @@ void launch_fill(float* x, long long n, float value, cudaStream_t st);
 void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st);
 int reduce_partials();
 
+// ---------------------------------------------------------------------------
+// Batches of problems advanced in lockstep (lockstep.cu): one launch per
+// transport step over the 32 x 32 tiles of every problem of the batch.
+//
+// Every array of a batch holds, for each problem p in order, a block of F
+// grid-sized fields (F fixed per array: 1 for a scalar field, 2 for a vector
+// field, nt + 1 for a state history, ...), so problem p's block starts at
+// F * off_p with off_p the sum of the earlier problems' point counts, and its
+// field k at F * off_p + k * N_p. A BRef names field k of such an array for
+// every problem at once.
+struct BDesc {
+  int n1, n2;
+  int log1;          // log2(n1) when both lengths are powers of two, else -1
+  int p2;            // both lengths powers of two
+  long long off;     // off_p (a multiple of 1024)
+  float s1, s2;      // h_t n_i / (2 pi): velocity to cells per time step
+};
+
+struct BRef {
+  float* base;       // NULL: no such field (an optional argument)
+  int F;             // fields per problem in the array
+  int k;             // field index within the problem's block
+};
+
+// What the batched kernels read about the batch. w and mask are written on
+// the device (w, per velocity) and by the host (mask, per phase).
+struct BatchView {
+  const BDesc* desc;   // per problem
+  const int* w;        // box width of the fused kernels (48 or 64; 0: a
+                       // displacement beyond their halo: the problem's
+                       // blocks skip the step)
+  const int* mask;     // nonzero: the problem takes part in this phase
+  const int4* tiles;   // per tile block: problem, tile column, tile row
+  const int* pmap;     // per 1024 consecutive points of the batch: problem
+  int ntiles;
+};
+
+// Per-problem partition of a reduction over L fields of each problem
+// (L * N_p values), the same as the one-problem reduction of L * N_p
+// values uses: nb[p] blocks whose partial sums sit at partial[first[p] ..].
+struct SegView {
+  const int2* blocks;  // per block: problem, block index within the problem
+  const int* nb;       // per problem
+  const int* first;    // per problem
+  int nblocks;
+};
+
+// transport.cu
+// h_t n / (2 pi) in FP32: a velocity in radians per unit time to cells per step
+float departure_scale(float ht, int n);
+void batch_fused_init();
+void launch_prefilter_b(const BatchView& B, BRef in, BRef out, int F, cudaStream_t st);
+void launch_departure_b(const BatchView& B, long long npts, BRef v, BRef cv, BRef dX, BRef dY,
+                        cudaStream_t st);
+void launch_copy_field_b(const BatchView& B, long long npts, BRef src, BRef dst, cudaStream_t st);
+void launch_set_w_b(int nprob, const double* dmax_x, const double* dmax_y, int* w, cudaStream_t st);
+void launch_adjoint_init_b(const BatchView& B, long long npts, float coef_b, BRef mR, BRef m1,
+                           BRef gm, BRef lam, BRef b, float sign, cudaStream_t st);
+void launch_gather_fused_b(const BatchView& B, BRef u, int F, BRef disp, BRef out,
+                           cudaStream_t st);
+void launch_adjoint_fused_b(const BatchView& B, float ht, float wb, BRef lam_next, BRef dY,
+                            BRef delta, BRef delta_bar, BRef gm, BRef lam_out, BRef b,
+                            cudaStream_t st);
+void launch_incstate_first_fused_b(const BatchView& B, float ht, BRef vt, BRef dX, BRef G1,
+                                   BRef gm1, BRef vtD, BRef out, cudaStream_t st);
+void launch_incstate_fused_b(const BatchView& B, float ht, BRef m_prev, BRef dX, BRef vt,
+                             BRef vtD, BRef G, BRef gm, BRef out, BRef gm_nt, BRef b,
+                             cudaStream_t st);
+
+// reduce.cu: per-problem sums (FP64 result per problem in out[p]) with the
+// arithmetic and summation order of the one-problem reductions, masked
+// problems skipped; per-problem Krylov updates.
+void launch_dot_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a, BRef b,
+                  int L, double* partial, double* out, cudaStream_t st);
+void launch_sumsq_diff_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
+                         BRef b, int L, double* partial, double* out, cudaStream_t st);
+void launch_maxabs_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
+                     int L, float* partial, double* out, cudaStream_t st);
+// z = a_p x + b_p y on the problems of the mask (arrays of F fields per
+// problem, n = F * total points; a_p, b_p per problem; y may be NULL)
+void launch_lincomb_b(const int* pmap, const int* mask, int F, long long n, const float* a,
+                      const float* x, const float* b, const float* y, float* z, cudaStream_t st);
+void launch_pcg_update_b(const int* pmap, const int* mask, int F, long long n, const double* rz,
+                         const double* pq, const float* p, const float* q, float* x, float* r,
+                         cudaStream_t st);
+void launch_pcg_direction_b(const int* pmap, const int* mask, int F, long long n,
+                            const double* rz_new, const double* rz_old, const float* z,
+                            float* p, cudaStream_t st);
+void launch_copy_scalars_b(int nprob, const int* mask, const double* src, double* dst,
+                           cudaStream_t st);
+
 }  // namespace regnk

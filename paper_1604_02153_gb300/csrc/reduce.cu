@@ -80,27 +80,35 @@ __device__ __forceinline__ void pair_term(Pair& a, float x, float y) {
   }
 }
 
-// mode 0: sum a*b; mode 1: sum (a-b)^2
+// Block `bi` of `nblk` of the two-stage sum over n values: mode 0: sum
+// a*b; mode 1: sum (a-b)^2. The result is valid in thread 0.
 template <int MODE>
-__global__ void __launch_bounds__(kRT)
-k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
-          double* __restrict__ partial, int vec4) {
-  pdl_enter();
+__device__ __forceinline__ double partial_sum(const float* __restrict__ a,
+                                              const float* __restrict__ b, long long n, int nblk,
+                                              int bi, int vec4) {
   Pair acc;
-  const long long stride = (long long)gridDim.x * kRT;
+  const long long stride = (long long)nblk * kRT;
   const long long n4 = vec4 ? (n >> 2) : 0;   // float4 path only for 16-byte aligned inputs
   const float4* a4 = reinterpret_cast<const float4*>(a);
   const float4* b4 = reinterpret_cast<const float4*>(b);
-  for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n4; i += stride) {
+  for (long long i = (long long)bi * kRT + threadIdx.x; i < n4; i += stride) {
     const float4 x = __ldg(a4 + i), y = __ldg(b4 + i);
     pair_term<MODE>(acc, x.x, y.x);
     pair_term<MODE>(acc, x.y, y.y);
     pair_term<MODE>(acc, x.z, y.z);
     pair_term<MODE>(acc, x.w, y.w);
   }
-  for (long long i = (n4 << 2) + (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride)
+  for (long long i = (n4 << 2) + (long long)bi * kRT + threadIdx.x; i < n; i += stride)
     pair_term<MODE>(acc, __ldg(a + i), __ldg(b + i));
-  const double s = block_sum((double)acc.s + (double)acc.c);
+  return block_sum((double)acc.s + (double)acc.c);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kRT)
+k_partial(const float* __restrict__ a, const float* __restrict__ b, long long n,
+          double* __restrict__ partial, int vec4) {
+  pdl_enter();
+  const double s = partial_sum<MODE>(a, b, n, gridDim.x, blockIdx.x, vec4);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
@@ -131,12 +139,16 @@ k_final_sum_fp32(const double* __restrict__ partial, int nb, double* __restrict_
   if (threadIdx.x == 0) *out = (double)s;
 }
 
+__device__ __forceinline__ double final_sum(const double* __restrict__ partial, int nb) {
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nb; i += kRT) acc += partial[i];
+  return block_sum(acc);
+}
+
 __global__ void __launch_bounds__(kRT)
 k_final_sum(const double* __restrict__ partial, int nb, double* __restrict__ out) {
   pdl_enter();
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nb; i += kRT) acc += partial[i];
-  const double s = block_sum(acc);
+  const double s = final_sum(partial, nb);
   if (threadIdx.x == 0) *out = s;
 }
 
@@ -167,12 +179,12 @@ void launch_sumsq_diff(const float* a, const float* b, long long n, double* part
   launch_sum<1>(a, b, n, partial, out, st);
 }
 
-__global__ void __launch_bounds__(kRT)
-k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ partial) {
-  pdl_enter();
+// block `bi` of `nblk`: the largest |a_i| (NaN propagates), valid in thread 0
+__device__ __forceinline__ float partial_maxabs(const float* __restrict__ a, long long n, int nblk,
+                                                int bi) {
   float m = 0.f;
-  const long long stride = (long long)gridDim.x * kRT;
-  for (long long i = (long long)blockIdx.x * kRT + threadIdx.x; i < n; i += stride) {
+  const long long stride = (long long)nblk * kRT;
+  for (long long i = (long long)bi * kRT + threadIdx.x; i < n; i += stride) {
     const float x = fabsf(__ldg(a + i));
     m = (x > m || x != x) ? x : m;  // NaN propagates
   }
@@ -181,20 +193,28 @@ k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ p
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) ws[w] = m;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float r = ws[0];
+  float r = ws[0];
+  if (threadIdx.x == 0)
     for (int k = 1; k < kRT / 32; ++k) r = (ws[k] > r || ws[k] != ws[k]) ? ws[k] : r;
-    partial[blockIdx.x] = r;
-  }
+  return r;
+}
+
+__device__ __forceinline__ double final_maxabs(const float* __restrict__ partial, int nb) {
+  float r = 0.f;
+  for (int i = 0; i < nb; ++i) r = (partial[i] > r || partial[i] != partial[i]) ? partial[i] : r;
+  return (double)r;
+}
+
+__global__ void __launch_bounds__(kRT)
+k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ partial) {
+  pdl_enter();
+  const float r = partial_maxabs(a, n, gridDim.x, blockIdx.x);
+  if (threadIdx.x == 0) partial[blockIdx.x] = r;
 }
 
 __global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double* out) {
   pdl_enter();
-  if (threadIdx.x == 0) {
-    float r = 0.f;
-    for (int i = 0; i < nb; ++i) r = (partial[i] > r || partial[i] != partial[i]) ? partial[i] : r;
-    *out = (double)r;
-  }
+  if (threadIdx.x == 0) *out = final_maxabs(partial, nb);
 }
 
 void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st) {
@@ -219,13 +239,18 @@ void launch_compare(const float* a, const float* b, long long n, int* flag, cuda
            reinterpret_cast<const unsigned*>(b), n, flag);
 }
 
+__device__ __forceinline__ float lincomb_elem(float a, const float* x, float b, const float* y,
+                                              long long i) {
+  return y ? fmaf(b, y[i], a * x[i]) : a * x[i];
+}
+
 // z may alias x or y (elementwise, same index)
 __global__ void k_lincomb(long long n, float a, const float* x, float b, const float* y,
                           float* z) {
   pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-    z[i] = a * x[i] + (y ? b * y[i] : 0.f);
+    z[i] = lincomb_elem(a, x, b, y, i);
 }
 
 void launch_lincomb(long long n, float a, const float* x, float b, const float* y, float* z,
@@ -296,6 +321,161 @@ __global__ void k_splitmix(float* x, long long n, unsigned long long seed) {
 
 void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st) {
   launch_k(k_splitmix, dim3(nblocks(n)), dim3(kRT), 0, st, x, n, seed);
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms (one launch over every problem of a batch, see SegView and
+// BatchView): each problem's sums use its own partition and the device
+// functions above, so every per-problem result is bitwise that of the
+// one-problem reduction.
+
+__device__ __forceinline__ const float* bref_c(const BRef& r, const BDesc& D) {
+  return r.base + (long long)r.F * D.off + (long long)r.k * D.n1 * D.n2;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kRT)
+k_partial_b(const BDesc* __restrict__ desc, SegView S, const int* __restrict__ mask, BRef a,
+            BRef b, int L, double* __restrict__ partial) {
+  pdl_enter();
+  const int2 sb = S.blocks[blockIdx.x];
+  if (!mask[sb.x]) return;
+  const BDesc D = desc[sb.x];
+  const float* pa = bref_c(a, D);
+  const float* pb = bref_c(b, D);
+  const int vec4 = ((reinterpret_cast<uintptr_t>(pa) | reinterpret_cast<uintptr_t>(pb)) & 15u) == 0;
+  const double s = partial_sum<MODE>(pa, pb, (long long)L * D.n1 * D.n2, S.nb[sb.x], sb.y, vec4);
+  if (threadIdx.x == 0) partial[S.first[sb.x] + sb.y] = s;
+}
+
+__global__ void __launch_bounds__(kRT)
+k_final_sum_b(SegView S, const int* __restrict__ mask, const double* __restrict__ partial,
+              double* __restrict__ out) {
+  pdl_enter();
+  const int p = blockIdx.x;
+  if (!mask[p]) return;
+  const double s = final_sum(partial + S.first[p], S.nb[p]);
+  if (threadIdx.x == 0) out[p] = s;
+}
+
+__global__ void __launch_bounds__(kRT)
+k_maxabs_partial_b(const BDesc* __restrict__ desc, SegView S, const int* __restrict__ mask,
+                   BRef a, int L, float* __restrict__ partial) {
+  pdl_enter();
+  const int2 sb = S.blocks[blockIdx.x];
+  if (!mask[sb.x]) return;
+  const BDesc D = desc[sb.x];
+  const float r = partial_maxabs(bref_c(a, D), (long long)L * D.n1 * D.n2, S.nb[sb.x], sb.y);
+  if (threadIdx.x == 0) partial[S.first[sb.x] + sb.y] = r;
+}
+
+__global__ void k_maxabs_final_b(int nprob, SegView S, const int* __restrict__ mask,
+                                 const float* __restrict__ partial, double* __restrict__ out) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob || !mask[p]) return;
+  out[p] = final_maxabs(partial + S.first[p], S.nb[p]);
+}
+
+template <int MODE>
+static void launch_sum_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
+                         BRef b, int L, double* partial, double* out, cudaStream_t st) {
+  launch_k(k_partial_b<MODE>, dim3(S.nblocks), dim3(kRT), 0, st, desc, S, mask, a, b, L, partial);
+  launch_k(k_final_sum_b, dim3(nprob), dim3(kRT), 0, st, S, mask, partial, out);
+}
+
+void launch_dot_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a, BRef b,
+                  int L, double* partial, double* out, cudaStream_t st) {
+  launch_sum_b<0>(desc, S, nprob, mask, a, b, L, partial, out, st);
+}
+
+void launch_sumsq_diff_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
+                         BRef b, int L, double* partial, double* out, cudaStream_t st) {
+  launch_sum_b<1>(desc, S, nprob, mask, a, b, L, partial, out, st);
+}
+
+void launch_maxabs_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
+                     int L, float* partial, double* out, cudaStream_t st) {
+  launch_k(k_maxabs_partial_b, dim3(S.nblocks), dim3(kRT), 0, st, desc, S, mask, a, L, partial);
+  launch_k(k_maxabs_final_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, S, mask, partial,
+           out);
+}
+
+// problem of element e of an array of F fields per problem
+__device__ __forceinline__ int elem_problem(const int* __restrict__ pmap, int F, long long e) {
+  return pmap[(F == 1 ? e : e >> 1) >> 10];
+}
+
+__global__ void k_lincomb_b(const int* __restrict__ pmap, const int* __restrict__ mask, int F,
+                            long long n, const float* __restrict__ a, const float* x,
+                            const float* __restrict__ b, const float* y, float* z) {
+  pdl_enter();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int p = elem_problem(pmap, F, i);
+    if (mask[p]) z[i] = lincomb_elem(a[p], x, b ? b[p] : 0.f, y, i);
+  }
+}
+
+void launch_lincomb_b(const int* pmap, const int* mask, int F, long long n, const float* a,
+                      const float* x, const float* b, const float* y, float* z, cudaStream_t st) {
+  launch_k(k_lincomb_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, a, x, b, y, z);
+}
+
+__global__ void k_pcg_update_b(const int* __restrict__ pmap, const int* __restrict__ mask, int F,
+                               long long n, const double* __restrict__ rz,
+                               const double* __restrict__ pq, const float* __restrict__ p,
+                               const float* __restrict__ q, float* __restrict__ x,
+                               float* __restrict__ r) {
+  pdl_enter();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int k = elem_problem(pmap, F, i);
+    if (!mask[k] || !(pq[k] > 0.0)) continue;
+    const double ad = rz[k] / pq[k];
+    const float alpha = (float)ad;
+    x[i] = fmaf(alpha, p[i], x[i]);
+    r[i] = fmaf(-alpha, q[i], r[i]);
+  }
+}
+
+void launch_pcg_update_b(const int* pmap, const int* mask, int F, long long n, const double* rz,
+                         const double* pq, const float* p, const float* q, float* x, float* r,
+                         cudaStream_t st) {
+  launch_k(k_pcg_update_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, rz, pq, p, q, x, r);
+}
+
+__global__ void k_pcg_direction_b(const int* __restrict__ pmap, const int* __restrict__ mask,
+                                  int F, long long n, const double* __restrict__ rz_new,
+                                  const double* __restrict__ rz_old, const float* __restrict__ z,
+                                  float* __restrict__ p) {
+  pdl_enter();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int k = elem_problem(pmap, F, i);
+    if (!mask[k]) continue;
+    const float beta = (float)(rz_new[k] / rz_old[k]);
+    p[i] = fmaf(beta, p[i], z[i]);
+  }
+}
+
+void launch_pcg_direction_b(const int* pmap, const int* mask, int F, long long n,
+                            const double* rz_new, const double* rz_old, const float* z,
+                            float* p, cudaStream_t st) {
+  launch_k(k_pcg_direction_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, rz_new, rz_old,
+           z, p);
+}
+
+__global__ void k_copy_scalars_b(int nprob, const int* __restrict__ mask,
+                                 const double* __restrict__ src, double* __restrict__ dst) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < nprob && mask[p]) dst[p] = src[p];
+}
+
+void launch_copy_scalars_b(int nprob, const int* mask, const double* src, double* dst,
+                           cudaStream_t st) {
+  launch_k(k_copy_scalars_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, mask, src, dst);
 }
 
 }  // namespace regnk

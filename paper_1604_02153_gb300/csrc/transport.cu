@@ -8,6 +8,7 @@
 // node index and the sub-cell offset stay separate in FP32: the stencil base
 // is i + floor(d) and the weights use t = d - floor(d), both exact.
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 #include "interp.cuh"
@@ -56,14 +57,12 @@ constexpr int kPT = 256;  // threads per block of the pointwise kernels
 //   Y* = x + h_t v(x),  Y_D = x + h_t/2 (v(x) + v(Y*))
 // cv holds the interpolation coefficients of v (spline) or v itself.
 template <bool P2>
-__global__ void __launch_bounds__(kPT)
-k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restrict__ v,
-            const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
-            int lagrange) {
-  pdl_enter();
+__device__ __forceinline__ void departure_point(long long idx, int n1, int n2, int log1, float s1,
+                                                float s2, const float* __restrict__ v,
+                                                const float* __restrict__ cv,
+                                                float* __restrict__ dX, float* __restrict__ dY,
+                                                int lagrange) {
   const long long N = (long long)n1 * n2;
-  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
-  if (idx >= N) return;
   int i, j;
   split_index<P2>(idx, n1, log1, i, j);
   const float v1 = __ldg(v + idx), v2 = __ldg(v + N + idx);
@@ -82,11 +81,24 @@ k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restric
   }
 }
 
+template <bool P2>
+__global__ void __launch_bounds__(kPT)
+k_departure(int n1, int n2, int log1, float s1, float s2, const float* __restrict__ v,
+            const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
+            int lagrange) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (idx >= (long long)n1 * n2) return;
+  departure_point<P2>(idx, n1, n2, log1, s1, s2, v, cv, dX, dY, lagrange);
+}
+
+float departure_scale(float ht, int n) { return ht * n / (2.0f * 3.14159265358979323846f); }
+
 void launch_departure(int n1, int n2, float ht, const float* v, const float* cv, float* dX,
                       float* dY, int lagrange, cudaStream_t st) {
   const long long N = (long long)n1 * n2;
-  const float s1 = ht * n1 / (2.0f * 3.14159265358979323846f);
-  const float s2 = ht * n2 / (2.0f * 3.14159265358979323846f);
+  const float s1 = departure_scale(ht, n1);
+  const float s2 = departure_scale(ht, n2);
   launch_k(pick(n1, n2, k_departure<true>, k_departure<false>), dim3((unsigned)((N + kPT - 1) / kPT)),
            dim3(kPT), 0, st, n1, n2, ilog2i(n1), s1, s2, v, cv, dX, dY, lagrange);
 }
@@ -194,6 +206,19 @@ void launch_state_step(int n1, int n2, const float* coef, const float* dX, float
 // Final condition of an adjoint solve and the first term of its time
 // integral: lam = sign * (mR - m1) (mR may be NULL: lam = -sign * m1),
 // b = coef_b * lam * grad m.
+__device__ __forceinline__ void adjoint_init_point(long long idx, long long N, float coef_b,
+                                                   const float* __restrict__ mR,
+                                                   const float* __restrict__ m1,
+                                                   const float* __restrict__ gm,
+                                                   float* __restrict__ lam, float* __restrict__ b,
+                                                   float sign) {
+  const float r = (mR ? __ldg(mR + idx) : 0.f) - __ldg(m1 + idx);
+  const float l = sign * r;
+  lam[idx] = l;
+  b[idx] = coef_b * l * __ldg(gm + idx);
+  b[N + idx] = coef_b * l * __ldg(gm + N + idx);
+}
+
 __global__ void __launch_bounds__(kPT)
 k_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
                const float* __restrict__ m1, const float* __restrict__ gm,
@@ -201,11 +226,7 @@ k_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
   pdl_enter();
   const long long idx = (long long)blockIdx.x * kPT + threadIdx.x;
   if (idx >= N) return;
-  const float r = (mR ? __ldg(mR + idx) : 0.f) - __ldg(m1 + idx);
-  const float l = sign * r;
-  lam[idx] = l;
-  b[idx] = coef_b * l * __ldg(gm + idx);
-  b[N + idx] = coef_b * l * __ldg(gm + N + idx);
+  adjoint_init_point(idx, N, coef_b, mR, m1, gm, lam, b, sign);
 }
 
 void launch_adjoint_init(int n1, int n2, float coef_b, const float* mR, const float* m1,
@@ -583,19 +604,20 @@ __device__ __forceinline__ void stf(float* p, const float (&a)[K]) {
   for (int q = 0; q < K; ++q) p[q * kFS] = a[q];
 }
 
+// The bodies of the fused kernels take the tile origin (x0, y0) and the
+// block's dynamic shared memory, so that the one-problem kernels (tile =
+// blockIdx) and the batched kernels (tile from a table over many problems)
+// run the same code.
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT, 2)
-k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
-                const float* __restrict__ dY, const float* __restrict__ delta,
-                const float* __restrict__ delta_bar, const float* __restrict__ gm,
-                float* __restrict__ lam_out, float* __restrict__ b) {
-  pdl_enter();
+__device__ __forceinline__ void adjoint_fused_body(
+    int n1, int n2, int log1, int x0, int y0, float* sm, float ht, float wb,
+    const float* __restrict__ lam_next, const float* __restrict__ dY,
+    const float* __restrict__ delta, const float* __restrict__ delta_bar,
+    const float* __restrict__ gm, float* __restrict__ lam_out, float* __restrict__ b) {
   using D = BoxDims<W>;
   constexpr int H = (W - 32) / 2;
-  extern __shared__ float sm[];
   float* stage = sm;
   float* mid = sm + D::kStage;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;   // threads per tile row
   const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
@@ -629,24 +651,32 @@ k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __res
   stf(b + N + idx, b2);
 }
 
+template <bool P2, int W>
+__global__ void __launch_bounds__(kFT, 2)
+k_adjoint_fused(int n1, int n2, int log1, float ht, float wb, const float* __restrict__ lam_next,
+                const float* __restrict__ dY, const float* __restrict__ delta,
+                const float* __restrict__ delta_bar, const float* __restrict__ gm,
+                float* __restrict__ lam_out, float* __restrict__ b) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  adjoint_fused_body<P2, W>(n1, n2, log1, blockIdx.x * 32, blockIdx.y * 32, sm, ht, wb, lam_next,
+                            dY, delta, delta_bar, gm, lam_out, b);
+}
+
 // gm_nt, b: non-NULL for the last step j = nt, which writes the final
 // condition of the incremental adjoint, lambda~_nt = -m~_nt, to `out` and
 // starts its time integral, b = h_t/2 lambda~_nt grad m_nt (the work of
 // k_adjoint_init).
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT, 2)
-k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
-                 const float* __restrict__ dX, const float* __restrict__ vt,
-                 const float* __restrict__ vtD, const float* __restrict__ G,
-                 const float* __restrict__ gm, float* __restrict__ out,
-                 const float* __restrict__ gm_nt, float* __restrict__ b) {
-  pdl_enter();
+__device__ __forceinline__ void incstate_fused_body(
+    int n1, int n2, int log1, int x0, int y0, float* sm, float ht,
+    const float* __restrict__ m_prev, const float* __restrict__ dX, const float* __restrict__ vt,
+    const float* __restrict__ vtD, const float* __restrict__ G, const float* __restrict__ gm,
+    float* __restrict__ out, const float* __restrict__ gm_nt, float* __restrict__ b) {
   using D = BoxDims<W>;
   constexpr int H = (W - 32) / 2;
-  extern __shared__ float sm[];
   float* stage = sm;
   float* mid = sm + D::kStage;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
   const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
@@ -692,25 +722,34 @@ k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m
   stf(b + N + idx, b2);
 }
 
+template <bool P2, int W>
+__global__ void __launch_bounds__(kFT, 2)
+k_incstate_fused(int n1, int n2, int log1, float ht, const float* __restrict__ m_prev,
+                 const float* __restrict__ dX, const float* __restrict__ vt,
+                 const float* __restrict__ vtD, const float* __restrict__ G,
+                 const float* __restrict__ gm, float* __restrict__ out,
+                 const float* __restrict__ gm_nt, float* __restrict__ b) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  incstate_fused_body<P2, W>(n1, n2, log1, blockIdx.x * 32, blockIdx.y * 32, sm, ht, m_prev, dX,
+                             vt, vtD, G, gm, out, gm_nt, b);
+}
+
 // v~ at the departure points and the first incremental state step in one
 // kernel: both components of v~ are prefiltered on the tile's box, gathered
 // at X_D (written to vtD, needed by every later step) and
 // m~_1 = -h_t/2 (v~(X_D) . grad m_0(X_D) + v~ . grad m_1) (m~_0 = 0).
 template <bool P2, int W>
-__global__ void __launch_bounds__(kFT, 2)
-k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restrict__ vt,
-                       const float* __restrict__ dX, const float* __restrict__ G1p,
-                       const float* __restrict__ gm1, float* __restrict__ vtD,
-                       float* __restrict__ out) {
-  pdl_enter();
+__device__ __forceinline__ void incstate_first_fused_body(
+    int n1, int n2, int log1, int x0, int y0, float* sm, float ht, const float* __restrict__ vt,
+    const float* __restrict__ dX, const float* __restrict__ G1p, const float* __restrict__ gm1,
+    float* __restrict__ vtD, float* __restrict__ out) {
   using D = BoxDims<W>;
   constexpr int H = (W - 32) / 2;
   constexpr int kBox = W * D::PB;
-  extern __shared__ float sm[];
   float* stage = sm;
   float* mid = sm + D::kStage;
   float* box1 = mid + D::kMid;
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
   const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
@@ -745,21 +784,32 @@ k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restri
   stf(out + idx, m);
 }
 
+template <bool P2, int W>
+__global__ void __launch_bounds__(kFT, 2)
+k_incstate_first_fused(int n1, int n2, int log1, float ht, const float* __restrict__ vt,
+                       const float* __restrict__ dX, const float* __restrict__ G1p,
+                       const float* __restrict__ gm1, float* __restrict__ vtD,
+                       float* __restrict__ out) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  incstate_first_fused_body<P2, W>(n1, n2, log1, blockIdx.x * 32, blockIdx.y * 32, sm, ht, vt, dX,
+                                   G1p, gm1, vtD, out);
+}
+
 // Prefilter + gather of F = 1 or 2 fields (fstride apart) at the departure
 // points disp, on the tile's box: the state step m_j = m_{j-1}(X_D) and the
 // history G_j = grad m_{j-1}(X_D) without a coefficient field in memory.
 template <bool P2, int W, int F>
-__global__ void __launch_bounds__(kFT, 2)
-k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long fstride,
-               const float* __restrict__ disp, float* __restrict__ out) {
-  pdl_enter();
+__device__ __forceinline__ void gather_fused_body(int n1, int n2, int log1, int x0, int y0,
+                                                  float* sm, const float* __restrict__ u,
+                                                  long long fstride,
+                                                  const float* __restrict__ disp,
+                                                  float* __restrict__ out) {
   using D = BoxDims<W>;
   constexpr int H = (W - 32) / 2;
-  extern __shared__ float sm[];
   float* stage = sm;
   float* mid = sm + D::kStage;
   float* box1 = mid + D::kMid;     // first field's box when F = 2
-  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
   const long long N = (long long)n1 * n2;
   constexpr int TPR = 32 / kFP;
   const int t = threadIdx.x, r = t / TPR, cx = t % TPR;
@@ -785,6 +835,16 @@ k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long 
   } else {
     stf(out + idx, o2);
   }
+}
+
+template <bool P2, int W, int F>
+__global__ void __launch_bounds__(kFT, 2)
+k_gather_fused(int n1, int n2, int log1, const float* __restrict__ u, long long fstride,
+               const float* __restrict__ disp, float* __restrict__ out) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  gather_fused_body<P2, W, F>(n1, n2, log1, blockIdx.x * 32, blockIdx.y * 32, sm, u, fstride,
+                              disp, out);
 }
 
 // box widths with a fused kernel: halo H = 8 and H = 16
@@ -885,6 +945,246 @@ void launch_gather_fused(int W, int n1, int n2, const float* u, long long fstrid
   else if (F == 1) REGNK_GF(64, 1, BoxDims<64>::kSmemBytes);
   else REGNK_GF(64, 2, first_smem<64>());
 #undef REGNK_GF
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: the same per-tile and per-point bodies over the tiles of
+// every problem of a batch in one launch (see BatchView). A tile block reads
+// its problem and tile from the table, skips problems outside the mask and
+// problems whose displacements exceed the fused kernels' halo (w = 0), and
+// runs the body for the problem's index arithmetic (power-of-two grid or
+// not) and box width, so each problem's results are bitwise those of the
+// one-problem kernels.
+
+__device__ __forceinline__ float* bref(const BRef& r, const BDesc& D) {
+  return r.base ? r.base + (long long)r.F * D.off + (long long)r.k * D.n1 * D.n2 : nullptr;
+}
+
+template <bool V>
+using BoolC = std::integral_constant<bool, V>;
+template <int V>
+using IntC = std::integral_constant<int, V>;
+
+// fn(P2, W) with both as compile-time constants
+template <typename Fn>
+__device__ __forceinline__ void by_shape(const BDesc& D, int W, Fn fn) {
+  if (D.p2) {
+    if (W == 48) fn(BoolC<true>{}, IntC<48>{});
+    else fn(BoolC<true>{}, IntC<64>{});
+  } else {
+    if (W == 48) fn(BoolC<false>{}, IntC<48>{});
+    else fn(BoolC<false>{}, IntC<64>{});
+  }
+}
+
+// The block's problem and tile origin; false if the block has nothing to do.
+__device__ __forceinline__ bool batch_tile(const BatchView& B, bool need_w, BDesc& D, int& W,
+                                           int& x0, int& y0) {
+  const int4 tj = B.tiles[blockIdx.x];
+  if (!B.mask[tj.x]) return false;
+  D = B.desc[tj.x];
+  W = need_w ? B.w[tj.x] : 48;
+  x0 = tj.y * 32;
+  y0 = tj.z * 32;
+  return W != 0;
+}
+
+// one block per tile and field (blockIdx.y)
+__global__ void __launch_bounds__(kPThreads)
+k_prefilter_b(BatchView B, BRef in, BRef out) {
+  pdl_enter();
+  __shared__ float sin_[kPH * kPIn];
+  __shared__ float smid[kPH * kPMid];
+  BDesc D;
+  int W, x0, y0;
+  if (!batch_tile(B, false, D, W, x0, y0)) return;
+  in.k += blockIdx.y;
+  out.k += blockIdx.y;
+  const float* src = bref(in, D);
+  float* dst = bref(out, D);
+  if (D.p2) prefilter_tile<true>(src, dst, D.n1, D.n2, D.log1, x0, y0, sin_, smid);
+  else prefilter_tile<false>(src, dst, D.n1, D.n2, D.log1, x0, y0, sin_, smid);
+}
+
+void launch_prefilter_b(const BatchView& B, BRef in, BRef out, int F, cudaStream_t st) {
+  launch_k(k_prefilter_b, dim3(B.ntiles, F), dim3(kPThreads), 0, st, B, in, out);
+}
+
+// one thread per point of the batch
+__global__ void __launch_bounds__(kPT)
+k_departure_b(BatchView B, long long npts, BRef v, BRef cv, BRef dX, BRef dY) {
+  pdl_enter();
+  const long long g = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (g >= npts) return;
+  const int p = B.pmap[g >> 10];
+  if (!B.mask[p]) return;
+  const BDesc D = B.desc[p];
+  const long long idx = g - D.off;
+  if (D.p2)
+    departure_point<true>(idx, D.n1, D.n2, D.log1, D.s1, D.s2, bref(v, D), bref(cv, D),
+                          bref(dX, D), bref(dY, D), 0);
+  else
+    departure_point<false>(idx, D.n1, D.n2, D.log1, D.s1, D.s2, bref(v, D), bref(cv, D),
+                           bref(dX, D), bref(dY, D), 0);
+}
+
+void launch_departure_b(const BatchView& B, long long npts, BRef v, BRef cv, BRef dX, BRef dY,
+                        cudaStream_t st) {
+  launch_k(k_departure_b, dim3((unsigned)((npts + kPT - 1) / kPT)), dim3(kPT), 0, st, B, npts, v,
+           cv, dX, dY);
+}
+
+// w_p from the largest displacements of X_D and Y_D, the rule of
+// fused_box_width
+__global__ void k_set_w_b(int nprob, const double* __restrict__ dmax_x,
+                          const double* __restrict__ dmax_y, int* __restrict__ w) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const double d = fmax(dmax_x[p], dmax_y[p]);
+  int W = 0;
+  if (d <= (double)((48 - 32) / 2 - 2)) W = 48;
+  else if (d <= (double)((64 - 32) / 2 - 2)) W = 64;
+  w[p] = W;
+}
+
+void launch_set_w_b(int nprob, const double* dmax_x, const double* dmax_y, int* w,
+                    cudaStream_t st) {
+  launch_k(k_set_w_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, dmax_x, dmax_y, w);
+}
+
+__global__ void __launch_bounds__(kPT)
+k_adjoint_init_b(BatchView B, long long npts, float coef_b, BRef mR, BRef m1, BRef gm, BRef lam,
+                 BRef b, float sign) {
+  pdl_enter();
+  const long long g = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (g >= npts) return;
+  const int p = B.pmap[g >> 10];
+  if (!B.mask[p]) return;
+  const BDesc D = B.desc[p];
+  adjoint_init_point(g - D.off, (long long)D.n1 * D.n2, coef_b, bref(mR, D), bref(m1, D),
+                     bref(gm, D), bref(lam, D), bref(b, D), sign);
+}
+
+void launch_adjoint_init_b(const BatchView& B, long long npts, float coef_b, BRef mR, BRef m1,
+                           BRef gm, BRef lam, BRef b, float sign, cudaStream_t st) {
+  launch_k(k_adjoint_init_b, dim3((unsigned)((npts + kPT - 1) / kPT)), dim3(kPT), 0, st, B, npts,
+           coef_b, mR, m1, gm, lam, b, sign);
+}
+
+// dst = src, one scalar field per problem (e.g. m_0 = m_T into the history)
+__global__ void __launch_bounds__(kPT)
+k_copy_field_b(BatchView B, long long npts, BRef src, BRef dst) {
+  pdl_enter();
+  const long long g = (long long)blockIdx.x * kPT + threadIdx.x;
+  if (g >= npts) return;
+  const int p = B.pmap[g >> 10];
+  if (!B.mask[p]) return;
+  const BDesc D = B.desc[p];
+  bref(dst, D)[g - D.off] = __ldg(bref(src, D) + (g - D.off));
+}
+
+void launch_copy_field_b(const BatchView& B, long long npts, BRef src, BRef dst, cudaStream_t st) {
+  launch_k(k_copy_field_b, dim3((unsigned)((npts + kPT - 1) / kPT)), dim3(kPT), 0, st, B, npts, src,
+           dst);
+}
+
+template <int F>
+__global__ void __launch_bounds__(kFT, 2)
+k_gather_fused_b(BatchView B, BRef u, BRef disp, BRef out) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  BDesc D;
+  int W, x0, y0;
+  if (!batch_tile(B, true, D, W, x0, y0)) return;
+  const long long N = (long long)D.n1 * D.n2;
+  by_shape(D, W, [&](auto P2, auto WC) {
+    gather_fused_body<decltype(P2)::value, decltype(WC)::value, F>(
+        D.n1, D.n2, D.log1, x0, y0, sm, bref(u, D), N, bref(disp, D), bref(out, D));
+  });
+}
+
+__global__ void __launch_bounds__(kFT, 2)
+k_adjoint_fused_b(BatchView B, float ht, float wb, BRef lam_next, BRef dY, BRef delta,
+                  BRef delta_bar, BRef gm, BRef lam_out, BRef b) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  BDesc D;
+  int W, x0, y0;
+  if (!batch_tile(B, true, D, W, x0, y0)) return;
+  by_shape(D, W, [&](auto P2, auto WC) {
+    adjoint_fused_body<decltype(P2)::value, decltype(WC)::value>(
+        D.n1, D.n2, D.log1, x0, y0, sm, ht, wb, bref(lam_next, D), bref(dY, D), bref(delta, D),
+        bref(delta_bar, D), bref(gm, D), bref(lam_out, D), bref(b, D));
+  });
+}
+
+__global__ void __launch_bounds__(kFT, 2)
+k_incstate_first_fused_b(BatchView B, float ht, BRef vt, BRef dX, BRef G1, BRef gm1, BRef vtD,
+                         BRef out) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  BDesc D;
+  int W, x0, y0;
+  if (!batch_tile(B, true, D, W, x0, y0)) return;
+  by_shape(D, W, [&](auto P2, auto WC) {
+    incstate_first_fused_body<decltype(P2)::value, decltype(WC)::value>(
+        D.n1, D.n2, D.log1, x0, y0, sm, ht, bref(vt, D), bref(dX, D), bref(G1, D), bref(gm1, D),
+        bref(vtD, D), bref(out, D));
+  });
+}
+
+__global__ void __launch_bounds__(kFT, 2)
+k_incstate_fused_b(BatchView B, float ht, BRef m_prev, BRef dX, BRef vt, BRef vtD, BRef G,
+                   BRef gm, BRef out, BRef gm_nt, BRef b) {
+  pdl_enter();
+  extern __shared__ float sm[];
+  BDesc D;
+  int W, x0, y0;
+  if (!batch_tile(B, true, D, W, x0, y0)) return;
+  by_shape(D, W, [&](auto P2, auto WC) {
+    incstate_fused_body<decltype(P2)::value, decltype(WC)::value>(
+        D.n1, D.n2, D.log1, x0, y0, sm, ht, bref(m_prev, D), bref(dX, D), bref(vt, D),
+        bref(vtD, D), bref(G, D), bref(gm, D), bref(out, D), bref(gm_nt, D), bref(b, D));
+  });
+}
+
+// shared memory of the batched fused kernels: the 64^2 box (any problem may need it)
+void batch_fused_init() {
+  allow_smem(k_gather_fused_b<1>, BoxDims<64>::kSmemBytes);
+  allow_smem(k_gather_fused_b<2>, first_smem<64>());
+  allow_smem(k_incstate_first_fused_b, first_smem<64>());
+  allow_smem(k_adjoint_fused_b, BoxDims<64>::kSmemBytes);
+  allow_smem(k_incstate_fused_b, BoxDims<64>::kSmemBytes);
+}
+
+void launch_gather_fused_b(const BatchView& B, BRef u, int F, BRef disp, BRef out,
+                           cudaStream_t st) {
+  if (F == 2)
+    launch_k(k_gather_fused_b<2>, dim3(B.ntiles), dim3(kFT), first_smem<64>(), st, B, u, disp, out);
+  else
+    launch_k(k_gather_fused_b<1>, dim3(B.ntiles), dim3(kFT), BoxDims<64>::kSmemBytes, st, B, u,
+             disp, out);
+}
+
+void launch_adjoint_fused_b(const BatchView& B, float ht, float wb, BRef lam_next, BRef dY,
+                            BRef delta, BRef delta_bar, BRef gm, BRef lam_out, BRef b,
+                            cudaStream_t st) {
+  launch_k(k_adjoint_fused_b, dim3(B.ntiles), dim3(kFT), BoxDims<64>::kSmemBytes, st, B, ht, wb,
+           lam_next, dY, delta, delta_bar, gm, lam_out, b);
+}
+
+void launch_incstate_first_fused_b(const BatchView& B, float ht, BRef vt, BRef dX, BRef G1,
+                                   BRef gm1, BRef vtD, BRef out, cudaStream_t st) {
+  launch_k(k_incstate_first_fused_b, dim3(B.ntiles), dim3(kFT), first_smem<64>(), st, B, ht, vt,
+           dX, G1, gm1, vtD, out);
+}
+
+void launch_incstate_fused_b(const BatchView& B, float ht, BRef m_prev, BRef dX, BRef vt,
+                             BRef vtD, BRef G, BRef gm, BRef out, BRef gm_nt, BRef b,
+                             cudaStream_t st) {
+  launch_k(k_incstate_fused_b, dim3(B.ntiles), dim3(kFT), BoxDims<64>::kSmemBytes, st, B, ht,
+           m_prev, dX, vt, vtD, G, gm, out, gm_nt, b);
 }
 
 }  // namespace regnk

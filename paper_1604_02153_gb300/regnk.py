@@ -111,6 +111,17 @@ _SIGNATURES = {
     "reg_batch_solve": [_P, ctypes.POINTER(_P), _D, _I, ctypes.POINTER(reg_info)],
     "reg_batch_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "reg_batch_last_error": [_P],
+    "reg_lockstep_create": [ctypes.POINTER(reg_grid), _I, _I, ctypes.POINTER(_D),
+                            ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
+    "reg_lockstep_destroy": [_P],
+    "reg_lockstep_set_stream": [_P, _P],
+    "reg_lockstep_set_images": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P)],
+    "reg_lockstep_objective_gradient": [_P, ctypes.POINTER(_P), ctypes.POINTER(_D),
+                                        ctypes.POINTER(_P)],
+    "reg_lockstep_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                    ctypes.POINTER(_P)],
+    "reg_lockstep_solve": [_P, ctypes.POINTER(_P), _D, ctypes.POINTER(reg_info)],
+    "reg_lockstep_last_error": [_P],
     "reg_unet_param_count": [],
     "reg_unet_create": [_I, _I, ctypes.POINTER(_P)],
     "reg_unet_destroy": [_P],
@@ -140,6 +151,7 @@ def load(path=LIB_PATH):
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = {"reg_last_error": ctypes.c_char_p, "reg_batch_last_error": ctypes.c_char_p,
+                      "reg_lockstep_last_error": ctypes.c_char_p,
                       "reg_unet_last_error": ctypes.c_char_p, "reg_launch_count": ctypes.c_longlong,
                       "reg_unet_param_count": ctypes.c_longlong}.get(name, ctypes.c_int)
     _lib = lib
@@ -391,6 +403,82 @@ class Batch:
         h = getattr(self, "h", None)
         if h is not None and h.value:
             self.lib.reg_batch_destroy(h)
+            self.h = None
+
+    __del__ = close
+
+
+class Lockstep:
+    """reg_lockstep: independent problems of uneven size advanced in lockstep
+    (one launch per transport step over all problems, one CUDA graph for the
+    matvec). Options as reg_options; precond defaults to P_REG here, the form
+    the lockstep batch requires. Methods take lists of tensors."""
+
+    def __init__(self, grids, nt, betas, **options):
+        self.lib = load()
+        self.grids = [(int(a), int(b)) for a, b in grids]
+        self.B = len(self.grids)
+        G = (reg_grid * self.B)(*[reg_grid(a, b) for a, b in self.grids])
+        Bt = (ctypes.c_double * self.B)(*[float(x) for x in betas])
+        options.setdefault("precond", REG_PC_REG)
+        self.options = default_options(**options)
+        h = ctypes.c_void_p()
+        s = self.lib.reg_lockstep_create(G, self.B, int(nt), Bt, ctypes.byref(self.options),
+                                         ctypes.byref(h))
+        if s != REG_OK:
+            raise RegError(s, "reg_lockstep_create failed")
+        self.h = h
+
+    def _ptrs(self, ts, per_point, name):
+        arr = (ctypes.c_void_p * self.B)()
+        for i, (t, (a, b)) in enumerate(zip(ts, self.grids)):
+            arr[i] = _ptr(t, per_point * a * b, f"{name}[{i}]").value
+        return arr
+
+    def _check(self, s):
+        if s != REG_OK:
+            raise RegError(s, self.lib.reg_lockstep_last_error(self.h).decode())
+
+    def _order(self):
+        import torch
+        s = torch.cuda.current_stream().cuda_stream
+        self._check(self.lib.reg_lockstep_set_stream(self.h, ctypes.c_void_p(s)))
+
+    def set_images(self, m_R, m_T):
+        self._order()
+        self._check(self.lib.reg_lockstep_set_images(self.h, self._ptrs(m_R, 1, "m_R"),
+                                                     self._ptrs(m_T, 1, "m_T")))
+
+    def objective_gradient(self, vs, gs=None):
+        self._order()
+        J = (ctypes.c_double * self.B)()
+        g = self._ptrs(gs, 2, "g") if gs is not None else None
+        self._check(self.lib.reg_lockstep_objective_gradient(self.h, self._ptrs(vs, 2, "v"), J, g))
+        return list(J)
+
+    def hessian_matvec(self, vs, vts, Hs):
+        self._order()
+        self._check(self.lib.reg_lockstep_hessian_matvec(self.h, self._ptrs(vs, 2, "v"),
+                                                         self._ptrs(vts, 2, "vt"),
+                                                         self._ptrs(Hs, 2, "Hvt")))
+
+    def solve(self, vs, gtol, allow=(REG_OK, REG_ENOTCONV, REG_ELINESEARCH)):
+        self._order()
+        infos = (reg_info * self.B)()
+        s = self.lib.reg_lockstep_solve(self.h, self._ptrs(vs, 2, "v"), float(gtol), infos)
+        if s not in allow:
+            self._check(s)
+        out = []
+        for i in range(self.B):
+            d = infos[i].as_dict()
+            d["status_name"] = STATUS_NAMES.get(d["status"], str(d["status"]))
+            out.append(d)
+        return out
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.reg_lockstep_destroy(h)
             self.h = None
 
     __del__ = close

@@ -121,3 +121,34 @@ def test_unet_arguments_and_no_cpu_fallback(lib):
     assert lib.reg_warm_start(None, None, None, None) == regnk.REG_EINVAL
     if not torch.cuda.is_available():
         assert lib.reg_unet_create(32, 1, ctypes.byref(h)) == regnk.REG_ECUDA and not h.value
+
+
+def test_lockstep_arguments_and_no_cpu_fallback(lib):
+    """reg_lockstep_create validates its grids and options on the host: the
+    lockstep form needs P_REG, the spline model, the Gauss-Newton matvec and
+    FP64 reductions; without a GPU a valid request fails with REG_ECUDA."""
+    import torch
+    G = (regnk.reg_grid * 2)(regnk.reg_grid(64, 64), regnk.reg_grid(128, 128))
+    beta = (ctypes.c_double * 2)(1e-2, 1e-2)
+    h = ctypes.c_void_p()
+
+    def create(grids=G, B=2, nt=4, b=beta, **kw):
+        kw.setdefault("precond", regnk.REG_PC_REG)
+        o = regnk.default_options(**kw)
+        return lib.reg_lockstep_create(grids, B, nt, b, ctypes.byref(o), ctypes.byref(h))
+
+    assert create(precond=regnk.REG_PC_2L) == regnk.REG_EINVAL
+    assert create(interp=regnk.REG_INTERP_LAGRANGE) == regnk.REG_EINVAL
+    assert create(hessian=regnk.REG_HESSIAN_FULL) == regnk.REG_EINVAL
+    assert create(precision=regnk.REG_PRECISION_FP32) == regnk.REG_EINVAL
+    assert create(incompressible=1) == regnk.REG_EINVAL
+    assert create(beta_w=1e-3) == regnk.REG_EINVAL
+    assert create(B=0) == regnk.REG_EINVAL
+    assert create(nt=0) == regnk.REG_EINVAL
+    bad = (regnk.reg_grid * 2)(regnk.reg_grid(64, 64), regnk.reg_grid(100, 100))
+    assert create(grids=bad) == regnk.REG_EINVAL
+    assert create(b=(ctypes.c_double * 2)(1e-2, 0.0)) == regnk.REG_EINVAL
+    assert lib.reg_lockstep_solve(None, None, 1e-2, None) == regnk.REG_EINVAL
+    assert lib.reg_lockstep_set_images(None, None, None) == regnk.REG_EINVAL
+    if not torch.cuda.is_available():
+        assert create() == regnk.REG_ECUDA and not h.value
