@@ -51,9 +51,13 @@ fft_comparator = the hand-written spectral operator (beta A)^-1 on two fields
             against cuFFT doing the same (torch.fft), 512^2 and 1024^2.
 config_256_512 = the 256^2 / 512^2 random-field configuration at nt 4, 8, 16:
             GN matvecs/s, transport solves/s and gradients/s through the C ABI.
-batch64_chosen_vs_plain = 64 problems of uneven size: concurrent contexts
-            (CUDA graphs, FP64-accurate reductions) against the plain FP32
-            method one by one, 5 batches per arm.
+batch64 = 64 problems of uneven size, 5 batches per arm: the lockstep batch
+            (one launch per transport step over all problems, one CUDA
+            graph per matvec, FP64-accurate reductions, P_REG) against
+            concurrent contexts, the same contexts one by one and the plain
+            FP32 method one by one (P_REG), and concurrent contexts and the
+            plain FP32 method with P_2L; the lockstep matvec of all 64
+            problems timed alone against its algorithmic bytes.
 learned_warm_start = the trained warm-start network (weights committed with
             the package) measured outside the timed region: cold versus warm
             time to ||g||rel 1e-2 on held-out pairs of the learned-warm-start
@@ -563,13 +567,19 @@ BATCH_BETA = 1e-2
 def batch_comparison(args, samples, warmup):
     """64 independent problems, grids drawn (seed 200) from BATCH_SIZES^2,
     each the analytic template/velocity pair with m_R = m_T transported by
-    v* (nt = 4, computed on the GPU), H1, beta = 1e-2, P_2L-CHEB(10) (coarse
-    problem as --coarse-nt / --coarse-interp), solved to ||g||rel 1e-2 from
-    v = 0: concurrently (reg_batch: one context and stream per problem, CUDA
-    graphs, FP64-accurate reductions), one by one on the same contexts, and
-    by the plain FP32 method one by one (FP32 reductions, no CUDA graphs,
-    plain launches). Wall time per batch between device synchronisations,
-    `samples` batches per arm after `warmup`."""
+    v* (nt = 4, computed on the GPU), H1, beta = 1e-2, solved to ||g||rel
+    1e-2 from v = 0. Arms with the spectral preconditioner P_REG:
+    lockstep (reg_lockstep: one launch per transport step over all 64
+    problems, one CUDA graph for the matvec, FP64-accurate reductions),
+    concurrent contexts (reg_batch: one context and stream per problem,
+    CUDA graphs, FP64-accurate reductions), the same contexts one by one,
+    and the plain FP32 method one by one (FP32 reductions, no CUDA graphs,
+    plain launches). Arms with P_2L-CHEB(10) (coarse problem as --coarse-nt
+    / --coarse-interp): concurrent contexts and plain FP32 one by one. Wall
+    time per batch between device synchronisations, `samples` batches per
+    arm after `warmup`. The lockstep matvec of all 64 problems is also
+    timed alone (graph replays, CUDA events) against its algorithmic bytes
+    sum_p 4 N_p (10 nt + 16)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -592,14 +602,15 @@ def batch_comparison(args, samples, warmup):
         mR.append(cache[n][0])
         mT.append(cache[n][1])
     grids = [(n, n) for n in sizes]
+    betas = [BATCH_BETA] * BATCH_B
     ci = {"lagrange": regnk.REG_INTERP_LAGRANGE, "spline": regnk.REG_INTERP_SPLINE}[args.coarse_interp]
     vs = [torch.zeros(2 * n * n, device=dev) for n in sizes]
 
-    def arm(batch, threads):
+    def arm(solve):
         for _ in range(max(1, warmup)):
             for v in vs:
                 v.zero_()
-            batch.solve(vs, GTOL, threads=threads)
+            solve()
         torch.cuda.synchronize()
         times, mv, infos = [], 0, None
         for _ in range(samples):
@@ -607,42 +618,76 @@ def batch_comparison(args, samples, warmup):
                 v.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            infos = batch.solve(vs, GTOL, threads=threads)
+            infos = solve()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             mv += sum(i["matvecs"] for i in infos)
         return times, mv, infos
 
-    batch = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
-                        coarse_interp=ci)
-    batch.set_images(mR, mT)
-    t_b, mv_b, infos = arm(batch, 0)
-    t_s, mv_s, infos1 = arm(batch, 1)        # one by one: the same contexts, one host thread
-    batch.close()
-    plain = regnk.Batch(grids, BATCH_NT, [BATCH_BETA] * BATCH_B, coarse_nt=args.coarse_nt,
-                        coarse_interp=ci, precision=regnk.REG_PRECISION_FP32, use_graphs=0,
-                        programmatic_launch=0)
-    plain.set_images(mR, mT)
-    t_p, mv_p, infos_p = arm(plain, 1)
-    plain.close()
+    def stats(t, mv, infos, per_problem):
+        d = {"samples": len(t), "seconds_per_batch_mean": float(np.mean(t)),
+             "seconds_per_batch_min": float(np.min(t)), "seconds_per_batch_std": float(np.std(t)),
+             "matvecs_per_s": mv / sum(t), "matvecs_per_batch": mv // len(t),
+             "newton_iters": int(sum(i["newton_iters"] for i in infos)),
+             "status": sorted(set(i["status_name"] for i in infos))}
+        if per_problem:
+            d["mean_time_to_solution_s"] = float(np.mean([i["seconds"] for i in infos]))
+        return d
 
-    def stats(t):
-        return {"samples": len(t), "seconds_per_batch_mean": float(np.mean(t)),
-                "seconds_per_batch_min": float(np.min(t)), "seconds_per_batch_std": float(np.std(t))}
-    tb, ts, tp = float(np.mean(t_b)), float(np.mean(t_s)), float(np.mean(t_p))
+    reg = dict(precond=regnk.REG_PC_REG)
+    plain = dict(precision=regnk.REG_PRECISION_FP32, use_graphs=0, programmatic_launch=0)
+    out = {}
+    L = regnk.Lockstep(grids, BATCH_NT, betas)
+    L.set_images(mR, mT)
+    r = arm(lambda: L.solve(vs, GTOL))
+    out["lockstep_reg"] = dict(stats(*r, per_problem=False), kernels_per_matvec=L.info()["matvec_graph_kernels"])
+    v_lock = [v.clone() for v in vs]
+    # the batched matvec alone at the solutions, against its algorithmic bytes
+    us = [f(inputs.random_velocity(n, seed=40 + i, vmax=0.2)) for i, n in enumerate(sizes)]
+    Hs = [torch.empty(2 * n * n, device=dev) for n in sizes]
+    L.hessian_matvec(v_lock, us, Hs)
+    L.hessian_matvec(v_lock, us, Hs)
+    ms = min(L.matvec_time(20) for _ in range(3))
+    algo = float(sum(4.0 * n * n * (10 * BATCH_NT + 16) for n in sizes))
+    peak, peak_kind = peaks()
+    out["lockstep_matvec"] = {"ms": ms, "algorithmic_bytes": algo, "achieved_gbs": algo / ms / 1e6,
+                              "peak_gbs": peak, "peak_kind": peak_kind,
+                              "frac": algo / ms / 1e6 / peak,
+                              "points": L.info()["points"], "tiles": L.info()["tiles"],
+                              "unit": "one GN matvec of all 64 problems (graph replay, CUDA events, "
+                                      "best of 3 means of 20)"}
+    L.close()
+    B = regnk.Batch(grids, BATCH_NT, betas, **reg)
+    B.set_images(mR, mT)
+    out["contexts_reg"] = stats(*arm(lambda: B.solve(vs, GTOL, threads=0)), per_problem=True)
+    out["one_by_one_reg"] = stats(*arm(lambda: B.solve(vs, GTOL, threads=1)), per_problem=True)
+    same = all(torch.equal(a, b) for a, b in zip(vs, v_lock))
+    B.close()
+    P = regnk.Batch(grids, BATCH_NT, betas, **reg, **plain)
+    P.set_images(mR, mT)
+    out["plain_fp32_reg"] = dict(stats(*arm(lambda: P.solve(vs, GTOL, threads=1)), per_problem=True),
+                                 options="P_REG one by one, FP32 reductions, no CUDA graphs, plain launches")
+    P.close()
+    B2 = regnk.Batch(grids, BATCH_NT, betas, coarse_nt=args.coarse_nt, coarse_interp=ci)
+    B2.set_images(mR, mT)
+    out["contexts_2l"] = stats(*arm(lambda: B2.solve(vs, GTOL, threads=0)), per_problem=True)
+    B2.close()
+    P2 = regnk.Batch(grids, BATCH_NT, betas, coarse_nt=args.coarse_nt, coarse_interp=ci, **plain)
+    P2.set_images(mR, mT)
+    out["plain_fp32_2l"] = dict(stats(*arm(lambda: P2.solve(vs, GTOL, threads=1)), per_problem=True),
+                                options="P_2L one by one, FP32 reductions, no CUDA graphs, plain launches")
+    P2.close()
+    t = {k: out[k]["seconds_per_batch_mean"] for k in out if "seconds_per_batch_mean" in out[k]}
     return {"workload": f"{BATCH_B} problems, grids from {list(BATCH_SIZES)}^2 (seed 200), analytic "
-                        f"pair, nt={BATCH_NT}, H1, beta={BATCH_BETA}, P_2L CHEB(10) coarse nt="
-                        f"{args.coarse_nt or BATCH_NT} {args.coarse_interp}, ||g||rel 1e-2",
-            "sizes": sizes,
-            "concurrent": dict(stats(t_b), matvecs_per_s=mv_b / sum(t_b),
-                               mean_time_to_solution_s=float(np.mean([i["seconds"] for i in infos])),
-                               status=sorted(set(i["status_name"] for i in infos))),
-            "one_by_one": dict(stats(t_s), matvecs_per_s=mv_s / sum(t_s),
-                               mean_time_to_solution_s=float(np.mean([i["seconds"] for i in infos1]))),
-            "plain_fp32": dict(stats(t_p), matvecs_per_s=mv_p / sum(t_p),
-                               options="one by one, FP32 reductions, no CUDA graphs, plain launches",
-                               status=sorted(set(i["status_name"] for i in infos_p))),
-            "speedup_vs_one_by_one": ts / tb, "speedup_vs_plain_fp32": tp / tb,
+                        f"pair, nt={BATCH_NT}, H1, beta={BATCH_BETA}, ||g||rel 1e-2; P_REG arms and "
+                        f"P_2L CHEB(10) arms (coarse nt={args.coarse_nt or BATCH_NT} {args.coarse_interp})",
+            "sizes": sizes, **out,
+            "lockstep_equals_one_by_one_bitwise": bool(same),
+            "speedup_lockstep_vs_one_by_one_reg": t["one_by_one_reg"] / t["lockstep_reg"],
+            "speedup_lockstep_vs_contexts_reg": t["contexts_reg"] / t["lockstep_reg"],
+            "speedup_lockstep_vs_plain_fp32_reg": t["plain_fp32_reg"] / t["lockstep_reg"],
+            "speedup_lockstep_vs_plain_fp32_2l": t["plain_fp32_2l"] / t["lockstep_reg"],
+            "speedup_lockstep_vs_contexts_2l": t["contexts_2l"] / t["lockstep_reg"],
             "learned_warm_start": "not applied: the network's input grid is 256^2 and it was "
                                   "trained on random-field pairs; the batch's analytic problems "
                                   "converge from v = 0 in a few Newton steps"}
@@ -651,10 +696,11 @@ def batch_comparison(args, samples, warmup):
 def run_batch(args):
     """The batch workload as its own bench line (--workload batch64)."""
     c = batch_comparison(args, max(1, args.steps), args.warmup)
-    line = {"metric": "aggregate Hessian matvecs/s, 64 independent problems of uneven size",
-            "value": c["concurrent"]["matvecs_per_s"], "unit": "matvecs/s", "n_gpus": 1,
+    line = {"metric": "aggregate Hessian matvecs/s, 64 independent problems of uneven size "
+                      "(lockstep batch, P_REG)",
+            "value": c["lockstep_reg"]["matvecs_per_s"], "unit": "matvecs/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * c["concurrent"]["seconds_per_batch_mean"],
+            "ms_per_step": 1e3 * c["lockstep_reg"]["seconds_per_batch_mean"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic", "config": {"workload": c["workload"], "sizes": c["sizes"]},
             "comparison": c}
@@ -975,7 +1021,7 @@ def main():
             # the batch workload's own coarse model (the problems' nt and splines)
             bargs = argparse.Namespace(**vars(args))
             bargs.coarse_nt, bargs.coarse_interp = 0, "spline"
-            line["batch64_chosen_vs_plain"] = batch_comparison(bargs, 5, 2)
+            line["batch64"] = batch_comparison(bargs, 5, 2)
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.incompressible, args.hessian, args.beta_w)
         if not args.no_warm_start:

@@ -455,6 +455,16 @@ reg_status reg_lockstep_hessian_matvec(reg_lockstep* batch, const float* const* 
  * receives the result; infos (host, B entries) may be NULL (seconds is the
  * whole batch's wall time). Returns as reg_batch_solve. */
 reg_status reg_lockstep_solve(reg_lockstep* batch, float* const* v, double gtol, reg_info* infos);
+/* Diagnostics: replays the matvec graph of the last reg_lockstep_hessian_matvec
+ * `reps` times between two CUDA events on the batch's stream (every problem
+ * active, the cached velocities) and returns the mean device time per
+ * matvec in *ms (REG_ESTATE before that graph exists: two matvec calls). */
+reg_status reg_lockstep_matvec_time(reg_lockstep* batch, int reps, double* ms);
+/* The batch's total grid points, 32 x 32 tiles and the kernels in one
+ * replay of the solver's matvec graph (0 before its capture); NULL outputs
+ * are skipped. */
+reg_status reg_lockstep_info(const reg_lockstep* batch, long long* points, int* tiles,
+                             int* launches);
 const char* reg_lockstep_last_error(const reg_lockstep* batch);
 
 /* ---- Learned warm start (no counterpart in the paper) --------------------

@@ -277,13 +277,18 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
   }
 }
 
+__device__ __forceinline__ bool field_skipped(const FieldMask& fm) {
+  return fm.mask && !fm.mask[fm.p0 + (int)blockIdx.y / fm.per];
+}
+
 // ---------------------------------------------------------------------------
 // 1. forward row transforms: F fields of n2 rows of length N = n1.
 template <int L, int T>
 __global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__ spec,
-           long long sstride, int n2, const float2* __restrict__ tw) {
+           long long sstride, int n2, const float2* __restrict__ tw, FieldMask fm) {
   pdl_enter();
+  if (field_skipped(fm)) return;
   constexpr int N = RowCfg<L, T>::N, P = RowCfg<L, T>::P, NT = RowCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
@@ -330,8 +335,9 @@ template <int L, int T, bool CHEB>
 __global__ void __launch_bounds__(RowCfg<L, T>::NT)
 k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict__ out,
            long long fstride, const float* __restrict__ add, long long astride, int n2,
-           const float2* __restrict__ tw, ChebEpilogue cheb) {
+           const float2* __restrict__ tw, ChebEpilogue cheb, FieldMask fm) {
   pdl_enter();
+  if (field_skipped(fm)) return;
   constexpr int N = RowCfg<L, T>::N, P = RowCfg<L, T>::P, NT = RowCfg<L, T>::NT;
   extern __shared__ float2 sm[];
   const int t = threadIdx.x;
@@ -596,6 +602,7 @@ struct ColCfg {
 template <int LI, int LO, int T>
 __global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 1024 / ColCfg<LI, LO, T>::NT) k_cols(ColArgs a) {
   pdl_enter();
+  if (field_skipped(a.fm)) return;
   constexpr int NI = FftCfg<LI, T>::N, NO = FftCfg<LO, T>::N;
   constexpr int NM = ColCfg<LI, LO, T>::NM;
   constexpr int P = ColCfg<LI, LO, T>::P, NT = ColCfg<LI, LO, T>::NT;
@@ -680,26 +687,26 @@ static void split_size(int n, int& L, int& T) {
 
 template <int L, int T>
 static void launch_r2c(const float* in, long long fstride, float2* spec, long long sstride,
-                       int n2, int F, const float2* tw, cudaStream_t st) {
+                       int n2, int F, const float2* tw, cudaStream_t st, const FieldMask& fm) {
   using C = RowCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
-  launch_k(k_rows_r2c<L, T>, dim3(grid), dim3(C::NT), smem, st, in, fstride, spec, sstride, n2, tw);
+  launch_k(k_rows_r2c<L, T>, dim3(grid), dim3(C::NT), smem, st, in, fstride, spec, sstride, n2, tw, fm);
 }
 
 template <int L, int T>
 static void launch_c2r(const float2* spec, long long sstride, float* out, long long fstride,
                        const float* add, long long astride, int n2, int F, const float2* tw,
-                       cudaStream_t st, const ChebEpilogue& cheb) {
+                       cudaStream_t st, const ChebEpilogue& cheb, const FieldMask& fm) {
   using C = RowCfg<L, T>;
   const size_t smem = (size_t)C::P * C::N * sizeof(float2);
   static_assert(C::P * C::N * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
   dim3 grid(n2 / (2 * C::P), F);
   if (cheb.r)
-    launch_k(k_rows_c2r<L, T, true>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
+    launch_k(k_rows_c2r<L, T, true>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb, fm);
   else
-    launch_k(k_rows_c2r<L, T, false>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb);
+    launch_k(k_rows_c2r<L, T, false>, dim3(grid), dim3(C::NT), smem, st, spec, sstride, out, fstride, add, astride, n2, tw, cheb, fm);
 }
 
 template <int LI, int LO, int T>
@@ -726,11 +733,12 @@ bool fft_size_supported(int n) {
 }
 
 void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
-                  long long sstride, int F, const float2* tw, cudaStream_t st) {
+                  long long sstride, int F, const float2* tw, cudaStream_t st,
+                  const FieldMask& fm) {
   int L, T;
   split_size(n1, L, T);
   switch (L * 2 + T) {
-#define CASE(LL, TT) case LL * 2 + TT: launch_r2c<LL, TT>(in, fstride, spec, sstride, n2, F, tw, st); break;
+#define CASE(LL, TT) case LL * 2 + TT: launch_r2c<LL, TT>(in, fstride, spec, sstride, n2, F, tw, st, fm); break;
     REGNK_SIZE_CASES(CASE)
 #undef CASE
     default: break;
@@ -739,13 +747,14 @@ void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* sp
 
 void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
                   long long fstride, const float* add, long long astride, int F,
-                  const float2* tw, cudaStream_t st, const ChebEpilogue* cheb) {
+                  const float2* tw, cudaStream_t st, const ChebEpilogue* cheb,
+                  const FieldMask& fm) {
   int L, T;
   split_size(n1, L, T);
   const ChebEpilogue none;
   const ChebEpilogue& ce = cheb ? *cheb : none;
   switch (L * 2 + T) {
-#define CASE(LL, TT) case LL * 2 + TT: launch_c2r<LL, TT>(spec, sstride, out, fstride, add, astride, n2, F, tw, st, ce); break;
+#define CASE(LL, TT) case LL * 2 + TT: launch_c2r<LL, TT>(spec, sstride, out, fstride, add, astride, n2, F, tw, st, ce, fm); break;
     REGNK_SIZE_CASES(CASE)
 #undef CASE
     default: break;

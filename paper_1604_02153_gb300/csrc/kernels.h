@@ -75,6 +75,15 @@ enum SpecOp {
   SPOP_REGPOW_KW = 11,   // 2 -> 2: REGPOW times KW
 };
 
+// Optional skip of whole fields in one FFT launch (batches of problems): a
+// block working on field (or group) u of the launch returns at once when
+// mask[p0 + u / per] is zero. mask = NULL: every field is transformed.
+struct FieldMask {
+  const int* mask = nullptr;
+  int p0 = 0;
+  int per = 1;
+};
+
 struct ColArgs {
   const float2* in;
   long long in_fstride;   // complex values between consecutive input spectra
@@ -92,11 +101,13 @@ struct ColArgs {
   float scale;            // 1 / (n1_in n2_in)
   const float2* tw_in;    // twiddles for length n2_in
   const float2* tw_out;   // twiddles for length n2_out
+  FieldMask fm;           // groups to skip (per = groups per problem)
 };
 
 // fft.cu
 void fft_rows_r2c(int n1, int n2, const float* in, long long fstride, float2* spec,
-                  long long sstride, int F, const float2* tw, cudaStream_t st);
+                  long long sstride, int F, const float2* tw, cudaStream_t st,
+                  const FieldMask& fm = FieldMask{});
 // Optional epilogue of the inverse row pass: with Ad = the pass's output
 // plus its addend, one Chebyshev iteration r -= Ad; d = a d + b r; x += d on
 // the same points, instead of storing Ad. The addend, if any, must be d
@@ -111,7 +122,7 @@ struct ChebEpilogue {
 void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* out,
                   long long fstride, const float* add, long long astride, int F,
                   const float2* tw, cudaStream_t st,
-                  const ChebEpilogue* cheb = nullptr);
+                  const ChebEpilogue* cheb = nullptr, const FieldMask& fm = FieldMask{});
 void fft_cols(const ColArgs& a, int groups, cudaStream_t st);
 // n = 2^L (L = 5..11) or 3 * 2^L (L = 5..9)
 bool fft_size_supported(int n);
@@ -331,12 +342,13 @@ void launch_maxabs_b(const BDesc* desc, const SegView& S, int nprob, const int* 
 // problem, n = F * total points; a_p, b_p per problem; y may be NULL)
 void launch_lincomb_b(const int* pmap, const int* mask, int F, long long n, const float* a,
                       const float* x, const float* b, const float* y, float* z, cudaStream_t st);
-void launch_pcg_update_b(const int* pmap, const int* mask, int F, long long n, const double* rz,
-                         const double* pq, const float* p, const float* q, float* x, float* r,
-                         cudaStream_t st);
-void launch_pcg_direction_b(const int* pmap, const int* mask, int F, long long n,
-                            const double* rz_new, const double* rz_old, const float* z,
-                            float* p, cudaStream_t st);
+// (coef, on: per-problem scratch of nprob entries)
+void launch_pcg_update_b(const int* pmap, const int* mask, int nprob, int F, long long n,
+                         const double* rz, const double* pq, float* coef, int* on, const float* p,
+                         const float* q, float* x, float* r, cudaStream_t st);
+void launch_pcg_direction_b(const int* pmap, const int* mask, int nprob, int F, long long n,
+                            const double* rz_new, const double* rz_old, float* coef, int* on,
+                            const float* z, float* p, cudaStream_t st);
 void launch_copy_scalars_b(int nprob, const int* mask, const double* src, double* dst,
                            cudaStream_t st);
 

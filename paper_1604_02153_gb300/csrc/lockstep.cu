@@ -46,7 +46,9 @@ int red_blocks(long long n) {
 }
 
 // per-problem FP64 scalars: slot kind * B + p
-enum LsSlot { L_J1 = 0, L_J2, L_GINF, L_G2, L_BB, L_RZ, L_RZNEW, L_PQ, L_RR, L_SLOPE, L_DMX, L_DMY,
+// (J1, J2, SLOPE adjacent: the line search reads the slope <g, s> with the
+// first trial's objective)
+enum LsSlot { L_J1 = 0, L_J2, L_SLOPE, L_GINF, L_G2, L_RZ, L_RZNEW, L_PQ, L_RR, L_DMX, L_DMY,
               L_NSLOTS };
 
 struct LsError {
@@ -97,7 +99,8 @@ struct reg_lockstep {
   double* dsc = nullptr;          // L_NSLOTS * B
   double* hsc = nullptr;          // pinned mirror
   float* dalpha = nullptr;        // per-problem coefficients of masked linear combinations
-  float* dones = nullptr;
+  float* dcoef = nullptr;         // per-problem PCG step / direction weights
+  int* don = nullptr;
   std::vector<Group> groups;
   std::vector<void*> allocs;
   std::vector<std::pair<int, float2*>> tw;
@@ -122,6 +125,9 @@ struct reg_lockstep {
   };
   std::vector<GraphEntry> graphs;
   std::vector<int> mask_now;
+  std::vector<cudaStream_t> side;   // streams of the FFT runs
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
   std::string err;
 };
 
@@ -197,18 +203,43 @@ void read_slots(reg_lockstep* L, int first, int count, bool with_w = false) {
   check(L, cudaStreamSynchronize(L->st), "synchronize");
 }
 
-// out (fout fields per group) = op(in (fin fields per group)) [+ add], for
-// every problem: the arrays hold Fin (Fout) fields per problem, each problem
-// Fin / fin groups.
-void spectral(reg_lockstep* L, int op, double s, const float* in, int Fin, int fin, float* out,
-              int Fout, int fout, const float* add) {
-  for (const Group& g : L->groups) {
+// The runs of equal grids transform concurrently: run g's passes go to side
+// stream g % kSideStreams, forked from and joined back to the batch's stream
+// with events (graph branches under capture).
+constexpr int kSideStreams = 8;
+
+void fork_groups(reg_lockstep* L) {
+  check(L, cudaEventRecord(L->ev_fork, L->st), "fork");
+  for (size_t k = 0; k < L->side.size(); ++k)
+    check(L, cudaStreamWaitEvent(L->side[k], L->ev_fork, 0), "fork");
+}
+
+void join_groups(reg_lockstep* L) {
+  for (size_t k = 0; k < L->side.size(); ++k) {
+    check(L, cudaEventRecord(L->ev_join[k], L->side[k]), "join");
+    check(L, cudaStreamWaitEvent(L->st, L->ev_join[k], 0), "join");
+  }
+}
+
+cudaStream_t group_stream(const reg_lockstep* L, size_t g) { return L->side[g % L->side.size()]; }
+
+// The forward half of out = op(in) [+ add] (row R2C and column passes) for
+// every problem: the arrays hold Fin fields per problem, each problem Fin /
+// fin groups of fin fields; the spectra stay in the runs' workspaces for
+// spectral_inv. Fields of problems outside the mask are skipped (their
+// outputs are not read before the problem's next phase recomputes them).
+void spectral_fwd(reg_lockstep* L, int op, double s, const float* in, int Fin, int fin, int fout) {
+  fork_groups(L);
+  for (size_t gi = 0; gi < L->groups.size(); ++gi) {
+    const Group& g = L->groups[gi];
+    const cudaStream_t st = group_stream(L, gi);
     const long long off = L->hdesc[g.p0].off;
     const int ng = g.count * (Fin / fin);
     float2* sin = g.spec;
     float2* sout = g.spec + (size_t)ng * fin * g.g.spec;
-    fft_rows_r2c(g.g.n1, g.g.n2, in + (size_t)Fin * off, g.g.N, sin, g.g.spec, ng * fin, g.tw1,
-                 L->st);
+    const FieldMask fmi{L->dmask, g.p0, Fin}, fmc{L->dmask, g.p0, Fin / fin};
+    fft_rows_r2c(g.g.n1, g.g.n2, in + (size_t)Fin * off, g.g.N, sin, g.g.spec, ng * fin, g.tw1, st,
+                 fmi);
     ColArgs a{};
     a.n1_in = a.n1_out = a.n1 = g.g.n1;
     a.n2_in = a.n2_out = a.n2 = g.g.n2;
@@ -226,11 +257,38 @@ void spectral(reg_lockstep* L, int op, double s, const float* in, int Fin, int f
     a.out_fstride = g.g.spec;
     a.nin = fin;
     a.nout = fout;
-    fft_cols(a, ng, L->st);
-    fft_rows_c2r(g.g.n1, g.g.n2, sout, g.g.spec, out + (size_t)Fout * off, g.g.N,
-                 add ? add + (size_t)Fout * off : nullptr, g.g.N, ng * fout, g.tw1, L->st);
+    a.fm = fmc;
+    fft_cols(a, ng, st);
   }
   check_launch(L, "spectral operator");
+}
+
+// The inverse half: row C2R passes of the spectra spectral_fwd left, with the
+// addend, after everything queued on the batch's stream; joins the runs'
+// streams back.
+void spectral_inv(reg_lockstep* L, int Fin, int fin, float* out, int Fout, int fout,
+                  const float* add) {
+  fork_groups(L);
+  for (size_t gi = 0; gi < L->groups.size(); ++gi) {
+    const Group& g = L->groups[gi];
+    const cudaStream_t st = group_stream(L, gi);
+    const long long off = L->hdesc[g.p0].off;
+    const int ng = g.count * (Fin / fin);
+    float2* sout = g.spec + (size_t)ng * fin * g.g.spec;
+    const FieldMask fmo{L->dmask, g.p0, Fout};
+    fft_rows_c2r(g.g.n1, g.g.n2, sout, g.g.spec, out + (size_t)Fout * off, g.g.N,
+                 add ? add + (size_t)Fout * off : nullptr, g.g.N, ng * fout, g.tw1, st, nullptr,
+                 fmo);
+  }
+  join_groups(L);
+  check_launch(L, "spectral operator");
+}
+
+// out (Fout fields per problem) = op(in (Fin fields per problem)) [+ add]
+void spectral(reg_lockstep* L, int op, double s, const float* in, int Fin, int fin, float* out,
+              int Fout, int fout, const float* add) {
+  spectral_fwd(L, op, s, in, Fin, fin, fout);
+  spectral_inv(L, Fin, fin, out, Fout, fout, add);
 }
 
 void dot(reg_lockstep* L, BRef a, BRef b, int len, int kind) {
@@ -295,7 +353,7 @@ std::vector<double> objective(reg_lockstep* L) {
                       L->partial, slot(L, L_J1), L->st);
   dot(L, R(L->v, 2), R(L->Av, 2), 2, L_J2);
   check_launch(L, "objective");
-  read_slots(L, L_J1, 2, true);
+  read_slots(L, L_J1, 3, true);
   std::vector<double> J(L->B);
   for (int p = 0; p < L->B; ++p) {
     const double hh = L->hh[p];
@@ -340,6 +398,9 @@ void hessian(reg_lockstep* L, const float* vt, float* out) {
   float* mt = L->fA;
   float* mt2 = L->fB;
   float* vtm = const_cast<float*>(vt);
+  // beta A v~: its forward transforms depend only on v~ and run on the runs'
+  // streams while the transport steps (which use no FFT workspace) run here
+  spectral_fwd(L, SPOP_REGPOW, 1.0, vt, 2, 1, 1);
   launch_incstate_first_fused_b(V, ht, R(vtm, 2), R(L->dX, 2), R(L->G, FG, 0), R(L->gm, Fg, 2),
                                 R(L->vtD, 2), R(mt2, 1), L->st);
   std::swap(mt, mt2);
@@ -367,7 +428,7 @@ void hessian(reg_lockstep* L, const float* vt, float* out) {
     std::swap(lt, lt2);
   }
   check_launch(L, "incremental adjoint");
-  spectral(L, SPOP_REGPOW, 1.0, vt, 2, 1, out, 2, 1, L->b);
+  spectral_inv(L, 2, 1, out, 2, 1, L->b);
 }
 
 // The matvec in -> out of every problem of the mask, captured as a CUDA
@@ -440,9 +501,11 @@ struct PcgOut {
 
 // PCG (Hestenes-Stiefel) from x = 0 on the problems of `act`, each with its
 // own tolerance: the same steps as the one-problem PCG, every vector
-// operation masked to the problems still iterating.
+// operation masked to the problems still iterating. bb[p] = <rhs, rhs> of
+// problem p (the right-hand side -g has the squared norm <g, g> the Newton
+// loop already holds, to the bit).
 PcgOut pcg(reg_lockstep* L, const std::vector<int>& act, const std::vector<double>& rtol,
-           int maxit) {
+           const std::vector<double>& bb, int maxit) {
   const int B = L->B;
   const long long n = 2 * L->NT;
   PcgOut out;
@@ -452,12 +515,10 @@ PcgOut pcg(reg_lockstep* L, const std::vector<int>& act, const std::vector<doubl
   set_mask(L, run);
   launch_fill(L->kx, n, 0.f, L->st);
   check(L, cudaMemcpyAsync(L->kr, L->rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, L->st), "copy");
-  dot(L, R(L->rhs, 2), R(L->rhs, 2), 2, L_BB);
-  read_slots(L, L_BB, 1);
   std::vector<double> bnorm(B, 0.0);
   for (int p = 0; p < B; ++p) {
     if (!run[p]) continue;
-    bnorm[p] = std::sqrt(hslot(L, L_BB, p));
+    bnorm[p] = std::sqrt(bb[p]);
     if (!(bnorm[p] > 0.0)) run[p] = 0;
   }
   if (std::none_of(run.begin(), run.end(), [](int x) { return x != 0; })) return out;
@@ -470,8 +531,8 @@ PcgOut pcg(reg_lockstep* L, const std::vector<int>& act, const std::vector<doubl
     for (int p = 0; p < B; ++p)
       if (run[p]) ++out.matvecs[p];
     dot(L, R(L->kp, 2), R(L->kq, 2), 2, L_PQ);
-    launch_pcg_update_b(L->dpmap, L->dmask, 2, n, slot(L, L_RZ), slot(L, L_PQ), L->kp, L->kq,
-                        L->kx, L->kr, L->st);
+    launch_pcg_update_b(L->dpmap, L->dmask, B, 2, n, slot(L, L_RZ), slot(L, L_PQ), L->dcoef, L->don,
+                        L->kp, L->kq, L->kx, L->kr, L->st);
     dot(L, R(L->kr, 2), R(L->kr, 2), 2, L_RR);
     read_slots(L, L_PQ, 2);
     std::vector<int> next = run;
@@ -495,8 +556,8 @@ PcgOut pcg(reg_lockstep* L, const std::vector<int>& act, const std::vector<doubl
     set_mask(L, run);
     precond(L, L->kr, L->kz);
     dot(L, R(L->kr, 2), R(L->kz, 2), 2, L_RZNEW);
-    launch_pcg_direction_b(L->dpmap, L->dmask, 2, n, slot(L, L_RZNEW), slot(L, L_RZ), L->kz, L->kp,
-                           L->st);
+    launch_pcg_direction_b(L->dpmap, L->dmask, B, 2, n, slot(L, L_RZNEW), slot(L, L_RZ), L->dcoef,
+                           L->don, L->kz, L->kp, L->st);
     launch_copy_scalars_b(B, L->dmask, slot(L, L_RZNEW), slot(L, L_RZ), L->st);
     check_launch(L, "pcg");
   }
@@ -671,6 +732,8 @@ reg_status reg_lockstep_create(const reg_grid* grids, int B, int nt, const doubl
     check(L, cudaMallocHost(&h, (size_t)L_NSLOTS * B * sizeof(double)), "cudaMallocHost");
     L->hsc = static_cast<double*>(h);
     L->dalpha = dalloc<float>(L, 2 * B);
+    L->dcoef = dalloc<float>(L, B);
+    L->don = dalloc<int>(L, B);
     // FFT groups
     for (int p = 0; p < B;) {
       Group g;
@@ -687,6 +750,14 @@ reg_status reg_lockstep_create(const reg_grid* grids, int B, int nt, const doubl
       g.spec = dalloc<float2>(L, (size_t)g.slots * g.g.spec);
       L->groups.push_back(g);
       p = q;
+    }
+    const size_t ns = std::min(L->groups.size(), (size_t)kSideStreams);
+    L->side.assign(ns, nullptr);
+    L->ev_join.assign(ns, nullptr);
+    check(L, cudaEventCreateWithFlags(&L->ev_fork, cudaEventDisableTiming), "event");
+    for (size_t k = 0; k < ns; ++k) {
+      check(L, cudaStreamCreateWithFlags(&L->side[k], cudaStreamNonBlocking), "stream");
+      check(L, cudaEventCreateWithFlags(&L->ev_join[k], cudaEventDisableTiming), "event");
     }
     const size_t N = (size_t)L->NT;
     L->mR = dalloc<float>(L, N);
@@ -718,6 +789,11 @@ reg_status reg_lockstep_destroy(reg_lockstep* L) {
     if (g.exec) cudaGraphExecDestroy(g.exec);
   for (void* p : L->allocs) cudaFree(p);
   if (L->hsc) cudaFreeHost(L->hsc);
+  for (cudaStream_t x : L->side)
+    if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t e : L->ev_join)
+    if (e) cudaEventDestroy(e);
+  if (L->ev_fork) cudaEventDestroy(L->ev_fork);
   if (L->cap) cudaStreamDestroy(L->cap);
   if (L->st) cudaStreamDestroy(L->st);
   delete L;
@@ -845,7 +921,7 @@ reg_status reg_lockstep_solve(reg_lockstep* L, float* const* v, double gtol, reg
                       slot(L, L_GINF), L->st);
       dot(L, R(L->gcur, 2), R(L->gcur, 2), 2, L_G2);
       read_slots(L, L_GINF, 2);
-      std::vector<double> rtol(B, 0.0);
+      std::vector<double> rtol(B, 0.0), gg(B, 0.0);
       for (int p = 0; p < B; ++p) {
         if (!active[p]) continue;
         ginf[p] = hslot(L, L_GINF, p);
@@ -857,22 +933,21 @@ reg_status reg_lockstep_solve(reg_lockstep* L, float* const* v, double gtol, reg
         rel[p] = ginf[p] / gref_inf[p];
         if (rel[p] <= gtol || ginf[p] <= o.gabs) { active[p] = 0; continue; }
         if (k == o.max_newton) { status[p] = REG_ENOTCONV; active[p] = 0; continue; }
-        rtol[p] = std::fmin(0.5, std::sqrt(hslot(L, L_G2, p)) / gref_2[p]);
+        gg[p] = hslot(L, L_G2, p);
+        rtol[p] = std::fmin(0.5, std::sqrt(gg[p]) / gref_2[p]);
       }
       if (std::none_of(active.begin(), active.end(), [](int x) { return x != 0; })) break;
       set_mask(L, active);
       ensure_G(L);
       launch_lincomb(n, -1.f, L->gcur, 0.f, nullptr, L->rhs, L->st);   // rhs = -g
-      const PcgOut pr = pcg(L, active, rtol, o.max_pcg);
+      const PcgOut pr = pcg(L, active, rtol, gg, o.max_pcg);
       for (int p = 0; p < B; ++p) {
         inf[p].pcg_iters += pr.iters[p];
         inf[p].matvecs += pr.matvecs[p];
       }
       set_mask(L, active);
-      dot(L, R(L->gcur, 2), R(L->kx, 2), 2, L_SLOPE);
-      read_slots(L, L_SLOPE, 1);
+      dot(L, R(L->gcur, 2), R(L->kx, 2), 2, L_SLOPE);   // read with the first trial's J
       std::vector<double> slope(B, 0.0), alpha(B, 1.0), Jt(B, 0.0);
-      for (int p = 0; p < B; ++p) slope[p] = L->hh[p] * hslot(L, L_SLOPE, p);
       std::vector<int> search = active, accepted(B, 0);
       for (int ls = 0; ls <= o.max_backtracks; ++ls) {
         set_mask(L, search);
@@ -881,6 +956,8 @@ reg_status reg_lockstep_solve(reg_lockstep* L, float* const* v, double gtol, reg
         lincomb_masked(L, a, L->vcur, al, L->kx, L->vtrial);
         set_velocity(L, L->vtrial);
         const std::vector<double> Jl = objective(L);
+        if (ls == 0)
+          for (int p = 0; p < B; ++p) slope[p] = L->hh[p] * hslot(L, L_SLOPE, p);
         for (int p = 0; p < B; ++p) {
           if (!search[p]) continue;
           Jt[p] = Jl[p];
@@ -941,6 +1018,46 @@ reg_status reg_lockstep_solve(reg_lockstep* L, float* const* v, double gtol, reg
   }
   if (s != REG_OK) return s;
   return worst;
+}
+
+reg_status reg_lockstep_matvec_time(reg_lockstep* L, int reps, double* ms) {
+  if (!L || reps < 1 || !ms) return REG_EINVAL;
+  return guarded(L, [&] {
+    reg_lockstep::GraphEntry* e = nullptr;
+    for (auto& g : L->graphs)
+      if (g.in == L->wv && g.out == L->wo) e = &g;
+    if (!e || !e->exec)
+      fail(L, REG_ESTATE, "call reg_lockstep_hessian_matvec twice first (the graph is captured on "
+                          "the second call)");
+    set_mask(L, all_of(L->B));
+    cudaEvent_t a, b;
+    check(L, cudaEventCreate(&a), "event");
+    check(L, cudaEventCreate(&b), "event");
+    check(L, cudaEventRecord(a, L->st), "event");
+    for (int r = 0; r < reps; ++r) {
+      check(L, cudaGraphLaunch(e->exec, L->st), "graph launch");
+      g_launch_count += e->kernels;
+    }
+    check(L, cudaEventRecord(b, L->st), "event");
+    check(L, cudaEventSynchronize(b), "event");
+    float t = 0.f;
+    check(L, cudaEventElapsedTime(&t, a, b), "event");
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = (double)t / reps;
+  });
+}
+
+reg_status reg_lockstep_info(const reg_lockstep* L, long long* points, int* tiles, int* launches) {
+  if (!L) return REG_EINVAL;
+  if (points) *points = L->NT;
+  if (tiles) *tiles = L->ntiles;
+  if (launches) {
+    *launches = 0;
+    for (const auto& g : L->graphs)
+      if (g.in == L->kp && g.exec) *launches = (int)g.kernels;
+  }
+  return REG_OK;
 }
 
 const char* reg_lockstep_last_error(const reg_lockstep* L) { return L ? L->err.c_str() : "null batch"; }

@@ -422,48 +422,64 @@ void launch_lincomb_b(const int* pmap, const int* mask, int F, long long n, cons
   launch_k(k_lincomb_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, a, x, b, y, z);
 }
 
-__global__ void k_pcg_update_b(const int* __restrict__ pmap, const int* __restrict__ mask, int F,
-                               long long n, const double* __restrict__ rz,
-                               const double* __restrict__ pq, const float* __restrict__ p,
-                               const float* __restrict__ q, float* __restrict__ x,
-                               float* __restrict__ r) {
+// Per-problem coefficients of the batched PCG updates, computed once per
+// problem (FP64 divisions stay off the per-element path): the step
+// alpha_p = (float)(rz_p / pq_p), on_p = 0 where the problem is masked or
+// pq_p <= 0 (mode 0); the direction weight beta_p = (float)(rz_new_p /
+// rz_old_p) (mode 1). The same roundings as the one-problem kernels.
+__global__ void k_pcg_coef_b(int nprob, const int* __restrict__ mask, int mode,
+                             const double* __restrict__ num, const double* __restrict__ den,
+                             float* __restrict__ coef, int* __restrict__ on) {
+  pdl_enter();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nprob) return;
+  const bool use = mask[p] && (mode == 1 || den[p] > 0.0);
+  on[p] = use;
+  coef[p] = use ? (float)(num[p] / den[p]) : 0.f;
+}
+
+__global__ void k_pcg_update_b(const int* __restrict__ pmap, int F, long long n,
+                               const float* __restrict__ coef, const int* __restrict__ on,
+                               const float* __restrict__ p, const float* __restrict__ q,
+                               float* __restrict__ x, float* __restrict__ r) {
   pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int k = elem_problem(pmap, F, i);
-    if (!mask[k] || !(pq[k] > 0.0)) continue;
-    const double ad = rz[k] / pq[k];
-    const float alpha = (float)ad;
+    if (!on[k]) continue;
+    const float alpha = coef[k];
     x[i] = fmaf(alpha, p[i], x[i]);
     r[i] = fmaf(-alpha, q[i], r[i]);
   }
 }
 
-void launch_pcg_update_b(const int* pmap, const int* mask, int F, long long n, const double* rz,
-                         const double* pq, const float* p, const float* q, float* x, float* r,
-                         cudaStream_t st) {
-  launch_k(k_pcg_update_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, rz, pq, p, q, x, r);
+void launch_pcg_update_b(const int* pmap, const int* mask, int nprob, int F, long long n,
+                         const double* rz, const double* pq, float* coef, int* on, const float* p,
+                         const float* q, float* x, float* r, cudaStream_t st) {
+  launch_k(k_pcg_coef_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, mask, 0, rz, pq, coef, on);
+  launch_k(k_pcg_update_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, F, n, (const float*)coef,
+           (const int*)on, p, q, x, r);
 }
 
-__global__ void k_pcg_direction_b(const int* __restrict__ pmap, const int* __restrict__ mask,
-                                  int F, long long n, const double* __restrict__ rz_new,
-                                  const double* __restrict__ rz_old, const float* __restrict__ z,
-                                  float* __restrict__ p) {
+__global__ void k_pcg_direction_b(const int* __restrict__ pmap, int F, long long n,
+                                  const float* __restrict__ coef, const int* __restrict__ on,
+                                  const float* __restrict__ z, float* __restrict__ p) {
   pdl_enter();
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const int k = elem_problem(pmap, F, i);
-    if (!mask[k]) continue;
-    const float beta = (float)(rz_new[k] / rz_old[k]);
-    p[i] = fmaf(beta, p[i], z[i]);
+    if (!on[k]) continue;
+    p[i] = fmaf(coef[k], p[i], z[i]);
   }
 }
 
-void launch_pcg_direction_b(const int* pmap, const int* mask, int F, long long n,
-                            const double* rz_new, const double* rz_old, const float* z,
-                            float* p, cudaStream_t st) {
-  launch_k(k_pcg_direction_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, mask, F, n, rz_new, rz_old,
-           z, p);
+void launch_pcg_direction_b(const int* pmap, const int* mask, int nprob, int F, long long n,
+                            const double* rz_new, const double* rz_old, float* coef, int* on,
+                            const float* z, float* p, cudaStream_t st) {
+  launch_k(k_pcg_coef_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, mask, 1, rz_new, rz_old,
+           coef, on);
+  launch_k(k_pcg_direction_b, dim3(nblocks(n)), dim3(kRT), 0, st, pmap, F, n, (const float*)coef,
+           (const int*)on, z, p);
 }
 
 __global__ void k_copy_scalars_b(int nprob, const int* __restrict__ mask,

@@ -121,6 +121,9 @@ _SIGNATURES = {
     "reg_lockstep_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                     ctypes.POINTER(_P)],
     "reg_lockstep_solve": [_P, ctypes.POINTER(_P), _D, ctypes.POINTER(reg_info)],
+    "reg_lockstep_matvec_time": [_P, _I, ctypes.POINTER(_D)],
+    "reg_lockstep_info": [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_I),
+                          ctypes.POINTER(_I)],
     "reg_lockstep_last_error": [_P],
     "reg_unet_param_count": [],
     "reg_unet_create": [_I, _I, ctypes.POINTER(_P)],
@@ -474,6 +477,19 @@ class Lockstep:
             d["status_name"] = STATUS_NAMES.get(d["status"], str(d["status"]))
             out.append(d)
         return out
+
+    def matvec_time(self, reps=20):
+        """Mean device time (ms) of one replay of the matvec graph of the last
+        hessian_matvec (call it twice first)."""
+        ms = ctypes.c_double()
+        self._check(self.lib.reg_lockstep_matvec_time(self.h, int(reps), ctypes.byref(ms)))
+        return ms.value
+
+    def info(self):
+        pts, tiles, launches = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.reg_lockstep_info(self.h, ctypes.byref(pts), ctypes.byref(tiles),
+                                               ctypes.byref(launches)))
+        return {"points": pts.value, "tiles": tiles.value, "matvec_graph_kernels": launches.value}
 
     def close(self):
         h = getattr(self, "h", None)
