@@ -95,6 +95,15 @@ __device__ __forceinline__ void dft8(const float2 (&a)[8], float2 (&y)[8]) {
   y[3] = cadd(e3, o3); y[7] = csub(e3, o3);
 }
 
+// Shared-memory position of element i of a block's FFT buffer: the low four
+// bits of i are XORed with bits 3..6 (a permutation inside each aligned run
+// of 16 float2). The Stockham passes store with strides 8 and 64 (radix-8
+// passes one and two), which put 8 or 4 lanes of a half-warp on the same
+// bank; with this permutation every pass and every aligned contiguous run is
+// conflict-free. Buffers start on multiples of 128 elements, so a buffer's
+// permutation does not depend on where it sits in shared memory.
+__device__ __forceinline__ int sw(int i) { return i ^ ((i >> 3) & 15); }
+
 // In-place FFT of P lines of length N = 2^L 3^T stored contiguously at s
 // (line l at s + l*N): radix-8 Stockham passes, then one radix-4 or radix-2
 // pass for the remaining factor of 2^L, then a radix-3 pass if T = 1, each
@@ -122,10 +131,9 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       if (TOT8 % NT == 0 || q < TOT8) {
         const int l = q / Q8, j = q % Q8;
         const int k = j & (Ns - 1);
-        const float2* x = s + l * N;
         float2 a[8];
 #pragma unroll
-        for (int r = 0; r < 8; ++r) a[r] = x[j + r * Q8];
+        for (int r = 0; r < 8; ++r) a[r] = s[sw(l * N + j + r * Q8)];
         if (lns > 0) {
 #pragma unroll
           for (int r = 1; r < 8; ++r) {
@@ -143,7 +151,7 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       const int q = t + b * NT;
       if (TOT8 % NT == 0 || q < TOT8) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) s[base[b] + r * Ns] = v[b][r];
+        for (int r = 0; r < 8; ++r) s[sw(base[b] + r * Ns)] = v[b][r];
       }
     }
     __syncthreads();
@@ -163,8 +171,8 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       if (TOT4 % NT == 0 || q < TOT4) {
         const int l = q / Q4, j = q % Q4;
         const int k = j & (Ns - 1);
-        const float2* x = s + l * N;
-        float2 a0 = x[j], a1 = x[j + Q4], a2 = x[j + 2 * Q4], a3 = x[j + 3 * Q4];
+        const int x = l * N + j;
+        float2 a0 = s[sw(x)], a1 = s[sw(x + Q4)], a2 = s[sw(x + 2 * Q4)], a3 = s[sw(x + 3 * Q4)];
         if (lns > 0) {
           const float2 w1 = __ldg(tw + k * tws);
           const float2 w2 = __ldg(tw + 2 * k * tws);
@@ -184,10 +192,10 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
     for (int b = 0; b < B4; ++b) {
       const int q = t + b * NT;
       if (TOT4 % NT == 0 || q < TOT4) {
-        s[base[b]] = v[b][0];
-        s[base[b] + Ns] = v[b][1];
-        s[base[b] + 2 * Ns] = v[b][2];
-        s[base[b] + 3 * Ns] = v[b][3];
+        s[sw(base[b])] = v[b][0];
+        s[sw(base[b] + Ns)] = v[b][1];
+        s[sw(base[b] + 2 * Ns)] = v[b][2];
+        s[sw(base[b] + 3 * Ns)] = v[b][3];
       }
     }
     __syncthreads();
@@ -207,9 +215,8 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       if (TOT2 % NT == 0 || q < TOT2) {
         const int l = q / Q2, j = q % Q2;
         const int k = j & (Ns - 1);
-        const float2* x = s + l * N;
-        const float2 a0 = x[j];
-        float2 a1 = x[j + Q2];
+        const float2 a0 = s[sw(l * N + j)];
+        float2 a1 = s[sw(l * N + j + Q2)];
         if (lns > 0) {
           const float2 w = __ldg(tw + k * tws);
           a1 = INV ? cmulc(a1, w) : cmul(a1, w);
@@ -224,8 +231,8 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
     for (int b = 0; b < B2; ++b) {
       const int q = t + b * NT;
       if (TOT2 % NT == 0 || q < TOT2) {
-        s[base[b]] = v0[b];
-        s[base[b] + Ns] = v1[b];
+        s[sw(base[b])] = v0[b];
+        s[sw(base[b] + Ns)] = v1[b];
       }
     }
     __syncthreads();
@@ -244,9 +251,8 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
       const int q = t + b * NT;
       if (TOT3 % NT == 0 || q < TOT3) {
         const int l = q / Q3, k = q % Q3;
-        const float2* x = s + l * N;
-        const float2 a0 = x[k];
-        float2 a1 = x[k + Q3], a2 = x[k + 2 * Q3];
+        const float2 a0 = s[sw(l * N + k)];
+        float2 a1 = s[sw(l * N + k + Q3)], a2 = s[sw(l * N + k + 2 * Q3)];
         if (L > 0) {
           const float2 w1 = __ldg(tw + k), w2 = __ldg(tw + 2 * k);
           a1 = INV ? cmulc(a1, w1) : cmul(a1, w1);
@@ -268,9 +274,9 @@ __device__ void fft_smem(float2* s, const float2* __restrict__ tw) {
     for (int b = 0; b < B3; ++b) {
       const int q = t + b * NT;
       if (TOT3 % NT == 0 || q < TOT3) {
-        s[base[b]] = v0[b];
-        s[base[b] + Q3] = v1[b];
-        s[base[b] + 2 * Q3] = v2[b];
+        s[sw(base[b])] = v0[b];
+        s[sw(base[b] + Q3)] = v1[b];
+        s[sw(base[b] + 2 * Q3)] = v2[b];
       }
     }
     __syncthreads();
@@ -308,7 +314,7 @@ k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__
 #pragma unroll
   for (int u = 0; u < LD; ++u) {
     const int q = t + u * NT;
-    if ((P * N) % NT == 0 || q < P * N) sm[q] = v[u];
+    if ((P * N) % NT == 0 || q < P * N) sm[sw(q)] = v[u];
   }
   __syncthreads();
   fft_smem<L, T, P, NT, false>(sm, tw);
@@ -316,8 +322,8 @@ k_rows_r2c(const float* __restrict__ in, long long fstride, float2* __restrict__
   constexpr int R = 2 * P;
   for (int q = t; q < (N / 2 + 1) * R; q += NT) {
     const int r = q % R, k = q / R, l = r >> 1;
-    const float2 Z = sm[l * N + k];
-    const float2 Zm = sm[l * N + (k == 0 ? 0 : N - k)];
+    const float2 Z = sm[sw(l * N + k)];
+    const float2 Zm = sm[sw(l * N + (k == 0 ? 0 : N - k))];
     float2 X;
     if (r & 1) {  // X_b = (Z - conj(Zm)) / (2i)
       X = make_float2(0.5f * (Z.y + Zm.y), -0.5f * (Z.x - Zm.x));
@@ -400,8 +406,8 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
         Xa.y = 0.f;
         Xb.y = 0.f;
       }
-      sm[l * N + k] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
-      if (k > 0 && k < N / 2) sm[l * N + N - k] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
+      sm[sw(l * N + k)] = make_float2(Xa.x - Xb.y, Xa.y + Xb.x);
+      if (k > 0 && k < N / 2) sm[sw(l * N + N - k)] = make_float2(Xa.x + Xb.y, Xb.x - Xa.y);
     }
   }
   __syncthreads();
@@ -424,7 +430,8 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const long long e = r + h * N;
-          const float Ad = (h ? sm[q].y : sm[q].x) + (ad ? cd_[u][h] : 0.f);
+          const float2 o = sm[sw(q)];
+          const float Ad = (h ? o.y : o.x) + (ad ? cd_[u][h] : 0.f);
           const float ri = cr_[u][h] - Ad;
           const float di = fmaf(cheb.a, cd_[u][h], cheb.b * ri);
           cr[e] = ri;
@@ -441,7 +448,8 @@ k_rows_c2r(const float2* __restrict__ spec, long long sstride, float* __restrict
     if ((P * N) % NT == 0 || q < P * N) {
       const int l = q / N, i = q % N;
       const long long r = (long long)(row0 + 2 * l) * N + i;
-      float a = sm[q].x, b = sm[q].y;
+      const float2 o = sm[sw(q)];
+      float a = o.x, b = o.y;
       if (ad) {
         a += cr_[u][0];
         b += cr_[u][1];
@@ -632,7 +640,7 @@ __global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 1024 / ColCfg<LI, LO, T
 #pragma unroll
     for (int u = 0; u < LD; ++u) {
       const int q = t + u * NT;
-      if (q < P * NI) bin[c * P * NM + q] = v[u];
+      if (q < P * NI) bin[c * P * NM + sw(q)] = v[u];
     }
   }
   __syncthreads();
@@ -655,11 +663,11 @@ __global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 1024 / ColCfg<LI, LO, T
       if (ok) {
         for (int c = 0; c < a.nin; ++c) {
           const float2 sg = symbol(a, o, c, k1, k2);
-          acc = cadd(acc, cmul(bin[c * P * NM + l * NI + ki], sg));
+          acc = cadd(acc, cmul(bin[c * P * NM + sw(l * NI + ki)], sg));
         }
         acc = cscale(acc, a.scale);
       }
-      bout[l * NO + ko] = acc;
+      bout[sw(l * NO + ko)] = acc;
     }
     __syncthreads();
     fft_smem<LO, T, P, NT, true>(bout, a.tw_out);
@@ -667,7 +675,7 @@ __global__ void __launch_bounds__(ColCfg<LI, LO, T>::NT, 1024 / ColCfg<LI, LO, T
     for (int q = t; q < P * NO; q += NT) {
       const int l = q / NO, k2 = q % NO;
       const int k1 = line0 + l;
-      if (k1 < a.nk1_out) dst[(long long)k1 * NO + k2] = bout[q];
+      if (k1 < a.nk1_out) dst[(long long)k1 * NO + k2] = bout[sw(q)];
     }
     __syncthreads();
   }
@@ -714,6 +722,7 @@ static void launch_cols(const ColArgs& a, int groups, cudaStream_t st) {
   using C = ColCfg<LI, LO, T>;
   const size_t smem = (size_t)(a.nin + 1) * C::P * C::NM * sizeof(float2);
   static_assert(3 * C::P * C::NM * sizeof(float2) <= 48 * 1024, "fits the default shared memory");
+  static_assert((C::P * C::NM) % 128 == 0, "buffers start on multiples of 128 elements (sw)");
   dim3 grid((a.nk1_out + C::P - 1) / C::P, groups);
   launch_k(k_cols<LI, LO, T>, dim3(grid), dim3(C::NT), smem, st, a);
 }
