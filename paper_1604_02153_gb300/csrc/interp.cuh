@@ -164,11 +164,14 @@ struct BoxDims {
   static constexpr int WS = W + 2 * kL;      // staged width and height
   static constexpr int PS = quad_pitch(WS);  // row pitch of the staged samples
   static constexpr int PT = quad_pitch(WS);  // row pitch of the transposed x-pass output
-  static constexpr int PB = W + 1;           // odd pitch of the coefficient box
+  // pitch of the coefficient box, 16 mod 32: the two tile rows a warp
+  // gathers for (16 lanes each) fall in opposite halves of the banks
+  static constexpr int PB = W + (48 - W % 32) % 32;
   static constexpr int kStage = WS * PS;     // floats
   static constexpr int kMid = W * PT;
   static constexpr size_t kSmemBytes = sizeof(float) * (kStage + kMid);
   static_assert(PS >= WS + 2 && PT >= WS + 2, "float4 reads run 2 samples past a chain");
+  static_assert(PB % 32 == 16 && W * PB <= kStage, "the box fits the staging buffer it reuses");
 };
 
 // float4 vectors per staged row (the first one starts at the 4-aligned
@@ -193,6 +196,11 @@ __device__ __forceinline__ void put_staged(float* stage, int r, int v, int off, 
   }
 }
 
+// Outputs per recursion chain of the box prefilter (a chain reads kL
+// samples more on each side). 8 gives the segments of k_prefilter (the same
+// coefficients to the bit).
+constexpr int kBoxSeg = 8;
+
 // The two recursion passes of prefilter_box on samples already staged
 // (stage[r * PS + c] = sample at node (bx0 - kL + c, by0 - kL + r)); ends
 // with a block barrier.
@@ -201,7 +209,8 @@ __device__ __forceinline__ void box_recursions(float* stage, float* mid, float* 
   using D = BoxDims<W>;
   constexpr int WS = D::WS, PS = D::PS, PT = D::PT, PB = D::PB;
   const int t = threadIdx.x;
-  constexpr int kSeg = 8, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
+  constexpr int kSeg = kBoxSeg, kSegs = W / kSeg, kLen = kSeg + 2 * kL;
+  static_assert(W % kSeg == 0 && kSeg % 4 == 0, "whole float4-aligned segments");
   constexpr int kQ = (kLen + 3) / 4;   // float4 reads per chain
   // x recursions: a warp walks 32 consecutive staged rows of one segment;
   // the outputs go to mid transposed (mid[column * PT + row])

@@ -582,10 +582,11 @@ constexpr int kFP = 1024 / kFT;   // points per thread
 constexpr int kFS = 32 / kFP;     // their spacing along the tile row
 
 // The kFP points of a thread in a fused kernel are kFS apart in the tile row,
-// so that the 32 lanes of a warp touch consecutive columns for each point: the
-// 4x4 gathers from the shared-memory coefficient box then hit 32 different
-// banks (adjacent points per thread gave 2-way conflicts), and the streamed
-// loads and stores stay coalesced.
+// so that the 16 lanes of a warp on one tile row touch consecutive columns for
+// each point (adjacent points per thread gave 2-way conflicts) and the
+// streamed loads and stores stay coalesced; with the box pitch 16 mod 32 the
+// warp's two tile rows fall in opposite halves of the banks, so a 4x4 gather
+// conflicts only where the stencil bases of neighbouring points jump.
 template <int K>
 __device__ __forceinline__ void ldf(const float* p, float (&a)[K]) {
 #pragma unroll
