@@ -259,6 +259,13 @@ void launch_pcg_direction(long long n, const double* rz_new, const double* rz_ol
 void launch_fill(float* x, long long n, float value, cudaStream_t st);
 void launch_splitmix(float* x, long long n, unsigned long long seed, cudaStream_t st);
 int reduce_partials();
+// Blocks (partial sums) of the two-stage reduction of n values: four float4
+// per thread of a 256-thread block, at most reduce_partials(). The batched
+// reductions use the same partition per problem, so both give the same bits.
+inline int reduce_blocks(long long n) {
+  const long long b = (n + 16LL * 256 - 1) / (16LL * 256);
+  return (int)(b < 1 ? 1 : (b > 1216 ? 1216 : b));
+}
 
 // ---------------------------------------------------------------------------
 // Batches of problems advanced in lockstep (lockstep.cu): one launch per

@@ -36,15 +36,6 @@ using namespace regnk;
 
 namespace {
 
-constexpr int kRedThreads = 256;   // threads of a reduction block (reduce.cu)
-constexpr int kRedBlocks = 1216;   // partial sums of a one-problem reduction (reduce.cu)
-
-// blocks of the one-problem reduction of n values (reduce.cu nblocks)
-int red_blocks(long long n) {
-  long long b = (n + 4LL * kRedThreads - 1) / (4LL * kRedThreads);
-  return (int)(b < 1 ? 1 : (b > kRedBlocks ? kRedBlocks : b));
-}
-
 // per-problem FP64 scalars: slot kind * B + p
 // (J1, J2, SLOPE adjacent: the line search reads the slope <g, s> with the
 // first trial's objective)
@@ -701,7 +692,7 @@ reg_status reg_lockstep_create(const reg_grid* grids, int B, int nt, const doubl
       std::vector<int> nb(B), first(B);
       for (int p = 0; p < B; ++p) {
         const long long n = (long long)len * L->hdesc[p].n1 * L->hdesc[p].n2;
-        nb[p] = red_blocks(n);
+        nb[p] = reduce_blocks(n);
         first[p] = (int)blocks.size();
         for (int k = 0; k < nb[p]; ++k) blocks.push_back(make_int2(p, k));
       }

@@ -19,6 +19,7 @@ constexpr int kRT = 256;       // threads per reduction block
 constexpr int kRB = 1216;      // maximum partial sums (8 per SM on 152 SMs)
 
 int reduce_partials() { return kRB; }
+static_assert(kRT == 256 && kRB == 1216, "reduce_blocks (kernels.h) assumes these");
 
 static int nblocks(long long n) {
   long long b = (n + 4LL * kRT - 1) / (4LL * kRT);
@@ -91,6 +92,7 @@ __device__ __forceinline__ double partial_sum(const float* __restrict__ a,
   const long long n4 = vec4 ? (n >> 2) : 0;   // float4 path only for 16-byte aligned inputs
   const float4* a4 = reinterpret_cast<const float4*>(a);
   const float4* b4 = reinterpret_cast<const float4*>(b);
+#pragma unroll 4
   for (long long i = (long long)bi * kRT + threadIdx.x; i < n4; i += stride) {
     const float4 x = __ldg(a4 + i), y = __ldg(b4 + i);
     pair_term<MODE>(acc, x.x, y.x);
@@ -159,7 +161,7 @@ static int aligned16(const void* a, const void* b) {
 template <int MODE>
 static void launch_sum(const float* a, const float* b, long long n, double* partial, double* out,
                        cudaStream_t st) {
-  const int nb = nblocks(n);
+  const int nb = reduce_blocks(n);
   if (t_plain_fp32_reduce) {
     launch_k(k_partial_fp32<MODE>, dim3(nb), dim3(kRT), 0, st, a, b, n, partial);
     launch_k(k_final_sum_fp32, dim3(1), dim3(kRT), 0, st, partial, nb, out);
@@ -184,6 +186,7 @@ __device__ __forceinline__ float partial_maxabs(const float* __restrict__ a, lon
                                                 int bi) {
   float m = 0.f;
   const long long stride = (long long)nblk * kRT;
+#pragma unroll 4
   for (long long i = (long long)bi * kRT + threadIdx.x; i < n; i += stride) {
     const float x = fabsf(__ldg(a + i));
     m = (x > m || x != x) ? x : m;  // NaN propagates
@@ -199,9 +202,17 @@ __device__ __forceinline__ float partial_maxabs(const float* __restrict__ a, lon
   return r;
 }
 
+// the larger of two values, NaN if either is NaN
+__device__ __forceinline__ float max_nan(float a, float b) { return (b > a || b != b) ? b : a; }
+
+// the largest of nb partials by one warp (lane-strided, then across lanes;
+// the maximum does not depend on the order), valid in every lane
 __device__ __forceinline__ double final_maxabs(const float* __restrict__ partial, int nb) {
+  const int lane = threadIdx.x & 31;
   float r = 0.f;
-  for (int i = 0; i < nb; ++i) r = (partial[i] > r || partial[i] != partial[i]) ? partial[i] : r;
+  for (int i = lane; i < nb; i += 32) r = max_nan(r, partial[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = max_nan(r, __shfl_xor_sync(0xffffffffu, r, o));
   return (double)r;
 }
 
@@ -214,11 +225,12 @@ k_maxabs_partial(const float* __restrict__ a, long long n, float* __restrict__ p
 
 __global__ void k_maxabs_final(const float* __restrict__ partial, int nb, double* out) {
   pdl_enter();
-  if (threadIdx.x == 0) *out = final_maxabs(partial, nb);
+  const double r = final_maxabs(partial, nb);
+  if (threadIdx.x == 0) *out = r;
 }
 
 void launch_maxabs(const float* a, long long n, float* partial, double* out, cudaStream_t st) {
-  const int nb = nblocks(n);
+  const int nb = reduce_blocks(n);
   launch_k(k_maxabs_partial, dim3(nb), dim3(kRT), 0, st, a, n, partial);
   launch_k(k_maxabs_final, dim3(1), dim3(32), 0, st, partial, nb, out);
 }
@@ -369,12 +381,14 @@ k_maxabs_partial_b(const BDesc* __restrict__ desc, SegView S, const int* __restr
   if (threadIdx.x == 0) partial[S.first[sb.x] + sb.y] = r;
 }
 
+// one warp per problem
 __global__ void k_maxabs_final_b(int nprob, SegView S, const int* __restrict__ mask,
                                  const float* __restrict__ partial, double* __restrict__ out) {
   pdl_enter();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   if (p >= nprob || !mask[p]) return;
-  out[p] = final_maxabs(partial + S.first[p], S.nb[p]);
+  const double r = final_maxabs(partial + S.first[p], S.nb[p]);
+  if ((threadIdx.x & 31) == 0) out[p] = r;
 }
 
 template <int MODE>
@@ -397,8 +411,7 @@ void launch_sumsq_diff_b(const BDesc* desc, const SegView& S, int nprob, const i
 void launch_maxabs_b(const BDesc* desc, const SegView& S, int nprob, const int* mask, BRef a,
                      int L, float* partial, double* out, cudaStream_t st) {
   launch_k(k_maxabs_partial_b, dim3(S.nblocks), dim3(kRT), 0, st, desc, S, mask, a, L, partial);
-  launch_k(k_maxabs_final_b, dim3((nprob + 127) / 128), dim3(128), 0, st, nprob, S, mask, partial,
-           out);
+  launch_k(k_maxabs_final_b, dim3((nprob + 3) / 4), dim3(128), 0, st, nprob, S, mask, partial, out);
 }
 
 // problem of element e of an array of F fields per problem

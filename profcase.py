@@ -9,6 +9,12 @@ once and times a PCG solve with it; `--pcg` times a PCG solve with the
 spectral preconditioner P_REG (graph replay of the matvec alone). Prints
 the wall time per matvec. The workload holds a few hundred MB
 on the device at 1024^2.
+
+    python profcase.py --lockstep 1
+
+instead solves the bench's batch64 workload (64 problems of uneven size,
+the analytic pair, nt = 4, beta = 1e-2, P_REG) with one lockstep batch that
+many times and prints the wall time per batch (about 1.5 GB on the device).
 """
 
 import argparse
@@ -41,9 +47,13 @@ def main():
                     help="cubic Lagrange on P_2L's coarse grid (the bench's chosen form)")
     ap.add_argument("--unet", type=int, default=0,
                     help="instead: this many warm-start network training steps (batch 8, 256^2)")
+    ap.add_argument("--lockstep", type=int, default=0,
+                    help="instead: this many lockstep solves of the 64-problem batch workload")
     a = ap.parse_args()
     if a.unet:
         return unet_case(a.unet)
+    if a.lockstep:
+        return lockstep_case(a.lockstep)
     import numpy as np
     import torch
 
@@ -118,6 +128,46 @@ def main():
         print(f"n={n} PCG {info['pcg_iters']} iterations {1e3 * dk / max(1, info['pcg_iters']):.3f} "
               f"ms per iteration (graph replay of matvec and P_2L)")
     R.close()
+
+
+def lockstep_case(solves):
+    """The batch of bench.py's batch64 workload (grids drawn with seed 200
+    from BATCH_SIZES^2, m_R = m_T transported by v* on the GPU) solved by a
+    lockstep batch with P_REG from v = 0 to ||g||rel 1e-2."""
+    import numpy as np
+    import torch
+    import bench
+    from paper_1604_02153_gb300 import inputs, regnk
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(200)
+    sizes = [int(x) for x in rng.choice(bench.BATCH_SIZES, size=bench.BATCH_B)]
+    f = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32).ravel(), device=dev)
+    cache, mR, mT = {}, [], []
+    for n in sizes:
+        if n not in cache:
+            m_T, vstar = inputs.sinusoid_pair(n)
+            R = regnk.Registration(n, n, bench.BATCH_NT, bench.BATCH_BETA, step_tile=0)
+            m1 = torch.empty(n * n, device=dev)
+            R.transport(f(vstar), f(m_T), m1)
+            torch.cuda.synchronize()
+            R.close()
+            cache[n] = (m1.clone(), f(m_T))
+        mR.append(cache[n][0])
+        mT.append(cache[n][1])
+    L = regnk.Lockstep([(n, n) for n in sizes], bench.BATCH_NT, [bench.BATCH_BETA] * len(sizes))
+    L.set_images(mR, mT)
+    vs = [torch.zeros(2 * n * n, device=dev) for n in sizes]
+    for _ in range(solves):
+        for v in vs:
+            v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos = L.solve(vs, bench.GTOL)
+        torch.cuda.synchronize()
+        print(f"lockstep batch of {len(sizes)}: {1e3 * (time.perf_counter() - t0):.2f} ms, "
+              f"{sum(i['matvecs'] for i in infos)} matvecs, "
+              f"max PCG iterations {max(i['pcg_iters'] for i in infos)}", flush=True)
+    L.close()
 
 
 def unet_case(steps):
