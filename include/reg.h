@@ -517,6 +517,16 @@ reg_status reg_unet_gradients(reg_unet* net, int B, const int* idx, const float*
  * the loss before the step */
 reg_status reg_unet_train_step(reg_unet* net, int B, const int* idx, const float* m_R,
                                const float* m_T, const float* v_target, float lr, double* loss);
+/* Tensor-core path of the forward and data-gradient 3x3 convolutions (no
+ * counterpart in the paper): 0 (default) BF16 mma.sync implicit GEMMs in
+ * registers; 1 the fifth-generation tensor cores (tcgen05.mma, BF16 operands
+ * staged in shared memory, the FP32 accumulator in tensor memory). Both
+ * accumulate in FP32; the results differ by accumulation order only. With
+ * path 1, forward, gradients and train_step synchronise once more to read
+ * the kernels' error flag: a convolution whose bounded wait for its MMAs ran
+ * out returns REG_ETIMEOUT (network still usable). The weight-gradient
+ * GEMMs stay on mma.sync. REG_EINVAL for other values. */
+reg_status reg_unet_set_conv_path(reg_unet* net, int path);
 const char* reg_unet_last_error(const reg_unet* net);
 
 /* Warm start for the context's images: restricts m_R, m_T spectrally to the

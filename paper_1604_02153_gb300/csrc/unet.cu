@@ -93,6 +93,7 @@ struct ConvArgs {
   int Kp;
   const float* bias;       // [Cout] or null
   int Cout;                // stored output channels (even)
+  int Cout_rows;           // weight rows (output channels rounded up to 64)
   void* out;
   int out_ld;
   const bf16* mask;        // optional: zero the output where mask <= 0
@@ -214,6 +215,288 @@ __global__ void __launch_bounds__(kCT) k_conv(ConvArgs a) {
         }
       }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on the fifth-generation tensor cores: tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulator in tensor memory) on a 128 x 64
+// or 128 x 128 output tile, one elected thread issuing the MMAs, the operands staged in
+// shared memory by all 128 threads (cp.async gathers of the periodic 3x3
+// taps), three stages of 64 K entries so that two chunks load while the
+// tensor core works on the current one; completion is tracked by an mbarrier per stage
+// that tcgen05.commit arrives on. The accumulator (128 lanes x 64 FP32
+// columns of tensor memory) is read back with tcgen05.ld by the four warps,
+// one pixel row per thread, for the same epilogue as k_conv.
+//
+// Shared-memory operand layout (no swizzle, K-major): 8 rows x 16 bytes
+// "core matrices", 128 bytes each, ordered [row group][K group] with the K
+// groups of a row group adjacent: the K-adjacent core matrices are 128 bytes
+// apart (leading byte offset), the row-adjacent ones 8 * 128 = 1024 bytes
+// apart (stride byte offset). One MMA (K = 16) reads two K-adjacent core
+// matrices per row group.
+//
+// Every wait is bounded: a stage whose MMAs have not completed after
+// kTcSpin polls sets *err, the block stops issuing, frees its tensor memory
+// and returns.
+constexpr int kTcSpin = 1 << 22;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor (no swizzle; version 1 at bits 46-47)
+__device__ __forceinline__ unsigned long long umma_sdesc(const void* smem, unsigned lbo,
+                                                         unsigned sbo) {
+  const unsigned a = smem_u32(smem);
+  return (unsigned long long)((a >> 4) & 0x3FFFu) |
+         ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28
+constexpr unsigned umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) |
+         ((unsigned)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned phase) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the given phase of an mbarrier
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned phase) {
+  for (int i = 0; i < kTcSpin; ++i)
+    if (mbar_try_wait(b, phase)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D (tensor memory) (+)= A (smem) B (smem)^T, issued by one thread
+__device__ __forceinline__ void tc_mma(unsigned d_tmem, unsigned long long a, unsigned long long b,
+                                       unsigned idesc, int accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// the mbarrier's arrival once every MMA this thread issued before has completed
+__device__ __forceinline__ void tc_commit(unsigned long long* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(b))
+               : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float (&v)[16]) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Tile of the tcgen05 convolution: 128 pixels x TBN output channels (64 or
+// 128), K in chunks of kTcBK = 64 (four MMAs of K = 16), kTcStages chunks in
+// flight.
+constexpr int kTcBK = 64;
+constexpr int kTcStages = 3;
+template <int TBN>
+constexpr size_t tc_smem() { return sizeof(bf16) * kTcStages * (BM + TBN) * kTcBK; }
+
+// element (row, 8-element K group kv) of a [rows][kTcBK] operand tile in the
+// core-matrix layout above
+__device__ __forceinline__ int tc_off(int row, int kv) {
+  return ((row >> 3) * (kTcBK / 8) + kv) * 64 + (row & 7) * 8;
+}
+
+constexpr int kTcThreads = 256;   // two threads per pixel row of the tile
+
+template <bool OUT_F32, int TBN>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(ConvArgs a, int* __restrict__ err) {
+  pdl_enter();
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  bf16* As = reinterpret_cast<bf16*>(tc_smem_raw);               // kTcStages x BM x kTcBK
+  bf16* Bs = As + kTcStages * BM * kTcBK;                         // kTcStages x TBN x kTcBK
+  __shared__ __align__(8) unsigned long long bar[kTcStages];
+  __shared__ unsigned tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int p0 = blockIdx.x * BM, n0 = blockIdx.y * TBN;
+  const int HW = a.H * a.W;
+  // loads: pixel row tid % BM, K groups (tid / BM) * 4 .. + 3 of a chunk;
+  // epilogue: warp w reads lane quadrant w % 4, column half w / 4
+  const int prow = tid % BM, khalf = tid / BM;
+  const int p = p0 + prow;
+  const bool pvalid = p < a.P;
+  int img = 0, h = 0, w = 0;
+  if (pvalid) {
+    img = p / HW;
+    const int r = p - img * HW;
+    h = r / a.W;
+    w = r - h * a.W;
+  }
+  const int nk = (a.Kp + kTcBK - 1) / kTcBK;
+  const int rows = a.Cout_rows;   // weight rows present (a multiple of 64)
+  if (warp == 0) {   // tensor memory for the accumulator (one warp allocates and frees)
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"((unsigned)TBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < kTcStages; ++i) mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = tmem_slot;
+
+  // K entries at or beyond Kp, and weight rows beyond the stored ones, are
+  // zero-filled (cp.async with no source bytes)
+  auto load_stage = [&](int kc, int s) {
+    bf16* as = As + s * BM * kTcBK;
+    bf16* bs = Bs + s * TBN * kTcBK;
+#pragma unroll
+    for (int vv = 0; vv < kTcBK / 16; ++vv) {
+      const int v = khalf * (kTcBK / 16) + vv;
+      const int k = kc * kTcBK + v * 8;
+      const int t = k / a.Cin, ci = k - t * a.Cin;
+      const bf16* src = a.in;
+      int bytes = 0;
+      if (pvalid && t < 9 && k < a.Kp) {
+        src = a.in + tap_pixel(img, h, w, t, a.H, a.W) * a.in_ld + ci;
+        bytes = 16;
+      }
+      cp_async16(&as[tc_off(prow, v)], src, bytes);
+    }
+#pragma unroll
+    for (int i = 0; i < TBN * (kTcBK / 8) / kTcThreads; ++i) {
+      const int q = tid + i * kTcThreads;
+      const int row = q / (kTcBK / 8), v = q % (kTcBK / 8);
+      const int k = kc * kTcBK + v * 8;
+      const bool okb = (n0 + row) < rows && k < a.Kp;
+      cp_async16(&bs[tc_off(row, v)], okb ? a.w + (long long)(n0 + row) * a.Kp + k : a.w,
+                 okb ? 16 : 0);
+    }
+  };
+
+  constexpr unsigned idesc = umma_idesc_bf16(BM, TBN);
+  constexpr unsigned kSbo = (kTcBK / 8) * 128;   // bytes between row-adjacent core matrices
+  // stage s holds chunk kc = s (mod kTcStages); the j-th MMA batch reading
+  // stage s completes phase j of bar[s]
+#pragma unroll
+  for (int st = 0; st < kTcStages - 1; ++st) {
+    if (st < nk) load_stage(st, st);
+    cp_async_commit();
+  }
+  bool ok = true;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc % kTcStages;
+    cp_async_wait<kTcStages - 2>();   // chunk kc has landed
+    // the generic-proxy writes of this stage become visible to the tensor core
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int ks = 0; ks < kTcBK / 16; ++ks) {
+        const unsigned long long ad = umma_sdesc(As + s * BM * kTcBK + ks * 2 * 64, 128, kSbo);
+        const unsigned long long bd = umma_sdesc(Bs + s * TBN * kTcBK + ks * 2 * 64, 128, kSbo);
+        tc_mma(tmem, ad, bd, idesc, (kc > 0 || ks > 0) ? 1 : 0);
+      }
+      tc_commit(&bar[s]);
+    }
+    // refill the stage the previous chunk's MMAs read
+    const int kn = kc + kTcStages - 1;
+    if (kn < nk) {
+      if (kc >= 1) {
+        const int sp = (kc - 1) % kTcStages;
+        ok = mbar_wait(&bar[sp], (unsigned)(((kc - 1) / kTcStages) & 1));
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+      }
+      load_stage(kn, kn % kTcStages);
+    }
+    cp_async_commit();
+  }
+  cp_async_wait<0>();
+  // MMAs complete in issue order: the last batch's arrival covers them all
+  if (ok) ok = mbar_wait(&bar[(nk - 1) % kTcStages], (unsigned)(((nk - 1) / kTcStages) & 1));
+  tc_fence_after();
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    // epilogue: warp w holds pixels p0 + 32 (w % 4) .. + 31 (one per lane) and
+    // columns n0 + (w / 4) TBN / 2 .. + TBN / 2 - 1
+    const int pp = p0 + (warp & 3) * 32 + (tid & 31);
+    const int cbase = (warp >> 2) * (TBN / 2);
+#pragma unroll 1
+    for (int c = cbase; c < cbase + TBN / 2; c += 16) {
+      float x[16];
+      tc_ld16(tmem + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)c, x);
+      if (pp < a.P) {
+#pragma unroll
+        for (int e = 0; e < 16; e += 2) {
+          const int col = n0 + c + e;
+          if (col >= a.Cout) continue;
+          float x0 = x[e], x1 = x[e + 1];
+          if (a.bias) {
+            x0 += a.bias[col];
+            x1 += a.bias[col + 1];
+          }
+          if (a.relu) {
+            x0 = fmaxf(x0, 0.f);
+            x1 = fmaxf(x1, 0.f);
+          }
+          if (a.mask) {
+            const bf162 m = *reinterpret_cast<const bf162*>(a.mask + (long long)pp * a.mask_ld + col);
+            x0 = __bfloat162float(m.x) > 0.f ? x0 : 0.f;
+            x1 = __bfloat162float(m.y) > 0.f ? x1 : 0.f;
+          }
+          if (OUT_F32) {
+            *reinterpret_cast<float2*>(static_cast<float*>(a.out) + (long long)pp * a.out_ld + col) =
+                make_float2(x0, x1);
+          } else {
+            *reinterpret_cast<bf162*>(static_cast<bf16*>(a.out) + (long long)pp * a.out_ld + col) =
+                __floats2bfloat162_rn(x0, x1);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((unsigned)TBN)
+                 : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -590,6 +873,8 @@ struct reg_unet {
   Act g_pred, g_d0b, g_d0a, g_cat0, g_e0a, g_x1, g_d1b, g_d1a, g_cat1, g_e1a, g_x2, g_d2b, g_d2a,
       g_cat2, g_e2a, g_x3, g_e3b, g_e3a;
   double* loss = nullptr;
+  int conv_path = 0;       // 0: mma.sync convolutions, 1: tcgen05 (tensor memory)
+  int* derr = nullptr;     // set by a tcgen05 convolution whose bounded wait ran out
 };
 
 namespace {
@@ -652,11 +937,42 @@ void conv(reg_unet* u, const Layer& l, const Act& in, int cin, long long P, int 
   a.mask = mask ? mask->p : nullptr;
   a.mask_ld = mask ? mask->ld : 0;
   const int rows = data_grad ? l.cinp : l.coutp;
+  a.Cout_rows = rows;
   const dim3 grid(nblk(P, BM), rows / BN);
+  if (u->conv_path == 1) {   // 128-channel tiles where there are 128 or more rows
+    if (rows >= 128) {
+      const dim3 g2(nblk(P, BM), (rows + 127) / 128);
+      if (out_f32)
+        launch_k(k_conv_tc<true, 128>, g2, dim3(kTcThreads), tc_smem<128>(), u->st, a, u->derr);
+      else
+        launch_k(k_conv_tc<false, 128>, g2, dim3(kTcThreads), tc_smem<128>(), u->st, a, u->derr);
+    } else {
+      if (out_f32)
+        launch_k(k_conv_tc<true, 64>, grid, dim3(kTcThreads), tc_smem<64>(), u->st, a, u->derr);
+      else
+        launch_k(k_conv_tc<false, 64>, grid, dim3(kTcThreads), tc_smem<64>(), u->st, a, u->derr);
+    }
+    return;
+  }
   if (out_f32)
     launch_k(k_conv<true>, grid, dim3(kCT), 0, u->st, a);
   else
     launch_k(k_conv<false>, grid, dim3(kCT), 0, u->st, a);
+}
+
+// With the tcgen05 convolutions: synchronises and reports a convolution
+// whose bounded wait ran out (REG_ETIMEOUT; the flag is cleared).
+void check_tc(reg_unet* u) {
+  if (u->conv_path != 1) return;
+  int e = 0;
+  ucheck(u, cudaMemcpyAsync(&e, u->derr, sizeof(int), cudaMemcpyDeviceToHost, u->st), "error flag");
+  ucheck(u, cudaStreamSynchronize(u->st), "error flag");
+  if (e) {
+    cudaMemsetAsync(u->derr, 0, sizeof(int), u->st);
+    cudaStreamSynchronize(u->st);
+    u->err = "a tcgen05 convolution gave up waiting for its MMAs";
+    throw UnetError{REG_ETIMEOUT};
+  }
 }
 
 void wgrad(reg_unet* u, const Layer& l, const Act& dz, const Act& in, long long P, int S) {
@@ -951,6 +1267,17 @@ reg_status reg_unet_create(int size, int batch_max, reg_unet** out) {
     u->g_e3b = act(u, P3, 256);
     u->g_e3a = act(u, P3, 256);
     u->loss = ualloc<double>(u, 1);
+    u->derr = ualloc<int>(u, 1);
+    // the tcgen05 convolutions' operand stages (72 KB and 96 KB of dynamic
+    // shared memory)
+    ucheck(u, cudaFuncSetAttribute(k_conv_tc<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem<64>()), "shared memory limit");
+    ucheck(u, cudaFuncSetAttribute(k_conv_tc<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem<64>()), "shared memory limit");
+    ucheck(u, cudaFuncSetAttribute(k_conv_tc<true, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem<128>()), "shared memory limit");
+    ucheck(u, cudaFuncSetAttribute(k_conv_tc<false, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)tc_smem<128>()), "shared memory limit");
     ucheck(u, cudaDeviceSynchronize(), "allocate");
   });
   if (s != REG_OK) {
@@ -1037,6 +1364,7 @@ reg_status reg_unet_forward(reg_unet* u, int B, const int* idx, const float* mR,
     const long long P0 = (long long)B * u->size * u->size;
     launch_k(k_unpack, dim3(nblk(P0, 256)), dim3(256), 0, u->st, (const float*)u->pred, B,
              u->size * u->size, v);
+    check_tc(u);
   });
 }
 
@@ -1047,6 +1375,7 @@ reg_status reg_unet_gradients(reg_unet* u, int B, const int* idx, const float* m
   return uguard(u, [&] {
     forward(u, B, idx, mR, mT);
     backward(u, B, idx, v_target);
+    check_tc(u);
     if (loss) {
       double s = 0.0;
       ucheck(u, cudaMemcpyAsync(&s, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->st), "loss");
@@ -1064,6 +1393,7 @@ reg_status reg_unet_train_step(reg_unet* u, int B, const int* idx, const float* 
   return uguard(u, [&] {
     forward(u, B, idx, mR, mT);
     backward(u, B, idx, v_target);
+    check_tc(u);
     adam(u, lr);
     if (loss) {
       double s = 0.0;
@@ -1072,6 +1402,12 @@ reg_status reg_unet_train_step(reg_unet* u, int B, const int* idx, const float* 
       *loss = s / (2.0 * (double)B * u->size * u->size);
     }
   });
+}
+
+reg_status reg_unet_set_conv_path(reg_unet* u, int path) {
+  if (!u || (path != 0 && path != 1)) return REG_EINVAL;
+  u->conv_path = path;
+  return REG_OK;
 }
 
 const char* reg_unet_last_error(const reg_unet* u) { return u ? u->err.c_str() : "null network"; }

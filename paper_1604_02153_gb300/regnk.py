@@ -135,6 +135,7 @@ _SIGNATURES = {
     "reg_unet_forward": [_P, _I, _P, _P, _P, _P],
     "reg_unet_gradients": [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D)],
     "reg_unet_train_step": [_P, _I, _P, _P, _P, _P, ctypes.c_float, ctypes.POINTER(_D)],
+    "reg_unet_set_conv_path": [_P, _I],
     "reg_unet_last_error": [_P],
     "reg_warm_start": [_P, _P, _P, ctypes.POINTER(_I)],
 }
@@ -552,6 +553,10 @@ class UNet:
         a = np.empty(self.param_count(), dtype=np.float32)
         self._call("reg_unet_get_params", a.ctypes.data_as(ctypes.c_void_p))
         return a
+
+    def set_conv_path(self, path):
+        """0: mma.sync convolutions; 1: tcgen05 convolutions (tensor memory)."""
+        self._call("reg_unet_set_conv_path", int(path))
 
     def forward(self, B, m_R, m_T, v, idx=None):
         self._call("reg_unet_forward", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),

@@ -47,11 +47,14 @@ def main():
                     help="cubic Lagrange on P_2L's coarse grid (the bench's chosen form)")
     ap.add_argument("--unet", type=int, default=0,
                     help="instead: this many warm-start network training steps (batch 8, 256^2)")
+    ap.add_argument("--conv-path", type=int, default=0,
+                    help="with --unet: 0 mma.sync convolutions, 1 tcgen05 convolutions")
+    ap.add_argument("--batch", type=int, default=8, help="with --unet: pairs per step")
     ap.add_argument("--lockstep", type=int, default=0,
                     help="instead: this many lockstep solves of the 64-problem batch workload")
     a = ap.parse_args()
     if a.unet:
-        return unet_case(a.unet)
+        return unet_case(a.unet, a.conv_path, a.batch)
     if a.lockstep:
         return lockstep_case(a.lockstep)
     import numpy as np
@@ -170,13 +173,14 @@ def lockstep_case(solves):
     L.close()
 
 
-def unet_case(steps):
+def unet_case(steps, conv_path=0, B=8):
     """Forward passes and training steps of the warm-start network on a batch
-    of 8 random 256^2 pairs (He-normal weights); prints the time per step."""
+    of B random 256^2 pairs (He-normal weights); prints the time per step."""
     import torch
     from paper_1604_02153_gb300 import inputs, regnk, warmstart
-    S, B = warmstart.S, 8
+    S = warmstart.S
     net = regnk.UNet(S, B)
+    net.set_conv_path(conv_path)
     net.set_params(inputs.he_normal(warmstart.SHAPES, seed=1))
     g = torch.Generator(device="cuda").manual_seed(0)
     mR = torch.rand(B * S * S, device="cuda", generator=g)
@@ -190,7 +194,7 @@ def unet_case(steps):
         net.train_step(B, mR, mT, vt, 1e-4)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    print(f"U-Net S={S} B={B}: {1e3 * dt:.3f} ms per training step (wall)")
+    print(f"U-Net S={S} B={B} conv path {conv_path}: {1e3 * dt:.3f} ms per training step (wall)")
     net.close()
 
 

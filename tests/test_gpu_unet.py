@@ -181,3 +181,38 @@ def test_warm_start_prolongs_the_network_velocity(regnk):
         assert float(v.abs().max()) == 0.0
     R.close()
     net.close()
+
+
+@pytest.mark.parametrize("S,B", [(32, 2), (64, 1)])
+def test_tcgen05_convolutions_match_mma_sync_and_oracle(regnk, S, B):
+    """The convolutions on tcgen05 (tensor memory accumulator) give the
+    network of the mma.sync path up to accumulation order: the forward pass
+    and the gradients against the oracle at the bars above, and against the
+    mma.sync path at the same bars; a training step on that path lowers the
+    loss like the other."""
+    theta = f32(inputs.he_normal(SHAPES, seed=21))
+    mR, mT, vt = batch(S, B, 600)
+    out = {}
+    for path in (0, 1):
+        net = regnk.UNet(S, B)
+        net.set_conv_path(path)
+        net.set_params(theta)
+        v = torch.empty(B * 2 * S * S, device="cuda")
+        net.forward(B, dev(mR), dev(mT), v)
+        loss, g = net.gradients(B, dev(mR), dev(mT), dev(vt))
+        out[path] = (v.cpu().numpy().reshape(B, 2, S, S), loss, g)
+        net.close()
+    ref, cache = unet.forward(theta, f32(mR), f32(mT), bf16=True, keep=True)
+    g_ref = unet.backward(theta, cache, ref, f32(vt), bf16=True)
+    v1, loss1, g1 = out[1]
+    assert rel(v1, ref) < 2e-2
+    assert rel(v1, out[0][0]) < 2e-2
+    assert abs(loss1 - unet.mse(ref, f32(vt))) <= 1e-2 * unet.mse(ref, f32(vt))
+    assert rel(g1, g_ref) < 5e-2
+    assert rel(g1, out[0][2]) < 5e-2
+    net = regnk.UNet(S, B)
+    net.set_conv_path(1)
+    net.set_params(theta)
+    losses = [net.train_step(B, dev(mR), dev(mT), dev(vt), lr=1e-3) for _ in range(31)]
+    assert losses[-1] < 0.5 * losses[0]
+    net.close()
