@@ -44,11 +44,17 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
 // with P N <= 2048 (at most 16 KB of shared memory per block) and P = 1
 // from N = 512 on, so that a 512^2 grid gives 256 blocks per field and pass
 // and 1024^2 over 500 (fewer, larger blocks measured slower at both sizes).
+// Elements per thread in the load and store phases of the FFT kernels. The
+// radix-8 passes have P N / 8 butterflies, so with 4 half of the threads wait
+// during them; 8 (every thread busy, half the threads) measured slower
+// (1024^2 operator 38.8 against 36.6 us: spills in the column pass).
+constexpr int kFftPer = 4;
+
 template <int L, int T>
 struct FftCfg {
   static constexpr int N = (1 << L) * (T ? 3 : 1);
   static constexpr int P = N >= 512 ? 1 : (N >= 256 ? 4 : (N >= 128 ? 8 : 16));
-  static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
+  static constexpr int NT = (P * N / kFftPer) < 256 ? P * N / kFftPer : 256;
 };
 
 // Lines per block and threads of the row passes (k_rows_r2c, k_rows_c2r): P
@@ -60,7 +66,7 @@ struct RowCfg {
   // two line pairs per block from N = 1024: each spectral line then receives
   // 32 contiguous bytes (a whole sector) per block (grad at 1024^2: 38 -> 34 us)
   static constexpr int P = N >= 1024 ? 2 : FftCfg<L, T>::P;
-  static constexpr int NT = (P * N / 4) < 256 ? P * N / 4 : 256;
+  static constexpr int NT = (P * N / kFftPer) < 256 ? P * N / kFftPer : 256;
 };
 
 // 8-point DFT in registers: two 4-point DFTs of the even and odd inputs,
