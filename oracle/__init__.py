@@ -31,4 +31,4 @@ Parity status of each function is given in its docstring; every function is
 pinned by a CPU test unless it says "parity unpinned".
 """
 
-from . import spectral, interp, transport, problem, krylov, solver  # noqa: F401
+from . import spectral, interp, transport, problem, krylov, solver, d3  # noqa: F401

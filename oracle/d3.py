@@ -1,0 +1,255 @@
+"""The registration problem on 3D periodic grids (FP64 oracle, d = 3).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+The paper's formulation is written for d = 2 or 3 (§2, §3); its experiments
+are 2D and it names 3D as the next step. This module restates, for d = 3,
+what spectral.py, interp.py, transport.py and problem.py compute for d = 2:
+
+* grid (§3.2): the 3-torus of side 2 pi, n_i nodes per axis, h_i = 2 pi / n_i;
+  arrays u[k, j, i] (axis 0 is x_3, axis 2 the fastest, x_1), vector fields
+  v[c, k, j, i] with c = 0, 1, 2 for x_1, x_2, x_3;
+* pseudospectral gradient and divergence (Nyquist modes zeroed), the
+  regularisation operator A with symbol |k|^(2p) (eq. diffopregv) and its
+  powers with the zero weight replaced by one (eq. reg-precond);
+* periodic tricubic interpolation (§3.5): the tensor product of the 1D cubic
+  weights over the 4 x 4 x 4 stencil, B-spline weights on the coefficients
+  of the spline interpolant (the samples divided by the B-spline sampling
+  symbol per axis) or Lagrange weights on the samples;
+* RK2 characteristics and the semi-Lagrangian state, adjoint, incremental
+  state and (Gauss-Newton) incremental adjoint steps of §3.3.2, the same
+  Heun and trapezoidal updates as in 2D with three velocity components;
+* J (eq. varopt:objective), the reduced gradient g = beta A v + int lambda
+  grad m dt (eq. control-elim) and the Gauss-Newton Hessian matvec
+  H v~ = beta A v~ + int lambda~ grad m dt (eq. hessian-matvec, lambda terms
+  dropped), compressible (K = I), trapezoidal rule in time.
+
+Pinned in tests/test_oracle_3d.py: spectral operators exact on trigonometric
+polynomials, integral shifts exact, nodal interpolation, reduction to the 2D
+oracle on fields constant along x_3 with v_3 = 0, the gradient against central
+finite differences of J, and the Hessian's symmetry and agreement with finite
+differences of the gradient at zero residual.
+"""
+
+import numpy as np
+
+from . import interp as interp2
+from .spectral import wavenumbers
+
+
+# -- spectral ------------------------------------------------------------------
+def _k_grids(n1, n2, n3, zero_nyquist):
+    k = []
+    for n in (n1, n2, n3):
+        kk = wavenumbers(n).copy()
+        if zero_nyquist:
+            kk[n // 2] = 0.0
+        k.append(kk)
+    K3, K2, K1 = np.meshgrid(k[2], k[1], k[0], indexing="ij")   # shapes (n3, n2, n1)
+    return K1, K2, K3
+
+
+def _shape(u):
+    n3, n2, n1 = u.shape[-3:]
+    return n1, n2, n3
+
+
+def fftn(u):
+    return np.fft.fftn(u)
+
+
+def ifftn_real(uh):
+    return np.real(np.fft.ifftn(uh))
+
+
+def grad(u):
+    """Spectral gradient (i k_1, i k_2, i k_3) u^, shape (3, n3, n2, n1)."""
+    K = _k_grids(*_shape(u), zero_nyquist=True)
+    uh = fftn(u)
+    return np.stack([ifftn_real(1j * Kc * uh) for Kc in K])
+
+
+def div(v):
+    """Spectral divergence of a 3-component field (Nyquist zeroed)."""
+    K = _k_grids(*_shape(v), zero_nyquist=True)
+    return ifftn_real(sum(1j * K[c] * fftn(v[c]) for c in range(3)))
+
+
+def reg_symbol(n1, n2, n3, reg_norm):
+    """|k|^(2p) of A = -Lap, Lap^2, -Lap^3 (H1, H2, H3; eq. diffopregv)."""
+    p = {"H1": 1, "H2": 2, "H3": 3}[reg_norm]
+    K1, K2, K3 = _k_grids(n1, n2, n3, zero_nyquist=False)
+    return (K1 * K1 + K2 * K2 + K3 * K3) ** p
+
+
+def reg_power(v, beta, reg_norm, s):
+    """(beta A)^s per component; for s != 1 the zero weight becomes one."""
+    g = beta * reg_symbol(*_shape(v), reg_norm)
+    if s != 1:
+        g = np.where(g == 0.0, 1.0, g) ** s
+    return np.stack([ifftn_real(g * fftn(v[c])) for c in range(v.shape[0])])
+
+
+def apply_reg(v, beta, reg_norm):
+    return reg_power(v, beta, reg_norm, 1)
+
+
+def spline_prefilter(u):
+    """Coefficients of the periodic tricubic B-spline interpolant of u: the
+    DFT divided by the sampling symbol (2 + cos(2 pi k / n)) / 3 per axis."""
+    n1, n2, n3 = _shape(u)
+    s = [(2.0 + np.cos(2.0 * np.pi * wavenumbers(n) / n)) / 3.0 for n in (n1, n2, n3)]
+    sym = s[2][:, None, None] * s[1][None, :, None] * s[0][None, None, :]
+    return ifftn_real(fftn(u) / sym)
+
+
+# -- interpolation ---------------------------------------------------------------
+def coefficients(u, kind):
+    if kind == "spline":
+        return spline_prefilter(u)
+    if kind == "lagrange":
+        return np.array(u, dtype=np.float64, copy=True)
+    raise ValueError(kind)
+
+
+def evaluate(c, p1, p2, p3, kind):
+    """The tricubic interpolant with coefficients c at index-space points."""
+    n1, n2, n3 = _shape(c)
+    wfun = interp2.bspline3_weights if kind == "spline" else interp2.lagrange3_weights
+    f = [np.floor(p) for p in (p1, p2, p3)]
+    w = [wfun(p - fp) for p, fp in zip((p1, p2, p3), f)]
+    i0 = [fp.astype(np.int64) for fp in f]
+    out = np.zeros(np.shape(p1), dtype=np.float64)
+    for cz in range(4):
+        kk = np.mod(i0[2] + (cz - 1), n3)
+        for b in range(4):
+            jj = np.mod(i0[1] + (b - 1), n2)
+            for a in range(4):
+                ii = np.mod(i0[0] + (a - 1), n1)
+                out += c[kk, jj, ii] * w[0][a] * w[1][b] * w[2][cz]
+    return out
+
+
+def node_coordinates(n1, n2, n3):
+    K, J, I = np.meshgrid(np.arange(n3, dtype=np.float64), np.arange(n2, dtype=np.float64),
+                          np.arange(n1, dtype=np.float64), indexing="ij")
+    return I, J, K
+
+
+def interp(u, p1, p2, p3, kind):
+    return evaluate(coefficients(u, kind), p1, p2, p3, kind)
+
+
+# -- transport -------------------------------------------------------------------
+def characteristic(v, nt, kind, backward):
+    """Departure displacement in index units (Heun, §3.3.2), 3 arrays."""
+    n1, n2, n3 = _shape(v)
+    h = [2.0 * np.pi / n for n in (n1, n2, n3)]
+    ht = 1.0 / nt
+    s = 1.0 if backward else -1.0
+    X = node_coordinates(n1, n2, n3)
+    p = [X[c] + s * ht * v[c] / h[c] for c in range(3)]
+    vs = [interp(v[c], *p, kind) for c in range(3)]
+    return tuple(s * 0.5 * ht * (v[c] + vs[c]) / h[c] for c in range(3))
+
+
+def at_departure(u, disp, kind):
+    X = node_coordinates(*_shape(u))
+    return interp(u, X[0] + disp[0], X[1] + disp[1], X[2] + disp[2], kind)
+
+
+def state_step(m_prev, dX, kind):
+    return at_departure(m_prev, dX, kind)
+
+
+def adjoint_step(lam_next, dY, delta, delta_bar, ht, kind):
+    lb = at_departure(lam_next, dY, kind)
+    lstar = lb + ht * lb * delta_bar
+    return lb + 0.5 * ht * (lb * delta_bar + lstar * delta)
+
+
+def incstate_step(mt_prev, dX, vt_dep, gm_prev_dep, vt, gm_cur, ht, kind):
+    mb = at_departure(mt_prev, dX, kind)
+    f_dep = -sum(vt_dep[c] * gm_prev_dep[c] for c in range(3))
+    f_arr = -sum(vt[c] * gm_cur[c] for c in range(3))
+    return mb + 0.5 * ht * (f_dep + f_arr)
+
+
+def trapezoid_weights(nt):
+    w = np.ones(nt + 1)
+    w[0] = 0.5
+    w[-1] = 0.5
+    return w
+
+
+# -- the problem -----------------------------------------------------------------
+class Problem3:
+    """One compressible registration problem on an (n3, n2, n1) grid."""
+
+    def __init__(self, m_R, m_T, nt, beta, reg_norm="H1", kind="spline"):
+        self.m_R = np.asarray(m_R, dtype=np.float64)
+        self.m_T = np.asarray(m_T, dtype=np.float64)
+        self.n1, self.n2, self.n3 = _shape(self.m_R)
+        self.nt = int(nt)
+        self.ht = 1.0 / self.nt
+        self.beta = float(beta)
+        self.reg_norm = reg_norm
+        self.kind = kind
+        self.hh = np.prod([2.0 * np.pi / n for n in (self.n1, self.n2, self.n3)])
+        self.w = trapezoid_weights(self.nt)
+
+    def inner(self, a, b):
+        """<a, b>_h = h_1 h_2 h_3 sum(a b) (midpoint rule)."""
+        return self.hh * float(np.sum(a * b))
+
+    def state_solve(self, v):
+        self.v = np.array(v, dtype=np.float64, copy=True)
+        self.dX = characteristic(self.v, self.nt, self.kind, backward=False)
+        m = [self.m_T]
+        for _ in range(self.nt):
+            m.append(state_step(m[-1], self.dX, self.kind))
+        self.m = m
+        self.gm = [grad(mj) for mj in m]
+        self.dY = characteristic(self.v, self.nt, self.kind, backward=True)
+        self.delta = div(self.v)
+        self.delta_bar = at_departure(self.delta, self.dY, self.kind)
+        return m[-1]
+
+    def objective(self, v):
+        self.state_solve(v)
+        r = self.m[-1] - self.m_R
+        return 0.5 * self.inner(r, r) + 0.5 * self.inner(self.v, apply_reg(self.v, self.beta,
+                                                                          self.reg_norm))
+
+    def gradient(self):
+        """g = beta A v + int_0^1 lambda grad m dt at the last state solve."""
+        nt, ht = self.nt, self.ht
+        lam = [None] * (nt + 1)
+        lam[nt] = self.m_R - self.m[nt]
+        for j in range(nt - 1, -1, -1):
+            lam[j] = adjoint_step(lam[j + 1], self.dY, self.delta, self.delta_bar, ht, self.kind)
+        b = np.zeros((3,) + self.m_R.shape)
+        for j in range(nt + 1):
+            b += ht * self.w[j] * lam[j] * self.gm[j]
+        self.lam = lam
+        return apply_reg(self.v, self.beta, self.reg_norm) + b
+
+    def objective_gradient(self, v):
+        J = self.objective(v)
+        return J, self.gradient()
+
+    def hessian_matvec(self, vt):
+        """Gauss-Newton H v~ at the velocity of the last state solve."""
+        nt, ht = self.nt, self.ht
+        vt = np.asarray(vt, dtype=np.float64)
+        vt_dep = [at_departure(vt[c], self.dX, self.kind) for c in range(3)]
+        mt = np.zeros(self.m_R.shape)
+        for j in range(1, nt + 1):
+            G = [at_departure(self.gm[j - 1][c], self.dX, self.kind) for c in range(3)]
+            mt = incstate_step(mt, self.dX, vt_dep, G, vt, self.gm[j], ht, self.kind)
+        lt = -mt
+        b = ht * self.w[nt] * lt * self.gm[nt]
+        for j in range(nt - 1, -1, -1):
+            lt = adjoint_step(lt, self.dY, self.delta, self.delta_bar, ht, self.kind)
+            b = b + ht * self.w[j] * lt * self.gm[j]
+        return apply_reg(vt, self.beta, self.reg_norm) + b

@@ -104,6 +104,38 @@ def random_velocity(n1, n2=None, seed=0, kmax=4, vmax=0.2):
     return v * (vmax / vn)
 
 
+def _cosine_series3(n1, n2, n3, kmax, rng):
+    """The 3D analogue of _cosine_series: |k|^-2 cos(k . x + phi_k) summed
+    over the modes 0 < |k| <= kmax of a half space (k3 > 0, or k3 = 0 and
+    the 2D half plane), shape (n3, n2, n1)."""
+    C = np.zeros((n3, n2, n1), dtype=complex)
+    for k3 in range(0, kmax + 1):
+        for k2 in range(-kmax, kmax + 1):
+            for k1 in range(-kmax, kmax + 1):
+                if k3 == 0 and (k2 < 0 or (k2 == 0 and k1 <= 0)):
+                    continue
+                r2 = k1 * k1 + k2 * k2 + k3 * k3
+                if 0 < r2 <= kmax * kmax:
+                    phi = rng.uniform(0.0, 2.0 * np.pi)
+                    C[k3 % n3, k2 % n2, k1 % n1] += np.exp(1j * phi) / float(r2)
+    return np.real(np.fft.ifftn(C)) * (n1 * n2 * n3)
+
+
+def random_field3(n1, n2, n3, seed=0, kmax=4):
+    """Band-limited random field on an n1 x n2 x n3 grid rescaled to [0, 1]."""
+    rng = np.random.default_rng(seed)
+    return rescale01(_cosine_series3(n1, n2, n3, kmax, rng))
+
+
+def random_velocity3(n1, n2, n3, seed=0, kmax=3, vmax=0.2):
+    """Smooth random 3-component velocity, max |v(x)|_2 = vmax, shape
+    (3, n3, n2, n1)."""
+    rng = np.random.default_rng(seed)
+    v = np.stack([_cosine_series3(n1, n2, n3, kmax, rng) for _ in range(3)])
+    vn = float(np.max(np.sqrt(np.sum(v * v, axis=0))))
+    return v * (vmax / vn)
+
+
 def gaussian_blur(u, sigma_px):
     """Periodic Gaussian blur with standard deviation sigma_px grid points."""
     n2, n1 = u.shape

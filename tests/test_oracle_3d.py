@@ -1,0 +1,118 @@
+"""Pins of the 3D oracle (oracle/d3.py) against what the method fixes.
+
+* spectral gradient and divergence exact on a trigonometric polynomial; the
+  regularisation operator's symbol on a single mode;
+* interpolation: integral displacements are exact shifts, zero displacement
+  returns the samples (spline and Lagrange);
+* reduction to 2D: fields constant along x_3 with v_3 = 0 give the 2D
+  oracle's state, gradient and Gauss-Newton matvec (the 2D oracle is pinned
+  on its own) and J times the x_3 extent 2 pi;
+* the reduced gradient against central finite differences of J, the gap
+  shrinking with the grid;
+* the Gauss-Newton matvec symmetric up to the adjoint error, positive, and
+  equal to the derivative of the gradient at zero residual.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import d3
+from oracle.problem import Problem
+from paper_1604_02153_gb300 import inputs
+
+
+def grid3(n1, n2, n3):
+    K, J, I = np.meshgrid(*(np.arange(n) * 2 * np.pi / n for n in (n3, n2, n1)), indexing="ij")
+    return I, J, K
+
+
+def test_spectral_operators_on_trig_polynomials():
+    n1, n2, n3 = 16, 12, 8
+    x1, x2, x3 = grid3(n1, n2, n3)
+    u = np.sin(x1) * np.cos(2 * x2) * np.sin(3 * x3) + np.cos(2 * x1 + x3)
+    g = d3.grad(u)
+    e1 = np.cos(x1) * np.cos(2 * x2) * np.sin(3 * x3) - 2 * np.sin(2 * x1 + x3)
+    e2 = -2 * np.sin(x1) * np.sin(2 * x2) * np.sin(3 * x3)
+    e3 = 3 * np.sin(x1) * np.cos(2 * x2) * np.cos(3 * x3) - np.sin(2 * x1 + x3)
+    for a, b in zip(g, (e1, e2, e3)):
+        assert np.max(np.abs(a - b)) < 1e-12
+    v = np.stack([np.sin(x2), np.cos(x3) * np.sin(x1), np.sin(2 * x3 + x1)])
+    assert np.max(np.abs(d3.div(v) - (np.cos(x3) * 0 + 2 * np.cos(2 * x3 + x1)))) < 1e-12
+    w = np.stack([np.cos(2 * x1 - x2 + 3 * x3)] * 3)
+    for p, reg in ((1, "H1"), (2, "H2")):
+        Aw = d3.apply_reg(w, 0.5, reg)
+        assert np.max(np.abs(Aw - 0.5 * 14 ** p * w)) < 1e-9
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+def test_interpolation_shifts_and_nodes(kind):
+    n1, n2, n3 = 16, 8, 12
+    u = inputs.random_field3(n1, n2, n3, seed=3, kmax=4)
+    shape = u.shape
+    got = d3.at_departure(u, (np.full(shape, 2.0), np.full(shape, -1.0), np.full(shape, 3.0)), kind)
+    assert np.max(np.abs(got - np.roll(u, (-3, 1, -2), axis=(0, 1, 2)))) < 1e-12
+    z = np.zeros(shape)
+    assert np.max(np.abs(d3.at_departure(u, (z, z, z), kind) - u)) < 1e-12
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+def test_reduces_to_the_2d_problem(kind):
+    n, n3, nt, beta = 16, 4, 4, 1e-2
+    m_T = inputs.random_field(n, seed=1, kmax=4)
+    m_R = inputs.random_field(n, seed=2, kmax=4)
+    v2 = inputs.random_velocity(n, seed=3, vmax=0.3)
+    u2 = inputs.random_velocity(n, seed=4, vmax=1.0)
+    tile = lambda a: np.repeat(a[None], n3, axis=0)
+    v3 = np.stack([tile(v2[0]), tile(v2[1]), np.zeros((n3, n, n))])
+    u3 = np.stack([tile(u2[0]), tile(u2[1]), np.zeros((n3, n, n))])
+    P2 = Problem(m_R, m_T, nt, beta, kind=kind)
+    P3 = d3.Problem3(tile(m_R), tile(m_T), nt, beta, kind=kind)
+    J2, g2 = P2.objective_gradient(v2)
+    J3, g3 = P3.objective_gradient(v3)
+    assert abs(J3 - 2 * np.pi * J2) < 1e-12 * abs(J3)
+    for c in range(2):
+        assert np.max(np.abs(g3[c] - tile(g2[c]))) < 1e-12 * np.max(np.abs(g2))
+    assert np.max(np.abs(g3[2])) < 1e-12 * np.max(np.abs(g2))
+    H2 = P2.hessian_matvec(u2)
+    H3 = P3.hessian_matvec(u3)
+    for c in range(2):
+        assert np.max(np.abs(H3[c] - tile(H2[c]))) < 1e-12 * np.max(np.abs(H2))
+    assert np.max(np.abs(H3[2])) < 1e-12 * np.max(np.abs(H2))
+
+
+def test_gradient_against_finite_differences():
+    gaps = []
+    for n in (12, 24):
+        m_T = inputs.random_field3(n, n, n, seed=1, kmax=2)
+        m_R = inputs.random_field3(n, n, n, seed=2, kmax=2)
+        v = inputs.random_velocity3(n, n, n, seed=3, kmax=2, vmax=0.05)
+        dv = inputs.random_velocity3(n, n, n, seed=4, kmax=2, vmax=1.0)
+        P = d3.Problem3(m_R, m_T, 8, 1e-2)
+        _, g = P.objective_gradient(v)
+        d = P.inner(g, dv)
+        eps = 1e-4
+        fd = (P.objective(v + eps * dv) - P.objective(v - eps * dv)) / (2 * eps)
+        gaps.append(abs(fd - d) / abs(d))
+    assert gaps[-1] < 1e-4 and gaps[1] < gaps[0] / 4, gaps
+
+
+def test_gauss_newton_matvec_symmetric_positive_and_derivative_at_zero_residual():
+    n, nt = 16, 4
+    m_T = inputs.random_field3(n, n, n, seed=5, kmax=2)
+    v = inputs.random_velocity3(n, n, n, seed=6, kmax=2, vmax=0.2)
+    m_R = d3.Problem3(np.zeros((n, n, n)), m_T, nt, 1e-2).state_solve(v)
+    P = d3.Problem3(m_R, m_T, nt, 1e-2)
+    P.state_solve(v)
+    a = inputs.random_velocity3(n, n, n, seed=7, kmax=2, vmax=1.0)
+    b = inputs.random_velocity3(n, n, n, seed=8, kmax=2, vmax=1.0)
+    Ha, Hb = P.hessian_matvec(a), P.hessian_matvec(b)
+    ab, ba = P.inner(Ha, b), P.inner(a, Hb)
+    assert abs(ab - ba) < 1e-3 * abs(ab)
+    assert P.inner(Ha, a) > 0
+    eps = 1e-4
+    P.state_solve(v + eps * a)
+    gp = P.gradient()
+    P.state_solve(v - eps * a)
+    gm = P.gradient()
+    fd = (gp - gm) / (2 * eps)
+    assert np.linalg.norm(fd - Ha) / np.linalg.norm(Ha) < 2e-3
