@@ -11,7 +11,7 @@ what spectral.py, interp.py, transport.py and problem.py compute for d = 2:
   v[c, k, j, i] with c = 0, 1, 2 for x_1, x_2, x_3;
 * pseudospectral gradient and divergence (Nyquist modes zeroed), the
   regularisation operator A with symbol |k|^(2p) (eq. diffopregv) and its
-  powers with the zero weight replaced by one (eq. reg-precond);
+  powers with the zero entry of that symbol replaced by one (eq. reg-precond);
 * periodic tricubic interpolation (§3.5): the tensor product of the 1D cubic
   weights over the 4 x 4 x 4 stencil, B-spline weights on the coefficients
   of the spline interpolant (the samples divided by the B-spline sampling
@@ -22,18 +22,23 @@ what spectral.py, interp.py, transport.py and problem.py compute for d = 2:
 * J (eq. varopt:objective), the reduced gradient g = beta A v + int lambda
   grad m dt (eq. control-elim) and the Gauss-Newton Hessian matvec
   H v~ = beta A v~ + int lambda~ grad m dt (eq. hessian-matvec, lambda terms
-  dropped), compressible (K = I), trapezoidal rule in time.
+  dropped), compressible (K = I), trapezoidal rule in time;
+* the inexact Newton-Krylov solve of §3.4.1 with PCG and the spectral
+  preconditioner P_REG = (beta A)^-1 (eq. reg-precond), the steps of
+  solver.Solver.solve.
 
 Pinned in tests/test_oracle_3d.py: spectral operators exact on trigonometric
 polynomials, integral shifts exact, nodal interpolation, reduction to the 2D
-oracle on fields constant along x_3 with v_3 = 0, the gradient against central
-finite differences of J, and the Hessian's symmetry and agreement with finite
-differences of the gradient at zero residual.
+oracle on fields constant along x_3 with v_3 = 0 (J, g, H v~ and the whole
+solve), the gradient against central finite differences of J, and the
+Hessian's symmetry and agreement with finite differences of the gradient at
+zero residual.
 """
 
 import numpy as np
 
 from . import interp as interp2
+from . import krylov
 from .spectral import wavenumbers
 
 
@@ -83,10 +88,13 @@ def reg_symbol(n1, n2, n3, reg_norm):
 
 
 def reg_power(v, beta, reg_norm, s):
-    """(beta A)^s per component; for s != 1 the zero weight becomes one."""
-    g = beta * reg_symbol(*_shape(v), reg_norm)
+    """(beta A)^s per component. For s != 1 the zero entry of A's symbol (at
+    k = 0) is replaced by one before the power (eq. reg-precond), so the mean
+    of each component is scaled by beta^s."""
+    gam = reg_symbol(*_shape(v), reg_norm)
     if s != 1:
-        g = np.where(g == 0.0, 1.0, g) ** s
+        gam = np.where(gam == 0, 1, gam)
+    g = (beta * gam.astype(np.float64)) ** s
     return np.stack([ifftn_real(g * fftn(v[c])) for c in range(v.shape[0])])
 
 
@@ -253,3 +261,46 @@ class Problem3:
             lt = adjoint_step(lt, self.dY, self.delta, self.delta_bar, ht, self.kind)
             b = b + ht * self.w[j] * lt * self.gm[j]
         return apply_reg(vt, self.beta, self.reg_norm) + b
+
+    def solve(self, v0, gtol, max_newton=50, max_pcg=100, max_backtracks=10, c1=1e-4, gabs=1e-5):
+        """Inexact Gauss-Newton-Krylov with Armijo backtracking (§3.4.1):
+        stop when ||g||_inf <= gtol ||g(0)||_inf; forcing term
+        min(0.5, ||g||_2 / ||g(0)||_2); PCG with P_REG. Returns (v, info)."""
+        z = np.zeros((3,) + self.m_R.shape)
+        _, g_ref = self.objective_gradient(z)
+        gref_inf = float(np.max(np.abs(g_ref)))
+        gref_2 = float(np.sqrt(np.sum(g_ref * g_ref)))
+        v = np.array(v0, dtype=np.float64, copy=True)
+        J, g = self.objective_gradient(v)
+        info = {"J0": J, "newton_iters": 0, "pcg_iters": 0, "matvecs": 0,
+                "line_search_fail": False}
+        rel = 1.0
+        for k in range(max_newton + 1):
+            ginf = float(np.max(np.abs(g)))
+            rel = ginf / gref_inf
+            if rel <= gtol or ginf <= gabs or k == max_newton:
+                break
+            eta = min(0.5, float(np.sqrt(np.sum(g * g))) / gref_2)
+            vt, kinfo = krylov.pcg(self.hessian_matvec, -g,
+                                   lambda r: reg_power(r, self.beta, self.reg_norm, -1), eta, max_pcg)
+            info["pcg_iters"] += kinfo["iters"]
+            info["matvecs"] += kinfo["matvecs"]
+            slope = self.inner(g, vt)
+            alpha, accepted = 1.0, False
+            for _ in range(max_backtracks + 1):
+                Jt = self.objective(v + alpha * vt)
+                if Jt <= J + c1 * alpha * slope:
+                    accepted = True
+                    break
+                alpha *= 0.5
+            if not accepted:
+                info["line_search_fail"] = True
+                self.state_solve(v)
+                break
+            v = v + alpha * vt
+            J = Jt
+            g = self.gradient()
+            info["newton_iters"] += 1
+        info["J"] = J
+        info["gnorm_rel"] = rel
+        return v, info

@@ -1,12 +1,14 @@
 """Pins of the 3D oracle (oracle/d3.py) against what the method fixes.
 
 * spectral gradient and divergence exact on a trigonometric polynomial; the
-  regularisation operator's symbol on a single mode;
+  regularisation operator's symbol on a single mode and its powers on a
+  mode plus a constant (the k = 0 weight of eq. reg-precond);
 * interpolation: integral displacements are exact shifts, zero displacement
   returns the samples (spline and Lagrange);
 * reduction to 2D: fields constant along x_3 with v_3 = 0 give the 2D
-  oracle's state, gradient and Gauss-Newton matvec (the 2D oracle is pinned
-  on its own) and J times the x_3 extent 2 pi;
+  oracle's state, gradient, Gauss-Newton matvec and powers of beta A on a
+  field with a nonzero mean (the 2D oracle is pinned on its own) and J times
+  the x_3 extent 2 pi;
 * the reduced gradient against central finite differences of J, the gap
   shrinking with the grid;
 * the Gauss-Newton matvec symmetric up to the adjoint error, positive, and
@@ -42,6 +44,12 @@ def test_spectral_operators_on_trig_polynomials():
     for p, reg in ((1, "H1"), (2, "H2")):
         Aw = d3.apply_reg(w, 0.5, reg)
         assert np.max(np.abs(Aw - 0.5 * 14 ** p * w)) < 1e-9
+    # powers of beta A (eq. reg-precond): the zero entry of A's symbol becomes
+    # one, so a constant c maps to beta^s c while |k|^2 = 14 maps to (14 beta)^s
+    beta, c0 = 0.02, 0.7
+    for s in (-1.0, -0.5, 0.5):
+        P = d3.reg_power(w + c0, beta, "H1", s)
+        assert np.max(np.abs(P - ((14 * beta) ** s * w + beta ** s * c0))) < 1e-9, s
 
 
 @pytest.mark.parametrize("kind", ["spline", "lagrange"])
@@ -78,6 +86,15 @@ def test_reduces_to_the_2d_problem(kind):
     for c in range(2):
         assert np.max(np.abs(H3[c] - tile(H2[c]))) < 1e-12 * np.max(np.abs(H2))
     assert np.max(np.abs(H3[2])) < 1e-12 * np.max(np.abs(H2))
+    # the powers of beta A on a field with a nonzero mean (the k = 0 weight)
+    from oracle import spectral
+    w2 = u2 + np.array([0.3, -0.2])[:, None, None]
+    w3 = np.stack([tile(w2[0]), tile(w2[1]), np.full((n3, n, n), 0.1)])
+    for s in (-1.0, -0.5):
+        P2s = spectral.reg_power(w2, beta, "H1", s)
+        P3s = d3.reg_power(w3, beta, "H1", s)
+        for c in range(2):
+            assert np.max(np.abs(P3s[c] - tile(P2s[c]))) < 1e-12 * np.max(np.abs(P2s))
 
 
 def test_gradient_against_finite_differences():
@@ -116,3 +133,25 @@ def test_gauss_newton_matvec_symmetric_positive_and_derivative_at_zero_residual(
     gm = P.gradient()
     fd = (gp - gm) / (2 * eps)
     assert np.linalg.norm(fd - Ha) / np.linalg.norm(Ha) < 2e-3
+
+
+def test_solve_reduces_to_the_2d_solve():
+    """The Newton-Krylov solve with P_REG on a problem constant along x_3
+    (v_3 = 0 throughout) takes the 2D oracle's iterations: every ratio the
+    method forms (step lengths, forcing terms, the Armijo test) is the 2D one,
+    the inner products carry the same factor 2 pi."""
+    from oracle.solver import Solver
+    n, n3, nt, beta, gtol = 16, 4, 4, 1e-2, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    v2, info2 = Solver(Problem(m_R, m_T, nt, beta), precond="REG").solve(np.zeros((2, n, n)), gtol)
+    tile = lambda a: np.repeat(a[None], n3, axis=0)
+    P3 = d3.Problem3(tile(m_R), tile(m_T), nt, beta)
+    v3, info3 = P3.solve(np.zeros((3, n3, n, n)), gtol)
+    assert info3["newton_iters"] == info2["newton_iters"] and info3["matvecs"] == info2["matvecs"]
+    assert info3["gnorm_rel"] <= gtol
+    # (the 3D and 2D FFTs round differently; PCG carries that into the
+    # iterates at the 1e-10 level)
+    for c in range(2):
+        assert np.max(np.abs(v3[c] - tile(v2[c]))) < 1e-8 * np.max(np.abs(v2))
+    assert np.max(np.abs(v3[2])) < 1e-8 * np.max(np.abs(v2))
