@@ -408,6 +408,51 @@ reg_status reg_batch_hessian_matvec(reg_batch* batch, const float* const* v,
                                     const float* const* vt, float* const* Hvt);
 const char* reg_batch_last_error(const reg_batch* batch);
 
+/* ---- 3D grids ------------------------------------------------------------
+ * The registration problem on an n1 x n2 x n3 periodic grid (d = 3 in the
+ * formulation of §2-§3; the paper's experiments are 2D and name 3D as the
+ * next step): RK2 departure points, periodic tricubic interpolation (cubic
+ * B-spline with a separable recursive prefilter, or cubic Lagrange), the
+ * semi-Lagrangian state, adjoint, incremental state and Gauss-Newton
+ * incremental adjoint steps of §3.3.2, pseudospectral grad, div and
+ * (beta A)^s by 3D FFTs, J (eq. varopt:objective), the reduced gradient
+ * (eq. control-elim, K = I) and the GN Hessian matvec (eq. hessian-matvec).
+ * Fields are float32 with x_1 fastest, then x_2, then x_3; vector fields
+ * are their three components back to back (3 n1 n2 n3 floats); device
+ * pointers, 16-byte aligned, owned by the caller. n_i in {32, 64, 128, 256,
+ * 96, 192}. Options as reg_create with precond = REG_PC_REG (the spectral
+ * preconditioner; required), compressible, Gauss-Newton; anything else
+ * REG_EINVAL. Calls run on the stream of reg3_set_stream (default stream
+ * otherwise). reg3_create allocates (73 + 7 nt) n1 n2 n3 floats of device
+ * memory (6.8 GB at 256^3, nt = 4), freed by reg3_destroy.
+ * Errors: REG_EINVAL for a NULL or unaligned pointer or an unknown op,
+ * REG_ESTATE when reg3_set_images has not been called, REG_ENOMEM or
+ * REG_ECUDA from the CUDA runtime (the message in reg3_last_error); the
+ * solve returns REG_ENOTCONV, REG_ELINESEARCH or REG_ENONFINITE as
+ * reg_solve does, with v holding the last accepted iterate. */
+typedef struct reg3_ctx reg3_ctx;
+reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_options* opt,
+                       reg3_ctx** out);
+reg_status reg3_destroy(reg3_ctx* ctx);
+reg_status reg3_set_stream(reg3_ctx* ctx, void* cuda_stream);
+reg_status reg3_set_images(reg3_ctx* ctx, const float* m_R, const float* m_T);
+/* m1 = the state solve of eq. state-slm from m0 with velocity v (3 fields) */
+reg_status reg3_transport(reg3_ctx* ctx, const float* v, const float* m0, float* m1);
+/* REG_SPEC_GRAD (1 -> 3 fields), REG_SPEC_DIV (3 -> 1), REG_SPEC_REGPOW
+ * (3 -> 3, (beta A)^s; for s != 1 the zero entry of A's symbol is one, so
+ * the mean is scaled by beta^s, eq. reg-precond) on the 3D grid; other ops
+ * REG_EINVAL */
+reg_status reg3_spectral(reg3_ctx* ctx, int op, double s, const float* in, float* out);
+/* *J (host) and, if g is not NULL, the reduced gradient (3 fields) at v;
+ * synchronises */
+reg_status reg3_objective_gradient(reg3_ctx* ctx, const float* v, double* J, float* g);
+/* Hvt = H(v) vt, the Gauss-Newton matvec; synchronises */
+reg_status reg3_hessian_matvec(reg3_ctx* ctx, const float* v, const float* vt, float* Hvt);
+/* the inexact Newton-Krylov solve of reg_solve (§3.4.1) with PCG and P_REG;
+ * v is the initial guess and receives the result; info may be NULL */
+reg_status reg3_solve(reg3_ctx* ctx, float* v, double gtol, reg_info* info);
+const char* reg3_last_error(const reg3_ctx* ctx);
+
 /* ---- Lockstep batches: one launch per step over every problem ------------
  * B independent problems (any grids reg_create accepts, nt shared, beta[i]
  * per problem) held in one set of device arrays with a table of (n1, n2,

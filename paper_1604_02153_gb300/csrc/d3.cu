@@ -1,0 +1,809 @@
+// The registration hot path on 3D periodic grids (d = 3; the paper's
+// formulation is written for d = 2 or 3, §2-§3, and names 3D as its next
+// step). The same method as the 2D library for a compressible problem with
+// the spectral preconditioner: RK2 departure points, periodic tricubic
+// interpolation (B-spline prefilter by separable recursions, or cubic
+// Lagrange), the semi-Lagrangian state, adjoint, incremental state and
+// Gauss-Newton incremental adjoint steps (§3.3.2), pseudospectral grad, div
+// and (beta A)^s by 3D FFTs (a complex pass per axis, fft_axis), J, the
+// reduced gradient, the GN Hessian matvec and the inexact Newton-Krylov
+// solve with P_REG (§3.4).
+//
+// Layout: a scalar field is n1 n2 n3 float32 with x_1 fastest, then x_2,
+// then x_3 (u[(k n2 + j) n1 + i]); a vector field its three components back
+// to back. Displacements are stored in cell units.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "interp.cuh"
+#include "kernels.h"
+#include "reg.h"
+
+namespace regnk {
+namespace d3 {
+
+constexpr int kT = 256;   // threads per block of the pointwise kernels
+
+struct Dims {
+  int n1, n2, n3;
+  long long N;
+};
+
+__device__ __forceinline__ void split3(long long idx, const Dims& d, int& i, int& j, int& k) {
+  i = (int)(idx % d.n1);
+  const long long r = idx / d.n1;
+  j = (int)(r % d.n2);
+  k = (int)(r / d.n2);
+}
+
+// --------------------------------------------------------------------------
+// B-spline prefilter along one axis: each thread produces 8 consecutive
+// coefficients of one line from a chain of kL + 8 + kL samples (the
+// recursions of interp.cuh, start-up length kL), periodic wrap. Consecutive
+// threads take consecutive x_1 (axes 1 and 2) or consecutive segments of
+// one line (axis 0).
+__global__ void __launch_bounds__(kT)
+k3_prefilter_axis(const float* __restrict__ in, float* __restrict__ out, Dims d, int axis) {
+  pdl_enter();
+  const long long t = (long long)blockIdx.x * kT + threadIdx.x;
+  if (t >= d.N / 8) return;
+  const int na = axis == 0 ? d.n1 : (axis == 1 ? d.n2 : d.n3);
+  const int nseg = na / 8;
+  long long base, step;
+  int seg;
+  if (axis == 0) {
+    seg = (int)(t % nseg);
+    base = (t / nseg) * d.n1;
+    step = 1;
+  } else if (axis == 1) {
+    const int i = (int)(t % d.n1);
+    const long long r = t / d.n1;
+    seg = (int)(r % nseg);
+    const long long k = r / nseg;
+    base = k * d.n2 * d.n1 + i;
+    step = d.n1;
+  } else {
+    const int i = (int)(t % d.n1);
+    const long long r = t / d.n1;
+    seg = (int)(r % nseg);
+    const long long j = r / nseg;
+    base = j * d.n1 + i;
+    step = (long long)d.n1 * d.n2;
+  }
+  constexpr int kLen = 8 + 2 * kL;
+  float v[kLen];
+  const int j0 = seg * 8 - kL;
+#pragma unroll
+  for (int q = 0; q < kLen; ++q) {
+    int j = j0 + q;
+    j = j < 0 ? j + na : (j >= na ? j - na : j);
+    v[q] = __ldg(in + base + (long long)j * step);
+  }
+  bspline_recursions<kLen, 8>(v, [&](int o, float x) { out[base + (long long)(seg * 8 + o) * step] = x; });
+}
+
+// --------------------------------------------------------------------------
+// Tricubic interpolation at node (i, j, k) + (d1, d2, d3) cells: the tensor
+// product of the 1D cubic weights over the 4 x 4 x 4 periodic stencil.
+struct Stencil3 {
+  int ii[4];
+  long long jj[4], kk[4];
+  float w1[4], w2[4], w3[4];
+};
+
+__device__ __forceinline__ Stencil3 stencil3(int i, int j, int k, float d1, float d2, float d3,
+                                             const Dims& d, bool lagrange) {
+  Stencil3 S;
+  const float f1 = floorf(d1), f2 = floorf(d2), f3 = floorf(d3);
+  cubic_weights(d1 - f1, S.w1, lagrange);
+  cubic_weights(d2 - f2, S.w2, lagrange);
+  cubic_weights(d3 - f3, S.w3, lagrange);
+  const int i0 = wrap_index<false>(i + (int)f1 - 1, d.n1);
+  const int j0 = wrap_index<false>(j + (int)f2 - 1, d.n2);
+  const int k0 = wrap_index<false>(k + (int)f3 - 1, d.n3);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int ia = i0 + a, ja = j0 + a, ka = k0 + a;
+    S.ii[a] = ia < d.n1 ? ia : ia - d.n1;
+    S.jj[a] = (long long)(ja < d.n2 ? ja : ja - d.n2) * d.n1;
+    S.kk[a] = (long long)(ka < d.n3 ? ka : ka - d.n3) * d.n1 * d.n2;
+  }
+  return S;
+}
+
+__device__ __forceinline__ float apply3(const Stencil3& S, const float* __restrict__ c) {
+  float acc = 0.f;
+#pragma unroll
+  for (int cz = 0; cz < 4; ++cz) {
+    float accy = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float* row = c + S.kk[cz] + S.jj[b];
+      const float r = S.w1[0] * __ldg(row + S.ii[0]) + S.w1[1] * __ldg(row + S.ii[1]) +
+                      S.w1[2] * __ldg(row + S.ii[2]) + S.w1[3] * __ldg(row + S.ii[3]);
+      accy = fmaf(S.w2[b], r, accy);
+    }
+    acc = fmaf(S.w3[cz], accy, acc);
+  }
+  return acc;
+}
+
+// Departure points of both characteristics (Heun, §3.3.2), cell units:
+// X* = x - a, X_D = x - (a + s v(X*)) / 2 and Y* = x + a, Y_D = x + (a +
+// s v(Y*)) / 2 with a = s v, s = h_t n / (2 pi) per axis; cv holds the
+// interpolation coefficients of v (or v itself, Lagrange).
+__global__ void __launch_bounds__(kT)
+k3_departure(Dims d, float s1, float s2, float s3, const float* __restrict__ v,
+             const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
+             int lagrange) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const float a1 = s1 * __ldg(v + idx), a2 = s2 * __ldg(v + N + idx), a3 = s3 * __ldg(v + 2 * N + idx);
+  {
+    const Stencil3 S = stencil3(i, j, k, -a1, -a2, -a3, d, lagrange);
+    dX[idx] = -0.5f * (a1 + s1 * apply3(S, cv));
+    dX[N + idx] = -0.5f * (a2 + s2 * apply3(S, cv + N));
+    dX[2 * N + idx] = -0.5f * (a3 + s3 * apply3(S, cv + 2 * N));
+  }
+  {
+    const Stencil3 S = stencil3(i, j, k, a1, a2, a3, d, lagrange);
+    dY[idx] = 0.5f * (a1 + s1 * apply3(S, cv));
+    dY[N + idx] = 0.5f * (a2 + s2 * apply3(S, cv + N));
+    dY[2 * N + idx] = 0.5f * (a3 + s3 * apply3(S, cv + 2 * N));
+  }
+}
+
+// out_f = I[coef_f](x + disp), F fields N apart
+__global__ void __launch_bounds__(kT)
+k3_gather(Dims d, const float* __restrict__ coef, const float* __restrict__ disp,
+          float* __restrict__ out, int F, int lagrange) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const Stencil3 S = stencil3(i, j, k, __ldg(disp + idx), __ldg(disp + N + idx),
+                              __ldg(disp + 2 * N + idx), d, lagrange);
+  for (int f = 0; f < F; ++f) out[f * N + idx] = apply3(S, coef + f * N);
+}
+
+// lambda = sign (mR - m1) (mR may be NULL), b = coef_b lambda grad m
+__global__ void __launch_bounds__(kT)
+k3_adjoint_init(long long N, float coef_b, const float* __restrict__ mR,
+                const float* __restrict__ m1, const float* __restrict__ gm,
+                float* __restrict__ lam, float* __restrict__ b, float sign) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= N) return;
+  const float l = sign * ((mR ? __ldg(mR + idx) : 0.f) - __ldg(m1 + idx));
+  lam[idx] = l;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) b[c * N + idx] = coef_b * l * __ldg(gm + c * N + idx);
+}
+
+// One backward step of the (incremental) adjoint along Y_D (Heun) fused with
+// b += wb lambda_j grad m_j.
+__global__ void __launch_bounds__(kT)
+k3_adjoint_step(Dims d, float ht, float wb, const float* __restrict__ coef,
+                const float* __restrict__ dY, const float* __restrict__ delta,
+                const float* __restrict__ delta_bar, const float* __restrict__ gm,
+                float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const float db = __ldg(delta_bar + idx), dd = __ldg(delta + idx);
+  const Stencil3 S = stencil3(i, j, k, __ldg(dY + idx), __ldg(dY + N + idx),
+                              __ldg(dY + 2 * N + idx), d, lagrange);
+  const float lb = apply3(S, coef);
+  const float lstar = fmaf(ht * lb, db, lb);
+  const float l = lb + 0.5f * ht * (lb * db + lstar * dd);
+  lam_out[idx] = l;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) b[c * N + idx] = fmaf(wb * l, __ldg(gm + c * N + idx), b[c * N + idx]);
+}
+
+// One forward step of the incremental state (GN):
+//   m~_j = m~_{j-1}(X_D) - h_t/2 (v~(X_D) . grad m_{j-1}(X_D) + v~ . grad m_j);
+// first: m~_0 = 0 and v~(X_D) gathered from cvt (written to vtD).
+__global__ void __launch_bounds__(kT)
+k3_incstate_step(Dims d, float ht, const float* __restrict__ coef, const float* __restrict__ dX,
+                 const float* __restrict__ vt, float* __restrict__ vtD,
+                 const float* __restrict__ G, const float* __restrict__ gm,
+                 float* __restrict__ out, int first, const float* __restrict__ cvt,
+                 int lagrange) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const Stencil3 S = stencil3(i, j, k, __ldg(dX + idx), __ldg(dX + N + idx),
+                              __ldg(dX + 2 * N + idx), d, lagrange);
+  float m = first ? 0.f : apply3(S, coef);
+  float w[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (first) {
+      w[c] = apply3(S, cvt + c * N);
+      vtD[c * N + idx] = w[c];
+    } else {
+      w[c] = __ldg(vtD + c * N + idx);
+    }
+  }
+  float src = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    src += w[c] * __ldg(G + c * N + idx) + __ldg(vt + c * N + idx) * __ldg(gm + c * N + idx);
+  out[idx] = m - 0.5f * ht * src;
+}
+
+// --------------------------------------------------------------------------
+// Spectral multipliers (3D): real fields in and out through complex
+// buffers; wavenumbers in FFT order, the Nyquist mode zeroed for the odd
+// operators (grad, div); (beta |k|^2p)^s with the zero entry of |k|^2p set to
+// one for s != 1 (eq. reg-precond: the mean is scaled by beta^s).
+enum Op3 { OP3_GRAD = 0, OP3_DIV = 1, OP3_REGPOW = 2 };
+
+__global__ void __launch_bounds__(kT)
+k3_pack(const float* __restrict__ in, float2* __restrict__ z, long long n) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx < n) z[idx] = make_float2(__ldg(in + idx), 0.f);
+}
+
+__global__ void __launch_bounds__(kT)
+k3_unpack(const float2* __restrict__ z, float* __restrict__ out, const float* __restrict__ add,
+          long long n) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx < n) out[idx] = z[idx].x + (add ? __ldg(add + idx) : 0.f);
+}
+
+__device__ __forceinline__ float regpow3(float beta, int p, float s, float k2n) {
+  float g = k2n;
+  if (p == 2) g = k2n * k2n;
+  else if (p == 3) g = k2n * k2n * k2n;
+  if (s == 1.f) return beta * g;
+  if (g == 0.f) g = 1.f;
+  const float bg = beta * g;
+  if (s == -1.f) return 1.f / bg;
+  if (s == -0.5f) return 1.f / sqrtf(bg);
+  if (s == 0.5f) return sqrtf(bg);
+  return powf(bg, s);
+}
+
+// zout = op(zin) scaled by 1 / N (the normalisation of the inverse passes)
+__global__ void __launch_bounds__(kT)
+k3_multiply(Dims d, int op, int F, float beta, int p, float s, const float2* __restrict__ zin,
+            float2* __restrict__ zout) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const float scale = 1.f / (float)N;
+  const float k1 = (float)signed_k(i, d.n1), k2 = (float)signed_k(j, d.n2),
+              k3 = (float)signed_k(k, d.n3);
+  const float q1 = (2 * i == d.n1) ? 0.f : k1, q2 = (2 * j == d.n2) ? 0.f : k2,
+              q3 = (2 * k == d.n3) ? 0.f : k3;
+  if (op == OP3_GRAD) {
+    const float2 u = zin[idx];
+    const float q[3] = {q1, q2, q3};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)   // i q u
+      zout[c * N + idx] = make_float2(-q[c] * u.y * scale, q[c] * u.x * scale);
+  } else if (op == OP3_DIV) {
+    const float2 a = zin[idx], b = zin[N + idx], c = zin[2 * N + idx];
+    const float re = -(q1 * a.y + q2 * b.y + q3 * c.y), im = q1 * a.x + q2 * b.x + q3 * c.x;
+    zout[idx] = make_float2(re * scale, im * scale);
+  } else {
+    const float g = regpow3(beta, p, s, k1 * k1 + k2 * k2 + k3 * k3) * scale;
+    for (int c = 0; c < F; ++c) {
+      const float2 u = zin[c * N + idx];
+      zout[c * N + idx] = make_float2(g * u.x, g * u.y);
+    }
+  }
+}
+
+inline unsigned nb(long long n) { return (unsigned)((n + kT - 1) / kT); }
+
+}  // namespace d3
+}  // namespace regnk
+
+using namespace regnk;
+using namespace regnk::d3;
+
+struct reg3_ctx {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  reg_options opt;
+  Dims d{};
+  int nt = 0;
+  float ht = 0.f;
+  double beta = 0, hh = 0;
+  bool lagrange = false;
+  float s1 = 0, s2 = 0, s3 = 0;
+  float2 *tw1 = nullptr, *tw2 = nullptr, *tw3 = nullptr;
+  float *mR = nullptr, *mT = nullptr, *v = nullptr, *cv = nullptr, *dX = nullptr, *dY = nullptr,
+        *delta = nullptr, *delta_bar = nullptr, *m = nullptr, *gm = nullptr, *G = nullptr,
+        *coef = nullptr, *c3 = nullptr, *tA = nullptr, *tB = nullptr, *fA = nullptr,
+        *fB = nullptr, *vtD = nullptr, *b = nullptr, *Av = nullptr;
+  float *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr,
+        *vtrial = nullptr, *gcur = nullptr, *rhs = nullptr;
+  float2 *zA = nullptr, *zB = nullptr;
+  double* partial = nullptr;
+  float* partialf = nullptr;
+  double* dsc = nullptr;
+  double* hsc = nullptr;
+  bool have_images = false, have_v = false, have_G = false;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+struct D3Error {
+  reg_status s;
+};
+
+void fail(reg3_ctx* c, reg_status s, const std::string& msg) {
+  c->err = msg;
+  throw D3Error{s};
+}
+
+void check(reg3_ctx* c, cudaError_t e, const char* what) {
+  if (e != cudaSuccess)
+    fail(c, e == cudaErrorMemoryAllocation ? REG_ENOMEM : REG_ECUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void check_launch(reg3_ctx* c, const char* what) { check(c, cudaGetLastError(), what); }
+
+template <typename T>
+T* dalloc(reg3_ctx* c, size_t n) {
+  void* p = nullptr;
+  check(c, cudaMalloc(&p, n * sizeof(T) + 16), "cudaMalloc");
+  c->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+float2* twiddles(reg3_ctx* c, int n) {
+  std::vector<float2> h(n);
+  for (int k = 0; k < n; ++k) {
+    const double a = -2.0 * M_PI * (double)k / (double)n;
+    h[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  float2* d = dalloc<float2>(c, n);
+  check(c, cudaMemcpy(d, h.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "twiddles");
+  return d;
+}
+
+// the three axis passes of a 3D FFT of F complex arrays in z
+void fft3(reg3_ctx* c, float2* z, int F, bool inverse) {
+  const Dims& d = c->d;
+  fft_axis(z, d.N, F, d.n1, 1, inverse, c->tw1, c->st);
+  fft_axis(z, d.N, F, d.n2, d.n1, inverse, c->tw2, c->st);
+  fft_axis(z, d.N, F, d.n3, (long long)d.n1 * d.n2, inverse, c->tw3, c->st);
+}
+
+// out (Fout fields) = op(in (Fin fields)) [+ add]
+void spectral3(reg3_ctx* c, int op, double s, const float* in, int Fin, float* out, int Fout,
+               const float* add) {
+  const long long N = c->d.N;
+  launch_k(k3_pack, dim3(nb(Fin * N)), dim3(kT), 0, c->st, in, c->zA, Fin * N);
+  fft3(c, c->zA, Fin, false);
+  launch_k(k3_multiply, dim3(nb(N)), dim3(kT), 0, c->st, c->d, op, Fin, (float)c->beta,
+           c->opt.reg_norm, (float)s, (const float2*)c->zA, c->zB);
+  fft3(c, c->zB, Fout, true);
+  launch_k(k3_unpack, dim3(nb(Fout * N)), dim3(kT), 0, c->st, (const float2*)c->zB, out, add,
+           Fout * N);
+  check_launch(c, "spectral operator");
+}
+
+// interpolation coefficients of F consecutive fields (the samples themselves
+// for cubic Lagrange)
+const float* coefficients(reg3_ctx* c, const float* u, int F, float* dst) {
+  if (c->lagrange) return u;
+  const long long N = c->d.N;
+  for (int f = 0; f < F; ++f) {
+    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, u + f * N, c->tA, c->d, 0);
+    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, (const float*)c->tA, c->tB, c->d, 1);
+    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, (const float*)c->tB, dst + f * N, c->d, 2);
+  }
+  check_launch(c, "prefilter");
+  return dst;
+}
+
+void gather(reg3_ctx* c, const float* u, int F, const float* disp, float* out, float* cbuf) {
+  const float* cu = coefficients(c, u, F, cbuf);
+  launch_k(k3_gather, dim3(nb(c->d.N)), dim3(kT), 0, c->st, c->d, cu, disp, out, F, (int)c->lagrange);
+  check_launch(c, "gather");
+}
+
+// v, its characteristics, the state history m_0..m_nt, grad m_j, div v and
+// div v at Y_D (§3.3.2)
+void set_velocity(reg3_ctx* c, const float* v) {
+  const long long N = c->d.N;
+  const int nt = c->nt;
+  if (v != c->v)
+    check(c, cudaMemcpyAsync(c->v, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
+  const float* cv = coefficients(c, c->v, 3, c->cv);
+  launch_k(k3_departure, dim3(nb(N)), dim3(kT), 0, c->st, c->d, c->s1, c->s2, c->s3,
+           (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+  check(c, cudaMemcpyAsync(c->m, c->mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "m_T");
+  for (int j = 1; j <= nt; ++j) gather(c, c->m + (j - 1) * N, 1, c->dX, c->m + j * N, c->coef);
+  for (int j = 0; j <= nt; ++j) spectral3(c, OP3_GRAD, 0.0, c->m + j * N, 1, c->gm + 3 * j * N, 3, nullptr);
+  spectral3(c, OP3_DIV, 0.0, c->v, 3, c->delta, 1, nullptr);
+  gather(c, c->delta, 1, c->dY, c->delta_bar, c->coef);
+  c->have_v = true;
+  c->have_G = false;
+}
+
+void ensure_G(reg3_ctx* c) {
+  if (c->have_G) return;
+  const long long N = c->d.N;
+  for (int j = 1; j <= c->nt; ++j)
+    gather(c, c->gm + 3 * (j - 1) * N, 3, c->dX, c->G + 3 * (j - 1) * N, c->c3);
+  c->have_G = true;
+}
+
+double dot_sync(reg3_ctx* c, const float* a, const float* b, long long n) {
+  launch_dot(a, b, n, c->partial, c->dsc, c->st);
+  check(c, cudaMemcpyAsync(c->hsc, c->dsc, sizeof(double), cudaMemcpyDeviceToHost, c->st), "read");
+  check(c, cudaStreamSynchronize(c->st), "synchronize");
+  return c->hsc[0];
+}
+
+// J = 1/2 <m_1 - m_R, m_1 - m_R>_h + beta/2 <v, A v>_h; leaves beta A v in Av
+double objective(reg3_ctx* c) {
+  const long long N = c->d.N;
+  spectral3(c, OP3_REGPOW, 1.0, c->v, 3, c->Av, 3, nullptr);
+  launch_sumsq_diff(c->m + c->nt * N, c->mR, N, c->partial, c->dsc, c->st);
+  launch_dot(c->v, c->Av, 3 * N, c->partial, c->dsc + 1, c->st);
+  check(c, cudaMemcpyAsync(c->hsc, c->dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "read");
+  check(c, cudaStreamSynchronize(c->st), "synchronize");
+  return 0.5 * c->hh * c->hsc[0] + 0.5 * c->hh * c->hsc[1];
+}
+
+// g = beta A v + int_0^1 lambda grad m dt (eq. control-elim, K = I)
+void gradient(reg3_ctx* c, float* g) {
+  const long long N = c->d.N;
+  const int nt = c->nt;
+  const float ht = c->ht;
+  float* lam = c->fA;
+  float* lam2 = c->fB;
+  launch_k(k3_adjoint_init, dim3(nb(N)), dim3(kT), 0, c->st, N, 0.5f * ht, (const float*)c->mR,
+           (const float*)(c->m + nt * N), (const float*)(c->gm + 3 * nt * N), lam, c->b, 1.f);
+  for (int j = nt - 1; j >= 0; --j) {
+    const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    const float* cl = coefficients(c, lam, 1, c->coef);
+    launch_k(k3_adjoint_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, wb, cl,
+             (const float*)c->dY, (const float*)c->delta, (const float*)c->delta_bar,
+             (const float*)(c->gm + 3 * j * N), lam2, c->b, (int)c->lagrange);
+    std::swap(lam, lam2);
+  }
+  launch_lincomb(3 * N, 1.f, c->Av, 1.f, c->b, g, c->st);
+  check_launch(c, "gradient");
+}
+
+// Gauss-Newton H v~ = beta A v~ + int lambda~ grad m dt (eq. hessian-matvec)
+void hessian(reg3_ctx* c, const float* vt, float* out) {
+  const long long N = c->d.N;
+  const int nt = c->nt;
+  const float ht = c->ht;
+  ensure_G(c);
+  const float* cvt = coefficients(c, vt, 3, c->c3);
+  float* mt = c->fA;
+  float* mt2 = c->fB;
+  for (int j = 1; j <= nt; ++j) {
+    const float* cm = j == 1 ? nullptr : coefficients(c, mt, 1, c->coef);
+    launch_k(k3_incstate_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, cm,
+             (const float*)c->dX, vt, c->vtD, (const float*)(c->G + 3 * (j - 1) * N),
+             (const float*)(c->gm + 3 * j * N), mt2, (int)(j == 1), cvt, (int)c->lagrange);
+    std::swap(mt, mt2);
+  }
+  // lambda~_nt = -m~_nt and the first term of the time integral
+  launch_k(k3_adjoint_init, dim3(nb(N)), dim3(kT), 0, c->st, N, 0.5f * ht, (const float*)nullptr,
+           (const float*)mt, (const float*)(c->gm + 3 * nt * N), mt2, c->b, 1.f);
+  float* lt = mt2;
+  float* lt2 = mt;
+  for (int j = nt - 1; j >= 0; --j) {
+    const float wb = ht * (j == 0 ? 0.5f : 1.0f);
+    const float* cl = coefficients(c, lt, 1, c->coef);
+    launch_k(k3_adjoint_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, wb, cl,
+             (const float*)c->dY, (const float*)c->delta, (const float*)c->delta_bar,
+             (const float*)(c->gm + 3 * j * N), lt2, c->b, (int)c->lagrange);
+    std::swap(lt, lt2);
+  }
+  spectral3(c, OP3_REGPOW, 1.0, vt, 3, out, 3, c->b);
+  check_launch(c, "hessian");
+}
+
+bool size_ok3(int n) { return n % 32 == 0 && fft_axis_supported(n); }
+bool unaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
+reg_status guarded(reg3_ctx* c, const std::function<void()>& body) {
+  if (!c) return REG_EINVAL;
+  const int saved = t_programmatic_launch;
+  const int saved_prec = t_plain_fp32_reduce;
+  t_programmatic_launch = c->opt.programmatic_launch ? 1 : 0;
+  t_plain_fp32_reduce = 0;
+  reg_status s = REG_OK;
+  try {
+    body();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      c->err = std::string("CUDA: ") + cudaGetErrorString(e);
+      s = REG_ECUDA;
+    }
+  } catch (const D3Error& e) {
+    s = e.s;
+  }
+  t_programmatic_launch = saved;
+  t_plain_fp32_reduce = saved_prec;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_options* opt,
+                       reg3_ctx** out) {
+  if (!out) return REG_EINVAL;
+  *out = nullptr;
+  if (!size_ok3(n1) || !size_ok3(n2) || !size_ok3(n3) || nt < 1 || nt > 4096 || !(beta > 0.0))
+    return REG_EINVAL;
+  reg_options o;
+  if (opt) o = *opt; else reg_default_options(&o);
+  if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
+      o.precond != REG_PC_REG || o.hessian != REG_HESSIAN_GN || o.incompressible ||
+      o.beta_w != 0.0 || o.max_pcg < 1 || o.max_newton < 0 || o.max_backtracks < 0)
+    return REG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
+  reg3_ctx* c = new reg3_ctx();
+  c->device = dev;
+  c->opt = o;
+  c->d = Dims{n1, n2, n3, (long long)n1 * n2 * n3};
+  c->nt = nt;
+  c->ht = 1.0f / (float)nt;
+  c->beta = beta;
+  c->hh = (2.0 * M_PI / n1) * (2.0 * M_PI / n2) * (2.0 * M_PI / n3);
+  c->lagrange = (o.interp == REG_INTERP_LAGRANGE);
+  c->s1 = departure_scale(c->ht, n1);
+  c->s2 = departure_scale(c->ht, n2);
+  c->s3 = departure_scale(c->ht, n3);
+  const reg_status s = guarded(c, [&] {
+    const size_t N = (size_t)c->d.N;
+    c->tw1 = twiddles(c, n1);
+    c->tw2 = twiddles(c, n2);
+    c->tw3 = twiddles(c, n3);
+    float** scalar[] = {&c->mR, &c->mT, &c->delta, &c->delta_bar, &c->coef, &c->tA, &c->tB,
+                        &c->fA, &c->fB};
+    for (float** f : scalar) *f = dalloc<float>(c, N);
+    float** vec[] = {&c->v, &c->cv, &c->dX, &c->dY, &c->c3, &c->vtD, &c->b, &c->Av, &c->kx,
+                     &c->kr, &c->kz, &c->kp, &c->kq, &c->vtrial, &c->gcur, &c->rhs};
+    for (float** f : vec) *f = dalloc<float>(c, 3 * N);
+    c->m = dalloc<float>(c, (size_t)(nt + 1) * N);
+    c->gm = dalloc<float>(c, 3 * (size_t)(nt + 1) * N);
+    c->G = dalloc<float>(c, 3 * (size_t)nt * N);
+    c->zA = dalloc<float2>(c, 3 * N);
+    c->zB = dalloc<float2>(c, 3 * N);
+    c->partial = dalloc<double>(c, reduce_partials());
+    c->partialf = dalloc<float>(c, reduce_partials());
+    c->dsc = dalloc<double>(c, 4);
+    void* h = nullptr;
+    check(c, cudaMallocHost(&h, 4 * sizeof(double)), "cudaMallocHost");
+    c->hsc = static_cast<double*>(h);
+    check(c, cudaDeviceSynchronize(), "create");
+  });
+  if (s != REG_OK) {
+    reg3_destroy(c);
+    return s;
+  }
+  *out = c;
+  return REG_OK;
+}
+
+reg_status reg3_destroy(reg3_ctx* c) {
+  if (!c) return REG_OK;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->hsc) cudaFreeHost(c->hsc);
+  delete c;
+  return REG_OK;
+}
+
+reg_status reg3_set_stream(reg3_ctx* c, void* stream) {
+  if (!c) return REG_EINVAL;
+  c->st = static_cast<cudaStream_t>(stream);
+  return REG_OK;
+}
+
+reg_status reg3_set_images(reg3_ctx* c, const float* mR, const float* mT) {
+  if (!c || !mR || !mT || unaligned(mR) || unaligned(mT)) return REG_EINVAL;
+  return guarded(c, [&] {
+    const size_t n = (size_t)c->d.N * sizeof(float);
+    check(c, cudaMemcpyAsync(c->mR, mR, n, cudaMemcpyDeviceToDevice, c->st), "copy m_R");
+    check(c, cudaMemcpyAsync(c->mT, mT, n, cudaMemcpyDeviceToDevice, c->st), "copy m_T");
+    c->have_images = true;
+    c->have_v = c->have_G = false;
+  });
+}
+
+reg_status reg3_transport(reg3_ctx* c, const float* v, const float* m0, float* m1) {
+  if (!c || !v || !m0 || !m1 || unaligned(v) || unaligned(m0) || unaligned(m1)) return REG_EINVAL;
+  return guarded(c, [&] {
+    const long long N = c->d.N;
+    if (v != c->v)
+      check(c, cudaMemcpyAsync(c->v, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
+    const float* cv = coefficients(c, c->v, 3, c->cv);
+    launch_k(k3_departure, dim3(nb(N)), dim3(kT), 0, c->st, c->d, c->s1, c->s2, c->s3,
+             (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+    check(c, cudaMemcpyAsync(c->fA, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m0");
+    float* a = c->fA;
+    float* b = c->fB;
+    for (int j = 1; j <= c->nt; ++j) {
+      gather(c, a, 1, c->dX, b, c->coef);
+      std::swap(a, b);
+    }
+    check(c, cudaMemcpyAsync(m1, a, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m1");
+    c->have_v = false;   // the cached state no longer matches v
+    c->have_G = false;
+  });
+}
+
+reg_status reg3_spectral(reg3_ctx* c, int op, double s, const float* in, float* out) {
+  if (!c || !in || !out || unaligned(in) || unaligned(out)) return REG_EINVAL;
+  int fin, fout, o3;
+  switch (op) {
+    case REG_SPEC_GRAD: fin = 1; fout = 3; o3 = OP3_GRAD; break;
+    case REG_SPEC_DIV: fin = 3; fout = 1; o3 = OP3_DIV; break;
+    case REG_SPEC_REGPOW: fin = 3; fout = 3; o3 = OP3_REGPOW; break;
+    default: return REG_EINVAL;
+  }
+  return guarded(c, [&] { spectral3(c, o3, s, in, fin, out, fout, nullptr); });
+}
+
+reg_status reg3_objective_gradient(reg3_ctx* c, const float* v, double* J, float* g) {
+  if (!c || !v || !J || unaligned(v) || (g && unaligned(g))) return REG_EINVAL;
+  return guarded(c, [&] {
+    if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
+    set_velocity(c, v);
+    *J = objective(c);
+    if (g) gradient(c, g);
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+  });
+}
+
+reg_status reg3_hessian_matvec(reg3_ctx* c, const float* v, const float* vt, float* Hvt) {
+  if (!c || !v || !vt || !Hvt || unaligned(v) || unaligned(vt) || unaligned(Hvt)) return REG_EINVAL;
+  return guarded(c, [&] {
+    if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
+    set_velocity(c, v);
+    hessian(c, vt, Hvt);
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+  });
+}
+
+// The inexact Newton-Krylov solve of reg_solve (§3.4.1) on the 3D problem:
+// ||g||_inf relative to g(0) as the stopping test, forcing term
+// min(0.5, ||g|| / ||g(0)||), PCG with P_REG = (beta A)^-1, Armijo
+// backtracking from the full step.
+reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
+  if (!c || !v || !(gtol > 0.0) || unaligned(v)) return REG_EINVAL;
+  reg_info inf;
+  std::memset(&inf, 0, sizeof inf);
+  reg_status result = REG_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  const reg_status s = guarded(c, [&] {
+    if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
+    const reg_options& o = c->opt;
+    const long long n = 3 * c->d.N;
+    auto maxabs = [&](const float* a) {
+      launch_maxabs(a, n, c->partialf, c->dsc, c->st);
+      check(c, cudaMemcpyAsync(c->hsc, c->dsc, sizeof(double), cudaMemcpyDeviceToHost, c->st), "read");
+      check(c, cudaStreamSynchronize(c->st), "synchronize");
+      return c->hsc[0];
+    };
+    launch_fill(c->vtrial, n, 0.f, c->st);
+    set_velocity(c, c->vtrial);
+    objective(c);
+    gradient(c, c->gcur);
+    const double gref_inf = maxabs(c->gcur);
+    const double gref_2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
+    inf.gref_inf = gref_inf;
+    set_velocity(c, v);
+    double J = objective(c);
+    inf.J0 = J;
+    gradient(c, c->gcur);
+    double rel = 1.0, ginf = 0.0;
+    for (int k = 0;; ++k) {
+      ginf = maxabs(c->gcur);
+      if (!std::isfinite(ginf) || !std::isfinite(J)) { result = REG_ENONFINITE; break; }
+      rel = ginf / gref_inf;
+      if (rel <= gtol || ginf <= o.gabs) break;
+      if (k == o.max_newton) { result = REG_ENOTCONV; break; }
+      const double g2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
+      const double eta = std::fmin(0.5, g2 / gref_2);
+      // PCG (Hestenes-Stiefel) on H s = -g from s = 0 with P_REG
+      launch_lincomb(n, -1.f, c->gcur, 0.f, nullptr, c->rhs, c->st);
+      launch_fill(c->kx, n, 0.f, c->st);
+      check(c, cudaMemcpyAsync(c->kr, c->rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+      const double bnorm = std::sqrt(dot_sync(c, c->rhs, c->rhs, n));
+      spectral3(c, OP3_REGPOW, -1.0, c->kr, 3, c->kz, 3, nullptr);
+      check(c, cudaMemcpyAsync(c->kp, c->kz, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+      double rz = dot_sync(c, c->kr, c->kz, n);
+      for (int it = 0; it < o.max_pcg && bnorm > 0.0; ++it) {
+        hessian(c, c->kp, c->kq);
+        ++inf.matvecs;
+        const double pq = dot_sync(c, c->kp, c->kq, n);
+        if (!(pq > 0.0)) {
+          if (it == 0)
+            check(c, cudaMemcpyAsync(c->kx, c->kz, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+          break;
+        }
+        const float alpha = (float)(rz / pq);
+        launch_lincomb(n, 1.f, c->kx, alpha, c->kp, c->kx, c->st);
+        launch_lincomb(n, 1.f, c->kr, -alpha, c->kq, c->kr, c->st);
+        ++inf.pcg_iters;
+        const double rr = dot_sync(c, c->kr, c->kr, n);
+        if (std::sqrt(rr) / bnorm <= eta) break;
+        spectral3(c, OP3_REGPOW, -1.0, c->kr, 3, c->kz, 3, nullptr);
+        const double rz_new = dot_sync(c, c->kr, c->kz, n);
+        launch_lincomb(n, 1.f, c->kz, (float)(rz_new / rz), c->kp, c->kp, c->st);
+        rz = rz_new;
+      }
+      const double slope = c->hh * dot_sync(c, c->gcur, c->kx, n);
+      double alpha = 1.0, Jt = J;
+      bool ok = false;
+      for (int ls = 0; ls <= o.max_backtracks; ++ls) {
+        launch_lincomb(n, 1.f, v, (float)alpha, c->kx, c->vtrial, c->st);
+        set_velocity(c, c->vtrial);
+        Jt = objective(c);
+        ++inf.line_search_steps;
+        if (Jt <= J + o.armijo_c1 * alpha * slope) { ok = true; break; }
+        alpha *= 0.5;
+      }
+      if (!ok) {
+        set_velocity(c, v);
+        objective(c);
+        result = REG_ELINESEARCH;
+        break;
+      }
+      check(c, cudaMemcpyAsync(v, c->vtrial, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "accept");
+      J = Jt;
+      gradient(c, c->gcur);
+      ++inf.newton_iters;
+    }
+    inf.J = J;
+    inf.gnorm_rel = rel;
+    inf.gnorm_inf = ginf;
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+  });
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (s != REG_OK) result = s;
+  inf.status = result;
+  if (info) *info = inf;
+  return result;
+}
+
+const char* reg3_last_error(const reg3_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

@@ -805,4 +805,94 @@ void fft_cols(const ColArgs& a, int groups, cudaStream_t st) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 3D grids: one pass of complex FFTs along one axis of F complex 3D arrays
+// (x_1 fastest, `total` values each, `fstride` apart). The lines have length
+// N and element stride `inner` (1 along x_1, n_1 along x_2, n_1 n_2 along
+// x_3): element j of line (o, i) sits at (o N + j) inner + i. A block
+// transforms P lines: consecutive o when inner = 1 (P N contiguous values),
+// else consecutive i (P adjacent values per j, coalesced). Forward or
+// inverse (unnormalised) Stockham passes as in the 2D kernels.
+template <int L, int T, bool INV>
+__global__ void __launch_bounds__(FftCfg<L, T>::NT)
+k_axis(float2* __restrict__ z, long long fstride, long long inner, const float2* __restrict__ tw) {
+  pdl_enter();
+  constexpr int N = FftCfg<L, T>::N, P = FftCfg<L, T>::P, NT = FftCfg<L, T>::NT;
+  extern __shared__ float2 sm[];
+  float2* zf = z + (long long)blockIdx.y * fstride;
+  const int t = threadIdx.x;
+  long long o0 = 0, i0 = 0;
+  if (inner == 1) {
+    o0 = (long long)blockIdx.x * P;
+  } else {
+    const long long per = inner / P;
+    o0 = blockIdx.x / per;
+    i0 = (blockIdx.x % per) * P;
+  }
+  auto addr = [&](int l, int j) -> long long {
+    return inner == 1 ? (o0 + l) * N + j : (o0 * N + j) * inner + i0 + l;
+  };
+  constexpr int LD = (P * N + NT - 1) / NT;
+  float2 v[LD];
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) {
+      const int l = inner == 1 ? q / N : q % P, j = inner == 1 ? q % N : q / P;
+      v[u] = zf[addr(l, j)];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) {
+      const int l = inner == 1 ? q / N : q % P, j = inner == 1 ? q % N : q / P;
+      sm[sw(l * N + j)] = v[u];
+    }
+  }
+  __syncthreads();
+  fft_smem<L, T, P, NT, INV>(sm, tw);
+#pragma unroll
+  for (int u = 0; u < LD; ++u) {
+    const int q = t + u * NT;
+    if ((P * N) % NT == 0 || q < P * N) {
+      const int l = inner == 1 ? q / N : q % P, j = inner == 1 ? q % N : q / P;
+      zf[addr(l, j)] = sm[sw(l * N + j)];
+    }
+  }
+}
+
+#define REGNK_AXIS_CASES(X) X(5, 0) X(6, 0) X(7, 0) X(8, 0) X(5, 1) X(6, 1)
+
+bool fft_axis_supported(int n) {
+  int L, T;
+  split_size(n, L, T);
+  return (T == 0 && L >= 5 && L <= 8) || (T == 1 && L >= 5 && L <= 6);
+}
+
+template <int L, int T>
+static void launch_axis(float2* z, long long total, int F, long long inner, bool inverse,
+                        const float2* tw, cudaStream_t st) {
+  using C = FftCfg<L, T>;
+  const size_t smem = (size_t)C::P * C::N * sizeof(float2);
+  const long long lines = total / C::N;
+  const dim3 grid((unsigned)(lines / C::P), F);
+  if (inverse)
+    launch_k(k_axis<L, T, true>, grid, dim3(C::NT), smem, st, z, total, inner, tw);
+  else
+    launch_k(k_axis<L, T, false>, grid, dim3(C::NT), smem, st, z, total, inner, tw);
+}
+
+void fft_axis(float2* z, long long total, int F, int n, long long inner, bool inverse,
+              const float2* tw, cudaStream_t st) {
+  int L, T;
+  split_size(n, L, T);
+  switch (L * 2 + T) {
+#define CASE(LL, TT) case LL * 2 + TT: launch_axis<LL, TT>(z, total, F, inner, inverse, tw, st); break;
+    REGNK_AXIS_CASES(CASE)
+#undef CASE
+    default: break;
+  }
+}
+
 }  // namespace regnk

@@ -126,6 +126,11 @@ void fft_rows_c2r(int n1, int n2, const float2* spec, long long sstride, float* 
 void fft_cols(const ColArgs& a, int groups, cudaStream_t st);
 // n = 2^L (L = 5..11) or 3 * 2^L (L = 5..9)
 bool fft_size_supported(int n);
+// 3D grids: complex FFTs along one axis of F arrays of `total` values (see
+// k_axis); n = 32, 64, 128, 256, 96 or 192
+bool fft_axis_supported(int n);
+void fft_axis(float2* z, long long total, int F, int n, long long inner, bool inverse,
+              const float2* tw, cudaStream_t st);
 
 // transport.cu
 struct PrefilterTaps;  // host-computed, passed by value below

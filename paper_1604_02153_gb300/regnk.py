@@ -111,6 +111,16 @@ _SIGNATURES = {
     "reg_batch_solve": [_P, ctypes.POINTER(_P), _D, _I, ctypes.POINTER(reg_info)],
     "reg_batch_hessian_matvec": [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)],
     "reg_batch_last_error": [_P],
+    "reg3_create": [_I, _I, _I, _I, _D, ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
+    "reg3_destroy": [_P],
+    "reg3_set_stream": [_P, _P],
+    "reg3_set_images": [_P, _P, _P],
+    "reg3_transport": [_P, _P, _P, _P],
+    "reg3_spectral": [_P, _I, _D, _P, _P],
+    "reg3_objective_gradient": [_P, _P, ctypes.POINTER(_D), _P],
+    "reg3_hessian_matvec": [_P, _P, _P, _P],
+    "reg3_solve": [_P, _P, _D, ctypes.POINTER(reg_info)],
+    "reg3_last_error": [_P],
     "reg_lockstep_create": [ctypes.POINTER(reg_grid), _I, _I, ctypes.POINTER(_D),
                             ctypes.POINTER(reg_options), ctypes.POINTER(_P)],
     "reg_lockstep_destroy": [_P],
@@ -156,6 +166,7 @@ def load(path=LIB_PATH):
         fn.argtypes = args
         fn.restype = {"reg_last_error": ctypes.c_char_p, "reg_batch_last_error": ctypes.c_char_p,
                       "reg_lockstep_last_error": ctypes.c_char_p,
+                      "reg3_last_error": ctypes.c_char_p,
                       "reg_unet_last_error": ctypes.c_char_p, "reg_launch_count": ctypes.c_longlong,
                       "reg_unet_param_count": ctypes.c_longlong}.get(name, ctypes.c_int)
     _lib = lib
@@ -407,6 +418,75 @@ class Batch:
         h = getattr(self, "h", None)
         if h is not None and h.value:
             self.lib.reg_batch_destroy(h)
+            self.h = None
+
+    __del__ = close
+
+
+class Registration3:
+    """reg3_ctx: the registration problem on an n1 x n2 x n3 periodic grid.
+    Fields are contiguous float32 CUDA tensors (x_1 fastest), vector fields
+    their three components back to back. Options as reg_options; precond
+    defaults to P_REG here, the form the 3D context requires."""
+
+    def __init__(self, n1, n2, n3, nt, beta, **options):
+        self.lib = load()
+        self.n1, self.n2, self.n3, self.nt = int(n1), int(n2), int(n3), int(nt)
+        self.N = self.n1 * self.n2 * self.n3
+        options.setdefault("precond", REG_PC_REG)
+        self.options = default_options(**options)
+        h = ctypes.c_void_p()
+        s = self.lib.reg3_create(self.n1, self.n2, self.n3, self.nt, float(beta),
+                                 ctypes.byref(self.options), ctypes.byref(h))
+        if s != REG_OK:
+            raise RegError(s, "reg3_create failed")
+        self.h = h
+
+    def _call(self, name, *args):
+        import torch
+        self.lib.reg3_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = getattr(self.lib, name)(self.h, *args)
+        if s != REG_OK:
+            raise RegError(s, self.lib.reg3_last_error(self.h).decode())
+        return s
+
+    def set_images(self, m_R, m_T):
+        self._call("reg3_set_images", _ptr(m_R, self.N, "m_R"), _ptr(m_T, self.N, "m_T"))
+
+    def transport(self, v, m0, m1):
+        self._call("reg3_transport", _ptr(v, 3 * self.N, "v"), _ptr(m0, self.N, "m0"),
+                   _ptr(m1, self.N, "m1"))
+
+    def spectral(self, op, x, out, s=1.0):
+        nin = self.N if op == REG_SPEC_GRAD else 3 * self.N
+        nout = self.N if op == REG_SPEC_DIV else 3 * self.N
+        self._call("reg3_spectral", int(op), float(s), _ptr(x, nin, "in"), _ptr(out, nout, "out"))
+
+    def objective_gradient(self, v, g=None):
+        J = ctypes.c_double()
+        self._call("reg3_objective_gradient", _ptr(v, 3 * self.N, "v"), ctypes.byref(J),
+                   _ptr(g, 3 * self.N, "g") if g is not None else None)
+        return J.value
+
+    def hessian_matvec(self, v, vt, out):
+        self._call("reg3_hessian_matvec", _ptr(v, 3 * self.N, "v"), _ptr(vt, 3 * self.N, "vt"),
+                   _ptr(out, 3 * self.N, "Hvt"))
+
+    def solve(self, v, gtol, allow=(REG_OK,)):
+        import torch
+        info = reg_info()
+        self.lib.reg3_set_stream(self.h, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = self.lib.reg3_solve(self.h, _ptr(v, 3 * self.N, "v"), float(gtol), ctypes.byref(info))
+        if s not in allow:
+            raise RegError(s, self.lib.reg3_last_error(self.h).decode())
+        d = info.as_dict()
+        d["status_name"] = STATUS_NAMES.get(s, str(s))
+        return d
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            self.lib.reg3_destroy(h)
             self.h = None
 
     __del__ = close

@@ -1,0 +1,159 @@
+"""The registration path on 3D grids (reg3_*) against the 3D FP64 oracle.
+
+Bars: the spectral operators within 1e-5 relative L2 (FP32 FFTs of smooth
+fields); transported images, the gradient and the Gauss-Newton matvec within
+the stated 1e-4 relative L2; J within 1e-5; the solve with the oracle's
+Newton and PCG iteration counts and the final velocity within 1e-3. A problem
+constant along x_3 also reproduces the 2D GPU path.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import d3
+from paper_1604_02153_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def regnk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1604_02153_gb300 import regnk as r
+    return r
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device="cuda")
+
+
+def host(t, shape):
+    return t.cpu().numpy().astype(np.float64).reshape(shape)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+N1, N2, N3 = 32, 64, 32
+
+
+def test_spectral_operators(regnk):
+    u = f32(inputs.random_field3(N1, N2, N3, seed=1, kmax=6))
+    v = f32(inputs.random_velocity3(N1, N2, N3, seed=2, kmax=5, vmax=1.0))
+    # a nonzero mean per component exercises the k = 0 weight beta^s of the
+    # negative powers (beta A discards the mean, so s = 1 takes v itself)
+    vm = f32(v + np.array([0.3, -0.2, 0.1])[:, None, None, None])
+    R = regnk.Registration3(N1, N2, N3, 4, 2e-2)
+    g = torch.empty(3 * R.N, device="cuda")
+    R.spectral(regnk.REG_SPEC_GRAD, dev(u), g)
+    assert rel(host(g, (3, N3, N2, N1)), d3.grad(u)) < 1e-5
+    dv = torch.empty(R.N, device="cuda")
+    R.spectral(regnk.REG_SPEC_DIV, dev(v), dv)
+    assert rel(host(dv, (N3, N2, N1)), d3.div(v)) < 1e-5
+    for s in (1.0, -1.0, -0.5):
+        x = v if s == 1.0 else vm
+        o = torch.empty(3 * R.N, device="cuda")
+        R.spectral(regnk.REG_SPEC_REGPOW, dev(x), o, s=s)
+        assert rel(host(o, (3, N3, N2, N1)), d3.reg_power(x, 2e-2, "H1", s)) < 1e-5, s
+    R.close()
+
+
+@pytest.mark.parametrize("interp", ["spline", "lagrange"])
+def test_transport(regnk, interp):
+    nt = 4
+    m0 = f32(inputs.random_field3(N1, N2, N3, seed=3, kmax=4))
+    v = f32(inputs.random_velocity3(N1, N2, N3, seed=4, kmax=3, vmax=0.5))
+    R = regnk.Registration3(N1, N2, N3, nt, 1e-2,
+                            interp=regnk.REG_INTERP_SPLINE if interp == "spline"
+                            else regnk.REG_INTERP_LAGRANGE)
+    m1 = torch.empty(R.N, device="cuda")
+    R.transport(dev(v), dev(m0), m1)
+    P = d3.Problem3(np.zeros_like(m0), m0, nt, 1e-2, kind=interp)
+    ref = P.state_solve(v)
+    assert rel(host(m1, (N3, N2, N1)), ref) < 1e-4
+    R.close()
+
+
+@pytest.mark.parametrize("interp", ["spline", "lagrange"])
+def test_objective_gradient_and_gauss_newton_matvec(regnk, interp):
+    nt, beta = 4, 1e-2
+    m_T = f32(inputs.random_field3(N1, N2, N3, seed=5, kmax=4))
+    m_R = f32(inputs.random_field3(N1, N2, N3, seed=6, kmax=4))
+    v = f32(inputs.random_velocity3(N1, N2, N3, seed=7, kmax=3, vmax=0.3))
+    u = f32(inputs.random_velocity3(N1, N2, N3, seed=8, kmax=3, vmax=1.0))
+    kind = regnk.REG_INTERP_SPLINE if interp == "spline" else regnk.REG_INTERP_LAGRANGE
+    R = regnk.Registration3(N1, N2, N3, nt, beta, interp=kind)
+    R.set_images(dev(m_R), dev(m_T))
+    g = torch.empty(3 * R.N, device="cuda")
+    J = R.objective_gradient(dev(v), g)
+    H = torch.empty(3 * R.N, device="cuda")
+    R.hessian_matvec(dev(v), dev(u), H)
+    P = d3.Problem3(m_R, m_T, nt, beta, kind=interp)
+    J_ref, g_ref = P.objective_gradient(v)
+    H_ref = P.hessian_matvec(u)
+    assert abs(J - J_ref) < 1e-5 * abs(J_ref)
+    assert rel(host(g, (3, N3, N2, N1)), g_ref) < 1e-4
+    assert rel(host(H, (3, N3, N2, N1)), H_ref) < 1e-4
+    R.close()
+
+
+def test_solve_matches_oracle(regnk):
+    n, nt, beta, gtol = 32, 4, 1e-2, 1e-2
+    m_T = f32(inputs.random_field3(n, n, n, seed=9, kmax=3))
+    vstar = f32(inputs.random_velocity3(n, n, n, seed=10, kmax=2, vmax=0.3))
+    m_R = f32(d3.Problem3(np.zeros_like(m_T), m_T, nt, beta).state_solve(vstar))
+    R = regnk.Registration3(n, n, n, nt, beta)
+    R.set_images(dev(m_R), dev(m_T))
+    v = torch.zeros(3 * R.N, device="cuda")
+    info = R.solve(v, gtol)
+    vo, oinfo = d3.Problem3(m_R, m_T, nt, beta).solve(np.zeros((3, n, n, n)), gtol)
+    assert info["gnorm_rel"] <= gtol
+    assert info["newton_iters"] == oinfo["newton_iters"]
+    assert info["pcg_iters"] == oinfo["pcg_iters"]
+    assert rel(host(v, (3, n, n, n)), vo) < 1e-3
+    assert abs(info["J"] - oinfo["J"]) < 1e-4 * oinfo["J"]
+    R.close()
+
+
+def test_constant_along_x3_gives_the_2d_path(regnk):
+    """Fields constant along x_3 and v_3 = 0: the 3D gradient and matvec
+    equal the 2D GPU path's (tiled), J the 2D J times 2 pi."""
+    n, n3, nt, beta = 64, 32, 4, 1e-2
+    m_T = f32(inputs.random_field(n, seed=11, kmax=6))
+    m_R = f32(inputs.random_field(n, seed=12, kmax=6))
+    v2 = f32(inputs.random_velocity(n, seed=13, vmax=0.3))
+    u2 = f32(inputs.random_velocity(n, seed=14, vmax=1.0))
+    tile = lambda a: np.repeat(a[None], n3, axis=0)
+    v3 = np.stack([tile(v2[0]), tile(v2[1]), np.zeros((n3, n, n))])
+    u3 = np.stack([tile(u2[0]), tile(u2[1]), np.zeros((n3, n, n))])
+    R2 = regnk.Registration(n, n, nt, beta, precond=regnk.REG_PC_REG)
+    R2.set_images(dev(m_R), dev(m_T))
+    g2 = torch.empty(2 * n * n, device="cuda")
+    J2 = R2.objective_gradient(dev(v2), g2)
+    H2 = torch.empty(2 * n * n, device="cuda")
+    R2.hessian_matvec(dev(v2), dev(u2), H2)
+    R3 = regnk.Registration3(n, n, n3, nt, beta)
+    R3.set_images(dev(tile(m_R)), dev(tile(m_T)))
+    g3 = torch.empty(3 * R3.N, device="cuda")
+    J3 = R3.objective_gradient(dev(v3), g3)
+    H3 = torch.empty(3 * R3.N, device="cuda")
+    R3.hessian_matvec(dev(v3), dev(u3), H3)
+    assert abs(J3 - 2 * np.pi * J2) < 1e-5 * abs(J3)
+    G2, G3 = host(g2, (2, n, n)), host(g3, (3, n3, n, n))
+    K2, K3 = host(H2, (2, n, n)), host(H3, (3, n3, n, n))
+    for c in range(2):
+        assert rel(G3[c], np.repeat(G2[c][None], n3, axis=0)) < 1e-5
+        assert rel(K3[c], np.repeat(K2[c][None], n3, axis=0)) < 1e-5
+    assert np.max(np.abs(G3[2])) < 1e-5 * np.max(np.abs(G2))
+    R2.close()
+    R3.close()
