@@ -15,6 +15,14 @@ on the device at 1024^2.
 instead solves the bench's batch64 workload (64 problems of uneven size,
 the analytic pair, nt = 4, beta = 1e-2, P_REG) with one lockstep batch that
 many times and prints the wall time per batch (about 1.5 GB on the device).
+
+    python profcase.py --d3 128 --nt 4 --matvecs 3
+
+instead sets up a 3D problem on an n^3 grid (band-limited random images,
+seeds 9 and 10, a smooth velocity with max |v| = 0.3), evaluates J and the
+gradient, then times the transport, the gradient and the GN matvec with
+CUDA events (median); (73 + 7 nt) n^3 floats on the device (1.6 GB at
+128^3, 6.8 GB at 256^3).
 """
 
 import argparse
@@ -52,7 +60,11 @@ def main():
     ap.add_argument("--batch", type=int, default=8, help="with --unet: pairs per step")
     ap.add_argument("--lockstep", type=int, default=0,
                     help="instead: this many lockstep solves of the 64-problem batch workload")
+    ap.add_argument("--d3", type=int, default=0,
+                    help="instead: the 3D path on a d3^3 grid (GN matvec, gradient, transport)")
     a = ap.parse_args()
+    if a.d3:
+        return d3_case(a.d3, a.nt, a.matvecs, a.lagrange)
     if a.unet:
         return unet_case(a.unet, a.conv_path, a.batch)
     if a.lockstep:
@@ -130,6 +142,48 @@ def main():
         dk = time.perf_counter() - t0
         print(f"n={n} PCG {info['pcg_iters']} iterations {1e3 * dk / max(1, info['pcg_iters']):.3f} "
               f"ms per iteration (graph replay of matvec and P_2L)")
+    R.close()
+
+
+def d3_case(n, nt, reps, lagrange):
+    import numpy as np
+    import torch
+
+    from paper_1604_02153_gb300 import inputs, regnk
+    f = lambda x: torch.tensor(np.ascontiguousarray(x, dtype=np.float32).ravel(), device="cuda")
+    m_T = f(inputs.random_field3(n, n, n, seed=9, kmax=4))
+    m_R = f(inputs.random_field3(n, n, n, seed=11, kmax=4))
+    v = f(inputs.random_velocity3(n, n, n, seed=10, kmax=3, vmax=0.3))
+    u = f(inputs.random_velocity3(n, n, n, seed=8, kmax=3, vmax=1.0))
+    R = regnk.Registration3(n, n, n, nt, 1e-2,
+                            interp=regnk.REG_INTERP_LAGRANGE if lagrange else regnk.REG_INTERP_SPLINE)
+    R.set_images(m_R, m_T)
+    g = torch.empty_like(v)
+    H = torch.empty_like(v)
+    m1 = torch.empty_like(m_T)
+    R.objective_gradient(v, g)
+    R.hessian_matvec(v, u, H)
+    R.transport(v, m_T, m1)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        ms = []
+        for _ in range(max(3, reps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    t_mv = timed(lambda: R.hessian_matvec(v, u, H))
+    t_g = timed(lambda: R.objective_gradient(v, g))
+    t_tr = timed(lambda: R.transport(v, m_T, m1))
+    print(f"3D n={n}^3 nt={nt} {'lagrange' if lagrange else 'spline'}: GN matvec {t_mv:.3f} ms, "
+          f"J + gradient (state solve included) {t_g:.3f} ms, transport {t_tr:.3f} ms "
+          f"(CUDA events, median of {max(3, reps)})")
     R.close()
 
 
