@@ -423,8 +423,12 @@ const char* reg_batch_last_error(const reg_batch* batch);
  * 96, 192}. Options as reg_create with precond = REG_PC_REG (the spectral
  * preconditioner; required), compressible, Gauss-Newton; anything else
  * REG_EINVAL. Calls run on the stream of reg3_set_stream (default stream
- * otherwise). reg3_create allocates (73 + 7 nt) n1 n2 n3 floats of device
- * memory (6.8 GB at 256^3, nt = 4), freed by reg3_destroy.
+ * otherwise). reg3_create allocates (74 + 7 nt) n1 n2 n3 floats of device
+ * memory (6.8 GB at 256^3, nt = 4), freed by reg3_destroy. fused_transport 1
+ * (default) gathers from shared-memory boxes around 32 x 8 x 8 tiles when the
+ * displacements of the velocity fit one (halo ceil(max |d|) + 2 cells per
+ * axis, at most 112 KB), from global memory otherwise; 0 always from global
+ * memory. Both forms compute every point with the same arithmetic.
  * Errors: REG_EINVAL for a NULL or unaligned pointer or an unknown op,
  * REG_ESTATE when reg3_set_images has not been called, REG_ENOMEM or
  * REG_ECUDA from the CUDA runtime (the message in reg3_last_error); the

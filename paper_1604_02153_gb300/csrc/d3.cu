@@ -43,52 +43,6 @@ __device__ __forceinline__ void split3(long long idx, const Dims& d, int& i, int
 }
 
 // --------------------------------------------------------------------------
-// B-spline prefilter along one axis: each thread produces 8 consecutive
-// coefficients of one line from a chain of kL + 8 + kL samples (the
-// recursions of interp.cuh, start-up length kL), periodic wrap. Consecutive
-// threads take consecutive x_1 (axes 1 and 2) or consecutive segments of
-// one line (axis 0).
-__global__ void __launch_bounds__(kT)
-k3_prefilter_axis(const float* __restrict__ in, float* __restrict__ out, Dims d, int axis) {
-  pdl_enter();
-  const long long t = (long long)blockIdx.x * kT + threadIdx.x;
-  if (t >= d.N / 8) return;
-  const int na = axis == 0 ? d.n1 : (axis == 1 ? d.n2 : d.n3);
-  const int nseg = na / 8;
-  long long base, step;
-  int seg;
-  if (axis == 0) {
-    seg = (int)(t % nseg);
-    base = (t / nseg) * d.n1;
-    step = 1;
-  } else if (axis == 1) {
-    const int i = (int)(t % d.n1);
-    const long long r = t / d.n1;
-    seg = (int)(r % nseg);
-    const long long k = r / nseg;
-    base = k * d.n2 * d.n1 + i;
-    step = d.n1;
-  } else {
-    const int i = (int)(t % d.n1);
-    const long long r = t / d.n1;
-    seg = (int)(r % nseg);
-    const long long j = r / nseg;
-    base = j * d.n1 + i;
-    step = (long long)d.n1 * d.n2;
-  }
-  constexpr int kLen = 8 + 2 * kL;
-  float v[kLen];
-  const int j0 = seg * 8 - kL;
-#pragma unroll
-  for (int q = 0; q < kLen; ++q) {
-    int j = j0 + q;
-    j = j < 0 ? j + na : (j >= na ? j - na : j);
-    v[q] = __ldg(in + base + (long long)j * step);
-  }
-  bspline_recursions<kLen, 8>(v, [&](int o, float x) { out[base + (long long)(seg * 8 + o) * step] = x; });
-}
-
-// --------------------------------------------------------------------------
 // Tricubic interpolation at node (i, j, k) + (d1, d2, d3) cells: the tensor
 // product of the 1D cubic weights over the 4 x 4 x 4 periodic stencil.
 struct Stencil3 {
@@ -176,6 +130,345 @@ k3_gather(Dims d, const float* __restrict__ coef, const float* __restrict__ disp
   const Stencil3 S = stencil3(i, j, k, __ldg(disp + idx), __ldg(disp + N + idx),
                               __ldg(disp + 2 * N + idx), d, lagrange);
   for (int f = 0; f < F; ++f) out[f * N + idx] = apply3(S, coef + f * N);
+}
+
+// --------------------------------------------------------------------------
+// B-spline prefilter along one axis with whole lines in shared memory: a
+// block stages 32 lines (axis 0: 32 consecutive rows; axes 1 and 2: the
+// lines through 32 consecutive x_1 of one plane) with coalesced loads; the
+// thread (lane, warp) runs the recursions of interp.cuh for the 32-point
+// segment `warp` of line `lane` from a chain of kL + 32 + kL samples
+// wrapped periodically in shared memory, and the block writes the
+// coefficients back with coalesced stores. blockDim.x = n (the line
+// length), blockIdx.y the field. Shared layout: axis 0 [line][n + 1] (odd
+// pitch), axes 1 and 2 [position][32]: a warp's 32 lines fall in 32 banks.
+constexpr int kPSeg = 32;   // outputs per recursion chain
+
+template <int AXIS>
+__global__ void __launch_bounds__(256)
+k3_prefilter_lines(const float* __restrict__ in, float* __restrict__ out, Dims d) {
+  pdl_enter();
+  extern __shared__ float sl[];
+  const int n = AXIS == 0 ? d.n1 : (AXIS == 1 ? d.n2 : d.n3);
+  const int t = threadIdx.x, lane = t & 31, seg = t >> 5;
+  in += (long long)blockIdx.y * d.N;
+  out += (long long)blockIdx.y * d.N;
+  long long base = 0, pstride = 1;
+  if (AXIS == 0) {
+    base = (long long)blockIdx.x * 32 * d.n1;
+  } else {
+    const int nx = d.n1 >> 5;
+    const long long r = blockIdx.x / nx;
+    const int x0 = (int)(blockIdx.x - r * nx) * 32;
+    if (AXIS == 1) {
+      base = r * d.n2 * d.n1 + x0;
+      pstride = d.n1;
+    } else {
+      base = r * d.n1 + x0;
+      pstride = (long long)d.n1 * d.n2;
+    }
+  }
+  const int nw = n >> 5;   // warps = segments per line
+  // element e = t + it * n of the block: axis 0 line it, position t; axes 1
+  // and 2 position t / 32 + it * nw, line lane
+#pragma unroll 8
+  for (int it = 0; it < 32; ++it) {
+    if (AXIS == 0) {
+      sl[it * (n + 1) + t] = __ldg(in + base + (long long)it * n + t);
+    } else {
+      const int p = seg + it * nw;
+      sl[p * 32 + lane] = __ldg(in + base + p * pstride + lane);
+    }
+  }
+  __syncthreads();
+  constexpr int NS = kPSeg + 2 * kL;
+  float v[NS];
+#pragma unroll
+  for (int q = 0; q < NS; ++q) {
+    const int p = wrap_once(seg * kPSeg - kL + q, n);
+    v[q] = AXIS == 0 ? sl[lane * (n + 1) + p] : sl[p * 32 + lane];
+  }
+  bspline_recursions<NS, kPSeg>(v, [&](int o, float x) { v[o + kL] = x; });
+  __syncthreads();
+#pragma unroll
+  for (int o = 0; o < kPSeg; ++o) {
+    const int p = seg * kPSeg + o;
+    if (AXIS == 0) sl[lane * (n + 1) + p] = v[o + kL];
+    else sl[p * 32 + lane] = v[o + kL];
+  }
+  __syncthreads();
+#pragma unroll 8
+  for (int it = 0; it < 32; ++it) {
+    if (AXIS == 0) {
+      out[base + (long long)it * n + t] = sl[it * (n + 1) + t];
+    } else {
+      const int p = seg + it * nw;
+      out[base + p * pstride + lane] = sl[p * 32 + lane];
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Tricubic gathers from a shared-memory box. A block of 256 threads owns a
+// 32 x 8 x 8 tile of points, thread (tx, ty) the eight points (i0 + tx,
+// j0 + ty, k0 + tz); the coefficients of the tile widened by h_a cells on
+// both sides of axis a are staged in shared memory and every tap of every
+// stencil reads them there. With |displacement_a| <= D_a the taps
+// floor(d) - 1 .. floor(d) + 2 stay inside the box for h_a = ceil(D_a) + 2;
+// the stencil base is clamped to the box all the same, so no access leaves
+// it whatever the displacements hold.
+constexpr int kBX = 32, kBY = 8, kBZ = 8, kBT = 256;
+constexpr int kBMinBlocks = 3;   // resident blocks per SM the register budget allows
+
+struct Box3 {
+  int h1, h2, h3;   // halo per axis (cells)
+  int b1, b2, b3;   // box extents: tile + 2 h
+};
+
+__device__ __forceinline__ void tile_origin(const Dims& d, int& i0, int& j0, int& k0) {
+  const int nx = d.n1 / kBX, ny = d.n2 / kBY;
+  const int b = blockIdx.x;
+  const int r = b / nx;
+  i0 = (b - r * nx) * kBX;
+  j0 = (r % ny) * kBY;
+  k0 = (r / ny) * kBZ;
+}
+
+// stage the box of field c with asynchronous 4-byte copies (every copy of
+// the block in flight at once, no registers held): warp w copies the box
+// rows (bz, by) with by = w, w + 8, ..., lane the columns lane and lane + 32
+// (b1 <= 64); ends with the wait and a block barrier
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void stage_box(const float* __restrict__ c, float* __restrict__ sm,
+                                          const Dims& d, const Box3& g, int i0, int j0, int k0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int xa = wrap_once(i0 - g.h1 + lane, d.n1);
+  const bool two = lane + 32 < g.b1;
+  const int xb = two ? wrap_once(i0 - g.h1 + lane + 32, d.n1) : 0;
+  for (int bz = 0; bz < g.b3; ++bz) {
+    const long long zrow = (long long)wrap_once(k0 - g.h3 + bz, d.n3) * d.n2;
+    for (int by = w; by < g.b2; by += kBT / 32) {
+      const float* row = c + (zrow + wrap_once(j0 - g.h2 + by, d.n2)) * d.n1;
+      float* srow = sm + (bz * g.b2 + by) * g.b1;
+      cp_async4(srow + lane, row + xa);
+      if (two) cp_async4(srow + lane + 32, row + xb);
+    }
+  }
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
+}
+
+struct BoxSt {
+  int base;   // shared offset of tap (0, 0, 0)
+  float w1[4], w2[4], w3[4];
+};
+
+__device__ __forceinline__ BoxSt box_stencil(int tx, int ty, int tz, float d1, float d2, float d3,
+                                             const Box3& g, bool lagrange) {
+  BoxSt S;
+  const float f1 = floorf(d1), f2 = floorf(d2), f3 = floorf(d3);
+  cubic_weights(d1 - f1, S.w1, lagrange);
+  cubic_weights(d2 - f2, S.w2, lagrange);
+  cubic_weights(d3 - f3, S.w3, lagrange);
+  const int x = min(max(tx + g.h1 + (int)f1 - 1, 0), g.b1 - 4);
+  const int y = min(max(ty + g.h2 + (int)f2 - 1, 0), g.b2 - 4);
+  const int z = min(max(tz + g.h3 + (int)f3 - 1, 0), g.b3 - 4);
+  S.base = (z * g.b2 + y) * g.b1 + x;
+  return S;
+}
+
+__device__ __forceinline__ float box_apply(const BoxSt& S, const float* __restrict__ sm,
+                                           const Box3& g) {
+  const int plane = g.b1 * g.b2;
+  float acc = 0.f;
+#pragma unroll
+  for (int cz = 0; cz < 4; ++cz) {
+    float accy = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float* row = sm + S.base + cz * plane + b * g.b1;
+      const float r = S.w1[0] * row[0] + S.w1[1] * row[1] + S.w1[2] * row[2] + S.w1[3] * row[3];
+      accy = fmaf(S.w2[b], r, accy);
+    }
+    acc = fmaf(S.w3[cz], accy, acc);
+  }
+  return acc;
+}
+
+__device__ __forceinline__ long long tile_index(const Dims& d, int i0, int j0, int k0, int tx,
+                                                int ty, int tz) {
+  return ((long long)(k0 + tz) * d.n2 + (j0 + ty)) * d.n1 + i0 + tx;
+}
+
+// The point loops below load the displacement of the next point while the
+// current one is evaluated (the first one during the staging), and issue the
+// streamed loads of a point before its 64 shared-memory taps.
+struct Disp3 {
+  float x, y, z;
+};
+
+__device__ __forceinline__ Disp3 load_disp(const float* __restrict__ p, long long N, long long idx) {
+  return Disp3{__ldg(p + idx), __ldg(p + N + idx), __ldg(p + 2 * N + idx)};
+}
+
+// out_f = I[coef_f](x + disp) for F fields N apart (box form of k3_gather)
+__global__ void __launch_bounds__(kBT, kBMinBlocks)
+k3b_gather(Dims d, Box3 g, const float* __restrict__ coef, const float* __restrict__ disp,
+           float* __restrict__ out, int F, int lagrange) {
+  pdl_enter();
+  extern __shared__ float sbox[];
+  int i0, j0, k0;
+  tile_origin(d, i0, j0, k0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long N = d.N, zs = (long long)d.n1 * d.n2;
+  const long long idx0 = tile_index(d, i0, j0, k0, tx, ty, 0);
+  for (int f = 0; f < F; ++f) {
+    Disp3 e = load_disp(disp, N, idx0);
+    if (f) __syncthreads();
+    stage_box(coef + f * N, sbox, d, g, i0, j0, k0);
+#pragma unroll 2
+    for (int tz = 0; tz < kBZ; ++tz) {
+      const long long idx = idx0 + tz * zs;
+      const Disp3 c = e;
+      if (tz + 1 < kBZ) e = load_disp(disp, N, idx + zs);
+      const BoxSt S = box_stencil(tx, ty, tz, c.x, c.y, c.z, g, lagrange);
+      out[f * N + idx] = box_apply(S, sbox, g);
+    }
+  }
+}
+
+// departure points of both characteristics (box form of k3_departure; the
+// box of each component of cv covers the reach of s v)
+__global__ void __launch_bounds__(kBT, kBMinBlocks)
+k3b_departure(Dims d, Box3 g, float s1, float s2, float s3, const float* __restrict__ v,
+              const float* __restrict__ cv, float* __restrict__ dX, float* __restrict__ dY,
+              int lagrange) {
+  pdl_enter();
+  extern __shared__ float sbox[];
+  int i0, j0, k0;
+  tile_origin(d, i0, j0, k0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long N = d.N, zs = (long long)d.n1 * d.n2;
+  const long long idx0 = tile_index(d, i0, j0, k0, tx, ty, 0);
+  for (int f = 0; f < 3; ++f) {
+    Disp3 e = load_disp(v, N, idx0);
+    if (f) __syncthreads();
+    stage_box(cv + f * N, sbox, d, g, i0, j0, k0);
+    const float sf = f == 0 ? s1 : (f == 1 ? s2 : s3);
+#pragma unroll 2
+    for (int tz = 0; tz < kBZ; ++tz) {
+      const long long idx = idx0 + tz * zs;
+      const float a1 = s1 * e.x, a2 = s2 * e.y, a3 = s3 * e.z;
+      if (tz + 1 < kBZ) e = load_disp(v, N, idx + zs);
+      const float af = f == 0 ? a1 : (f == 1 ? a2 : a3);
+      const BoxSt Sm = box_stencil(tx, ty, tz, -a1, -a2, -a3, g, lagrange);
+      dX[f * N + idx] = -0.5f * (af + sf * box_apply(Sm, sbox, g));
+      const BoxSt Sp = box_stencil(tx, ty, tz, a1, a2, a3, g, lagrange);
+      dY[f * N + idx] = 0.5f * (af + sf * box_apply(Sp, sbox, g));
+    }
+  }
+}
+
+// one backward (incremental) adjoint step (box form of k3_adjoint_step)
+__global__ void __launch_bounds__(kBT, kBMinBlocks)
+k3b_adjoint_step(Dims d, Box3 g, float ht, float wb, const float* __restrict__ coef,
+                 const float* __restrict__ dY, const float* __restrict__ delta,
+                 const float* __restrict__ delta_bar, const float* __restrict__ gm,
+                 float* __restrict__ lam_out, float* __restrict__ b, int lagrange) {
+  pdl_enter();
+  extern __shared__ float sbox[];
+  int i0, j0, k0;
+  tile_origin(d, i0, j0, k0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long N = d.N, zs = (long long)d.n1 * d.n2;
+  const long long idx0 = tile_index(d, i0, j0, k0, tx, ty, 0);
+  Disp3 e = load_disp(dY, N, idx0);
+  stage_box(coef, sbox, d, g, i0, j0, k0);
+#pragma unroll 1
+  for (int tz = 0; tz < kBZ; ++tz) {
+    const long long idx = idx0 + tz * zs;
+    const Disp3 c = e;
+    if (tz + 1 < kBZ) e = load_disp(dY, N, idx + zs);
+    const float db = __ldg(delta_bar + idx), dl = __ldg(delta + idx);
+    float gv[3], bv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      gv[q] = __ldg(gm + q * N + idx);
+      bv[q] = b[q * N + idx];
+    }
+    const BoxSt S = box_stencil(tx, ty, tz, c.x, c.y, c.z, g, lagrange);
+    const float lb = box_apply(S, sbox, g);
+    const float lstar = fmaf(ht * lb, db, lb);
+    const float l = lb + 0.5f * ht * (lb * db + lstar * dl);
+    lam_out[idx] = l;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) b[q * N + idx] = fmaf(wb * l, gv[q], bv[q]);
+  }
+}
+
+// one forward step of the incremental state (box form of k3_incstate_step):
+// the first step gathers the three components of v~ at X_D (stored in vtD)
+// and starts from m~_0 = 0, the others gather m~_{j-1}
+__global__ void __launch_bounds__(kBT, kBMinBlocks)
+k3b_incstate_step(Dims d, Box3 g, float ht, const float* __restrict__ coef,
+                  const float* __restrict__ dX, const float* __restrict__ vt,
+                  float* __restrict__ vtD, const float* __restrict__ G,
+                  const float* __restrict__ gm, float* __restrict__ out, int first,
+                  const float* __restrict__ cvt, int lagrange) {
+  pdl_enter();
+  extern __shared__ float sbox[];
+  int i0, j0, k0;
+  tile_origin(d, i0, j0, k0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const long long N = d.N, zs = (long long)d.n1 * d.n2;
+  const long long idx0 = tile_index(d, i0, j0, k0, tx, ty, 0);
+  if (first) {
+    for (int c = 0; c < 3; ++c) {
+      Disp3 e = load_disp(dX, N, idx0);
+      if (c) __syncthreads();
+      stage_box(cvt + c * N, sbox, d, g, i0, j0, k0);
+#pragma unroll 1
+      for (int tz = 0; tz < kBZ; ++tz) {
+        const long long idx = idx0 + tz * zs;
+        const Disp3 q = e;
+        if (tz + 1 < kBZ) e = load_disp(dX, N, idx + zs);
+        const BoxSt S = box_stencil(tx, ty, tz, q.x, q.y, q.z, g, lagrange);
+        vtD[c * N + idx] = box_apply(S, sbox, g);
+      }
+    }
+  }
+  Disp3 e{0.f, 0.f, 0.f};
+  if (!first) {
+    e = load_disp(dX, N, idx0);
+    stage_box(coef, sbox, d, g, i0, j0, k0);
+  }
+#pragma unroll 1
+  for (int tz = 0; tz < kBZ; ++tz) {
+    const long long idx = idx0 + tz * zs;
+    const Disp3 q = e;
+    if (!first && tz + 1 < kBZ) e = load_disp(dX, N, idx + zs);
+    float w[3], Gv[3], vv[3], gv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w[c] = vtD[c * N + idx];
+      Gv[c] = __ldg(G + c * N + idx);
+      vv[c] = __ldg(vt + c * N + idx);
+      gv[c] = __ldg(gm + c * N + idx);
+    }
+    float m = 0.f;
+    if (!first) {
+      const BoxSt S = box_stencil(tx, ty, tz, q.x, q.y, q.z, g, lagrange);
+      m = box_apply(S, sbox, g);
+    }
+    float src = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) src += w[c] * Gv[c] + vv[c] * gv[c];
+    out[idx] = m - 0.5f * ht * src;
+  }
 }
 
 // lambda = sign (mR - m1) (mR may be NULL), b = coef_b lambda grad m
@@ -341,7 +634,7 @@ struct reg3_ctx {
   float2 *tw1 = nullptr, *tw2 = nullptr, *tw3 = nullptr;
   float *mR = nullptr, *mT = nullptr, *v = nullptr, *cv = nullptr, *dX = nullptr, *dY = nullptr,
         *delta = nullptr, *delta_bar = nullptr, *m = nullptr, *gm = nullptr, *G = nullptr,
-        *coef = nullptr, *c3 = nullptr, *tA = nullptr, *tB = nullptr, *fA = nullptr,
+        *coef = nullptr, *c3 = nullptr, *tA = nullptr, *fA = nullptr,
         *fB = nullptr, *vtD = nullptr, *b = nullptr, *Av = nullptr;
   float *kx = nullptr, *kr = nullptr, *kz = nullptr, *kp = nullptr, *kq = nullptr,
         *vtrial = nullptr, *gcur = nullptr, *rhs = nullptr;
@@ -350,7 +643,14 @@ struct reg3_ctx {
   float* partialf = nullptr;
   double* dsc = nullptr;
   double* hsc = nullptr;
+  int* dflag = nullptr;
+  int* hflag = nullptr;
   bool have_images = false, have_v = false, have_G = false;
+  // shared-memory boxes of the gathers along X_D, Y_D and of the departure
+  // kernel (reach s v); use_* false: the global-load kernels
+  bool boxes = true;
+  Box3 boxX{}, boxY{}, boxV{};
+  bool useX = false, useY = false, useV = false;
   std::vector<void*> allocs;
   std::string err;
 };
@@ -419,20 +719,93 @@ void spectral3(reg3_ctx* c, int op, double s, const float* in, int Fin, float* o
 // for cubic Lagrange)
 const float* coefficients(reg3_ctx* c, const float* u, int F, float* dst) {
   if (c->lagrange) return u;
-  const long long N = c->d.N;
-  for (int f = 0; f < F; ++f) {
-    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, u + f * N, c->tA, c->d, 0);
-    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, (const float*)c->tA, c->tB, c->d, 1);
-    launch_k(k3_prefilter_axis, dim3(nb(N / 8)), dim3(kT), 0, c->st, (const float*)c->tB, dst + f * N, c->d, 2);
-  }
+  const Dims& d = c->d;
+  // x_1 pass into dst, x_2 pass dst -> tA, x_3 pass tA -> dst (F fields each)
+  launch_k(k3_prefilter_lines<0>, dim3((unsigned)(d.N / d.n1 / 32), F), dim3(d.n1),
+           (size_t)32 * (d.n1 + 1) * sizeof(float), c->st, u, dst, d);
+  launch_k(k3_prefilter_lines<1>, dim3((unsigned)(d.n1 / 32 * d.n3), F), dim3(d.n2),
+           (size_t)32 * d.n2 * sizeof(float), c->st, (const float*)dst, c->tA, d);
+  launch_k(k3_prefilter_lines<2>, dim3((unsigned)(d.n1 / 32 * d.n2), F), dim3(d.n3),
+           (size_t)32 * d.n3 * sizeof(float), c->st, (const float*)c->tA, dst, d);
   check_launch(c, "prefilter");
   return dst;
 }
 
+// box of a gather whose displacements are bounded by D_a cells per axis;
+// false when it does not fit (the global-load kernels run instead)
+constexpr size_t kBoxMaxBytes = 112 * 1024;
+
+bool make_box(const reg3_ctx* c, const double D[3], Box3& g) {
+  int h[3];
+  const int n[3] = {c->d.n1, c->d.n2, c->d.n3};
+  for (int a = 0; a < 3; ++a) {
+    if (!(D[a] >= 0.0) || D[a] > 64.0) return false;   // NaN, or far outside any box
+    h[a] = (int)std::ceil(D[a]) + 2;
+    if (h[a] >= n[a]) return false;
+  }
+  g = Box3{h[0], h[1], h[2], kBX + 2 * h[0], kBY + 2 * h[1], kBZ + 2 * h[2]};
+  return g.b1 <= 64 && (size_t)g.b1 * g.b2 * g.b3 * sizeof(float) <= kBoxMaxBytes;
+}
+
+size_t box_bytes(const Box3& g) { return (size_t)g.b1 * g.b2 * g.b3 * sizeof(float); }
+
+unsigned box_blocks(const Dims& d) { return (unsigned)((d.n1 / kBX) * (d.n2 / kBY) * (d.n3 / kBZ)); }
+
+// max |u_a| of the three components of a vector field, to the host
+void max3(reg3_ctx* c, const float* u, double out[3]) {
+  const long long N = c->d.N;
+  for (int a = 0; a < 3; ++a) launch_maxabs(u + a * N, N, c->partialf, c->dsc + a, c->st);
+  check(c, cudaMemcpyAsync(c->hsc, c->dsc, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st), "read");
+  check(c, cudaStreamSynchronize(c->st), "synchronize");
+  for (int a = 0; a < 3; ++a) out[a] = c->hsc[a];
+}
+
+// the box of the gathers along disp (X_D or Y_D of the cached velocity)
+bool box_for(const reg3_ctx* c, const float* disp, Box3& g) {
+  if (disp == c->dX && c->useX) { g = c->boxX; return true; }
+  if (disp == c->dY && c->useY) { g = c->boxY; return true; }
+  return false;
+}
+
 void gather(reg3_ctx* c, const float* u, int F, const float* disp, float* out, float* cbuf) {
   const float* cu = coefficients(c, u, F, cbuf);
-  launch_k(k3_gather, dim3(nb(c->d.N)), dim3(kT), 0, c->st, c->d, cu, disp, out, F, (int)c->lagrange);
+  Box3 g;
+  if (box_for(c, disp, g))
+    launch_k(k3b_gather, dim3(box_blocks(c->d)), dim3(kBT), box_bytes(g), c->st, c->d, g, cu, disp,
+             out, F, (int)c->lagrange);
+  else
+    launch_k(k3_gather, dim3(nb(c->d.N)), dim3(kT), 0, c->st, c->d, cu, disp, out, F, (int)c->lagrange);
   check_launch(c, "gather");
+}
+
+// departure points X_D, Y_D of c->v (coefficients cv) and the boxes of the
+// gathers along them
+void departure(reg3_ctx* c, const float* cv) {
+  const long long N = c->d.N;
+  c->useV = c->useX = c->useY = false;
+  if (c->boxes) {
+    double vm[3];
+    max3(c, c->v, vm);
+    // the reach |s_a v_a| of the first Heun stage, with a margin for the
+    // FP32 product
+    const double D[3] = {vm[0] * c->s1 * (1.0 + 1e-5), vm[1] * c->s2 * (1.0 + 1e-5),
+                         vm[2] * c->s3 * (1.0 + 1e-5)};
+    c->useV = make_box(c, D, c->boxV);
+  }
+  if (c->useV)
+    launch_k(k3b_departure, dim3(box_blocks(c->d)), dim3(kBT), box_bytes(c->boxV), c->st, c->d,
+             c->boxV, c->s1, c->s2, c->s3, (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+  else
+    launch_k(k3_departure, dim3(nb(N)), dim3(kT), 0, c->st, c->d, c->s1, c->s2, c->s3,
+             (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+  check_launch(c, "departure");
+  if (c->boxes) {
+    double DX[3], DY[3];
+    max3(c, c->dX, DX);
+    max3(c, c->dY, DY);
+    c->useX = make_box(c, DX, c->boxX);
+    c->useY = make_box(c, DY, c->boxY);
+  }
 }
 
 // v, its characteristics, the state history m_0..m_nt, grad m_j, div v and
@@ -442,9 +815,7 @@ void set_velocity(reg3_ctx* c, const float* v) {
   const int nt = c->nt;
   if (v != c->v)
     check(c, cudaMemcpyAsync(c->v, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
-  const float* cv = coefficients(c, c->v, 3, c->cv);
-  launch_k(k3_departure, dim3(nb(N)), dim3(kT), 0, c->st, c->d, c->s1, c->s2, c->s3,
-           (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+  departure(c, coefficients(c, c->v, 3, c->cv));
   check(c, cudaMemcpyAsync(c->m, c->mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "m_T");
   for (int j = 1; j <= nt; ++j) gather(c, c->m + (j - 1) * N, 1, c->dX, c->m + j * N, c->coef);
   for (int j = 0; j <= nt; ++j) spectral3(c, OP3_GRAD, 0.0, c->m + j * N, 1, c->gm + 3 * j * N, 3, nullptr);
@@ -452,6 +823,20 @@ void set_velocity(reg3_ctx* c, const float* v) {
   gather(c, c->delta, 1, c->dY, c->delta_bar, c->coef);
   c->have_v = true;
   c->have_G = false;
+}
+
+// set_velocity unless v equals the cached velocity bit for bit (a device
+// compare and one synchronisation)
+void sync_velocity(reg3_ctx* c, const float* v) {
+  bool differ = true;
+  if (c->have_v) {
+    check(c, cudaMemsetAsync(c->dflag, 0, sizeof(int), c->st), "memset");
+    launch_compare(v, c->v, 3 * c->d.N, c->dflag, c->st);
+    check(c, cudaMemcpyAsync(c->hflag, c->dflag, sizeof(int), cudaMemcpyDeviceToHost, c->st), "flag");
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+    differ = (*c->hflag != 0);
+  }
+  if (differ) set_velocity(c, v);
 }
 
 void ensure_G(reg3_ctx* c) {
@@ -480,6 +865,31 @@ double objective(reg3_ctx* c) {
   return 0.5 * c->hh * c->hsc[0] + 0.5 * c->hh * c->hsc[1];
 }
 
+// one backward (incremental) adjoint step along Y_D from the coefficients cl
+void adjoint_step(reg3_ctx* c, const float* cl, float wb, const float* gmj, float* lam_out) {
+  if (c->useY)
+    launch_k(k3b_adjoint_step, dim3(box_blocks(c->d)), dim3(kBT), box_bytes(c->boxY), c->st, c->d,
+             c->boxY, c->ht, wb, cl, (const float*)c->dY, (const float*)c->delta,
+             (const float*)c->delta_bar, gmj, lam_out, c->b, (int)c->lagrange);
+  else
+    launch_k(k3_adjoint_step, dim3(nb(c->d.N)), dim3(kT), 0, c->st, c->d, c->ht, wb, cl,
+             (const float*)c->dY, (const float*)c->delta, (const float*)c->delta_bar, gmj, lam_out,
+             c->b, (int)c->lagrange);
+}
+
+// one forward incremental state step along X_D (first: m~_0 = 0 and v~(X_D)
+// gathered from cvt into vtD)
+void incstate_step(reg3_ctx* c, const float* cm, const float* vt, const float* Gj,
+                   const float* gmj, float* out, bool first, const float* cvt) {
+  if (c->useX)
+    launch_k(k3b_incstate_step, dim3(box_blocks(c->d)), dim3(kBT), box_bytes(c->boxX), c->st, c->d,
+             c->boxX, c->ht, cm, (const float*)c->dX, vt, c->vtD, Gj, gmj, out, (int)first, cvt,
+             (int)c->lagrange);
+  else
+    launch_k(k3_incstate_step, dim3(nb(c->d.N)), dim3(kT), 0, c->st, c->d, c->ht, cm,
+             (const float*)c->dX, vt, c->vtD, Gj, gmj, out, (int)first, cvt, (int)c->lagrange);
+}
+
 // g = beta A v + int_0^1 lambda grad m dt (eq. control-elim, K = I)
 void gradient(reg3_ctx* c, float* g) {
   const long long N = c->d.N;
@@ -491,10 +901,7 @@ void gradient(reg3_ctx* c, float* g) {
            (const float*)(c->m + nt * N), (const float*)(c->gm + 3 * nt * N), lam, c->b, 1.f);
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
-    const float* cl = coefficients(c, lam, 1, c->coef);
-    launch_k(k3_adjoint_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, wb, cl,
-             (const float*)c->dY, (const float*)c->delta, (const float*)c->delta_bar,
-             (const float*)(c->gm + 3 * j * N), lam2, c->b, (int)c->lagrange);
+    adjoint_step(c, coefficients(c, lam, 1, c->coef), wb, c->gm + 3 * j * N, lam2);
     std::swap(lam, lam2);
   }
   launch_lincomb(3 * N, 1.f, c->Av, 1.f, c->b, g, c->st);
@@ -512,9 +919,7 @@ void hessian(reg3_ctx* c, const float* vt, float* out) {
   float* mt2 = c->fB;
   for (int j = 1; j <= nt; ++j) {
     const float* cm = j == 1 ? nullptr : coefficients(c, mt, 1, c->coef);
-    launch_k(k3_incstate_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, cm,
-             (const float*)c->dX, vt, c->vtD, (const float*)(c->G + 3 * (j - 1) * N),
-             (const float*)(c->gm + 3 * j * N), mt2, (int)(j == 1), cvt, (int)c->lagrange);
+    incstate_step(c, cm, vt, c->G + 3 * (j - 1) * N, c->gm + 3 * j * N, mt2, j == 1, cvt);
     std::swap(mt, mt2);
   }
   // lambda~_nt = -m~_nt and the first term of the time integral
@@ -524,10 +929,7 @@ void hessian(reg3_ctx* c, const float* vt, float* out) {
   float* lt2 = mt;
   for (int j = nt - 1; j >= 0; --j) {
     const float wb = ht * (j == 0 ? 0.5f : 1.0f);
-    const float* cl = coefficients(c, lt, 1, c->coef);
-    launch_k(k3_adjoint_step, dim3(nb(N)), dim3(kT), 0, c->st, c->d, ht, wb, cl,
-             (const float*)c->dY, (const float*)c->delta, (const float*)c->delta_bar,
-             (const float*)(c->gm + 3 * j * N), lt2, c->b, (int)c->lagrange);
+    adjoint_step(c, coefficients(c, lt, 1, c->coef), wb, c->gm + 3 * j * N, lt2);
     std::swap(lt, lt2);
   }
   spectral3(c, OP3_REGPOW, 1.0, vt, 3, out, 3, c->b);
@@ -594,10 +996,9 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
     c->tw1 = twiddles(c, n1);
     c->tw2 = twiddles(c, n2);
     c->tw3 = twiddles(c, n3);
-    float** scalar[] = {&c->mR, &c->mT, &c->delta, &c->delta_bar, &c->coef, &c->tA, &c->tB,
-                        &c->fA, &c->fB};
+    float** scalar[] = {&c->mR, &c->mT, &c->delta, &c->delta_bar, &c->coef, &c->fA, &c->fB};
     for (float** f : scalar) *f = dalloc<float>(c, N);
-    float** vec[] = {&c->v, &c->cv, &c->dX, &c->dY, &c->c3, &c->vtD, &c->b, &c->Av, &c->kx,
+    float** vec[] = {&c->v, &c->cv, &c->dX, &c->dY, &c->c3, &c->tA, &c->vtD, &c->b, &c->Av, &c->kx,
                      &c->kr, &c->kz, &c->kp, &c->kq, &c->vtrial, &c->gcur, &c->rhs};
     for (float** f : vec) *f = dalloc<float>(c, 3 * N);
     c->m = dalloc<float>(c, (size_t)(nt + 1) * N);
@@ -608,9 +1009,18 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
     c->partial = dalloc<double>(c, reduce_partials());
     c->partialf = dalloc<float>(c, reduce_partials());
     c->dsc = dalloc<double>(c, 4);
+    c->dflag = dalloc<int>(c, 1);
     void* h = nullptr;
-    check(c, cudaMallocHost(&h, 4 * sizeof(double)), "cudaMallocHost");
+    check(c, cudaMallocHost(&h, 4 * sizeof(double) + sizeof(int)), "cudaMallocHost");
     c->hsc = static_cast<double*>(h);
+    c->hflag = reinterpret_cast<int*>(c->hsc + 4);
+    c->boxes = o.fused_transport != 0;
+    // the box kernels may take more than the default 48 KB of shared memory
+    const int maxb = (int)kBoxMaxBytes;
+    check(c, cudaFuncSetAttribute(k3b_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
+    check(c, cudaFuncSetAttribute(k3b_departure, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
+    check(c, cudaFuncSetAttribute(k3b_adjoint_step, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
+    check(c, cudaFuncSetAttribute(k3b_incstate_step, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
     check(c, cudaDeviceSynchronize(), "create");
   });
   if (s != REG_OK) {
@@ -653,9 +1063,7 @@ reg_status reg3_transport(reg3_ctx* c, const float* v, const float* m0, float* m
     const long long N = c->d.N;
     if (v != c->v)
       check(c, cudaMemcpyAsync(c->v, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
-    const float* cv = coefficients(c, c->v, 3, c->cv);
-    launch_k(k3_departure, dim3(nb(N)), dim3(kT), 0, c->st, c->d, c->s1, c->s2, c->s3,
-             (const float*)c->v, cv, c->dX, c->dY, (int)c->lagrange);
+    departure(c, coefficients(c, c->v, 3, c->cv));
     check(c, cudaMemcpyAsync(c->fA, m0, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m0");
     float* a = c->fA;
     float* b = c->fB;
@@ -685,7 +1093,7 @@ reg_status reg3_objective_gradient(reg3_ctx* c, const float* v, double* J, float
   if (!c || !v || !J || unaligned(v) || (g && unaligned(g))) return REG_EINVAL;
   return guarded(c, [&] {
     if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
-    set_velocity(c, v);
+    sync_velocity(c, v);
     *J = objective(c);
     if (g) gradient(c, g);
     check(c, cudaStreamSynchronize(c->st), "synchronize");
@@ -696,7 +1104,7 @@ reg_status reg3_hessian_matvec(reg3_ctx* c, const float* v, const float* vt, flo
   if (!c || !v || !vt || !Hvt || unaligned(v) || unaligned(vt) || unaligned(Hvt)) return REG_EINVAL;
   return guarded(c, [&] {
     if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
-    set_velocity(c, v);
+    sync_velocity(c, v);
     hessian(c, vt, Hvt);
     check(c, cudaStreamSynchronize(c->st), "synchronize");
   });

@@ -157,3 +157,44 @@ def test_constant_along_x3_gives_the_2d_path(regnk):
     assert np.max(np.abs(G3[2])) < 1e-5 * np.max(np.abs(G2))
     R2.close()
     R3.close()
+
+
+@pytest.mark.parametrize("interp", ["spline", "lagrange"])
+@pytest.mark.parametrize("vmax", [0.3, 6.0])
+def test_box_and_global_gathers(regnk, interp, vmax):
+    """The tricubic gathers from shared-memory boxes (fused_transport 1 when
+    the displacements fit a box: at vmax 0.3 the reach is under one cell, a
+    box of 38 x 14 x 14 floats) and from global memory (fused_transport 0,
+    and the fallback of fused_transport 1 at vmax 6, a reach of about 15
+    cells along x_2 that needs a 244 KB box): transported image, gradient
+    and GN matvec against the oracle at the stated bars, and the two forms
+    against each other (the same stencil arithmetic) within 1e-6."""
+    nt, beta = 4, 1e-2
+    kind = regnk.REG_INTERP_SPLINE if interp == "spline" else regnk.REG_INTERP_LAGRANGE
+    m_T = f32(inputs.random_field3(N1, N2, N3, seed=15, kmax=4))
+    m_R = f32(inputs.random_field3(N1, N2, N3, seed=16, kmax=4))
+    v = f32(inputs.random_velocity3(N1, N2, N3, seed=17, kmax=3, vmax=vmax))
+    u = f32(inputs.random_velocity3(N1, N2, N3, seed=18, kmax=3, vmax=1.0))
+    P = d3.Problem3(m_R, m_T, nt, beta, kind=interp)
+    m1_ref = P.state_solve(v)
+    J_ref, g_ref = P.objective_gradient(v)
+    H_ref = P.hessian_matvec(u)
+    out = {}
+    for fused in (0, 1):
+        R = regnk.Registration3(N1, N2, N3, nt, beta, interp=kind, fused_transport=fused)
+        m1 = torch.empty(R.N, device="cuda")
+        R.transport(dev(v), dev(m_T), m1)
+        R.set_images(dev(m_R), dev(m_T))
+        g = torch.empty(3 * R.N, device="cuda")
+        J = R.objective_gradient(dev(v), g)
+        H = torch.empty(3 * R.N, device="cuda")
+        R.hessian_matvec(dev(v), dev(u), H)
+        o = (host(m1, (N3, N2, N1)), host(g, (3, N3, N2, N1)), host(H, (3, N3, N2, N1)))
+        assert rel(o[0], m1_ref) < 1e-4
+        assert abs(J - J_ref) < 1e-5 * abs(J_ref)
+        assert rel(o[1], g_ref) < 1e-4
+        assert rel(o[2], H_ref) < 1e-4
+        out[fused] = o
+        R.close()
+    for a, b in zip(out[0], out[1]):
+        assert rel(b, a) < 1e-6
