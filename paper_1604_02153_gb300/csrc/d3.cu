@@ -214,15 +214,20 @@ k3_prefilter_lines(const float* __restrict__ in, float* __restrict__ out, Dims d
 // j0 + ty, k0 + tz); the coefficients of the tile widened by h_a cells on
 // both sides of axis a are staged in shared memory and every tap of every
 // stencil reads them there. With |displacement_a| <= D_a the taps
-// floor(d) - 1 .. floor(d) + 2 stay inside the box for h_a = ceil(D_a) + 2;
-// the stencil base is clamped to the box all the same, so no access leaves
-// it whatever the displacements hold.
+// floor(d) - 1 .. floor(d) + 2 lie between ceil(D_a) + 1 cells below and
+// floor(D_a) + 2 cells above the point, the box's margins; the stencil base
+// is clamped to the box all the same, so no access leaves it whatever the
+// displacements hold. Box rows are 64 floats apart (a multiple of the 32
+// banks), so lanes whose stencils fall on different rows or planes read
+// different banks.
 constexpr int kBX = 32, kBY = 8, kBZ = 8, kBT = 256;
 constexpr int kBMinBlocks = 3;   // resident blocks per SM the register budget allows
 
+constexpr int kBoxPitch = 64;   // floats per box row (b1 <= 64)
+
 struct Box3 {
-  int h1, h2, h3;   // halo per axis (cells)
-  int b1, b2, b3;   // box extents: tile + 2 h
+  int h1, h2, h3;   // lower margin per axis (cells): the box starts h_a before the tile
+  int b1, b2, b3;   // box extents: tile + lower + upper margin
 };
 
 __device__ __forceinline__ void tile_origin(const Dims& d, int& i0, int& j0, int& k0) {
@@ -253,7 +258,7 @@ __device__ __forceinline__ void stage_box(const float* __restrict__ c, float* __
     const long long zrow = (long long)wrap_once(k0 - g.h3 + bz, d.n3) * d.n2;
     for (int by = w; by < g.b2; by += kBT / 32) {
       const float* row = c + (zrow + wrap_once(j0 - g.h2 + by, d.n2)) * d.n1;
-      float* srow = sm + (bz * g.b2 + by) * g.b1;
+      float* srow = sm + (bz * g.b2 + by) * kBoxPitch;
       cp_async4(srow + lane, row + xa);
       if (two) cp_async4(srow + lane + 32, row + xb);
     }
@@ -277,20 +282,20 @@ __device__ __forceinline__ BoxSt box_stencil(int tx, int ty, int tz, float d1, f
   const int x = min(max(tx + g.h1 + (int)f1 - 1, 0), g.b1 - 4);
   const int y = min(max(ty + g.h2 + (int)f2 - 1, 0), g.b2 - 4);
   const int z = min(max(tz + g.h3 + (int)f3 - 1, 0), g.b3 - 4);
-  S.base = (z * g.b2 + y) * g.b1 + x;
+  S.base = (z * g.b2 + y) * kBoxPitch + x;
   return S;
 }
 
 __device__ __forceinline__ float box_apply(const BoxSt& S, const float* __restrict__ sm,
                                            const Box3& g) {
-  const int plane = g.b1 * g.b2;
+  const int plane = kBoxPitch * g.b2;
   float acc = 0.f;
 #pragma unroll
   for (int cz = 0; cz < 4; ++cz) {
     float accy = 0.f;
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-      const float* row = sm + S.base + cz * plane + b * g.b1;
+      const float* row = sm + S.base + cz * plane + b * kBoxPitch;
       const float r = S.w1[0] * row[0] + S.w1[1] * row[1] + S.w1[2] * row[2] + S.w1[3] * row[3];
       accy = fmaf(S.w2[b], r, accy);
     }
@@ -613,6 +618,83 @@ k3_multiply(Dims d, int op, int F, float beta, int p, float s, const float2* __r
   }
 }
 
+// Two real fields share one complex transform. The multipliers below (i q_a
+// of the gradient, Nyquist zeroed, and the real even (beta |k|^2p)^s) map
+// real fields to real fields, so the inverse transform of op applied to the
+// spectrum of u + i w is op(u) + i op(w): half the transforms of separate
+// fields, and no separation of the two spectra.
+
+// z_p = in_{2p} + i in_{2p+1} (imaginary part 0 for the last of an odd F);
+// blockIdx.y = p
+__global__ void __launch_bounds__(kT)
+k3_pack_pairs(const float* __restrict__ in, int F, float2* __restrict__ z, long long N) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  const int p = blockIdx.y;
+  if (idx >= N) return;
+  const float re = __ldg(in + 2 * p * N + idx);
+  const float im = 2 * p + 1 < F ? __ldg(in + (2 * p + 1) * N + idx) : 0.f;
+  z[p * N + idx] = make_float2(re, im);
+}
+
+// F output fields (+ add) from packed results, blockIdx.y = p: the real
+// and imaginary parts of z_p go to out_{2p} and out_{2p+1} (interleaved,
+// mode 0; no imaginary output past F) or to out_p and out_{p+H} (blocked,
+// mode 1, F = 2 H)
+__global__ void __launch_bounds__(kT)
+k3_unpack_pairs(const float2* __restrict__ z, int mode, int H, int F, float* __restrict__ out,
+                const float* __restrict__ add, long long N) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  const int p = blockIdx.y;
+  if (idx >= N) return;
+  const int fr = mode == 0 ? 2 * p : p, fi = mode == 0 ? 2 * p + 1 : p + H;
+  const float2 v = z[p * N + idx];
+  out[fr * N + idx] = v.x + (add ? __ldg(add + fr * N + idx) : 0.f);
+  if (fi < F) out[fi * N + idx] = v.y + (add ? __ldg(add + fi * N + idx) : 0.f);
+}
+
+enum Op3P {
+  OPP_REGPOW = 0,   // P packed spectra times (beta |k|^2p)^s
+  OPP_GRAD1 = 1,    // spectrum U of one real field -> i q1 U + i (i q2 U), i q3 U
+  OPP_GRAD2 = 2     // packed pair Z -> i q_c Z, c = 1, 2, 3
+};
+
+// zout = op(zin) scaled by 1 / N (the normalisation of the inverse passes)
+__global__ void __launch_bounds__(kT)
+k3_multiply_pairs(Dims d, int op, int P, float beta, int p, float s,
+                  const float2* __restrict__ zin, float2* __restrict__ zout) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= d.N) return;
+  int i, j, k;
+  split3(idx, d, i, j, k);
+  const long long N = d.N;
+  const float scale = 1.f / (float)N;
+  const float k1 = (float)signed_k(i, d.n1), k2 = (float)signed_k(j, d.n2),
+              k3 = (float)signed_k(k, d.n3);
+  const float q1 = (2 * i == d.n1) ? 0.f : k1, q2 = (2 * j == d.n2) ? 0.f : k2,
+              q3 = (2 * k == d.n3) ? 0.f : k3;
+  if (op == OPP_REGPOW) {
+    const float g = regpow3(beta, p, s, k1 * k1 + k2 * k2 + k3 * k3) * scale;
+    for (int c = 0; c < P; ++c) {
+      const float2 u = zin[c * N + idx];
+      zout[c * N + idx] = make_float2(g * u.x, g * u.y);
+    }
+  } else if (op == OPP_GRAD1) {
+    const float2 u = zin[idx];
+    // i q1 U + i (i q2 U) = (-q1 u.y - q2 u.x, q1 u.x - q2 u.y)
+    zout[idx] = make_float2((-q1 * u.y - q2 * u.x) * scale, (q1 * u.x - q2 * u.y) * scale);
+    zout[N + idx] = make_float2(-q3 * u.y * scale, q3 * u.x * scale);
+  } else {
+    const float2 u = zin[idx];
+    const float q[3] = {q1, q2, q3};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)   // i q u
+      zout[c * N + idx] = make_float2(-q[c] * u.y * scale, q[c] * u.x * scale);
+  }
+}
+
 inline unsigned nb(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 }  // namespace d3
@@ -705,14 +787,41 @@ void fft3(reg3_ctx* c, float2* z, int F, bool inverse) {
 void spectral3(reg3_ctx* c, int op, double s, const float* in, int Fin, float* out, int Fout,
                const float* add) {
   const long long N = c->d.N;
-  launch_k(k3_pack, dim3(nb(Fin * N)), dim3(kT), 0, c->st, in, c->zA, Fin * N);
-  fft3(c, c->zA, Fin, false);
-  launch_k(k3_multiply, dim3(nb(N)), dim3(kT), 0, c->st, c->d, op, Fin, (float)c->beta,
-           c->opt.reg_norm, (float)s, (const float2*)c->zA, c->zB);
-  fft3(c, c->zB, Fout, true);
-  launch_k(k3_unpack, dim3(nb(Fout * N)), dim3(kT), 0, c->st, (const float2*)c->zB, out, add,
-           Fout * N);
+  if (op == OP3_DIV) {   // 3 -> 1: three separate spectra
+    launch_k(k3_pack, dim3(nb(Fin * N)), dim3(kT), 0, c->st, in, c->zA, Fin * N);
+    fft3(c, c->zA, Fin, false);
+    launch_k(k3_multiply, dim3(nb(N)), dim3(kT), 0, c->st, c->d, op, Fin, (float)c->beta,
+             c->opt.reg_norm, (float)s, (const float2*)c->zA, c->zB);
+    fft3(c, c->zB, Fout, true);
+    launch_k(k3_unpack, dim3(nb(Fout * N)), dim3(kT), 0, c->st, (const float2*)c->zB, out, add,
+             Fout * N);
+  } else {   // grad (1 -> 3) or (beta A)^s (F -> F) on packed pairs
+    const int Pin = (Fin + 1) / 2, Pout = (Fout + 1) / 2;
+    launch_k(k3_pack_pairs, dim3(nb(N), Pin), dim3(kT), 0, c->st, in, Fin, c->zA, N);
+    fft3(c, c->zA, Pin, false);
+    launch_k(k3_multiply_pairs, dim3(nb(N)), dim3(kT), 0, c->st, c->d,
+             op == OP3_GRAD ? (int)OPP_GRAD1 : (int)OPP_REGPOW, Pin, (float)c->beta,
+             c->opt.reg_norm, (float)s, (const float2*)c->zA, c->zB);
+    fft3(c, c->zB, Pout, true);
+    launch_k(k3_unpack_pairs, dim3(nb(N), Pout), dim3(kT), 0, c->st, (const float2*)c->zB, 0, 0,
+             Fout, out, add, N);
+  }
   check_launch(c, "spectral operator");
+}
+
+// the gradients of the two consecutive fields u and u + N into out (the three
+// components of the first, then those of the second) with one forward and
+// three inverse transforms
+void grad_pair(reg3_ctx* c, const float* u, float* out) {
+  const long long N = c->d.N;
+  launch_k(k3_pack_pairs, dim3(nb(N), 1), dim3(kT), 0, c->st, u, 2, c->zA, N);
+  fft3(c, c->zA, 1, false);
+  launch_k(k3_multiply_pairs, dim3(nb(N)), dim3(kT), 0, c->st, c->d, (int)OPP_GRAD2, 1,
+           (float)c->beta, c->opt.reg_norm, 0.f, (const float2*)c->zA, c->zB);
+  fft3(c, c->zB, 3, true);
+  launch_k(k3_unpack_pairs, dim3(nb(N), 3), dim3(kT), 0, c->st, (const float2*)c->zB, 1, 3, 6, out,
+           (const float*)nullptr, N);
+  check_launch(c, "gradient pair");
 }
 
 // interpolation coefficients of F consecutive fields (the samples themselves
@@ -736,18 +845,19 @@ const float* coefficients(reg3_ctx* c, const float* u, int F, float* dst) {
 constexpr size_t kBoxMaxBytes = 112 * 1024;
 
 bool make_box(const reg3_ctx* c, const double D[3], Box3& g) {
-  int h[3];
+  int lo[3], hi[3];
   const int n[3] = {c->d.n1, c->d.n2, c->d.n3};
   for (int a = 0; a < 3; ++a) {
     if (!(D[a] >= 0.0) || D[a] > 64.0) return false;   // NaN, or far outside any box
-    h[a] = (int)std::ceil(D[a]) + 2;
-    if (h[a] >= n[a]) return false;
+    lo[a] = (int)std::ceil(D[a]) + 1;
+    hi[a] = (int)std::floor(D[a]) + 2;
+    if (lo[a] >= n[a] || hi[a] >= n[a]) return false;
   }
-  g = Box3{h[0], h[1], h[2], kBX + 2 * h[0], kBY + 2 * h[1], kBZ + 2 * h[2]};
-  return g.b1 <= 64 && (size_t)g.b1 * g.b2 * g.b3 * sizeof(float) <= kBoxMaxBytes;
+  g = Box3{lo[0], lo[1], lo[2], kBX + lo[0] + hi[0], kBY + lo[1] + hi[1], kBZ + lo[2] + hi[2]};
+  return g.b1 <= kBoxPitch && (size_t)kBoxPitch * g.b2 * g.b3 * sizeof(float) <= kBoxMaxBytes;
 }
 
-size_t box_bytes(const Box3& g) { return (size_t)g.b1 * g.b2 * g.b3 * sizeof(float); }
+size_t box_bytes(const Box3& g) { return (size_t)kBoxPitch * g.b2 * g.b3 * sizeof(float); }
 
 unsigned box_blocks(const Dims& d) { return (unsigned)((d.n1 / kBX) * (d.n2 / kBY) * (d.n3 / kBZ)); }
 
@@ -818,7 +928,9 @@ void set_velocity(reg3_ctx* c, const float* v) {
   departure(c, coefficients(c, c->v, 3, c->cv));
   check(c, cudaMemcpyAsync(c->m, c->mT, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "m_T");
   for (int j = 1; j <= nt; ++j) gather(c, c->m + (j - 1) * N, 1, c->dX, c->m + j * N, c->coef);
-  for (int j = 0; j <= nt; ++j) spectral3(c, OP3_GRAD, 0.0, c->m + j * N, 1, c->gm + 3 * j * N, 3, nullptr);
+  int j = 0;
+  for (; j + 1 <= nt; j += 2) grad_pair(c, c->m + j * N, c->gm + 3 * j * N);
+  if (j == nt) spectral3(c, OP3_GRAD, 0.0, c->m + j * N, 1, c->gm + 3 * j * N, 3, nullptr);
   spectral3(c, OP3_DIV, 0.0, c->v, 3, c->delta, 1, nullptr);
   gather(c, c->delta, 1, c->dY, c->delta_bar, c->coef);
   c->have_v = true;

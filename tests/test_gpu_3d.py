@@ -164,9 +164,9 @@ def test_constant_along_x3_gives_the_2d_path(regnk):
 def test_box_and_global_gathers(regnk, interp, vmax):
     """The tricubic gathers from shared-memory boxes (fused_transport 1 when
     the displacements fit a box: at vmax 0.3 the reach is under one cell, a
-    box of 38 x 14 x 14 floats) and from global memory (fused_transport 0,
-    and the fallback of fused_transport 1 at vmax 6, a reach of about 15
-    cells along x_2 that needs a 244 KB box): transported image, gradient
+    box of about 36 x 12 x 12 floats) and from global memory (fused_transport
+    0, and the fallback of fused_transport 1 at vmax 6, a reach of about 15
+    cells along x_2 that needs a box of over 200 KB): transported image, gradient
     and GN matvec against the oracle at the stated bars, and the two forms
     against each other (the same stencil arithmetic) within 1e-6."""
     nt, beta = 4, 1e-2
