@@ -264,7 +264,12 @@ class Registration:
                    _ptr(out, self.N, "out"))
 
     def spectral(self, op, inp, out, s=0.0):
-        self._call("reg_spectral", int(op), float(s), _ptr(inp, name="in"), _ptr(out, name="out"))
+        # fields in and out per op (include/reg.h): grad scalar -> vector,
+        # div vector -> scalar, prefilter scalar -> scalar, the rest vector -> vector
+        nin = {REG_SPEC_GRAD: 1, REG_SPEC_PREFILTER: 1}.get(op, 2)
+        nout = {REG_SPEC_DIV: 1, REG_SPEC_PREFILTER: 1}.get(op, 2)
+        self._call("reg_spectral", int(op), float(s), _ptr(inp, nin * self.N, "in"),
+                   _ptr(out, nout * self.N, "out"))
 
     def restrict(self, fine, coarse):
         self._call("reg_restrict", _ptr(fine, 2 * self.N, "fine"), _ptr(coarse, self.N // 2, "coarse"))
@@ -350,8 +355,8 @@ class Registration:
 
     def dot(self, a, b):
         out = ctypes.c_double()
-        self._call("reg_dot", _ptr(a, name="a"), _ptr(b, name="b"), ctypes.c_longlong(a.numel()),
-                   ctypes.byref(out))
+        self._call("reg_dot", _ptr(a, name="a"), _ptr(b, b.numel() if a is None else a.numel(), "b"),
+                   ctypes.c_longlong(a.numel()), ctypes.byref(out))
         return out.value
 
 
@@ -612,13 +617,29 @@ class UNet:
         if s != REG_OK:
             raise RegError(s, self.lib.reg_unet_last_error(self.h).decode())
 
-    def _idx(self, idx, B):
+    def _idx(self, idx, B, *arrays):
+        """idx as a pointer after checking the image-pair arrays it selects
+        from: without idx each array holds B pairs' worth of S x S fields,
+        with idx a whole number of them and every index below that count
+        (a read of the indices, one synchronisation)."""
         import torch
+        S2 = self.S * self.S
+        for a, per in arrays:
+            if a is None:
+                continue
+            _ptr(a, None, "images")
+            if idx is None and a.numel() != B * per * S2:
+                raise ValueError(f"{a.numel()} elements, expected {B * per * S2}")
+            if a.numel() % (per * S2):
+                raise ValueError(f"{a.numel()} elements: not whole {per} x {self.S}^2 fields")
         if idx is None:
             return None
         if not (isinstance(idx, torch.Tensor) and idx.is_cuda and idx.dtype == torch.int32
                 and idx.is_contiguous() and idx.numel() == B):
             raise TypeError("idx must be a contiguous int32 CUDA tensor of B entries")
+        count = min(a.numel() // (per * S2) for a, per in arrays if a is not None)
+        if B and (int(idx.min()) < 0 or int(idx.max()) >= count):
+            raise ValueError(f"idx outside the {count} pairs of the arrays")
         return ctypes.c_void_p(idx.data_ptr())
 
     def set_params(self, theta):
@@ -639,7 +660,7 @@ class UNet:
         self._call("reg_unet_set_conv_path", int(path))
 
     def forward(self, B, m_R, m_T, v, idx=None):
-        self._call("reg_unet_forward", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+        self._call("reg_unet_forward", int(B), self._idx(idx, B, (m_R, 1), (m_T, 1)), _ptr(m_R, name="m_R"),
                    _ptr(m_T, name="m_T"), _ptr(v, 2 * B * self.S * self.S, "v"))
 
     def gradients(self, B, m_R, m_T, v_target, idx=None):
@@ -647,14 +668,16 @@ class UNet:
         import numpy as np
         g = np.empty(self.param_count(), dtype=np.float32)
         loss = ctypes.c_double()
-        self._call("reg_unet_gradients", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+        self._call("reg_unet_gradients", int(B), self._idx(idx, B, (m_R, 1), (m_T, 1), (v_target, 2)),
+                   _ptr(m_R, name="m_R"),
                    _ptr(m_T, name="m_T"), _ptr(v_target, name="v_target"),
                    g.ctypes.data_as(ctypes.c_void_p), ctypes.byref(loss))
         return loss.value, g
 
     def train_step(self, B, m_R, m_T, v_target, lr, idx=None):
         loss = ctypes.c_double()
-        self._call("reg_unet_train_step", int(B), self._idx(idx, B), _ptr(m_R, name="m_R"),
+        self._call("reg_unet_train_step", int(B), self._idx(idx, B, (m_R, 1), (m_T, 1), (v_target, 2)),
+                   _ptr(m_R, name="m_R"),
                    _ptr(m_T, name="m_T"), _ptr(v_target, name="v_target"), ctypes.c_float(lr),
                    ctypes.byref(loss))
         return loss.value

@@ -128,9 +128,10 @@ def test_spectral_operators(regnk, n1, n2):
     # bounded symbol (|sigma| <= 1) on white noise (three quarters of its
     # energy in the band): element-wise against the oracle at the
     # interpolation bar
-    w = np.random.default_rng(14).standard_normal((n2, n1)).astype(np.float32)
-    R.spectral(regnk.REG_SPEC_HIGHPASS, dev(w), out1)
-    assert rel(host(out1, (n2, n1)), spectral.highpass(w.astype(np.float64))) < 1e-5
+    w = np.random.default_rng(14).standard_normal((2, n2, n1)).astype(np.float32)
+    R.spectral(regnk.REG_SPEC_HIGHPASS, dev(w), out2)
+    high_w = np.stack([spectral.highpass(w[c].astype(np.float64)) for c in range(2)])
+    assert rel(host(out2, (2, n2, n1)), high_w) < 1e-5
     R.spectral(regnk.REG_SPEC_PREFILTER, ud, out1)
     assert rel(host(out1, (n2, n1)), spectral.spline_prefilter(u)) < 1e-5
     R.close()
