@@ -25,14 +25,20 @@ what spectral.py, interp.py, transport.py and problem.py compute for d = 2:
   dropped), compressible (K = I), trapezoidal rule in time;
 * the inexact Newton-Krylov solve of §3.4.1 with PCG and the spectral
   preconditioner P_REG = (beta A)^-1 (eq. reg-precond), the steps of
-  solver.Solver.solve.
+  solver.Solver.solve;
+* the deformation map y (u = y - x, the composition of the departure maps)
+  and det grad y (§2, §4), as transport.deformation_map and
+  spectral.det_grad_map do in 2D.
 
 Pinned in tests/test_oracle_3d.py: spectral operators exact on trigonometric
 polynomials, integral shifts exact, nodal interpolation, reduction to the 2D
 oracle on fields constant along x_3 with v_3 = 0 (J, g, H v~ and the whole
 solve), the gradient against central finite differences of J, and the
 Hessian's symmetry and agreement with finite differences of the gradient at
-zero residual.
+zero residual; the deformation map by the shear flow (exact u and det = 1),
+a constant velocity (u = -c), reduction to the 2D map and determinant, and
+m_T o y approaching the state solve's m_1 under grid refinement; the
+determinant's expansion against numpy.linalg.det.
 """
 
 import numpy as np
@@ -188,6 +194,35 @@ def trapezoid_weights(nt):
     w[0] = 0.5
     w[-1] = 0.5
     return w
+
+
+# -- deformation map -------------------------------------------------------------
+def deformation_map(v, nt, kind="spline"):
+    """Displacement u = y - x (physical units, (3, n3, n2, n1)) of the
+    deformation map y with m_1 = m_T o y (§2, computed from v after the
+    solve): y(x) is where the characteristic through x at t = 1 was at t = 0,
+    the composition of the nt departure maps X_D. From u_0 = 0, each step
+    interpolates the previous displacement at the departure points and adds
+    the step's own: u_j = u_{j-1}(X_D) + (X_D - x)."""
+    n1, n2, n3 = _shape(v)
+    h = [2.0 * np.pi / n for n in (n1, n2, n3)]
+    dX = characteristic(v, nt, kind, backward=False)
+    u = np.zeros((3,) + v.shape[1:])
+    for _ in range(nt):
+        u = np.stack([at_departure(u[c], dX, kind) + h[c] * dX[c] for c in range(3)])
+    return u
+
+
+def det_grad_map(u):
+    """det grad y for y = x + u (u periodic, (3, n3, n2, n1)): the determinant
+    of J = I + grad u, J[a][b] = delta_ab + d_b u_a, with spectral derivatives,
+    expanded along the first row (the quantity bounded in the beta selection
+    of §4)."""
+    d = [grad(u[a]) for a in range(3)]    # d[a][b] = d_b u_a
+    J = [[(1.0 if a == b else 0.0) + d[a][b] for b in range(3)] for a in range(3)]
+    return (J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1])
+            - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0])
+            + J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]))
 
 
 # -- the problem -----------------------------------------------------------------

@@ -155,3 +155,59 @@ def test_solve_reduces_to_the_2d_solve():
     for c in range(2):
         assert np.max(np.abs(v3[c] - tile(v2[c]))) < 1e-8 * np.max(np.abs(v2))
     assert np.max(np.abs(v3[2])) < 1e-8 * np.max(np.abs(v2))
+
+
+@pytest.mark.parametrize("kind", ["spline", "lagrange"])
+def test_deformation_map_shear_and_constant_velocity(kind):
+    """Shear flow v = (a sin x_2, 0, 0): every characteristic keeps x_2, so
+    y = x - v, u = (-a sin x_2, 0, 0) exactly and det grad y = 1 (a unit
+    triangular J); a constant velocity c gives u = -c."""
+    n1, n2, n3, nt, a = 16, 12, 8, 4, 0.3
+    x1, x2, x3 = grid3(n1, n2, n3)
+    z = np.zeros_like(x1)
+    v = np.stack([a * np.sin(x2), z, z])
+    u = d3.deformation_map(v, nt, kind)
+    assert np.max(np.abs(u[0] + a * np.sin(x2))) < 1e-12
+    assert np.max(np.abs(u[1])) < 1e-12 and np.max(np.abs(u[2])) < 1e-12
+    assert np.max(np.abs(d3.det_grad_map(u) - 1.0)) < 1e-12
+    c = np.array([0.37, -0.21, 0.55])
+    u = d3.deformation_map(np.stack([np.full_like(x1, cc) for cc in c]), nt, kind)
+    for k in range(3):
+        assert np.max(np.abs(u[k] + c[k])) < 1e-12
+
+
+def test_deformation_map_reduces_to_2d():
+    from oracle import spectral
+    from oracle import transport as transport2
+    n, n3, nt = 16, 4, 4
+    v2 = inputs.random_velocity(n, seed=21, vmax=0.5)
+    tile = lambda a: np.repeat(a[None], n3, axis=0)
+    v3 = np.stack([tile(v2[0]), tile(v2[1]), np.zeros((n3, n, n))])
+    u2 = transport2.deformation_map(v2, nt, "spline")
+    u3 = d3.deformation_map(v3, nt, "spline")
+    for c in range(2):
+        assert np.max(np.abs(u3[c] - tile(u2[c]))) < 1e-12
+    assert np.max(np.abs(u3[2])) < 1e-14
+    assert np.max(np.abs(d3.det_grad_map(u3) - tile(spectral.det_grad_map(u2)))) < 1e-12
+
+
+def test_det_grad_map_expansion_and_composition():
+    """The first-row expansion equals numpy's determinant of I + grad u at
+    every node; interpolating m_T at y reproduces the state solve's m_1 up to
+    the interpolation error, which falls with the grid (16^3 -> 32^3)."""
+    n, nt = 12, 4
+    u = 0.4 * inputs.random_velocity3(n, n, n, seed=23, kmax=2, vmax=1.0)
+    d = np.stack([d3.grad(u[a]) for a in range(3)])           # d[a, b] = d_b u_a
+    J = np.moveaxis(d, (0, 1), (-2, -1)) + np.eye(3)
+    assert np.max(np.abs(d3.det_grad_map(u) - np.linalg.det(J))) < 1e-12
+    errs = []
+    for n in (16, 32):
+        m_T = inputs.random_field3(n, n, n, seed=24, kmax=2)
+        v = inputs.random_velocity3(n, n, n, seed=25, kmax=2, vmax=0.3)
+        m1 = d3.Problem3(np.zeros_like(m_T), m_T, nt, 1e-2).state_solve(v)
+        uy = d3.deformation_map(v, nt)
+        h = 2.0 * np.pi / n
+        X = d3.node_coordinates(n, n, n)
+        my = d3.interp(m_T, X[0] + uy[0] / h, X[1] + uy[1] / h, X[2] + uy[2] / h, "spline")
+        errs.append(np.linalg.norm(my - m1) / np.linalg.norm(m1))
+    assert errs[0] < 1e-2 and errs[1] < errs[0] / 4, errs
