@@ -543,6 +543,79 @@ def measurement_c2(dev, hbm, l2_bytes):
             "rows": out}
 
 
+def d3_bytes_per_point(nt, lagrange=False):
+    """Algorithmic bytes per grid point of one 3D GN matvec, summed over its
+    kernels (each kernel's inputs read once, outputs written once): the
+    prefilter of v~ (3 fields x 3 axis passes x 8 B), the first incremental
+    state step (76 B), nt - 1 more with their prefilters (68 + 24 B),
+    lambda~_nt with the first term of b~ (32 B), nt adjoint steps with their
+    prefilters (64 + 24 B), and beta A v~ + b~ on two packed complex fields
+    (pack 28 B, six FFT passes 192 B, multiply 32 B, unpack and add 40 B).
+    Cubic Lagrange has no prefilter passes."""
+    pre = 0 if lagrange else 24
+    return 3 * pre + 76 + (nt - 1) * (68 + pre) + 32 + nt * (64 + pre) + 292
+
+
+def measurement_3d(dev, hbm, sizes=(128, 256), nt=4):
+    """The 3D path (row f4): GN matvec, J + gradient at a new velocity (state
+    solve included) and state transport at n^3 through the C ABI (CUDA
+    events, median), the matvec's roofline in the algorithmic bytes of its
+    kernels, and one Newton-Krylov solve at the smallest size."""
+    import torch
+    from paper_1604_02153_gb300 import inputs, regnk
+    f = lambda a: torch.tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device=dev)
+    rows = []
+    for n in sizes:
+        for lagrange in ((False, True) if n == max(sizes) else (False,)):
+            m_T = f(inputs.random_field3(n, n, n, seed=9, kmax=4))
+            vstar = f(inputs.random_velocity3(n, n, n, seed=10, kmax=3, vmax=0.3))
+            u = f(inputs.random_velocity3(n, n, n, seed=8, kmax=3, vmax=1.0))
+            R = regnk.Registration3(n, n, n, nt, 1e-2, interp=regnk.REG_INTERP_LAGRANGE
+                                    if lagrange else regnk.REG_INTERP_SPLINE)
+            m_R = torch.empty_like(m_T)
+            R.transport(vstar, m_T, m_R)
+            R.set_images(m_R, m_T)
+            v = 0.5 * vstar
+            g = torch.empty_like(v)
+            H = torch.empty_like(v)
+            m1 = torch.empty_like(m_T)
+            R.objective_gradient(v, g)
+            t_mv = _median_ms(lambda: R.hessian_matvec(v, u, H), reps=5, inner=10, warm=3)
+            va, vb = v, v * (1.0 + 1e-3)
+            flip = [0]
+
+            def grad():
+                flip[0] ^= 1
+                R.objective_gradient(va if flip[0] else vb, g)
+            t_gr = _median_ms(grad, reps=5, inner=4, warm=2)
+            t_tr = _median_ms(lambda: R.transport(v, m_T, m1), reps=5, inner=10, warm=3)
+            N = n ** 3
+            b_mv = float(N) * d3_bytes_per_point(nt, lagrange)
+            row = {"grid": [n, n, n], "nt": nt, "interp": "lagrange" if lagrange else "spline",
+                   "matvec_ms": t_mv, "gradient_at_new_velocity_ms": t_gr, "transport_ms": t_tr,
+                   "matvec_algorithmic_bytes": b_mv,
+                   "roofline_matvec": {"achieved": b_mv / (t_mv / 1e3) / 1e9, "peak": hbm,
+                                       "unit": "GB/s", "frac": b_mv / (t_mv / 1e3) / 1e9 / hbm}}
+            if n == min(sizes) and not lagrange:
+                x = torch.zeros_like(v)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                info = R.solve(x, 1e-2)
+                e1.record()
+                torch.cuda.synchronize()
+                row["solve"] = {"gtol": 1e-2, "beta": 1e-2, "seconds": e0.elapsed_time(e1) / 1e3,
+                                "newton_iters": info["newton_iters"], "pcg_iters": info["pcg_iters"],
+                                "gnorm_rel": info["gnorm_rel"]}
+            rows.append(row)
+            R.close()
+            del m_T, vstar, u, m_R, v, g, H, m1
+    return {"what": "3D random-field pair (m_T k <= 4, v* k <= 3, max |v*| 0.3, m_R = m_T "
+                    "transported by v*), evaluated at v = v*/2, beta 1e-2, P_REG, CUDA events "
+                    "(median); matvec bytes per point summed over its kernels "
+                    "(380 + 180 nt with splines)", "rows": rows}
+
+
 def aggregate_ranks(dist, device, total_ms, matvecs, e2e_ms, e2e_matvecs):
     """Whole-job figures over replicas: time = max over ranks, work = sum.
 
@@ -1018,6 +1091,7 @@ def main():
             l2 = torch.cuda.get_device_properties(dev).L2_cache_size
             line["fft_comparator"] = fft_comparator(dev, hbm)
             line["config_256_512"] = measurement_c2(dev, hbm, l2)
+            line["grids_3d"] = measurement_3d(dev, hbm)
             # the batch workload's own coarse model (the problems' nt and splines)
             bargs = argparse.Namespace(**vars(args))
             bargs.coarse_nt, bargs.coarse_interp = 0, "spline"

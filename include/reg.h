@@ -442,6 +442,13 @@ reg_status reg3_set_stream(reg3_ctx* ctx, void* cuda_stream);
 reg_status reg3_set_images(reg3_ctx* ctx, const float* m_R, const float* m_T);
 /* m1 = the state solve of eq. state-slm from m0 with velocity v (3 fields) */
 reg_status reg3_transport(reg3_ctx* ctx, const float* v, const float* m0, float* m1);
+/* Deformation map of v (§2: m_1 = m_T o y, from v after the solve): u = y - x
+ * (3 fields, physical units), the composition of the nt departure maps
+ * (u_j = u_{j-1}(X_D) + X_D - x, the context's interpolation model), and,
+ * if det is not NULL, det grad y = det(I + grad u) with spectral derivatives
+ * (one field; the quantity §4 bounds when choosing beta). u and det must not
+ * overlap (REG_EINVAL). The next call at a velocity rebuilds its state. */
+reg_status reg3_deformation_map(reg3_ctx* ctx, const float* v, float* u, float* det);
 /* REG_SPEC_GRAD (1 -> 3 fields), REG_SPEC_DIV (3 -> 1), REG_SPEC_REGPOW
  * (3 -> 3, (beta A)^s; for s != 1 the zero entry of A's symbol is one, so
  * the mean is scaled by beta^s, eq. reg-precond) on the 3D grid; other ops

@@ -695,6 +695,38 @@ k3_multiply_pairs(Dims d, int op, int P, float beta, int p, float s,
   }
 }
 
+// u_c += h_c dX_c (the step's own displacement, cells -> physical units)
+__global__ void __launch_bounds__(kT)
+k3_add_disp(long long N, float h1, float h2, float h3, const float* __restrict__ dX,
+            float* __restrict__ u) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= N) return;
+  u[idx] = u[idx] + h1 * __ldg(dX + idx);
+  u[N + idx] = u[N + idx] + h2 * __ldg(dX + N + idx);
+  u[2 * N + idx] = u[2 * N + idx] + h3 * __ldg(dX + 2 * N + idx);
+}
+
+// det (I + grad u) expanded along its first row; d12 holds grad u_1 then
+// grad u_2 (six fields), d3 grad u_3 (three), field b of grad u_a = d_b u_a
+__global__ void __launch_bounds__(kT)
+k3_det_grad(long long N, const float* __restrict__ d12, const float* __restrict__ d3f,
+            float* __restrict__ det) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= N) return;
+  float J[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    J[0][b] = (b == 0 ? 1.f : 0.f) + __ldg(d12 + b * N + idx);
+    J[1][b] = (b == 1 ? 1.f : 0.f) + __ldg(d12 + (3 + b) * N + idx);
+    J[2][b] = (b == 2 ? 1.f : 0.f) + __ldg(d3f + b * N + idx);
+  }
+  det[idx] = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+             J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+             J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
 inline unsigned nb(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 }  // namespace d3
@@ -1185,6 +1217,41 @@ reg_status reg3_transport(reg3_ctx* c, const float* v, const float* m0, float* m
     }
     check(c, cudaMemcpyAsync(m1, a, N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy m1");
     c->have_v = false;   // the cached state no longer matches v
+    c->have_G = false;
+  });
+}
+
+// u = y - x of the deformation map of v (physical units, 3 fields) and, if
+// det is not NULL, det grad y (§2, §4)
+reg_status reg3_deformation_map(reg3_ctx* c, const float* v, float* u, float* det) {
+  if (!c || !v || !u || unaligned(v) || unaligned(u) || (det && unaligned(det))) return REG_EINVAL;
+  const long long N = c->d.N;
+  if (det && det < u + 3 * N && u < det + N) return REG_EINVAL;   // overlapping outputs
+  return guarded(c, [&] {
+    if (v != c->v)
+      check(c, cudaMemcpyAsync(c->v, v, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy v");
+    departure(c, coefficients(c, c->v, 3, c->cv));
+    const float h1 = (float)(2.0 * M_PI / c->d.n1), h2 = (float)(2.0 * M_PI / c->d.n2),
+                h3 = (float)(2.0 * M_PI / c->d.n3);
+    // u_0 = 0, u_j = u_{j-1}(X_D) + h dX (the first step without the gather of zeros)
+    float* a = c->kx;
+    float* nxt = c->kr;
+    launch_fill(a, 3 * N, 0.f, c->st);
+    launch_k(k3_add_disp, dim3(nb(N)), dim3(kT), 0, c->st, N, h1, h2, h3, (const float*)c->dX, a);
+    for (int j = 2; j <= c->nt; ++j) {
+      gather(c, a, 3, c->dX, nxt, c->c3);
+      launch_k(k3_add_disp, dim3(nb(N)), dim3(kT), 0, c->st, N, h1, h2, h3, (const float*)c->dX, nxt);
+      std::swap(a, nxt);
+    }
+    check(c, cudaMemcpyAsync(u, a, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy u");
+    if (det) {
+      grad_pair(c, a, c->gm);                                        // grad u_1, grad u_2
+      spectral3(c, OP3_GRAD, 0.0, a + 2 * N, 1, c->b, 3, nullptr);   // grad u_3
+      launch_k(k3_det_grad, dim3(nb(N)), dim3(kT), 0, c->st, N, (const float*)c->gm,
+               (const float*)c->b, det);
+    }
+    check_launch(c, "deformation map");
+    c->have_v = false;   // the characteristics and gradients of the cached velocity are gone
     c->have_G = false;
   });
 }

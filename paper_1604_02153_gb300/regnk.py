@@ -117,6 +117,7 @@ _SIGNATURES = {
     "reg3_set_images": [_P, _P, _P],
     "reg3_transport": [_P, _P, _P, _P],
     "reg3_spectral": [_P, _I, _D, _P, _P],
+    "reg3_deformation_map": [_P, _P, _P, _P],
     "reg3_objective_gradient": [_P, _P, ctypes.POINTER(_D), _P],
     "reg3_hessian_matvec": [_P, _P, _P, _P],
     "reg3_solve": [_P, _P, _D, ctypes.POINTER(reg_info)],
@@ -461,6 +462,10 @@ class Registration3:
     def transport(self, v, m0, m1):
         self._call("reg3_transport", _ptr(v, 3 * self.N, "v"), _ptr(m0, self.N, "m0"),
                    _ptr(m1, self.N, "m1"))
+
+    def deformation_map(self, v, u, det=None):
+        self._call("reg3_deformation_map", _ptr(v, 3 * self.N, "v"), _ptr(u, 3 * self.N, "u"),
+                   _ptr(det, self.N, "det"))
 
     def spectral(self, op, x, out, s=1.0):
         nin = self.N if op == REG_SPEC_GRAD else 3 * self.N

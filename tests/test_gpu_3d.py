@@ -198,3 +198,30 @@ def test_box_and_global_gathers(regnk, interp, vmax):
         R.close()
     for a, b in zip(out[0], out[1]):
         assert rel(b, a) < 1e-6
+
+
+@pytest.mark.parametrize("interp", ["spline", "lagrange"])
+def test_deformation_map(regnk, interp):
+    """u = y - x and det grad y against the oracle (the composed gathers
+    within 1e-4 relative L2, the determinant within 1e-4 of the oracle's at
+    every node); the shear flow v = (a sin x_2, 0, 0) gives u = (-a sin x_2,
+    0, 0) and det = 1 to FP32 rounding."""
+    nt = 4
+    kind = regnk.REG_INTERP_SPLINE if interp == "spline" else regnk.REG_INTERP_LAGRANGE
+    v = f32(inputs.random_velocity3(N1, N2, N3, seed=31, kmax=3, vmax=0.5))
+    R = regnk.Registration3(N1, N2, N3, nt, 1e-2, interp=kind)
+    u = torch.empty(3 * R.N, device="cuda")
+    det = torch.empty(R.N, device="cuda")
+    R.deformation_map(dev(v), u, det)
+    u_ref = d3.deformation_map(v, nt, interp)
+    assert rel(host(u, (3, N3, N2, N1)), u_ref) < 1e-4
+    assert np.max(np.abs(host(det, (N3, N2, N1)) - d3.det_grad_map(u_ref))) < 1e-4
+    K, J, I = np.meshgrid(*(np.arange(n) * 2 * np.pi / n for n in (N3, N2, N1)), indexing="ij")
+    a = 0.3
+    vs = np.stack([a * np.sin(J), np.zeros_like(J), np.zeros_like(J)])
+    R.deformation_map(dev(vs), u, det)
+    us = host(u, (3, N3, N2, N1))
+    assert np.max(np.abs(us[0] + a * np.sin(J))) < 1e-5
+    assert np.max(np.abs(us[1])) < 1e-6 and np.max(np.abs(us[2])) < 1e-6
+    assert np.max(np.abs(host(det, (N3, N2, N1)) - 1.0)) < 1e-5
+    R.close()
