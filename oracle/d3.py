@@ -28,7 +28,10 @@ what spectral.py, interp.py, transport.py and problem.py compute for d = 2:
   solver.Solver.solve;
 * the deformation map y (u = y - x, the composition of the departure maps)
   and det grad y (§2, §4), as transport.deformation_map and
-  spectral.det_grad_map do in 2D.
+  spectral.det_grad_map do in 2D;
+* the two-level preconditioner P_2L of §3.4.2 (spectral restriction,
+  prolongation and high-pass on the 3-torus, the coarse split operator with
+  CHEB(k), Lanczos and e_min bounds) in Solver3, the steps of solver.Solver.
 
 Pinned in tests/test_oracle_3d.py: spectral operators exact on trigonometric
 polynomials, integral shifts exact, nodal interpolation, reduction to the 2D
@@ -38,7 +41,10 @@ Hessian's symmetry and agreement with finite differences of the gradient at
 zero residual; the deformation map by the shear flow (exact u and det = 1),
 a constant velocity (u = -c), reduction to the 2D map and determinant, and
 m_T o y approaching the state solve's m_1 under grid refinement; the
-determinant's expansion against numpy.linalg.det.
+determinant's expansion against numpy.linalg.det; spectral restriction,
+prolongation and high-pass on trigonometric polynomials, R P = I, P R + H =
+I and reduction to the 2D operators; the P_2L solve by reduction to the 2D
+P_2L solve (same Chebyshev bounds), and Solver3 with P_REG = Problem3.solve.
 """
 
 import numpy as np
@@ -102,6 +108,61 @@ def reg_power(v, beta, reg_norm, s):
         gam = np.where(gam == 0, 1, gam)
     g = (beta * gam.astype(np.float64)) ** s
     return np.stack([ifftn_real(g * fftn(v[c])) for c in range(v.shape[0])])
+
+
+def lowpass_mask3(n1, n2, n3):
+    """Modes with |k_i| < n_i / 4 on every axis (§3.4.2 "Filters"): exactly
+    those the grid of n_i / 2 points holds without its own Nyquist modes."""
+    K1, K2, K3 = _k_grids(n1, n2, n3, zero_nyquist=False)
+    return (np.abs(K1) < n1 / 4) & (np.abs(K2) < n2 / 4) & (np.abs(K3) < n3 / 4)
+
+
+def highpass3(u):
+    n1, n2, n3 = _shape(u)
+    return ifftn_real(~lowpass_mask3(n1, n2, n3) * fftn(u))
+
+
+def _kept(n):
+    """Fine-grid and coarse-grid FFT indices of the wavenumbers |k| < n / 4."""
+    k = np.arange(-(n // 4) + 1, n // 4)
+    return k % n, k % (n // 2)
+
+
+def restrict3(u):
+    """Spectral restriction to the grid of n_i / 2 points (§3.4.2): the
+    trigonometric interpolant of the modes the cut-off keeps, sampled on
+    the coarse grid (numpy's inverse transform is normalised, so the kept
+    coefficients scale by N_c / N_f)."""
+    n1, n2, n3 = _shape(u)
+    (f1, c1), (f2, c2), (f3, c3) = _kept(n1), _kept(n2), _kept(n3)
+    U = fftn(u)
+    C = np.zeros((n3 // 2, n2 // 2, n1 // 2), dtype=complex)
+    C[np.ix_(c3, c2, c1)] = U[np.ix_(f3, f2, f1)] / 8.0
+    return ifftn_real(C)
+
+
+def prolong3(u):
+    """Spectral prolongation to the grid of 2 n_i points by zero padding; the
+    coarse Nyquist modes are dropped, so restrict3(prolong3(u)) = u on fields
+    without them and prolong3(restrict3(u)) is the low-pass part of u."""
+    c1n, c2n, c3n = _shape(u)
+    (f1, c1), (f2, c2), (f3, c3) = _kept(2 * c1n), _kept(2 * c2n), _kept(2 * c3n)
+    C = fftn(u)
+    U = np.zeros((2 * c3n, 2 * c2n, 2 * c1n), dtype=complex)
+    U[np.ix_(f3, f2, f1)] = C[np.ix_(c3, c2, c1)] * 8.0
+    return ifftn_real(U)
+
+
+def restrict_vec3(v):
+    return np.stack([restrict3(v[c]) for c in range(v.shape[0])])
+
+
+def prolong_vec3(v):
+    return np.stack([prolong3(v[c]) for c in range(v.shape[0])])
+
+
+def highpass_vec3(v):
+    return np.stack([highpass3(v[c]) for c in range(v.shape[0])])
 
 
 def apply_reg(v, beta, reg_norm):
@@ -281,6 +342,11 @@ class Problem3:
         J = self.objective(v)
         return J, self.gradient()
 
+    def data_matvec(self, vt):
+        """The Gauss-Newton data term Q v~ = H v~ - beta A v~."""
+        vt = np.asarray(vt, dtype=np.float64)
+        return self.hessian_matvec(vt) - apply_reg(vt, self.beta, self.reg_norm)
+
     def hessian_matvec(self, vt):
         """Gauss-Newton H v~ at the velocity of the last state solve."""
         nt, ht = self.nt, self.ht
@@ -338,4 +404,119 @@ class Problem3:
             info["newton_iters"] += 1
         info["J"] = J
         info["gnorm_rel"] = rel
+        return v, info
+
+
+# -- the two-level preconditioner -------------------------------------------------
+class Solver3:
+    """The inexact Newton-Krylov solve of Problem3.solve with P_REG or the
+    two-level preconditioner P_2L of §3.4.2, read as solver.Solver reads it
+    in 2D:
+        r'  = (beta A)^-1/2 r,  r_c = R r',
+        s_c = (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2)^-1 r_c  by CHEB(k),
+        z   = (beta A)^-1/2 (P s_c + H r')
+    with R, P the spectral restriction and prolongation, H the high-pass
+    filter and Q_c the Gauss-Newton data term of the coarse problem (m_R,
+    m_T and v restricted, the same nt). CHEB bounds: e_max from Lanczos on the
+    coarse split operator at v = 0 (lanczos_steps steps from lanczos_v0,
+    times emax_safety), e_min = min over the coarse modes of 1 + 1/(beta
+    gamma_k)."""
+
+    def __init__(self, problem, precond="2L", cheb_iters=10, gabs=1e-5, max_newton=50,
+                 max_pcg=100, lanczos_steps=30, emax_safety=1.05, lanczos_v0=None, c1=1e-4,
+                 max_backtracks=10):
+        self.p = problem
+        self.precond = precond
+        self.cheb_iters = cheb_iters
+        self.gabs = gabs
+        self.max_newton = max_newton
+        self.max_pcg = max_pcg
+        self.lanczos_steps = lanczos_steps
+        self.emax_safety = emax_safety
+        self.lanczos_v0 = lanczos_v0
+        self.c1 = c1
+        self.max_backtracks = max_backtracks
+        self.eig = None
+        self.coarse_matvecs = 0
+        self.coarse = None
+        if precond == "2L":
+            p = problem
+            self.coarse = Problem3(restrict3(p.m_R), restrict3(p.m_T), p.nt, p.beta, p.reg_norm,
+                                   p.kind)
+
+    def coarse_split_op(self, s):
+        c = self.coarse
+        u = reg_power(s, c.beta, c.reg_norm, -0.5)
+        q = c.data_matvec(u)
+        self.coarse_matvecs += 1
+        return s + reg_power(q, c.beta, c.reg_norm, -0.5)
+
+    def estimate_eigenvalues(self):
+        c = self.coarse
+        shape = (3,) + c.m_R.shape
+        c.state_solve(np.zeros(shape))
+        if self.lanczos_v0 is None:
+            v0 = np.random.default_rng(1234).uniform(-1.0, 1.0, shape)
+        else:
+            v0 = np.asarray(self.lanczos_v0, dtype=np.float64).reshape(shape)
+        _, rmax, _ = krylov.lanczos_extremal(self.coarse_split_op, v0, self.lanczos_steps)
+        gam = reg_symbol(c.n1, c.n2, c.n3, c.reg_norm).astype(np.float64)
+        gam = np.where(gam == 0, 1.0, gam)
+        emin = float(np.min(1.0 + 1.0 / (c.beta * gam)))
+        self.eig = {"emin": emin, "emax": rmax * self.emax_safety}
+        return self.eig
+
+    def apply_precond(self, r):
+        p = self.p
+        if self.precond == "REG":
+            return reg_power(r, p.beta, p.reg_norm, -1)
+        r1 = reg_power(r, p.beta, p.reg_norm, -0.5)
+        sc, _ = krylov.chebyshev(self.coarse_split_op, restrict_vec3(r1), self.eig["emin"],
+                                 self.eig["emax"], self.cheb_iters)
+        return reg_power(prolong_vec3(sc) + highpass_vec3(r1), p.beta, p.reg_norm, -0.5)
+
+    def solve(self, v0, gtol):
+        """Problem3.solve's loop with this preconditioner; returns (v, info)."""
+        p = self.p
+        z = np.zeros((3,) + p.m_R.shape)
+        _, g_ref = p.objective_gradient(z)
+        gref_inf = float(np.max(np.abs(g_ref)))
+        gref_2 = float(np.sqrt(np.sum(g_ref * g_ref)))
+        if self.precond == "2L" and self.eig is None:
+            self.estimate_eigenvalues()
+        v = np.array(v0, dtype=np.float64, copy=True)
+        J, g = p.objective_gradient(v)
+        info = {"J0": J, "newton_iters": 0, "pcg_iters": 0, "matvecs": 0,
+                "line_search_fail": False}
+        rel = 1.0
+        for k in range(self.max_newton + 1):
+            ginf = float(np.max(np.abs(g)))
+            rel = ginf / gref_inf
+            if rel <= gtol or ginf <= self.gabs or k == self.max_newton:
+                break
+            eta = min(0.5, float(np.sqrt(np.sum(g * g))) / gref_2)
+            if self.coarse is not None:
+                self.coarse.state_solve(restrict_vec3(v))
+            vt, kinfo = krylov.pcg(p.hessian_matvec, -g, self.apply_precond, eta, self.max_pcg)
+            info["pcg_iters"] += kinfo["iters"]
+            info["matvecs"] += kinfo["matvecs"]
+            slope = p.inner(g, vt)
+            alpha, accepted = 1.0, False
+            for _ in range(self.max_backtracks + 1):
+                Jt = p.objective(v + alpha * vt)
+                if Jt <= J + self.c1 * alpha * slope:
+                    accepted = True
+                    break
+                alpha *= 0.5
+            if not accepted:
+                info["line_search_fail"] = True
+                p.state_solve(v)
+                break
+            v = v + alpha * vt
+            J = Jt
+            g = p.gradient()
+            info["newton_iters"] += 1
+        info["J"] = J
+        info["gnorm_rel"] = rel
+        info["coarse_matvecs"] = self.coarse_matvecs
         return v, info

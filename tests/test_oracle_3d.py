@@ -211,3 +211,63 @@ def test_det_grad_map_expansion_and_composition():
         my = d3.interp(m_T, X[0] + uy[0] / h, X[1] + uy[1] / h, X[2] + uy[2] / h, "spline")
         errs.append(np.linalg.norm(my - m1) / np.linalg.norm(m1))
     assert errs[0] < 1e-2 and errs[1] < errs[0] / 4, errs
+
+
+def test_restriction_prolongation_and_filters():
+    """R of a mode below the cut-off is that mode on the coarse grid; R P = I
+    on coarse fields without Nyquist modes; P R + H = I; on fields constant
+    along x_3 all three reduce to the 2D operators."""
+    from oracle import spectral
+    n1, n2, n3 = 32, 16, 8
+    x1, x2, x3 = grid3(n1, n2, n3)
+    c1, c2, c3 = grid3(n1 // 2, n2 // 2, n3 // 2)
+    f = lambda a, b, c: np.cos(2 * a - 3 * b + c) + 0.5 * np.sin(a + b)
+    assert np.max(np.abs(d3.restrict3(f(x1, x2, x3)) - f(c1, c2, c3))) < 1e-12
+    assert np.max(np.abs(d3.prolong3(f(c1, c2, c3)) - f(x1, x2, x3))) < 1e-12
+    u = np.random.default_rng(3).standard_normal((n3, n2, n1))
+    uc = d3.restrict3(u)
+    assert np.max(np.abs(d3.restrict3(d3.prolong3(uc)) - uc)) < 1e-12
+    assert np.max(np.abs(d3.prolong3(uc) + d3.highpass3(u) - u)) < 1e-12
+    u2 = np.random.default_rng(4).standard_normal((n2, n1))
+    tile = lambda a, k: np.repeat(a[None], k, axis=0)
+    assert np.max(np.abs(d3.restrict3(tile(u2, n3)) - tile(spectral.restrict(u2), n3 // 2))) < 1e-12
+    assert np.max(np.abs(d3.highpass3(tile(u2, n3)) - tile(spectral.highpass(u2), n3))) < 1e-12
+    w2 = spectral.restrict(u2)
+    assert np.max(np.abs(d3.prolong3(tile(w2, n3 // 2)) - tile(spectral.prolong(w2), n3))) < 1e-12
+
+
+def test_solver3_two_level_reduces_to_the_2d_solve():
+    """The Newton-Krylov solve with P_2L (CHEB(10) coarse solves) on a problem
+    constant along x_3, v_3 = 0 and a Lanczos start vector likewise: every
+    operator of the preconditioner reduces to the 2D one, so with the same
+    Chebyshev bounds (the 3D coarse grid's e_min includes the x_3 modes; the
+    2D solver takes it over) the iterations and the solution are the 2D
+    oracle's; with P_REG Solver3 repeats Problem3.solve."""
+    from oracle.solver import Solver
+    n, n3, nt, beta, gtol = 16, 8, 4, 1e-2, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    tile = lambda a, k: np.repeat(a[None], k, axis=0)
+    lv2 = inputs.splitmix64_uniform(2 * (n // 2) ** 2, 7).reshape(2, n // 2, n // 2)
+    lv3 = np.stack([tile(lv2[0], n3 // 2), tile(lv2[1], n3 // 2), np.zeros((n3 // 2, n // 2, n // 2))])
+    S3 = d3.Solver3(d3.Problem3(tile(m_R, n3), tile(m_T, n3), nt, beta), precond="2L", lanczos_v0=lv3)
+    eig3 = S3.estimate_eigenvalues()
+    S2 = Solver(Problem(m_R, m_T, nt, beta), precond="2L", lanczos_v0=lv2)
+    eig2 = S2.estimate_eigenvalues()
+    assert abs(eig3["emax"] - eig2["emax"]) < 1e-10 * eig2["emax"]
+    assert eig3["emin"] < eig2["emin"]
+    S2.eig["emin"] = eig3["emin"]
+    v2, i2 = S2.solve(np.zeros((2, n, n)), gtol)
+    v3, i3 = S3.solve(np.zeros((3, n3, n, n)), gtol)
+    assert i3["newton_iters"] == i2["newton_iters"] and i3["matvecs"] == i2["matvecs"]
+    assert i3["gnorm_rel"] <= gtol
+    for c in range(2):
+        assert np.max(np.abs(v3[c] - tile(v2[c], n3))) < 1e-8 * np.max(np.abs(v2))
+    assert np.max(np.abs(v3[2])) < 1e-8 * np.max(np.abs(v2))
+    m_T3 = inputs.random_field3(n, n, n, seed=41, kmax=2)
+    m_R3 = d3.Problem3(np.zeros_like(m_T3), m_T3, nt, beta).state_solve(
+        inputs.random_velocity3(n, n, n, seed=42, kmax=2, vmax=0.3))
+    va, ia = d3.Problem3(m_R3, m_T3, nt, beta).solve(np.zeros((3, n, n, n)), gtol)
+    vb, ib = d3.Solver3(d3.Problem3(m_R3, m_T3, nt, beta), precond="REG").solve(np.zeros((3, n, n, n)), gtol)
+    assert ia["newton_iters"] == ib["newton_iters"] and ia["pcg_iters"] == ib["pcg_iters"]
+    assert np.max(np.abs(va - vb)) == 0.0
