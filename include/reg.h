@@ -420,11 +420,15 @@ const char* reg_batch_last_error(const reg_batch* batch);
  * Fields are float32 with x_1 fastest, then x_2, then x_3; vector fields
  * are their three components back to back (3 n1 n2 n3 floats); device
  * pointers, 16-byte aligned, owned by the caller. n_i in {32, 64, 128, 256,
- * 96, 192}. Options as reg_create with precond = REG_PC_REG (the spectral
- * preconditioner; required), compressible, Gauss-Newton; anything else
- * REG_EINVAL. Calls run on the stream of reg3_set_stream (default stream
+ * 96, 192}. Options as reg_create: precond REG_PC_REG (the spectral
+ * preconditioner) or REG_PC_2L (the two-level preconditioner of §3.4.2 with
+ * CHEB(cheb_iters) coarse solves; every n_i / 2 must be a supported size,
+ * the coarse problem has the same nt and interpolation model), compressible,
+ * Gauss-Newton; anything else REG_EINVAL. Calls run on the stream of reg3_set_stream (default stream
  * otherwise). reg3_create allocates (74 + 7 nt) n1 n2 n3 floats of device
- * memory (6.8 GB at 256^3, nt = 4), freed by reg3_destroy. fused_transport 1
+ * memory (6.8 GB at 256^3, nt = 4), with P_2L also a coarse-grid context
+ * (one eighth of that) and 3 n1 n2 n3 floats of coarse work vectors, freed
+ * by reg3_destroy. fused_transport 1
  * (default) gathers from shared-memory boxes around 32 x 8 x 8 tiles when the
  * displacements of the velocity fit one (halo ceil(max |d|) + 2 cells per
  * axis, at most 112 KB), from global memory otherwise; 0 always from global
@@ -462,6 +466,14 @@ reg_status reg3_hessian_matvec(reg3_ctx* ctx, const float* v, const float* vt, f
 /* the inexact Newton-Krylov solve of reg_solve (§3.4.1) with PCG and P_REG;
  * v is the initial guess and receives the result; info may be NULL */
 reg_status reg3_solve(reg3_ctx* ctx, float* v, double gtol, reg_info* info);
+/* z = P^-1 r with the context's preconditioner (3 fields each; P_2L at the
+ * velocity v: its coarse problem is restricted from v, and the Chebyshev
+ * bounds are estimated on first use); synchronises */
+reg_status reg3_precond_apply(reg3_ctx* ctx, const float* v, const float* r, float* z);
+/* Chebyshev bounds of P_2L's coarse split operator at v = 0 (§3.4.2
+ * "Eigenvalue Estimates"; e_max from Lanczos, e_min analytic), estimated by
+ * this call; REG_EINVAL for a P_REG context */
+reg_status reg3_eigen_bounds(reg3_ctx* ctx, double* emin, double* emax);
 const char* reg3_last_error(const reg3_ctx* ctx);
 
 /* ---- Lockstep batches: one launch per step over every problem ------------

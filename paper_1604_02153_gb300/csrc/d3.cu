@@ -727,6 +727,112 @@ k3_det_grad(long long N, const float* __restrict__ d12, const float* __restrict_
              J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
 }
 
+// ---------------------------------------------------------------------------
+// Two-level preconditioner (§3.4.2) on 3D grids: spectra of the fine grid
+// (n_i) and of the coarse grid (n_i / 2), P packed spectra N apart. A fine
+// mode is kept by the cut-off when |k_i| < n_i / 4 on every axis: exactly the
+// coarse grid's modes without its Nyquist planes. e = -1/2 multiplies by
+// (beta |k|^2p)^-1/2 (the split preconditioner's factor), e = 0 by one.
+__device__ __forceinline__ float split_weight(float beta, int p, float e, float k2n) {
+  return e == 0.f ? 1.f : regpow3(beta, p, e, k2n);
+}
+
+// C_q = s w(k) Z_q at the coarse modes below the cut-off, 0 on the coarse
+// Nyquist planes (grid over the coarse points)
+__global__ void __launch_bounds__(kT)
+k3_restrict_spec(Dims df, Dims dc, int P, float s, float beta, int p, float e,
+                 const float2* __restrict__ Z, float2* __restrict__ C) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= dc.N) return;
+  int i, j, k;
+  split3(idx, dc, i, j, k);
+  if (2 * i == dc.n1 || 2 * j == dc.n2 || 2 * k == dc.n3) {
+    for (int q = 0; q < P; ++q) C[q * dc.N + idx] = make_float2(0.f, 0.f);
+    return;
+  }
+  const int k1 = signed_k(i, dc.n1), k2 = signed_k(j, dc.n2), k3 = signed_k(k, dc.n3);
+  const int fi = k1 < 0 ? k1 + df.n1 : k1, fj = k2 < 0 ? k2 + df.n2 : k2,
+            fk = k3 < 0 ? k3 + df.n3 : k3;
+  const long long fidx = ((long long)fk * df.n2 + fj) * df.n1 + fi;
+  const float w = s * split_weight(beta, p, e, (float)(k1 * k1 + k2 * k2 + k3 * k3));
+  for (int q = 0; q < P; ++q) {
+    const float2 z = Z[q * df.N + fidx];
+    C[q * dc.N + idx] = make_float2(w * z.x, w * z.y);
+  }
+}
+
+// H_q = w(k) Z_q above the cut-off, 0 below (grid over the fine points)
+__global__ void __launch_bounds__(kT)
+k3_highpass_spec(Dims df, int P, float beta, int p, float e, const float2* __restrict__ Z,
+                 float2* __restrict__ H) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= df.N) return;
+  int i, j, k;
+  split3(idx, df, i, j, k);
+  const int k1 = signed_k(i, df.n1), k2 = signed_k(j, df.n2), k3 = signed_k(k, df.n3);
+  const bool kept = 4 * abs(k1) < df.n1 && 4 * abs(k2) < df.n2 && 4 * abs(k3) < df.n3;
+  const float w = kept ? 0.f : split_weight(beta, p, e, (float)(k1 * k1 + k2 * k2 + k3 * k3));
+  for (int q = 0; q < P; ++q) {
+    const float2 z = Z[q * df.N + idx];
+    H[q * df.N + idx] = make_float2(w * z.x, w * z.y);
+  }
+}
+
+// out_q = w(k) (sc Sc_q[coarse(k)] below the cut-off, sh H_q above; H may be
+// NULL: 0) on the fine grid: prolongation by zero padding plus the high band
+__global__ void __launch_bounds__(kT)
+k3_prolong_spec(Dims df, Dims dc, int P, float sc, const float2* __restrict__ Sc, float sh,
+                const float2* __restrict__ H, float beta, int p, float e,
+                float2* __restrict__ out) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= df.N) return;
+  int i, j, k;
+  split3(idx, df, i, j, k);
+  const int k1 = signed_k(i, df.n1), k2 = signed_k(j, df.n2), k3 = signed_k(k, df.n3);
+  const bool kept = 4 * abs(k1) < df.n1 && 4 * abs(k2) < df.n2 && 4 * abs(k3) < df.n3;
+  const float w = split_weight(beta, p, e, (float)(k1 * k1 + k2 * k2 + k3 * k3));
+  long long cidx = 0;
+  if (kept) {
+    const int ci = k1 < 0 ? k1 + dc.n1 : k1, cj = k2 < 0 ? k2 + dc.n2 : k2,
+              ck = k3 < 0 ? k3 + dc.n3 : k3;
+    cidx = ((long long)ck * dc.n2 + cj) * dc.n1 + ci;
+  }
+  for (int q = 0; q < P; ++q) {
+    float2 z = make_float2(0.f, 0.f);
+    if (kept) {
+      const float2 c = Sc[q * dc.N + cidx];
+      z = make_float2(sc * c.x, sc * c.y);
+    } else if (H) {
+      const float2 h = H[q * df.N + idx];
+      z = make_float2(sh * h.x, sh * h.y);
+    }
+    out[q * df.N + idx] = make_float2(w * z.x, w * z.y);
+  }
+}
+
+// z = a + i b for two separate real fields; a = Re z, b = Im z back
+__global__ void __launch_bounds__(kT)
+k3_pack_two(const float* __restrict__ a, const float* __restrict__ b, float2* __restrict__ z,
+            long long N) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx < N) z[idx] = make_float2(__ldg(a + idx), __ldg(b + idx));
+}
+
+__global__ void __launch_bounds__(kT)
+k3_unpack_two(const float2* __restrict__ z, float* __restrict__ a, float* __restrict__ b,
+              long long N) {
+  pdl_enter();
+  const long long idx = (long long)blockIdx.x * kT + threadIdx.x;
+  if (idx >= N) return;
+  const float2 v = z[idx];
+  a[idx] = v.x;
+  b[idx] = v.y;
+}
+
 inline unsigned nb(long long n) { return (unsigned)((n + kT - 1) / kT); }
 
 }  // namespace d3
@@ -765,6 +871,15 @@ struct reg3_ctx {
   bool boxes = true;
   Box3 boxX{}, boxY{}, boxV{};
   bool useX = false, useY = false, useV = false;
+  // P_2L (§3.4.2): the coarse problem on the grid of n_i / 2 points (its own
+  // context), the Chebyshev bounds of its split operator and coarse-grid
+  // work vectors (three fields each)
+  reg3_ctx* coarse = nullptr;
+  double emin = 0, emax = 0;
+  bool have_eig = false;
+  int coarse_matvecs = 0;
+  float *pc_rc = nullptr, *pc_sc = nullptr, *pc_r = nullptr, *pc_d = nullptr, *pc_w = nullptr,
+        *pc_u = nullptr, *pc_q = nullptr, *pc_v = nullptr;
   std::vector<void*> allocs;
   std::string err;
 };
@@ -1052,8 +1167,9 @@ void gradient(reg3_ctx* c, float* g) {
   check_launch(c, "gradient");
 }
 
-// Gauss-Newton H v~ = beta A v~ + int lambda~ grad m dt (eq. hessian-matvec)
-void hessian(reg3_ctx* c, const float* vt, float* out) {
+// Gauss-Newton H v~ = beta A v~ + int lambda~ grad m dt (eq. hessian-matvec);
+// data_only: the data term int lambda~ grad m dt alone
+void hessian(reg3_ctx* c, const float* vt, float* out, bool data_only = false) {
   const long long N = c->d.N;
   const int nt = c->nt;
   const float ht = c->ht;
@@ -1076,8 +1192,185 @@ void hessian(reg3_ctx* c, const float* vt, float* out) {
     adjoint_step(c, coefficients(c, lt, 1, c->coef), wb, c->gm + 3 * j * N, lt2);
     std::swap(lt, lt2);
   }
-  spectral3(c, OP3_REGPOW, 1.0, vt, 3, out, 3, c->b);
+  if (data_only)
+    check(c, cudaMemcpyAsync(out, c->b, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  else
+    spectral3(c, OP3_REGPOW, 1.0, vt, 3, out, 3, c->b);
   check_launch(c, "hessian");
+}
+
+// -- two-level preconditioner --------------------------------------------------
+// the three components of a fine-grid vector field restricted to the coarse
+// grid (§3.4.2): one fine transform, the kept modes copied, one coarse
+// transform
+void restrict_to_coarse(reg3_ctx* c, const float* in, float* out) {
+  reg3_ctx* cc = c->coarse;
+  const long long Nf = c->d.N, Nc = cc->d.N;
+  launch_k(k3_pack_pairs, dim3(nb(Nf), 2), dim3(kT), 0, c->st, in, 3, c->zA, Nf);
+  fft3(c, c->zA, 2, false);
+  launch_k(k3_restrict_spec, dim3(nb(Nc)), dim3(kT), 0, c->st, c->d, cc->d, 2, 1.f / (float)Nf, 0.f,
+           0, 0.f, (const float2*)c->zA, cc->zB);
+  fft3(cc, cc->zB, 2, true);
+  launch_k(k3_unpack_pairs, dim3(nb(Nc), 2), dim3(kT), 0, c->st, (const float2*)cc->zB, 0, 0, 3, out,
+           (const float*)nullptr, Nc);
+  check_launch(c, "restriction");
+}
+
+void restrict_images(reg3_ctx* c) {
+  reg3_ctx* cc = c->coarse;
+  const long long Nf = c->d.N, Nc = cc->d.N;
+  launch_k(k3_pack_two, dim3(nb(Nf)), dim3(kT), 0, c->st, (const float*)c->mR, (const float*)c->mT,
+           c->zA, Nf);
+  fft3(c, c->zA, 1, false);
+  launch_k(k3_restrict_spec, dim3(nb(Nc)), dim3(kT), 0, c->st, c->d, cc->d, 1, 1.f / (float)Nf, 0.f,
+           0, 0.f, (const float2*)c->zA, cc->zB);
+  fft3(cc, cc->zB, 1, true);
+  launch_k(k3_unpack_two, dim3(nb(Nc)), dim3(kT), 0, c->st, (const float2*)cc->zB, cc->mR, cc->mT, Nc);
+  check_launch(c, "restriction");
+  cc->have_images = true;
+  cc->have_v = cc->have_G = false;
+}
+
+// out = (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2) s on the coarse grid
+void coarse_split(reg3_ctx* c, const float* s, float* out) {
+  reg3_ctx* cc = c->coarse;
+  spectral3(cc, OP3_REGPOW, -0.5, s, 3, c->pc_u, 3, nullptr);
+  hessian(cc, c->pc_u, c->pc_q, true);
+  spectral3(cc, OP3_REGPOW, -0.5, c->pc_q, 3, out, 3, s);
+  ++c->coarse_matvecs;
+}
+
+// CHEB(k) with the bounds [emin, emax] on the coarse split operator, from
+// x = 0: the three-term Chebyshev iteration (k updates, k - 1 operator
+// applications)
+void cheb(reg3_ctx* c, const float* b, float* x) {
+  const long long n = 3 * c->coarse->d.N;
+  const double theta = 0.5 * (c->emax + c->emin), delta = 0.5 * (c->emax - c->emin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  check(c, cudaMemcpyAsync(c->pc_r, b, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  launch_lincomb(n, (float)(1.0 / theta), b, 0.f, nullptr, c->pc_d, c->st);
+  launch_fill(x, n, 0.f, c->st);
+  const int k = c->opt.cheb_iters;
+  for (int it = 0; it < k; ++it) {
+    launch_lincomb(n, 1.f, x, 1.f, c->pc_d, x, c->st);
+    if (it == k - 1) break;
+    coarse_split(c, c->pc_d, c->pc_w);
+    launch_lincomb(n, 1.f, c->pc_r, -1.f, c->pc_w, c->pc_r, c->st);
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    launch_lincomb(n, (float)(rho_new * rho), c->pc_d, (float)(2.0 * rho_new / delta), c->pc_r,
+                   c->pc_d, c->st);
+    rho = rho_new;
+  }
+}
+
+// largest eigenvalue of the symmetric tridiagonal matrix (diagonal a,
+// off-diagonal b) by bisection on the Sturm sequence count
+double tridiag_largest(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  if (m == 0) return 0.0;
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::fmin(lo, a[i] - r);
+    hi = std::fmax(hi, a[i] + r);
+  }
+  auto below = [&](double x) {   // number of eigenvalues below x
+    int cnt = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      q = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      cnt += q < 0.0;
+    }
+    return cnt;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fmax(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) == m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Chebyshev bounds of the coarse split operator at v = 0 (§3.4.2 "Eigenvalue
+// Estimates"): e_max from lanczos_steps Lanczos steps (FP32 vectors, FP64
+// inner products, SplitMix64 start vector of lanczos_seed) times
+// emax_safety; e_min = min over the coarse modes of 1 + 1/(beta gamma_k)
+void estimate_eig(reg3_ctx* c) {
+  reg3_ctx* cc = c->coarse;
+  const long long n = 3 * cc->d.N;
+  launch_fill(c->pc_v, n, 0.f, c->st);
+  set_velocity(cc, c->pc_v);
+  float* q = c->pc_r;
+  float* qprev = c->pc_d;
+  float* w = c->pc_w;
+  launch_splitmix(q, n, c->opt.lanczos_seed, c->st);
+  const double nq = std::sqrt(dot_sync(cc, q, q, n));
+  launch_lincomb(n, (float)(1.0 / nq), q, 0.f, nullptr, q, c->st);
+  launch_fill(qprev, n, 0.f, c->st);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int k = 0; k < c->opt.lanczos_steps; ++k) {
+    coarse_split(c, q, w);
+    const double alpha = dot_sync(cc, q, w, n);
+    launch_lincomb(n, 1.f, w, (float)-alpha, q, w, c->st);
+    launch_lincomb(n, 1.f, w, (float)-beta, qprev, w, c->st);
+    al.push_back(alpha);
+    const double bn = std::sqrt(dot_sync(cc, w, w, n));
+    if (!(bn > 1e-12 * std::fabs(alpha))) break;
+    be.push_back(bn);
+    std::swap(qprev, q);
+    launch_lincomb(n, (float)(1.0 / bn), w, 0.f, nullptr, q, c->st);
+    beta = bn;
+  }
+  be.resize(al.empty() ? 0 : al.size() - 1);
+  const double kn = 0.25 * ((double)cc->d.n1 * cc->d.n1 + (double)cc->d.n2 * cc->d.n2 +
+                            (double)cc->d.n3 * cc->d.n3);
+  c->emin = 1.0 + 1.0 / (c->beta * std::pow(kn, c->opt.reg_norm));
+  c->emax = tridiag_largest(al, be) * c->opt.emax_safety;
+  c->have_eig = true;
+}
+
+// the coarse problem at the restriction of v
+void set_velocity_coarse(reg3_ctx* c, const float* v) {
+  restrict_to_coarse(c, v, c->pc_v);
+  set_velocity(c->coarse, c->pc_v);
+}
+
+// z = P_2L^-1 r: one fine transform of r, the high band kept in spectral form
+// while CHEB(k) solves the coarse split system for the low band, then one
+// fine transform of (beta A)^-1/2 (P s_c + H r'), r' = (beta A)^-1/2 r
+void precond_2l(reg3_ctx* c, const float* r, float* z) {
+  reg3_ctx* cc = c->coarse;
+  const long long Nf = c->d.N, Nc = cc->d.N;
+  const float b = (float)c->beta;
+  const int p = c->opt.reg_norm;
+  launch_k(k3_pack_pairs, dim3(nb(Nf), 2), dim3(kT), 0, c->st, r, 3, c->zA, Nf);
+  fft3(c, c->zA, 2, false);
+  launch_k(k3_restrict_spec, dim3(nb(Nc)), dim3(kT), 0, c->st, c->d, cc->d, 2, 1.f / (float)Nf, b, p,
+           -0.5f, (const float2*)c->zA, cc->zB);
+  launch_k(k3_highpass_spec, dim3(nb(Nf)), dim3(kT), 0, c->st, c->d, 2, b, p, -0.5f,
+           (const float2*)c->zA, c->zB);
+  fft3(cc, cc->zB, 2, true);
+  launch_k(k3_unpack_pairs, dim3(nb(Nc), 2), dim3(kT), 0, c->st, (const float2*)cc->zB, 0, 0, 3,
+           c->pc_rc, (const float*)nullptr, Nc);
+  cheb(c, c->pc_rc, c->pc_sc);
+  launch_k(k3_pack_pairs, dim3(nb(Nc), 2), dim3(kT), 0, c->st, (const float*)c->pc_sc, 3, cc->zA, Nc);
+  fft3(cc, cc->zA, 2, false);
+  launch_k(k3_prolong_spec, dim3(nb(Nf)), dim3(kT), 0, c->st, c->d, cc->d, 2, 1.f / (float)Nc,
+           (const float2*)cc->zA, 1.f / (float)Nf, (const float2*)c->zB, b, p, -0.5f, c->zA);
+  fft3(c, c->zA, 2, true);
+  launch_k(k3_unpack_pairs, dim3(nb(Nf), 2), dim3(kT), 0, c->st, (const float2*)c->zA, 0, 0, 3, z,
+           (const float*)nullptr, Nf);
+  check_launch(c, "P_2L");
+}
+
+// the configured preconditioner inverse
+void precond(reg3_ctx* c, const float* r, float* z) {
+  if (c->coarse)
+    precond_2l(c, r, z);
+  else
+    spectral3(c, OP3_REGPOW, -1.0, r, 3, z, 3, nullptr);
 }
 
 bool size_ok3(int n) { return n % 32 == 0 && fft_axis_supported(n); }
@@ -1099,6 +1392,10 @@ reg_status guarded(reg3_ctx* c, const std::function<void()>& body) {
     }
   } catch (const D3Error& e) {
     s = e.s;
+    if (c->coarse && !c->coarse->err.empty()) {
+      c->err = "coarse grid: " + c->coarse->err;
+      c->coarse->err.clear();
+    }
   }
   t_programmatic_launch = saved;
   t_plain_fp32_reduce = saved_prec;
@@ -1117,8 +1414,15 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
     return REG_EINVAL;
   reg_options o;
   if (opt) o = *opt; else reg_default_options(&o);
+  const bool two_level = o.precond == REG_PC_2L;
+  if (two_level &&
+      (!size_ok3(n1 / 2) || !size_ok3(n2 / 2) || !size_ok3(n3 / 2) || n1 % 2 || n2 % 2 || n3 % 2 ||
+       o.pc_solver != REG_PCSOLVER_CHEB || o.cheb_iters < 1 || o.lanczos_steps < 1 ||
+       !(o.emax_safety >= 1.0) || (o.coarse_nt != 0 && o.coarse_nt != nt) ||
+       (o.coarse_interp != -1 && o.coarse_interp != o.interp)))
+    return REG_EINVAL;
   if (o.reg_norm < 1 || o.reg_norm > 3 || (o.interp != 0 && o.interp != 1) ||
-      o.precond != REG_PC_REG || o.hessian != REG_HESSIAN_GN || o.incompressible ||
+      (o.precond != REG_PC_REG && !two_level) || o.hessian != REG_HESSIAN_GN || o.incompressible ||
       o.beta_w != 0.0 || o.max_pcg < 1 || o.max_newton < 0 || o.max_backtracks < 0)
     return REG_EINVAL;
   int dev = 0;
@@ -1165,6 +1469,16 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
     check(c, cudaFuncSetAttribute(k3b_departure, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
     check(c, cudaFuncSetAttribute(k3b_adjoint_step, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
     check(c, cudaFuncSetAttribute(k3b_incstate_step, cudaFuncAttributeMaxDynamicSharedMemorySize, maxb), "attr");
+    if (two_level) {   // the coarse problem: same nt, model and options, P_REG inside
+      reg_options oc = o;
+      oc.precond = REG_PC_REG;
+      const reg_status sc = reg3_create(n1 / 2, n2 / 2, n3 / 2, nt, beta, &oc, &c->coarse);
+      if (sc != REG_OK) fail(c, sc, "coarse-grid context");
+      const size_t Nc = (size_t)c->coarse->d.N;
+      float** cvec[] = {&c->pc_rc, &c->pc_sc, &c->pc_r, &c->pc_d, &c->pc_w, &c->pc_u, &c->pc_q,
+                        &c->pc_v};
+      for (float** f : cvec) *f = dalloc<float>(c, 3 * Nc);
+    }
     check(c, cudaDeviceSynchronize(), "create");
   });
   if (s != REG_OK) {
@@ -1178,6 +1492,7 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
 reg_status reg3_destroy(reg3_ctx* c) {
   if (!c) return REG_OK;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->coarse) reg3_destroy(c->coarse);
   for (void* p : c->allocs) cudaFree(p);
   if (c->hsc) cudaFreeHost(c->hsc);
   delete c;
@@ -1187,6 +1502,7 @@ reg_status reg3_destroy(reg3_ctx* c) {
 reg_status reg3_set_stream(reg3_ctx* c, void* stream) {
   if (!c) return REG_EINVAL;
   c->st = static_cast<cudaStream_t>(stream);
+  if (c->coarse) c->coarse->st = c->st;
   return REG_OK;
 }
 
@@ -1198,6 +1514,10 @@ reg_status reg3_set_images(reg3_ctx* c, const float* mR, const float* mT) {
     check(c, cudaMemcpyAsync(c->mT, mT, n, cudaMemcpyDeviceToDevice, c->st), "copy m_T");
     c->have_images = true;
     c->have_v = c->have_G = false;
+    if (c->coarse) {
+      restrict_images(c);
+      c->have_eig = false;
+    }
   });
 }
 
@@ -1316,6 +1636,8 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
     const double gref_inf = maxabs(c->gcur);
     const double gref_2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
     inf.gref_inf = gref_inf;
+    const int cm0 = c->coarse_matvecs;
+    if (c->coarse && !c->have_eig) estimate_eig(c);
     set_velocity(c, v);
     double J = objective(c);
     inf.J0 = J;
@@ -1329,12 +1651,13 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
       if (k == o.max_newton) { result = REG_ENOTCONV; break; }
       const double g2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
       const double eta = std::fmin(0.5, g2 / gref_2);
+      if (c->coarse) set_velocity_coarse(c, v);
       // PCG (Hestenes-Stiefel) on H s = -g from s = 0 with P_REG
       launch_lincomb(n, -1.f, c->gcur, 0.f, nullptr, c->rhs, c->st);
       launch_fill(c->kx, n, 0.f, c->st);
       check(c, cudaMemcpyAsync(c->kr, c->rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
       const double bnorm = std::sqrt(dot_sync(c, c->rhs, c->rhs, n));
-      spectral3(c, OP3_REGPOW, -1.0, c->kr, 3, c->kz, 3, nullptr);
+      precond(c, c->kr, c->kz);
       check(c, cudaMemcpyAsync(c->kp, c->kz, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
       double rz = dot_sync(c, c->kr, c->kz, n);
       for (int it = 0; it < o.max_pcg && bnorm > 0.0; ++it) {
@@ -1352,7 +1675,7 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
         ++inf.pcg_iters;
         const double rr = dot_sync(c, c->kr, c->kr, n);
         if (std::sqrt(rr) / bnorm <= eta) break;
-        spectral3(c, OP3_REGPOW, -1.0, c->kr, 3, c->kz, 3, nullptr);
+        precond(c, c->kr, c->kz);
         const double rz_new = dot_sync(c, c->kr, c->kz, n);
         launch_lincomb(n, 1.f, c->kz, (float)(rz_new / rz), c->kp, c->kp, c->st);
         rz = rz_new;
@@ -1382,6 +1705,7 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
     inf.J = J;
     inf.gnorm_rel = rel;
     inf.gnorm_inf = ginf;
+    inf.coarse_matvecs = c->coarse_matvecs - cm0;
     check(c, cudaStreamSynchronize(c->st), "synchronize");
   });
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1389,6 +1713,31 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
   inf.status = result;
   if (info) *info = inf;
   return result;
+}
+
+reg_status reg3_precond_apply(reg3_ctx* c, const float* v, const float* r, float* z) {
+  if (!c || !v || !r || !z || r == z || unaligned(v) || unaligned(r) || unaligned(z)) return REG_EINVAL;
+  return guarded(c, [&] {
+    if (c->coarse) {
+      if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
+      if (!c->have_eig) estimate_eig(c);
+      set_velocity_coarse(c, v);
+    }
+    precond(c, r, z);
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+  });
+}
+
+reg_status reg3_eigen_bounds(reg3_ctx* c, double* emin, double* emax) {
+  if (!c || !emin || !emax) return REG_EINVAL;
+  return guarded(c, [&] {
+    if (!c->coarse) fail(c, REG_EINVAL, "the context runs P_REG");
+    if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
+    estimate_eig(c);
+    check(c, cudaStreamSynchronize(c->st), "synchronize");
+    *emin = c->emin;
+    *emax = c->emax;
+  });
 }
 
 const char* reg3_last_error(const reg3_ctx* c) { return c ? c->err.c_str() : "null context"; }

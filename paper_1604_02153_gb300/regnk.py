@@ -118,6 +118,8 @@ _SIGNATURES = {
     "reg3_transport": [_P, _P, _P, _P],
     "reg3_spectral": [_P, _I, _D, _P, _P],
     "reg3_deformation_map": [_P, _P, _P, _P],
+    "reg3_precond_apply": [_P, _P, _P, _P],
+    "reg3_eigen_bounds": [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     "reg3_objective_gradient": [_P, _P, ctypes.POINTER(_D), _P],
     "reg3_hessian_matvec": [_P, _P, _P, _P],
     "reg3_solve": [_P, _P, _D, ctypes.POINTER(reg_info)],
@@ -433,7 +435,8 @@ class Registration3:
     """reg3_ctx: the registration problem on an n1 x n2 x n3 periodic grid.
     Fields are contiguous float32 CUDA tensors (x_1 fastest), vector fields
     their three components back to back. Options as reg_options; precond
-    defaults to P_REG here, the form the 3D context requires."""
+    defaults to P_REG here (REG_PC_2L, the two-level preconditioner with
+    CHEB(k), needs every n_i / 2 to be a supported size)."""
 
     def __init__(self, n1, n2, n3, nt, beta, **options):
         self.lib = load()
@@ -462,6 +465,15 @@ class Registration3:
     def transport(self, v, m0, m1):
         self._call("reg3_transport", _ptr(v, 3 * self.N, "v"), _ptr(m0, self.N, "m0"),
                    _ptr(m1, self.N, "m1"))
+
+    def precond_apply(self, v, r, z):
+        self._call("reg3_precond_apply", _ptr(v, 3 * self.N, "v"), _ptr(r, 3 * self.N, "r"),
+                   _ptr(z, 3 * self.N, "z"))
+
+    def eigen_bounds(self):
+        lo, hi = ctypes.c_double(), ctypes.c_double()
+        self._call("reg3_eigen_bounds", ctypes.byref(lo), ctypes.byref(hi))
+        return lo.value, hi.value
 
     def deformation_map(self, v, u, det=None):
         self._call("reg3_deformation_map", _ptr(v, 3 * self.N, "v"), _ptr(u, 3 * self.N, "u"),
