@@ -293,3 +293,29 @@ def test_two_level_solve_matches_oracle(regnk):
     assert info["matvecs"] < ir["matvecs"]
     R.close()
     Rr.close()
+
+
+def test_rejected_arguments_3d(regnk):
+    """reg3_create refuses axis lengths it has no FFT or tiles for, P_2L
+    whose coarse grid would not be one, and the variants the 3D context does
+    not run; a P_REG context has no Chebyshev bounds; a gradient before the
+    images is a state error; the binding checks tensor sizes."""
+    with pytest.raises(regnk.RegError):
+        regnk.Registration3(48, 64, 64, 4, 1e-2)
+    with pytest.raises(regnk.RegError):
+        regnk.Registration3(32, 64, 64, 4, 1e-2, precond=regnk.REG_PC_2L)
+    with pytest.raises(regnk.RegError):
+        regnk.Registration3(64, 64, 64, 4, 1e-2, precond=regnk.REG_PC_2L,
+                            pc_solver=regnk.REG_PCSOLVER_PCG)
+    with pytest.raises(regnk.RegError):
+        regnk.Registration3(64, 64, 64, 4, 1e-2, incompressible=1)
+    R = regnk.Registration3(32, 32, 32, 4, 1e-2)
+    with pytest.raises(regnk.RegError):
+        R.eigen_bounds()
+    v = torch.zeros(3 * R.N, device="cuda")
+    g = torch.empty(3 * R.N, device="cuda")
+    with pytest.raises(regnk.RegError):
+        R.objective_gradient(v, g)
+    with pytest.raises(ValueError):
+        R.spectral(regnk.REG_SPEC_GRAD, torch.empty(R.N + 4, device="cuda"), g)
+    R.close()
