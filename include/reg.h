@@ -422,7 +422,8 @@ const char* reg_batch_last_error(const reg_batch* batch);
  * pointers, 16-byte aligned, owned by the caller. n_i in {32, 64, 128, 256,
  * 96, 192}. Options as reg_create: precond REG_PC_REG (the spectral
  * preconditioner) or REG_PC_2L (the two-level preconditioner of §3.4.2 with
- * CHEB(cheb_iters) coarse solves; every n_i / 2 must be a supported size,
+ * CHEB(cheb_iters) or PCG(pc_eps * eta) coarse solves, eta the Newton step's
+ * forcing term (0.5 outside a solve); every n_i / 2 must be a supported size,
  * the coarse problem has the same nt and interpolation model), compressible,
  * Gauss-Newton; anything else REG_EINVAL. Calls run on the stream of reg3_set_stream (default stream
  * otherwise). reg3_create allocates (74 + 7 nt) n1 n2 n3 floats of device

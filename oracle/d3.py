@@ -413,7 +413,8 @@ class Solver3:
     two-level preconditioner P_2L of §3.4.2, read as solver.Solver reads it
     in 2D:
         r'  = (beta A)^-1/2 r,  r_c = R r',
-        s_c = (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2)^-1 r_c  by CHEB(k),
+        s_c = (I + (beta A_c)^-1/2 Q_c (beta A_c)^-1/2)^-1 r_c  by CHEB(k)
+              or PCG(eps * eta_k) (pc_solver "cheb" or "pcg"),
         z   = (beta A)^-1/2 (P s_c + H r')
     with R, P the spectral restriction and prolongation, H the high-pass
     filter and Q_c the Gauss-Newton data term of the coarse problem (m_R,
@@ -424,9 +425,12 @@ class Solver3:
 
     def __init__(self, problem, precond="2L", cheb_iters=10, gabs=1e-5, max_newton=50,
                  max_pcg=100, lanczos_steps=30, emax_safety=1.05, lanczos_v0=None, c1=1e-4,
-                 max_backtracks=10):
+                 max_backtracks=10, pc_solver="cheb", pc_eps=0.1):
         self.p = problem
         self.precond = precond
+        self.pc_solver = pc_solver
+        self.pc_eps = pc_eps
+        self.eta = 0.5
         self.cheb_iters = cheb_iters
         self.gabs = gabs
         self.max_newton = max_newton
@@ -471,8 +475,12 @@ class Solver3:
         if self.precond == "REG":
             return reg_power(r, p.beta, p.reg_norm, -1)
         r1 = reg_power(r, p.beta, p.reg_norm, -0.5)
-        sc, _ = krylov.chebyshev(self.coarse_split_op, restrict_vec3(r1), self.eig["emin"],
-                                 self.eig["emax"], self.cheb_iters)
+        if self.pc_solver == "cheb":
+            sc, _ = krylov.chebyshev(self.coarse_split_op, restrict_vec3(r1), self.eig["emin"],
+                                     self.eig["emax"], self.cheb_iters)
+        else:
+            sc, _ = krylov.pcg(self.coarse_split_op, restrict_vec3(r1), lambda x: x,
+                               self.pc_eps * self.eta, self.max_pcg)
         return reg_power(prolong_vec3(sc) + highpass_vec3(r1), p.beta, p.reg_norm, -0.5)
 
     def solve(self, v0, gtol):
@@ -482,7 +490,7 @@ class Solver3:
         _, g_ref = p.objective_gradient(z)
         gref_inf = float(np.max(np.abs(g_ref)))
         gref_2 = float(np.sqrt(np.sum(g_ref * g_ref)))
-        if self.precond == "2L" and self.eig is None:
+        if self.precond == "2L" and self.pc_solver == "cheb" and self.eig is None:
             self.estimate_eigenvalues()
         v = np.array(v0, dtype=np.float64, copy=True)
         J, g = p.objective_gradient(v)
@@ -495,6 +503,7 @@ class Solver3:
             if rel <= gtol or ginf <= self.gabs or k == self.max_newton:
                 break
             eta = min(0.5, float(np.sqrt(np.sum(g * g))) / gref_2)
+            self.eta = eta
             if self.coarse is not None:
                 self.coarse.state_solve(restrict_vec3(v))
             vt, kinfo = krylov.pcg(p.hessian_matvec, -g, self.apply_precond, eta, self.max_pcg)

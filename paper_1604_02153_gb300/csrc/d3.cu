@@ -878,6 +878,7 @@ struct reg3_ctx {
   double emin = 0, emax = 0;
   bool have_eig = false;
   int coarse_matvecs = 0;
+  double eta = 0.5;   // forcing term of the Newton step (PCG(eps eta) coarse solves)
   float *pc_rc = nullptr, *pc_sc = nullptr, *pc_r = nullptr, *pc_d = nullptr, *pc_w = nullptr,
         *pc_u = nullptr, *pc_q = nullptr, *pc_v = nullptr;
   std::vector<void*> allocs;
@@ -1264,6 +1265,39 @@ void cheb(reg3_ctx* c, const float* b, float* x) {
   }
 }
 
+// PCG(rtol) without preconditioner on the coarse split operator from x = 0
+// (the steps of the outer PCG: stop at ||r|| <= rtol ||b||, keep the
+// current iterate at a non-positive curvature, b itself at the first step)
+void coarse_pcg(reg3_ctx* c, const float* b, float* x, double rtol) {
+  reg3_ctx* cc = c->coarse;
+  const long long n = 3 * cc->d.N;
+  launch_fill(x, n, 0.f, c->st);
+  const double bnorm = std::sqrt(dot_sync(cc, b, b, n));
+  if (!(bnorm > 0.0)) return;
+  float* r = c->pc_r;
+  float* p = c->pc_d;
+  float* q = c->pc_w;
+  check(c, cudaMemcpyAsync(r, b, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  check(c, cudaMemcpyAsync(p, b, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+  double rz = bnorm * bnorm;
+  for (int it = 0; it < c->opt.max_pcg; ++it) {
+    coarse_split(c, p, q);
+    const double pq = dot_sync(cc, p, q, n);
+    if (!(pq > 0.0)) {
+      if (it == 0)
+        check(c, cudaMemcpyAsync(x, b, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st), "copy");
+      break;
+    }
+    const float alpha = (float)(rz / pq);
+    launch_lincomb(n, 1.f, x, alpha, p, x, c->st);
+    launch_lincomb(n, 1.f, r, -alpha, q, r, c->st);
+    const double rr = dot_sync(cc, r, r, n);
+    if (std::sqrt(rr) / bnorm <= rtol) break;
+    launch_lincomb(n, 1.f, r, (float)(rr / rz), p, p, c->st);
+    rz = rr;
+  }
+}
+
 // largest eigenvalue of the symmetric tridiagonal matrix (diagonal a,
 // off-diagonal b) by bisection on the Sturm sequence count
 double tridiag_largest(const std::vector<double>& a, const std::vector<double>& b) {
@@ -1338,7 +1372,8 @@ void set_velocity_coarse(reg3_ctx* c, const float* v) {
 }
 
 // z = P_2L^-1 r: one fine transform of r, the high band kept in spectral form
-// while CHEB(k) solves the coarse split system for the low band, then one
+// while CHEB(k) or PCG(eps eta) solves the coarse split system for the low
+// band, then one
 // fine transform of (beta A)^-1/2 (P s_c + H r'), r' = (beta A)^-1/2 r
 void precond_2l(reg3_ctx* c, const float* r, float* z) {
   reg3_ctx* cc = c->coarse;
@@ -1354,7 +1389,10 @@ void precond_2l(reg3_ctx* c, const float* r, float* z) {
   fft3(cc, cc->zB, 2, true);
   launch_k(k3_unpack_pairs, dim3(nb(Nc), 2), dim3(kT), 0, c->st, (const float2*)cc->zB, 0, 0, 3,
            c->pc_rc, (const float*)nullptr, Nc);
-  cheb(c, c->pc_rc, c->pc_sc);
+  if (c->opt.pc_solver == REG_PCSOLVER_PCG)
+    coarse_pcg(c, c->pc_rc, c->pc_sc, c->opt.pc_eps * c->eta);
+  else
+    cheb(c, c->pc_rc, c->pc_sc);
   launch_k(k3_pack_pairs, dim3(nb(Nc), 2), dim3(kT), 0, c->st, (const float*)c->pc_sc, 3, cc->zA, Nc);
   fft3(cc, cc->zA, 2, false);
   launch_k(k3_prolong_spec, dim3(nb(Nf)), dim3(kT), 0, c->st, c->d, cc->d, 2, 1.f / (float)Nc,
@@ -1417,7 +1455,9 @@ reg_status reg3_create(int n1, int n2, int n3, int nt, double beta, const reg_op
   const bool two_level = o.precond == REG_PC_2L;
   if (two_level &&
       (!size_ok3(n1 / 2) || !size_ok3(n2 / 2) || !size_ok3(n3 / 2) || n1 % 2 || n2 % 2 || n3 % 2 ||
-       o.pc_solver != REG_PCSOLVER_CHEB || o.cheb_iters < 1 || o.lanczos_steps < 1 ||
+       (o.pc_solver != REG_PCSOLVER_CHEB && o.pc_solver != REG_PCSOLVER_PCG) ||
+       (o.pc_solver == REG_PCSOLVER_PCG && !(o.pc_eps > 0.0)) || o.cheb_iters < 1 ||
+       o.lanczos_steps < 1 ||
        !(o.emax_safety >= 1.0) || (o.coarse_nt != 0 && o.coarse_nt != nt) ||
        (o.coarse_interp != -1 && o.coarse_interp != o.interp)))
     return REG_EINVAL;
@@ -1637,7 +1677,8 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
     const double gref_2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
     inf.gref_inf = gref_inf;
     const int cm0 = c->coarse_matvecs;
-    if (c->coarse && !c->have_eig) estimate_eig(c);
+    const bool use_cheb = c->coarse && o.pc_solver == REG_PCSOLVER_CHEB;
+    if (use_cheb && !c->have_eig) estimate_eig(c);
     set_velocity(c, v);
     double J = objective(c);
     inf.J0 = J;
@@ -1651,6 +1692,7 @@ reg_status reg3_solve(reg3_ctx* c, float* v, double gtol, reg_info* info) {
       if (k == o.max_newton) { result = REG_ENOTCONV; break; }
       const double g2 = std::sqrt(dot_sync(c, c->gcur, c->gcur, n));
       const double eta = std::fmin(0.5, g2 / gref_2);
+      c->eta = eta;
       if (c->coarse) set_velocity_coarse(c, v);
       // PCG (Hestenes-Stiefel) on H s = -g from s = 0 with P_REG
       launch_lincomb(n, -1.f, c->gcur, 0.f, nullptr, c->rhs, c->st);
@@ -1720,7 +1762,7 @@ reg_status reg3_precond_apply(reg3_ctx* c, const float* v, const float* r, float
   return guarded(c, [&] {
     if (c->coarse) {
       if (!c->have_images) fail(c, REG_ESTATE, "reg3_set_images has not been called");
-      if (!c->have_eig) estimate_eig(c);
+      if (c->opt.pc_solver == REG_PCSOLVER_CHEB && !c->have_eig) estimate_eig(c);
       set_velocity_coarse(c, v);
     }
     precond(c, r, z);

@@ -264,21 +264,25 @@ def test_two_level_preconditioner(regnk):
     R.close()
 
 
-def test_two_level_solve_matches_oracle(regnk):
-    """The Newton-Krylov solve with P_2L (CHEB(10)) on 64^3 against the
-    oracle's (the same Lanczos start vector): the same Newton iterations,
-    PCG iterations within one, v within the stated 1e-3 and J within 1e-4;
-    P_2L needs fewer fine-grid matvecs than P_REG on the same problem."""
+@pytest.mark.parametrize("pc", ["cheb", "pcg"])
+def test_two_level_solve_matches_oracle(regnk, pc):
+    """The Newton-Krylov solve with P_2L (CHEB(10), or nested PCG(0.1 eta))
+    on 64^3 against the oracle's (the same Lanczos start vector): the same
+    Newton iterations, PCG iterations within one, v within the stated 1e-3
+    and J within 1e-4; P_2L needs fewer fine-grid matvecs than P_REG on the
+    same problem."""
     n, nt, beta, gtol = 64, 4, 1e-2, 1e-2
     m_R, m_T = two_level_problem(n, nt, beta)
-    R = regnk.Registration3(n, n, n, nt, beta, precond=regnk.REG_PC_2L)
+    R = regnk.Registration3(n, n, n, nt, beta, precond=regnk.REG_PC_2L,
+                            pc_solver=regnk.REG_PCSOLVER_CHEB if pc == "cheb"
+                            else regnk.REG_PCSOLVER_PCG)
     R.set_images(dev(m_R), dev(m_T))
     v = torch.zeros(3 * R.N, device="cuda")
     info = R.solve(v, gtol)
     nc = n // 2
     v0 = inputs.splitmix64_uniform(3 * nc ** 3, regnk.default_options().lanczos_seed)
     S = d3.Solver3(d3.Problem3(m_R, m_T, nt, beta), precond="2L",
-                   lanczos_v0=v0.reshape(3, nc, nc, nc))
+                   lanczos_v0=v0.reshape(3, nc, nc, nc), pc_solver=pc)
     vo, oinfo = S.solve(np.zeros((3, n, n, n)), gtol)
     assert info["gnorm_rel"] <= gtol
     assert info["newton_iters"] == oinfo["newton_iters"]
@@ -297,8 +301,8 @@ def test_two_level_solve_matches_oracle(regnk):
 
 def test_rejected_arguments_3d(regnk):
     """reg3_create refuses axis lengths it has no FFT or tiles for, P_2L
-    whose coarse grid would not be one, and the variants the 3D context does
-    not run; a P_REG context has no Chebyshev bounds; a gradient before the
+    whose coarse grid would not be one or whose nested PCG has no tolerance,
+    and the variants the 3D context does not run; a P_REG context has no Chebyshev bounds; a gradient before the
     images is a state error; the binding checks tensor sizes."""
     with pytest.raises(regnk.RegError):
         regnk.Registration3(48, 64, 64, 4, 1e-2)
@@ -306,7 +310,7 @@ def test_rejected_arguments_3d(regnk):
         regnk.Registration3(32, 64, 64, 4, 1e-2, precond=regnk.REG_PC_2L)
     with pytest.raises(regnk.RegError):
         regnk.Registration3(64, 64, 64, 4, 1e-2, precond=regnk.REG_PC_2L,
-                            pc_solver=regnk.REG_PCSOLVER_PCG)
+                            pc_solver=regnk.REG_PCSOLVER_PCG, pc_eps=0.0)
     with pytest.raises(regnk.RegError):
         regnk.Registration3(64, 64, 64, 4, 1e-2, incompressible=1)
     R = regnk.Registration3(32, 32, 32, 4, 1e-2)

@@ -271,3 +271,31 @@ def test_solver3_two_level_reduces_to_the_2d_solve():
     vb, ib = d3.Solver3(d3.Problem3(m_R3, m_T3, nt, beta), precond="REG").solve(np.zeros((3, n, n, n)), gtol)
     assert ia["newton_iters"] == ib["newton_iters"] and ia["pcg_iters"] == ib["pcg_iters"]
     assert np.max(np.abs(va - vb)) == 0.0
+
+
+def test_solver3_nested_pcg_reduces_to_the_2d_solve():
+    """P_2L with nested PCG(eps eta) coarse solves on a problem constant along
+    x_3: no Chebyshev bounds enter, so the 3D solve is the 2D oracle's
+    (Newton steps, matvecs, coarse matvecs of the nested solves and the
+    solution)."""
+    from oracle.solver import Solver
+    n, n3, nt, beta, gtol = 16, 8, 4, 1e-2, 1e-2
+    m_T, vstar = inputs.sinusoid_pair(n)
+    m_R = Problem(np.zeros((n, n)), m_T, nt, beta).state_solve(vstar)
+    tile = lambda a, k: np.repeat(a[None], k, axis=0)
+    S3 = d3.Solver3(d3.Problem3(tile(m_R, n3), tile(m_T, n3), nt, beta), precond="2L",
+                    pc_solver="pcg")
+    S2 = Solver(Problem(m_R, m_T, nt, beta), precond="2L", pc_solver="pcg")
+    v2, i2 = S2.solve(np.zeros((2, n, n)), gtol)
+    v3, i3 = S3.solve(np.zeros((3, n3, n, n)), gtol)
+    assert i3["newton_iters"] == i2["newton_iters"] and i3["matvecs"] == i2["matvecs"]
+    # the 2D solver runs its Lanczos estimate (30 coarse matvecs) before any
+    # P_2L solve; Solver3 only when CHEB needs the bounds
+    assert i3["coarse_matvecs"] == i2["coarse_matvecs"] - S2.lanczos_steps
+    # CG to a tolerance on the coarse split operator (not symmetric to the
+    # SL scheme's adjoint error) amplifies the FP64 rounding differences of
+    # the 2D and 3D transforms: the iterates agree to 1e-14 after one Newton
+    # step and 2.5e-5 after four, so the solution is held to the solve's 1e-3
+    for c in range(2):
+        assert np.max(np.abs(v3[c] - tile(v2[c], n3))) < 1e-3 * np.max(np.abs(v2))
+    assert np.max(np.abs(v3[2])) < 1e-8 * np.max(np.abs(v2))
