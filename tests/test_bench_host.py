@@ -51,3 +51,19 @@ def test_single_rank_aggregation():
     import bench
     v, e = bench.aggregate_ranks(None, None, 2000.0, 40, 4000.0, 40)
     assert v == pytest.approx(20.0) and e == pytest.approx(10.0)
+
+
+def test_3d_matvec_bytes_count_each_kernel():
+    """The algorithmic bytes per point of a 3D GN matvec add up its kernels:
+    spline prefilter of v~ (3 fields x 3 axis passes x 8 B), the first
+    incremental step (v~ and G at X_D, v~, grad m, m~ out: 76 B), nt - 1
+    further steps with their prefilters, lambda~_nt with the first term of
+    b~, nt adjoint steps with their prefilters, and the spectral beta A v~ +
+    b~ on two packed complex fields (292 B); cubic Lagrange drops every
+    prefilter pass."""
+    import bench
+    for nt in (1, 2, 4, 8):
+        spline = 3 * 24 + 76 + (nt - 1) * (68 + 24) + 32 + nt * (64 + 24) + 292
+        assert bench.d3_bytes_per_point(nt) == spline == 380 + 180 * nt
+        lag = 76 + (nt - 1) * 68 + 32 + nt * 64 + 292
+        assert bench.d3_bytes_per_point(nt, lagrange=True) == lag
