@@ -436,7 +436,8 @@ class Registration3:
     Fields are contiguous float32 CUDA tensors (x_1 fastest), vector fields
     their three components back to back. Options as reg_options; precond
     defaults to P_REG here (REG_PC_2L, the two-level preconditioner with
-    CHEB(k), needs every n_i / 2 to be a supported size)."""
+    CHEB(k) or nested PCG(eps) coarse solves, needs every n_i / 2 to be a
+    supported size). Methods carry the C names without the reg3_ prefix."""
 
     def __init__(self, n1, n2, n3, nt, beta, **options):
         self.lib = load()
