@@ -41,6 +41,10 @@ cpu_baseline / --impl reference = the FP64 numpy oracle on the host cores,
             timed on a bounded sample: one GN Hessian matvec at 1024^2, nt = 8
             on one core; one such matvec per core at once (process pool); and
             the 64^2 analytic problem solved to ||g||rel 1e-2 on one core.
+            The ratio of the two arms' values compares solve-level GPU
+            matvecs/s (gradients, line search and the coarse level included
+            in the time) with bare oracle matvecs/s: a deliberately slow
+            program, not a like-for-like rate.
 plain_form = the same solve with FP32 reductions, no CUDA graphs and plain
             launches (as many timed solves as the chosen form, after one
             warm-up, CUDA events): the "plain FP32" form the chosen one is
